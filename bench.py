@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput of the MPS time step (particle-steps/s) on the 3D dam break.
+
+Workload: 0.40 x 0.60 x 0.30 m water column in a 1.6 x 0.6 x 0.6 m open-top tank,
+l0 = 0.0075 m, 2 wall + 2 dummy layers to full height: 169,600 fluid + 270,432 wall/dummy
+= 440,032 particles; re_n = 2.1 l0, re_lap = 4 l0, dt = 5e-5 s, PPE by CG to a relative
+FP64 residual of 1e-8.  Synthetic seeded lattice with 1e-4 l0 jitter.
+
+The headline `value` is the mixed-precision path (FP32 pair terms and inner CG, FP64 number
+density, dot products and refinement); the plain FP64 path is timed on the same scene and
+reported under "fp64".  `e2e` repeats the mixed measurement through the C ABI with host
+buffers: every step uploads positions, velocities and kinds from pinned memory and reads
+back positions, velocities and pressure.
+
+--impl reference times the FP64 CPU oracle on the host cores on the same workload (one
+oracle step per bench step).
+
+Multi-GPU: a single scene does not shard (replicas only): each rank runs an independent
+replica and `value` sums the particle-steps of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "particle-steps/s (3D ~200k dam break) FP64 vs mixed at PPE resid 1e-8; % HBM peak"
+UNIT = "particle-steps/s"
+WORKLOAD = "3D dam break, 0.40x0.60x0.30 m column in 1.6x0.6x0.6 m tank, l0=0.0075 m"
+
+# Algorithmic bytes per particle per stage (matrix-free minimum: each array read or written
+# once per stage; neighbour re-reads served on chip).
+STAGE_BYTES = {
+    "bucket": 182.0,
+    "predict": {0: 97.0, 1: 113.0},
+    "build": 42.0,
+    "update": 146.0,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed steps of the FP64 comparison (default: --steps)")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--cpu-sample-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--l0", type=float, default=0.0075, help="particle spacing (testing only)")
+    ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
+                    help="time one precision only and print its stage profile (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}",
+                                       f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle_rate(sc, steps: int, threads: int | None = None):
+    import oracle
+    oracle.build()
+    if threads:
+        oracle.set_threads(threads)
+    used = oracle.get_threads()
+    prm = oracle.params_for(sc, dt=5e-5)
+    st = oracle.State.from_scene(sc)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.step(prm, st)
+    dt = time.perf_counter() - t0
+    return sc.n * steps / dt, used, dt
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    sc = scenes.dam_break_3d(seed=args.seed, l0=args.l0)
+    threads = os.cpu_count()
+    import oracle
+    oracle.build()
+    oracle.set_threads(threads)
+    prm = oracle.params_for(sc, dt=5e-5)
+    st = oracle.State.from_scene(sc)
+    for _ in range(args.warmup):
+        oracle.step(prm, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.step(prm, st)
+    dt = time.perf_counter() - t0
+    value = sc.n * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": sc.n, "fluid": sc.n_fluid, "dt": 5e-5,
+                   "cg_tol": 1e-8, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
+                         "kind": "oracle",
+                         "sample": f"{args.steps} oracle steps of the full workload after {args.warmup} warm-up steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU
+def run_gb300(args):
+    import torch
+
+    from paper_2105_01677_gb300 import mps
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # before any CUDA work: the oracle on the host cores, bounded sample
+        sc_cpu = scenes.dam_break_3d(seed=args.seed, l0=args.l0)
+        v, cores, secs = cpu_oracle_rate(sc_cpu, args.cpu_sample_steps, os.cpu_count())
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sample_steps} FP64 oracle steps of the full 440,032-particle "
+                         f"workload ({secs:.1f} s)"}
+
+    sc = scenes.dam_break_3d(seed=args.seed + rank, l0=args.l0)
+    n = sc.n
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+    common = dict(dt=5e-5, cg_tol=1e-8)
+
+    def timed_steps(sim, k, profile=False):
+        if profile:
+            mps.mps_set_profiling(sim.h, True)
+        total = 0.0
+        s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+        iters = []
+        for i in range(k):
+            flush.zero_()
+            s_ev[i].record(stream)
+            rc, rep = sim.step(1)
+            e_ev[i].record(stream)
+            iters.append((rep["cg_iters"], rep["cg_outer"], rep["cg_resid"]))
+        torch.cuda.synchronize(dev)
+        for i in range(k):
+            total += s_ev[i].elapsed_time(e_ev[i])
+        prof = mps.mps_get_profile(sim.h) if profile else None
+        return total, iters, prof
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    if args.only:
+        prec = 1 if args.only == "mixed" else 0
+        simo = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, precision=prec, **common)
+        simo.step(args.warmup)
+        barrier()
+        ms, its, prof = timed_steps(simo, args.steps, profile=True)
+        simo.close()
+        if rank == 0:
+            print(json.dumps({"only": args.only, "particles": n, "ms_per_step": ms / args.steps,
+                              "value": n * args.steps / (ms * 1e-3), "cg": its, "profile": prof}),
+                  flush=True)
+        return
+
+    # ---- mixed (headline)
+    sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, precision=1, **common)
+    sim.step(args.warmup)
+    clocks = ClockSampler(local)
+    barrier()
+    ms_mixed, it_mixed, prof = timed_steps(sim, args.steps, profile=True)
+    barrier()
+    clk = clocks.stop()
+    ms_mixed = max_over_ranks(ms_mixed)
+    sim.close()
+
+    # ---- plain FP64 on the same scene
+    k64 = args.fp64_steps or args.steps
+    sim64 = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, precision=0, **common)
+    sim64.step(args.warmup)
+    barrier()
+    ms_64, it_64, prof64 = timed_steps(sim64, k64, profile=True)
+    barrier()
+    ms_64 = max_over_ranks(ms_64)
+    sim64.close()
+
+    # ---- end to end through the C ABI with host buffers (mixed)
+    ke = args.e2e_steps or args.steps
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    h_pos = pin((n, 3), torch.float64)
+    h_vel = pin((n, 3), torch.float64)
+    h_typ = pin((n,), torch.int8)
+    h_p = pin((n,), torch.float64)
+    h_pos[:] = sc.pos
+    h_vel[:] = sc.vel
+    h_typ[:] = sc.types
+    sime = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, precision=1, **common)
+    for _ in range(args.warmup):
+        sime.write(h_pos, h_vel, h_typ)
+        sime.step(1)
+        sime.read(pos=h_pos, vel=h_vel, p=h_p, want=("pos", "vel", "p"))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        sime.write(h_pos, h_vel, h_typ)
+        sime.step(1)
+        sime.read(pos=h_pos, vel=h_vel, p=h_p, want=("pos", "vel", "p"))
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    sime.close()
+    h2d = h_pos.nbytes + h_vel.nbytes + h_typ.nbytes
+    d2h = h_pos.nbytes + h_vel.nbytes + h_p.nbytes
+
+    if rank != 0:
+        return
+
+    # ---- roofline of the dominant stage (live stage timers on the library's stream)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    st_ms = prof["stage_ms"]
+    st_calls = prof["stage_calls"]
+    per_call = {k: (st_ms[k] / st_calls[k] if st_calls[k] else 0.0) for k in st_ms}
+    top = max(per_call, key=per_call.get)
+    iters_mean = float(np.mean([x[0] for x in it_mixed]))
+    outer_mean = float(np.mean([x[1] for x in it_mixed]))
+    if top == "ppe":
+        bytes_unit = 57.0 * iters_mean + 65.0 * (outer_mean + 1)
+    else:
+        b = STAGE_BYTES[top]
+        bytes_unit = b[1] if isinstance(b, dict) else b
+    achieved = bytes_unit * n / (per_call[top] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "bytes_per_particle": bytes_unit,
+                "stage_ms_per_step": {k: per_call[k] for k in per_call},
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}
+
+    value = world * n * args.steps / (ms_mixed * 1e-3)
+    value64 = world * n * k64 / (ms_64 * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": n, "fluid": sc.n_fluid, "dt": 5e-5,
+                   "cg_tol": 1e-8, "precision": "mixed", "parallelism": f"replicas{world}",
+                   "l2": "flushed (512 MiB write) before every timed step",
+                   "fluid_particle_steps_per_s": world * sc.n_fluid * args.steps / (ms_mixed * 1e-3)},
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms_64 / k64, "steps": k64,
+                 "cg_iters_mean": float(np.mean([x[0] for x in it_64])),
+                 "stage_ms_per_step": {k: (prof64["stage_ms"][k] / prof64["stage_calls"][k]
+                                           if prof64["stage_calls"][k] else 0.0)
+                                       for k in prof64["stage_ms"]}},
+        "mixed_over_fp64": value / value64,
+        "cg": {"inner_iters_mean": iters_mean, "outer_mean": outer_mean,
+               "resid_max": float(max(x[2] for x in it_mixed))},
+        "e2e": {"value": world * n * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(prof["launches"]),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

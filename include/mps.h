@@ -1,0 +1,204 @@
+/*
+ * mps.h -- C ABI of the GB300 MPS time-step library.
+ *
+ * One Moving Particle Semi-implicit (MPS) time step, after Vieira-e-Silva et al., "A fluid
+ * simulation system based on the MPS method" (arXiv 2105.01677):
+ *   - cell-linked-list neighbour search (Sec. 5.1), here a Morton-sorted bucket grid;
+ *   - particle number density (Eq. 5), Laplacian model (Eq. 7) and pressure gradient
+ *     (difference form of the multi-density gradient, Sec. 3.2.1) with w(r) = re/r - 1 (Eq. 4);
+ *   - the pressure Poisson equation (Eq. 13) assembled as in the CUDA PPE listing of Sec. 5.3
+ *     and solved by conjugate gradients (Sec. 3.1.2), or
+ *   - the weakly-compressible equation-of-state pressure (Eq. 16).
+ *
+ * Conventions for every call:
+ *   - Return 0 (MPS_OK) on success or a negative MPS_E* code; mps_strerror() names it.
+ *   - Host pointers are ordinary (pageable or pinned) host memory owned by the caller; the
+ *     library only reads or writes them during the call.
+ *   - Particle arrays are indexed by the caller's particle id 0..n-1 ("original order").
+ *     Vector quantities are array-of-structs with `dim` doubles per particle (x, y[, z]).
+ *   - Particle kinds (int8): MPS_FLUID, MPS_WALL, MPS_DUMMY, MPS_GHOST.  WALL particles take
+ *     part in the PPE but never move; DUMMY particles only count towards the number density
+ *     (the "bcon == -1" particles of the PPE listing); GHOST particles are out of the domain
+ *     and ignored.  A particle that leaves the cell grid becomes a GHOST (not an error).
+ *   - Calls on one context are not thread-safe; different contexts are independent.
+ *   - Every call is synchronous with respect to the host: when it returns, its device work
+ *     is complete.
+ *   - The context owns all device memory it allocates (from `alloc`/`release` if given,
+ *     else cudaMalloc/cudaFree) until mps_destroy().
+ */
+#ifndef MPS_GB300_H
+#define MPS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Particle kinds. */
+#define MPS_FLUID 0
+#define MPS_WALL 1
+#define MPS_DUMMY 2
+#define MPS_GHOST 3
+
+/* Status codes. */
+#define MPS_OK 0
+#define MPS_EINVAL -1       /* bad argument: dim, radii, sizes, non-positive n, grid too large */
+#define MPS_ENOMEM -2       /* device or host allocation failed                              */
+#define MPS_ECG_NOCONV -3   /* CG did not reach cg_tol within cg_max_iter (report filled)    */
+#define MPS_ENONFINITE -4   /* NaN or Inf in a position or velocity                          */
+#define MPS_ESKIN -5        /* a particle moved more than half the cell skin within a step   */
+#define MPS_ECOINCIDENT -6  /* two neighbouring particles at distance 0 (w infinite, Eq. 4)  */
+#define MPS_ECAP -7         /* a caller buffer or the per-particle neighbour cap is too small */
+#define MPS_EDEVICE -8      /* a CUDA call failed or a device-side wait gave up              */
+
+/* Device memory hooks: alloc returns a device pointer of >= bytes (256-byte aligned) or
+ * NULL; release frees it.  Both receive `user`.  Both NULL: cudaMalloc / cudaFree. */
+typedef void* (*mps_alloc_fn)(size_t bytes, void* user);
+typedef void (*mps_release_fn)(void* ptr, void* user);
+
+typedef struct {
+    int32_t dim;              /* 2 or 3                                                        */
+    int32_t pressure_mode;    /* 0: PPE solved by CG (Eq. 13); 1: equation of state (Eq. 16)  */
+    double l0;                /* average particle distance [m]                                */
+    double re_n;              /* influence radius of number density, gradient, p_hat [m]      */
+    double re_lap;            /* influence radius of the Laplacian (viscosity, PPE) [m]       */
+    double rho;               /* density [kg/m^3]                                             */
+    double nu;                /* kinematic viscosity [m^2/s]                                  */
+    double dt;                /* time step [s]                                                */
+    double beta;              /* free-surface threshold of Eq. 15 (paper: 0.97)               */
+    double g[3];              /* external acceleration [m/s^2]                                */
+    double c0;                /* speed of sound of Eq. 16 [m/s]                               */
+    double gamma;             /* exponent of Eq. 16 (paper: 7)                                */
+    double alpha_c;           /* PPE diagonal term alpha_c/dt^2 (listing of Sec. 5.3: 1e-7)   */
+    double cg_tol;            /* stop when ||b - A p|| / ||b|| <= cg_tol (FP64 residual)       */
+    int32_t cg_max_iter;      /* total CG iteration cap per solve; <= 0: 10 n                 */
+    int32_t precision;        /* 0: FP64 throughout; 1: mixed (FP32 pair terms and inner CG,   *
+                               *    FP64 number density, dot products, residual, refinement)  */
+    int32_t clamp_negative_p; /* PPE only: p = max(p, 0) after the solve (default 1)          */
+    int32_t nbr_cap;          /* max stored non-dummy neighbours per particle within re_lap;   *
+                               * <= 0: 1.5x the ideal-lattice count, rounded up to 32          */
+    double cell_skin;         /* s: cell side h = max(re_n, re_lap) (1 + s); a step fails with *
+                               * MPS_ESKIN if a particle moves more than s max(re)/2           */
+    double box_min[3];        /* cell grid origin [m]; unused axes ignored                    */
+    double box_max[3];        /* cell grid extent: ncell = floor((max - min)/h) + 1 per axis  */
+    double inner_tol;         /* mixed: relative residual reduction of each FP32 inner CG      */
+    int32_t max_outer;        /* mixed: cap on FP64 refinement sweeps                          */
+    int32_t ppe_operator;     /* mixed inner operator: 0 stored FP32 coefficients,             *
+                               * 1 matrix-free (coefficients recomputed from positions)        */
+    int32_t device;           /* CUDA device ordinal                                           */
+    int32_t reserved0;
+    void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
+    mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
+    mps_release_fn release;
+    void* alloc_user;
+} mps_params;
+
+/* Per-step diagnostics (values of the last step of a call). */
+typedef struct {
+    int32_t status;           /* MPS_OK or the first error seen                               */
+    int32_t cg_iters;         /* CG iterations (mixed: FP32 inner iterations, all sweeps)     */
+    int32_t cg_outer;         /* mixed: FP64 refinement sweeps; FP64: restarts                 */
+    int32_t reserved0;
+    double cg_resid;          /* FP64 relative residual ||b - A p|| / ||b|| at exit            */
+    int64_t n_surface;        /* FLUID/WALL particles with n* < beta n0 (Eq. 15)               */
+    int64_t n_ghost;
+    int64_t n_ppe_rows;       /* unknowns of the PPE                                          */
+    double max_disp;          /* max |r* - r| over FLUID particles [m]                         */
+    double n0_pnd;            /* reference number density at re_n (ideal lattice)             */
+    double n0_lap;            /* reference number density at re_lap                           */
+    double lambda;            /* lambda of Eq. 7 at re_lap [m^2]                               */
+    int64_t steps_done;       /* steps completed by this context so far                       */
+} mps_report;
+
+/* Opaque context: device buffers, stream and derived constants of one particle system. */
+typedef struct mps_ctx mps_ctx;
+
+/* Fill *p with the defaults: dim 2, l0 0.01, re_n 2.1 l0, re_lap 4 l0, rho 1000, nu 1e-6,
+ * dt 1e-4, beta 0.97, g (0, -9.81, 0), c0 20, gamma 7, alpha_c 1e-7, cg_tol 1e-8,
+ * cg_max_iter 0, precision 0, clamp 1, nbr_cap 0, cell_skin 0.1, box [0,1]^dim,
+ * inner_tol 1e-4, max_outer 30, ppe_operator 0, device 0, no stream, no hooks. */
+void mps_params_default(mps_params* p);
+
+/* Create a context from n particles (the problem statement of Sec. 3 and the particle kinds
+ * of the PPE listing, Sec. 5.3).
+ * pos: n*dim doubles; vel: n*dim doubles or NULL (zero); types: n int8 kinds.
+ * The reference densities n0 (at re_n and re_lap) and lambda (at re_lap) are computed on the
+ * host from an ideal lattice of spacing l0: all offsets o with 0 < |o| l0 < re (Eq. 5 and the
+ * weighted mean of r^2 under Eq. 7).
+ * Errors: MPS_EINVAL (params, n <= 0 or n >= 2^31, unknown kind, grid over 2^10 cells per
+ * axis in 3D or 2^16 in 2D), MPS_ENONFINITE, MPS_ENOMEM, MPS_EDEVICE.
+ * *out is written only on success; the caller's arrays are copied and not retained. */
+int mps_create(const double* pos, const double* vel, const int8_t* types, int64_t n,
+               const mps_params* params, mps_ctx** out);
+
+/* Advance nsteps time steps (Sec. 3, semi-implicit predictor-corrector):
+ *   1. bucket build at r^k: cell keys, Morton radix sort, cell table by scan (Sec. 5.1);
+ *   2. predict FLUID u* = u + dt (nu lap(u) + g) (Eq. 2, Eq. 7 over re_lap), r* = r + dt u*;
+ *   3. number density n* at r* (Eq. 5, re_n); free surface n* < beta n0 (Eq. 15);
+ *   4. pressure: PPE A p = b (Eq. 13; A = -(1/rho) Lap + alpha_c/dt^2 I on FLUID/WALL rows
+ *      off the surface, b = (n* - n0)/(n0 dt^2)) by CG, or the equation of state (Eq. 16);
+ *   5. PPE: clamp p >= 0, p_hat_i = min of p over i and its non-dummy re_n neighbours;
+ *   6. FLUID u = u* - (dt/rho) grad p, r = r* + dt (u - u*), gradient over re_n at r*.
+ * last (nullable) receives the report of the final step.  On an error the remaining steps
+ * are skipped and the state is unspecified (read it only to diagnose).
+ * Errors: MPS_ECG_NOCONV, MPS_ESKIN, MPS_ECOINCIDENT, MPS_ECAP, MPS_ENONFINITE, MPS_EDEVICE. */
+int mps_step(mps_ctx* ctx, int32_t nsteps, mps_report* last);
+
+/* Steps 1-4 (and 5) of mps_step at the current state without advancing it: afterwards
+ * mps_read_state returns the new p, n* and flags while positions and velocities are
+ * unchanged.  Errors as mps_step. */
+int mps_solve_ppe(mps_ctx* ctx, mps_report* out);
+
+/* Copy the state to caller buffers in original particle order; any pointer may be NULL.
+ * pos, vel: n*dim doubles; p, n_star: n doubles (of the last step or solve; 0 before any);
+ * flags: n bytes, bit 0 = free surface; types: n int8 (GHOST for particles that left). */
+int mps_read_state(mps_ctx* ctx, double* pos, double* vel, double* p, double* n_star,
+                   uint8_t* flags, int8_t* types);
+
+/* Replace positions, velocities and kinds (original order; vel or types may be NULL to keep
+ * them).  Same checks as mps_create.  Used to restart from a saved state. */
+int mps_write_state(mps_ctx* ctx, const double* pos, const double* vel, const int8_t* types);
+
+/* Cell key of every particle at the current positions (original order): the Morton code
+ * (x in bit 0) of c = floor((x - box_min)/h) per axis, or 0xFFFFFFFF for a particle outside
+ * the grid or a GHOST.  Bit-exact with the floor definition. */
+int mps_debug_cells(mps_ctx* ctx, uint32_t* cell_key);
+
+/* Neighbour sets at the current positions through the GPU bucket grid and gather:
+ * which = 0: radius re_n, 1: radius re_lap.  j is a neighbour of i iff j != i, neither is a
+ * GHOST and ((dx*dx)+(dy*dy))+(dz*dz) < re*re in binary64.  offsets: n+1 int64; ids: cap
+ * int32, rows in ascending original id.  If ids is NULL or cap is too small only offsets
+ * are written and MPS_ECAP is returned when ids was given. */
+int mps_debug_neighbors(mps_ctx* ctx, int32_t which, int64_t* offsets, int32_t* ids,
+                        int64_t cap);
+
+/* Derived constants: out[0] n0 at re_n, out[1] n0 at re_lap, out[2] lambda [m^2],
+ * out[3] cell side h [m], out[4] cells per axis x, out[5] y, out[6] z, out[7] nbr_cap. */
+int mps_get_constants(mps_ctx* ctx, double* out);
+
+/* Stage timers (CUDA events recorded on the context's stream around each stage of a step)
+ * and a count of the kernel launches the context issued.  Stages: */
+#define MPS_STAGE_BUCKET 0   /* cell keys, radix sort, cell table, permutation        */
+#define MPS_STAGE_PREDICT 1  /* viscosity + gravity prediction gather                 */
+#define MPS_STAGE_BUILD 2    /* number density, flags, PPE rows, neighbour lists       */
+#define MPS_STAGE_PPE 3      /* CG solve (includes the host's convergence polls)      */
+#define MPS_STAGE_UPDATE 4   /* clamp, minimum pressure, gradient correction          */
+#define MPS_NSTAGES 5
+/* on != 0 enables the stage timers (off by default) and resets timers and counter. */
+int mps_set_profiling(mps_ctx* ctx, int32_t on);
+/* stage_ms[MPS_NSTAGES]: accumulated milliseconds; stage_calls[MPS_NSTAGES]: stages timed;
+ * launches: kernels launched since the last reset.  Any pointer may be NULL. */
+int mps_get_profile(mps_ctx* ctx, double* stage_ms, int64_t* stage_calls, int64_t* launches);
+
+/* Release every device buffer and the owned stream.  NULL is ignored. */
+void mps_destroy(mps_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* mps_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

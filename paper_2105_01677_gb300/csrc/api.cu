@@ -1,0 +1,640 @@
+// api.cu -- the C ABI declared in include/mps.h: context set-up, the step driver and the
+// host transfers.  Every stage of the step runs in this library's kernels; the host only
+// sequences launches, polls the CG convergence flag and reads the status word.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mps_internal.cuh"
+
+namespace mps {
+
+int cuda_fail(Ctx* c, cudaError_t e, const char* what) {
+    if (c) {
+        char buf[512];
+        snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+        c->last_error = buf;
+    }
+    return MPS_EDEVICE;
+}
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Reference density and lambda of an ideal lattice (Eq. 5; lambda of Eq. 7): every integer
+// offset o != 0 with |o| l0 < re contributes w = re/(|o| l0) - 1, and w |o|^2 l0^2 to lambda.
+void lattice_constants(int dim, double l0, double re, double* n0, double* lambda, int* count) {
+    const int m = (int)std::ceil(re / l0) + 1;
+    const int mz = dim == 3 ? m : 0;
+    double sw = 0.0, swr2 = 0.0;
+    int cnt = 0;
+    for (int c = -mz; c <= mz; c++)
+        for (int b = -m; b <= m; b++)
+            for (int a = -m; a <= m; a++) {
+                const int k = a * a + b * b + c * c;
+                if (k == 0) continue;
+                const double r = l0 * std::sqrt((double)k);
+                if (!(r < re)) continue;
+                const double w = re / r - 1.0;
+                sw += w;
+                swr2 += w * r * r;
+                cnt++;
+            }
+    *n0 = sw;
+    *lambda = sw > 0.0 ? swr2 / sw : 0.0;
+    *count = cnt;
+}
+
+// FP32 pre-filter band for r^2 < re^2 (see gather.cu).  Coordinates are stored relative to
+// the grid origin, so |x| <= X; each is rounded once to FP32 (error <= 2^-24 X), the
+// difference and the squares add a few more roundings.
+Radius make_radius(double re, double X) {
+    Radius r;
+    r.re = re;
+    r.re2 = re * re;
+    r.re_f = (float)re;
+    const double E = std::ldexp(X, -23);
+    const double delta = 2.0 * E + std::ldexp(re, -22);
+    const double eps = 2.0 * (3.0 * delta * (2.0 * re + delta)) + std::ldexp(re * re, -19);
+    r.lo = std::nextafter((float)(r.re2 - eps), 0.0f);
+    r.hi = std::nextafter((float)(r.re2 + eps), INFINITY);
+    if (!(r.lo > 0.0f)) r.lo = 0.0f;
+    return r;
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+template <class T>
+int alloc_dev(Ctx* c, T** out, size_t count) {
+    size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+    void* p = nullptr;
+    if (c->prm.alloc) {
+        p = c->prm.alloc(bytes, c->prm.alloc_user);
+        if (!p) return MPS_ENOMEM;
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->last_error = "cudaMalloc failed";
+            return MPS_ENOMEM;
+        }
+    }
+    c->allocations.push_back(p);
+    *out = (T*)p;
+    return MPS_OK;
+}
+
+void free_all(Ctx* c) {
+    for (void* p : c->allocations) {
+        if (c->prm.alloc && c->prm.release) c->prm.release(p, c->prm.alloc_user);
+        else if (!c->prm.alloc) cudaFree(p);
+    }
+    c->allocations.clear();
+}
+
+void free_one(Ctx* c, void* p) {
+    auto it = std::find(c->allocations.begin(), c->allocations.end(), p);
+    if (it == c->allocations.end()) return;
+    c->allocations.erase(it);
+    if (c->prm.alloc && c->prm.release) c->prm.release(p, c->prm.alloc_user);
+    else if (!c->prm.alloc) cudaFree(p);
+}
+
+int check_params(const mps_params* P) {
+    if (!P) return MPS_EINVAL;
+    if (P->dim != 2 && P->dim != 3) return MPS_EINVAL;
+    if (!(P->l0 > 0) || !(P->re_n > 0) || !(P->re_lap > 0) || !(P->rho > 0) || !(P->dt > 0))
+        return MPS_EINVAL;
+    if (!(P->nu >= 0) || !(P->beta >= 0) || !(P->cell_skin >= 0) || !(P->alpha_c >= 0))
+        return MPS_EINVAL;
+    if (P->pressure_mode != 0 && P->pressure_mode != 1) return MPS_EINVAL;
+    if (P->precision != 0 && P->precision != 1) return MPS_EINVAL;
+    if (P->pressure_mode == 0 && !(P->cg_tol > 0)) return MPS_EINVAL;
+    if (P->pressure_mode == 1 && !(P->gamma > 0)) return MPS_EINVAL;
+    if ((P->alloc == nullptr) != (P->release == nullptr)) return MPS_EINVAL;
+    for (int a = 0; a < P->dim; a++)
+        if (!(P->box_max[a] > P->box_min[a]) || !std::isfinite(P->box_min[a]) ||
+            !std::isfinite(P->box_max[a]))
+            return MPS_EINVAL;
+    return MPS_OK;
+}
+
+int check_host_state(int64_t n, int dim, const double* pos, const double* vel, const int8_t* types) {
+    for (int64_t k = 0; k < n * dim; k++) {
+        if (pos && !std::isfinite(pos[k])) return MPS_ENONFINITE;
+        if (vel && !std::isfinite(vel[k])) return MPS_ENONFINITE;
+    }
+    if (types)
+        for (int64_t i = 0; i < n; i++)
+            if (types[i] < MPS_FLUID || types[i] > MPS_GHOST) return MPS_EINVAL;
+    return MPS_OK;
+}
+
+int setup(Ctx* c) {
+    const mps_params& P = c->prm;
+    const int dim = P.dim;
+    c->dim = dim;
+    int cnt_n, cnt_l;
+    double lam_n;
+    lattice_constants(dim, P.l0, P.re_n, &c->n0_pnd, &lam_n, &cnt_n);
+    lattice_constants(dim, P.l0, P.re_lap, &c->n0_lap, &c->lambda, &cnt_l);
+    if (!(c->n0_pnd > 0) || !(c->n0_lap > 0)) return MPS_EINVAL;
+    c->coef_lap = (2.0 * dim) / (c->n0_lap * c->lambda);
+    c->coef_ppe = (2.0 * dim) / (c->n0_lap * c->lambda * P.rho);
+    c->coef_grad = (double)dim / c->n0_pnd;
+    c->inv_dt2 = 1.0 / (P.dt * P.dt);
+    c->diag_add = P.alpha_c / (P.dt * P.dt);
+    c->cap = P.nbr_cap > 0 ? round_up(P.nbr_cap, 32) : round_up((int)std::ceil(1.5 * cnt_l), 32);
+    c->cap_n = round_up(std::max((int)std::ceil(1.5 * cnt_n),
+                                 (int)std::ceil((double)c->cap * cnt_n / std::max(cnt_l, 1))), 32);
+    {
+        // candidate lists hold every kind within h = max(re)(1 + s): size them from the
+        // ideal-lattice count within h, scaled like the neighbour cap
+        double n0h, lamh;
+        int cnt_h;
+        lattice_constants(dim, P.l0, std::max(P.re_n, P.re_lap) * (1.0 + P.cell_skin), &n0h,
+                          &lamh, &cnt_h);
+        c->cap_v = round_up(std::max((int)std::ceil(1.5 * cnt_h),
+                                     (int)std::ceil((double)c->cap * cnt_h / std::max(cnt_l, 1))), 32);
+    }
+    // grid
+    const double re_max = std::max(P.re_n, P.re_lap);
+    c->h = re_max * (1.0 + P.cell_skin);
+    GridDesc& g = c->grid;
+    g.dim = dim;
+    g.h = c->h;
+    int maxc = 1;
+    double X = 0.0;
+    for (int a = 0; a < 3; a++) {
+        if (a < dim) {
+            g.bmin[a] = P.box_min[a];
+            const double q = std::floor((P.box_max[a] - P.box_min[a]) / c->h) + 1.0;
+            if (q > 16384.0) return MPS_EINVAL;
+            g.ncell[a] = (int)q;
+            maxc = std::max(maxc, g.ncell[a]);
+            X = std::max(X, (q + 1.0) * c->h);
+        } else {
+            g.bmin[a] = 0.0;
+            g.ncell[a] = 1;
+        }
+    }
+    int bits = 1;
+    while ((1 << bits) < maxc) bits++;
+    if (dim * bits > 28) return MPS_EINVAL;
+    g.bits = bits;
+    g.ghost_key = 1u << (dim * bits);
+    c->ntable = (int64_t)1 << (dim * bits);
+    c->sort_bits = dim * bits + 1;
+    c->r_n = make_radius(P.re_n, X);
+    c->r_lap = make_radius(P.re_lap, X);
+    c->r_v = make_radius(c->h, X);
+    return MPS_OK;
+}
+
+int allocate(Ctx* c) {
+    const size_t n = (size_t)c->n;
+    int rc = 0;
+#define A(ptr, count) \
+    if ((rc = alloc_dev(c, &c->ptr, (count)))) return rc;
+    A(pos, n) A(vel, n) A(pos_alt, n) A(vel_alt, n) A(type, n) A(type_alt, n) A(id, n) A(id_alt, n)
+    A(p, n) A(p_alt, n) A(pos32, n) A(pos_star, n) A(vel_star, n) A(pos32_star, n) A(nstar, n)
+    A(flag, n) A(bvec, n) A(diag, n) A(phat, n)
+    A(vl_col, n * c->cap_v) A(vl_cnt, n) A(vel32, n)
+    A(nb_lap_col, n * c->cap) A(nb_lap_cnt, n) A(nb_n_col, n * c->cap_n) A(nb_n_cnt, n)
+    if (c->prm.pressure_mode == 0) {
+        A(nb_lap_v64, n * c->cap)
+        if (c->prm.precision == 1) { A(nb_lap_v32, n * c->cap) }
+        A(cg_r, n) A(cg_d, n) A(cg_q, n)
+        if (c->prm.precision == 1) { A(cg_r32, n) A(cg_d32, n) A(cg_q32, n) A(cg_x32, n) }
+    } else {
+        A(nb_lap_v64, n * c->cap)
+    }
+    A(key, n) A(key_alt, n) A(perm, n) A(perm_alt, n)
+    const int64_t tiles = ((int64_t)n + 2047) / 2048;
+    A(hist, 256 * tiles) A(hist_scan, 256 * tiles)
+    A(cell_count, c->ntable) A(cell_start, c->ntable + 1) A(occ, n + 1)
+    const int64_t sw = std::max(scan_scratch_words(256 * tiles), scan_scratch_words(c->ntable + 1));
+    A(scan_scratch, sw)
+    A(partials, 4096) A(cg, 1) A(st, 1)
+    c->stage_bytes = n * (3 * 8 * 2 + 8 + 8 + 4 + 2) + 1024;
+    { uint8_t* s8 = nullptr; if ((rc = alloc_dev(c, &s8, c->stage_bytes))) return rc; c->stage = s8; }
+#undef A
+    if (cudaMallocHost(&c->st_host, sizeof(DevStatus)) != cudaSuccess) return MPS_ENOMEM;
+    if (cudaMallocHost(&c->cg_host, sizeof(CgScalars)) != cudaSuccess) return MPS_ENOMEM;
+    MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
+    MPS_CUDA(c, cudaMemsetAsync(c->cg, 0, sizeof(CgScalars), c->stream));
+    MPS_CUDA(c, cudaMemsetAsync(c->nb_lap_cnt, 0, n * sizeof(int32_t), c->stream));
+    MPS_CUDA(c, cudaMemsetAsync(c->nb_n_cnt, 0, n * sizeof(int32_t), c->stream));
+    MPS_CUDA(c, cudaMemsetAsync(c->phat, 0, n * sizeof(double), c->stream));
+    return MPS_OK;
+}
+
+// Host data -> device staging (original order) -> state arrays (slot = id).
+int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* types, bool have_state) {
+    const size_t n = (size_t)c->n, dim = (size_t)c->dim;
+    uint8_t* base = (uint8_t*)c->stage;
+    double* d_pos = (double*)base;
+    double* d_vel = d_pos + n * dim;
+    int8_t* d_t = (int8_t*)(d_vel + n * dim);
+    if (have_state && (!vel || !types)) {
+        // keep the current velocities / kinds: bring them to original order first
+        launch_unpermute(c, nullptr, vel ? nullptr : d_vel, nullptr, nullptr, nullptr,
+                         types ? nullptr : d_t);
+    }
+    MPS_CUDA(c, cudaMemcpyAsync(d_pos, pos, n * dim * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (vel) MPS_CUDA(c, cudaMemcpyAsync(d_vel, vel, n * dim * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    else if (!have_state) MPS_CUDA(c, cudaMemsetAsync(d_vel, 0, n * dim * sizeof(double), c->stream));
+    if (types) MPS_CUDA(c, cudaMemcpyAsync(d_t, types, n, cudaMemcpyHostToDevice, c->stream));
+    launch_ingest(c, d_pos, d_vel, d_t, false, false);
+    MPS_CUDA(c, cudaGetLastError());
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MPS_OK;
+}
+
+int read_status(Ctx* c) {
+    MPS_CUDA(c, cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MPS_OK;
+}
+
+int status_error(const DevStatus& s) {
+    if (s.err & kErrNonfinite) return MPS_ENONFINITE;
+    if (s.err & kErrCoincident) return MPS_ECOINCIDENT;
+    if (s.err & kErrCap) return MPS_ECAP;
+    if (s.err & kErrWait) return MPS_EDEVICE;
+    return MPS_OK;
+}
+
+double bits_to_double(unsigned long long b) {
+    double d;
+    std::memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+void stage_begin(Ctx* c, int s) {
+    if (c->profiling) cudaEventRecord(c->ev[2 * s], c->stream);
+}
+void stage_end(Ctx* c, int s) {
+    if (c->profiling) cudaEventRecord(c->ev[2 * s + 1], c->stream);
+}
+// after a stream sync: add the elapsed time of every stage recorded in this step
+void stage_collect(Ctx* c, const bool* used) {
+    if (!c->profiling) return;
+    for (int s = 0; s < MPS_NSTAGES; s++) {
+        if (!used[s]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev[2 * s], c->ev[2 * s + 1]) == cudaSuccess) {
+            c->stage_ms[s] += ms;
+            c->stage_calls[s] += 1;
+        }
+    }
+}
+
+// One step (advance) or steps 1-5 only (solve).
+int do_step(Ctx* c, bool advance, mps_report* rep) {
+    const mps_params& P = c->prm;
+    int rc;
+    bool used[MPS_NSTAGES] = {true, true, true, P.pressure_mode == 0, true};
+    MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
+    stage_begin(c, MPS_STAGE_BUCKET);
+    if ((rc = bucket_build(c, true))) return rc;                   // 1
+    stage_end(c, MPS_STAGE_BUCKET);
+    launch_copy_state_star(c);
+    MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, (size_t)c->n * sizeof(int32_t), c->stream));
+    stage_begin(c, MPS_STAGE_PREDICT);
+    launch_verlet(c);                                              // candidates at r^k
+    launch_predict_rows(c);                                        // 2
+    stage_end(c, MPS_STAGE_PREDICT);
+    // per-slot outputs of the build; slots it does not visit (GHOST) keep these zeros
+    const size_t n = (size_t)c->n;
+    MPS_CUDA(c, cudaMemsetAsync(c->nstar, 0, n * sizeof(double), c->stream));
+    MPS_CUDA(c, cudaMemsetAsync(c->flag, 0, n, c->stream));
+    MPS_CUDA(c, cudaMemsetAsync(c->diag, 0, n * sizeof(double), c->stream));
+    MPS_CUDA(c, cudaMemsetAsync(c->bvec, 0, n * sizeof(double), c->stream));
+    MPS_CUDA(c, cudaMemsetAsync(c->nb_lap_cnt, 0, n * sizeof(int32_t), c->stream));
+    MPS_CUDA(c, cudaMemsetAsync(c->nb_n_cnt, 0, n * sizeof(int32_t), c->stream));
+    if (P.pressure_mode == 1) MPS_CUDA(c, cudaMemsetAsync(c->p, 0, n * sizeof(double), c->stream));
+    stage_begin(c, MPS_STAGE_BUILD);
+    launch_build_rows(c);                                          // 3 (+ 4 for the EOS)
+    stage_end(c, MPS_STAGE_BUILD);
+    MPS_CUDA(c, cudaGetLastError());
+    if ((rc = read_status(c))) return rc;
+    const DevStatus& s = *c->st_host;
+    rep->n_ghost = s.n_ghost;
+    rep->n_surface = s.n_surface;
+    rep->n_ppe_rows = s.n_ppe;
+    rep->max_disp = bits_to_double(s.max_disp_bits);
+    rep->n0_pnd = c->n0_pnd;
+    rep->n0_lap = c->n0_lap;
+    rep->lambda = c->lambda;
+    rep->cg_iters = rep->cg_outer = 0;
+    rep->cg_resid = 0.0;
+    if ((rc = status_error(s))) return rc;
+    if (rep->max_disp > 0.5 * P.cell_skin * std::max(P.re_n, P.re_lap)) return MPS_ESKIN;
+    if (P.pressure_mode == 0) {                                    // 4, 5
+        stage_begin(c, MPS_STAGE_PPE);
+        if ((rc = ppe_solve(c, rep))) return rc;
+        stage_end(c, MPS_STAGE_PPE);
+    }
+    stage_begin(c, MPS_STAGE_UPDATE);
+    if (P.pressure_mode == 0) {
+        launch_clamp_pmin(c);
+    } else {
+        MPS_CUDA(c, cudaMemcpyAsync(c->phat, c->p, sizeof(double) * (size_t)c->n,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (advance) launch_gradient_correct(c);                       // 6
+    stage_end(c, MPS_STAGE_UPDATE);
+    MPS_CUDA(c, cudaGetLastError());
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    stage_collect(c, used);
+    if (advance) c->steps_done++;
+    rep->steps_done = c->steps_done;
+    return MPS_OK;
+}
+
+}  // namespace
+}  // namespace mps
+
+using namespace mps;
+
+struct mps_ctx : public mps::Ctx {};
+
+extern "C" {
+
+void mps_params_default(mps_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->dim = 2;
+    p->pressure_mode = 0;
+    p->l0 = 0.01;
+    p->re_n = 2.1 * 0.01;
+    p->re_lap = 4.0 * 0.01;
+    p->rho = 1000.0;
+    p->nu = 1e-6;
+    p->dt = 1e-4;
+    p->beta = 0.97;
+    p->g[1] = -9.81;
+    p->c0 = 20.0;
+    p->gamma = 7.0;
+    p->alpha_c = 1e-7;
+    p->cg_tol = 1e-8;
+    p->clamp_negative_p = 1;
+    p->cell_skin = 0.1;
+    p->box_max[0] = p->box_max[1] = p->box_max[2] = 1.0;
+    p->inner_tol = 1e-4;
+    p->max_outer = 30;
+}
+
+int mps_create(const double* pos, const double* vel, const int8_t* types, int64_t n,
+               const mps_params* params, mps_ctx** out) {
+    if (!out || !pos || !types || n <= 0 || n >= ((int64_t)1 << 31)) return MPS_EINVAL;
+    int rc = check_params(params);
+    if (rc) return rc;
+    if ((rc = check_host_state(n, params->dim, pos, vel, types))) return rc;
+    DeviceGuard dg(params->device);
+    if (!dg.ok) return MPS_EDEVICE;
+    mps_ctx* c = new (std::nothrow) mps_ctx();
+    if (!c) return MPS_ENOMEM;
+    c->prm = *params;
+    c->n = n;
+    c->steps_done = 0;
+    c->last_cg_iters = 8;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, params->device) != cudaSuccess) {
+        delete c;
+        return MPS_EDEVICE;
+    }
+    if (params->stream) {
+        c->stream = (cudaStream_t)params->stream;
+        c->own_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return MPS_EDEVICE;
+        }
+        c->own_stream = true;
+    }
+    if ((rc = setup(c)) || (rc = allocate(c)) || (rc = upload_state(c, pos, vel, types, false))) {
+        mps_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return MPS_OK;
+}
+
+int mps_step(mps_ctx* c, int32_t nsteps, mps_report* last) {
+    if (!c || nsteps < 0) return MPS_EINVAL;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    mps_report rep;
+    std::memset(&rep, 0, sizeof rep);
+    rep.steps_done = c->steps_done;
+    int rc = MPS_OK;
+    for (int k = 0; k < nsteps && rc == MPS_OK; k++) rc = do_step(c, true, &rep);
+    rep.status = rc;
+    if (last) *last = rep;
+    return rc;
+}
+
+int mps_solve_ppe(mps_ctx* c, mps_report* out) {
+    if (!c) return MPS_EINVAL;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    mps_report rep;
+    std::memset(&rep, 0, sizeof rep);
+    int rc = do_step(c, false, &rep);
+    rep.status = rc;
+    if (out) *out = rep;
+    return rc;
+}
+
+int mps_read_state(mps_ctx* c, double* pos, double* vel, double* p, double* n_star,
+                   uint8_t* flags, int8_t* types) {
+    if (!c) return MPS_EINVAL;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    const size_t n = (size_t)c->n, dim = (size_t)c->dim;
+    uint8_t* base = (uint8_t*)c->stage;
+    double* d_pos = (double*)base;
+    double* d_vel = d_pos + n * dim;
+    double* d_p = d_vel + n * dim;
+    double* d_n = d_p + n;
+    uint8_t* d_f = (uint8_t*)(d_n + n);
+    int8_t* d_t = (int8_t*)(d_f + n);
+    launch_unpermute(c, pos ? d_pos : nullptr, vel ? d_vel : nullptr, p ? d_p : nullptr,
+                     n_star ? d_n : nullptr, flags ? d_f : nullptr, types ? d_t : nullptr);
+    MPS_CUDA(c, cudaGetLastError());
+    if (pos) MPS_CUDA(c, cudaMemcpyAsync(pos, d_pos, n * dim * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (vel) MPS_CUDA(c, cudaMemcpyAsync(vel, d_vel, n * dim * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (p) MPS_CUDA(c, cudaMemcpyAsync(p, d_p, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (n_star) MPS_CUDA(c, cudaMemcpyAsync(n_star, d_n, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (flags) MPS_CUDA(c, cudaMemcpyAsync(flags, d_f, n, cudaMemcpyDeviceToHost, c->stream));
+    if (types) MPS_CUDA(c, cudaMemcpyAsync(types, d_t, n, cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MPS_OK;
+}
+
+int mps_write_state(mps_ctx* c, const double* pos, const double* vel, const int8_t* types) {
+    if (!c || !pos) return MPS_EINVAL;
+    int rc = check_host_state(c->n, c->dim, pos, vel, types);
+    if (rc) return rc;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    return upload_state(c, pos, vel, types, true);
+}
+
+int mps_debug_cells(mps_ctx* c, uint32_t* cell_key) {
+    if (!c || !cell_key) return MPS_EINVAL;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    uint32_t* d_out = (uint32_t*)c->stage;
+    launch_cell_keys_only(c, c->key_alt);
+    launch_unpermute_u32(c, c->key_alt, d_out);
+    MPS_CUDA(c, cudaGetLastError());
+    MPS_CUDA(c, cudaMemcpyAsync(cell_key, d_out, (size_t)c->n * 4, cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MPS_OK;
+}
+
+int mps_debug_neighbors(mps_ctx* c, int32_t which, int64_t* offsets, int32_t* ids, int64_t cap) {
+    if (!c || !offsets || (which != 0 && which != 1)) return MPS_EINVAL;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    const int n = (int)c->n;
+    int rc;
+    MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
+    if ((rc = bucket_build(c, false))) return rc;
+    const Radius& r = which == 0 ? c->r_n : c->r_lap;
+    int32_t* d_cnt = nullptr;
+    int64_t* d_off = nullptr;
+    int32_t* d_ids = nullptr;
+    if ((rc = alloc_dev(c, &d_cnt, (size_t)n))) return rc;
+    MPS_CUDA(c, cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * n, c->stream));
+    launch_debug_neighbors(c, r, nullptr, nullptr, d_cnt);
+    std::vector<int32_t> cnt(n), slot_id(n);
+    MPS_CUDA(c, cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaMemcpyAsync(slot_id.data(), c->id, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<int64_t> soff(n + 1, 0);
+    for (int s = 0; s < n; s++) soff[s + 1] = soff[s] + cnt[s];
+    // offsets in original order
+    std::vector<int64_t> ocnt(n, 0);
+    for (int s = 0; s < n; s++) ocnt[slot_id[s]] = cnt[s];
+    offsets[0] = 0;
+    for (int i = 0; i < n; i++) offsets[i + 1] = offsets[i] + ocnt[i];
+    const int64_t total = soff[n];
+    if (!ids) {
+        free_one(c, d_cnt);
+        return MPS_OK;
+    }
+    if (total > cap) {
+        free_one(c, d_cnt);
+        return MPS_ECAP;
+    }
+    if ((rc = alloc_dev(c, &d_off, (size_t)n + 1)) || (rc = alloc_dev(c, &d_ids, (size_t)std::max<int64_t>(total, 1)))) {
+        free_one(c, d_cnt);
+        if (d_off) free_one(c, d_off);
+        return rc;
+    }
+    MPS_CUDA(c, cudaMemcpyAsync(d_off, soff.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream));
+    launch_debug_neighbors(c, r, d_off, d_ids, d_cnt);
+    std::vector<int32_t> sids(std::max<int64_t>(total, 1));
+    MPS_CUDA(c, cudaMemcpyAsync(sids.data(), d_ids, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int s = 0; s < n; s++) {
+        const int i = slot_id[s];
+        int32_t* dst = ids + offsets[i];
+        std::copy(sids.begin() + soff[s], sids.begin() + soff[s + 1], dst);
+        std::sort(dst, dst + cnt[s]);
+    }
+    free_one(c, d_cnt);
+    free_one(c, d_off);
+    free_one(c, d_ids);
+    return MPS_OK;
+}
+
+int mps_get_constants(mps_ctx* c, double* out) {
+    if (!c || !out) return MPS_EINVAL;
+    out[0] = c->n0_pnd;
+    out[1] = c->n0_lap;
+    out[2] = c->lambda;
+    out[3] = c->h;
+    out[4] = c->grid.ncell[0];
+    out[5] = c->grid.ncell[1];
+    out[6] = c->grid.ncell[2];
+    out[7] = c->cap;
+    return MPS_OK;
+}
+
+int mps_set_profiling(mps_ctx* c, int32_t on) {
+    if (!c) return MPS_EINVAL;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    if (on && !c->ev[0]) {
+        for (int k = 0; k < 2 * MPS_NSTAGES; k++)
+            MPS_CUDA(c, cudaEventCreate(&c->ev[k]));
+    }
+    c->profiling = on != 0;
+    c->launches = 0;
+    for (int s = 0; s < MPS_NSTAGES; s++) {
+        c->stage_ms[s] = 0.0;
+        c->stage_calls[s] = 0;
+    }
+    return MPS_OK;
+}
+
+int mps_get_profile(mps_ctx* c, double* stage_ms, int64_t* stage_calls, int64_t* launches) {
+    if (!c) return MPS_EINVAL;
+    for (int s = 0; s < MPS_NSTAGES; s++) {
+        if (stage_ms) stage_ms[s] = c->stage_ms[s];
+        if (stage_calls) stage_calls[s] = c->stage_calls[s];
+    }
+    if (launches) *launches = c->launches;
+    return MPS_OK;
+}
+
+void mps_destroy(mps_ctx* c) {
+    if (!c) return;
+    {
+        DeviceGuard dg(c->prm.device);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        for (int k = 0; k < 2 * MPS_NSTAGES; k++)
+            if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+        free_all(c);
+        if (c->st_host) cudaFreeHost(c->st_host);
+        if (c->cg_host) cudaFreeHost(c->cg_host);
+        if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    }
+    delete c;
+}
+
+const char* mps_strerror(int status) {
+    switch (status) {
+        case MPS_OK: return "MPS_OK";
+        case MPS_EINVAL: return "MPS_EINVAL: invalid argument";
+        case MPS_ENOMEM: return "MPS_ENOMEM: allocation failed";
+        case MPS_ECG_NOCONV: return "MPS_ECG_NOCONV: CG did not converge within cg_max_iter";
+        case MPS_ENONFINITE: return "MPS_ENONFINITE: non-finite position or velocity";
+        case MPS_ESKIN: return "MPS_ESKIN: a particle moved more than half the cell skin";
+        case MPS_ECOINCIDENT: return "MPS_ECOINCIDENT: two neighbouring particles coincide";
+        case MPS_ECAP: return "MPS_ECAP: neighbour capacity exceeded";
+        case MPS_EDEVICE: return "MPS_EDEVICE: CUDA error";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

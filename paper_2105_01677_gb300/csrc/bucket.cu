@@ -1,0 +1,210 @@
+// bucket.cu -- bucket build of the cell-linked list (Sec. 5.1).
+//
+// Per step, at the current positions r^k:
+//   1. cell key of every particle: c = floor((x - box_min)/h) per axis in binary64, Morton
+//      interleave (x in bit 0); a particle outside the grid becomes a GHOST and sorts last;
+//   2. stable LSD radix sort of (key, slot), 8-bit digits: per-tile digit histogram, a
+//      device-wide exclusive scan of the digit-major histogram table, and a stable scatter
+//      that ranks equal digits with warp match masks;
+//   3. per-cell counts and their exclusive scan give cell_start (a cell's particles are
+//      contiguous in Morton order); occupied cells are collected for the gathers;
+//   4. every per-particle array is permuted into the new order (slot s <- old slot perm[s]).
+#include "mps_internal.cuh"
+
+namespace mps {
+
+namespace {
+constexpr int kBT = 256;
+constexpr int kItems = 8;
+constexpr int kTile = kBT * kItems;
+constexpr int kRadixBits = 8;
+constexpr int kDigits = 1 << kRadixBits;
+
+__global__ void __launch_bounds__(kBT)
+    k_cell_keys(double4* pos, double4* vel, int8_t* type, uint32_t* key, int32_t* slot, int n,
+                GridDesc g, DevStatus* st, int mutate, uint32_t outside_key) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double4 p = pos[i];
+    int8_t t = type[i];
+    if (mutate) {
+        double4 u = vel[i];
+        bool fin = isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(u.x) &&
+                   isfinite(u.y) && isfinite(u.z);
+        if (!fin && t != kGhost) atomicOr(&st->err, kErrNonfinite);
+    }
+    uint32_t k = outside_key;
+    if (t != kGhost) {
+        int c[3] = {0, 0, 0};
+        const double xs[3] = {p.x, p.y, p.z};
+        bool inside = true;
+        for (int a = 0; a < g.dim; a++) {
+            double q = floor(__ddiv_rn(__dsub_rn(xs[a], g.bmin[a]), g.h));
+            if (!(q >= 0.0 && q < (double)g.ncell[a])) inside = false;
+            else c[a] = (int)q;
+        }
+        if (inside) {
+            k = morton_encode(c, g.dim, g.bits);
+        } else if (mutate) {
+            type[i] = kGhost;
+            vel[i] = make_double4(0.0, 0.0, 0.0, 0.0);
+        }
+    }
+    if (mutate && k == outside_key) atomicAdd(&st->n_ghost, 1u);
+    key[i] = k;
+    if (slot) slot[i] = i;
+}
+
+__global__ void __launch_bounds__(kBT)
+    k_radix_hist(const uint32_t* keys, int n, int shift, uint32_t* hist) {
+    __shared__ uint32_t s_h[kDigits];
+    for (int d = threadIdx.x; d < kDigits; d += kBT) s_h[d] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kTile;
+    for (int r = 0; r < kItems; r++) {
+        int i = base + r * kBT + threadIdx.x;
+        if (i < n) atomicAdd(&s_h[(keys[i] >> shift) & (kDigits - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kDigits; d += kBT) hist[(size_t)d * gridDim.x + blockIdx.x] = s_h[d];
+}
+
+// Stable scatter: the tile is visited in rounds of kBT consecutive keys; within a round a
+// key's rank among equal digits is (equal digits in earlier warps) + (equal digits in
+// earlier lanes of its own warp), on top of the running per-digit offset of the tile.
+__global__ void __launch_bounds__(kBT)
+    k_radix_scatter(const uint32_t* kin, const int32_t* vin, uint32_t* kout, int32_t* vout, int n,
+                    int shift, const uint32_t* offsets) {
+    __shared__ uint32_t s_off[kDigits];
+    __shared__ uint32_t s_wc[kBT / 32][kDigits];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int d = threadIdx.x; d < kDigits; d += kBT) s_off[d] = offsets[(size_t)d * gridDim.x + blockIdx.x];
+    const int base = blockIdx.x * kTile;
+    for (int r = 0; r < kItems; r++) {
+        for (int q = threadIdx.x; q < (kBT / 32) * kDigits; q += kBT) (&s_wc[0][0])[q] = 0;
+        __syncthreads();
+        int i = base + r * kBT + threadIdx.x;
+        bool valid = i < n;
+        uint32_t k = valid ? kin[i] : 0u;
+        int32_t v = valid ? vin[i] : 0;
+        int d = valid ? (int)((k >> shift) & (kDigits - 1)) : kDigits;   // sentinel digit
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & lt);
+        if (valid && rank == 0) s_wc[w][d] = __popc(peers);
+        __syncthreads();
+        uint32_t tot = 0;
+        for (int dd = threadIdx.x; dd < kDigits; dd += kBT) {
+            uint32_t run = 0;
+            for (int ww = 0; ww < kBT / 32; ww++) {
+                uint32_t cnt = s_wc[ww][dd];
+                s_wc[ww][dd] = run;
+                run += cnt;
+            }
+            tot = run;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t dst = s_off[d] + s_wc[w][d] + (uint32_t)rank;
+            kout[dst] = k;
+            vout[dst] = v;
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < kDigits; dd += kBT) s_off[dd] += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kBT)
+    k_cell_count(const uint32_t* key, int n, uint32_t ghost_key, uint32_t* count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && key[i] != ghost_key) atomicAdd(&count[key[i]], 1u);
+}
+
+// first slot of each run of equal keys (sorted) marks an occupied cell
+__global__ void __launch_bounds__(kBT)
+    k_occupied(const uint32_t* key, int n, uint32_t ghost_key, uint32_t* occ, DevStatus* st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t k = key[i];
+    if (k == ghost_key) return;
+    if (i == 0 || key[i - 1] != k) {
+        unsigned int q = atomicAdd(&st->n_occ, 1u);
+        occ[q] = k;
+    }
+}
+
+__global__ void __launch_bounds__(kBT)
+    k_permute(const int32_t* perm, int n, const double4* pos, const double4* vel,
+              const int8_t* type, const int32_t* id, const double* p, double4* pos_o,
+              double4* vel_o, int8_t* type_o, int32_t* id_o, double* p_o, float4* pos32,
+              float4* vel32, GridDesc g) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int j = perm[s];
+    double4 x = pos[j];
+    int8_t t = type[j];
+    const double4 u = vel[j];
+    pos_o[s] = x;
+    vel_o[s] = u;
+    vel32[s] = make_float4((float)u.x, (float)u.y, (float)u.z, 0.f);
+    type_o[s] = t;
+    id_o[s] = id[j];
+    p_o[s] = p[j];
+    pos32[s] = make_float4((float)(x.x - g.bmin[0]), (float)(x.y - g.bmin[1]),
+                           (float)(x.z - g.bmin[2]), __int_as_float((int)t));
+}
+}  // namespace
+
+void launch_cell_keys_only(Ctx* c, uint32_t* out_key) {
+    int n = (int)c->n;
+    // exported keys mark particles outside the grid (and GHOSTs) with 0xFFFFFFFF
+    k_cell_keys<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(c->pos, c->vel, c->type, out_key,
+                                                             nullptr, n, c->grid, c->st, 0,
+                                                             0xFFFFFFFFu);
+    c->launches += 1;
+}
+
+int bucket_build(Ctx* c, bool mutate) {
+    const int n = (int)c->n;
+    cudaStream_t s = c->stream;
+    const int nb1 = (n + kBT - 1) / kBT;
+    k_cell_keys<<<nb1, kBT, 0, s>>>(c->pos, c->vel, c->type, c->key, c->perm, n, c->grid, c->st,
+                                    mutate ? 1 : 0, c->grid.ghost_key);
+    // LSD radix sort over sort_bits
+    const int nt = (n + kTile - 1) / kTile;
+    uint32_t* kin = c->key;
+    int32_t* vin = c->perm;
+    uint32_t* kout = c->key_alt;
+    int32_t* vout = c->perm_alt;
+    for (int shift = 0; shift < c->sort_bits; shift += kRadixBits) {
+        k_radix_hist<<<nt, kBT, 0, s>>>(kin, n, shift, c->hist);
+        c->launches += 2 + scan_exclusive(c->hist, c->hist_scan, (int64_t)kDigits * nt, false,
+                                          c->scan_scratch, s);
+        k_radix_scatter<<<nt, kBT, 0, s>>>(kin, vin, kout, vout, n, shift, c->hist_scan);
+        uint32_t* tk = kin; kin = kout; kout = tk;
+        int32_t* tv = vin; vin = vout; vout = tv;
+    }
+    // kin/vin hold the sorted keys and the permutation
+    if (kin != c->key) { c->key_alt = c->key; c->key = kin; }
+    if (vin != c->perm) { c->perm_alt = c->perm; c->perm = vin; }
+    // cell table
+    MPS_CUDA(c, cudaMemsetAsync(c->cell_count, 0, sizeof(uint32_t) * (size_t)c->ntable, s));
+    k_cell_count<<<nb1, kBT, 0, s>>>(c->key, n, c->grid.ghost_key, c->cell_count);
+    c->launches += 4 + scan_exclusive(c->cell_count, (uint32_t*)c->cell_start, c->ntable, true,
+                                      c->scan_scratch, s);
+    k_occupied<<<nb1, kBT, 0, s>>>(c->key, n, c->grid.ghost_key, c->occ, c->st);
+    // permute the state into the new order
+    k_permute<<<nb1, kBT, 0, s>>>(c->perm, n, c->pos, c->vel, c->type, c->id, c->p, c->pos_alt,
+                                  c->vel_alt, c->type_alt, c->id_alt, c->p_alt, c->pos32, c->vel32,
+                                  c->grid);
+    std::swap(c->pos, c->pos_alt);
+    std::swap(c->vel, c->vel_alt);
+    std::swap(c->type, c->type_alt);
+    std::swap(c->id, c->id_alt);
+    std::swap(c->p, c->p_alt);
+    MPS_CUDA(c, cudaGetLastError());
+    return MPS_OK;
+}
+
+}  // namespace mps

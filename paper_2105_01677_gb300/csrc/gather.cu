@@ -1,0 +1,233 @@
+// gather.cu -- neighbour gathers over the Morton bucket grid (Sec. 5.1: a particle's
+// neighbours are looked up in its own cell and the adjacent cells).
+//
+// One thread block per occupied cell; each thread owns one particle of that cell.  The
+// particles of the 3^d surrounding cells are staged in shared memory in chunks (FP32
+// positions relative to the grid origin, the kind in the fourth lane), and every thread
+// walks the same staged candidates, so the shared-memory reads are broadcasts and the
+// rare FP64 loads of a candidate are warp-uniform.
+//
+// Distance predicate of the exact sets: a candidate is classified from its FP32 squared
+// distance against a band [lo, hi) around re^2 that bounds the FP32 rounding error; only
+// candidates inside the band are decided in binary64 with the exact
+// ((dx*dx)+(dy*dy))+(dz*dz) < re*re of the definition, so neighbour sets are identical to
+// an FP64 evaluation.
+//
+// Ops:
+//   VerletOp   (r^k): the step's candidate lists, every j within h = max(re)(1 + s) (FP32
+//              with a rounding margin: a superset); the pair sums of the step run over
+//              these lists (rows.cu).
+//   NbrOp      (debug export of exact neighbour sets at r^k).
+#include "mps_internal.cuh"
+
+namespace mps {
+
+namespace {
+
+template <int BT, int CHUNK, bool STAGE_X, class Op>
+__global__ void __launch_bounds__(BT)
+    k_gather(Op op, const int32_t* __restrict__ cell_start, const uint32_t* __restrict__ occ,
+             const DevStatus* st, GridDesc g) {
+    __shared__ float4 s_p[CHUNK];
+    __shared__ int s_j[CHUNK];
+    __shared__ float4 s_x[STAGE_X ? CHUNK : 1];
+    __shared__ int s_cs[27], s_pref[28];
+    __shared__ int s_nc;
+    const unsigned n_occ = *(volatile const unsigned*)&st->n_occ;
+    for (unsigned ci = blockIdx.x; ci < n_occ; ci += gridDim.x) {
+        const uint32_t code = occ[ci];
+        const int c0 = cell_start[code], c1 = cell_start[code + 1];
+        if (threadIdx.x == 0) {
+            int cc[3];
+            morton_decode(code, g.dim, g.bits, cc);
+            int m = 0, pref = 0;
+            const int zr = (g.dim == 3) ? 1 : 0;
+            for (int dz = -zr; dz <= zr; dz++)
+                for (int dy = -1; dy <= 1; dy++)
+                    for (int dx = -1; dx <= 1; dx++) {
+                        int nc[3] = {cc[0] + dx, cc[1] + dy, cc[2] + dz};
+                        if (nc[0] < 0 || nc[1] < 0 || nc[2] < 0 || nc[0] >= g.ncell[0] ||
+                            nc[1] >= g.ncell[1] || nc[2] >= g.ncell[2])
+                            continue;
+                        uint32_t k2 = morton_encode(nc, g.dim, g.bits);
+                        int s0 = cell_start[k2], s1 = cell_start[k2 + 1];
+                        if (s1 > s0) {
+                            s_cs[m] = s0;
+                            s_pref[m] = pref;
+                            pref += s1 - s0;
+                            m++;
+                        }
+                    }
+            s_pref[m] = pref;
+            s_nc = m;
+        }
+        __syncthreads();
+        const int ncand = s_pref[s_nc];
+        for (int ib = c0; ib < c1; ib += BT) {
+            const int i = ib + threadIdx.x;
+            const bool act = (i < c1) && op.active(i);
+            if (!__syncthreads_or(act)) continue;
+            typename Op::Center ctr;
+            op.begin(i, act, ctr);
+            for (int base = 0; base < ncand; base += CHUNK) {
+                const int len = min(CHUNK, ncand - base);
+                for (int k = threadIdx.x; k < len; k += BT) {
+                    const int f = base + k;
+                    int m = 0;
+                    while (s_pref[m + 1] <= f) ++m;
+                    const int j = s_cs[m] + (f - s_pref[m]);
+                    s_j[k] = j;
+                    s_p[k] = op.pos32[j];
+                    if (STAGE_X) s_x[k] = op.stage(j);
+                }
+                __syncthreads();
+                if (act) {
+#pragma unroll 4
+                    for (int k = 0; k < len; k++)
+                        op.visit(ctr, i, s_j[k], s_p[k], STAGE_X ? s_x[k] : s_p[k]);
+                    op.end_chunk(ctr);
+                }
+                __syncthreads();
+            }
+            op.finish(i, act, ctr);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ float dist2_f(const float4& a, const float4& b) {
+    float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+__device__ __forceinline__ int kind_of(const float4& q) { return __float_as_int(q.w) & 0xff; }
+
+// ------------------------------------------------------------------------------ Verlet
+// Candidate list of every non-ghost particle: all j != i with FP32 squared distance below
+// the candidate radius h^2 plus its rounding margin (a superset of the exact set within h).
+struct VerletOp {
+    const float4* pos32;
+    const int8_t* type;
+    DevStatus* st;
+    float hv2;
+    int cap_v;
+    int32_t* vcol;
+    int32_t* vcnt;
+
+    struct Center {
+        float4 p32;
+        int cnt;
+        size_t base;
+    };
+    __device__ bool active(int i) const { return type[i] != kGhost; }
+    __device__ float4 stage(int) const { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ void begin(int i, bool act, Center& c) const {
+        c.cnt = 0;
+        c.base = (size_t)i * cap_v;
+        if (act) c.p32 = pos32[i];
+    }
+    __device__ void visit(Center& c, int i, int j, const float4& q, const float4&) const {
+        if (j == i || dist2_f(c.p32, q) >= hv2) return;
+        if (c.cnt < cap_v) vcol[c.base + c.cnt] = j;
+        c.cnt++;
+    }
+    __device__ void end_chunk(Center&) const {}
+    __device__ void finish(int i, bool act, const Center& c) const {
+        if (!act) return;
+        vcnt[i] = min(c.cnt, cap_v);
+        if (c.cnt > cap_v) atomicOr(&st->err, kErrCap);
+    }
+};
+
+// ------------------------------------------------------------------------------ debug
+struct NbrOp {
+    const float4* pos32;
+    const double4* pos;
+    const int8_t* type;
+    const int32_t* id;
+    Radius r;
+    const int64_t* row_off;
+    int32_t* out_ids;
+    int32_t* out_cnt;
+    struct Center {
+        double4 p;
+        float4 p32;
+        int cnt;
+    };
+    __device__ bool active(int i) const { return type[i] != kGhost; }
+    __device__ float4 stage(int) const { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ void begin(int i, bool act, Center& c) const {
+        c.cnt = 0;
+        if (!act) return;
+        c.p = pos[i];
+        c.p32 = pos32[i];
+    }
+    __device__ void visit(Center& c, int i, int j, const float4& q, const float4&) const {
+        if (j == i) return;
+        if (!in_radius(dist2_f(c.p32, q), r, pos, i, j, c.p)) return;
+        if (row_off) out_ids[row_off[i] + c.cnt] = id[j];
+        c.cnt++;
+    }
+    __device__ void end_chunk(Center&) const {}
+    __device__ void finish(int i, bool act, const Center& c) const {
+        if (act && !row_off) out_cnt[i] = c.cnt;
+    }
+};
+
+__global__ void k_copy_star(int n, const double4* pos, const double4* vel, const float4* pos32,
+                            double4* ps, double4* vs, float4* p32s) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    ps[i] = pos[i];
+    vs[i] = vel[i];
+    p32s[i] = pos32[i];
+}
+
+template <class Op, bool STAGE_X>
+void launch_gather(Ctx* c, const Op& op) {
+    c->launches += 1;
+    if (c->dim == 3) {
+        k_gather<128, 1024, STAGE_X, Op><<<c->sms * 6, 128, 0, c->stream>>>(op, c->cell_start, c->occ,
+                                                                         c->st, c->grid);
+    } else {
+        k_gather<32, 256, STAGE_X, Op><<<c->sms * 16, 32, 0, c->stream>>>(op, c->cell_start, c->occ,
+                                                                      c->st, c->grid);
+    }
+}
+
+}  // namespace
+
+void launch_copy_state_star(Ctx* c) {
+    int n = (int)c->n;
+    k_copy_star<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->pos, c->vel, c->pos32, c->pos_star,
+                                                         c->vel_star, c->pos32_star);
+    c->launches += 1;
+}
+
+void launch_verlet(Ctx* c) {
+    VerletOp op;
+    op.pos32 = c->pos32;
+    op.type = c->type;
+    op.st = c->st;
+    op.hv2 = c->r_v.hi;
+    op.cap_v = c->cap_v;
+    op.vcol = c->vl_col;
+    op.vcnt = c->vl_cnt;
+    launch_gather<VerletOp, false>(c, op);
+}
+
+void launch_debug_neighbors(Ctx* c, const Radius& r, const int64_t* row_off, int32_t* out_ids,
+                            int32_t* out_cnt) {
+    NbrOp op;
+    op.pos32 = c->pos32;
+    op.pos = c->pos;
+    op.type = c->type;
+    op.id = c->id;
+    op.r = r;
+    op.row_off = row_off;
+    op.out_ids = out_ids;
+    op.out_cnt = out_cnt;
+    launch_gather<NbrOp, false>(c, op);
+}
+
+}  // namespace mps

@@ -1,0 +1,285 @@
+// mps_internal.cuh -- shared declarations of the GB300 MPS library's translation units.
+//
+// Layout in HBM (all per-particle arrays are in the current Morton-sorted order, "slot" s):
+//   pos, vel        double4 (x, y, z, 0)           FP64 master state
+//   pos32           float4 (x-xmin, y-ymin, z-zmin, kind bits)   FP32 copy for filtering
+//   type            int8, id int32 (caller's particle id of slot s)
+//   pos_star/vel_star double4, pos32_star float4   predicted r*, u* of the step
+//   vl              ELL rows of `cap_v` int32 slots: candidates within h at r^k (superset)
+//   vel32           float4 velocities (mixed-precision viscosity terms)
+//   nb_lap          ELL rows of `cap` int32 slots: non-dummy neighbours within re_lap at r*,
+//                   with FP64 (val64) and FP32 (val32) coefficients c_ij of the PPE
+//   nb_n            ELL rows of `cap_n` int32 slots: non-dummy neighbours within re_n at r*
+//   cell_start      int32[2^(dim*bits) + 1], indexed by Morton code: exclusive scan of
+//                   per-cell counts, so cell m holds slots [cell_start[m], cell_start[m+1])
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "mps.h"
+
+namespace mps {
+
+constexpr int kFluid = MPS_FLUID, kWall = MPS_WALL, kDummy = MPS_DUMMY, kGhost = MPS_GHOST;
+
+// device error bits (DevStatus::err)
+constexpr unsigned kErrCoincident = 1u, kErrCap = 2u, kErrNonfinite = 4u, kErrWait = 8u;
+
+struct DevStatus {
+    unsigned int err;
+    unsigned int n_ghost;
+    unsigned int n_occ;
+    unsigned int n_surface;
+    unsigned int n_ppe;
+    unsigned int pad0;
+    unsigned long long max_disp_bits;   // atomicMax over bit patterns of non-negative doubles
+    unsigned int counter[8];            // last-block-done tickets of grid reductions
+};
+
+// Scalars of one CG solve; updated by the last block of each reduction kernel.
+struct CgScalars {
+    double rho;        // r.r of the current iterate
+    double rho0;       // r.r at the (re)start of this solve
+    double dq;         // d.q
+    double alpha, beta;
+    double rr;         // generic reduction result (residual norms)
+    double stop2;      // stop when rho <= stop2
+    int done;          // recurrence residual below the stop threshold
+    int iters;         // iterations executed by this solve
+    int max_iters;
+    int pad;
+};
+
+struct GridDesc {
+    double bmin[3];
+    double h;
+    int ncell[3];
+    int bits;
+    int dim;
+    uint32_t ghost_key;   // 1 << (dim*bits): sorts after every cell
+};
+
+// Precomputed bounds for the FP32 pre-filter of a distance predicate r^2 < re^2:
+// r2_32 < lo  => certainly inside; r2_32 >= hi => certainly outside; else decide in FP64.
+struct Radius {
+    double re, re2;
+    float lo, hi;
+    float re_f;
+};
+
+struct Ctx;
+
+// ---------------------------------------------------------------- bucket.cu
+int bucket_build(Ctx* c, bool mutate);            // keys, sort, cell table, permute
+void launch_cell_keys_only(Ctx* c, uint32_t* out_key);
+
+// ---------------------------------------------------------------- scan.cu
+// exclusive scan of m uint32 values; writes out[m] = total when write_total.
+// Returns the number of kernels launched.
+int scan_exclusive(const uint32_t* in, uint32_t* out, int64_t m, bool write_total,
+                   uint32_t* scratch, cudaStream_t s);
+int64_t scan_scratch_words(int64_t m);
+
+// ---------------------------------------------------------------- gather.cu
+void launch_copy_state_star(Ctx* c);
+void launch_verlet(Ctx* c);
+void launch_debug_neighbors(Ctx* c, const Radius& r, const int64_t* row_off, int32_t* out_ids,
+                            int32_t* out_cnt);
+
+// ---------------------------------------------------------------- rows.cu
+void launch_predict_rows(Ctx* c);
+void launch_build_rows(Ctx* c);
+
+// ---------------------------------------------------------------- ppe.cu
+int ppe_solve(Ctx* c, mps_report* rep);
+
+// ---------------------------------------------------------------- update.cu
+void launch_clamp_pmin(Ctx* c);
+void launch_gradient_correct(Ctx* c);
+void launch_unpermute(Ctx* c, double* d_pos, double* d_vel, double* d_p, double* d_nstar,
+                      uint8_t* d_flags, int8_t* d_types);
+void launch_ingest(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types,
+                   bool keep_vel, bool keep_types);
+void launch_unpermute_u32(Ctx* c, const uint32_t* in, uint32_t* out);
+
+// ---------------------------------------------------------------- context
+struct Ctx {
+    mps_params prm;
+    int64_t n;
+    int dim;
+    int sms;
+    cudaStream_t stream;
+    bool own_stream;
+    std::string last_error;
+    std::vector<void*> allocations;
+
+    // derived constants
+    double n0_pnd, n0_lap, lambda, h;
+    double coef_lap;     // 2d/(n0_lap lambda)            (Eq. 7)
+    double coef_ppe;     // 2d/(n0_lap lambda rho)        (PPE coefficient)
+    double coef_grad;    // d/n0_pnd                      (gradient)
+    double diag_add;     // alpha_c/dt^2
+    double inv_dt2;
+    int cap, cap_n, cap_v;
+    GridDesc grid;
+    int64_t ntable;      // 2^(dim*bits)
+    int sort_bits;
+    Radius r_n, r_lap, r_v;   // r_v: candidate radius h (only r_v.hi is used)
+    int64_t steps_done;
+    int last_cg_iters;
+
+    // state (sorted order) and double buffers
+    double4 *pos, *vel, *pos_alt, *vel_alt;
+    int8_t *type, *type_alt;
+    int32_t *id, *id_alt;
+    double *p, *p_alt;
+    float4* pos32;
+    // step buffers
+    double4 *pos_star, *vel_star;
+    float4* pos32_star;
+    float4* vel32;
+    double* nstar;
+    uint8_t* flag;
+    double* bvec;
+    double* diag;        // PPE diagonal; 0 on rows outside the PPE
+    int32_t *vl_col, *vl_cnt;     // candidate (Verlet) lists at r^k, radius h
+    int32_t *nb_lap_col, *nb_lap_cnt, *nb_n_col, *nb_n_cnt;
+    double* nb_lap_v64;
+    float* nb_lap_v32;
+    double* phat;
+    // bucket build
+    uint32_t *key, *key_alt;
+    int32_t *perm, *perm_alt;
+    uint32_t* hist;        // radix digit histograms
+    uint32_t* hist_scan;
+    uint32_t* cell_count;
+    int32_t* cell_start;
+    uint32_t* occ;         // occupied cell codes
+    uint32_t* scan_scratch;
+    // CG (FP64): x = p, r, d, q ; FP32: r32, d32, q32, x32
+    double *cg_r, *cg_d, *cg_q;
+    float *cg_r32, *cg_d32, *cg_q32, *cg_x32;
+    double* partials;       // per-block partial sums
+    CgScalars* cg;          // device
+    DevStatus* st;          // device
+    DevStatus* st_host;     // pinned mirror
+    CgScalars* cg_host;     // pinned mirror
+    // staging for host transfers (original order)
+    void* stage;
+    size_t stage_bytes;
+    // profiling: kernel launches issued, and per-stage CUDA-event timers
+    int64_t launches;
+    bool profiling;
+    cudaEvent_t ev[2 * MPS_NSTAGES];
+    double stage_ms[MPS_NSTAGES];
+    int64_t stage_calls[MPS_NSTAGES];
+};
+
+// launch geometry
+constexpr int kVecBlock = 256;
+inline int vec_grid(const Ctx* c) { return c->sms * 4; }
+
+// error helpers
+int cuda_fail(Ctx* c, cudaError_t e, const char* what);
+#define MPS_CUDA(c, call)                                        \
+    do {                                                         \
+        cudaError_t e__ = (call);                                \
+        if (e__ != cudaSuccess) return ::mps::cuda_fail((c), e__, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------- device helpers
+__host__ __device__ inline uint32_t morton_encode(const int c[3], int dim, int bits) {
+    uint32_t key = 0;
+    for (int k = 0; k < bits; k++)
+        for (int a = 0; a < dim; a++) key |= (uint32_t)((c[a] >> k) & 1) << (k * dim + a);
+    return key;
+}
+
+__host__ __device__ inline void morton_decode(uint32_t key, int dim, int bits, int c[3]) {
+    c[0] = c[1] = c[2] = 0;
+    for (int k = 0; k < bits; k++)
+        for (int a = 0; a < dim; a++) c[a] |= (int)((key >> (k * dim + a)) & 1u) << k;
+}
+
+// Squared distance in binary64 with one rounding per operation and the fixed order
+// ((dx*dx)+(dy*dy))+(dz*dz): no fused multiply-add, so the predicate r^2 < re^2 is
+// decided identically to a plain IEEE evaluation of the definition.
+__device__ __forceinline__ double exact_dist2(const double4& a, const double4& b) {
+    double dx = __dsub_rn(b.x, a.x), dy = __dsub_rn(b.y, a.y), dz = __dsub_rn(b.z, a.z);
+    double s = __dmul_rn(dx, dx);
+    s = __dadd_rn(s, __dmul_rn(dy, dy));
+    s = __dadd_rn(s, __dmul_rn(dz, dz));
+    return s;
+}
+
+// Classify a pair for radius r from its FP32 squared distance; only pairs inside the
+// rounding band around re^2 are decided from the FP64 positions.
+__device__ __forceinline__ bool in_radius(float r2, const Radius& r, const double4* pos, int i,
+                                          int j, const double4& pi) {
+    if (r2 < r.lo) return true;
+    if (r2 >= r.hi) return false;
+    return exact_dist2(pi, pos[j]) < r.re2;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed tree); every thread must call it.  Returns the sum to
+// all threads.
+template <int BT>
+__device__ __forceinline__ double block_sum(double v, double* smem /* >= BT/32 */) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) smem[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = (lane < BT / 32) ? smem[lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) smem[0] = t;
+    }
+    __syncthreads();
+    t = smem[0];
+    __syncthreads();
+    return t;
+}
+
+// Grid reduction with a deterministic finish: each block stores its partial; the last
+// block to arrive sums the partials in block order.  Returns true in the last block,
+// where *total is valid (in every thread of that block).
+template <int BT>
+__device__ bool grid_sum(double block_partial, double* partials, unsigned int* counter,
+                         double* total, double* smem) {
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = block_partial;
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double v = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += BT) v += ((volatile double*)partials)[b];
+    v = block_sum<BT>(v, smem);
+    if (threadIdx.x == 0) *counter = 0u;
+    *total = v;
+    return true;
+}
+
+}  // namespace mps

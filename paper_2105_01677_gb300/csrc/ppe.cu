@@ -1,0 +1,400 @@
+// ppe.cu -- conjugate-gradient solve of the PPE A p = b (Eq. 13 assembled as in the CUDA
+// PPE listing of Sec. 5.3; the paper solves it by (IC)CG, Sec. 3.1.2 and Sec. 5.3).
+//
+// A is applied from the per-step neighbour lists built at r*:
+//   (A x)_i = diag_i x_i - sum_{j in nb_lap(i)} c_ij x_j   for rows of the PPE (diag_i > 0),
+//   (A x)_i = 0 elsewhere,
+// where every CG vector vanishes outside the PPE rows, so neighbours j outside them drop out
+// of the sum exactly as the off-diagonal entries of the listing do.
+//
+// FP64 mode: textbook CG in binary64 with stored FP64 coefficients; the recurrence residual
+// stops the iteration and the true residual b - A p is recomputed, restarting if needed.
+// Mixed mode: outer refinement in binary64 (r = b - A x with FP64 coefficients, x += e),
+// inner CG in FP32 on A e = r/|r| with FP32 coefficients (stored, or recomputed from the FP32
+// positions: matrix-free), FP64 dot products.
+//
+// Reductions are deterministic: per-block partials summed in block order by the last block.
+// Convergence is decided on the device; the host polls one flag per chunk of iterations.
+#include "mps_internal.cuh"
+
+namespace mps {
+
+namespace {
+constexpr int kBT = 256;
+constexpr int kWarps = kBT / 32;
+
+// Plain-data view of the PPE operator handed to the kernels.
+struct PpeView {
+    int n, cap;
+    const int32_t* col;
+    const int32_t* cnt;
+    const double* v64;
+    const float* v32;
+    const double* diag;
+    const double* bvec;
+    const float4* pos32s;
+    double* partials;
+    unsigned int* counter;
+};
+
+// ------------------------------------------------------------------ SpMV building blocks
+__device__ __forceinline__ double row_dot64(const PpeView& c, int i, const double* x, int lane) {
+    const int cnt = c.cnt[i];
+    const size_t base = (size_t)i * c.cap;
+    double acc = 0.0;
+    for (int k = lane; k < cnt; k += 32) acc = fma(c.v64[base + k], x[c.col[base + k]], acc);
+    return warp_sum(acc);
+}
+
+template <bool MATRIX_FREE>
+__device__ __forceinline__ float row_dot32(const PpeView& c, int i, const float* x, int lane,
+                                           float4 pi, float coef, float re_f) {
+    const int cnt = c.cnt[i];
+    const size_t base = (size_t)i * c.cap;
+    float acc = 0.f;
+    for (int k = lane; k < cnt; k += 32) {
+        const int j = c.col[base + k];
+        float a;
+        if (MATRIX_FREE) {
+            const float4 q = c.pos32s[j];
+            const float dx = q.x - pi.x, dy = q.y - pi.y, dz = q.z - pi.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            a = coef * fmaf(re_f, rsqrtf(r2), -1.f);
+        } else {
+            a = c.v32[base + k];
+        }
+        acc = fmaf(a, x[j], acc);
+    }
+    return warp_sum_f(acc);
+}
+
+// ------------------------------------------------------------------ FP64 kernels
+// r = b - A x, d = r; rr = r.r.  set_stop: stop2 = tol2 * rr (first call of a solve).
+__global__ void __launch_bounds__(kBT) k_resid64(PpeView c, const double* x, double* r, double* d,
+                                                 CgScalars* cg, double tol2, int set_stop,
+                                                 int set_cg) {
+    __shared__ double sm[kWarps];
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * kBT + threadIdx.x) >> 5, nw = (gridDim.x * kBT) >> 5;
+    double part = 0.0;
+    for (int i = gw; i < c.n; i += nw) {
+        const double dg = c.diag[i];
+        double ri = 0.0;
+        if (dg != 0.0) {
+            const double s = row_dot64(c, i, x, lane);
+            ri = c.bvec[i] - (dg * x[i] - s);
+        }
+        if (lane == 0) {
+            r[i] = ri;
+            if (d) d[i] = ri;
+            part += ri * ri;
+        }
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, c.partials, &c.counter[0], &tot, sm) && threadIdx.x == 0) {
+        cg->rr = tot;
+        if (set_stop) cg->stop2 = tol2 * tot;
+        if (set_cg) {
+            cg->rho = tot;
+            cg->rho0 = tot;
+            cg->done = (tot <= cg->stop2) ? 1 : 0;
+        }
+    }
+}
+
+// q = A d, alpha = rho / (d.q)
+__global__ void __launch_bounds__(kBT) k_spmv64(PpeView c, const double* d, double* q, CgScalars* cg) {
+    if (*(volatile int*)&cg->done) return;
+    __shared__ double sm[kWarps];
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * kBT + threadIdx.x) >> 5, nw = (gridDim.x * kBT) >> 5;
+    double part = 0.0;
+    for (int i = gw; i < c.n; i += nw) {
+        const double dg = c.diag[i];
+        double qi = 0.0;
+        if (dg != 0.0) qi = dg * d[i] - row_dot64(c, i, d, lane);
+        if (lane == 0) {
+            q[i] = qi;
+            part += d[i] * qi;
+        }
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, c.partials, &c.counter[1], &tot, sm) && threadIdx.x == 0) {
+        cg->dq = tot;
+        cg->alpha = (tot > 0.0) ? cg->rho / tot : 0.0;
+    }
+}
+
+// x += alpha d; r -= alpha q; rho' = r.r; beta = rho'/rho; convergence flag
+__global__ void __launch_bounds__(kBT) k_xr64(int n, double* x, double* r, const double* d,
+                                              const double* q, CgScalars* cg, double* partials,
+                                              unsigned int* counter) {
+    if (*(volatile int*)&cg->done) return;
+    __shared__ double sm[kWarps];
+    const double alpha = cg->alpha;
+    double part = 0.0;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) {
+        x[i] = fma(alpha, d[i], x[i]);
+        const double ri = fma(-alpha, q[i], r[i]);
+        r[i] = ri;
+        part += ri * ri;
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, partials, counter, &tot, sm) && threadIdx.x == 0) {
+        cg->beta = (cg->rho > 0.0) ? tot / cg->rho : 0.0;
+        cg->rho = tot;
+        cg->iters += 1;
+        if (tot <= cg->stop2 || cg->iters >= cg->max_iters || !(cg->dq > 0.0)) cg->done = 1;
+    }
+}
+
+__global__ void __launch_bounds__(kBT) k_d64(int n, const double* r, double* d, const CgScalars* cg) {
+    if (*(volatile const int*)&cg->done) return;
+    const double beta = cg->beta;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) d[i] = fma(beta, d[i], r[i]);
+}
+
+// ------------------------------------------------------------------ FP32 inner kernels
+// r32 = r64 / |r64|, d32 = r32, x32 = 0; rho = r32.r32; stop2 = itol2 * rho
+__global__ void __launch_bounds__(kBT) k_inner_init(int n, const double* r64, float* r32, float* d32,
+                                                    float* x32, CgScalars* cg, double itol2,
+                                                    int max_iters, double* partials,
+                                                    unsigned int* counter) {
+    __shared__ double sm[kWarps];
+    const double scale = 1.0 / sqrt(cg->rr);
+    double part = 0.0;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) {
+        const float v = (float)(r64[i] * scale);
+        r32[i] = v;
+        d32[i] = v;
+        x32[i] = 0.f;
+        part += (double)v * (double)v;
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, partials, counter, &tot, sm) && threadIdx.x == 0) {
+        cg->rho = tot;
+        cg->rho0 = tot;
+        cg->stop2 = itol2 * tot;
+        cg->iters = 0;
+        cg->max_iters = max_iters;
+        cg->done = (tot > 0.0 && max_iters > 0) ? 0 : 1;
+    }
+}
+
+template <bool MATRIX_FREE>
+__global__ void __launch_bounds__(kBT) k_spmv32(PpeView c, const float* d, float* q, CgScalars* cg,
+                                                float coef, float re_f) {
+    if (*(volatile int*)&cg->done) return;
+    __shared__ double sm[kWarps];
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * kBT + threadIdx.x) >> 5, nw = (gridDim.x * kBT) >> 5;
+    double part = 0.0;
+    for (int i = gw; i < c.n; i += nw) {
+        const double dg = c.diag[i];
+        float qi = 0.f;
+        if (dg != 0.0) {
+            const float4 pi = MATRIX_FREE ? c.pos32s[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            qi = (float)dg * d[i] - row_dot32<MATRIX_FREE>(c, i, d, lane, pi, coef, re_f);
+        }
+        if (lane == 0) {
+            q[i] = qi;
+            part += (double)d[i] * (double)qi;
+        }
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, c.partials, &c.counter[1], &tot, sm) && threadIdx.x == 0) {
+        cg->dq = tot;
+        cg->alpha = (tot > 0.0) ? cg->rho / tot : 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(kBT) k_xr32(int n, float* x, float* r, const float* d, const float* q,
+                                              CgScalars* cg, double* partials, unsigned int* counter) {
+    if (*(volatile int*)&cg->done) return;
+    __shared__ double sm[kWarps];
+    const float alpha = (float)cg->alpha;
+    double part = 0.0;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) {
+        x[i] = fmaf(alpha, d[i], x[i]);
+        const float ri = fmaf(-alpha, q[i], r[i]);
+        r[i] = ri;
+        part += (double)ri * (double)ri;
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, partials, counter, &tot, sm) && threadIdx.x == 0) {
+        cg->beta = (cg->rho > 0.0) ? tot / cg->rho : 0.0;
+        cg->rho = tot;
+        cg->iters += 1;
+        if (tot <= cg->stop2 || cg->iters >= cg->max_iters || !(cg->dq > 0.0)) cg->done = 1;
+    }
+}
+
+__global__ void __launch_bounds__(kBT) k_d32(int n, const float* r, float* d, const CgScalars* cg) {
+    if (*(volatile const int*)&cg->done) return;
+    const float beta = (float)cg->beta;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) d[i] = fmaf(beta, d[i], r[i]);
+}
+
+// x64 += |r64| x32   (|r64| = sqrt(rr) of the residual that started the inner solve)
+__global__ void __launch_bounds__(kBT) k_outer_update(int n, double* x, const float* e, double scale_rr) {
+    const double s = sqrt(scale_rr);
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) x[i] = fma(s, (double)e[i], x[i]);
+}
+
+__global__ void k_clear_x(int n, double* x) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = 0.0;
+}
+}  // namespace
+
+static PpeView view(Ctx* c) {
+    PpeView v;
+    v.n = (int)c->n;
+    v.cap = c->cap;
+    v.col = c->nb_lap_col;
+    v.cnt = c->nb_lap_cnt;
+    v.v64 = c->nb_lap_v64;
+    v.v32 = c->nb_lap_v32;
+    v.diag = c->diag;
+    v.bvec = c->bvec;
+    v.pos32s = c->pos32_star;
+    v.partials = c->partials;
+    v.counter = c->st->counter;
+    return v;
+}
+
+// Poll the device scalars (one small copy + stream sync).
+static int read_scalars(Ctx* c) {
+    MPS_CUDA(c, cudaMemcpyAsync(c->cg_host, c->cg, sizeof(CgScalars), cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MPS_OK;
+}
+
+static int set_cg_limits(Ctx* c, int max_iters) {
+    CgScalars init{};
+    init.max_iters = max_iters;
+    MPS_CUDA(c, cudaMemcpyAsync(c->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream));
+    return MPS_OK;
+}
+
+// Launch up to `chunk` iterations of FP64 CG (extra launches exit at once once done).
+static void cg64_chunk(Ctx* c, int chunk) {
+    const int n = (int)c->n;
+    const int gv = vec_grid(c), gs = c->sms * 8;
+    double* x = c->p;
+    c->launches += 3 * chunk;
+    for (int k = 0; k < chunk; k++) {
+        k_spmv64<<<gs, kBT, 0, c->stream>>>(view(c), c->cg_d, c->cg_q, c->cg);
+        k_xr64<<<gv, kBT, 0, c->stream>>>(n, x, c->cg_r, c->cg_d, c->cg_q, c->cg, c->partials,
+                                          &c->st->counter[2]);
+        k_d64<<<gv, kBT, 0, c->stream>>>(n, c->cg_r, c->cg_d, c->cg);
+    }
+}
+
+static void cg32_chunk(Ctx* c, int chunk) {
+    const int n = (int)c->n;
+    const int gv = vec_grid(c), gs = c->sms * 8;
+    const float coef = (float)c->coef_ppe, re_f = (float)c->r_lap.re;
+    c->launches += 3 * chunk;
+    for (int k = 0; k < chunk; k++) {
+        if (c->prm.ppe_operator == 1)
+            k_spmv32<true><<<gs, kBT, 0, c->stream>>>(view(c), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+        else
+            k_spmv32<false><<<gs, kBT, 0, c->stream>>>(view(c), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+        k_xr32<<<gv, kBT, 0, c->stream>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_q32, c->cg,
+                                          c->partials, &c->st->counter[2]);
+        k_d32<<<gv, kBT, 0, c->stream>>>(n, c->cg_r32, c->cg_d32, c->cg);
+    }
+}
+
+int ppe_solve(Ctx* c, mps_report* rep) {
+    const int n = (int)c->n;
+    const double tol2 = c->prm.cg_tol * c->prm.cg_tol;
+    const int max_total = c->prm.cg_max_iter > 0 ? c->prm.cg_max_iter : (int)std::min<int64_t>(10 * c->n, 1 << 30);
+    const int gs = c->sms * 8, gv = vec_grid(c);
+    int rc;
+    k_clear_x<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->p);
+    c->launches += 2;
+    if ((rc = set_cg_limits(c, max_total))) return rc;
+    // r = b, d = b, rho = |b|^2, stop2 = tol^2 |b|^2
+    k_resid64<<<gs, kBT, 0, c->stream>>>(view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2, 1, 1);
+    if ((rc = read_scalars(c))) return rc;
+    const double bnorm2 = c->cg_host->rr;
+    const double stop2 = c->cg_host->stop2;
+    int total_iters = 0, outer = 0;
+    double rel = 0.0;
+    if (bnorm2 == 0.0) {
+        rep->cg_iters = 0;
+        rep->cg_outer = 0;
+        rep->cg_resid = 0.0;
+        return MPS_OK;
+    }
+    int chunk = std::max(4, c->last_cg_iters + 1);
+    if (c->prm.precision == 0) {
+        for (;;) {
+            cg64_chunk(c, chunk);
+            if ((rc = read_scalars(c))) return rc;
+            if (!c->cg_host->done) { chunk = std::max(4, chunk / 2); continue; }
+            total_iters = c->cg_host->iters;
+            // true residual; restart from it if the recurrence drifted
+            c->launches += 1;
+            k_resid64<<<gs, kBT, 0, c->stream>>>(view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2, 0, 1);
+            if ((rc = read_scalars(c))) return rc;
+            rel = sqrt(c->cg_host->rr / bnorm2);
+            if (c->cg_host->rr <= stop2) break;
+            if (total_iters >= max_total) {
+                rep->cg_iters = total_iters;
+                rep->cg_outer = outer;
+                rep->cg_resid = rel;
+                return MPS_ECG_NOCONV;
+            }
+            outer++;   // restart with the true residual (done was reset by k_resid64)
+            chunk = 4;
+        }
+    } else {
+        // mixed: x = 0, r = b already.  Loop: inner FP32 solve, x += e, true residual.
+        const double itol2 = c->prm.inner_tol * c->prm.inner_tol;
+        const int max_outer = c->prm.max_outer > 0 ? c->prm.max_outer : 30;
+        double rr = bnorm2;
+        for (;;) {
+            if (rr <= stop2) break;
+            if (outer >= max_outer || total_iters >= max_total) {
+                rep->cg_iters = total_iters;
+                rep->cg_outer = outer;
+                rep->cg_resid = sqrt(rr / bnorm2);
+                return MPS_ECG_NOCONV;
+            }
+            c->launches += 3;
+            k_inner_init<<<gv, kBT, 0, c->stream>>>(n, c->cg_r, c->cg_r32, c->cg_d32, c->cg_x32, c->cg,
+                                                    itol2, max_total - total_iters, c->partials,
+                                                    &c->st->counter[3]);
+            for (;;) {
+                cg32_chunk(c, chunk);
+                if ((rc = read_scalars(c))) return rc;
+                if (c->cg_host->done) break;
+                chunk = std::max(4, chunk / 2);
+            }
+            total_iters += c->cg_host->iters;
+            k_outer_update<<<gv, kBT, 0, c->stream>>>(n, c->p, c->cg_x32, rr);
+            k_resid64<<<gs, kBT, 0, c->stream>>>(view(c), c->p, c->cg_r, nullptr, c->cg, tol2, 0, 0);
+            if ((rc = read_scalars(c))) return rc;
+            rr = c->cg_host->rr;
+            outer++;
+        }
+        rel = sqrt(rr / bnorm2);
+    }
+    c->last_cg_iters = (c->prm.precision == 0) ? total_iters : std::max(4, total_iters / std::max(outer, 1));
+    rep->cg_iters = total_iters;
+    rep->cg_outer = outer;
+    rep->cg_resid = rel;
+    MPS_CUDA(c, cudaGetLastError());
+    return MPS_OK;
+}
+
+}  // namespace mps

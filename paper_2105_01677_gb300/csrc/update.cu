@@ -1,0 +1,207 @@
+// update.cu -- pressure clamp and minimum pressure, gradient correction, state transfers.
+//
+// Clamp / p_hat (PPE path): p_i = max(p_i, 0); p_hat_i = min(p_i, min_j p_j) over the
+// non-dummy neighbours j within re_n at r* (the stabilising p_hat of the gradient).
+// Gradient (difference form of the multi-density gradient of Sec. 3.2.1, one density):
+//   grad p_i = d/n0 sum_j (p_j - p_hat_i)/|r_ij|^2 r_ij w(|r_ij|),  r_ij = r*_j - r*_i,
+// over non-dummy j within re_n; FLUID only:
+//   u' = -(dt/rho) grad p_i,  u = u* + u',  r = r* + dt u'   (first-order Euler, Sec. 3.1).
+#include "mps_internal.cuh"
+
+namespace mps {
+
+namespace {
+constexpr int kBT = 256;
+
+__global__ void __launch_bounds__(kBT)
+    k_clamp_pmin(int n, const int8_t* type, double* p, double* phat, const int32_t* ncol,
+                 const int32_t* ncnt, int cap_n, int clamp) {
+    int i = blockIdx.x * kBT + threadIdx.x;
+    if (i >= n) return;
+    double pi = p[i];
+    if (clamp) pi = fmax(pi, 0.0);
+    double m = pi;
+    if (type[i] == kFluid) {
+        const int cnt = ncnt[i];
+        const size_t base = (size_t)i * cap_n;
+        for (int k = 0; k < cnt; k++) {
+            double pj = p[ncol[base + k]];
+            if (clamp) pj = fmax(pj, 0.0);
+            m = fmin(m, pj);
+        }
+    }
+    phat[i] = m;
+}
+
+// p was clamped on read above; store the clamped values once every p_hat is computed
+__global__ void __launch_bounds__(kBT) k_clamp_store(int n, double* p) {
+    int i = blockIdx.x * kBT + threadIdx.x;
+    if (i < n) p[i] = fmax(p[i], 0.0);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kBT)
+    k_gradient(int n, const int8_t* type, const double4* ps, const float4* ps32, const double4* us,
+               const double* p, const double* phat, const int32_t* ncol, const int32_t* ncnt,
+               int cap_n, double re, float re_f, double coef_grad, double dt, double rho,
+               double4* pos, double4* vel) {
+    int i = blockIdx.x * kBT + threadIdx.x;
+    if (i >= n || type[i] != kFluid) return;
+    const double4 pi = ps[i];
+    const double ph = phat[i];
+    const int cnt = ncnt[i];
+    const size_t base = (size_t)i * cap_n;
+    double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    if (MIXED) {
+        const float4 qi = ps32[i];
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+        for (int k = 0; k < cnt; k++) {
+            const int j = ncol[base + k];
+            const float4 qj = ps32[j];
+            const float dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            const float rs = rsqrtf(r2);
+            const float w = fmaf(re_f, rs, -1.f);
+            const float f = (float)(p[j] - ph) * (w * rs * rs);
+            f0 = fmaf(f, dx, f0);
+            f1 = fmaf(f, dy, f1);
+            f2 = fmaf(f, dz, f2);
+        }
+        g0 = f0;
+        g1 = f1;
+        g2 = f2;
+    } else {
+        for (int k = 0; k < cnt; k++) {
+            const int j = ncol[base + k];
+            const double4 pj = ps[j];
+            const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+            const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            const double rs = rsqrt(r2);
+            const double w = fma(re, rs, -1.0);
+            const double f = (p[j] - ph) * (w * rs * rs);
+            g0 = fma(f, dx, g0);
+            g1 = fma(f, dy, g1);
+            g2 = fma(f, dz, g2);
+        }
+    }
+    const double k = -(dt / rho) * coef_grad;
+    const double4 u = us[i];
+    const double d0 = k * g0, d1 = k * g1, d2 = k * g2;
+    vel[i] = make_double4(u.x + d0, u.y + d1, u.z + d2, 0.0);
+    pos[i] = make_double4(pi.x + dt * d0, pi.y + dt * d1, pi.z + dt * d2, 0.0);
+}
+
+// non-fluid particles keep r = r*, u = u* (walls and dummies do not move)
+__global__ void __launch_bounds__(kBT) k_copy_back(int n, const int8_t* type, const double4* ps,
+                                                   const double4* us, double4* pos, double4* vel) {
+    int i = blockIdx.x * kBT + threadIdx.x;
+    if (i >= n || type[i] == kFluid) return;
+    pos[i] = ps[i];
+    vel[i] = us[i];
+}
+
+__global__ void __launch_bounds__(kBT)
+    k_unpermute(int n, int dim, const int32_t* id, const double4* pos, const double4* vel,
+                const double* p, const double* nstar, const uint8_t* flag, const int8_t* type,
+                double* o_pos, double* o_vel, double* o_p, double* o_n, uint8_t* o_f, int8_t* o_t) {
+    int s = blockIdx.x * kBT + threadIdx.x;
+    if (s >= n) return;
+    const int i = id[s];
+    const double4 x = pos[s], u = vel[s];
+    const double xa[3] = {x.x, x.y, x.z}, ua[3] = {u.x, u.y, u.z};
+    for (int a = 0; a < dim; a++) {
+        if (o_pos) o_pos[(size_t)i * dim + a] = xa[a];
+        if (o_vel) o_vel[(size_t)i * dim + a] = ua[a];
+    }
+    if (o_p) o_p[i] = p[s];
+    if (o_n) o_n[i] = nstar[s];
+    if (o_f) o_f[i] = flag[s];
+    if (o_t) o_t[i] = type[s];
+}
+
+__global__ void __launch_bounds__(kBT) k_unpermute_u32(int n, const int32_t* id, const uint32_t* in,
+                                                       uint32_t* out) {
+    int s = blockIdx.x * kBT + threadIdx.x;
+    if (s < n) out[id[s]] = in[s];
+}
+
+// state from caller order; slot s = particle s (identity order until the next sort)
+__global__ void __launch_bounds__(kBT)
+    k_ingest(int n, int dim, const double* i_pos, const double* i_vel, const int8_t* i_t,
+             double4* pos, double4* vel, int8_t* type, int32_t* id, double* p, double* nstar,
+             uint8_t* flag, int keep_vel, int keep_types, GridDesc g, float4* pos32) {
+    int s = blockIdx.x * kBT + threadIdx.x;
+    if (s >= n) return;
+    double x[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < dim; a++) x[a] = i_pos[(size_t)s * dim + a];
+    pos[s] = make_double4(x[0], x[1], x[2], 0.0);
+    if (!keep_vel) {
+        double u[3] = {0.0, 0.0, 0.0};
+        if (i_vel)
+            for (int a = 0; a < dim; a++) u[a] = i_vel[(size_t)s * dim + a];
+        vel[s] = make_double4(u[0], u[1], u[2], 0.0);
+    }
+    if (!keep_types) type[s] = i_t[s];
+    id[s] = s;
+    p[s] = 0.0;
+    nstar[s] = 0.0;
+    flag[s] = 0;
+    pos32[s] = make_float4((float)(x[0] - g.bmin[0]), (float)(x[1] - g.bmin[1]),
+                           (float)(x[2] - g.bmin[2]), __int_as_float((int)type[s]));
+}
+}  // namespace
+
+void launch_clamp_pmin(Ctx* c) {
+    const int n = (int)c->n;
+    const int nb = (n + kBT - 1) / kBT;
+    const int clamp = c->prm.clamp_negative_p ? 1 : 0;
+    k_clamp_pmin<<<nb, kBT, 0, c->stream>>>(n, c->type, c->p, c->phat, c->nb_n_col, c->nb_n_cnt,
+                                            c->cap_n, clamp);
+    if (clamp) k_clamp_store<<<nb, kBT, 0, c->stream>>>(n, c->p);
+    c->launches += clamp ? 2 : 1;
+}
+
+void launch_gradient_correct(Ctx* c) {
+    const int n = (int)c->n;
+    const int nb = (n + kBT - 1) / kBT;
+    const mps_params& P = c->prm;
+    if (P.precision == 1)
+        k_gradient<true><<<nb, kBT, 0, c->stream>>>(n, c->type, c->pos_star, c->pos32_star, c->vel_star,
+                                                    c->p, c->phat, c->nb_n_col, c->nb_n_cnt, c->cap_n,
+                                                    c->r_n.re, c->r_n.re_f, c->coef_grad, P.dt, P.rho,
+                                                    c->pos, c->vel);
+    else
+        k_gradient<false><<<nb, kBT, 0, c->stream>>>(n, c->type, c->pos_star, c->pos32_star, c->vel_star,
+                                                     c->p, c->phat, c->nb_n_col, c->nb_n_cnt, c->cap_n,
+                                                     c->r_n.re, c->r_n.re_f, c->coef_grad, P.dt, P.rho,
+                                                     c->pos, c->vel);
+    k_copy_back<<<nb, kBT, 0, c->stream>>>(n, c->type, c->pos_star, c->vel_star, c->pos, c->vel);
+    c->launches += 2;
+}
+
+void launch_unpermute(Ctx* c, double* d_pos, double* d_vel, double* d_p, double* d_nstar,
+                      uint8_t* d_flags, int8_t* d_types) {
+    const int n = (int)c->n;
+    k_unpermute<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(n, c->dim, c->id, c->pos, c->vel, c->p,
+                                                             c->nstar, c->flag, c->type, d_pos, d_vel,
+                                                             d_p, d_nstar, d_flags, d_types);
+    c->launches += 1;
+}
+
+void launch_unpermute_u32(Ctx* c, const uint32_t* in, uint32_t* out) {
+    const int n = (int)c->n;
+    k_unpermute_u32<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(n, c->id, in, out);
+    c->launches += 1;
+}
+
+void launch_ingest(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types,
+                   bool keep_vel, bool keep_types) {
+    const int n = (int)c->n;
+    k_ingest<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(n, c->dim, d_pos, d_vel, d_types, c->pos,
+                                                          c->vel, c->type, c->id, c->p, c->nstar,
+                                                          c->flag, keep_vel ? 1 : 0,
+                                                          keep_types ? 1 : 0, c->grid, c->pos32);
+    c->launches += 1;
+}
+
+}  // namespace mps

@@ -1,0 +1,322 @@
+"""ctypes binding of the GB300 MPS library (C ABI in include/mps.h).
+
+Argument marshalling only: every stage of the time step runs in the library's CUDA kernels.
+Functions keep the C names (mps_create, mps_step, mps_solve_ppe, mps_read_state, ...).
+Device memory for a context comes from PyTorch's caching allocator when `torch_alloc=True`
+(through the library's allocation hooks) and the context runs on the current PyTorch stream.
+
+There is no CPU fallback: if the shared library is missing or cannot be loaded, `lib()`
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+FLUID, WALL, DUMMY, GHOST = 0, 1, 2, 3
+OK, EINVAL, ENOMEM, ECG_NOCONV, ENONFINITE, ESKIN, ECOINCIDENT, ECAP, EDEVICE = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+RELEASE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class mps_params(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("pressure_mode", C.c_int32), ("l0", C.c_double),
+                ("re_n", C.c_double), ("re_lap", C.c_double), ("rho", C.c_double),
+                ("nu", C.c_double), ("dt", C.c_double), ("beta", C.c_double),
+                ("g", C.c_double * 3), ("c0", C.c_double), ("gamma", C.c_double),
+                ("alpha_c", C.c_double), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
+                ("precision", C.c_int32), ("clamp_negative_p", C.c_int32),
+                ("nbr_cap", C.c_int32), ("cell_skin", C.c_double),
+                ("box_min", C.c_double * 3), ("box_max", C.c_double * 3),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32),
+                ("ppe_operator", C.c_int32), ("device", C.c_int32), ("reserved0", C.c_int32),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
+                ("alloc_user", C.c_void_p)]
+
+
+class mps_report(C.Structure):
+    _fields_ = [("status", C.c_int32), ("cg_iters", C.c_int32), ("cg_outer", C.c_int32),
+                ("reserved0", C.c_int32), ("cg_resid", C.c_double), ("n_surface", C.c_int64),
+                ("n_ghost", C.c_int64), ("n_ppe_rows", C.c_int64), ("max_disp", C.c_double),
+                ("n0_pnd", C.c_double), ("n0_lap", C.c_double), ("lambda_", C.c_double),
+                ("steps_done", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved0"}
+        d["lambda"] = d.pop("lambda_")
+        return d
+
+
+EXPORTS = ("mps_params_default", "mps_create", "mps_step", "mps_solve_ppe", "mps_read_state",
+           "mps_write_state", "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants",
+           "mps_set_profiling", "mps_get_profile", "mps_destroy", "mps_strerror")
+STAGES = ("bucket", "predict", "build", "ppe", "update")
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib(build_if_missing: bool = False):
+    """Load the shared library (optionally building it first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB_PATH
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"GB300 MPS library not built ({path}); run __graft_entry__.build()")
+    L = C.CDLL(path)
+    d, i8, u8 = C.POINTER(C.c_double), C.POINTER(C.c_int8), C.POINTER(C.c_uint8)
+    vpp = C.POINTER(C.c_void_p)
+    L.mps_params_default.argtypes = [C.POINTER(mps_params)]
+    L.mps_params_default.restype = None
+    L.mps_create.argtypes = [d, d, i8, C.c_int64, C.POINTER(mps_params), vpp]
+    L.mps_step.argtypes = [C.c_void_p, C.c_int32, C.POINTER(mps_report)]
+    L.mps_solve_ppe.argtypes = [C.c_void_p, C.POINTER(mps_report)]
+    L.mps_read_state.argtypes = [C.c_void_p, d, d, d, d, u8, i8]
+    L.mps_write_state.argtypes = [C.c_void_p, d, d, i8]
+    L.mps_debug_cells.argtypes = [C.c_void_p, C.POINTER(C.c_uint32)]
+    L.mps_debug_neighbors.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int32), C.c_int64]
+    L.mps_get_constants.argtypes = [C.c_void_p, d]
+    L.mps_set_profiling.argtypes = [C.c_void_p, C.c_int32]
+    L.mps_get_profile.argtypes = [C.c_void_p, d, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.mps_destroy.argtypes = [C.c_void_p]
+    L.mps_destroy.restype = None
+    L.mps_strerror.argtypes = [C.c_int]
+    L.mps_strerror.restype = C.c_char_p
+    for f in ("mps_create", "mps_step", "mps_solve_ppe", "mps_read_state", "mps_write_state",
+              "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants", "mps_set_profiling",
+              "mps_get_profile"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+class MPSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().mps_strerror(code).decode()
+        super().__init__(f"{where}: {msg}")
+        self.code = code
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise MPSError(rc, where)
+
+
+def _ptr(a, ct):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ct))
+
+
+def mps_strerror(code: int) -> str:
+    return lib().mps_strerror(code).decode()
+
+
+def mps_params_default(**kw) -> mps_params:
+    """Defaults of the C library, then keyword overrides (g / box as sequences)."""
+    P = mps_params()
+    lib().mps_params_default(C.byref(P))
+    for k, v in kw.items():
+        if k in ("g", "box_min", "box_max"):
+            arr = getattr(P, k)
+            for a in range(3):
+                arr[a] = float(v[a]) if a < len(v) else 0.0
+        else:
+            setattr(P, k, v)
+    return P
+
+
+class _TorchAllocator:
+    """Device memory hooks backed by torch.cuda's caching allocator."""
+
+    def __init__(self, device: int, stream_ptr):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.stream = stream_ptr
+        self._live = {}
+
+        def _alloc(nbytes, user):
+            try:
+                ptr = torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device)
+            except Exception:
+                return None
+            self._live[ptr] = nbytes
+            return ptr
+
+        def _release(ptr, user):
+            if ptr in self._live:
+                del self._live[ptr]
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.release = RELEASE_FN(_release)
+
+
+def mps_create(pos, vel, types, params: mps_params, torch_alloc: bool = False,
+               use_torch_stream: bool = False):
+    """Create a context; returns an opaque handle (c_void_p).  pos/vel: (n, dim) float64."""
+    L = lib()
+    pos = np.ascontiguousarray(pos, np.float64)
+    vel = None if vel is None else np.ascontiguousarray(vel, np.float64)
+    types = np.ascontiguousarray(types, np.int8)
+    n = len(types)
+    keep = None
+    if torch_alloc or use_torch_stream:
+        import torch
+        dev = int(params.device)
+        if use_torch_stream:
+            params.stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        if torch_alloc:
+            keep = _TorchAllocator(dev, params.stream)
+            params.alloc = keep.alloc
+            params.release = keep.release
+    h = C.c_void_p()
+    rc = L.mps_create(_ptr(pos, C.c_double), _ptr(vel, C.c_double), _ptr(types, C.c_int8), n,
+                      C.byref(params), C.byref(h))
+    _check(rc, "mps_create")
+    _keepalive[h.value] = (keep, params)
+    return h
+
+
+_keepalive = {}
+
+
+def mps_step(h, nsteps: int = 1, check: bool = True):
+    rep = mps_report()
+    rc = lib().mps_step(h, int(nsteps), C.byref(rep))
+    if check:
+        _check(rc, "mps_step")
+    return rc, rep.as_dict()
+
+
+def mps_solve_ppe(h, check: bool = True):
+    rep = mps_report()
+    rc = lib().mps_solve_ppe(h, C.byref(rep))
+    if check:
+        _check(rc, "mps_solve_ppe")
+    return rc, rep.as_dict()
+
+
+def mps_read_state(h, n: int, dim: int, pos=None, vel=None, p=None, n_star=None, flags=None,
+                   types=None, want=("pos", "vel", "p", "n_star", "flags", "types")):
+    """Read the state in original particle order into (optional, preallocated) arrays."""
+    out = {}
+    if "pos" in want:
+        out["pos"] = pos if pos is not None else np.empty((n, dim), np.float64)
+    if "vel" in want:
+        out["vel"] = vel if vel is not None else np.empty((n, dim), np.float64)
+    if "p" in want:
+        out["p"] = p if p is not None else np.empty(n, np.float64)
+    if "n_star" in want:
+        out["n_star"] = n_star if n_star is not None else np.empty(n, np.float64)
+    if "flags" in want:
+        out["flags"] = flags if flags is not None else np.empty(n, np.uint8)
+    if "types" in want:
+        out["types"] = types if types is not None else np.empty(n, np.int8)
+    rc = lib().mps_read_state(h, _ptr(out.get("pos"), C.c_double), _ptr(out.get("vel"), C.c_double),
+                              _ptr(out.get("p"), C.c_double), _ptr(out.get("n_star"), C.c_double),
+                              _ptr(out.get("flags"), C.c_uint8), _ptr(out.get("types"), C.c_int8))
+    _check(rc, "mps_read_state")
+    return out
+
+
+def mps_write_state(h, pos, vel=None, types=None):
+    pos = np.ascontiguousarray(pos, np.float64)
+    vel = None if vel is None else np.ascontiguousarray(vel, np.float64)
+    types = None if types is None else np.ascontiguousarray(types, np.int8)
+    _check(lib().mps_write_state(h, _ptr(pos, C.c_double), _ptr(vel, C.c_double),
+                                 _ptr(types, C.c_int8)), "mps_write_state")
+
+
+def mps_debug_cells(h, n: int):
+    out = np.empty(n, np.uint32)
+    _check(lib().mps_debug_cells(h, _ptr(out, C.c_uint32)), "mps_debug_cells")
+    return out
+
+
+def mps_debug_neighbors(h, n: int, which: int):
+    off = np.empty(n + 1, np.int64)
+    _check(lib().mps_debug_neighbors(h, which, _ptr(off, C.c_int64), None, 0), "mps_debug_neighbors")
+    ids = np.empty(max(int(off[-1]), 1), np.int32)
+    _check(lib().mps_debug_neighbors(h, which, _ptr(off, C.c_int64), _ptr(ids, C.c_int32), len(ids)),
+           "mps_debug_neighbors")
+    return off, ids[: off[-1]]
+
+
+def mps_get_constants(h):
+    out = np.zeros(8, np.float64)
+    _check(lib().mps_get_constants(h, _ptr(out, C.c_double)), "mps_get_constants")
+    return dict(n0_pnd=out[0], n0_lap=out[1], lambda_=out[2], h=out[3],
+                ncell=(int(out[4]), int(out[5]), int(out[6])), cap=int(out[7]))
+
+
+def mps_set_profiling(h, on: bool = True):
+    _check(lib().mps_set_profiling(h, 1 if on else 0), "mps_set_profiling")
+
+
+def mps_get_profile(h):
+    ms = np.zeros(len(STAGES), np.float64)
+    calls = np.zeros(len(STAGES), np.int64)
+    launches = np.zeros(1, np.int64)
+    _check(lib().mps_get_profile(h, _ptr(ms, C.c_double), _ptr(calls, C.c_int64),
+                                 _ptr(launches, C.c_int64)), "mps_get_profile")
+    return dict(stage_ms=dict(zip(STAGES, ms.tolist())),
+                stage_calls=dict(zip(STAGES, calls.tolist())), launches=int(launches[0]))
+
+
+def mps_destroy(h):
+    if h is not None and h.value:
+        lib().mps_destroy(h)
+        _keepalive.pop(h.value, None)
+
+
+class Simulation:
+    """Convenience owner of one context built from a scene-like object."""
+
+    def __init__(self, scene, torch_alloc: bool = False, use_torch_stream: bool = False, **params):
+        self.n, self.dim = scene.n, scene.dim
+        g = (0.0, -9.81, 0.0) if scene.dim == 2 else (0.0, 0.0, -9.81)
+        base = dict(dim=scene.dim, l0=scene.l0, re_n=2.1 * scene.l0, re_lap=4.0 * scene.l0, g=g,
+                    box_min=tuple(scene.box_min), box_max=tuple(scene.box_max))
+        base.update(params)
+        self.params = mps_params_default(**base)
+        self.h = mps_create(scene.pos, scene.vel, scene.types, self.params, torch_alloc,
+                            use_torch_stream)
+
+    def step(self, nsteps: int = 1, check: bool = True):
+        return mps_step(self.h, nsteps, check)
+
+    def solve_ppe(self, check: bool = True):
+        return mps_solve_ppe(self.h, check)
+
+    def read(self, **kw):
+        return mps_read_state(self.h, self.n, self.dim, **kw)
+
+    def write(self, pos, vel=None, types=None):
+        mps_write_state(self.h, pos, vel, types)
+
+    def constants(self):
+        return mps_get_constants(self.h)
+
+    def close(self):
+        mps_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            if self.h is not None:
+                self.close()
+        except Exception:
+            pass

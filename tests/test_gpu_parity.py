@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on the same
+seeded inputs.  Bit-exact: cell keys, neighbour sets, free-surface flags (outside a
+documented rounding band, asserted empty).  FP64: relative error <= 1e-10 with both CG
+solves run to 1e-13.  Mixed precision: the stated bound (p: relative L2 over fluid <= 1e-5,
+positions: <= 1e-6 l0) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+import scenes
+from _parity import (FP64_TOL, PARITY_CG_TOL, compare_step, gpu_params, oracle_params, rel_err,
+                     run_gpu, run_oracle, small_3d)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    __graft_entry__.build()
+    oracle.set_threads(0)
+
+
+def _mps():
+    from paper_2105_01677_gb300 import mps
+    return mps
+
+
+# ------------------------------------------------------------------ constants, keys, sets
+@pytest.mark.parametrize("dim", [2, 3])
+def test_constants_match_oracle(dim):
+    sc = scenes.dam_break_2d() if dim == 2 else small_3d()
+    mps = _mps()
+    sim = mps.Simulation(sc, **{})
+    c = sim.constants()
+    sim.close()
+    n0n, _ = oracle.lattice(dim, sc.l0, 2.1 * sc.l0)
+    n0l, lam = oracle.lattice(dim, sc.l0, 4.0 * sc.l0)
+    assert c["n0_pnd"] == pytest.approx(n0n, rel=1e-14)
+    assert c["n0_lap"] == pytest.approx(n0l, rel=1e-14)
+    assert c["lambda_"] == pytest.approx(lam, rel=1e-14)
+
+
+def _key_scenes():
+    out = [scenes.dam_break_2d(seed=2), small_3d(seed=2)]
+    for n, dim in ((2049, 2), (4097, 3), (6143, 3)):
+        out.append(scenes.random_cloud(n, dim, seed=n, clustered=(dim == 3)))
+    # particles exactly on cell faces and just outside the grid
+    sc = scenes.random_cloud(3000, 3, seed=5)
+    h = 4.0 * sc.l0 * 1.1
+    k = np.arange(30) % 7
+    sc.pos[:30, 0] = sc.box_min[0] + k * h
+    sc.pos[30:40, 1] = sc.box_max[1] + 0.01
+    sc.pos[40:50, 2] = sc.box_min[2] - 1e-12
+    out.append(sc)
+    return out
+
+
+@pytest.mark.parametrize("idx", range(6))
+def test_cell_keys_bit_exact(idx):
+    sc = _key_scenes()[idx]
+    mps = _mps()
+    sim = mps.Simulation(sc)
+    got = mps.mps_debug_cells(sim.h, sc.n)
+    sim.close()
+    prm = oracle_params(sc)
+    ref, _ = oracle.cell_keys(prm, sc.pos, sc.types)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("idx", range(5))
+@pytest.mark.parametrize("which", [0, 1])
+def test_neighbor_sets_bit_exact(idx, which):
+    sc = _key_scenes()[idx]
+    types = sc.types.copy()
+    types[::29] = scenes.GHOST
+    sc = scenes.Scene(sc.dim, sc.l0, sc.pos, sc.vel, types, sc.box_min, sc.box_max)
+    mps = _mps()
+    sim = mps.Simulation(sc)
+    off, ids = mps.mps_debug_neighbors(sim.h, sc.n, which)
+    sim.close()
+    re = (2.1 if which == 0 else 4.0) * sc.l0
+    mode = 0 if sc.n <= 5000 else 1
+    roff, rids = oracle.neighbors(sc.dim, sc.pos, types, re, mode=mode)
+    assert np.array_equal(off, roff)
+    assert np.array_equal(ids, rids)
+
+
+# ------------------------------------------------------------------ one FP64 step
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_step_fp64_dam_break_2d(seed):
+    sc = scenes.dam_break_2d(seed=seed)
+    kw = dict(cg_tol=PARITY_CG_TOL)
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc, **kw))
+    orep, ost, prm = run_oracle(sc, **kw)
+    compare_step(sc, got, ost, prm)
+    assert rep["n_surface"] == orep["n_surface"] and rep["n_ppe_rows"] == orep["n_ppe_rows"]
+    assert rep["cg_resid"] <= PARITY_CG_TOL
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_step_fp64_dam_break_3d_small(seed):
+    sc = small_3d(seed=seed)
+    kw = dict(cg_tol=PARITY_CG_TOL)
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc, **kw))
+    orep, ost, prm = run_oracle(sc, **kw)
+    compare_step(sc, got, ost, prm)
+    assert rep["n_ppe_rows"] == orep["n_ppe_rows"]
+
+
+def test_solve_ppe_fp64_leaves_state():
+    sc = scenes.dam_break_2d(seed=1)
+    kw = dict(cg_tol=PARITY_CG_TOL)
+    rc, rep, got, _ = run_gpu(sc, solve_only=True, **gpu_params(sc, **kw))
+    orep, ost, prm = run_oracle(sc, solve_only=True, **kw)
+    assert rel_err(got["p"], ost.p) <= FP64_TOL
+    assert rel_err(got["n_star"], ost.nstar) <= FP64_TOL
+    assert np.array_equal(got["pos"], sc.pos) and np.array_equal(got["vel"], sc.vel)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_step_eos_fp64(dim):
+    sc = scenes.dam_break_2d(seed=3) if dim == 2 else small_3d(seed=3)
+    kw = dict(pressure_mode=1, c0=20.0)
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc, **kw))
+    orep, ost, prm = run_oracle(sc, **kw)
+    compare_step(sc, got, ost, prm)
+
+
+def test_step_without_clamp_and_with_viscosity():
+    sc = scenes.dam_break_2d(seed=2)
+    rng = np.random.default_rng(0)
+    sc.vel[sc.types == 0] = rng.standard_normal((sc.n_fluid, 2)) * 0.1
+    kw = dict(cg_tol=PARITY_CG_TOL, clamp_negative_p=0, nu=1e-3)
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc, **kw))
+    orep, ost, prm = run_oracle(sc, **kw)
+    compare_step(sc, got, ost, prm)
+
+
+# ------------------------------------------------------------------ mixed precision
+def _mixed_errors(sc, got, ost):
+    f = sc.types == scenes.FLUID
+    ep = np.linalg.norm(got["p"][f] - ost.p[f]) / np.linalg.norm(ost.p[f])
+    ex = np.abs(got["pos"] - ost.pos).max() / sc.l0
+    return ep, ex
+
+
+@pytest.mark.parametrize("op", [0, 1])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_step_mixed_precision_bound(dim, op):
+    sc = scenes.dam_break_2d(seed=1) if dim == 2 else small_3d(seed=1)
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc, precision=1, ppe_operator=op, cg_tol=1e-8))
+    orep, ost, prm = run_oracle(sc, cg_tol=PARITY_CG_TOL)
+    ep, ex = _mixed_errors(sc, got, ost)
+    assert rep["cg_resid"] <= 1e-8
+    assert ep <= 1e-5, ep
+    assert ex <= 1e-6, ex
+    assert np.array_equal(got["flags"], ost.flags)
+    assert rel_err(got["n_star"], ost.nstar) <= 1e-12
+
+
+# ------------------------------------------------------------------ along a trajectory
+def test_single_steps_from_oracle_states_along_dam_break():
+    """Oracle trajectory; at steps 0, 50 and 99 the GPU restarts from the oracle state
+    (mps_write_state) and both take one step."""
+    sc = scenes.dam_break_2d(seed=1)
+    kw = dict(cg_tol=PARITY_CG_TOL)
+    prm = oracle_params(sc, **kw)
+    st = oracle.State.from_scene(sc)
+    mps = _mps()
+    sim = mps.Simulation(sc, torch_alloc=True, **gpu_params(sc, **kw))
+    try:
+        for k in range(100):
+            if k in (0, 50, 99):
+                sim.write(st.pos, st.vel, st.types)
+                sim.step(1)
+                got = sim.read()
+                before = oracle.State(st.pos.copy(), st.vel.copy(), st.types.copy(), st.p, st.nstar, st.flags)
+                nxt = st.copy()
+                oracle.step(prm, nxt)
+                ref_scene = scenes.Scene(2, sc.l0, before.pos, before.vel, before.types, sc.box_min, sc.box_max)
+                compare_step(ref_scene, got, nxt, prm)
+            oracle.step(prm, st)
+    finally:
+        sim.close()
+
+
+def test_gpu_dam_break_100_steps():
+    sc = scenes.dam_break_2d(seed=3)
+    mps = _mps()
+    sim = mps.Simulation(sc, torch_alloc=True)
+    n0, _ = oracle.lattice(2, sc.l0, 2.1 * sc.l0)
+    for _ in range(100):
+        rc, rep = sim.step(1)
+        assert rep["cg_resid"] <= 1e-8
+    got = sim.read()
+    sim.close()
+    assert np.all(np.isfinite(got["pos"])) and np.all(np.isfinite(got["p"]))
+    assert np.count_nonzero(got["types"] == scenes.FLUID) == 800
+    assert got["n_star"][got["types"] == scenes.FLUID].max() < 1.2 * n0
+    assert rep["steps_done"] == 100
+
+
+def test_deterministic_bits():
+    sc = small_3d(seed=1)
+    outs = []
+    for _ in range(2):
+        rc, rep, got, _ = run_gpu(sc, nsteps=3, **gpu_params(sc))
+        outs.append(got)
+    for k in ("pos", "vel", "p", "n_star", "flags"):
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+# ------------------------------------------------------------------ edge cases and errors
+def test_lone_particle_free_fall():
+    sc = scenes.Scene(2, 0.01, np.array([[0.3, 0.3]]), np.array([[0.2, -0.1]]),
+                      np.zeros(1, np.int8), np.zeros(3), np.array([1.0, 1.0, 0.0]))
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc, dt=1e-3))
+    u1 = np.array([0.2, -0.1 - 9.81e-3])
+    np.testing.assert_allclose(got["vel"][0], u1, rtol=1e-15)
+    np.testing.assert_allclose(got["pos"][0], [0.3 + 1e-3 * 0.2, 0.3 + 1e-3 * u1[1]], rtol=1e-15)
+    assert got["flags"][0] == 1 and got["p"][0] == 0.0
+
+
+def test_all_ghost_scene_is_a_no_op():
+    sc = scenes.dam_break_2d(seed=1)
+    sc.types[:] = scenes.GHOST
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc))
+    assert rc == 0 and rep["n_ppe_rows"] == 0 and rep["n_ghost"] == sc.n
+    assert np.array_equal(got["pos"], sc.pos)
+
+
+def test_particle_leaving_grid_becomes_ghost():
+    sc = scenes.dam_break_2d(seed=1)
+    sc.pos[7] = [5.0, 5.0]
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc))
+    orep, ost, prm = run_oracle(sc)
+    assert got["types"][7] == scenes.GHOST and rep["n_ghost"] == 1 == orep["n_ghost"]
+    assert np.all(got["vel"][7] == 0.0)
+
+
+@pytest.mark.parametrize("case", ["coincident", "noconv", "skin", "cap"])
+def test_error_statuses(case):
+    mps = _mps()
+    sc = scenes.dam_break_2d(seed=1)
+    kw = {}
+    if case == "coincident":
+        sc.pos[5] = sc.pos[6]
+        expect = mps.ECOINCIDENT
+    elif case == "noconv":
+        kw = dict(cg_max_iter=1)
+        expect = mps.ECG_NOCONV
+    elif case == "skin":
+        kw = dict(cell_skin=0.0)
+        expect = mps.ESKIN
+    else:
+        kw = dict(nbr_cap=8)
+        expect = mps.ECAP
+    rc, rep, got, _ = run_gpu(sc, check=False, **gpu_params(sc, **kw))
+    assert rc == expect, mps.mps_strerror(rc)
+    if case != "cap":
+        orc, _ = oracle.step(oracle_params(sc, **kw), oracle.State.from_scene(sc), check=False)
+        assert orc == expect
+
+
+def test_default_allocator_and_own_stream():
+    sc = scenes.dam_break_2d(seed=1)
+    rc, rep, got, _ = run_gpu(sc, torch_alloc=False, **gpu_params(sc, cg_tol=PARITY_CG_TOL))
+    orep, ost, prm = run_oracle(sc, cg_tol=PARITY_CG_TOL)
+    compare_step(sc, got, ost, prm)
