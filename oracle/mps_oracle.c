@@ -121,7 +121,7 @@ int orc_lattice(int32_t dim, double l0, double re, double* n0_out, double* lambd
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Background cell grid (Sec. 5.1, cell-linked list).  Side h = max(re_n, re_lap)(1+s). */
+/* Background cell grid (Sec. 4.1, cell-linked list).  Side h = max(re_n, re_lap)(1+s). */
 /* Cell coordinate per axis c = floor((x - box_min)/h); a particle whose coordinate is   */
 /* outside [0, ncell) on any axis is outside the grid and becomes a GHOST.  The cell's   */
 /* Morton key interleaves the bits of (cx, cy[, cz]) with x in the least-significant     */
@@ -182,7 +182,7 @@ int orc_cell_keys(const orc_params* p, int64_t n, const double* pos, const int8_
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Neighbour sets (Sec. 5.1).  j is a neighbour of i iff j != i, neither is a GHOST and  */
+/* Neighbour sets (Sec. 4.1).  j is a neighbour of i iff j != i, neither is a GHOST and  */
 /* ((dx*dx)+(dy*dy))+(dz*dz) < re*re with d = r_j - r_i, all in binary64 (w = 0 at      */
 /* r >= re, Eq. 4).  Rows are returned in ascending id order.                            */
 /* mode 0: brute force over all pairs.  mode 1: plain cell-linked list of side re.       */
@@ -448,7 +448,7 @@ int orc_gradient(int32_t dim, int64_t n, const double* pos, const int8_t* type, 
 
 /* ------------------------------------------------------------------------------------ */
 /* PPE assembly (Eq. 13 with the Laplacian of Eq. 7, the matrix layout of the CUDA PPE  */
-/* listing of Sec. 5.3).  Rows P = FLUID/WALL particles not on the free surface.        */
+/* listing of Sec. 4.3).  Rows P = FLUID/WALL particles not on the free surface.        */
 /*   c_ij = 2d/(n0_lap lambda rho) w(r_ij), j a non-DUMMY neighbour within re_lap;      */
 /*   A_ii = sum_j c_ij + alpha_c/dt^2;  A_ij = -c_ij when j is in P (p_j = 0 otherwise); */
 /*   b_i  = (1/dt^2) (n*_i - n0)/n0.                                                    */

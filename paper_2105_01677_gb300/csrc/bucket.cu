@@ -1,4 +1,4 @@
-// bucket.cu -- bucket build of the cell-linked list (Sec. 5.1).
+// bucket.cu -- bucket build of the cell-linked list (Sec. 4.1).
 //
 // Per step, at the current positions r^k:
 //   1. cell key of every particle: c = floor((x - box_min)/h) per axis in binary64, Morton

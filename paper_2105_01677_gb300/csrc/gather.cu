@@ -1,4 +1,4 @@
-// gather.cu -- neighbour gathers over the Morton bucket grid (Sec. 5.1: a particle's
+// gather.cu -- neighbour gathers over the Morton bucket grid (Sec. 4.1: a particle's
 // neighbours are looked up in its own cell and the adjacent cells).
 //
 // One thread block per occupied cell; each thread owns one particle of that cell.  The

@@ -12,7 +12,7 @@
 //            pressure term; lap by Eq. 7), r* = r + dt u*.
 //   build   (r*, all non-ghost rows):   n* (Eq. 5, re_n, every kind), free surface (Eq. 15),
 //            PPE row: b (Eq. 13), c_ij = 2d/(n0 lambda rho) w (non-dummy j within re_lap;
-//            PPE listing of Sec. 5.3), diagonal sum c_ij + alpha_c/dt^2, compacted neighbour
+//            PPE listing (Listing 2) of Sec. 4.3), diagonal sum c_ij + alpha_c/dt^2, compacted neighbour
 //            lists for the PPE and for the gradient (non-dummy j within re_n), and the
 //            equation-of-state pressure (Eq. 16).
 #include "mps_internal.cuh"

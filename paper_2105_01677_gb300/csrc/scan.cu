@@ -1,6 +1,6 @@
 // scan.cu -- device-wide exclusive prefix sum of uint32 values (reduce, scan the block
 // totals, scan again with the block offsets).  Used for the radix-sort digit offsets and
-// for the cell table (Sec. 5.1: each cell's first particle is the count of particles in
+// for the cell table (Sec. 4.1: each cell's first particle is the count of particles in
 // the cells before it in Morton order).
 #include "mps_internal.cuh"
 

@@ -4,10 +4,10 @@ This module only places particles on lattices and draws seeded jitter; it holds 
 MPS arithmetic (no kernel weight, no number density, no pressure).  Both the CPU oracle and
 the GB300 library consume the exact bytes produced here.
 
-Scenes follow the shapes of the paper's dam-break workloads (Sec. 4.2 "Dam break": a water
+Scenes follow the shapes of the paper's dam-break workloads (Sec. 5.2 "Dam break": a water
 column of height 2L on a floor of 4L, average particle distance l0) in 2D and 3D, with
 2 wall layers and 2 dummy layers on the tank walls (the wall / dummy particle kinds are the
-boundary flags of the PPE assembly listing in Sec. 5.3).
+boundary flags of the PPE assembly listing (Listing 2, Sec. 4.3)).
 
 Particle kinds (int8): FLUID=0, WALL=1, DUMMY=2, GHOST=3.
 
