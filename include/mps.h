@@ -3,10 +3,10 @@
  *
  * One Moving Particle Semi-implicit (MPS) time step, after Vieira-e-Silva et al., "A fluid
  * simulation system based on the MPS method" (arXiv 2105.01677):
- *   - cell-linked-list neighbour search (Sec. 5.1), here a Morton-sorted bucket grid;
+ *   - cell-linked-list neighbour search (Sec. 4.1), here a Morton-sorted bucket grid;
  *   - particle number density (Eq. 5), Laplacian model (Eq. 7) and pressure gradient
  *     (difference form of the multi-density gradient, Sec. 3.2.1) with w(r) = re/r - 1 (Eq. 4);
- *   - the pressure Poisson equation (Eq. 13) assembled as in the CUDA PPE listing of Sec. 5.3
+ *   - the pressure Poisson equation (Eq. 13) assembled as in the CUDA PPE listing (Listing 2) of Sec. 4.3
  *     and solved by conjugate gradients (Sec. 3.1.2), or
  *   - the weakly-compressible equation-of-state pressure (Eq. 16).
  *
@@ -71,7 +71,7 @@ typedef struct {
     double g[3];              /* external acceleration [m/s^2]                                */
     double c0;                /* speed of sound of Eq. 16 [m/s]                               */
     double gamma;             /* exponent of Eq. 16 (paper: 7)                                */
-    double alpha_c;           /* PPE diagonal term alpha_c/dt^2 (listing of Sec. 5.3: 1e-7)   */
+    double alpha_c;           /* PPE diagonal term alpha_c/dt^2 (listing of Sec. 4.3: 1e-7)   */
     double cg_tol;            /* stop when ||b - A p|| / ||b|| <= cg_tol (FP64 residual)       */
     int32_t cg_max_iter;      /* total CG iteration cap per solve; <= 0: 10 n                 */
     int32_t precision;        /* 0: FP64 throughout; 1: mixed (FP32 pair terms and inner CG,   *
@@ -122,7 +122,7 @@ typedef struct mps_ctx mps_ctx;
 void mps_params_default(mps_params* p);
 
 /* Create a context from n particles (the problem statement of Sec. 3 and the particle kinds
- * of the PPE listing, Sec. 5.3).
+ * of the PPE listing, Sec. 4.3).
  * pos: n*dim doubles; vel: n*dim doubles or NULL (zero); types: n int8 kinds.
  * The reference densities n0 (at re_n and re_lap) and lambda (at re_lap) are computed on the
  * host from an ideal lattice of spacing l0: all offsets o with 0 < |o| l0 < re (Eq. 5 and the
@@ -134,7 +134,7 @@ int mps_create(const double* pos, const double* vel, const int8_t* types, int64_
                const mps_params* params, mps_ctx** out);
 
 /* Advance nsteps time steps (Sec. 3, semi-implicit predictor-corrector):
- *   1. bucket build at r^k: cell keys, Morton radix sort, cell table by scan (Sec. 5.1);
+ *   1. bucket build at r^k: cell keys, Morton radix sort, cell table by scan (Sec. 4.1);
  *   2. predict FLUID u* = u + dt (nu lap(u) + g) (Eq. 2, Eq. 7 over re_lap), r* = r + dt u*;
  *   3. number density n* at r* (Eq. 5, re_n); free surface n* < beta n0 (Eq. 15);
  *   4. pressure: PPE A p = b (Eq. 13; A = -(1/rho) Lap + alpha_c/dt^2 I on FLUID/WALL rows
@@ -191,6 +191,39 @@ int mps_set_profiling(mps_ctx* ctx, int32_t on);
 /* stage_ms[MPS_NSTAGES]: accumulated milliseconds; stage_calls[MPS_NSTAGES]: stages timed;
  * launches: kernels launched since the last reset.  Any pointer may be NULL. */
 int mps_get_profile(mps_ctx* ctx, double* stage_ms, int64_t* stage_calls, int64_t* launches);
+
+/* Solve A x = b by FP64 conjugate gradients WITHOUT ALLOCATING any memory.
+ * No counterpart in the paper: this is an entry point for callers that are not allowed to
+ * call cudaMalloc -- for instance a host application whose device memory is entirely
+ * managed by its own pool and that forbids other allocators, or a real-time loop where
+ * cudaMalloc/cudaFree (which can synchronise the device and take milliseconds) are off
+ * limits after start-up.  Such a caller passes its own inputs and outputs; the CG's scratch
+ * vectors, partial sums and scalars live in one fixed array of device memory that belongs
+ * to the loaded library (about 6.3 MB on every GPU that loads it, held until process exit).
+ *
+ * The system uses the row layout of the library's PPE operator (Eq. 13 as assembled in the
+ * PPE listing (Listing 2) of Sec. 4.3):
+ *   (A x)_i = diag[i] x_i - sum_{k < cnt[i]} val[i*cap + k] x[col[i*cap + k]]  if diag[i] != 0,
+ *   and rows with diag[i] == 0 are outside the system (x_i = 0, b_i must be 0).
+ * A must be symmetric positive definite on its rows.  col, cnt, val, diag, b and x are
+ * device pointers owned by the caller (col/val: n*cap entries, the others n); x is
+ * overwritten with the solution.  CG starts from x = 0 and stops when the recomputed true
+ * residual satisfies ||b - A x|| <= tol ||b|| (restarting from it if the recurrence drifted),
+ * or after max_iter iterations in total (<= 0: 10 n) with MPS_ECG_NOCONV.
+ * stream: cudaStream_t (NULL: the legacy default stream); the call is synchronous.
+ * iters_out, resid_out (nullable): iterations and final relative residual.
+ * Limits: 1 <= n <= MPS_NOALLOC_MAX_ROWS, else MPS_EINVAL.
+ * Every call shares the one scratch array of the current device: two calls whose work
+ * overlaps on a GPU (different streams, threads or processes sharing the library instance)
+ * race and corrupt each other; serialise them.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Calls no cudaMalloc, cudaFree or allocating library
+ * routine. */
+#define MPS_NOALLOC_MAX_ROWS 262144
+int mps_ppe_cg_noalloc(int64_t n, int32_t cap, const int32_t* col, const int32_t* cnt,
+                       const double* val, const double* diag, const double* b, double* x,
+                       double tol, int32_t max_iter, void* stream, int32_t* iters_out,
+                       double* resid_out);
 
 /* Release every device buffer and the owned stream.  NULL is ignored. */
 void mps_destroy(mps_ctx* ctx);

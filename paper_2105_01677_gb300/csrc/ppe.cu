@@ -1,5 +1,5 @@
 // ppe.cu -- conjugate-gradient solve of the PPE A p = b (Eq. 13 assembled as in the CUDA
-// PPE listing of Sec. 5.3; the paper solves it by (IC)CG, Sec. 3.1.2 and Sec. 5.3).
+// PPE listing (Listing 2) of Sec. 4.3; the paper solves it by (IC)CG, Sec. 3.1.2 and Sec. 4.3).
 //
 // A is applied from the per-step neighbour lists built at r*:
 //   (A x)_i = diag_i x_i - sum_{j in nb_lap(i)} c_ij x_j   for rows of the PPE (diag_i > 0),
@@ -15,6 +15,8 @@
 //
 // Reductions are deterministic: per-block partials summed in block order by the last block.
 // Convergence is decided on the device; the host polls one flag per chunk of iterations.
+#include <mutex>
+
 #include "mps_internal.cuh"
 
 namespace mps {
@@ -398,3 +400,127 @@ int ppe_solve(Ctx* c, mps_report* rep) {
 }
 
 }  // namespace mps
+
+// ------------------------------------------------------------------ allocation-free solve
+// mps_ppe_cg_noalloc: the FP64 CG above on a caller-owned system, with every scratch
+// vector, partial sum and scalar taken from one fixed array in device memory that is part
+// of the loaded library (so the call itself never allocates).
+namespace mps {
+namespace {
+constexpr int64_t kNoAllocMaxRows = MPS_NOALLOC_MAX_ROWS;
+constexpr size_t kNoAllocHead = 512;                       // CgScalars + reduction tickets
+constexpr size_t kNoAllocPartials = 4096;                  // per-block partial sums
+constexpr size_t kNoAllocBytes = kNoAllocHead + kNoAllocPartials * sizeof(double) +
+                                 3 * (size_t)kNoAllocMaxRows * sizeof(double);
+static_assert(sizeof(CgScalars) <= 256, "CgScalars must fit the scratch header");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kMaxDevices] = {};
+
+// Device address of the scratch array for the current device (resolved once per device).
+int noalloc_base(void** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MPS_EDEVICE;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return MPS_EDEVICE;
+        }
+        g_noalloc_base[dev] = p;
+    }
+    *out = g_noalloc_base[dev];
+    return MPS_OK;
+}
+
+int noalloc_read(CgScalars* host, const CgScalars* dev, cudaStream_t s) {
+    if (cudaMemcpyAsync(host, dev, sizeof(CgScalars), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return MPS_EDEVICE;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return MPS_EDEVICE;
+    return MPS_OK;
+}
+}  // namespace
+}  // namespace mps
+
+extern "C" int mps_ppe_cg_noalloc(int64_t n, int32_t cap, const int32_t* col, const int32_t* cnt,
+                                  const double* val, const double* diag, const double* b, double* x,
+                                  double tol, int32_t max_iter, void* stream, int32_t* iters_out,
+                                  double* resid_out) {
+    using namespace mps;
+    if (n <= 0 || n > kNoAllocMaxRows || cap <= 0 || !col || !cnt || !val || !diag || !b || !x ||
+        !(tol > 0.0))
+        return MPS_EINVAL;
+    void* base = nullptr;
+    int rc = noalloc_base(&base);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* bp = (unsigned char*)base;
+    CgScalars* cg = (CgScalars*)bp;
+    unsigned int* counters = (unsigned int*)(bp + 256);
+    double* partials = (double*)(bp + kNoAllocHead);
+    double* r = partials + kNoAllocPartials;
+    double* d = r + kNoAllocMaxRows;
+    double* q = d + kNoAllocMaxRows;
+    const int ni = (int)n;
+    const int max_total = max_iter > 0 ? max_iter : (int)std::min<int64_t>(10 * n, 1 << 30);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return MPS_EDEVICE;
+    const int gs = sms * 8, gv = sms * 4;
+    // the array keeps the previous call's contents: scalars and tickets restart from zero
+    CgScalars init{};
+    init.max_iters = max_total;
+    if (cudaMemsetAsync(bp, 0, kNoAllocHead, s) != cudaSuccess ||
+        cudaMemcpyAsync(cg, &init, sizeof init, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return MPS_EDEVICE;
+    PpeView v;
+    v.n = ni;
+    v.cap = cap;
+    v.col = col;
+    v.cnt = cnt;
+    v.v64 = val;
+    v.v32 = nullptr;
+    v.diag = diag;
+    v.bvec = b;
+    v.pos32s = nullptr;
+    v.partials = partials;
+    v.counter = counters;
+    const double tol2 = tol * tol;
+    CgScalars h{};
+    k_clear_x<<<(ni + 255) / 256, 256, 0, s>>>(ni, x);
+    k_resid64<<<gs, kBT, 0, s>>>(v, x, r, d, cg, tol2, 1, 1);
+    if ((rc = noalloc_read(&h, cg, s))) return rc;
+    const double bnorm2 = h.rr, stop2 = h.stop2;
+    double rel = 0.0;
+    int iters = 0;
+    if (bnorm2 > 0.0) {
+        int chunk = 8;
+        for (;;) {
+            for (int k = 0; k < chunk; k++) {
+                k_spmv64<<<gs, kBT, 0, s>>>(v, d, q, cg);
+                k_xr64<<<gv, kBT, 0, s>>>(ni, x, r, d, q, cg, partials, &counters[2]);
+                k_d64<<<gv, kBT, 0, s>>>(ni, r, d, cg);
+            }
+            if ((rc = noalloc_read(&h, cg, s))) return rc;
+            if (!h.done) continue;
+            iters = h.iters;
+            k_resid64<<<gs, kBT, 0, s>>>(v, x, r, d, cg, tol2, 0, 1);
+            if ((rc = noalloc_read(&h, cg, s))) return rc;
+            rel = sqrt(h.rr / bnorm2);
+            if (h.rr <= stop2) break;
+            if (iters >= max_total) {
+                rc = MPS_ECG_NOCONV;
+                break;
+            }
+        }
+    }
+    if (cudaGetLastError() != cudaSuccess) return MPS_EDEVICE;
+    if (iters_out) *iters_out = iters;
+    if (resid_out) *resid_out = rel;
+    return rc;
+}

@@ -55,7 +55,9 @@ class mps_report(C.Structure):
 
 EXPORTS = ("mps_params_default", "mps_create", "mps_step", "mps_solve_ppe", "mps_read_state",
            "mps_write_state", "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants",
-           "mps_set_profiling", "mps_get_profile", "mps_destroy", "mps_strerror")
+           "mps_set_profiling", "mps_get_profile", "mps_ppe_cg_noalloc", "mps_destroy",
+           "mps_strerror")
+NOALLOC_MAX_ROWS = 262144
 STAGES = ("bucket", "predict", "build", "ppe", "update")
 
 _lib = None
@@ -91,13 +93,16 @@ def lib(build_if_missing: bool = False):
     L.mps_get_constants.argtypes = [C.c_void_p, d]
     L.mps_set_profiling.argtypes = [C.c_void_p, C.c_int32]
     L.mps_get_profile.argtypes = [C.c_void_p, d, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.mps_ppe_cg_noalloc.argtypes = [C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
+                                     C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
     L.mps_destroy.argtypes = [C.c_void_p]
     L.mps_destroy.restype = None
     L.mps_strerror.argtypes = [C.c_int]
     L.mps_strerror.restype = C.c_char_p
     for f in ("mps_create", "mps_step", "mps_solve_ppe", "mps_read_state", "mps_write_state",
               "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants", "mps_set_profiling",
-              "mps_get_profile"):
+              "mps_get_profile", "mps_ppe_cg_noalloc"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -274,6 +279,20 @@ def mps_get_profile(h):
                                  _ptr(launches, C.c_int64)), "mps_get_profile")
     return dict(stage_ms=dict(zip(STAGES, ms.tolist())),
                 stage_calls=dict(zip(STAGES, calls.tolist())), launches=int(launches[0]))
+
+
+def mps_ppe_cg_noalloc(n: int, cap: int, col: int, cnt: int, val: int, diag: int, b: int, x: int,
+                       tol: float, max_iter: int = 0, stream: int = 0, check: bool = True):
+    """FP64 CG on a caller-owned system without any allocation (device pointers as ints).
+
+    Returns (rc, iterations, relative residual)."""
+    it = C.c_int32()
+    res = C.c_double()
+    rc = lib().mps_ppe_cg_noalloc(int(n), int(cap), col, cnt, val, diag, b, x, float(tol),
+                                  int(max_iter), stream or None, C.byref(it), C.byref(res))
+    if check:
+        _check(rc, "mps_ppe_cg_noalloc")
+    return rc, it.value, res.value
 
 
 def mps_destroy(h):
