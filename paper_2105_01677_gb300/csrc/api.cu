@@ -73,6 +73,15 @@ Radius make_radius(double re, double X) {
     r.lo = std::nextafter((float)(r.re2 - eps), 0.0f);
     r.hi = std::nextafter((float)(r.re2 + eps), INFINITY);
     if (!(r.lo > 0.0f)) r.lo = 0.0f;
+    // float-float tier: coordinates split into hi + lo floats carry ~2^-48 X of error, the
+    // float-float squares and sums ~2^-46 relative; the binary64 evaluation it must agree
+    // with rounds at 2^-53.  Pairs closer to the cutoff than this go to binary64.
+    r.re2_h = (float)r.re2;
+    r.re2_l = (float)(r.re2 - (double)r.re2_h);
+    r.re_l = (float)(re - (double)r.re_f);
+    const double tol = 8.0 * (2.0 * re * std::sqrt(3.0) * std::ldexp(X, -46)) +
+                       8.0 * std::ldexp(re * re, -45);
+    r.ff_tol = (float)tol;
     return r;
 }
 
@@ -210,18 +219,18 @@ int allocate(Ctx* c) {
     int rc = 0;
 #define A(ptr, count) \
     if ((rc = alloc_dev(c, &c->ptr, (count)))) return rc;
+    const size_t sv = sell_size(c->n, c->cap_v), sl = sell_size(c->n, c->cap),
+                 sn = sell_size(c->n, c->cap_n);
     A(pos, n) A(vel, n) A(pos_alt, n) A(vel_alt, n) A(type, n) A(type_alt, n) A(id, n) A(id_alt, n)
-    A(p, n) A(p_alt, n) A(pos32, n) A(pos_star, n) A(vel_star, n) A(pos32_star, n) A(nstar, n)
-    A(flag, n) A(bvec, n) A(diag, n) A(phat, n)
-    A(vl_col, n * c->cap_v) A(vl_cnt, n) A(vel32, n)
-    A(nb_lap_col, n * c->cap) A(nb_lap_cnt, n) A(nb_n_col, n * c->cap_n) A(nb_n_cnt, n)
+    A(p, n) A(p_alt, n) A(pos32, n) A(pos32lo, n) A(pos_star, n) A(vel_star, n) A(pos32_star, n)
+    A(pos32lo_star, n) A(nstar, n) A(flag, n) A(bvec, n) A(diag, n) A(diag32, n) A(phat, n)
+    A(vl_col, sv) A(vl_cnt, n) A(vel32, n)
+    A(nb_n_col, sn) A(nb_n_cnt, n) A(nb_lap_cnt, n)
     if (c->prm.pressure_mode == 0) {
-        A(nb_lap_v64, n * c->cap)
-        if (c->prm.precision == 1) { A(nb_lap_v32, n * c->cap) }
+        A(nb_lap_col, sl) A(nb_lap_v64, sl)
+        if (c->prm.precision == 1) { A(nb_lap_v32, sl) }
         A(cg_r, n) A(cg_d, n) A(cg_q, n)
         if (c->prm.precision == 1) { A(cg_r32, n) A(cg_d32, n) A(cg_q32, n) A(cg_x32, n) }
-    } else {
-        A(nb_lap_v64, n * c->cap)
     }
     A(key, n) A(key_alt, n) A(perm, n) A(perm_alt, n)
     const int64_t tiles = ((int64_t)n + 2047) / 2048;

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kBT)
     k_permute(const int32_t* perm, int n, const double4* pos, const double4* vel,
               const int8_t* type, const int32_t* id, const double* p, double4* pos_o,
               double4* vel_o, int8_t* type_o, int32_t* id_o, double* p_o, float4* pos32,
-              float4* vel32, GridDesc g) {
+              float4* pos32lo, float4* vel32, GridDesc g) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int j = perm[s];
@@ -151,8 +151,14 @@ __global__ void __launch_bounds__(kBT)
     type_o[s] = t;
     id_o[s] = id[j];
     p_o[s] = p[j];
-    pos32[s] = make_float4((float)(x.x - g.bmin[0]), (float)(x.y - g.bmin[1]),
-                           (float)(x.z - g.bmin[2]), __int_as_float((int)t));
+    float4 h, l;
+    split_rel(x.x, g.bmin[0], &h.x, &l.x);
+    split_rel(x.y, g.bmin[1], &h.y, &l.y);
+    split_rel(x.z, g.bmin[2], &h.z, &l.z);
+    h.w = __int_as_float((int)t);
+    l.w = 0.f;
+    pos32[s] = h;
+    pos32lo[s] = l;
 }
 }  // namespace
 
@@ -196,8 +202,8 @@ int bucket_build(Ctx* c, bool mutate) {
     k_occupied<<<nb1, kBT, 0, s>>>(c->key, n, c->grid.ghost_key, c->occ, c->st);
     // permute the state into the new order
     k_permute<<<nb1, kBT, 0, s>>>(c->perm, n, c->pos, c->vel, c->type, c->id, c->p, c->pos_alt,
-                                  c->vel_alt, c->type_alt, c->id_alt, c->p_alt, c->pos32, c->vel32,
-                                  c->grid);
+                                  c->vel_alt, c->type_alt, c->id_alt, c->p_alt, c->pos32,
+                                  c->pos32lo, c->vel32, c->grid);
     std::swap(c->pos, c->pos_alt);
     std::swap(c->vel, c->vel_alt);
     std::swap(c->type, c->type_alt);

@@ -104,7 +104,8 @@ __device__ __forceinline__ int kind_of(const float4& q) { return __float_as_int(
 
 // ------------------------------------------------------------------------------ Verlet
 // Candidate list of every non-ghost particle: all j != i with FP32 squared distance below
-// the candidate radius h^2 plus its rounding margin (a superset of the exact set within h).
+// the candidate radius h^2 plus its rounding margin (a superset of the exact set within h),
+// written as SELL-32 rows.
 struct VerletOp {
     const float4* pos32;
     const int8_t* type;
@@ -117,18 +118,16 @@ struct VerletOp {
     struct Center {
         float4 p32;
         int cnt;
-        size_t base;
     };
     __device__ bool active(int i) const { return type[i] != kGhost; }
     __device__ float4 stage(int) const { return make_float4(0.f, 0.f, 0.f, 0.f); }
     __device__ void begin(int i, bool act, Center& c) const {
         c.cnt = 0;
-        c.base = (size_t)i * cap_v;
         if (act) c.p32 = pos32[i];
     }
     __device__ void visit(Center& c, int i, int j, const float4& q, const float4&) const {
         if (j == i || dist2_f(c.p32, q) >= hv2) return;
-        if (c.cnt < cap_v) vcol[c.base + c.cnt] = j;
+        if (c.cnt < cap_v) vcol[sell(i, c.cnt, cap_v)] = j;
         c.cnt++;
     }
     __device__ void end_chunk(Center&) const {}
@@ -175,12 +174,14 @@ struct NbrOp {
 };
 
 __global__ void k_copy_star(int n, const double4* pos, const double4* vel, const float4* pos32,
-                            double4* ps, double4* vs, float4* p32s) {
+                            const float4* pos32lo, double4* ps, double4* vs, float4* p32s,
+                            float4* p32los) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     ps[i] = pos[i];
     vs[i] = vel[i];
     p32s[i] = pos32[i];
+    p32los[i] = pos32lo[i];
 }
 
 template <class Op, bool STAGE_X>
@@ -199,8 +200,9 @@ void launch_gather(Ctx* c, const Op& op) {
 
 void launch_copy_state_star(Ctx* c) {
     int n = (int)c->n;
-    k_copy_star<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->pos, c->vel, c->pos32, c->pos_star,
-                                                         c->vel_star, c->pos32_star);
+    k_copy_star<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->pos, c->vel, c->pos32, c->pos32lo,
+                                                         c->pos_star, c->vel_star, c->pos32_star,
+                                                         c->pos32lo_star);
     c->launches += 1;
 }
 

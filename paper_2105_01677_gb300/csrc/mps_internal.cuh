@@ -5,11 +5,15 @@
 //   pos32           float4 (x-xmin, y-ymin, z-zmin, kind bits)   FP32 copy for filtering
 //   type            int8, id int32 (caller's particle id of slot s)
 //   pos_star/vel_star double4, pos32_star float4   predicted r*, u* of the step
-//   vl              ELL rows of `cap_v` int32 slots: candidates within h at r^k (superset)
+//   pos32lo         float4 low parts: x - xmin = pos32.x + pos32lo.x to ~48 bits (float-float)
+//   vl              SELL-32 rows of `cap_v` int32 slots: candidates within h at r^k (superset)
 //   vel32           float4 velocities (mixed-precision viscosity terms)
-//   nb_lap          ELL rows of `cap` int32 slots: non-dummy neighbours within re_lap at r*,
-//                   with FP64 (val64) and FP32 (val32) coefficients c_ij of the PPE
-//   nb_n            ELL rows of `cap_n` int32 slots: non-dummy neighbours within re_n at r*
+//   nb_lap          SELL-32 rows of `cap` int32 slots: non-dummy neighbours within re_lap at
+//                   r*, with FP64 (val64) and FP32 (val32) coefficients c_ij of the PPE
+//   nb_n            SELL-32 rows of `cap_n` int32 slots: non-dummy neighbours within re_n at r*
+//   SELL-32: the rows of 32 consecutive slots form a slice; entry k of row i sits at
+//   ((i / 32) cap + k) 32 + i % 32, so a warp (one row per lane) reads entry k of its 32
+//   rows in one coalesced 128-byte access.
 //   cell_start      int32[2^(dim*bits) + 1], indexed by Morton code: exclusive scan of
 //                   per-cell counts, so cell m holds slots [cell_start[m], cell_start[m+1])
 #pragma once
@@ -69,9 +73,20 @@ struct GridDesc {
 // r2_32 < lo  => certainly inside; r2_32 >= hi => certainly outside; else decide in FP64.
 struct Radius {
     double re, re2;
-    float lo, hi;
+    float lo, hi;       // FP32 band
     float re_f;
+    float re2_h, re2_l; // re^2 as float-float
+    float ff_tol;       // float-float band: |r2_ff - re^2| < ff_tol is decided in binary64
+    float re_l;         // re = re_f + re_l (float-float)
 };
+
+// slot of entry k of row i in a SELL-32 array with `cap` entries per row
+__host__ __device__ __forceinline__ size_t sell(int i, int k, int cap) {
+    return ((size_t)(i >> 5) * (size_t)cap + (size_t)k) * 32 + (size_t)(i & 31);
+}
+__host__ __device__ __forceinline__ size_t sell_size(int64_t n, int cap) {
+    return (size_t)((n + 31) / 32) * 32 * (size_t)cap;
+}
 
 struct Ctx;
 
@@ -106,6 +121,13 @@ void launch_unpermute(Ctx* c, double* d_pos, double* d_vel, double* d_p, double*
                       uint8_t* d_flags, int8_t* d_types);
 void launch_ingest(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types,
                    bool keep_vel, bool keep_types);
+// FP32 hi/lo split of a coordinate relative to the grid origin (float-float)
+__device__ __forceinline__ void split_rel(double x, double xmin, float* hi, float* lo) {
+    const double r = x - xmin;
+    const float h = (float)r;
+    *hi = h;
+    *lo = (float)(r - (double)h);
+}
 void launch_unpermute_u32(Ctx* c, const uint32_t* in, uint32_t* out);
 
 // ---------------------------------------------------------------- context
@@ -139,15 +161,16 @@ struct Ctx {
     int8_t *type, *type_alt;
     int32_t *id, *id_alt;
     double *p, *p_alt;
-    float4* pos32;
+    float4 *pos32, *pos32lo;
     // step buffers
     double4 *pos_star, *vel_star;
-    float4* pos32_star;
+    float4 *pos32_star, *pos32lo_star;
     float4* vel32;
     double* nstar;
     uint8_t* flag;
     double* bvec;
     double* diag;        // PPE diagonal; 0 on rows outside the PPE
+    float* diag32;
     int32_t *vl_col, *vl_cnt;     // candidate (Verlet) lists at r^k, radius h
     int32_t *nb_lap_col, *nb_lap_cnt, *nb_n_col, *nb_n_cnt;
     double* nb_lap_v64;

@@ -1,7 +1,8 @@
 // ppe.cu -- conjugate-gradient solve of the PPE A p = b (Eq. 13 assembled as in the CUDA
 // PPE listing (Listing 2) of Sec. 4.3; the paper solves it by (IC)CG, Sec. 3.1.2 and Sec. 4.3).
 //
-// A is applied from the per-step neighbour lists built at r*:
+// A is applied from the per-step neighbour lists built at r* (SELL-32 rows, one thread per
+// row; the allocation-free entry point below takes caller rows in plain row-major layout):
 //   (A x)_i = diag_i x_i - sum_{j in nb_lap(i)} c_ij x_j   for rows of the PPE (diag_i > 0),
 //   (A x)_i = 0 elsewhere,
 // where every CG vector vanishes outside the PPE rows, so neighbours j outside them drop out
@@ -25,7 +26,7 @@ namespace {
 constexpr int kBT = 256;
 constexpr int kWarps = kBT / 32;
 
-// Plain-data view of the PPE operator handed to the kernels.
+// Plain-data view of a row-major PPE operator (the allocation-free entry point's layout).
 struct PpeView {
     int n, cap;
     const int32_t* col;
@@ -46,28 +47,6 @@ __device__ __forceinline__ double row_dot64(const PpeView& c, int i, const doubl
     double acc = 0.0;
     for (int k = lane; k < cnt; k += 32) acc = fma(c.v64[base + k], x[c.col[base + k]], acc);
     return warp_sum(acc);
-}
-
-template <bool MATRIX_FREE>
-__device__ __forceinline__ float row_dot32(const PpeView& c, int i, const float* x, int lane,
-                                           float4 pi, float coef, float re_f) {
-    const int cnt = c.cnt[i];
-    const size_t base = (size_t)i * c.cap;
-    float acc = 0.f;
-    for (int k = lane; k < cnt; k += 32) {
-        const int j = c.col[base + k];
-        float a;
-        if (MATRIX_FREE) {
-            const float4 q = c.pos32s[j];
-            const float dx = q.x - pi.x, dy = q.y - pi.y, dz = q.z - pi.z;
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            a = coef * fmaf(re_f, rsqrtf(r2), -1.f);
-        } else {
-            a = c.v32[base + k];
-        }
-        acc = fmaf(a, x[j], acc);
-    }
-    return warp_sum_f(acc);
 }
 
 // ------------------------------------------------------------------ FP64 kernels
@@ -187,34 +166,6 @@ __global__ void __launch_bounds__(kBT) k_inner_init(int n, const double* r64, fl
     }
 }
 
-template <bool MATRIX_FREE>
-__global__ void __launch_bounds__(kBT) k_spmv32(PpeView c, const float* d, float* q, CgScalars* cg,
-                                                float coef, float re_f) {
-    if (*(volatile int*)&cg->done) return;
-    __shared__ double sm[kWarps];
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * kBT + threadIdx.x) >> 5, nw = (gridDim.x * kBT) >> 5;
-    double part = 0.0;
-    for (int i = gw; i < c.n; i += nw) {
-        const double dg = c.diag[i];
-        float qi = 0.f;
-        if (dg != 0.0) {
-            const float4 pi = MATRIX_FREE ? c.pos32s[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-            qi = (float)dg * d[i] - row_dot32<MATRIX_FREE>(c, i, d, lane, pi, coef, re_f);
-        }
-        if (lane == 0) {
-            q[i] = qi;
-            part += (double)d[i] * (double)qi;
-        }
-    }
-    double tot;
-    part = block_sum<kBT>(part, sm);
-    if (grid_sum<kBT>(part, c.partials, &c.counter[1], &tot, sm) && threadIdx.x == 0) {
-        cg->dq = tot;
-        cg->alpha = (tot > 0.0) ? cg->rho / tot : 0.0;
-    }
-}
-
 __global__ void __launch_bounds__(kBT) k_xr32(int n, float* x, float* r, const float* d, const float* q,
                                               CgScalars* cg, double* partials, unsigned int* counter) {
     if (*(volatile int*)&cg->done) return;
@@ -243,6 +194,122 @@ __global__ void __launch_bounds__(kBT) k_d32(int n, const float* r, float* d, co
     for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) d[i] = fmaf(beta, d[i], r[i]);
 }
 
+// ------------------------------------------------------------------ thread-per-row (SELL-32)
+// The step's PPE rows are SELL-32: each thread owns a row, a warp reads entry k of 32 rows
+// with one coalesced access, and every FP64 operation runs with all lanes busy.
+struct SellView {
+    int n, cap;
+    const int32_t* col;
+    const int32_t* cnt;
+    const double* v64;
+    const float* v32;
+    const double* diag;
+    const float* diag32;
+    const double* bvec;
+    const float4* pos32s;
+    double* partials;
+    unsigned int* counter;
+};
+
+__device__ __forceinline__ double sell_dot64(const SellView& c, int i, const double* x) {
+    const int cnt = c.cnt[i];
+    double acc = 0.0;
+    for (int k = 0; k < cnt; k++) {
+        const size_t q = sell(i, k, c.cap);
+        acc = fma(c.v64[q], x[c.col[q]], acc);
+    }
+    return acc;
+}
+
+// r = b - A x, d = r (if d); rr = r.r
+__global__ void __launch_bounds__(kBT) k_resid64_t(SellView c, const double* x, double* r,
+                                                   double* d, CgScalars* cg, double tol2,
+                                                   int set_stop, int set_cg) {
+    __shared__ double sm[kWarps];
+    double part = 0.0;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT) {
+        const double dg = c.diag[i];
+        double ri = 0.0;
+        if (dg != 0.0) ri = c.bvec[i] - (dg * x[i] - sell_dot64(c, i, x));
+        r[i] = ri;
+        if (d) d[i] = ri;
+        part = fma(ri, ri, part);
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, c.partials, &c.counter[0], &tot, sm) && threadIdx.x == 0) {
+        cg->rr = tot;
+        if (set_stop) cg->stop2 = tol2 * tot;
+        if (set_cg) {
+            cg->rho = tot;
+            cg->rho0 = tot;
+            cg->done = (tot <= cg->stop2) ? 1 : 0;
+        }
+    }
+}
+
+// q = A d, alpha = rho / (d.q)
+__global__ void __launch_bounds__(kBT) k_spmv64_t(SellView c, const double* d, double* q,
+                                                  CgScalars* cg) {
+    if (*(volatile int*)&cg->done) return;
+    __shared__ double sm[kWarps];
+    double part = 0.0;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT) {
+        const double dg = c.diag[i];
+        double qi = 0.0;
+        if (dg != 0.0) qi = dg * d[i] - sell_dot64(c, i, d);
+        q[i] = qi;
+        part = fma(d[i], qi, part);
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, c.partials, &c.counter[1], &tot, sm) && threadIdx.x == 0) {
+        cg->dq = tot;
+        cg->alpha = (tot > 0.0) ? cg->rho / tot : 0.0;
+    }
+}
+
+// FP32 operator: stored FP32 coefficients, or recomputed from the FP32 positions at r*
+template <bool MATRIX_FREE>
+__global__ void __launch_bounds__(kBT) k_spmv32_t(SellView c, const float* d, float* q,
+                                                  CgScalars* cg, float coef, float re_f) {
+    if (*(volatile int*)&cg->done) return;
+    __shared__ double sm[kWarps];
+    double part = 0.0;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT) {
+        const float dg = c.diag32[i];
+        float qi = 0.f;
+        if (dg != 0.f) {
+            const int cnt = c.cnt[i];
+            float acc = 0.f;
+            if (MATRIX_FREE) {
+                const float4 pi = c.pos32s[i];
+                for (int k = 0; k < cnt; k++) {
+                    const int j = c.col[sell(i, k, c.cap)];
+                    const float4 pj = c.pos32s[j];
+                    const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    acc = fmaf(coef * fmaf(re_f, rsqrtf(r2), -1.f), d[j], acc);
+                }
+            } else {
+                for (int k = 0; k < cnt; k++) {
+                    const size_t s = sell(i, k, c.cap);
+                    acc = fmaf(c.v32[s], d[c.col[s]], acc);
+                }
+            }
+            qi = dg * d[i] - acc;
+        }
+        q[i] = qi;
+        part = fma((double)d[i], (double)qi, part);
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, c.partials, &c.counter[1], &tot, sm) && threadIdx.x == 0) {
+        cg->dq = tot;
+        cg->alpha = (tot > 0.0) ? cg->rho / tot : 0.0;
+    }
+}
+
 // x64 += |r64| x32   (|r64| = sqrt(rr) of the residual that started the inner solve)
 __global__ void __launch_bounds__(kBT) k_outer_update(int n, double* x, const float* e, double scale_rr) {
     const double s = sqrt(scale_rr);
@@ -255,8 +322,8 @@ __global__ void k_clear_x(int n, double* x) {
 }
 }  // namespace
 
-static PpeView view(Ctx* c) {
-    PpeView v;
+static SellView sell_view(Ctx* c) {
+    SellView v;
     v.n = (int)c->n;
     v.cap = c->cap;
     v.col = c->nb_lap_col;
@@ -264,6 +331,7 @@ static PpeView view(Ctx* c) {
     v.v64 = c->nb_lap_v64;
     v.v32 = c->nb_lap_v32;
     v.diag = c->diag;
+    v.diag32 = c->diag32;
     v.bvec = c->bvec;
     v.pos32s = c->pos32_star;
     v.partials = c->partials;
@@ -292,7 +360,7 @@ static void cg64_chunk(Ctx* c, int chunk) {
     double* x = c->p;
     c->launches += 3 * chunk;
     for (int k = 0; k < chunk; k++) {
-        k_spmv64<<<gs, kBT, 0, c->stream>>>(view(c), c->cg_d, c->cg_q, c->cg);
+        k_spmv64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->cg_d, c->cg_q, c->cg);
         k_xr64<<<gv, kBT, 0, c->stream>>>(n, x, c->cg_r, c->cg_d, c->cg_q, c->cg, c->partials,
                                           &c->st->counter[2]);
         k_d64<<<gv, kBT, 0, c->stream>>>(n, c->cg_r, c->cg_d, c->cg);
@@ -306,9 +374,9 @@ static void cg32_chunk(Ctx* c, int chunk) {
     c->launches += 3 * chunk;
     for (int k = 0; k < chunk; k++) {
         if (c->prm.ppe_operator == 1)
-            k_spmv32<true><<<gs, kBT, 0, c->stream>>>(view(c), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+            k_spmv32_t<true><<<gs, kBT, 0, c->stream>>>(sell_view(c), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
         else
-            k_spmv32<false><<<gs, kBT, 0, c->stream>>>(view(c), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+            k_spmv32_t<false><<<gs, kBT, 0, c->stream>>>(sell_view(c), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
         k_xr32<<<gv, kBT, 0, c->stream>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_q32, c->cg,
                                           c->partials, &c->st->counter[2]);
         k_d32<<<gv, kBT, 0, c->stream>>>(n, c->cg_r32, c->cg_d32, c->cg);
@@ -325,7 +393,7 @@ int ppe_solve(Ctx* c, mps_report* rep) {
     c->launches += 2;
     if ((rc = set_cg_limits(c, max_total))) return rc;
     // r = b, d = b, rho = |b|^2, stop2 = tol^2 |b|^2
-    k_resid64<<<gs, kBT, 0, c->stream>>>(view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2, 1, 1);
+    k_resid64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2, 1, 1);
     if ((rc = read_scalars(c))) return rc;
     const double bnorm2 = c->cg_host->rr;
     const double stop2 = c->cg_host->stop2;
@@ -346,7 +414,7 @@ int ppe_solve(Ctx* c, mps_report* rep) {
             total_iters = c->cg_host->iters;
             // true residual; restart from it if the recurrence drifted
             c->launches += 1;
-            k_resid64<<<gs, kBT, 0, c->stream>>>(view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2, 0, 1);
+            k_resid64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2, 0, 1);
             if ((rc = read_scalars(c))) return rc;
             rel = sqrt(c->cg_host->rr / bnorm2);
             if (c->cg_host->rr <= stop2) break;
@@ -384,7 +452,7 @@ int ppe_solve(Ctx* c, mps_report* rep) {
             }
             total_iters += c->cg_host->iters;
             k_outer_update<<<gv, kBT, 0, c->stream>>>(n, c->p, c->cg_x32, rr);
-            k_resid64<<<gs, kBT, 0, c->stream>>>(view(c), c->p, c->cg_r, nullptr, c->cg, tol2, 0, 0);
+            k_resid64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_r, nullptr, c->cg, tol2, 0, 0);
             if ((rc = read_scalars(c))) return rc;
             rr = c->cg_host->rr;
             outer++;

@@ -1,26 +1,36 @@
-// rows.cu -- per-particle pair sums over the step's candidate (Verlet) lists, one warp per
-// particle: the lanes split the particle's candidates, so the pair arithmetic runs with
-// (nearly) full warps whatever the hit pattern.
+// rows.cu -- per-particle pair sums over the step's candidate (Verlet) lists, one thread per
+// particle.  Lists are SELL-32, so a warp reads entry k of its 32 rows in one access, and
+// every per-particle FP64 operation (the state update, the PPE row) runs with all lanes of
+// the warp busy: on GB300 an FP64 warp instruction costs the FP64 pipe ~64 cycles whatever
+// the number of active lanes.
 //
 // The candidate list of particle i holds every j whose FP32 distance at r^k is below
 // h = max(re_n, re_lap)(1 + s) (plus the FP32 rounding margin).  A pair closer than re_lap
 // at r^k, or closer than max(re) at r* = r^k + dt u*, is in it as long as no particle moves
-// more than s max(re)/2 in the step (checked; MPS_ESKIN otherwise).  Every use re-decides
-// the exact predicate r^2 < re^2 in binary64 where the FP32 distance is inside the band.
+// more than s max(re)/2 in the step (checked; MPS_ESKIN otherwise).
 //
-//   predict (r^k, re_lap, FLUID rows):  u* = u + dt (nu lap(u) + g)  (Eq. 2 without the
-//            pressure term; lap by Eq. 7), r* = r + dt u*.
-//   build   (r*, all non-ghost rows):   n* (Eq. 5, re_n, every kind), free surface (Eq. 15),
-//            PPE row: b (Eq. 13), c_ij = 2d/(n0 lambda rho) w (non-dummy j within re_lap;
-//            PPE listing (Listing 2) of Sec. 4.3), diagonal sum c_ij + alpha_c/dt^2, compacted neighbour
-//            lists for the PPE and for the gradient (non-dummy j within re_n), and the
+// Exact predicate r^2 < re^2 of the binary64 definition, in three tiers: the FP32 squared
+// distance decides outside a band of its rounding error; inside it, a float-float distance
+// decides outside a band ~1e-11 re^2 wide; the few pairs left (exact lattice geometry of
+// unjittered walls) are decided in binary64 with ((dx*dx)+(dy*dy))+(dz*dz) < re*re.
+//
+//   predict (r^k, re_lap, FLUID):  u* = u + dt (nu lap(u) + g)  (Eq. 2 without the pressure
+//            term; lap by Eq. 7), r* = r + dt u*.
+//   build   (r*, every non-ghost particle):  n* (Eq. 5, re_n, every kind), free surface
+//            (Eq. 15), PPE row: b (Eq. 13), c_ij = 2d/(n0 lambda rho) w (non-dummy j within
+//            re_lap; PPE listing (Listing 2) of Sec. 4.3), diagonal sum c_ij + alpha_c/dt^2,
+//            neighbour lists for the PPE and the gradient (non-dummy j within re_n), and the
 //            equation-of-state pressure (Eq. 16).
+// Precision: FP64 mode evaluates pair terms in binary64; mixed mode evaluates the viscosity
+// terms in FP32 and the number density and PPE coefficients in float-float (relative error
+// ~1e-13), accumulated in float-float and stored in binary64.
+#include "ff.cuh"
 #include "mps_internal.cuh"
 
 namespace mps {
 
 namespace {
-constexpr int kBT = 256;
+constexpr int kBT = 128;
 
 __device__ __forceinline__ float dist2_f(const float4& a, const float4& b) {
     float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
@@ -28,11 +38,33 @@ __device__ __forceinline__ float dist2_f(const float4& a, const float4& b) {
 }
 __device__ __forceinline__ int kind_of(const float4& q) { return __float_as_int(q.w) & 0xff; }
 
-struct PredictRows {
+// float-float squared distance from hi/lo coordinate pairs
+__device__ __forceinline__ ff pair_r2(const float4& ih, const float4& il, const float4& jh,
+                                     const float4& jl) {
+    return ff_dist2(ff_diff(ih.x, il.x, jh.x, jl.x), ff_diff(ih.y, il.y, jh.y, jl.y),
+                    ff_diff(ih.z, il.z, jh.z, jl.z));
+}
+
+// tier 2 and 3 of the predicate for a pair inside the FP32 band
+__device__ __forceinline__ bool decide_band(const ff& r2, const Radius& r, const double4* pos,
+                                            const double4& pi, int j) {
+    const float d = (r2.h - r.re2_h) + (r2.l - r.re2_l);
+    if (d <= -r.ff_tol) return true;
+    if (d >= r.ff_tol) return false;
+    return exact_dist2(pi, pos[j]) < r.re2;
+}
+
+// 1 inside, 0 outside, from the FP32 distance; 2: needs the finer tiers
+__device__ __forceinline__ int tier1(float r2, const Radius& r) {
+    return r2 < r.lo ? 1 : (r2 >= r.hi ? 0 : 2);
+}
+
+struct PredictArgs {
     int n, cap_v;
     const int32_t* vcol;
     const int32_t* vcnt;
     const float4* pos32;
+    const float4* pos32lo;
     const double4* pos;
     const double4* vel;
     const float4* vel32;
@@ -40,37 +72,41 @@ struct PredictRows {
     double4* pos_star;
     double4* vel_star;
     float4* pos32_star;
+    float4* pos32lo_star;
     DevStatus* st;
     Radius r;
-    float tiny2;
     double coef_lap, nu, dt, g0, g1, g2, bmin0, bmin1, bmin2;
 };
 
 template <bool MIXED>
-__global__ void __launch_bounds__(kBT) k_predict_rows(PredictRows a) {
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * kBT + threadIdx.x) >> 5, nw = (gridDim.x * kBT) >> 5;
-    double dmax = 0.0;
-    for (int i = gw; i < a.n; i += nw) {
-        if (a.type[i] != kFluid) continue;
-        const float4 pi32 = a.pos32[i];
+__global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
+    const int i = blockIdx.x * kBT + threadIdx.x;
+    double disp = 0.0;
+    if (i < a.n && a.type[i] == kFluid) {
+        const float4 ih = a.pos32[i], il = a.pos32lo[i];
         const double4 pi = a.pos[i];
         const double4 ui = a.vel[i];
-        const float4 ui32 = make_float4((float)ui.x, (float)ui.y, (float)ui.z, 0.f);
+        const float4 u32 = a.vel32[i];
         const int cnt = a.vcnt[i];
-        const size_t base = (size_t)i * a.cap_v;
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-        for (int k = lane; k < cnt; k += 32) {
-            const int j = a.vcol[base + k];
-            const float r2 = dist2_f(pi32, a.pos32[j]);
-            if (!in_radius(r2, a.r, a.pos, i, j, pi)) continue;
-            if (MIXED && r2 >= a.tiny2) {
+        ff f0 = {0.f, 0.f}, f1 = {0.f, 0.f}, f2 = {0.f, 0.f};
+        for (int k = 0; k < cnt; k++) {
+            const int j = a.vcol[sell(i, k, a.cap_v)];
+            const float4 jh = a.pos32[j];
+            const float r2 = dist2_f(ih, jh);
+            int t = tier1(r2, a.r);
+            if (t == 2) t = decide_band(pair_r2(ih, il, jh, a.pos32lo[j]), a.r, a.pos, pi, j) ? 1 : 0;
+            if (!t) continue;
+            if (MIXED) {
+                if (!(r2 > 0.f)) {   // coincident to FP32: decide in binary64
+                    if (!(exact_dist2(pi, a.pos[j]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
+                    continue;
+                }
                 const float w = fmaf(a.r.re_f, rsqrtf(r2), -1.f);
                 const float4 uj = a.vel32[j];
-                f0 = fmaf(uj.x - ui32.x, w, f0);
-                f1 = fmaf(uj.y - ui32.y, w, f1);
-                f2 = fmaf(uj.z - ui32.z, w, f2);
+                f0 = ff_add_f(f0, (uj.x - u32.x) * w);
+                f1 = ff_add_f(f1, (uj.y - u32.y) * w);
+                f2 = ff_add_f(f2, (uj.z - u32.z) * w);
             } else {
                 const double4 pj = a.pos[j];
                 const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
@@ -86,43 +122,60 @@ __global__ void __launch_bounds__(kBT) k_predict_rows(PredictRows a) {
                 s2 = fma(uj.z - ui.z, w, s2);
             }
         }
-        s0 = warp_sum(s0 + (double)f0);
-        s1 = warp_sum(s1 + (double)f1);
-        s2 = warp_sum(s2 + (double)f2);
-        if (lane == 0) {
-            // u* = u + dt (nu lap(u) + g); r* = r + dt u*  (one rounding per operation)
-            const double l0 = a.coef_lap * s0, l1 = a.coef_lap * s1, l2 = a.coef_lap * s2;
-            double4 us, ps;
-            us.x = __dadd_rn(ui.x, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(a.nu, l0), a.g0)));
-            us.y = __dadd_rn(ui.y, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(a.nu, l1), a.g1)));
-            us.z = __dadd_rn(ui.z, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(a.nu, l2), a.g2)));
-            us.w = 0.0;
-            ps.x = __dadd_rn(pi.x, __dmul_rn(a.dt, us.x));
-            ps.y = __dadd_rn(pi.y, __dmul_rn(a.dt, us.y));
-            ps.z = __dadd_rn(pi.z, __dmul_rn(a.dt, us.z));
-            ps.w = 0.0;
-            a.vel_star[i] = us;
-            a.pos_star[i] = ps;
-            a.pos32_star[i] = make_float4((float)(ps.x - a.bmin0), (float)(ps.y - a.bmin1),
-                                          (float)(ps.z - a.bmin2), pi32.w);
-            const double dx = ps.x - pi.x, dy = ps.y - pi.y, dz = ps.z - pi.z;
-            dmax = fmax(dmax, sqrt(dx * dx + dy * dy + dz * dz));
+        if (MIXED) {
+            s0 = ff_to_double(f0);
+            s1 = ff_to_double(f1);
+            s2 = ff_to_double(f2);
         }
+        // u* = u + dt (nu lap(u) + g); r* = r + dt u*  (one rounding per operation)
+        const double l0 = a.coef_lap * s0, l1 = a.coef_lap * s1, l2 = a.coef_lap * s2;
+        double4 us, ps;
+        us.x = __dadd_rn(ui.x, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(a.nu, l0), a.g0)));
+        us.y = __dadd_rn(ui.y, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(a.nu, l1), a.g1)));
+        us.z = __dadd_rn(ui.z, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(a.nu, l2), a.g2)));
+        us.w = 0.0;
+        ps.x = __dadd_rn(pi.x, __dmul_rn(a.dt, us.x));
+        ps.y = __dadd_rn(pi.y, __dmul_rn(a.dt, us.y));
+        ps.z = __dadd_rn(pi.z, __dmul_rn(a.dt, us.z));
+        ps.w = 0.0;
+        a.vel_star[i] = us;
+        a.pos_star[i] = ps;
+        float4 h4, l4;
+        split_rel(ps.x, a.bmin0, &h4.x, &l4.x);
+        split_rel(ps.y, a.bmin1, &h4.y, &l4.y);
+        split_rel(ps.z, a.bmin2, &h4.z, &l4.z);
+        h4.w = ih.w;
+        l4.w = 0.f;
+        a.pos32_star[i] = h4;
+        a.pos32lo_star[i] = l4;
+        const double dx = ps.x - pi.x, dy = ps.y - pi.y, dz = ps.z - pi.z;
+        disp = sqrt(dx * dx + dy * dy + dz * dz);
     }
-    if (lane == 0 && dmax > 0.0)
-        atomicMax(&a.st->max_disp_bits, (unsigned long long)__double_as_longlong(dmax));
+    // block max of the displacement, one atomic per block
+    __shared__ double s_max[kBT / 32];
+    double v = disp;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < kBT / 32; w++) m = fmax(m, s_max[w]);
+        if (m > 0.0) atomicMax(&a.st->max_disp_bits, (unsigned long long)__double_as_longlong(m));
+    }
 }
 
-struct BuildRows {
+struct BuildArgs {
     int n, cap_v, cap, cap_n, pressure_mode;
     const int32_t* vcol;
     const int32_t* vcnt;
-    const float4* pos32;   // r*
-    const double4* pos;    // r*
+    const float4* pos32;     // r*
+    const float4* pos32lo;   // r*
+    const double4* pos;      // r*
     const int8_t* type;
     DevStatus* st;
     Radius rn, rl;
     double coef_ppe, n0, beta, inv_dt2, diag_add, wc_k, gamma;
+    ff coef_ff;
     int32_t* lap_col;
     double* lap_v64;
     float* lap_v32;
@@ -133,106 +186,117 @@ struct BuildRows {
     uint8_t* flag;
     double* bvec;
     double* diag;
+    float* diag32;
     double* p;
 };
 
-__global__ void __launch_bounds__(kBT) k_build_rows(BuildRows a) {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
-    const int gw = (blockIdx.x * kBT + threadIdx.x) >> 5, nw = (gridDim.x * kBT) >> 5;
-    unsigned n_surf = 0, n_ppe = 0;
-    for (int i = gw; i < a.n; i += nw) {
+template <bool MIXED>
+__global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
+    const int i = blockIdx.x * kBT + threadIdx.x;
+    bool surf = false, ppe = false;
+    if (i < a.n && a.type[i] != kGhost) {
         const int ti = a.type[i];
-        if (ti == kGhost) continue;
         const bool rows = (ti == kFluid || ti == kWall);
-        const float4 pi32 = a.pos32[i];
+        const float4 ih = a.pos32[i], il = a.pos32lo[i];
         const double4 pi = a.pos[i];
         const int cnt = a.vcnt[i];
-        const size_t base = (size_t)i * a.cap_v;
-        const size_t lbase = (size_t)i * a.cap, nbase = (size_t)i * a.cap_n;
         double nd = 0.0, dg = 0.0;
+        ff ndf = {0.f, 0.f}, dgf = {0.f, 0.f};
         int out_l = 0, out_n = 0;
-        for (int kb = 0; kb < cnt; kb += 32) {
-            const int k = kb + lane;
-            bool inl = false, inn = false;
-            int j = 0, kj = kDummy;
-            double rs = 0.0;
-            if (k < cnt) {
-                j = a.vcol[base + k];
-                const float4 q = a.pos32[j];
-                kj = kind_of(q);
-                const float r2 = dist2_f(pi32, q);
-                inl = in_radius(r2, a.rl, a.pos, i, j, pi);
-                inn = in_radius(r2, a.rn, a.pos, i, j, pi);
-                if (inl || inn) {
-                    const double4 pj = a.pos[j];
-                    const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
-                    const double rr2 = fma(dz, dz, fma(dy, dy, dx * dx));
-                    if (!(rr2 > 0.0)) {
-                        atomicOr(&a.st->err, kErrCoincident);
-                        inl = inn = false;
-                    } else {
-                        rs = rsqrt(rr2);
+        for (int k = 0; k < cnt; k++) {
+            const int j = a.vcol[sell(i, k, a.cap_v)];
+            const float4 jh = a.pos32[j];
+            const float r2 = dist2_f(ih, jh);
+            const bool nb_ok = rows && kind_of(jh) != kDummy;
+            // PPE rows exist only on the PPE path
+            int tl = (nb_ok && a.pressure_mode == 0) ? tier1(r2, a.rl) : 0;
+            int tn = tier1(r2, a.rn);
+            if (!tl && !tn) continue;
+            const bool band = (tl == 2 || tn == 2);
+            ff r2f;
+            if (MIXED || band) r2f = pair_r2(ih, il, jh, a.pos32lo[j]);
+            if (tl == 2) tl = decide_band(r2f, a.rl, a.pos, pi, j) ? 1 : 0;
+            if (tn == 2) tn = decide_band(r2f, a.rn, a.pos, pi, j) ? 1 : 0;
+            if (!tl && !tn) continue;
+            if (MIXED) {
+                if (!(r2f.h > 0.f)) {
+                    if (!(exact_dist2(pi, a.pos[j]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
+                    continue;
+                }
+                const ff y = ff_rsqrt(r2f);   // 1/r
+                if (tn) ndf = ff_add(ndf, ff_add_f(ff_mul({a.rn.re_f, a.rn.re_l}, y), -1.f));
+                if (tl) {
+                    const ff c = ff_mul(a.coef_ff, ff_add_f(ff_mul({a.rl.re_f, a.rl.re_l}, y), -1.f));
+                    dgf = ff_add(dgf, c);
+                    if (out_l < a.cap) {
+                        const size_t q = sell(i, out_l, a.cap);
+                        a.lap_col[q] = j;
+                        a.lap_v64[q] = ff_to_double(c);
+                        if (a.lap_v32) a.lap_v32[q] = c.h + c.l;
                     }
+                    out_l++;
+                }
+            } else {
+                const double4 pj = a.pos[j];
+                const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                const double rr2 = fma(dz, dz, fma(dy, dy, dx * dx));
+                if (!(rr2 > 0.0)) {
+                    atomicOr(&a.st->err, kErrCoincident);
+                    continue;
+                }
+                const double rs = rsqrt(rr2);
+                if (tn) nd += fma(a.rn.re, rs, -1.0);
+                if (tl) {
+                    const double c = a.coef_ppe * fma(a.rl.re, rs, -1.0);
+                    dg += c;
+                    if (out_l < a.cap) {
+                        const size_t q = sell(i, out_l, a.cap);
+                        a.lap_col[q] = j;
+                        a.lap_v64[q] = c;
+                        if (a.lap_v32) a.lap_v32[q] = (float)c;
+                    }
+                    out_l++;
                 }
             }
-            if (inn) nd += fma(a.rn.re, rs, -1.0);
-            const bool emit_l = rows && inl && kj != kDummy;
-            const bool emit_n = rows && inn && kj != kDummy;
-            double cij = 0.0;
-            if (emit_l) {
-                cij = a.coef_ppe * fma(a.rl.re, rs, -1.0);
-                dg += cij;
+            if (tn && nb_ok) {
+                if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j;
+                out_n++;
             }
-            const unsigned bl = __ballot_sync(0xffffffffu, emit_l);
-            const unsigned bn = __ballot_sync(0xffffffffu, emit_n);
-            if (emit_l) {
-                const int q = out_l + __popc(bl & lt);
-                if (q < a.cap) {
-                    a.lap_col[lbase + q] = j;
-                    a.lap_v64[lbase + q] = cij;
-                    if (a.lap_v32) a.lap_v32[lbase + q] = (float)cij;
-                }
-            }
-            if (emit_n) {
-                const int q = out_n + __popc(bn & lt);
-                if (q < a.cap_n) a.n_col[nbase + q] = j;
-            }
-            out_l += __popc(bl);
-            out_n += __popc(bn);
         }
-        nd = warp_sum(nd);
-        dg = warp_sum(dg);
-        if (lane == 0) {
-            const bool surf = rows && (nd < a.beta * a.n0);
-            const bool ppe = rows && !surf;
-            a.nstar[i] = nd;
-            a.flag[i] = surf ? 1 : 0;
-            a.bvec[i] = ppe ? a.inv_dt2 * ((nd - a.n0) / a.n0) : 0.0;
-            a.diag[i] = ppe ? dg + a.diag_add : 0.0;
-            a.lap_cnt[i] = min(out_l, a.cap);
-            a.n_cnt[i] = min(out_n, a.cap_n);
-            if (out_l > a.cap || out_n > a.cap_n) atomicOr(&a.st->err, kErrCap);
-            if (a.pressure_mode == 1) a.p[i] = ppe ? a.wc_k * (pow(nd / a.n0, a.gamma) - 1.0) : 0.0;
-            n_surf += surf ? 1u : 0u;
-            n_ppe += ppe ? 1u : 0u;
+        if (MIXED) {
+            nd = ff_to_double(ndf);
+            dg = ff_to_double(dgf);
         }
+        surf = rows && (nd < a.beta * a.n0);
+        ppe = rows && !surf;
+        a.nstar[i] = nd;
+        a.flag[i] = surf ? 1 : 0;
+        a.bvec[i] = ppe ? a.inv_dt2 * ((nd - a.n0) / a.n0) : 0.0;
+        const double dgv = ppe ? dg + a.diag_add : 0.0;
+        a.diag[i] = dgv;
+        a.diag32[i] = (float)dgv;
+        a.lap_cnt[i] = min(out_l, a.cap);
+        a.n_cnt[i] = min(out_n, a.cap_n);
+        if (out_l > a.cap || out_n > a.cap_n) atomicOr(&a.st->err, kErrCap);
+        if (a.pressure_mode == 1) a.p[i] = ppe ? a.wc_k * (pow(nd / a.n0, a.gamma) - 1.0) : 0.0;
     }
-    if (lane == 0) {
-        if (n_surf) atomicAdd(&a.st->n_surface, n_surf);
-        if (n_ppe) atomicAdd(&a.st->n_ppe, n_ppe);
+    const unsigned bs = __ballot_sync(0xffffffffu, surf), bp = __ballot_sync(0xffffffffu, ppe);
+    if ((threadIdx.x & 31) == 0) {
+        if (bs) atomicAdd(&a.st->n_surface, (unsigned)__popc(bs));
+        if (bp) atomicAdd(&a.st->n_ppe, (unsigned)__popc(bp));
     }
 }
 }  // namespace
 
 void launch_predict_rows(Ctx* c) {
     const mps_params& P = c->prm;
-    PredictRows a;
+    PredictArgs a;
     a.n = (int)c->n;
     a.cap_v = c->cap_v;
     a.vcol = c->vl_col;
     a.vcnt = c->vl_cnt;
     a.pos32 = c->pos32;
+    a.pos32lo = c->pos32lo;
     a.pos = c->pos;
     a.vel = c->vel;
     a.vel32 = c->vel32;
@@ -240,9 +304,9 @@ void launch_predict_rows(Ctx* c) {
     a.pos_star = c->pos_star;
     a.vel_star = c->vel_star;
     a.pos32_star = c->pos32_star;
+    a.pos32lo_star = c->pos32lo_star;
     a.st = c->st;
     a.r = c->r_lap;
-    a.tiny2 = (float)(1e-6 * c->r_lap.re2);
     a.coef_lap = c->coef_lap;
     a.nu = P.nu;
     a.dt = P.dt;
@@ -252,15 +316,15 @@ void launch_predict_rows(Ctx* c) {
     a.bmin0 = c->grid.bmin[0];
     a.bmin1 = c->grid.bmin[1];
     a.bmin2 = c->grid.bmin[2];
-    const int grid = c->sms * 8;
-    if (P.precision == 1) k_predict_rows<true><<<grid, kBT, 0, c->stream>>>(a);
-    else k_predict_rows<false><<<grid, kBT, 0, c->stream>>>(a);
+    const int grid = (int)((c->n + kBT - 1) / kBT);
+    if (P.precision == 1) k_predict<true><<<grid, kBT, 0, c->stream>>>(a);
+    else k_predict<false><<<grid, kBT, 0, c->stream>>>(a);
     c->launches += 1;
 }
 
 void launch_build_rows(Ctx* c) {
     const mps_params& P = c->prm;
-    BuildRows a;
+    BuildArgs a;
     a.n = (int)c->n;
     a.cap_v = c->cap_v;
     a.cap = c->cap;
@@ -269,12 +333,14 @@ void launch_build_rows(Ctx* c) {
     a.vcol = c->vl_col;
     a.vcnt = c->vl_cnt;
     a.pos32 = c->pos32_star;
+    a.pos32lo = c->pos32lo_star;
     a.pos = c->pos_star;
     a.type = c->type;
     a.st = c->st;
     a.rn = c->r_n;
     a.rl = c->r_lap;
     a.coef_ppe = c->coef_ppe;
+    a.coef_ff = ff_from_double(c->coef_ppe);
     a.n0 = c->n0_pnd;
     a.beta = P.beta;
     a.inv_dt2 = c->inv_dt2;
@@ -291,8 +357,11 @@ void launch_build_rows(Ctx* c) {
     a.flag = c->flag;
     a.bvec = c->bvec;
     a.diag = c->diag;
+    a.diag32 = c->diag32;
     a.p = c->p;
-    k_build_rows<<<c->sms * 8, kBT, 0, c->stream>>>(a);
+    const int grid = (int)((c->n + kBT - 1) / kBT);
+    if (P.precision == 1) k_build<true><<<grid, kBT, 0, c->stream>>>(a);
+    else k_build<false><<<grid, kBT, 0, c->stream>>>(a);
     c->launches += 1;
 }
 

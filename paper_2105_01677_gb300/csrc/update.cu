@@ -23,9 +23,8 @@ __global__ void __launch_bounds__(kBT)
     double m = pi;
     if (type[i] == kFluid) {
         const int cnt = ncnt[i];
-        const size_t base = (size_t)i * cap_n;
         for (int k = 0; k < cnt; k++) {
-            double pj = p[ncol[base + k]];
+            double pj = p[ncol[sell(i, k, cap_n)]];
             if (clamp) pj = fmax(pj, 0.0);
             m = fmin(m, pj);
         }
@@ -50,13 +49,12 @@ __global__ void __launch_bounds__(kBT)
     const double4 pi = ps[i];
     const double ph = phat[i];
     const int cnt = ncnt[i];
-    const size_t base = (size_t)i * cap_n;
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
     if (MIXED) {
         const float4 qi = ps32[i];
         float f0 = 0.f, f1 = 0.f, f2 = 0.f;
         for (int k = 0; k < cnt; k++) {
-            const int j = ncol[base + k];
+            const int j = ncol[sell(i, k, cap_n)];
             const float4 qj = ps32[j];
             const float dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -72,7 +70,7 @@ __global__ void __launch_bounds__(kBT)
         g2 = f2;
     } else {
         for (int k = 0; k < cnt; k++) {
-            const int j = ncol[base + k];
+            const int j = ncol[sell(i, k, cap_n)];
             const double4 pj = ps[j];
             const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
             const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
@@ -129,7 +127,8 @@ __global__ void __launch_bounds__(kBT) k_unpermute_u32(int n, const int32_t* id,
 __global__ void __launch_bounds__(kBT)
     k_ingest(int n, int dim, const double* i_pos, const double* i_vel, const int8_t* i_t,
              double4* pos, double4* vel, int8_t* type, int32_t* id, double* p, double* nstar,
-             uint8_t* flag, int keep_vel, int keep_types, GridDesc g, float4* pos32) {
+             uint8_t* flag, int keep_vel, int keep_types, GridDesc g, float4* pos32,
+             float4* pos32lo) {
     int s = blockIdx.x * kBT + threadIdx.x;
     if (s >= n) return;
     double x[3] = {0.0, 0.0, 0.0};
@@ -146,8 +145,14 @@ __global__ void __launch_bounds__(kBT)
     p[s] = 0.0;
     nstar[s] = 0.0;
     flag[s] = 0;
-    pos32[s] = make_float4((float)(x[0] - g.bmin[0]), (float)(x[1] - g.bmin[1]),
-                           (float)(x[2] - g.bmin[2]), __int_as_float((int)type[s]));
+    float4 h, l;
+    split_rel(x[0], g.bmin[0], &h.x, &l.x);
+    split_rel(x[1], g.bmin[1], &h.y, &l.y);
+    split_rel(x[2], g.bmin[2], &h.z, &l.z);
+    h.w = __int_as_float((int)type[s]);
+    l.w = 0.f;
+    pos32[s] = h;
+    pos32lo[s] = l;
 }
 }  // namespace
 
@@ -200,7 +205,8 @@ void launch_ingest(Ctx* c, const double* d_pos, const double* d_vel, const int8_
     k_ingest<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(n, c->dim, d_pos, d_vel, d_types, c->pos,
                                                           c->vel, c->type, c->id, c->p, c->nstar,
                                                           c->flag, keep_vel ? 1 : 0,
-                                                          keep_types ? 1 : 0, c->grid, c->pos32);
+                                                          keep_types ? 1 : 0, c->grid, c->pos32,
+                                                          c->pos32lo);
     c->launches += 1;
 }
 
