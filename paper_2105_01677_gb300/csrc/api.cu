@@ -346,7 +346,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     rep->n_ghost = s.n_ghost;
     rep->n_surface = s.n_surface;
     rep->n_ppe_rows = s.n_ppe;
-    rep->max_disp = bits_to_double(s.max_disp_bits);
+    rep->max_disp = std::sqrt(bits_to_double(s.max_disp_bits));   // device keeps the square
     rep->n0_pnd = c->n0_pnd;
     rep->n0_lap = c->n0_lap;
     rep->lambda = c->lambda;

@@ -90,7 +90,29 @@ __device__ __forceinline__ ff ff_rsqrt(ff x) {
     return ff_rsqrt_step(x, ff_rsqrt_step(x, y0));
 }
 
+// one Newton step only: relative error ~1e-13 (the FP32 estimate's error squared)
+__device__ __forceinline__ ff ff_rsqrt1(ff x) {
+    const ff y0 = {rsqrtf(x.h), 0.0f};
+    return ff_rsqrt_step(x, y0);
+}
+
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.h + (double)a.l; }
+
+// float -> double by moving the bits (exact for normal floats; zero and subnormal floats
+// give a signed zero, an error below 1.2e-38), on the integer pipes
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    if (e == 0u) return __longlong_as_double((long long)sign);
+    if (e == 0xffu) return (double)f;   // infinities and NaN keep their meaning
+    const unsigned long long bits =
+        sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// float-float -> double with a single FP64 operation (the conversions are bit moves)
+__device__ __forceinline__ double ff_to_double_fast(ff a) { return f2d_bits(a.h) + f2d_bits(a.l); }
 
 __host__ inline ff ff_from_double(double v) {
     const float h = (float)v;

@@ -2,10 +2,10 @@
 // neighbours are looked up in its own cell and the adjacent cells).
 //
 // One thread block per occupied cell; each thread owns one particle of that cell.  The
-// particles of the 3^d surrounding cells are staged in shared memory in chunks (FP32
-// positions relative to the grid origin, the kind in the fourth lane), and every thread
-// walks the same staged candidates, so the shared-memory reads are broadcasts and the
-// rare FP64 loads of a candidate are warp-uniform.
+// 3^d surrounding cells' particles are staged in shared memory per cell (FP32 positions
+// relative to the grid origin, the slot in the fourth lane), and every thread walks the same
+// staged candidates, so the shared-memory reads are broadcasts and the rare FP64 loads of a
+// candidate are warp-uniform.
 //
 // Distance predicate of the exact sets: a candidate is classified from its FP32 squared
 // distance against a band [lo, hi) around re^2 that bounds the FP32 rounding error; only
@@ -24,19 +24,23 @@ namespace mps {
 
 namespace {
 
-template <int BT, int CHUNK, bool STAGE_X, class Op>
+// One block per occupied cell, one thread per particle of the cell.  The particles of the
+// 3^d surrounding cells (contiguous slot ranges in Morton order) are staged once in shared
+// memory as (x, y, z, slot) and every thread walks the same staged candidates, so each read
+// is a shared-memory broadcast; one barrier pair per cell (more only when a cell's
+// neighbourhood exceeds CHUNK candidates).
+template <int BT, int CHUNK, class Op>
 __global__ void __launch_bounds__(BT)
     k_gather(Op op, const int32_t* __restrict__ cell_start, const uint32_t* __restrict__ occ,
              const DevStatus* st, GridDesc g) {
-    __shared__ float4 s_p[CHUNK];
-    __shared__ int s_j[CHUNK];
-    __shared__ float4 s_x[STAGE_X ? CHUNK : 1];
+    extern __shared__ float4 s_q[];   // CHUNK entries
     __shared__ int s_cs[27], s_pref[28];
     __shared__ int s_nc;
     const unsigned n_occ = *(volatile const unsigned*)&st->n_occ;
     for (unsigned ci = blockIdx.x; ci < n_occ; ci += gridDim.x) {
         const uint32_t code = occ[ci];
         const int c0 = cell_start[code], c1 = cell_start[code + 1];
+        __syncthreads();   // previous cell's staged data and ranges no longer in use
         if (threadIdx.x == 0) {
             int cc[3];
             morton_decode(code, g.dim, g.bits, cc);
@@ -63,35 +67,46 @@ __global__ void __launch_bounds__(BT)
         }
         __syncthreads();
         const int ncand = s_pref[s_nc];
+        const int ncells = s_nc;
+        const bool once = ncand <= CHUNK;   // whole neighbourhood staged once for the cell
+        // copy candidates [base, base + len) cell by cell (coalesced slot ranges)
+        auto stage = [&](int base, int len) {
+            for (int m = 0; m < ncells; m++) {
+                const int a = max(s_pref[m], base), b = min(s_pref[m + 1], base + len);
+                const int off = s_cs[m] - s_pref[m];
+                for (int f = a + (int)threadIdx.x; f < b; f += BT) {
+                    float4 q = op.pos32[f + off];
+                    q.w = __int_as_float(f + off);
+                    s_q[f - base] = q;
+                }
+            }
+        };
+        if (once) {
+            stage(0, ncand);
+            __syncthreads();
+        }
         for (int ib = c0; ib < c1; ib += BT) {
             const int i = ib + threadIdx.x;
             const bool act = (i < c1) && op.active(i);
-            if (!__syncthreads_or(act)) continue;
             typename Op::Center ctr;
             op.begin(i, act, ctr);
             for (int base = 0; base < ncand; base += CHUNK) {
                 const int len = min(CHUNK, ncand - base);
-                for (int k = threadIdx.x; k < len; k += BT) {
-                    const int f = base + k;
-                    int m = 0;
-                    while (s_pref[m + 1] <= f) ++m;
-                    const int j = s_cs[m] + (f - s_pref[m]);
-                    s_j[k] = j;
-                    s_p[k] = op.pos32[j];
-                    if (STAGE_X) s_x[k] = op.stage(j);
+                if (!once) {
+                    if (base > 0 || ib > c0) __syncthreads();   // buffer reuse
+                    stage(base, len);
+                    __syncthreads();
                 }
-                __syncthreads();
                 if (act) {
 #pragma unroll 4
-                    for (int k = 0; k < len; k++)
-                        op.visit(ctr, i, s_j[k], s_p[k], STAGE_X ? s_x[k] : s_p[k]);
-                    op.end_chunk(ctr);
+                    for (int k = 0; k < len; k++) {
+                        const float4 q = s_q[k];
+                        op.visit(ctr, i, __float_as_int(q.w), q);
+                    }
                 }
-                __syncthreads();
             }
             op.finish(i, act, ctr);
         }
-        __syncthreads();
     }
 }
 
@@ -120,17 +135,15 @@ struct VerletOp {
         int cnt;
     };
     __device__ bool active(int i) const { return type[i] != kGhost; }
-    __device__ float4 stage(int) const { return make_float4(0.f, 0.f, 0.f, 0.f); }
     __device__ void begin(int i, bool act, Center& c) const {
         c.cnt = 0;
         if (act) c.p32 = pos32[i];
     }
-    __device__ void visit(Center& c, int i, int j, const float4& q, const float4&) const {
+    __device__ void visit(Center& c, int i, int j, const float4& q) const {
         if (j == i || dist2_f(c.p32, q) >= hv2) return;
         if (c.cnt < cap_v) vcol[sell(i, c.cnt, cap_v)] = j;
         c.cnt++;
     }
-    __device__ void end_chunk(Center&) const {}
     __device__ void finish(int i, bool act, const Center& c) const {
         if (!act) return;
         vcnt[i] = min(c.cnt, cap_v);
@@ -154,20 +167,18 @@ struct NbrOp {
         int cnt;
     };
     __device__ bool active(int i) const { return type[i] != kGhost; }
-    __device__ float4 stage(int) const { return make_float4(0.f, 0.f, 0.f, 0.f); }
     __device__ void begin(int i, bool act, Center& c) const {
         c.cnt = 0;
         if (!act) return;
         c.p = pos[i];
         c.p32 = pos32[i];
     }
-    __device__ void visit(Center& c, int i, int j, const float4& q, const float4&) const {
+    __device__ void visit(Center& c, int i, int j, const float4& q) const {
         if (j == i) return;
         if (!in_radius(dist2_f(c.p32, q), r, pos, i, j, c.p)) return;
         if (row_off) out_ids[row_off[i] + c.cnt] = id[j];
         c.cnt++;
     }
-    __device__ void end_chunk(Center&) const {}
     __device__ void finish(int i, bool act, const Center& c) const {
         if (act && !row_off) out_cnt[i] = c.cnt;
     }
@@ -184,15 +195,17 @@ __global__ void k_copy_star(int n, const double4* pos, const double4* vel, const
     p32los[i] = pos32lo[i];
 }
 
-template <class Op, bool STAGE_X>
+template <class Op>
 void launch_gather(Ctx* c, const Op& op) {
     c->launches += 1;
     if (c->dim == 3) {
-        k_gather<128, 1024, STAGE_X, Op><<<c->sms * 6, 128, 0, c->stream>>>(op, c->cell_start, c->occ,
-                                                                         c->st, c->grid);
+        constexpr int kChunk = 512;
+        k_gather<96, kChunk, Op><<<c->sms * 16, 96, kChunk * sizeof(float4), c->stream>>>(
+            op, c->cell_start, c->occ, c->st, c->grid);
     } else {
-        k_gather<32, 256, STAGE_X, Op><<<c->sms * 16, 32, 0, c->stream>>>(op, c->cell_start, c->occ,
-                                                                      c->st, c->grid);
+        constexpr int kChunk = 512;
+        k_gather<32, kChunk, Op><<<c->sms * 32, 32, kChunk * sizeof(float4), c->stream>>>(
+            op, c->cell_start, c->occ, c->st, c->grid);
     }
 }
 
@@ -215,7 +228,7 @@ void launch_verlet(Ctx* c) {
     op.cap_v = c->cap_v;
     op.vcol = c->vl_col;
     op.vcnt = c->vl_cnt;
-    launch_gather<VerletOp, false>(c, op);
+    launch_gather<VerletOp>(c, op);
 }
 
 void launch_debug_neighbors(Ctx* c, const Radius& r, const int64_t* row_off, int32_t* out_ids,
@@ -229,7 +242,7 @@ void launch_debug_neighbors(Ctx* c, const Radius& r, const int64_t* row_off, int
     op.row_off = row_off;
     op.out_ids = out_ids;
     op.out_cnt = out_cnt;
-    launch_gather<NbrOp, false>(c, op);
+    launch_gather<NbrOp>(c, op);
 }
 
 }  // namespace mps

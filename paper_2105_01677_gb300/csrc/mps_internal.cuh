@@ -42,7 +42,7 @@ struct DevStatus {
     unsigned int n_surface;
     unsigned int n_ppe;
     unsigned int pad0;
-    unsigned long long max_disp_bits;   // atomicMax over bit patterns of non-negative doubles
+    unsigned long long max_disp_bits;   // max squared FLUID displacement (bit pattern of a non-negative double)
     unsigned int counter[8];            // last-block-done tickets of grid reductions
 };
 

@@ -248,6 +248,29 @@ __global__ void __launch_bounds__(kBT) k_resid64_t(SellView c, const double* x, 
     }
 }
 
+// start of a solve from x = 0: x = 0, r = b, d = b, rr = rho = b.b, stop2 = tol2 b.b
+__global__ void __launch_bounds__(kBT) k_start64(SellView c, double* x, double* r, double* d,
+                                                 CgScalars* cg, double tol2) {
+    __shared__ double sm[kWarps];
+    double part = 0.0;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT) {
+        const double bi = c.bvec[i];
+        x[i] = 0.0;
+        r[i] = bi;
+        d[i] = bi;
+        part = fma(bi, bi, part);
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, c.partials, &c.counter[0], &tot, sm) && threadIdx.x == 0) {
+        cg->rr = tot;
+        cg->stop2 = tol2 * tot;
+        cg->rho = tot;
+        cg->rho0 = tot;
+        cg->done = (tot <= cg->stop2) ? 1 : 0;
+    }
+}
+
 // q = A d, alpha = rho / (d.q)
 __global__ void __launch_bounds__(kBT) k_spmv64_t(SellView c, const double* d, double* q,
                                                   CgScalars* cg) {
@@ -389,11 +412,10 @@ int ppe_solve(Ctx* c, mps_report* rep) {
     const int max_total = c->prm.cg_max_iter > 0 ? c->prm.cg_max_iter : (int)std::min<int64_t>(10 * c->n, 1 << 30);
     const int gs = c->sms * 8, gv = vec_grid(c);
     int rc;
-    k_clear_x<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->p);
-    c->launches += 2;
     if ((rc = set_cg_limits(c, max_total))) return rc;
-    // r = b, d = b, rho = |b|^2, stop2 = tol^2 |b|^2
-    k_resid64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2, 1, 1);
+    // x = 0, r = b, d = b, rho = |b|^2, stop2 = tol^2 |b|^2
+    k_start64<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2);
+    c->launches += 1;
     if ((rc = read_scalars(c))) return rc;
     const double bnorm2 = c->cg_host->rr;
     const double stop2 = c->cg_host->stop2;

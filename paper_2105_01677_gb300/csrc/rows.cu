@@ -22,8 +22,9 @@
 //            neighbour lists for the PPE and the gradient (non-dummy j within re_n), and the
 //            equation-of-state pressure (Eq. 16).
 // Precision: FP64 mode evaluates pair terms in binary64; mixed mode evaluates the viscosity
-// terms in FP32 and the number density and PPE coefficients in float-float (relative error
-// ~1e-13), accumulated in float-float and stored in binary64.
+// terms in FP32 (summed in float-float, stored in binary64) and the number density
+// and PPE coefficients in float-float (relative error ~1e-13), accumulated in float-float
+// and stored in binary64.
 #include "ff.cuh"
 #include "mps_internal.cuh"
 
@@ -89,10 +90,17 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
         const float4 u32 = a.vel32[i];
         const int cnt = a.vcnt[i];
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        ff f0 = {0.f, 0.f}, f1 = {0.f, 0.f}, f2 = {0.f, 0.f};
+        ff f0 = {0.f, 0.f}, f1 = {0.f, 0.f}, f2 = {0.f, 0.f};   // FP32 terms, float-float sums
+        // two-stage software pipeline: the slot of k+2 and the position of k+1 are in flight
+        int jn = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : 0;
+        int j0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
+        float4 qn = a.pos32[j0];
         for (int k = 0; k < cnt; k++) {
-            const int j = a.vcol[sell(i, k, a.cap_v)];
-            const float4 jh = a.pos32[j];
+            const int j = j0;
+            const float4 jh = qn;
+            j0 = jn;
+            if (k + 1 < cnt) qn = a.pos32[jn];
+            if (k + 2 < cnt) jn = a.vcol[sell(i, k + 2, a.cap_v)];
             const float r2 = dist2_f(ih, jh);
             int t = tier1(r2, a.r);
             if (t == 2) t = decide_band(pair_r2(ih, il, jh, a.pos32lo[j]), a.r, a.pos, pi, j) ? 1 : 0;
@@ -123,9 +131,9 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
             }
         }
         if (MIXED) {
-            s0 = ff_to_double(f0);
-            s1 = ff_to_double(f1);
-            s2 = ff_to_double(f2);
+            s0 = ff_to_double_fast(f0);
+            s1 = ff_to_double_fast(f1);
+            s2 = ff_to_double_fast(f2);
         }
         // u* = u + dt (nu lap(u) + g); r* = r + dt u*  (one rounding per operation)
         const double l0 = a.coef_lap * s0, l1 = a.coef_lap * s1, l2 = a.coef_lap * s2;
@@ -149,19 +157,15 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
         a.pos32_star[i] = h4;
         a.pos32lo_star[i] = l4;
         const double dx = ps.x - pi.x, dy = ps.y - pi.y, dz = ps.z - pi.z;
-        disp = sqrt(dx * dx + dy * dy + dz * dz);
+        disp = fma(dz, dz, fma(dy, dy, dx * dx));   // squared; the host takes the root
     }
-    // block max of the displacement, one atomic per block
-    __shared__ double s_max[kBT / 32];
-    double v = disp;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int w = 0; w < kBT / 32; w++) m = fmax(m, s_max[w]);
-        if (m > 0.0) atomicMax(&a.st->max_disp_bits, (unsigned long long)__double_as_longlong(m));
+    // warp max of the squared displacement (non-negative doubles order like their bits)
+    unsigned long long v = (unsigned long long)__double_as_longlong(disp);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
     }
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(&a.st->max_disp_bits, v);
 }
 
 struct BuildArgs {
@@ -175,7 +179,7 @@ struct BuildArgs {
     DevStatus* st;
     Radius rn, rl;
     double coef_ppe, n0, beta, inv_dt2, diag_add, wc_k, gamma;
-    ff coef_ff;
+    ff cre_ff, ncoef_ff;   // coef_ppe * re_lap and -coef_ppe as float-float
     int32_t* lap_col;
     double* lap_v64;
     float* lap_v32;
@@ -203,9 +207,15 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
         double nd = 0.0, dg = 0.0;
         ff ndf = {0.f, 0.f}, dgf = {0.f, 0.f};
         int out_l = 0, out_n = 0;
+        int jn = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : 0;
+        int j0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
+        float4 qn = a.pos32[j0];
         for (int k = 0; k < cnt; k++) {
-            const int j = a.vcol[sell(i, k, a.cap_v)];
-            const float4 jh = a.pos32[j];
+            const int j = j0;
+            const float4 jh = qn;
+            j0 = jn;
+            if (k + 1 < cnt) qn = a.pos32[jn];
+            if (k + 2 < cnt) jn = a.vcol[sell(i, k + 2, a.cap_v)];
             const float r2 = dist2_f(ih, jh);
             const bool nb_ok = rows && kind_of(jh) != kDummy;
             // PPE rows exist only on the PPE path
@@ -223,15 +233,21 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                     if (!(exact_dist2(pi, a.pos[j]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
                     continue;
                 }
-                const ff y = ff_rsqrt(r2f);   // 1/r
-                if (tn) ndf = ff_add(ndf, ff_add_f(ff_mul({a.rn.re_f, a.rn.re_l}, y), -1.f));
+                // 1/r: one Newton step (~1e-13) serves the PPE coefficient; the number density
+                // takes a second (~1e-15) so that n* stays far inside the flag band
+                ff y = ff_rsqrt1(r2f);
+                if (tn) {
+                    y = ff_rsqrt_step(r2f, y);
+                    ndf = ff_add(ndf, ff_add_f(ff_mul({a.rn.re_f, a.rn.re_l}, y), -1.f));
+                }
                 if (tl) {
-                    const ff c = ff_mul(a.coef_ff, ff_add_f(ff_mul({a.rl.re_f, a.rl.re_l}, y), -1.f));
+                    // c = coef (re/r - 1) = (coef re) y - coef
+                    const ff c = ff_add(ff_mul(a.cre_ff, y), a.ncoef_ff);
                     dgf = ff_add(dgf, c);
                     if (out_l < a.cap) {
                         const size_t q = sell(i, out_l, a.cap);
                         a.lap_col[q] = j;
-                        a.lap_v64[q] = ff_to_double(c);
+                        a.lap_v64[q] = ff_to_double_fast(c);
                         if (a.lap_v32) a.lap_v32[q] = c.h + c.l;
                     }
                     out_l++;
@@ -264,8 +280,8 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
             }
         }
         if (MIXED) {
-            nd = ff_to_double(ndf);
-            dg = ff_to_double(dgf);
+            nd = ff_to_double_fast(ndf);
+            dg = ff_to_double_fast(dgf);
         }
         surf = rows && (nd < a.beta * a.n0);
         ppe = rows && !surf;
@@ -340,7 +356,8 @@ void launch_build_rows(Ctx* c) {
     a.rn = c->r_n;
     a.rl = c->r_lap;
     a.coef_ppe = c->coef_ppe;
-    a.coef_ff = ff_from_double(c->coef_ppe);
+    a.cre_ff = ff_from_double(c->coef_ppe * c->r_lap.re);
+    a.ncoef_ff = ff_from_double(-c->coef_ppe);
     a.n0 = c->n0_pnd;
     a.beta = P.beta;
     a.inv_dt2 = c->inv_dt2;
