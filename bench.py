@@ -40,14 +40,23 @@ METRIC = "particle-steps/s (3D ~200k dam break) FP64 vs mixed at PPE resid 1e-8;
 UNIT = "particle-steps/s"
 WORKLOAD = "3D dam break, 0.40x0.60x0.30 m column in 1.6x0.6x0.6 m tank, l0=0.0075 m"
 
-# Algorithmic bytes per particle per stage (matrix-free minimum: each array read or written
-# once per stage; neighbour re-reads served on chip).
-STAGE_BYTES = {
-    "bucket": 182.0,
-    "predict": {0: 97.0, 1: 113.0},
-    "build": 42.0,
-    "update": 146.0,
-}
+# Whole-step algorithmic bytes per particle (matrix-free minimum: every array read or
+# written once per stage, neighbour re-reads served on chip): bucket 182, predict 97 (FP64)
+# or 113 (mixed), density/flags/RHS 42, clamp + gradient 146; the PPE 113 per FP64 CG
+# iteration, or 57 per FP32 inner iteration plus 65 per FP64 residual (mixed).
+STEP_BYTES_FIXED = {0: 182.0 + 97.0 + 42.0 + 146.0, 1: 182.0 + 113.0 + 42.0 + 146.0}
+
+# Algorithmic FP32 flops (fused multiply-add = 2) of the ALU-bound kernels, per unit of
+# work counted live by the library:
+#   candidate gather: 8 per distance test (3 differences, 1 square, 2 fused squares);
+#   build (mixed): 133 per PPE coefficient in float-float (distance 70, one Newton step
+#   for 1/r 31, coefficient and diagonal sum 32) and 62 more per number-density term
+#   (second Newton step 31, weight and sum 31).
+FLOPS_PER_TEST = 8.0
+FLOPS_PER_PPE_PAIR = 133.0
+FLOPS_PER_PND_PAIR = 62.0
+# FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def parse():
@@ -219,7 +228,8 @@ def run_gb300(args):
             s_ev[i].record(stream)
             rc, rep = sim.step(1)
             e_ev[i].record(stream)
-            iters.append((rep["cg_iters"], rep["cg_outer"], rep["cg_resid"]))
+            iters.append((rep["cg_iters"], rep["cg_outer"], rep["cg_resid"], rep["cand_tests"],
+                          rep["pairs_ppe"], rep["pairs_pnd"]))
         torch.cuda.synchronize(dev)
         for i in range(k):
             total += s_ev[i].elapsed_time(e_ev[i])
@@ -304,26 +314,36 @@ def run_gb300(args):
     if rank != 0:
         return
 
-    # ---- roofline of the dominant stage (live stage timers on the library's stream)
+    # ---- roofline of the dominant kernel (live stage timers on the library's stream)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
     st_ms = prof["stage_ms"]
     st_calls = prof["stage_calls"]
     per_call = {k: (st_ms[k] / st_calls[k] if st_calls[k] else 0.0) for k in st_ms}
-    top = max(per_call, key=per_call.get)
-    iters_mean = float(np.mean([x[0] for x in it_mixed]))
-    outer_mean = float(np.mean([x[1] for x in it_mixed]))
-    if top == "ppe":
-        bytes_unit = 57.0 * iters_mean + 65.0 * (outer_mean + 1)
+    mean = lambda idx: float(np.mean([x[idx] for x in it_mixed]))
+    inner, outer = mean(0), mean(1)
+    tests, ppe_pairs, pnd_pairs = mean(3), mean(4), mean(5)
+    # the two single-kernel stages that dominate the step
+    single = {"gather": "k_gather<VerletOp>", "build": "k_build<mixed>"}
+    top = max(single, key=lambda k: per_call[k])
+    if top == "gather":
+        flops = FLOPS_PER_TEST * tests
     else:
-        b = STAGE_BYTES[top]
-        bytes_unit = b[1] if isinstance(b, dict) else b
-    achieved = bytes_unit * n / (per_call[top] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                "bytes_per_particle": bytes_unit,
-                "stage_ms_per_step": {k: per_call[k] for k in per_call},
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback"}
+        flops = FLOPS_PER_PPE_PAIR * ppe_pairs + FLOPS_PER_PND_PAIR * pnd_pairs
+    achieved = flops / (per_call[top] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": single[top], "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": None, "work": {"cand_tests": tests, "pairs_ppe": ppe_pairs,
+                                          "pairs_pnd": pnd_pairs},
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "stage_ms_per_step": {k: per_call[k] for k in per_call}}
+    step_bytes = n * (STEP_BYTES_FIXED[1] + 57.0 * inner + 65.0 * (outer + 1))
+    step_hbm = {"bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms_mixed / args.steps * 1e-3) / 1e9,
+                "peak_gbs": hbm, "frac": step_bytes / (ms_mixed / args.steps * 1e-3) / 1e9 / hbm,
+                "peak_source": hbm_src,
+                "model": "matrix-free minimum bytes per particle: 483 + 57 per FP32 inner CG "
+                         "iteration + 65 per FP64 residual"}
 
     value = world * n * args.steps / (ms_mixed * 1e-3)
     value64 = world * n * k64 / (ms_64 * 1e-3)
@@ -347,6 +367,7 @@ def run_gb300(args):
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(prof["launches"]),
         "roofline": roofline,
+        "step_hbm": step_hbm,
         "cpu_baseline": cpu,
         "clocks": clk,
     }

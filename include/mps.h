@@ -88,7 +88,8 @@ typedef struct {
     int32_t ppe_operator;     /* mixed inner operator: 0 stored FP32 coefficients,             *
                                * 1 matrix-free (coefficients recomputed from positions)        */
     int32_t device;           /* CUDA device ordinal                                           */
-    int32_t reserved0;
+    int32_t gather_block;     /* threads per cell block of the candidate gather: 32, 64, 96 or *
+                               * 128; 0 chooses by dimension (tuning only, results identical)  */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;
@@ -110,6 +111,9 @@ typedef struct {
     double n0_lap;            /* reference number density at re_lap                           */
     double lambda;            /* lambda of Eq. 7 at re_lap [m^2]                               */
     int64_t steps_done;       /* steps completed by this context so far                       */
+    int64_t cand_tests;       /* distance tests of the cell gather (candidate lists)          */
+    int64_t pairs_ppe;        /* PPE coefficients evaluated (non-dummy pairs within re_lap)   */
+    int64_t pairs_pnd;        /* number-density terms evaluated (pairs within re_n)           */
 } mps_report;
 
 /* Opaque context: device buffers, stream and derived constants of one particle system. */
@@ -152,7 +156,8 @@ int mps_step(mps_ctx* ctx, int32_t nsteps, mps_report* last);
 int mps_solve_ppe(mps_ctx* ctx, mps_report* out);
 
 /* Copy the state to caller buffers in original particle order; any pointer may be NULL.
- * pos, vel: n*dim doubles; p, n_star: n doubles (of the last step or solve; 0 before any);
+ * pos, vel: n*dim doubles; p, n_star: n doubles (of the last step or solve; 0 before any;
+ * n_star is 0 for DUMMY and GHOST particles, whose own density enters no equation);
  * flags: n bytes, bit 0 = free surface; types: n int8 (GHOST for particles that left). */
 int mps_read_state(mps_ctx* ctx, double* pos, double* vel, double* p, double* n_star,
                    uint8_t* flags, int8_t* types);
@@ -181,11 +186,12 @@ int mps_get_constants(mps_ctx* ctx, double* out);
 /* Stage timers (CUDA events recorded on the context's stream around each stage of a step)
  * and a count of the kernel launches the context issued.  Stages: */
 #define MPS_STAGE_BUCKET 0   /* cell keys, radix sort, cell table, permutation        */
-#define MPS_STAGE_PREDICT 1  /* viscosity + gravity prediction gather                 */
-#define MPS_STAGE_BUILD 2    /* number density, flags, PPE rows, neighbour lists       */
-#define MPS_STAGE_PPE 3      /* CG solve (includes the host's convergence polls)      */
-#define MPS_STAGE_UPDATE 4   /* clamp, minimum pressure, gradient correction          */
-#define MPS_NSTAGES 5
+#define MPS_STAGE_GATHER 1   /* candidate lists from the cell grid (one kernel)       */
+#define MPS_STAGE_PREDICT 2  /* viscosity + gravity prediction (one kernel)           */
+#define MPS_STAGE_BUILD 3    /* number density, flags, PPE rows, lists (one kernel)   */
+#define MPS_STAGE_PPE 4      /* CG solve (includes the host's convergence polls)      */
+#define MPS_STAGE_UPDATE 5   /* clamp, minimum pressure, gradient correction          */
+#define MPS_NSTAGES 6
 /* on != 0 enables the stage timers (off by default) and resets timers and counter. */
 int mps_set_profiling(mps_ctx* ctx, int32_t on);
 /* stage_ms[MPS_NSTAGES]: accumulated milliseconds; stage_calls[MPS_NSTAGES]: stages timed;

@@ -135,6 +135,9 @@ int check_params(const mps_params* P) {
     if (P->pressure_mode == 0 && !(P->cg_tol > 0)) return MPS_EINVAL;
     if (P->pressure_mode == 1 && !(P->gamma > 0)) return MPS_EINVAL;
     if ((P->alloc == nullptr) != (P->release == nullptr)) return MPS_EINVAL;
+    if (P->gather_block != 0 && P->gather_block != 32 && P->gather_block != 64 &&
+        P->gather_block != 96 && P->gather_block != 128)
+        return MPS_EINVAL;
     for (int a = 0; a < P->dim; a++)
         if (!(P->box_max[a] > P->box_min[a]) || !std::isfinite(P->box_min[a]) ||
             !std::isfinite(P->box_max[a]))
@@ -225,12 +228,16 @@ int allocate(Ctx* c) {
     A(p, n) A(p_alt, n) A(pos32, n) A(pos32lo, n) A(pos_star, n) A(vel_star, n) A(pos32_star, n)
     A(pos32lo_star, n) A(nstar, n) A(flag, n) A(bvec, n) A(diag, n) A(diag32, n) A(phat, n)
     A(vl_col, sv) A(vl_cnt, n) A(vel32, n)
-    A(nb_n_col, sn) A(nb_n_cnt, n) A(nb_lap_cnt, n)
+    // nb_lap_col also stages the number-density entries of a row while it is assembled
+    A(nb_n_col, sn) A(nb_n_cnt, n) A(nb_lap_cnt, n) A(nb_lap_col, sl)
     if (c->prm.pressure_mode == 0) {
-        A(nb_lap_col, sl) A(nb_lap_v64, sl)
-        if (c->prm.precision == 1) { A(nb_lap_v32, sl) }
+        if (c->prm.precision == 1) {
+            A(nb_lap_v32, sl) A(nb_lap_vlo, sl)
+            A(cg_r32, n) A(cg_d32, n) A(cg_q32, n) A(cg_x32, n) A(cg_xhl, n)
+        } else {
+            A(nb_lap_v64, sl)
+        }
         A(cg_r, n) A(cg_d, n) A(cg_q, n)
-        if (c->prm.precision == 1) { A(cg_r32, n) A(cg_d32, n) A(cg_q32, n) A(cg_x32, n) }
     }
     A(key, n) A(key_alt, n) A(perm, n) A(perm_alt, n)
     const int64_t tiles = ((int64_t)n + 2047) / 2048;
@@ -317,15 +324,17 @@ void stage_collect(Ctx* c, const bool* used) {
 int do_step(Ctx* c, bool advance, mps_report* rep) {
     const mps_params& P = c->prm;
     int rc;
-    bool used[MPS_NSTAGES] = {true, true, true, P.pressure_mode == 0, true};
+    bool used[MPS_NSTAGES] = {true, true, true, true, P.pressure_mode == 0, true};
     MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
     stage_begin(c, MPS_STAGE_BUCKET);
     if ((rc = bucket_build(c, true))) return rc;                   // 1
     stage_end(c, MPS_STAGE_BUCKET);
     launch_copy_state_star(c);
     MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, (size_t)c->n * sizeof(int32_t), c->stream));
-    stage_begin(c, MPS_STAGE_PREDICT);
+    stage_begin(c, MPS_STAGE_GATHER);
     launch_verlet(c);                                              // candidates at r^k
+    stage_end(c, MPS_STAGE_GATHER);
+    stage_begin(c, MPS_STAGE_PREDICT);
     launch_predict_rows(c);                                        // 2
     stage_end(c, MPS_STAGE_PREDICT);
     // per-slot outputs of the build; slots it does not visit (GHOST) keep these zeros
@@ -347,6 +356,9 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     rep->n_surface = s.n_surface;
     rep->n_ppe_rows = s.n_ppe;
     rep->max_disp = std::sqrt(bits_to_double(s.max_disp_bits));   // device keeps the square
+    rep->cand_tests = (int64_t)s.cand_tests;
+    rep->pairs_ppe = (int64_t)s.pairs_lap;
+    rep->pairs_pnd = (int64_t)s.pairs_n;
     rep->n0_pnd = c->n0_pnd;
     rep->n0_lap = c->n0_lap;
     rep->lambda = c->lambda;

@@ -88,6 +88,9 @@ __global__ void __launch_bounds__(BT)
         for (int ib = c0; ib < c1; ib += BT) {
             const int i = ib + threadIdx.x;
             const bool act = (i < c1) && op.active(i);
+            const int nact = __syncthreads_count(act);
+            if (threadIdx.x == 0 && nact)
+                atomicAdd(&((DevStatus*)st)->cand_tests, (unsigned long long)nact * (unsigned long long)ncand);
             typename Op::Center ctr;
             op.begin(i, act, ctr);
             for (int base = 0; base < ncand; base += CHUNK) {
@@ -118,9 +121,9 @@ __device__ __forceinline__ float dist2_f(const float4& a, const float4& b) {
 __device__ __forceinline__ int kind_of(const float4& q) { return __float_as_int(q.w) & 0xff; }
 
 // ------------------------------------------------------------------------------ Verlet
-// Candidate list of every non-ghost particle: all j != i with FP32 squared distance below
-// the candidate radius h^2 plus its rounding margin (a superset of the exact set within h),
-// written as SELL-32 rows.
+// Candidate list of every FLUID and WALL particle: all j != i with FP32 squared distance
+// below the candidate radius h^2 plus its rounding margin (a superset of the exact set
+// within h), written as SELL-32 rows.
 struct VerletOp {
     const float4* pos32;
     const int8_t* type;
@@ -134,7 +137,8 @@ struct VerletOp {
         float4 p32;
         int cnt;
     };
-    __device__ bool active(int i) const { return type[i] != kGhost; }
+    // DUMMY particles only ever appear as neighbours: they get no candidate list
+    __device__ bool active(int i) const { const int t = type[i]; return t == kFluid || t == kWall; }
     __device__ void begin(int i, bool act, Center& c) const {
         c.cnt = 0;
         if (act) c.p32 = pos32[i];
@@ -195,17 +199,23 @@ __global__ void k_copy_star(int n, const double4* pos, const double4* vel, const
     p32los[i] = pos32lo[i];
 }
 
+template <int BT, class Op>
+void launch_gather_bt(Ctx* c, const Op& op, int blocks_per_sm) {
+    constexpr int kChunk = 512;
+    k_gather<BT, kChunk, Op><<<c->sms * blocks_per_sm, BT, kChunk * sizeof(float4), c->stream>>>(
+        op, c->cell_start, c->occ, c->st, c->grid);
+}
+
 template <class Op>
 void launch_gather(Ctx* c, const Op& op) {
     c->launches += 1;
-    if (c->dim == 3) {
-        constexpr int kChunk = 512;
-        k_gather<96, kChunk, Op><<<c->sms * 16, 96, kChunk * sizeof(float4), c->stream>>>(
-            op, c->cell_start, c->occ, c->st, c->grid);
-    } else {
-        constexpr int kChunk = 512;
-        k_gather<32, kChunk, Op><<<c->sms * 32, 32, kChunk * sizeof(float4), c->stream>>>(
-            op, c->cell_start, c->occ, c->st, c->grid);
+    int bt = c->prm.gather_block;
+    if (bt == 0) bt = (c->dim == 3) ? 128 : 32;   // measured best on the 3D dam break
+    switch (bt) {
+        case 32: launch_gather_bt<32>(c, op, 24); break;
+        case 64: launch_gather_bt<64>(c, op, 20); break;
+        case 128: launch_gather_bt<128>(c, op, 12); break;
+        default: launch_gather_bt<96>(c, op, 16); break;
     }
 }
 

@@ -9,7 +9,8 @@
 //   vl              SELL-32 rows of `cap_v` int32 slots: candidates within h at r^k (superset)
 //   vel32           float4 velocities (mixed-precision viscosity terms)
 //   nb_lap          SELL-32 rows of `cap` int32 slots: non-dummy neighbours within re_lap at
-//                   r*, with FP64 (val64) and FP32 (val32) coefficients c_ij of the PPE
+//                   r*, with the PPE coefficients c_ij: binary64 (v64, FP64 mode) or
+//                   float-float hi/lo (v32/vlo, mixed mode; v32 is the FP32 coefficient)
 //   nb_n            SELL-32 rows of `cap_n` int32 slots: non-dummy neighbours within re_n at r*
 //   SELL-32: the rows of 32 consecutive slots form a slice; entry k of row i sits at
 //   ((i / 32) cap + k) 32 + i % 32, so a warp (one row per lane) reads entry k of its 32
@@ -44,6 +45,9 @@ struct DevStatus {
     unsigned int pad0;
     unsigned long long max_disp_bits;   // max squared FLUID displacement (bit pattern of a non-negative double)
     unsigned int counter[8];            // last-block-done tickets of grid reductions
+    unsigned long long cand_tests;      // candidate distance tests of the cell gather
+    unsigned long long pairs_lap;       // PPE coefficients evaluated (pairs within re_lap)
+    unsigned long long pairs_n;         // number-density terms evaluated (pairs within re_n)
 };
 
 // Scalars of one CG solve; updated by the last block of each reduction kernel.
@@ -173,8 +177,9 @@ struct Ctx {
     float* diag32;
     int32_t *vl_col, *vl_cnt;     // candidate (Verlet) lists at r^k, radius h
     int32_t *nb_lap_col, *nb_lap_cnt, *nb_n_col, *nb_n_cnt;
-    double* nb_lap_v64;
-    float* nb_lap_v32;
+    double* nb_lap_v64;     // FP64 mode: binary64 coefficients
+    float* nb_lap_v32;      // mixed mode: coefficient = v32 + vlo (float-float; v32 alone
+    float* nb_lap_vlo;      //   is the FP32 coefficient of the inner solve)
     double* phat;
     // bucket build
     uint32_t *key, *key_alt;
@@ -188,6 +193,7 @@ struct Ctx {
     // CG (FP64): x = p, r, d, q ; FP32: r32, d32, q32, x32
     double *cg_r, *cg_d, *cg_q;
     float *cg_r32, *cg_d32, *cg_q32, *cg_x32;
+    float2* cg_xhl;         // mixed: the FP64 iterate as float-float (hi, lo) for the outer residual
     double* partials;       // per-block partial sums
     CgScalars* cg;          // device
     DevStatus* st;          // device

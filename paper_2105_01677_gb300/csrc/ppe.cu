@@ -10,14 +10,16 @@
 //
 // FP64 mode: textbook CG in binary64 with stored FP64 coefficients; the recurrence residual
 // stops the iteration and the true residual b - A p is recomputed, restarting if needed.
-// Mixed mode: outer refinement in binary64 (r = b - A x with FP64 coefficients, x += e),
-// inner CG in FP32 on A e = r/|r| with FP32 coefficients (stored, or recomputed from the FP32
-// positions: matrix-free), FP64 dot products.
+// Mixed mode: outer refinement in binary64 (x and the residual b - A x in binary64, the
+// products of A x formed in float-float from float-float coefficients), inner CG in FP32 on
+// A e = r/|r| with FP32 coefficients (stored, or recomputed from the FP32 positions:
+// matrix-free), FP64 dot products.
 //
 // Reductions are deterministic: per-block partials summed in block order by the last block.
 // Convergence is decided on the device; the host polls one flag per chunk of iterations.
 #include <mutex>
 
+#include "ff.cuh"
 #include "mps_internal.cuh"
 
 namespace mps {
@@ -203,6 +205,7 @@ struct SellView {
     const int32_t* cnt;
     const double* v64;
     const float* v32;
+    const float* vlo;
     const double* diag;
     const float* diag32;
     const double* bvec;
@@ -248,14 +251,48 @@ __global__ void __launch_bounds__(kBT) k_resid64_t(SellView c, const double* x, 
     }
 }
 
+// mixed outer residual r = b - A x with A's coefficients as float-float (v32 + vlo) and
+// x as float-float (xh + xl) beside its binary64 value: each product and the row sum are
+// formed with error-free transformations on the FP32 pipes (~2^-46 relative per term), the
+// row result is combined with b and the diagonal in binary64.
+__global__ void __launch_bounds__(kBT) k_resid_ff_t(SellView c, const double* x, const float2* xhl,
+                                                    double* r, CgScalars* cg) {
+    __shared__ double sm[kWarps];
+    double part = 0.0;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT) {
+        const double dg = c.diag[i];
+        double ri = 0.0;
+        if (dg != 0.0) {
+            const int cnt = c.cnt[i];
+            ff acc = {0.f, 0.f};
+            for (int k = 0; k < cnt; k++) {
+                const size_t q = sell(i, k, c.cap);
+                const int j = c.col[q];
+                const float ch = c.v32[q], cl = c.vlo[q];
+                const float2 y = xhl[j];
+                ff p = ff_two_prod(ch, y.x);
+                p.l = fmaf(ch, y.y, fmaf(cl, y.x, p.l));
+                acc = ff_add(acc, p);
+            }
+            ri = c.bvec[i] - (dg * x[i] - ff_to_double_fast(acc));
+        }
+        r[i] = ri;
+        part = fma(ri, ri, part);
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, c.partials, &c.counter[0], &tot, sm) && threadIdx.x == 0) cg->rr = tot;
+}
+
 // start of a solve from x = 0: x = 0, r = b, d = b, rr = rho = b.b, stop2 = tol2 b.b
 __global__ void __launch_bounds__(kBT) k_start64(SellView c, double* x, double* r, double* d,
-                                                 CgScalars* cg, double tol2) {
+                                                 CgScalars* cg, double tol2, float2* xhl) {
     __shared__ double sm[kWarps];
     double part = 0.0;
     for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT) {
         const double bi = c.bvec[i];
         x[i] = 0.0;
+        if (xhl) xhl[i] = make_float2(0.f, 0.f);
         r[i] = bi;
         d[i] = bi;
         part = fma(bi, bi, part);
@@ -333,10 +370,17 @@ __global__ void __launch_bounds__(kBT) k_spmv32_t(SellView c, const float* d, fl
     }
 }
 
-// x64 += |r64| x32   (|r64| = sqrt(rr) of the residual that started the inner solve)
-__global__ void __launch_bounds__(kBT) k_outer_update(int n, double* x, const float* e, double scale_rr) {
+// x64 += |r64| x32   (|r64| = sqrt(rr) of the residual that started the inner solve); the
+// float-float copy of x for the next outer residual is refreshed at the same time
+__global__ void __launch_bounds__(kBT) k_outer_update(int n, double* x, const float* e, double scale_rr,
+                                                      float2* xhl) {
     const double s = sqrt(scale_rr);
-    for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) x[i] = fma(s, (double)e[i], x[i]);
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) {
+        const double v = fma(s, (double)e[i], x[i]);
+        x[i] = v;
+        const float h = (float)v;
+        xhl[i] = make_float2(h, (float)(v - (double)h));
+    }
 }
 
 __global__ void k_clear_x(int n, double* x) {
@@ -353,6 +397,7 @@ static SellView sell_view(Ctx* c) {
     v.cnt = c->nb_lap_cnt;
     v.v64 = c->nb_lap_v64;
     v.v32 = c->nb_lap_v32;
+    v.vlo = c->nb_lap_vlo;
     v.diag = c->diag;
     v.diag32 = c->diag32;
     v.bvec = c->bvec;
@@ -414,7 +459,7 @@ int ppe_solve(Ctx* c, mps_report* rep) {
     int rc;
     if ((rc = set_cg_limits(c, max_total))) return rc;
     // x = 0, r = b, d = b, rho = |b|^2, stop2 = tol^2 |b|^2
-    k_start64<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2);
+    k_start64<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2, c->cg_xhl);
     c->launches += 1;
     if ((rc = read_scalars(c))) return rc;
     const double bnorm2 = c->cg_host->rr;
@@ -473,8 +518,8 @@ int ppe_solve(Ctx* c, mps_report* rep) {
                 chunk = std::max(4, chunk / 2);
             }
             total_iters += c->cg_host->iters;
-            k_outer_update<<<gv, kBT, 0, c->stream>>>(n, c->p, c->cg_x32, rr);
-            k_resid64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_r, nullptr, c->cg, tol2, 0, 0);
+            k_outer_update<<<gv, kBT, 0, c->stream>>>(n, c->p, c->cg_x32, rr, c->cg_xhl);
+            k_resid_ff_t<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_xhl, c->cg_r, c->cg);
             if ((rc = read_scalars(c))) return rc;
             rr = c->cg_host->rr;
             outer++;

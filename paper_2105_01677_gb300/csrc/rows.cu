@@ -16,13 +16,13 @@
 //
 //   predict (r^k, re_lap, FLUID):  u* = u + dt (nu lap(u) + g)  (Eq. 2 without the pressure
 //            term; lap by Eq. 7), r* = r + dt u*.
-//   build   (r*, every non-ghost particle):  n* (Eq. 5, re_n, every kind), free surface
+//   build   (r*, FLUID and WALL particles):  n* (Eq. 5, re_n, neighbours of every kind), free surface
 //            (Eq. 15), PPE row: b (Eq. 13), c_ij = 2d/(n0 lambda rho) w (non-dummy j within
 //            re_lap; PPE listing (Listing 2) of Sec. 4.3), diagonal sum c_ij + alpha_c/dt^2,
 //            neighbour lists for the PPE and the gradient (non-dummy j within re_n), and the
 //            equation-of-state pressure (Eq. 16).
 // Precision: FP64 mode evaluates pair terms in binary64; mixed mode evaluates the viscosity
-// terms in FP32 (summed in float-float, stored in binary64) and the number density
+// terms in FP32 (compensated FP32 sums, stored in binary64) and the number density
 // and PPE coefficients in float-float (relative error ~1e-13), accumulated in float-float
 // and stored in binary64.
 #include "ff.cuh"
@@ -53,6 +53,14 @@ __device__ __forceinline__ bool decide_band(const ff& r2, const Radius& r, const
     if (d <= -r.ff_tol) return true;
     if (d >= r.ff_tol) return false;
     return exact_dist2(pi, pos[j]) < r.re2;
+}
+
+// compensated summation (Kahan): s + (-e) carries the sum to about twice FP32 precision
+__device__ __forceinline__ void kahan_add(float& s, float& e, float v) {
+    const float y = v - e;
+    const float t = s + y;
+    e = (t - s) - y;
+    s = t;
 }
 
 // 1 inside, 0 outside, from the FP32 distance; 2: needs the finer tiers
@@ -90,7 +98,8 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
         const float4 u32 = a.vel32[i];
         const int cnt = a.vcnt[i];
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        ff f0 = {0.f, 0.f}, f1 = {0.f, 0.f}, f2 = {0.f, 0.f};   // FP32 terms, float-float sums
+        // FP32 terms in compensated (Kahan) FP32 sums: value f, running correction e
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f;
         // two-stage software pipeline: the slot of k+2 and the position of k+1 are in flight
         int jn = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : 0;
         int j0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
@@ -112,9 +121,9 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
                 }
                 const float w = fmaf(a.r.re_f, rsqrtf(r2), -1.f);
                 const float4 uj = a.vel32[j];
-                f0 = ff_add_f(f0, (uj.x - u32.x) * w);
-                f1 = ff_add_f(f1, (uj.y - u32.y) * w);
-                f2 = ff_add_f(f2, (uj.z - u32.z) * w);
+                kahan_add(f0, e0, (uj.x - u32.x) * w);
+                kahan_add(f1, e1, (uj.y - u32.y) * w);
+                kahan_add(f2, e2, (uj.z - u32.z) * w);
             } else {
                 const double4 pj = a.pos[j];
                 const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
@@ -131,9 +140,9 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
             }
         }
         if (MIXED) {
-            s0 = ff_to_double_fast(f0);
-            s1 = ff_to_double_fast(f1);
-            s2 = ff_to_double_fast(f2);
+            s0 = ff_to_double_fast({f0, -e0});
+            s1 = ff_to_double_fast({f1, -e1});
+            s2 = ff_to_double_fast({f2, -e2});
         }
         // u* = u + dt (nu lap(u) + g); r* = r + dt u*  (one rounding per operation)
         const double l0 = a.coef_lap * s0, l1 = a.coef_lap * s1, l2 = a.coef_lap * s2;
@@ -181,8 +190,9 @@ struct BuildArgs {
     double coef_ppe, n0, beta, inv_dt2, diag_add, wc_k, gamma;
     ff cre_ff, ncoef_ff;   // coef_ppe * re_lap and -coef_ppe as float-float
     int32_t* lap_col;
-    double* lap_v64;
-    float* lap_v32;
+    double* lap_v64;   // FP64 mode
+    float* lap_v32;    // mixed mode: hi part (the FP32 coefficient)
+    float* lap_vlo;    // mixed mode: lo part
     int32_t* lap_cnt;
     int32_t* n_col;
     int32_t* n_cnt;
@@ -194,19 +204,31 @@ struct BuildArgs {
     double* p;
 };
 
+// Entry flags while a PPE row is being assembled (slots are < 2^30)
+constexpr int kEntryN = 1 << 30;   // within re_n: contributes to n*
+constexpr int kEntryL = 1 << 29;   // non-dummy within re_lap: a PPE coefficient
+constexpr int kSlotMask = kEntryL - 1;
+
+// Two passes per row.  Classification walks the candidate list, decides the predicates
+// (FP32 / float-float / binary64 tiers) and writes the hits into the row's PPE slots: the
+// entries within re_n from the front, PPE-only entries from the back.  The dense pass then
+// evaluates every hit with (nearly) all lanes of the warp busy, accumulates n* and the
+// diagonal, and compacts the PPE coefficients in place to the front of the row.
 template <bool MIXED>
 __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
     const int i = blockIdx.x * kBT + threadIdx.x;
     bool surf = false, ppe = false;
-    if (i < a.n && a.type[i] != kGhost) {
-        const int ti = a.type[i];
-        const bool rows = (ti == kFluid || ti == kWall);
+    unsigned n_lap = 0, n_pnd = 0;   // pairs evaluated by this row
+    // FLUID and WALL rows only: a DUMMY particle's own n* enters no equation (no free-surface
+    // test, no PPE row, no gradient), so it is not evaluated (reported as 0)
+    if (i < a.n && (a.type[i] == kFluid || a.type[i] == kWall)) {
         const float4 ih = a.pos32[i], il = a.pos32lo[i];
         const double4 pi = a.pos[i];
         const int cnt = a.vcnt[i];
-        double nd = 0.0, dg = 0.0;
-        ff ndf = {0.f, 0.f}, dgf = {0.f, 0.f};
-        int out_l = 0, out_n = 0;
+        const bool with_ppe = (a.pressure_mode == 0);
+        int m_f = 0, m_b = 0, out_n = 0;
+        bool overflow = false;
+        // ---- classification
         int jn = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : 0;
         int j0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
         float4 qn = a.pos32[j0];
@@ -217,40 +239,59 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
             if (k + 1 < cnt) qn = a.pos32[jn];
             if (k + 2 < cnt) jn = a.vcol[sell(i, k + 2, a.cap_v)];
             const float r2 = dist2_f(ih, jh);
-            const bool nb_ok = rows && kind_of(jh) != kDummy;
-            // PPE rows exist only on the PPE path
-            int tl = (nb_ok && a.pressure_mode == 0) ? tier1(r2, a.rl) : 0;
+            const bool nb_ok = kind_of(jh) != kDummy;
+            int tl = (nb_ok && with_ppe) ? tier1(r2, a.rl) : 0;
             int tn = tier1(r2, a.rn);
             if (!tl && !tn) continue;
-            const bool band = (tl == 2 || tn == 2);
-            ff r2f;
-            if (MIXED || band) r2f = pair_r2(ih, il, jh, a.pos32lo[j]);
-            if (tl == 2) tl = decide_band(r2f, a.rl, a.pos, pi, j) ? 1 : 0;
-            if (tn == 2) tn = decide_band(r2f, a.rn, a.pos, pi, j) ? 1 : 0;
-            if (!tl && !tn) continue;
+            if (tl == 2 || tn == 2) {
+                const ff r2f = pair_r2(ih, il, jh, a.pos32lo[j]);
+                if (tl == 2) tl = decide_band(r2f, a.rl, a.pos, pi, j) ? 1 : 0;
+                if (tn == 2) tn = decide_band(r2f, a.rn, a.pos, pi, j) ? 1 : 0;
+                if (!tl && !tn) continue;
+            }
+            if (tn && nb_ok) {
+                if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j;
+                out_n++;
+            }
+            if (m_f + m_b >= a.cap) {
+                overflow = true;
+                continue;
+            }
+            if (tn) a.lap_col[sell(i, m_f++, a.cap)] = j | kEntryN | (tl ? kEntryL : 0);
+            else a.lap_col[sell(i, a.cap - 1 - m_b++, a.cap)] = j | kEntryL;
+        }
+        // ---- dense evaluation and in-place compaction (write slot <= read slot)
+        double nd = 0.0, dg = 0.0;
+        ff ndf = {0.f, 0.f}, dgf = {0.f, 0.f};
+        int out_l = 0;
+        const int m_all = m_f + m_b;
+        for (int t = 0; t < m_all; t++) {
+            const int k = t < m_f ? t : a.cap - m_b + (t - m_f);
+            const size_t qk = sell(i, k, a.cap);
+            const int e = a.lap_col[qk];
+            const int j = e & kSlotMask;
+            const bool tn = (e & kEntryN) != 0, tl = (e & kEntryL) != 0;
+            double cd = 0.0;
+            ff cf = {0.f, 0.f};
+            bool ok = true;
             if (MIXED) {
+                const ff r2f = pair_r2(ih, il, a.pos32[j], a.pos32lo[j]);
                 if (!(r2f.h > 0.f)) {
                     if (!(exact_dist2(pi, a.pos[j]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
-                    continue;
-                }
-                // 1/r: one Newton step (~1e-13) serves the PPE coefficient; the number density
-                // takes a second (~1e-15) so that n* stays far inside the flag band
-                ff y = ff_rsqrt1(r2f);
-                if (tn) {
-                    y = ff_rsqrt_step(r2f, y);
-                    ndf = ff_add(ndf, ff_add_f(ff_mul({a.rn.re_f, a.rn.re_l}, y), -1.f));
-                }
-                if (tl) {
-                    // c = coef (re/r - 1) = (coef re) y - coef
-                    const ff c = ff_add(ff_mul(a.cre_ff, y), a.ncoef_ff);
-                    dgf = ff_add(dgf, c);
-                    if (out_l < a.cap) {
-                        const size_t q = sell(i, out_l, a.cap);
-                        a.lap_col[q] = j;
-                        a.lap_v64[q] = ff_to_double_fast(c);
-                        if (a.lap_v32) a.lap_v32[q] = c.h + c.l;
+                    ok = false;
+                } else {
+                    // 1/r: one Newton step (~1e-13) serves the PPE coefficient; n* takes a
+                    // second (~1e-15) so that it stays far inside the flag band
+                    ff y = ff_rsqrt1(r2f);
+                    if (tn) {
+                        y = ff_rsqrt_step(r2f, y);
+                        ndf = ff_add(ndf, ff_add_f(ff_mul({a.rn.re_f, a.rn.re_l}, y), -1.f));
                     }
-                    out_l++;
+                    if (tl) {
+                        // c = coef (re/r - 1) = (coef re) y - coef
+                        cf = ff_add(ff_mul(a.cre_ff, y), a.ncoef_ff);
+                        dgf = ff_add(dgf, cf);
+                    }
                 }
             } else {
                 const double4 pj = a.pos[j];
@@ -258,48 +299,57 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                 const double rr2 = fma(dz, dz, fma(dy, dy, dx * dx));
                 if (!(rr2 > 0.0)) {
                     atomicOr(&a.st->err, kErrCoincident);
-                    continue;
-                }
-                const double rs = rsqrt(rr2);
-                if (tn) nd += fma(a.rn.re, rs, -1.0);
-                if (tl) {
-                    const double c = a.coef_ppe * fma(a.rl.re, rs, -1.0);
-                    dg += c;
-                    if (out_l < a.cap) {
-                        const size_t q = sell(i, out_l, a.cap);
-                        a.lap_col[q] = j;
-                        a.lap_v64[q] = c;
-                        if (a.lap_v32) a.lap_v32[q] = (float)c;
+                    ok = false;
+                } else {
+                    const double rs = rsqrt(rr2);
+                    if (tn) nd += fma(a.rn.re, rs, -1.0);
+                    if (tl) {
+                        cd = a.coef_ppe * fma(a.rl.re, rs, -1.0);
+                        dg += cd;
                     }
-                    out_l++;
                 }
             }
-            if (tn && nb_ok) {
-                if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j;
-                out_n++;
+            if (ok && tl) {
+                const size_t q = sell(i, out_l, a.cap);
+                a.lap_col[q] = j;
+                if (MIXED) {
+                    a.lap_v32[q] = cf.h;
+                    a.lap_vlo[q] = cf.l;
+                } else {
+                    a.lap_v64[q] = cd;
+                }
+                out_l++;
             }
         }
         if (MIXED) {
             nd = ff_to_double_fast(ndf);
             dg = ff_to_double_fast(dgf);
         }
-        surf = rows && (nd < a.beta * a.n0);
-        ppe = rows && !surf;
+        surf = nd < a.beta * a.n0;
+        ppe = !surf;
         a.nstar[i] = nd;
         a.flag[i] = surf ? 1 : 0;
         a.bvec[i] = ppe ? a.inv_dt2 * ((nd - a.n0) / a.n0) : 0.0;
         const double dgv = ppe ? dg + a.diag_add : 0.0;
         a.diag[i] = dgv;
         a.diag32[i] = (float)dgv;
-        a.lap_cnt[i] = min(out_l, a.cap);
+        a.lap_cnt[i] = out_l;
         a.n_cnt[i] = min(out_n, a.cap_n);
-        if (out_l > a.cap || out_n > a.cap_n) atomicOr(&a.st->err, kErrCap);
+        if (overflow || out_n > a.cap_n) atomicOr(&a.st->err, kErrCap);
         if (a.pressure_mode == 1) a.p[i] = ppe ? a.wc_k * (pow(nd / a.n0, a.gamma) - 1.0) : 0.0;
+        n_lap = (unsigned)out_l;
+        n_pnd = (unsigned)m_f;
     }
     const unsigned bs = __ballot_sync(0xffffffffu, surf), bp = __ballot_sync(0xffffffffu, ppe);
+    for (int o = 16; o > 0; o >>= 1) {
+        n_lap += __shfl_xor_sync(0xffffffffu, n_lap, o);
+        n_pnd += __shfl_xor_sync(0xffffffffu, n_pnd, o);
+    }
     if ((threadIdx.x & 31) == 0) {
         if (bs) atomicAdd(&a.st->n_surface, (unsigned)__popc(bs));
         if (bp) atomicAdd(&a.st->n_ppe, (unsigned)__popc(bp));
+        if (n_lap) atomicAdd(&a.st->pairs_lap, (unsigned long long)n_lap);
+        if (n_pnd) atomicAdd(&a.st->pairs_n, (unsigned long long)n_pnd);
     }
 }
 }  // namespace
@@ -367,6 +417,7 @@ void launch_build_rows(Ctx* c) {
     a.lap_col = c->nb_lap_col;
     a.lap_v64 = c->nb_lap_v64;
     a.lap_v32 = c->nb_lap_v32;
+    a.lap_vlo = c->nb_lap_vlo;
     a.lap_cnt = c->nb_lap_cnt;
     a.n_col = c->nb_n_col;
     a.n_cnt = c->nb_n_cnt;

@@ -35,7 +35,7 @@ class mps_params(C.Structure):
                 ("nbr_cap", C.c_int32), ("cell_skin", C.c_double),
                 ("box_min", C.c_double * 3), ("box_max", C.c_double * 3),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32),
-                ("ppe_operator", C.c_int32), ("device", C.c_int32), ("reserved0", C.c_int32),
+                ("ppe_operator", C.c_int32), ("device", C.c_int32), ("gather_block", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
                 ("alloc_user", C.c_void_p)]
 
@@ -45,7 +45,8 @@ class mps_report(C.Structure):
                 ("reserved0", C.c_int32), ("cg_resid", C.c_double), ("n_surface", C.c_int64),
                 ("n_ghost", C.c_int64), ("n_ppe_rows", C.c_int64), ("max_disp", C.c_double),
                 ("n0_pnd", C.c_double), ("n0_lap", C.c_double), ("lambda_", C.c_double),
-                ("steps_done", C.c_int64)]
+                ("steps_done", C.c_int64), ("cand_tests", C.c_int64), ("pairs_ppe", C.c_int64),
+                ("pairs_pnd", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved0"}
@@ -58,7 +59,7 @@ EXPORTS = ("mps_params_default", "mps_create", "mps_step", "mps_solve_ppe", "mps
            "mps_set_profiling", "mps_get_profile", "mps_ppe_cg_noalloc", "mps_destroy",
            "mps_strerror")
 NOALLOC_MAX_ROWS = 262144
-STAGES = ("bucket", "predict", "build", "ppe", "update")
+STAGES = ("bucket", "gather", "predict", "build", "ppe", "update")
 
 _lib = None
 
