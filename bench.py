@@ -361,7 +361,7 @@ def run_gb300(args):
                                            if prof64["stage_calls"][k] else 0.0)
                                        for k in prof64["stage_ms"]}},
         "mixed_over_fp64": value / value64,
-        "cg": {"inner_iters_mean": iters_mean, "outer_mean": outer_mean,
+        "cg": {"inner_iters_mean": inner, "outer_mean": outer,
                "resid_max": float(max(x[2] for x in it_mixed))},
         "e2e": {"value": world * n * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
