@@ -3,9 +3,9 @@
 //
 // One thread block per occupied cell; each thread owns one particle of that cell.  The
 // 3^d surrounding cells' particles are staged in shared memory per cell (FP32 positions
-// relative to the grid origin, the slot in the fourth lane), and every thread walks the same
-// staged candidates, so the shared-memory reads are broadcasts and the rare FP64 loads of a
-// candidate are warp-uniform.
+// relative to the grid origin and slots, as separate arrays), and every thread walks the
+// same staged candidates, two at a time with packed FP32x2 arithmetic, so the shared-memory
+// reads are broadcasts and the rare FP64 loads of a candidate are warp-uniform.
 //
 // Distance predicate of the exact sets: a candidate is classified from its FP32 squared
 // distance against a band [lo, hi) around re^2 that bounds the FP32 rounding error; only
@@ -33,7 +33,12 @@ template <int BT, int CHUNK, class Op>
 __global__ void __launch_bounds__(BT)
     k_gather(Op op, const int32_t* __restrict__ cell_start, const uint32_t* __restrict__ occ,
              const DevStatus* st, GridDesc g) {
-    extern __shared__ float4 s_q[];   // CHUNK entries
+    // staged candidates, structure of arrays: x, y, z relative to the grid origin, slot
+    extern __shared__ float s_buf[];
+    float* s_x = s_buf;
+    float* s_y = s_buf + CHUNK;
+    float* s_z = s_buf + 2 * CHUNK;
+    int* s_j = (int*)(s_buf + 3 * CHUNK);
     __shared__ int s_cs[27], s_pref[28];
     __shared__ int s_nc;
     const unsigned n_occ = *(volatile const unsigned*)&st->n_occ;
@@ -75,9 +80,11 @@ __global__ void __launch_bounds__(BT)
                 const int a = max(s_pref[m], base), b = min(s_pref[m + 1], base + len);
                 const int off = s_cs[m] - s_pref[m];
                 for (int f = a + (int)threadIdx.x; f < b; f += BT) {
-                    float4 q = op.pos32[f + off];
-                    q.w = __int_as_float(f + off);
-                    s_q[f - base] = q;
+                    const float4 q = op.pos32[f + off];
+                    s_x[f - base] = q.x;
+                    s_y[f - base] = q.y;
+                    s_z[f - base] = q.z;
+                    s_j[f - base] = f + off;
                 }
             }
         };
@@ -101,11 +108,12 @@ __global__ void __launch_bounds__(BT)
                     __syncthreads();
                 }
                 if (act) {
-#pragma unroll 4
-                    for (int k = 0; k < len; k++) {
-                        const float4 q = s_q[k];
-                        op.visit(ctr, i, __float_as_int(q.w), q);
-                    }
+                    int k = 0;
+#pragma unroll 2
+                    for (; k + 1 < len; k += 2)
+                        op.visit2(ctr, i, *(const float2*)&s_x[k], *(const float2*)&s_y[k],
+                                  *(const float2*)&s_z[k], *(const int2*)&s_j[k]);
+                    if (k < len) op.visit(ctr, i, s_j[k], make_float4(s_x[k], s_y[k], s_z[k], 0.f));
                 }
             }
             op.finish(i, act, ctr);
@@ -136,17 +144,31 @@ struct VerletOp {
     struct Center {
         float4 p32;
         int cnt;
+        int32_t* row;   // entry k of this row at row[32 k] (SELL-32)
     };
     // DUMMY particles only ever appear as neighbours: they get no candidate list
     __device__ bool active(int i) const { const int t = type[i]; return t == kFluid || t == kWall; }
     __device__ void begin(int i, bool act, Center& c) const {
         c.cnt = 0;
+        c.row = vcol + sell(i, 0, cap_v);
         if (act) c.p32 = pos32[i];
+    }
+    __device__ __forceinline__ void push(Center& c, int j) const {
+        if (c.cnt < cap_v) c.row[(size_t)c.cnt * 32] = j;
+        c.cnt++;
     }
     __device__ void visit(Center& c, int i, int j, const float4& q) const {
         if (j == i || dist2_f(c.p32, q) >= hv2) return;
-        if (c.cnt < cap_v) vcol[sell(i, c.cnt, cap_v)] = j;
-        c.cnt++;
+        push(c, j);
+    }
+    // two candidates with packed FP32x2 arithmetic; same rounding as visit()
+    __device__ void visit2(Center& c, int i, float2 x, float2 y, float2 z, int2 j) const {
+        const float2 dx = __fadd2_rn(x, make_float2(-c.p32.x, -c.p32.x));
+        const float2 dy = __fadd2_rn(y, make_float2(-c.p32.y, -c.p32.y));
+        const float2 dz = __fadd2_rn(z, make_float2(-c.p32.z, -c.p32.z));
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        if (r2.x < hv2 && j.x != i) push(c, j.x);
+        if (r2.y < hv2 && j.y != i) push(c, j.y);
     }
     __device__ void finish(int i, bool act, const Center& c) const {
         if (!act) return;
@@ -183,6 +205,10 @@ struct NbrOp {
         if (row_off) out_ids[row_off[i] + c.cnt] = id[j];
         c.cnt++;
     }
+    __device__ void visit2(Center& c, int i, float2 x, float2 y, float2 z, int2 j) const {
+        visit(c, i, j.x, make_float4(x.x, y.x, z.x, 0.f));
+        visit(c, i, j.y, make_float4(x.y, y.y, z.y, 0.f));
+    }
     __device__ void finish(int i, bool act, const Center& c) const {
         if (act && !row_off) out_cnt[i] = c.cnt;
     }
@@ -202,7 +228,7 @@ __global__ void k_copy_star(int n, const double4* pos, const double4* vel, const
 template <int BT, class Op>
 void launch_gather_bt(Ctx* c, const Op& op, int blocks_per_sm) {
     constexpr int kChunk = 512;
-    k_gather<BT, kChunk, Op><<<c->sms * blocks_per_sm, BT, kChunk * sizeof(float4), c->stream>>>(
+    k_gather<BT, kChunk, Op><<<c->sms * blocks_per_sm, BT, kChunk * 4 * sizeof(float), c->stream>>>(
         op, c->cell_start, c->occ, c->st, c->grid);
 }
 
