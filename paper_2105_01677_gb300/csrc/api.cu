@@ -183,6 +183,10 @@ int setup(Ctx* c) {
         c->cap_v = round_up(std::max((int)std::ceil(1.5 * cnt_h),
                                      (int)std::ceil((double)c->cap * cnt_h / std::max(cnt_l, 1))), 32);
     }
+    // at least one SELL slot group per list (a radius below l0 has no lattice neighbours)
+    c->cap = std::max(c->cap, 32);
+    c->cap_n = std::max(c->cap_n, 32);
+    c->cap_v = std::max(c->cap_v, 32);
     // grid
     const double re_max = std::max(P.re_n, P.re_lap);
     c->h = re_max * (1.0 + P.cell_skin);

@@ -26,15 +26,15 @@ namespace {
 
 // One block per occupied cell, one thread per particle of the cell.  The particles of the
 // 3^d surrounding cells (contiguous slot ranges in Morton order) are staged once in shared
-// memory as (x, y, z, slot) and every thread walks the same staged candidates, so each read
-// is a shared-memory broadcast; one barrier pair per cell (more only when a cell's
+// memory as (x, y, z, slot) and every thread walks the same staged candidates, four per
+// shared-memory load, so each read is a broadcast; one barrier pair per cell (more only when a cell's
 // neighbourhood exceeds CHUNK candidates).
 template <int BT, int CHUNK, class Op>
 __global__ void __launch_bounds__(BT)
     k_gather(Op op, const int32_t* __restrict__ cell_start, const uint32_t* __restrict__ occ,
              const DevStatus* st, GridDesc g) {
     // staged candidates, structure of arrays: x, y, z relative to the grid origin, slot
-    extern __shared__ float s_buf[];
+    extern __shared__ __align__(16) float s_buf[];
     float* s_x = s_buf;
     float* s_y = s_buf + CHUNK;
     float* s_z = s_buf + 2 * CHUNK;
@@ -75,6 +75,8 @@ __global__ void __launch_bounds__(BT)
         const int ncells = s_nc;
         const bool once = ncand <= CHUNK;   // whole neighbourhood staged once for the cell
         // copy candidates [base, base + len) cell by cell (coalesced slot ranges)
+        // (padded with up to three sentinels at infinity, so that the walk below reads four
+        // candidates per shared-memory load and needs no tail)
         auto stage = [&](int base, int len) {
             for (int m = 0; m < ncells; m++) {
                 const int a = max(s_pref[m], base), b = min(s_pref[m + 1], base + len);
@@ -86,6 +88,13 @@ __global__ void __launch_bounds__(BT)
                     s_z[f - base] = q.z;
                     s_j[f - base] = f + off;
                 }
+            }
+            const int pad = len + (int)threadIdx.x;
+            if (pad < ((len + 3) & ~3)) {
+                s_x[pad] = __int_as_float(0x7f800000);
+                s_y[pad] = 0.f;
+                s_z[pad] = 0.f;
+                s_j[pad] = -1;
             }
         };
         if (once) {
@@ -108,12 +117,15 @@ __global__ void __launch_bounds__(BT)
                     __syncthreads();
                 }
                 if (act) {
-                    int k = 0;
-#pragma unroll 2
-                    for (; k + 1 < len; k += 2)
-                        op.visit2(ctr, i, *(const float2*)&s_x[k], *(const float2*)&s_y[k],
-                                  *(const float2*)&s_z[k], *(const int2*)&s_j[k]);
-                    if (k < len) op.visit(ctr, i, s_j[k], make_float4(s_x[k], s_y[k], s_z[k], 0.f));
+                    for (int k = 0; k < len; k += 4) {
+                        const float4 x4 = *(const float4*)&s_x[k], y4 = *(const float4*)&s_y[k];
+                        const float4 z4 = *(const float4*)&s_z[k];
+                        const int4 j4 = *(const int4*)&s_j[k];
+                        op.visit2(ctr, i, make_float2(x4.x, x4.y), make_float2(y4.x, y4.y),
+                                  make_float2(z4.x, z4.y), make_int2(j4.x, j4.y));
+                        op.visit2(ctr, i, make_float2(x4.z, x4.w), make_float2(y4.z, y4.w),
+                                  make_float2(z4.z, z4.w), make_int2(j4.z, j4.w));
+                    }
                 }
             }
             op.finish(i, act, ctr);
@@ -153,22 +165,24 @@ struct VerletOp {
         c.row = vcol + sell(i, 0, cap_v);
         if (act) c.p32 = pos32[i];
     }
-    __device__ __forceinline__ void push(Center& c, int j) const {
-        if (c.cnt < cap_v) c.row[(size_t)c.cnt * 32] = j;
-        c.cnt++;
+    // Branch-free append: a predicated store into the row's next slot.  Past the cap every
+    // hit rewrites the last slot (the row is then reported as overflowed by finish()).
+    __device__ __forceinline__ void push(Center& c, bool hit, int j) const {
+        int32_t* dst = c.row + (size_t)min(c.cnt, cap_v - 1) * 32;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.global.u32 [%0], %1;\n\t}"
+            :: "l"(dst), "r"(j), "r"((unsigned)hit));
+        c.cnt += hit ? 1 : 0;
     }
-    __device__ void visit(Center& c, int i, int j, const float4& q) const {
-        if (j == i || dist2_f(c.p32, q) >= hv2) return;
-        push(c, j);
-    }
-    // two candidates with packed FP32x2 arithmetic; same rounding as visit()
-    __device__ void visit2(Center& c, int i, float2 x, float2 y, float2 z, int2 j) const {
+    // two candidates with packed FP32x2 arithmetic (each lane of the pair rounds like the
+    // scalar dx*dx + dy*dy + dz*dz with fused multiply-adds)
+    __device__ __forceinline__ void visit2(Center& c, int i, float2 x, float2 y, float2 z, int2 j) const {
         const float2 dx = __fadd2_rn(x, make_float2(-c.p32.x, -c.p32.x));
         const float2 dy = __fadd2_rn(y, make_float2(-c.p32.y, -c.p32.y));
         const float2 dz = __fadd2_rn(z, make_float2(-c.p32.z, -c.p32.z));
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        if (r2.x < hv2 && j.x != i) push(c, j.x);
-        if (r2.y < hv2 && j.y != i) push(c, j.y);
+        push(c, r2.x < hv2 && j.x != i, j.x);
+        push(c, r2.y < hv2 && j.y != i, j.y);
     }
     __device__ void finish(int i, bool act, const Center& c) const {
         if (!act) return;
@@ -206,8 +220,8 @@ struct NbrOp {
         c.cnt++;
     }
     __device__ void visit2(Center& c, int i, float2 x, float2 y, float2 z, int2 j) const {
-        visit(c, i, j.x, make_float4(x.x, y.x, z.x, 0.f));
-        visit(c, i, j.y, make_float4(x.y, y.y, z.y, 0.f));
+        if (j.x >= 0) visit(c, i, j.x, make_float4(x.x, y.x, z.x, 0.f));
+        if (j.y >= 0) visit(c, i, j.y, make_float4(x.y, y.y, z.y, 0.f));
     }
     __device__ void finish(int i, bool act, const Center& c) const {
         if (act && !row_off) out_cnt[i] = c.cnt;

@@ -224,6 +224,35 @@ __device__ __forceinline__ double sell_dot64(const SellView& c, int i, const dou
     return acc;
 }
 
+// sum_k v_k x_{col_k} over one SELL-32 row (entry k at offset 32 k), in entry order; the
+// loads of eight entries are issued before their products so that each thread keeps
+// several independent gathers in flight
+__device__ __forceinline__ float sell_dot32(const int32_t* __restrict__ cp, const float* __restrict__ vp,
+                                            int cnt, const float* __restrict__ x) {
+    float acc = 0.f;
+    int k = 0;
+    for (; k + 8 <= cnt; k += 8) {
+        int j[8];
+        float v[8], y[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) j[u] = cp[32 * u];
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = vp[32 * u];
+#pragma unroll
+        for (int u = 0; u < 8; u++) y[u] = x[j[u]];
+#pragma unroll
+        for (int u = 0; u < 8; u++) acc = fmaf(v[u], y[u], acc);
+        cp += 256;
+        vp += 256;
+    }
+    for (; k < cnt; k++) {
+        acc = fmaf(*vp, x[*cp], acc);
+        cp += 32;
+        vp += 32;
+    }
+    return acc;
+}
+
 // r = b - A x, d = r (if d); rr = r.r
 __global__ void __launch_bounds__(kBT) k_resid64_t(SellView c, const double* x, double* r,
                                                    double* d, CgScalars* cg, double tol2,
@@ -265,14 +294,39 @@ __global__ void __launch_bounds__(kBT) k_resid_ff_t(SellView c, const double* x,
         if (dg != 0.0) {
             const int cnt = c.cnt[i];
             ff acc = {0.f, 0.f};
-            for (int k = 0; k < cnt; k++) {
-                const size_t q = sell(i, k, c.cap);
-                const int j = c.col[q];
-                const float ch = c.v32[q], cl = c.vlo[q];
-                const float2 y = xhl[j];
+            const size_t q0 = sell(i, 0, c.cap);
+            const int32_t* cp = c.col + q0;
+            const float* hp = c.v32 + q0;
+            const float* lp = c.vlo + q0;
+            auto term = [&](float ch, float cl, float2 y) {
                 ff p = ff_two_prod(ch, y.x);
                 p.l = fmaf(ch, y.y, fmaf(cl, y.x, p.l));
                 acc = ff_add(acc, p);
+            };
+            int k = 0;
+            for (; k + 4 <= cnt; k += 4) {   // loads of four entries ahead of their products
+                int j[4];
+                float ch[4], cl[4];
+                float2 y[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) j[u] = cp[32 * u];
+#pragma unroll
+                for (int u = 0; u < 4; u++) ch[u] = hp[32 * u];
+#pragma unroll
+                for (int u = 0; u < 4; u++) cl[u] = lp[32 * u];
+#pragma unroll
+                for (int u = 0; u < 4; u++) y[u] = xhl[j[u]];
+#pragma unroll
+                for (int u = 0; u < 4; u++) term(ch[u], cl[u], y[u]);
+                cp += 128;
+                hp += 128;
+                lp += 128;
+            }
+            for (; k < cnt; k++) {
+                term(*hp, *lp, xhl[*cp]);
+                cp += 32;
+                hp += 32;
+                lp += 32;
             }
             ri = c.bvec[i] - (dg * x[i] - ff_to_double_fast(acc));
         }
@@ -352,10 +406,7 @@ __global__ void __launch_bounds__(kBT) k_spmv32_t(SellView c, const float* d, fl
                     acc = fmaf(coef * fmaf(re_f, rsqrtf(r2), -1.f), d[j], acc);
                 }
             } else {
-                for (int k = 0; k < cnt; k++) {
-                    const size_t s = sell(i, k, c.cap);
-                    acc = fmaf(c.v32[s], d[c.col[s]], acc);
-                }
+                acc = sell_dot32(c.col + sell(i, 0, c.cap), c.v32 + sell(i, 0, c.cap), cnt, d);
             }
             qi = dg * d[i] - acc;
         }
@@ -388,6 +439,11 @@ __global__ void k_clear_x(int n, double* x) {
     if (i < n) x[i] = 0.0;
 }
 }  // namespace
+
+// One thread per row, one block per 256 rows (up to the 4096 partial sums of the grid
+// reductions; beyond that the row kernels stride): the block scheduler then balances the
+// uneven rows (dummy and surface rows are empty) across the SMs.
+static int row_grid(const Ctx* c) { return (int)std::min<int64_t>((c->n + kBT - 1) / kBT, 4096); }
 
 static SellView sell_view(Ctx* c) {
     SellView v;
@@ -424,7 +480,7 @@ static int set_cg_limits(Ctx* c, int max_iters) {
 // Launch up to `chunk` iterations of FP64 CG (extra launches exit at once once done).
 static void cg64_chunk(Ctx* c, int chunk) {
     const int n = (int)c->n;
-    const int gv = vec_grid(c), gs = c->sms * 8;
+    const int gv = vec_grid(c), gs = row_grid(c);
     double* x = c->p;
     c->launches += 3 * chunk;
     for (int k = 0; k < chunk; k++) {
@@ -437,7 +493,7 @@ static void cg64_chunk(Ctx* c, int chunk) {
 
 static void cg32_chunk(Ctx* c, int chunk) {
     const int n = (int)c->n;
-    const int gv = vec_grid(c), gs = c->sms * 8;
+    const int gv = vec_grid(c), gs = row_grid(c);
     const float coef = (float)c->coef_ppe, re_f = (float)c->r_lap.re;
     c->launches += 3 * chunk;
     for (int k = 0; k < chunk; k++) {
@@ -455,7 +511,7 @@ int ppe_solve(Ctx* c, mps_report* rep) {
     const int n = (int)c->n;
     const double tol2 = c->prm.cg_tol * c->prm.cg_tol;
     const int max_total = c->prm.cg_max_iter > 0 ? c->prm.cg_max_iter : (int)std::min<int64_t>(10 * c->n, 1 << 30);
-    const int gs = c->sms * 8, gv = vec_grid(c);
+    const int gs = row_grid(c), gv = vec_grid(c);
     int rc;
     if ((rc = set_cg_limits(c, max_total))) return rc;
     // x = 0, r = b, d = b, rho = |b|^2, stop2 = tol^2 |b|^2

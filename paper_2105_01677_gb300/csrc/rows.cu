@@ -228,6 +228,25 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
         const bool with_ppe = (a.pressure_mode == 0);
         int m_f = 0, m_b = 0, out_n = 0;
         bool overflow = false;
+        // a decided pair: into the gradient list and the row's PPE slots
+        auto append = [&](int j, bool tl, bool tn, bool nb_ok) {
+            if (!tl && !tn) return;
+            if (tn && nb_ok) {
+                if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j;
+                out_n++;
+            }
+            if (m_f + m_b >= a.cap) {
+                overflow = true;
+                return;
+            }
+            if (tn) a.lap_col[sell(i, m_f++, a.cap)] = j | kEntryN | (tl ? kEntryL : 0);
+            else a.lap_col[sell(i, a.cap - 1 - m_b++, a.cap)] = j | kEntryL;
+        };
+        // band pairs are set aside and decided after the walk, so that the lanes of a warp
+        // take the float-float and binary64 tiers together rather than one by one
+        constexpr int kPend = 16;
+        int pend[kPend];
+        int np = 0;
         // ---- classification
         int jn = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : 0;
         int j0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
@@ -244,21 +263,27 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
             int tn = tier1(r2, a.rn);
             if (!tl && !tn) continue;
             if (tl == 2 || tn == 2) {
+                if (np < kPend) {
+                    pend[np++] = k;
+                    continue;
+                }
                 const ff r2f = pair_r2(ih, il, jh, a.pos32lo[j]);
                 if (tl == 2) tl = decide_band(r2f, a.rl, a.pos, pi, j) ? 1 : 0;
                 if (tn == 2) tn = decide_band(r2f, a.rn, a.pos, pi, j) ? 1 : 0;
-                if (!tl && !tn) continue;
             }
-            if (tn && nb_ok) {
-                if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j;
-                out_n++;
-            }
-            if (m_f + m_b >= a.cap) {
-                overflow = true;
-                continue;
-            }
-            if (tn) a.lap_col[sell(i, m_f++, a.cap)] = j | kEntryN | (tl ? kEntryL : 0);
-            else a.lap_col[sell(i, a.cap - 1 - m_b++, a.cap)] = j | kEntryL;
+            append(j, tl, tn, nb_ok);
+        }
+        for (int q = 0; q < np; q++) {
+            const int j = a.vcol[sell(i, pend[q], a.cap_v)];
+            const float4 jh = a.pos32[j];
+            const float r2 = dist2_f(ih, jh);
+            const bool nb_ok = kind_of(jh) != kDummy;
+            int tl = (nb_ok && with_ppe) ? tier1(r2, a.rl) : 0;
+            int tn = tier1(r2, a.rn);
+            const ff r2f = pair_r2(ih, il, jh, a.pos32lo[j]);
+            if (tl == 2) tl = decide_band(r2f, a.rl, a.pos, pi, j) ? 1 : 0;
+            if (tn == 2) tn = decide_band(r2f, a.rn, a.pos, pi, j) ? 1 : 0;
+            append(j, tl, tn, nb_ok);
         }
         // ---- dense evaluation and in-place compaction (write slot <= read slot)
         double nd = 0.0, dg = 0.0;
