@@ -8,7 +8,8 @@ FP64 residual of 1e-8.  Synthetic seeded lattice with 1e-4 l0 jitter.
 
 The headline `value` is the mixed-precision path (FP32 pair terms and inner CG, FP64 number
 density, dot products and refinement); the plain FP64 path is timed on the same scene and
-reported under "fp64".  `e2e` repeats the mixed measurement through the C ABI with host
+reported under "fp64", and the mixed path with candidate lists kept for up to 4 steps
+under "kept_lists" (exact neighbour sets either way).  `e2e` repeats the mixed measurement through the C ABI with host
 buffers: every step uploads positions, velocities and kinds from pinned memory and reads
 back positions, velocities and pressure.
 
@@ -62,7 +63,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200, help="timed steps (the workload runs 200)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--seed", type=int, default=1)
@@ -74,6 +75,10 @@ def parse():
     ap.add_argument("--l0", type=float, default=0.0075, help="particle spacing (testing only)")
     ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
                     help="time one precision only and print its stage profile (profiling runs)")
+    ap.add_argument("--list-every", type=int, default=0,
+                    help="with --only: keep candidate lists for up to this many steps")
+    ap.add_argument("--kept-steps", type=int, default=None,
+                    help="timed steps of the kept-list comparison (default: --steps)")
     return ap.parse_args()
 
 
@@ -252,7 +257,8 @@ def run_gb300(args):
 
     if args.only:
         prec = 1 if args.only == "mixed" else 0
-        simo = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, precision=prec, **common)
+        simo = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, precision=prec,
+                              list_every=args.list_every, **common)
         simo.step(args.warmup)
         barrier()
         ms, its, prof = timed_steps(simo, args.steps, profile=True)
@@ -283,6 +289,18 @@ def run_gb300(args):
     barrier()
     ms_64 = max_over_ranks(ms_64)
     sim64.close()
+
+    # ---- mixed with candidate lists kept for up to 4 steps (the paper's fast mode refreshes
+    # its neighbour lists every 4 steps; here the sets stay exact)
+    kk = args.kept_steps or args.steps
+    simk = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, precision=1, list_every=4,
+                          **common)
+    simk.step(args.warmup)
+    barrier()
+    ms_k, it_k, profk = timed_steps(simk, kk, profile=True)
+    barrier()
+    ms_k = max_over_ranks(ms_k)
+    simk.close()
 
     # ---- end to end through the C ABI with host buffers (mixed)
     ke = args.e2e_steps or args.steps
@@ -361,6 +379,10 @@ def run_gb300(args):
                                            if prof64["stage_calls"][k] else 0.0)
                                        for k in prof64["stage_ms"]}},
         "mixed_over_fp64": value / value64,
+        "kept_lists": {"list_every": 4, "value": world * n * kk / (ms_k * 1e-3), "unit": UNIT,
+                       "ms_per_step": ms_k / kk, "steps": kk,
+                       "gathers": int(profk["stage_calls"]["gather"]),
+                       "stage_ms_per_step": {k: profk["stage_ms"][k] / kk for k in profk["stage_ms"]}},
         "cg": {"inner_iters_mean": inner, "outer_mean": outer,
                "resid_max": float(max(x[2] for x in it_mixed))},
         "e2e": {"value": world * n * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),

@@ -90,6 +90,13 @@ typedef struct {
     int32_t device;           /* CUDA device ordinal                                           */
     int32_t gather_block;     /* threads per cell block of the candidate gather: 32, 64, 96 or *
                                * 128; 0 chooses by dimension (tuning only, results identical)  */
+    int32_t list_every;       /* candidate lists (cell gather within h): 0 or 1 gathers them  *
+                               * every step; K > 1 keeps them for up to K steps, gathering    *
+                               * afresh earlier as soon as a particle has moved more than     *
+                               * s max(re)/2 from where they were gathered or leaves the grid. *
+                               * Neighbour sets stay exact either way (Sec. 5.6.3 runs the    *
+                               * paper's fast mode with a refresh every 4 steps).              */
+    int32_t reserved1;        /* must be 0 */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;
@@ -101,12 +108,13 @@ typedef struct {
     int32_t status;           /* MPS_OK or the first error seen                               */
     int32_t cg_iters;         /* CG iterations (mixed: FP32 inner iterations, all sweeps)     */
     int32_t cg_outer;         /* mixed: FP64 refinement sweeps; FP64: restarts                 */
-    int32_t reserved0;
+    int32_t list_gathered;    /* 1 if the step gathered its candidate lists afresh            */
     double cg_resid;          /* FP64 relative residual ||b - A p|| / ||b|| at exit            */
     int64_t n_surface;        /* FLUID/WALL particles with n* < beta n0 (Eq. 15)               */
     int64_t n_ghost;
     int64_t n_ppe_rows;       /* unknowns of the PPE                                          */
-    double max_disp;          /* max |r* - r| over FLUID particles [m]                         */
+    double max_disp;          /* max |r* - r_b| over FLUID particles [m], r_b the positions   *
+                               * the candidate lists were gathered at (r^k when every step)    */
     double n0_pnd;            /* reference number density at re_n (ideal lattice)             */
     double n0_lap;            /* reference number density at re_lap                           */
     double lambda;            /* lambda of Eq. 7 at re_lap [m^2]                               */

@@ -135,6 +135,7 @@ int check_params(const mps_params* P) {
     if (P->pressure_mode == 0 && !(P->cg_tol > 0)) return MPS_EINVAL;
     if (P->pressure_mode == 1 && !(P->gamma > 0)) return MPS_EINVAL;
     if ((P->alloc == nullptr) != (P->release == nullptr)) return MPS_EINVAL;
+    if (P->list_every < 0 || P->reserved1 != 0) return MPS_EINVAL;
     if (P->gather_block != 0 && P->gather_block != 32 && P->gather_block != 64 &&
         P->gather_block != 96 && P->gather_block != 128)
         return MPS_EINVAL;
@@ -243,6 +244,7 @@ int allocate(Ctx* c) {
         }
         A(cg_r, n) A(cg_d, n) A(cg_q, n)
     }
+    if (c->prm.list_every > 1) A(pos_b, n)
     A(key, n) A(key_alt, n) A(perm, n) A(perm_alt, n)
     const int64_t tiles = ((int64_t)n + 2047) / 2048;
     A(hist, 256 * tiles) A(hist_scan, 256 * tiles)
@@ -265,6 +267,7 @@ int allocate(Ctx* c) {
 
 // Host data -> device staging (original order) -> state arrays (slot = id).
 int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* types, bool have_state) {
+    c->need_list = true;
     const size_t n = (size_t)c->n, dim = (size_t)c->dim;
     uint8_t* base = (uint8_t*)c->stage;
     double* d_pos = (double*)base;
@@ -328,48 +331,75 @@ void stage_collect(Ctx* c, const bool* used) {
 int do_step(Ctx* c, bool advance, mps_report* rep) {
     const mps_params& P = c->prm;
     int rc;
-    bool used[MPS_NSTAGES] = {true, true, true, true, P.pressure_mode == 0, true};
-    MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
-    stage_begin(c, MPS_STAGE_BUCKET);
-    if ((rc = bucket_build(c, true))) return rc;                   // 1
-    stage_end(c, MPS_STAGE_BUCKET);
-    launch_copy_state_star(c);
-    MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, (size_t)c->n * sizeof(int32_t), c->stream));
-    stage_begin(c, MPS_STAGE_GATHER);
-    launch_verlet(c);                                              // candidates at r^k
-    stage_end(c, MPS_STAGE_GATHER);
-    stage_begin(c, MPS_STAGE_PREDICT);
-    launch_predict_rows(c);                                        // 2
-    stage_end(c, MPS_STAGE_PREDICT);
-    // per-slot outputs of the build; slots it does not visit (GHOST) keep these zeros
+    const bool keep = P.list_every > 1;
+    const double skin_half = 0.5 * P.cell_skin * std::max(P.re_n, P.re_lap);
     const size_t n = (size_t)c->n;
-    MPS_CUDA(c, cudaMemsetAsync(c->nstar, 0, n * sizeof(double), c->stream));
-    MPS_CUDA(c, cudaMemsetAsync(c->flag, 0, n, c->stream));
-    MPS_CUDA(c, cudaMemsetAsync(c->diag, 0, n * sizeof(double), c->stream));
-    MPS_CUDA(c, cudaMemsetAsync(c->bvec, 0, n * sizeof(double), c->stream));
-    MPS_CUDA(c, cudaMemsetAsync(c->nb_lap_cnt, 0, n * sizeof(int32_t), c->stream));
-    MPS_CUDA(c, cudaMemsetAsync(c->nb_n_cnt, 0, n * sizeof(int32_t), c->stream));
-    if (P.pressure_mode == 1) MPS_CUDA(c, cudaMemsetAsync(c->p, 0, n * sizeof(double), c->stream));
-    stage_begin(c, MPS_STAGE_BUILD);
-    launch_build_rows(c);                                          // 3 (+ 4 for the EOS)
-    stage_end(c, MPS_STAGE_BUILD);
-    MPS_CUDA(c, cudaGetLastError());
-    if ((rc = read_status(c))) return rc;
-    const DevStatus& s = *c->st_host;
-    rep->n_ghost = s.n_ghost;
-    rep->n_surface = s.n_surface;
-    rep->n_ppe_rows = s.n_ppe;
-    rep->max_disp = std::sqrt(bits_to_double(s.max_disp_bits));   // device keeps the square
-    rep->cand_tests = (int64_t)s.cand_tests;
-    rep->pairs_ppe = (int64_t)s.pairs_lap;
-    rep->pairs_pnd = (int64_t)s.pairs_n;
-    rep->n0_pnd = c->n0_pnd;
-    rep->n0_lap = c->n0_lap;
-    rep->lambda = c->lambda;
-    rep->cg_iters = rep->cg_outer = 0;
-    rep->cg_resid = 0.0;
-    if ((rc = status_error(s))) return rc;
-    if (rep->max_disp > 0.5 * P.cell_skin * std::max(P.re_n, P.re_lap)) return MPS_ESKIN;
+    // Candidate lists are gathered at r_b and serve while every particle stays within
+    // s max(re)/2 of r_b: a pair closer than re at r^k or r* is then closer than h at r_b.
+    // A kept list that fails the check for r* is gathered afresh at r^k and the step
+    // restarts (r^k, u^k are untouched until the update).
+    bool fresh = !keep || c->need_list || c->list_age >= P.list_every;
+    for (;;) {
+        MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
+        if (fresh) {
+            stage_begin(c, MPS_STAGE_BUCKET);
+            if ((rc = bucket_build(c, true))) return rc;               // 1
+            stage_end(c, MPS_STAGE_BUCKET);
+            if (keep)
+                MPS_CUDA(c, cudaMemcpyAsync(c->pos_b, c->pos, n * sizeof(double4),
+                                            cudaMemcpyDeviceToDevice, c->stream));
+        }
+        launch_copy_state_star(c);
+        if (fresh) {
+            MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), c->stream));
+            stage_begin(c, MPS_STAGE_GATHER);
+            launch_verlet(c);                                          // candidates at r_b = r^k
+            stage_end(c, MPS_STAGE_GATHER);
+        }
+        stage_begin(c, MPS_STAGE_PREDICT);
+        launch_predict_rows(c);                                        // 2
+        stage_end(c, MPS_STAGE_PREDICT);
+        // per-slot outputs of the build; slots it does not visit (GHOST) keep these zeros
+        MPS_CUDA(c, cudaMemsetAsync(c->nstar, 0, n * sizeof(double), c->stream));
+        MPS_CUDA(c, cudaMemsetAsync(c->flag, 0, n, c->stream));
+        MPS_CUDA(c, cudaMemsetAsync(c->diag, 0, n * sizeof(double), c->stream));
+        MPS_CUDA(c, cudaMemsetAsync(c->bvec, 0, n * sizeof(double), c->stream));
+        MPS_CUDA(c, cudaMemsetAsync(c->nb_lap_cnt, 0, n * sizeof(int32_t), c->stream));
+        MPS_CUDA(c, cudaMemsetAsync(c->nb_n_cnt, 0, n * sizeof(int32_t), c->stream));
+        if (P.pressure_mode == 1) MPS_CUDA(c, cudaMemsetAsync(c->p, 0, n * sizeof(double), c->stream));
+        stage_begin(c, MPS_STAGE_BUILD);
+        launch_build_rows(c);                                          // 3 (+ 4 for the EOS)
+        stage_end(c, MPS_STAGE_BUILD);
+        MPS_CUDA(c, cudaGetLastError());
+        if ((rc = read_status(c))) return rc;
+        const DevStatus& s = *c->st_host;
+        if (fresh) c->n_ghost_last = s.n_ghost;
+        rep->n_ghost = c->n_ghost_last;
+        rep->n_surface = s.n_surface;
+        rep->n_ppe_rows = s.n_ppe;
+        rep->max_disp = std::sqrt(bits_to_double(s.max_disp_bits));   // device keeps the square
+        rep->cand_tests = (int64_t)s.cand_tests;
+        rep->pairs_ppe = (int64_t)s.pairs_lap;
+        rep->pairs_pnd = (int64_t)s.pairs_n;
+        rep->n0_pnd = c->n0_pnd;
+        rep->n0_lap = c->n0_lap;
+        rep->lambda = c->lambda;
+        rep->cg_iters = rep->cg_outer = 0;
+        rep->cg_resid = 0.0;
+        rep->list_gathered = fresh ? 1 : 0;
+        if ((rc = status_error(s))) return rc;
+        if (rep->max_disp > skin_half) {
+            if (fresh) return MPS_ESKIN;
+            fresh = true;                                              // gather afresh at r^k
+            continue;
+        }
+        break;
+    }
+    if (fresh) {
+        c->list_age = 0;
+        c->need_list = false;
+    }
+    bool used[MPS_NSTAGES] = {fresh, fresh, true, true, P.pressure_mode == 0, true};
     if (P.pressure_mode == 0) {                                    // 4, 5
         stage_begin(c, MPS_STAGE_PPE);
         if ((rc = ppe_solve(c, rep))) return rc;
@@ -385,8 +415,18 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     if (advance) launch_gradient_correct(c);                       // 6
     stage_end(c, MPS_STAGE_UPDATE);
     MPS_CUDA(c, cudaGetLastError());
+    if (keep && advance) {
+        // where r^{k+1} stands against r_b decides whether the next step may keep the lists
+        MPS_CUDA(c, cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                                    c->stream));
+    }
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
     stage_collect(c, used);
+    if (keep && advance) {
+        const DevStatus& s = *c->st_host;
+        c->list_age++;
+        if (s.leave || std::sqrt(bits_to_double(s.max_disp_next_bits)) > skin_half) c->need_list = true;
+    }
     if (advance) c->steps_done++;
     rep->steps_done = c->steps_done;
     return MPS_OK;
@@ -543,6 +583,7 @@ int mps_debug_neighbors(mps_ctx* c, int32_t which, int64_t* offsets, int32_t* id
     int rc;
     MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
     if ((rc = bucket_build(c, false))) return rc;
+    c->need_list = true;   // the state was reordered: kept candidate lists no longer apply
     const Radius& r = which == 0 ? c->r_n : c->r_lap;
     int32_t* d_cnt = nullptr;
     int64_t* d_off = nullptr;

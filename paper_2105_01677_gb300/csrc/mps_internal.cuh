@@ -42,12 +42,13 @@ struct DevStatus {
     unsigned int n_occ;
     unsigned int n_surface;
     unsigned int n_ppe;
-    unsigned int pad0;
+    unsigned int leave;                 // kept lists: particles whose next position leaves the grid or is not finite
     unsigned long long max_disp_bits;   // max squared FLUID displacement (bit pattern of a non-negative double)
     unsigned int counter[8];            // last-block-done tickets of grid reductions
     unsigned long long cand_tests;      // candidate distance tests of the cell gather
     unsigned long long pairs_lap;       // PPE coefficients evaluated (pairs within re_lap)
     unsigned long long pairs_n;         // number-density terms evaluated (pairs within re_n)
+    unsigned long long max_disp_next_bits;   // kept lists: max squared |r^{k+1} - r_b| (as above)
 };
 
 // Scalars of one CG solve; updated by the last block of each reduction kernel.
@@ -159,6 +160,12 @@ struct Ctx {
     Radius r_n, r_lap, r_v;   // r_v: candidate radius h (only r_v.hi is used)
     int64_t steps_done;
     int last_cg_iters;
+    // candidate lists kept across steps (list_every > 1): positions r_b where they were
+    // gathered, advanced steps since then, and whether the next step must gather afresh
+    double4* pos_b = nullptr;
+    int list_age = 0;
+    bool need_list = true;
+    int64_t n_ghost_last = 0;
 
     // state (sorted order) and double buffers
     double4 *pos, *vel, *pos_alt, *vel_alt;

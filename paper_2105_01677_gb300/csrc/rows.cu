@@ -75,6 +75,7 @@ struct PredictArgs {
     const float4* pos32;
     const float4* pos32lo;
     const double4* pos;
+    const double4* pos_b;   // where the candidate lists were gathered (r^k when gathered this step)
     const double4* vel;
     const float4* vel32;
     const int8_t* type;
@@ -165,7 +166,8 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
         l4.w = 0.f;
         a.pos32_star[i] = h4;
         a.pos32lo_star[i] = l4;
-        const double dx = ps.x - pi.x, dy = ps.y - pi.y, dz = ps.z - pi.z;
+        const double4 pb = a.pos_b ? a.pos_b[i] : pi;
+        const double dx = ps.x - pb.x, dy = ps.y - pb.y, dz = ps.z - pb.z;
         disp = fma(dz, dz, fma(dy, dy, dx * dx));   // squared; the host takes the root
     }
     // warp max of the squared displacement (non-negative doubles order like their bits)
@@ -389,6 +391,7 @@ void launch_predict_rows(Ctx* c) {
     a.pos32 = c->pos32;
     a.pos32lo = c->pos32lo;
     a.pos = c->pos;
+    a.pos_b = c->pos_b;
     a.vel = c->vel;
     a.vel32 = c->vel32;
     a.type = c->type;

@@ -38,14 +38,27 @@ __global__ void __launch_bounds__(kBT) k_clamp_store(int n, double* p) {
     if (i < n) p[i] = fmax(p[i], 0.0);
 }
 
+// Candidate lists kept across steps: the update also refreshes the FP32 copies of r, u
+// and measures r^{k+1} against the positions r_b the lists were gathered at.
+struct Keep {
+    const double4* pos_b;   // null: lists are gathered every step (nothing else is used)
+    float4* pos32;
+    float4* pos32lo;
+    float4* vel32;
+    GridDesc g;
+    DevStatus* st;
+};
+
+// One FLUID row of the pressure-gradient correction; returns |r^{k+1} - r_b|^2 when
+// candidate lists are kept (0 otherwise)
 template <bool MIXED>
-__global__ void __launch_bounds__(kBT)
-    k_gradient(int n, const int8_t* type, const double4* ps, const float4* ps32, const double4* us,
-               const double* p, const double* phat, const int32_t* ncol, const int32_t* ncnt,
-               int cap_n, double re, float re_f, double coef_grad, double dt, double rho,
-               double4* pos, double4* vel) {
-    int i = blockIdx.x * kBT + threadIdx.x;
-    if (i >= n || type[i] != kFluid) return;
+__device__ __forceinline__ double gradient_row(int i, const int8_t* type, const double4* ps,
+                                               const float4* ps32, const double4* us,
+                                               const double* p, const double* phat,
+                                               const int32_t* ncol, const int32_t* ncnt, int cap_n,
+                                               double re, float re_f, double coef_grad, double dt,
+                                               double rho, double4* pos, double4* vel,
+                                               const Keep& kp) {
     const double4 pi = ps[i];
     const double ph = phat[i];
     const int cnt = ncnt[i];
@@ -85,8 +98,55 @@ __global__ void __launch_bounds__(kBT)
     const double k = -(dt / rho) * coef_grad;
     const double4 u = us[i];
     const double d0 = k * g0, d1 = k * g1, d2 = k * g2;
-    vel[i] = make_double4(u.x + d0, u.y + d1, u.z + d2, 0.0);
-    pos[i] = make_double4(pi.x + dt * d0, pi.y + dt * d1, pi.z + dt * d2, 0.0);
+    const double4 un = make_double4(u.x + d0, u.y + d1, u.z + d2, 0.0);
+    const double4 xn = make_double4(pi.x + dt * d0, pi.y + dt * d1, pi.z + dt * d2, 0.0);
+    vel[i] = un;
+    pos[i] = xn;
+    if (kp.pos_b == nullptr) return 0.0;
+    // the next step starts without a bucket build: refresh the FP32 copies at r^{k+1} and
+    // flag a particle that leaves the cell grid (or is not finite) for a fresh gather
+    const GridDesc& g = kp.g;
+    float4 h4, l4;
+    split_rel(xn.x, g.bmin[0], &h4.x, &l4.x);
+    split_rel(xn.y, g.bmin[1], &h4.y, &l4.y);
+    split_rel(xn.z, g.bmin[2], &h4.z, &l4.z);
+    h4.w = __int_as_float((int)type[i]);
+    l4.w = 0.f;
+    kp.pos32[i] = h4;
+    kp.pos32lo[i] = l4;
+    kp.vel32[i] = make_float4((float)un.x, (float)un.y, (float)un.z, 0.f);
+    const double xs[3] = {xn.x, xn.y, xn.z};
+    bool inside = isfinite(un.x) && isfinite(un.y) && isfinite(un.z);
+    for (int a = 0; a < g.dim; a++) {
+        const double q = floor(__ddiv_rn(__dsub_rn(xs[a], g.bmin[a]), g.h));
+        if (!(q >= 0.0 && q < (double)g.ncell[a])) inside = false;
+    }
+    if (!inside) atomicAdd(&kp.st->leave, 1u);
+    const double4 b = kp.pos_b[i];
+    const double ex = xn.x - b.x, ey = xn.y - b.y, ez = xn.z - b.z;
+    return fma(ez, ez, fma(ey, ey, ex * ex));
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kBT)
+    k_gradient(int n, const int8_t* type, const double4* ps, const float4* ps32, const double4* us,
+               const double* p, const double* phat, const int32_t* ncol, const int32_t* ncnt,
+               int cap_n, double re, float re_f, double coef_grad, double dt, double rho,
+               double4* pos, double4* vel, Keep kp) {
+    int i = blockIdx.x * kBT + threadIdx.x;
+    const bool act = i < n && type[i] == kFluid;
+    if (kp.pos_b == nullptr && !act) return;
+    double disp = 0.0;
+    if (act) disp = gradient_row<MIXED>(i, type, ps, ps32, us, p, phat, ncol, ncnt, cap_n, re, re_f,
+                                        coef_grad, dt, rho, pos, vel, kp);
+    if (kp.pos_b == nullptr) return;
+    // kept candidate lists: the largest |r^{k+1} - r_b| of the warp
+    unsigned long long v = (unsigned long long)__double_as_longlong(disp);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    if ((threadIdx.x & 31) == 0 && v) atomicMax(&kp.st->max_disp_next_bits, v);
 }
 
 // non-fluid particles keep r = r*, u = u* (walls and dummies do not move)
@@ -170,16 +230,23 @@ void launch_gradient_correct(Ctx* c) {
     const int n = (int)c->n;
     const int nb = (n + kBT - 1) / kBT;
     const mps_params& P = c->prm;
+    Keep kp;
+    kp.pos_b = c->pos_b;
+    kp.pos32 = c->pos32;
+    kp.pos32lo = c->pos32lo;
+    kp.vel32 = c->vel32;
+    kp.g = c->grid;
+    kp.st = c->st;
     if (P.precision == 1)
         k_gradient<true><<<nb, kBT, 0, c->stream>>>(n, c->type, c->pos_star, c->pos32_star, c->vel_star,
                                                     c->p, c->phat, c->nb_n_col, c->nb_n_cnt, c->cap_n,
                                                     c->r_n.re, c->r_n.re_f, c->coef_grad, P.dt, P.rho,
-                                                    c->pos, c->vel);
+                                                    c->pos, c->vel, kp);
     else
         k_gradient<false><<<nb, kBT, 0, c->stream>>>(n, c->type, c->pos_star, c->pos32_star, c->vel_star,
                                                      c->p, c->phat, c->nb_n_col, c->nb_n_cnt, c->cap_n,
                                                      c->r_n.re, c->r_n.re_f, c->coef_grad, P.dt, P.rho,
-                                                     c->pos, c->vel);
+                                                     c->pos, c->vel, kp);
     k_copy_back<<<nb, kBT, 0, c->stream>>>(n, c->type, c->pos_star, c->vel_star, c->pos, c->vel);
     c->launches += 2;
 }

@@ -36,20 +36,21 @@ class mps_params(C.Structure):
                 ("box_min", C.c_double * 3), ("box_max", C.c_double * 3),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32),
                 ("ppe_operator", C.c_int32), ("device", C.c_int32), ("gather_block", C.c_int32),
+                ("list_every", C.c_int32), ("reserved1", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
                 ("alloc_user", C.c_void_p)]
 
 
 class mps_report(C.Structure):
     _fields_ = [("status", C.c_int32), ("cg_iters", C.c_int32), ("cg_outer", C.c_int32),
-                ("reserved0", C.c_int32), ("cg_resid", C.c_double), ("n_surface", C.c_int64),
+                ("list_gathered", C.c_int32), ("cg_resid", C.c_double), ("n_surface", C.c_int64),
                 ("n_ghost", C.c_int64), ("n_ppe_rows", C.c_int64), ("max_disp", C.c_double),
                 ("n0_pnd", C.c_double), ("n0_lap", C.c_double), ("lambda_", C.c_double),
                 ("steps_done", C.c_int64), ("cand_tests", C.c_int64), ("pairs_ppe", C.c_int64),
                 ("pairs_pnd", C.c_int64)]
 
     def as_dict(self) -> dict:
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved0"}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
         d["lambda"] = d.pop("lambda_")
         return d
 

@@ -103,3 +103,24 @@ def compare_step(scene, gpu_st, ora_st, prm, tol=FP64_TOL, fields=("p", "n_star"
     for k, v in errs.items():
         assert v <= tol, f"{k}: relative error {v:.3e} > {tol:.1e}"
     return errs
+
+
+def ulp_sensitivity(scene, nsteps, seed=0, **kw):
+    """Conditioning of the oracle's own trajectory: relative change of each field after
+    `nsteps` oracle steps when every FLUID coordinate is moved by one ulp (random sign).
+    The PPE right-hand side (n* - n0)/(n0 dt^2) amplifies position rounding by ~1/dt^2,
+    so over several steps p differs at ~1e-10 between two runs that differ only in the
+    rounding of one operation; multi-step comparisons take a bound from this."""
+    prm = oracle_params(scene, **kw)
+    a = oracle.State.from_scene(scene)
+    b = oracle.State.from_scene(scene)
+    f = scene.types == scenes.FLUID
+    rng = np.random.default_rng(seed)
+    pert = b.pos.copy()
+    pert[f] = np.nextafter(pert[f], pert[f] + rng.choice([-1.0, 1.0], size=pert[f].shape))
+    b.pos = pert
+    for _ in range(nsteps):
+        oracle.step(prm, a)
+        oracle.step(prm, b)
+    return {k: rel_err(getattr(b, k), getattr(a, k)) for k in ("p", "vel", "pos")}
+
