@@ -249,7 +249,9 @@ int allocate(Ctx* c) {
     const int64_t tiles = ((int64_t)n + 2047) / 2048;
     A(hist, 256 * tiles) A(hist_scan, 256 * tiles)
     A(cell_count, c->ntable) A(cell_start, c->ntable + 1) A(occ, n + 1)
-    const int64_t sw = std::max(scan_scratch_words(256 * tiles), scan_scratch_words(c->ntable + 1));
+    A(mark_f, n + 1) A(mark_fw, n + 1) A(scan_f, n + 1) A(scan_fw, n + 1) A(rows_f, n) A(rows_fw, n)
+    const int64_t sw = std::max(std::max(scan_scratch_words(256 * tiles), scan_scratch_words(c->ntable + 1)),
+                                scan_scratch_words((int64_t)n + 1));
     A(scan_scratch, sw)
     A(partials, 4096) A(cg, 1) A(st, 1)
     c->stage_bytes = n * (3 * 8 * 2 + 8 + 8 + 4 + 2) + 1024;

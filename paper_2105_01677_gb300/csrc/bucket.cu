@@ -160,6 +160,25 @@ __global__ void __launch_bounds__(kBT)
     pos32[s] = h;
     pos32lo[s] = l;
 }
+// active-row marks of the new order (one scan each gives the row lists)
+__global__ void __launch_bounds__(kBT)
+    k_mark_rows(int n, const int8_t* type, uint32_t* mark_f, uint32_t* mark_fw) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int t = type[s];
+    mark_f[s] = t == kFluid ? 1u : 0u;
+    mark_fw[s] = (t == kFluid || t == kWall) ? 1u : 0u;
+}
+
+__global__ void __launch_bounds__(kBT)
+    k_scatter_rows(int n, const int8_t* type, const uint32_t* scan_f, const uint32_t* scan_fw,
+                   int32_t* rows_f, int32_t* rows_fw) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int t = type[s];
+    if (t == kFluid) rows_f[scan_f[s]] = s;
+    if (t == kFluid || t == kWall) rows_fw[scan_fw[s]] = s;
+}
 }  // namespace
 
 void launch_cell_keys_only(Ctx* c, uint32_t* out_key) {
@@ -209,6 +228,11 @@ int bucket_build(Ctx* c, bool mutate) {
     std::swap(c->type, c->type_alt);
     std::swap(c->id, c->id_alt);
     std::swap(c->p, c->p_alt);
+    // FLUID rows and FLUID / WALL rows in slot order, for the per-row kernels
+    k_mark_rows<<<nb1, kBT, 0, s>>>(n, c->type, c->mark_f, c->mark_fw);
+    c->launches += 2 + scan_exclusive(c->mark_f, c->scan_f, n, true, c->scan_scratch, s);
+    c->launches += scan_exclusive(c->mark_fw, c->scan_fw, n, true, c->scan_scratch, s);
+    k_scatter_rows<<<nb1, kBT, 0, s>>>(n, c->type, c->scan_f, c->scan_fw, c->rows_f, c->rows_fw);
     MPS_CUDA(c, cudaGetLastError());
     return MPS_OK;
 }

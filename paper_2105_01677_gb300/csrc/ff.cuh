@@ -114,6 +114,90 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // float-float -> double with a single FP64 operation (the conversions are bit moves)
 __device__ __forceinline__ double ff_to_double_fast(ff a) { return f2d_bits(a.h) + f2d_bits(a.l); }
 
+// ---------------------------------------------------------------- packed pairs
+// The same transformations on two independent values at once with the FP32x2 instructions
+// (sm_100 and later): lane x and lane y never mix.  Every operation is an explicit
+// round-to-nearest intrinsic, so none of them is contracted into a fused multiply-add.
+struct ff2 {
+    float2 h, l;
+};
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+__device__ __forceinline__ ff2 ff2_two_sum(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    const float2 e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff2 ff2_fast_two_sum(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    return {s, sub2(b, sub2(s, a))};
+}
+
+__device__ __forceinline__ ff2 ff2_two_prod(float2 a, float2 b) {
+    const float2 p = mul2(a, b);
+    return {p, fma2(a, b, neg2(p))};
+}
+
+__device__ __forceinline__ ff2 ff2_add(ff2 a, ff2 b) {
+    const ff2 s = ff2_two_sum(a.h, b.h);
+    return ff2_fast_two_sum(s.h, add2(s.l, add2(a.l, b.l)));
+}
+
+__device__ __forceinline__ ff2 ff2_add_f(ff2 a, float2 b) {
+    const ff2 s = ff2_two_sum(a.h, b);
+    return ff2_fast_two_sum(s.h, add2(s.l, a.l));
+}
+
+__device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b) {
+    ff2 p = ff2_two_prod(a.h, b.h);
+    p.l = fma2(a.h, b.l, fma2(a.l, b.h, p.l));
+    return ff2_fast_two_sum(p.h, p.l);
+}
+
+// (bh + bl) - (ah + al) for two coordinate pairs b against one a
+__device__ __forceinline__ ff2 ff2_diff(float ah, float al, float2 bh, float2 bl) {
+    const ff2 s = ff2_two_sum(bh, f2(-ah));
+    return ff2_fast_two_sum(s.h, add2(s.l, sub2(bl, f2(al))));
+}
+
+__device__ __forceinline__ ff2 ff2_sqr_raw(ff2 a) {
+    ff2 p = ff2_two_prod(a.h, a.h);
+    p.l = fma2(add2(a.h, a.h), a.l, p.l);
+    return p;
+}
+
+__device__ __forceinline__ ff2 ff2_dist2(ff2 dx, ff2 dy, ff2 dz) {
+    const ff2 x = ff2_sqr_raw(dx), y = ff2_sqr_raw(dy), z = ff2_sqr_raw(dz);
+    const ff2 s1 = ff2_two_sum(x.h, y.h);
+    const ff2 s2 = ff2_two_sum(s1.h, z.h);
+    return ff2_fast_two_sum(s2.h, add2(add2(add2(s1.l, s2.l), add2(x.l, y.l)), z.l));
+}
+
+__device__ __forceinline__ ff2 ff2_rsqrt_step(ff2 x, ff2 y) {
+    const ff2 t = ff2_mul(y, y);
+    ff2 u = ff2_two_prod(x.h, t.h);
+    u.l = fma2(x.h, t.l, fma2(x.l, t.h, u.l));
+    const float2 hres = sub2(sub2(f2(1.0f), u.h), u.l);
+    return ff2_add_f(y, mul2(mul2(f2(0.5f), y.h), hres));
+}
+
+// one Newton step from the FP32 estimate (relative error ~1e-13)
+__device__ __forceinline__ ff2 ff2_rsqrt1(ff2 x) {
+    const ff2 y0 = {make_float2(rsqrtf(x.h.x), rsqrtf(x.h.y)), f2(0.f)};
+    return ff2_rsqrt_step(x, y0);
+}
+
+__device__ __forceinline__ ff ff2_lo(const ff2& a) { return {a.h.x, a.l.x}; }
+__device__ __forceinline__ ff ff2_hi(const ff2& a) { return {a.h.y, a.l.y}; }
+
 __host__ inline ff ff_from_double(double v) {
     const float h = (float)v;
     return {h, (float)(v - (double)h)};

@@ -196,6 +196,10 @@ struct Ctx {
     uint32_t* cell_count;
     int32_t* cell_start;
     uint32_t* occ;         // occupied cell codes
+    // active rows in slot order, rebuilt with every bucket build: FLUID slots (rows_f) and
+    // FLUID or WALL slots (rows_fw); their counts sit after the exclusive scans
+    uint32_t *mark_f, *mark_fw, *scan_f, *scan_fw;   // n + 1 each
+    int32_t *rows_f, *rows_fw;
     uint32_t* scan_scratch;
     // CG (FP64): x = p, r, d, q ; FP32: r32, d32, q32, x32
     double *cg_r, *cg_d, *cg_q;

@@ -76,6 +76,8 @@ struct PredictArgs {
     const float4* pos32lo;
     const double4* pos;
     const double4* pos_b;   // where the candidate lists were gathered (r^k when gathered this step)
+    const int32_t* rows;    // FLUID slots in slot order
+    const uint32_t* nrows;  // their count
     const double4* vel;
     const float4* vel32;
     const int8_t* type;
@@ -90,9 +92,11 @@ struct PredictArgs {
 
 template <bool MIXED>
 __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
-    const int i = blockIdx.x * kBT + threadIdx.x;
+    // one thread per FLUID row (the bucket build's list of FLUID slots)
+    const int tid = blockIdx.x * kBT + threadIdx.x;
+    const int i = tid < (int)*a.nrows ? a.rows[tid] : -1;
     double disp = 0.0;
-    if (i < a.n && a.type[i] == kFluid) {
+    if (i >= 0) {
         const float4 ih = a.pos32[i], il = a.pos32lo[i];
         const double4 pi = a.pos[i];
         const double4 ui = a.vel[i];
@@ -181,6 +185,8 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
 
 struct BuildArgs {
     int n, cap_v, cap, cap_n, pressure_mode;
+    const int32_t* rows;    // FLUID and WALL slots in slot order
+    const uint32_t* nrows;  // their count
     const int32_t* vcol;
     const int32_t* vcnt;
     const float4* pos32;     // r*
@@ -218,12 +224,14 @@ constexpr int kSlotMask = kEntryL - 1;
 // diagonal, and compacts the PPE coefficients in place to the front of the row.
 template <bool MIXED>
 __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
-    const int i = blockIdx.x * kBT + threadIdx.x;
+    // FLUID and WALL rows only (the bucket build's list of them): a DUMMY particle's own n*
+    // enters no equation (no free-surface test, no PPE row, no gradient), so it is not
+    // evaluated (reported as 0)
+    const int tid = blockIdx.x * kBT + threadIdx.x;
+    const int i = tid < (int)*a.nrows ? a.rows[tid] : -1;
     bool surf = false, ppe = false;
     unsigned n_lap = 0, n_pnd = 0;   // pairs evaluated by this row
-    // FLUID and WALL rows only: a DUMMY particle's own n* enters no equation (no free-surface
-    // test, no PPE row, no gradient), so it is not evaluated (reported as 0)
-    if (i < a.n && (a.type[i] == kFluid || a.type[i] == kWall)) {
+    if (i >= 0) {
         const float4 ih = a.pos32[i], il = a.pos32lo[i];
         const double4 pi = a.pos[i];
         const int cnt = a.vcnt[i];
@@ -289,68 +297,89 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
         }
         // ---- dense evaluation and in-place compaction (write slot <= read slot)
         double nd = 0.0, dg = 0.0;
-        ff ndf = {0.f, 0.f}, dgf = {0.f, 0.f};
         int out_l = 0;
         const int m_all = m_f + m_b;
-        for (int t = 0; t < m_all; t++) {
-            const int k = t < m_f ? t : a.cap - m_b + (t - m_f);
-            const size_t qk = sell(i, k, a.cap);
-            const int e = a.lap_col[qk];
-            const int j = e & kSlotMask;
-            const bool tn = (e & kEntryN) != 0, tl = (e & kEntryL) != 0;
-            double cd = 0.0;
-            ff cf = {0.f, 0.f};
-            bool ok = true;
-            if (MIXED) {
-                const ff r2f = pair_r2(ih, il, a.pos32[j], a.pos32lo[j]);
-                if (!(r2f.h > 0.f)) {
-                    if (!(exact_dist2(pi, a.pos[j]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
-                    ok = false;
-                } else {
-                    // 1/r: one Newton step (~1e-13) serves the PPE coefficient; n* takes a
-                    // second (~1e-15) so that it stays far inside the flag band
-                    ff y = ff_rsqrt1(r2f);
-                    if (tn) {
-                        y = ff_rsqrt_step(r2f, y);
-                        ndf = ff_add(ndf, ff_add_f(ff_mul({a.rn.re_f, a.rn.re_l}, y), -1.f));
-                    }
-                    if (tl) {
-                        // c = coef (re/r - 1) = (coef re) y - coef
-                        cf = ff_add(ff_mul(a.cre_ff, y), a.ncoef_ff);
-                        dgf = ff_add(dgf, cf);
-                    }
+        auto slot_of = [&](int t) { return t < m_f ? t : a.cap - m_b + (t - m_f); };
+        if (MIXED) {
+            // Two entries per iteration, their pair terms in packed FP32x2 float-float.
+            // 1/r: one Newton step (~1e-13) serves the PPE coefficient; n* takes a second
+            // (~1e-15) so that it stays far inside the flag band.  The terms are summed in
+            // entry order into (n*, diagonal) as one packed float-float accumulator; an
+            // entry without a term adds an exact zero.
+            ff2 acc = {f2(0.f), f2(0.f)};
+            const ff2 ren = {f2(a.rn.re_f), f2(a.rn.re_l)};
+            const ff2 cre = {f2(a.cre_ff.h), f2(a.cre_ff.l)};
+            const ff2 ncoef = {f2(a.ncoef_ff.h), f2(a.ncoef_ff.l)};
+            // the entries of the next pair are loaded one iteration ahead (each slot is
+            // read before the compaction can write it: writes go to slots <= t + 1)
+            int n0 = m_all > 0 ? a.lap_col[sell(i, slot_of(0), a.cap)] : 0;
+            int n1 = m_all > 1 ? a.lap_col[sell(i, slot_of(1), a.cap)] : n0;
+            for (int t = 0; t < m_all; t += 2) {
+                const bool two = t + 1 < m_all;
+                const int e0 = n0, e1 = n1;
+                if (t + 2 < m_all) {
+                    n0 = a.lap_col[sell(i, slot_of(t + 2), a.cap)];
+                    n1 = t + 3 < m_all ? a.lap_col[sell(i, slot_of(t + 3), a.cap)] : n0;
                 }
-            } else {
+                const int j0 = e0 & kSlotMask, j1 = e1 & kSlotMask;
+                const float4 h0 = a.pos32[j0], l0 = a.pos32lo[j0];
+                const float4 h1 = a.pos32[j1], l1 = a.pos32lo[j1];
+                const ff2 r2 = ff2_dist2(
+                    ff2_diff(ih.x, il.x, make_float2(h0.x, h1.x), make_float2(l0.x, l1.x)),
+                    ff2_diff(ih.y, il.y, make_float2(h0.y, h1.y), make_float2(l0.y, l1.y)),
+                    ff2_diff(ih.z, il.z, make_float2(h0.z, h1.z), make_float2(l0.z, l1.z)));
+                const bool ok0 = r2.h.x > 0.f, ok1 = two && r2.h.y > 0.f;
+                if (!ok0 && !(exact_dist2(pi, a.pos[j0]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
+                if (two && !ok1 && !(exact_dist2(pi, a.pos[j1]) > 0.0))
+                    atomicOr(&a.st->err, kErrCoincident);
+                const bool tn0 = ok0 && (e0 & kEntryN), tl0 = ok0 && (e0 & kEntryL);
+                const bool tn1 = ok1 && (e1 & kEntryN), tl1 = ok1 && (e1 & kEntryL);
+                const ff2 y = ff2_rsqrt1(r2);
+                ff2 w = {f2(0.f), f2(0.f)};
+                if (tn0 || tn1) w = ff2_add_f(ff2_mul(ren, ff2_rsqrt_step(r2, y)), f2(-1.f));
+                // c = coef (re/r - 1) = (coef re) y - coef
+                const ff2 c = ff2_add(ff2_mul(cre, y), ncoef);
+                acc = ff2_add(acc, {make_float2(tn0 ? w.h.x : 0.f, tl0 ? c.h.x : 0.f),
+                                    make_float2(tn0 ? w.l.x : 0.f, tl0 ? c.l.x : 0.f)});
+                acc = ff2_add(acc, {make_float2(tn1 ? w.h.y : 0.f, tl1 ? c.h.y : 0.f),
+                                    make_float2(tn1 ? w.l.y : 0.f, tl1 ? c.l.y : 0.f)});
+                if (tl0) {
+                    const size_t q = sell(i, out_l++, a.cap);
+                    a.lap_col[q] = j0;
+                    a.lap_v32[q] = c.h.x;
+                    a.lap_vlo[q] = c.l.x;
+                }
+                if (tl1) {
+                    const size_t q = sell(i, out_l++, a.cap);
+                    a.lap_col[q] = j1;
+                    a.lap_v32[q] = c.h.y;
+                    a.lap_vlo[q] = c.l.y;
+                }
+            }
+            nd = ff_to_double_fast(ff2_lo(acc));
+            dg = ff_to_double_fast(ff2_hi(acc));
+        } else {
+            for (int t = 0; t < m_all; t++) {
+                const int e = a.lap_col[sell(i, slot_of(t), a.cap)];
+                const int j = e & kSlotMask;
+                const bool tn = (e & kEntryN) != 0, tl = (e & kEntryL) != 0;
                 const double4 pj = a.pos[j];
                 const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
                 const double rr2 = fma(dz, dz, fma(dy, dy, dx * dx));
                 if (!(rr2 > 0.0)) {
                     atomicOr(&a.st->err, kErrCoincident);
-                    ok = false;
-                } else {
-                    const double rs = rsqrt(rr2);
-                    if (tn) nd += fma(a.rn.re, rs, -1.0);
-                    if (tl) {
-                        cd = a.coef_ppe * fma(a.rl.re, rs, -1.0);
-                        dg += cd;
-                    }
+                    continue;
                 }
-            }
-            if (ok && tl) {
-                const size_t q = sell(i, out_l, a.cap);
-                a.lap_col[q] = j;
-                if (MIXED) {
-                    a.lap_v32[q] = cf.h;
-                    a.lap_vlo[q] = cf.l;
-                } else {
+                const double rs = rsqrt(rr2);
+                if (tn) nd += fma(a.rn.re, rs, -1.0);
+                if (tl) {
+                    const double cd = a.coef_ppe * fma(a.rl.re, rs, -1.0);
+                    dg += cd;
+                    const size_t q = sell(i, out_l++, a.cap);
+                    a.lap_col[q] = j;
                     a.lap_v64[q] = cd;
                 }
-                out_l++;
             }
-        }
-        if (MIXED) {
-            nd = ff_to_double_fast(ndf);
-            dg = ff_to_double_fast(dgf);
         }
         surf = nd < a.beta * a.n0;
         ppe = !surf;
@@ -392,6 +421,8 @@ void launch_predict_rows(Ctx* c) {
     a.pos32lo = c->pos32lo;
     a.pos = c->pos;
     a.pos_b = c->pos_b;
+    a.rows = c->rows_f;
+    a.nrows = c->scan_f + c->n;
     a.vel = c->vel;
     a.vel32 = c->vel32;
     a.type = c->type;
@@ -424,6 +455,8 @@ void launch_build_rows(Ctx* c) {
     a.cap = c->cap;
     a.cap_n = c->cap_n;
     a.pressure_mode = P.pressure_mode;
+    a.rows = c->rows_fw;
+    a.nrows = c->scan_fw + c->n;
     a.vcol = c->vl_col;
     a.vcnt = c->vl_cnt;
     a.pos32 = c->pos32_star;

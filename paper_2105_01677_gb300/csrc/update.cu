@@ -132,9 +132,11 @@ __global__ void __launch_bounds__(kBT)
     k_gradient(int n, const int8_t* type, const double4* ps, const float4* ps32, const double4* us,
                const double* p, const double* phat, const int32_t* ncol, const int32_t* ncnt,
                int cap_n, double re, float re_f, double coef_grad, double dt, double rho,
-               double4* pos, double4* vel, Keep kp) {
-    int i = blockIdx.x * kBT + threadIdx.x;
-    const bool act = i < n && type[i] == kFluid;
+               double4* pos, double4* vel, const int32_t* rows, const uint32_t* nrows, Keep kp) {
+    // one thread per FLUID row (the bucket build's list of FLUID slots)
+    const int tid = blockIdx.x * kBT + threadIdx.x;
+    const int i = tid < (int)*nrows ? rows[tid] : -1;
+    const bool act = i >= 0;
     if (kp.pos_b == nullptr && !act) return;
     double disp = 0.0;
     if (act) disp = gradient_row<MIXED>(i, type, ps, ps32, us, p, phat, ncol, ncnt, cap_n, re, re_f,
@@ -241,12 +243,12 @@ void launch_gradient_correct(Ctx* c) {
         k_gradient<true><<<nb, kBT, 0, c->stream>>>(n, c->type, c->pos_star, c->pos32_star, c->vel_star,
                                                     c->p, c->phat, c->nb_n_col, c->nb_n_cnt, c->cap_n,
                                                     c->r_n.re, c->r_n.re_f, c->coef_grad, P.dt, P.rho,
-                                                    c->pos, c->vel, kp);
+                                                    c->pos, c->vel, c->rows_f, c->scan_f + c->n, kp);
     else
         k_gradient<false><<<nb, kBT, 0, c->stream>>>(n, c->type, c->pos_star, c->pos32_star, c->vel_star,
                                                      c->p, c->phat, c->nb_n_col, c->nb_n_cnt, c->cap_n,
                                                      c->r_n.re, c->r_n.re_f, c->coef_grad, P.dt, P.rho,
-                                                     c->pos, c->vel, kp);
+                                                     c->pos, c->vel, c->rows_f, c->scan_f + c->n, kp);
     k_copy_back<<<nb, kBT, 0, c->stream>>>(n, c->type, c->pos_star, c->vel_star, c->pos, c->vel);
     c->launches += 2;
 }
