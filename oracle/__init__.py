@@ -53,7 +53,8 @@ class Params(C.Structure):
                 ("gamma", C.c_double), ("alpha_c", C.c_double), ("cg_tol", C.c_double),
                 ("cg_max_iter", C.c_int32), ("clamp_negative_p", C.c_int32),
                 ("cell_skin", C.c_double), ("box_min", C.c_double * 3),
-                ("box_max", C.c_double * 3)]
+                ("box_max", C.c_double * 3), ("rho_i", C.POINTER(C.c_double)),
+                ("nu_i", C.POINTER(C.c_double))]
 
 
 class Report(C.Structure):
@@ -134,6 +135,9 @@ class StepParams:
     cell_skin: float = 0.1
     box_min: tuple = (0.0, 0.0, 0.0)
     box_max: tuple = (1.0, 1.0, 0.0)
+    # two-phase flow (Sec. 3.2.1): per-particle density / viscosity in particle order
+    rho_i: np.ndarray | None = None
+    nu_i: np.ndarray | None = None
 
     @property
     def re_n(self):
@@ -157,6 +161,15 @@ class StepParams:
         P.cg_max_iter = self.cg_max_iter if self.cg_max_iter > 0 else 10 * n
         P.clamp_negative_p = self.clamp_negative_p
         P.cell_skin = self.cell_skin
+        # the arrays stay referenced by this StepParams while the struct is in use
+        for name in ("rho_i", "nu_i"):
+            a = getattr(self, name)
+            if a is not None:
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                if a.shape != (n,):
+                    raise ValueError(f"{name} must have one value per particle")
+                setattr(self, name, a)
+                setattr(P, name, _p(a, C.c_double))
         return P
 
 

@@ -49,7 +49,14 @@ typedef struct {
     int32_t clamp_negative_p;
     double cell_skin;
     double box_min[3], box_max[3];
+    /* Two-phase (multi-density, multi-viscosity) flow, Sec. 3.2.1: per-particle density  */
+    /* and kinematic viscosity in particle order, or NULL for the uniform rho and nu.    */
+    const double* rho_i;
+    const double* nu_i;
 } orc_params;
+
+static double rho_of(const orc_params* p, int64_t i) { return p->rho_i ? p->rho_i[i] : p->rho; }
+static double nu_of(const orc_params* p, int64_t i) { return p->nu_i ? p->nu_i[i] : p->nu; }
 
 typedef struct {
     int32_t cg_iters;
@@ -468,11 +475,15 @@ static int in_ppe(const int8_t* type, const uint8_t* flags, int64_t i) {
     return (type[i] == ORC_FLUID || type[i] == ORC_WALL) && !(flags[i] & 1);
 }
 
+/* Two-phase (per-particle densities given): the 1/rho of the Laplacian becomes the pair */
+/* factor 2/(rho_i + rho_j) (the reciprocal of the pair's mean density), which keeps A    */
+/* symmetric:  c_ij = (2d/(n0_lap lambda)) (2/(rho_i + rho_j)) w(r_ij).                   */
 static int assemble_ppe(const orc_params* p, int64_t n, const double* pos, const int8_t* type,
                         const uint8_t* flags, const csr_t* nb_lap, double n0_lap, double lambda,
                         mat_t* A) {
     int dim = p->dim;
     double coef = (2.0 * dim) / (n0_lap * lambda * p->rho);
+    double coef0 = (2.0 * dim) / (n0_lap * lambda);
     A->off = calloc((size_t)n + 1, sizeof(int64_t));
     if (!A->off) return ORC_ENOMEM;
     for (int64_t i = 0; i < n; i++) {
@@ -499,7 +510,8 @@ static int assemble_ppe(const orc_params* p, int64_t n, const double* pos, const
             if (type[j] == ORC_DUMMY) continue;
             double xj, yj, zj;
             coords(pos, dim, j, &xj, &yj, &zj);
-            double c = coef * weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), p->re_lap);
+            double w = weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), p->re_lap);
+            double c = p->rho_i ? (coef0 * (2.0 / (p->rho_i[i] + p->rho_i[j]))) * w : coef * w;
             diag = diag + c;
             if (in_ppe(type, flags, j)) {
                 A->col[k] = (int32_t)j;
@@ -604,10 +616,12 @@ int orc_dense_spd_solve(int64_t n, double* a, const double* b, double* x) {
 
 /* ------------------------------------------------------------------------------------ */
 /* Weakly-compressible pressure, Eq. 16: p = rho c0^2/gamma ((n* / n0)^gamma - 1) on    */
-/* FLUID/WALL particles not on the free surface; 0 elsewhere.                           */
+/* FLUID/WALL particles not on the free surface; 0 elsewhere.  Two-phase (Sec. 3.2.1):   */
+/* p_i = rho_i alpha_i with alpha_i = c0^2/gamma ((n*_i/n0)^gamma - 1), the particle's  */
+/* own density.                                                                          */
 /* ------------------------------------------------------------------------------------ */
-static double wc_pressure(const orc_params* p, double nstar, double n0) {
-    return p->rho * p->c0 * p->c0 / p->gamma * (pow(nstar / n0, p->gamma) - 1.0);
+static double wc_pressure(const orc_params* p, double rho, double nstar, double n0) {
+    return rho * p->c0 * p->c0 / p->gamma * (pow(nstar / n0, p->gamma) - 1.0);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -620,7 +634,10 @@ static double wc_pressure(const orc_params* p, double nstar, double n0) {
 /*  4. pressure: PPE (Eq. 13, assembled as above, CG) or equation of state (Eq. 16);    */
 /*  5. PPE: negative pressure clamped to 0 (optional); p_hat_i = min over i and its     */
 /*     non-DUMMY neighbours within re_n.  Equation of state: p_hat_i = p_i;             */
-/*  6. correction: FLUID u' = -(dt/rho) grad p (gradient above, re_n, at r*);           */
+/*  6. correction: FLUID u' = -(dt/rho) grad p (gradient above, re_n, at r*); two-phase */
+/*     u' = -(dt/rho_i) grad p, the multi-density pressure term of Sec. 3.2.1 (with       */
+/*     p_j = rho_j alpha_j the bracket (rho_j/rho_i) alpha_j - alpha_i is (p_j - p_i)/rho_i);*/
+/*     the viscosity of step 2 is the particle's own nu_i.                                */
 /*     u = u* + u', r = r* + dt u'.                                                      */
 /* ------------------------------------------------------------------------------------ */
 
@@ -668,7 +685,7 @@ static int stage_predict(const orc_params* p, int64_t n, const double* pos, cons
             for (int a = 0; a < dim; a++) {
                 int64_t q = i * dim + a;
                 if (type[i] == ORC_FLUID) {
-                    us[q] = vel[q] + p->dt * (p->nu * lap[q] + p->g[a]);
+                    us[q] = vel[q] + p->dt * (nu_of(p, i) * lap[q] + p->g[a]);
                     ps[q] = pos[q] + p->dt * us[q];
                 } else {
                     us[q] = vel[q];
@@ -724,6 +741,10 @@ static int check_params(const orc_params* p, int64_t n) {
     if ((dim != 2 && dim != 3) || n <= 0 || !(p->l0 > 0) || !(p->re_n > 0) || !(p->re_lap > 0) ||
         !(p->rho > 0) || !(p->dt > 0) || !(p->cell_skin >= 0))
         return ORC_EINVAL;
+    for (int64_t i = 0; i < n; i++) {
+        if (p->rho_i && !(p->rho_i[i] > 0.0 && isfinite(p->rho_i[i]))) return ORC_EINVAL;
+        if (p->nu_i && !(p->nu_i[i] >= 0.0 && isfinite(p->nu_i[i]))) return ORC_EINVAL;
+    }
     return ORC_OK;
 }
 
@@ -779,7 +800,7 @@ int orc_step(const orc_params* p, int64_t n, double* pos, double* vel, int8_t* t
         }
     } else {                                                            /* 4, 5: EOS */
         for (int64_t i = 0; i < n; i++) {
-            pres[i] = in_ppe(type, flags, i) ? wc_pressure(p, nstar[i], n0) : 0.0;
+            pres[i] = in_ppe(type, flags, i) ? wc_pressure(p, rho_of(p, i), nstar[i], n0) : 0.0;
             phat[i] = pres[i];
         }
     }
@@ -790,7 +811,7 @@ int orc_step(const orc_params* p, int64_t n, double* pos, double* vel, int8_t* t
         for (int a = 0; a < dim; a++) {
             int64_t q = i * dim + a;
             if (type[i] == ORC_FLUID) {
-                double du = -(p->dt / p->rho) * grad[q];
+                double du = -(p->dt / rho_of(p, i)) * grad[q];
                 vel[q] = us[q] + du;
                 pos[q] = ps[q] + p->dt * du;
             }

@@ -149,6 +149,23 @@ def dam_break_3d(seed: int = 1, l0: float = 0.0075, jitter: float = 1e-4,
                       seed=seed, jitter=jitter)
 
 
+def two_phase(scene: Scene, rho=(1000.0, 800.0), nu=(1e-6, 5e-6)):
+    """Per-particle density and kinematic viscosity of a two-layer fluid (material inputs of
+    the multi-density model, Sec. 3.2.1): fluid lattice layers whose centres lie in the lower
+    half of the column are phase 0 (rho[0], nu[0]), the others phase 1; walls and dummies
+    take phase 0's values.  Returns (rho, nu) arrays in particle order."""
+    up = scene.dim - 1
+    f = scene.types == FLUID
+    h = scene.pos[f, up]
+    base = h.min() - 0.5 * scene.l0          # bottom of the column (lattice sites at +l0/2)
+    layers = int(round((h.max() - h.min()) / scene.l0)) + 1
+    split = base + 0.5 * layers * scene.l0 + 0.25 * scene.l0   # between two layer centres
+    upper = f & (scene.pos[:, up] > split)
+    rho_i = np.where(upper, rho[1], rho[0]).astype(np.float64)
+    nu_i = np.where(upper, nu[1], nu[0]).astype(np.float64)
+    return rho_i, nu_i
+
+
 def still_tank_2d(l0: float = 0.01, width: float = 0.2, depth: float = 0.2, seed: int = 1,
                   jitter: float = 0.0) -> Scene:
     """Fluid at rest filling the full width of a 2D tank (hydrostatic check)."""
