@@ -174,6 +174,21 @@ int mps_read_state(mps_ctx* ctx, double* pos, double* vel, double* p, double* n_
  * them).  Same checks as mps_create.  Used to restart from a saved state. */
 int mps_write_state(mps_ctx* ctx, const double* pos, const double* vel, const int8_t* types);
 
+/* Two-phase (multi-density, multi-viscosity) flow of Sec. 3.2.1: a density rho_i [kg/m^3]
+ * and a kinematic viscosity nu_i [m^2/s] per particle, n doubles each in the original
+ * particle order (copied; the caller keeps its arrays).  NULL leaves that property uniform
+ * (params->rho or params->nu); both NULL returns to single-phase flow.  With densities:
+ *   equation of state (Eq. 16)   p_i = rho_i c0^2/gamma ((n*_i/n0)^gamma - 1);
+ *   pressure correction          u'_i = -(dt/rho_i) grad p_i  (the multi-density pressure
+ *                                term, (rho_j/rho_i) alpha_j - alpha_i = (p_j - p_i)/rho_i);
+ *   PPE (Eq. 13, Listing 2)      c_ij = 2d/(n0 lambda) * 2/(rho_i + rho_j) * w(r_ij), the
+ *                                1/rho of one phase replaced by the pair's mean density;
+ * with viscosities the prediction uses the particle's own nu_i.  The properties stay with
+ * their particles across steps and mps_write_state.
+ * Errors: MPS_EINVAL (a density not finite and > 0, a viscosity not finite and >= 0, or
+ * densities with the matrix-free inner operator, ppe_operator 1), MPS_ENOMEM. */
+int mps_set_fluid_properties(mps_ctx* ctx, const double* rho, const double* nu);
+
 /* Cell key of every particle at the current positions (original order): the Morton code
  * (x in bit 0) of c = floor((x - box_min)/h) per axis, or 0xFFFFFFFF for a particle outside
  * the grid or a GHOST.  Bit-exact with the floor definition. */

@@ -285,6 +285,7 @@ int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* typ
     else if (!have_state) MPS_CUDA(c, cudaMemsetAsync(d_vel, 0, n * dim * sizeof(double), c->stream));
     if (types) MPS_CUDA(c, cudaMemcpyAsync(d_t, types, n, cudaMemcpyHostToDevice, c->stream));
     launch_ingest(c, d_pos, d_vel, d_t, false, false);
+    launch_gather_props(c);   // slot = id again
     MPS_CUDA(c, cudaGetLastError());
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
     return MPS_OK;
@@ -562,6 +563,53 @@ int mps_write_state(mps_ctx* c, const double* pos, const double* vel, const int8
     DeviceGuard dg(c->prm.device);
     if (!dg.ok) return MPS_EDEVICE;
     return upload_state(c, pos, vel, types, true);
+}
+
+int mps_set_fluid_properties(mps_ctx* c, const double* rho, const double* nu) {
+    if (!c) return MPS_EINVAL;
+    const int64_t n = c->n;
+    if (rho) {
+        if (c->prm.pressure_mode == 0 && c->prm.ppe_operator == 1) return MPS_EINVAL;
+        for (int64_t i = 0; i < n; i++)
+            if (!(std::isfinite(rho[i]) && rho[i] > 0.0)) return MPS_EINVAL;
+    }
+    if (nu)
+        for (int64_t i = 0; i < n; i++)
+            if (!(std::isfinite(nu[i]) && nu[i] >= 0.0)) return MPS_EINVAL;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    const size_t bytes = (size_t)n * sizeof(double);
+    int rc;
+    if (rho) {
+        if (!c->rho_id) {
+            if ((rc = alloc_dev(c, &c->rho_id, (size_t)n)) || (rc = alloc_dev(c, &c->rho_s, (size_t)n)) ||
+                (rc = alloc_dev(c, &c->rho_ff, (size_t)n)))
+                return rc;
+        }
+        MPS_CUDA(c, cudaMemcpyAsync(c->rho_id, rho, bytes, cudaMemcpyHostToDevice, c->stream));
+    } else if (c->rho_id) {
+        free_one(c, c->rho_id);
+        free_one(c, c->rho_s);
+        free_one(c, c->rho_ff);
+        c->rho_id = c->rho_s = nullptr;
+        c->rho_ff = nullptr;
+    }
+    if (nu) {
+        if (!c->nu_id) {
+            if ((rc = alloc_dev(c, &c->nu_id, (size_t)n)) || (rc = alloc_dev(c, &c->nu_s, (size_t)n)))
+                return rc;
+        }
+        MPS_CUDA(c, cudaMemcpyAsync(c->nu_id, nu, bytes, cudaMemcpyHostToDevice, c->stream));
+    } else if (c->nu_id) {
+        free_one(c, c->nu_id);
+        free_one(c, c->nu_s);
+        c->nu_id = c->nu_s = nullptr;
+    }
+    launch_gather_props(c);
+    MPS_CUDA(c, cudaGetLastError());
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MPS_OK;
 }
 
 int mps_debug_cells(mps_ctx* c, uint32_t* cell_key) {

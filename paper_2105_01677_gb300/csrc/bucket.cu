@@ -233,6 +233,7 @@ int bucket_build(Ctx* c, bool mutate) {
     c->launches += 2 + scan_exclusive(c->mark_f, c->scan_f, n, true, c->scan_scratch, s);
     c->launches += scan_exclusive(c->mark_fw, c->scan_fw, n, true, c->scan_scratch, s);
     k_scatter_rows<<<nb1, kBT, 0, s>>>(n, c->type, c->scan_f, c->scan_fw, c->rows_f, c->rows_fw);
+    launch_gather_props(c);   // two-phase properties follow their particles
     MPS_CUDA(c, cudaGetLastError());
     return MPS_OK;
 }

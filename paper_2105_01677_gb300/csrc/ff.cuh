@@ -195,6 +195,17 @@ __device__ __forceinline__ ff2 ff2_rsqrt1(ff2 x) {
     return ff2_rsqrt_step(x, y0);
 }
 
+// 2/x for x > 0: the correctly rounded FP32 reciprocal y0 of x.h and one Newton step
+// y = y0 + y0 (1 - x y0) with the residual formed from an exact product (relative error
+// ~1e-14), doubled exactly
+__device__ __forceinline__ ff2 ff2_two_over(ff2 x) {
+    const float2 y0 = make_float2(__frcp_rn(x.h.x), __frcp_rn(x.h.y));
+    const ff2 t = ff2_two_prod(x.h, y0);
+    const float2 e = sub2(sub2(sub2(f2(1.0f), t.h), t.l), mul2(x.l, y0));
+    const ff2 y = ff2_add_f({y0, f2(0.f)}, mul2(y0, e));
+    return {add2(y.h, y.h), add2(y.l, y.l)};
+}
+
 __device__ __forceinline__ ff ff2_lo(const ff2& a) { return {a.h.x, a.l.x}; }
 __device__ __forceinline__ ff ff2_hi(const ff2& a) { return {a.h.y, a.l.y}; }
 

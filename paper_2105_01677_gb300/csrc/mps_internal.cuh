@@ -134,6 +134,7 @@ __device__ __forceinline__ void split_rel(double x, double xmin, float* hi, floa
     *lo = (float)(r - (double)h);
 }
 void launch_unpermute_u32(Ctx* c, const uint32_t* in, uint32_t* out);
+void launch_gather_props(Ctx* c);
 
 // ---------------------------------------------------------------- context
 struct Ctx {
@@ -196,6 +197,11 @@ struct Ctx {
     uint32_t* cell_count;
     int32_t* cell_start;
     uint32_t* occ;         // occupied cell codes
+    // two-phase flow: per-particle density / viscosity in original order (as given) and in
+    // slot order (gathered by id after every reordering); null when uniform
+    double *rho_id = nullptr, *nu_id = nullptr;
+    double *rho_s = nullptr, *nu_s = nullptr;
+    float2* rho_ff = nullptr;   // slot-order density as float-float (hi, lo)
     // active rows in slot order, rebuilt with every bucket build: FLUID slots (rows_f) and
     // FLUID or WALL slots (rows_fw); their counts sit after the exclusive scans
     uint32_t *mark_f, *mark_fw, *scan_f, *scan_fw;   // n + 1 each

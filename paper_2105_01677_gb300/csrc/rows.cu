@@ -78,6 +78,7 @@ struct PredictArgs {
     const double4* pos_b;   // where the candidate lists were gathered (r^k when gathered this step)
     const int32_t* rows;    // FLUID slots in slot order
     const uint32_t* nrows;  // their count
+    const double* nu_s;     // two-phase: per-slot viscosity (null: nu)
     const double4* vel;
     const float4* vel32;
     const int8_t* type;
@@ -152,9 +153,10 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
         // u* = u + dt (nu lap(u) + g); r* = r + dt u*  (one rounding per operation)
         const double l0 = a.coef_lap * s0, l1 = a.coef_lap * s1, l2 = a.coef_lap * s2;
         double4 us, ps;
-        us.x = __dadd_rn(ui.x, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(a.nu, l0), a.g0)));
-        us.y = __dadd_rn(ui.y, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(a.nu, l1), a.g1)));
-        us.z = __dadd_rn(ui.z, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(a.nu, l2), a.g2)));
+        const double nu = a.nu_s ? a.nu_s[i] : a.nu;
+        us.x = __dadd_rn(ui.x, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(nu, l0), a.g0)));
+        us.y = __dadd_rn(ui.y, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(nu, l1), a.g1)));
+        us.z = __dadd_rn(ui.z, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(nu, l2), a.g2)));
         us.w = 0.0;
         ps.x = __dadd_rn(pi.x, __dmul_rn(a.dt, us.x));
         ps.y = __dadd_rn(pi.y, __dmul_rn(a.dt, us.y));
@@ -187,6 +189,11 @@ struct BuildArgs {
     int n, cap_v, cap, cap_n, pressure_mode;
     const int32_t* rows;    // FLUID and WALL slots in slot order
     const uint32_t* nrows;  // their count
+    // two-phase: per-slot density (FP64 and float-float) or null; the PPE coefficient then
+    // takes coef0 = 2d/(n0 lambda) times the pair factor 2/(rho_i + rho_j)
+    const double* rho_s;
+    const float2* rho_ff;
+    double coef0, wc_c;     // wc_c = c0^2/gamma
     const int32_t* vcol;
     const int32_t* vcnt;
     const float4* pos32;     // r*
@@ -310,6 +317,7 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
             const ff2 ren = {f2(a.rn.re_f), f2(a.rn.re_l)};
             const ff2 cre = {f2(a.cre_ff.h), f2(a.cre_ff.l)};
             const ff2 ncoef = {f2(a.ncoef_ff.h), f2(a.ncoef_ff.l)};
+            const float2 rhoi = a.rho_ff ? a.rho_ff[i] : make_float2(0.f, 0.f);
             // the entries of the next pair are loaded one iteration ahead (each slot is
             // read before the compaction can write it: writes go to slots <= t + 1)
             int n0 = m_all > 0 ? a.lap_col[sell(i, slot_of(0), a.cap)] : 0;
@@ -338,7 +346,12 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                 ff2 w = {f2(0.f), f2(0.f)};
                 if (tn0 || tn1) w = ff2_add_f(ff2_mul(ren, ff2_rsqrt_step(r2, y)), f2(-1.f));
                 // c = coef (re/r - 1) = (coef re) y - coef
-                const ff2 c = ff2_add(ff2_mul(cre, y), ncoef);
+                ff2 c = ff2_add(ff2_mul(cre, y), ncoef);
+                if (a.rho_ff) {   // two-phase: times 2/(rho_i + rho_j)
+                    const float2 q0 = a.rho_ff[j0], q1 = a.rho_ff[j1];
+                    c = ff2_mul(c, ff2_two_over(ff2_add({f2(rhoi.x), f2(rhoi.y)},
+                                                        {make_float2(q0.x, q1.x), make_float2(q0.y, q1.y)})));
+                }
                 acc = ff2_add(acc, {make_float2(tn0 ? w.h.x : 0.f, tl0 ? c.h.x : 0.f),
                                     make_float2(tn0 ? w.l.x : 0.f, tl0 ? c.l.x : 0.f)});
                 acc = ff2_add(acc, {make_float2(tn1 ? w.h.y : 0.f, tl1 ? c.h.y : 0.f),
@@ -373,7 +386,9 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                 const double rs = rsqrt(rr2);
                 if (tn) nd += fma(a.rn.re, rs, -1.0);
                 if (tl) {
-                    const double cd = a.coef_ppe * fma(a.rl.re, rs, -1.0);
+                    const double cd =
+                        a.rho_s ? (a.coef0 * (2.0 / (a.rho_s[i] + a.rho_s[j]))) * fma(a.rl.re, rs, -1.0)
+                                : a.coef_ppe * fma(a.rl.re, rs, -1.0);
                     dg += cd;
                     const size_t q = sell(i, out_l++, a.cap);
                     a.lap_col[q] = j;
@@ -392,7 +407,10 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
         a.lap_cnt[i] = out_l;
         a.n_cnt[i] = min(out_n, a.cap_n);
         if (overflow || out_n > a.cap_n) atomicOr(&a.st->err, kErrCap);
-        if (a.pressure_mode == 1) a.p[i] = ppe ? a.wc_k * (pow(nd / a.n0, a.gamma) - 1.0) : 0.0;
+        if (a.pressure_mode == 1) {
+            const double k = a.rho_s ? a.rho_s[i] * a.wc_c : a.wc_k;   // rho_i c0^2 / gamma
+            a.p[i] = ppe ? k * (pow(nd / a.n0, a.gamma) - 1.0) : 0.0;
+        }
         n_lap = (unsigned)out_l;
         n_pnd = (unsigned)m_f;
     }
@@ -423,6 +441,7 @@ void launch_predict_rows(Ctx* c) {
     a.pos_b = c->pos_b;
     a.rows = c->rows_f;
     a.nrows = c->scan_f + c->n;
+    a.nu_s = c->nu_s;
     a.vel = c->vel;
     a.vel32 = c->vel32;
     a.type = c->type;
@@ -457,6 +476,10 @@ void launch_build_rows(Ctx* c) {
     a.pressure_mode = P.pressure_mode;
     a.rows = c->rows_fw;
     a.nrows = c->scan_fw + c->n;
+    a.rho_s = c->rho_s;
+    a.rho_ff = c->rho_ff;
+    a.coef0 = c->coef_lap;   // 2d/(n0_lap lambda), the Laplacian's coefficient
+    a.wc_c = P.c0 * P.c0 / P.gamma;
     a.vcol = c->vl_col;
     a.vcnt = c->vl_cnt;
     a.pos32 = c->pos32_star;
@@ -467,8 +490,10 @@ void launch_build_rows(Ctx* c) {
     a.rn = c->r_n;
     a.rl = c->r_lap;
     a.coef_ppe = c->coef_ppe;
-    a.cre_ff = ff_from_double(c->coef_ppe * c->r_lap.re);
-    a.ncoef_ff = ff_from_double(-c->coef_ppe);
+    // the coefficient without the pair factor when densities are per particle
+    const double cpf = c->rho_s ? c->coef_lap : c->coef_ppe;
+    a.cre_ff = ff_from_double(cpf * c->r_lap.re);
+    a.ncoef_ff = ff_from_double(-cpf);
     a.n0 = c->n0_pnd;
     a.beta = P.beta;
     a.inv_dt2 = c->inv_dt2;

@@ -38,9 +38,11 @@ __global__ void __launch_bounds__(kBT) k_clamp_store(int n, double* p) {
     if (i < n) p[i] = fmax(p[i], 0.0);
 }
 
-// Candidate lists kept across steps: the update also refreshes the FP32 copies of r, u
-// and measures r^{k+1} against the positions r_b the lists were gathered at.
+// Per-row extras of the update: the two-phase density, and for candidate lists kept across
+// steps the refresh of the FP32 copies of r, u and r^{k+1} measured against the positions
+// r_b the lists were gathered at.
 struct Keep {
+    const double* rho_s;    // two-phase: per-slot density (null: the uniform rho)
     const double4* pos_b;   // null: lists are gathered every step (nothing else is used)
     float4* pos32;
     float4* pos32lo;
@@ -95,7 +97,7 @@ __device__ __forceinline__ double gradient_row(int i, const int8_t* type, const 
             g2 = fma(f, dz, g2);
         }
     }
-    const double k = -(dt / rho) * coef_grad;
+    const double k = -(dt / (kp.rho_s ? kp.rho_s[i] : rho)) * coef_grad;
     const double4 u = us[i];
     const double d0 = k * g0, d1 = k * g1, d2 = k * g2;
     const double4 un = make_double4(u.x + d0, u.y + d1, u.z + d2, 0.0);
@@ -216,6 +218,22 @@ __global__ void __launch_bounds__(kBT)
     pos32[s] = h;
     pos32lo[s] = l;
 }
+// two-phase properties into slot order (slot s holds particle id[s]); the density also as
+// float-float for the pair factors of the mixed build
+__global__ void __launch_bounds__(kBT)
+    k_gather_props(int n, const int32_t* id, const double* rho_id, const double* nu_id,
+                   double* rho_s, double* nu_s, float2* rho_ff) {
+    int s = blockIdx.x * kBT + threadIdx.x;
+    if (s >= n) return;
+    const int q = id[s];
+    if (rho_id) {
+        const double r = rho_id[q];
+        const float h = (float)r;
+        rho_s[s] = r;
+        rho_ff[s] = make_float2(h, (float)(r - (double)h));
+    }
+    if (nu_id) nu_s[s] = nu_id[q];
+}
 }  // namespace
 
 void launch_clamp_pmin(Ctx* c) {
@@ -233,6 +251,7 @@ void launch_gradient_correct(Ctx* c) {
     const int nb = (n + kBT - 1) / kBT;
     const mps_params& P = c->prm;
     Keep kp;
+    kp.rho_s = c->rho_s;
     kp.pos_b = c->pos_b;
     kp.pos32 = c->pos32;
     kp.pos32lo = c->pos32lo;
@@ -259,6 +278,14 @@ void launch_unpermute(Ctx* c, double* d_pos, double* d_vel, double* d_p, double*
     k_unpermute<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(n, c->dim, c->id, c->pos, c->vel, c->p,
                                                              c->nstar, c->flag, c->type, d_pos, d_vel,
                                                              d_p, d_nstar, d_flags, d_types);
+    c->launches += 1;
+}
+
+void launch_gather_props(Ctx* c) {
+    if (!c->rho_id && !c->nu_id) return;
+    const int n = (int)c->n;
+    k_gather_props<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(n, c->id, c->rho_id, c->nu_id,
+                                                               c->rho_s, c->nu_s, c->rho_ff);
     c->launches += 1;
 }
 

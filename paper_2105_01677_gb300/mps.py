@@ -58,7 +58,7 @@ class mps_report(C.Structure):
 EXPORTS = ("mps_params_default", "mps_create", "mps_step", "mps_solve_ppe", "mps_read_state",
            "mps_write_state", "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants",
            "mps_set_profiling", "mps_get_profile", "mps_ppe_cg_noalloc", "mps_destroy",
-           "mps_strerror")
+           "mps_strerror", "mps_set_fluid_properties")
 NOALLOC_MAX_ROWS = 262144
 STAGES = ("bucket", "gather", "predict", "build", "ppe", "update")
 
@@ -89,6 +89,7 @@ def lib(build_if_missing: bool = False):
     L.mps_solve_ppe.argtypes = [C.c_void_p, C.POINTER(mps_report)]
     L.mps_read_state.argtypes = [C.c_void_p, d, d, d, d, u8, i8]
     L.mps_write_state.argtypes = [C.c_void_p, d, d, i8]
+    L.mps_set_fluid_properties.argtypes = [C.c_void_p, d, d]
     L.mps_debug_cells.argtypes = [C.c_void_p, C.POINTER(C.c_uint32)]
     L.mps_debug_neighbors.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int32), C.c_int64]
@@ -104,7 +105,7 @@ def lib(build_if_missing: bool = False):
     L.mps_strerror.restype = C.c_char_p
     for f in ("mps_create", "mps_step", "mps_solve_ppe", "mps_read_state", "mps_write_state",
               "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants", "mps_set_profiling",
-              "mps_get_profile", "mps_ppe_cg_noalloc"):
+              "mps_get_profile", "mps_ppe_cg_noalloc", "mps_set_fluid_properties"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -247,6 +248,17 @@ def mps_write_state(h, pos, vel=None, types=None):
                                  _ptr(types, C.c_int8)), "mps_write_state")
 
 
+def mps_set_fluid_properties(h, rho=None, nu=None, check: bool = True):
+    """Per-particle density / viscosity (original order) of a two-phase flow; None keeps that
+    property uniform.  Returns the status."""
+    rho = None if rho is None else np.ascontiguousarray(rho, np.float64)
+    nu = None if nu is None else np.ascontiguousarray(nu, np.float64)
+    rc = lib().mps_set_fluid_properties(h, _ptr(rho, C.c_double), _ptr(nu, C.c_double))
+    if check:
+        _check(rc, "mps_set_fluid_properties")
+    return rc
+
+
 def mps_debug_cells(h, n: int):
     out = np.empty(n, np.uint32)
     _check(lib().mps_debug_cells(h, _ptr(out, C.c_uint32)), "mps_debug_cells")
@@ -306,7 +318,8 @@ def mps_destroy(h):
 class Simulation:
     """Convenience owner of one context built from a scene-like object."""
 
-    def __init__(self, scene, torch_alloc: bool = False, use_torch_stream: bool = False, **params):
+    def __init__(self, scene, torch_alloc: bool = False, use_torch_stream: bool = False,
+                 rho_i=None, nu_i=None, **params):
         self.n, self.dim = scene.n, scene.dim
         g = (0.0, -9.81, 0.0) if scene.dim == 2 else (0.0, 0.0, -9.81)
         base = dict(dim=scene.dim, l0=scene.l0, re_n=2.1 * scene.l0, re_lap=4.0 * scene.l0, g=g,
@@ -315,6 +328,11 @@ class Simulation:
         self.params = mps_params_default(**base)
         self.h = mps_create(scene.pos, scene.vel, scene.types, self.params, torch_alloc,
                             use_torch_stream)
+        if rho_i is not None or nu_i is not None:
+            self.set_fluid_properties(rho_i, nu_i)
+
+    def set_fluid_properties(self, rho=None, nu=None, check: bool = True):
+        return mps_set_fluid_properties(self.h, rho, nu, check)
 
     def step(self, nsteps: int = 1, check: bool = True):
         return mps_step(self.h, nsteps, check)
