@@ -9,7 +9,8 @@ FP64 residual of 1e-8.  Synthetic seeded lattice with 1e-4 l0 jitter.
 The headline `value` is the mixed-precision path (FP32 pair terms and inner CG, FP64 number
 density, dot products and refinement); the plain FP64 path is timed on the same scene and
 reported under "fp64", and the mixed path with candidate lists kept for up to 4 steps
-under "kept_lists" (exact neighbour sets either way).  `e2e` repeats the mixed measurement through the C ABI with host
+under "kept_lists" (exact neighbour sets either way); the two-phase 3D dam break (Sec. 3.2.1,
+l0 = 0.004 m, 1,125,000 fluid particles) under "two_phase".  `e2e` repeats the mixed measurement through the C ABI with host
 buffers: every step uploads positions, velocities and kinds from pinned memory and reads
 back positions, velocities and pressure.
 
@@ -79,6 +80,9 @@ def parse():
                     help="with --only: keep candidate lists for up to this many steps")
     ap.add_argument("--kept-steps", type=int, default=None,
                     help="timed steps of the kept-list comparison (default: --steps)")
+    ap.add_argument("--two-phase-steps", type=int, default=20,
+                    help="timed steps of each two-phase path (0: skip)")
+    ap.add_argument("--two-phase-l0", type=float, default=0.004)
     return ap.parse_args()
 
 
@@ -302,6 +306,33 @@ def run_gb300(args):
     ms_k = max_over_ranks(ms_k)
     simk.close()
 
+    # ---- two-phase 3D dam break (light fluid over water in the same column geometry):
+    # equation-of-state and PPE paths, mixed precision
+    two_phase = None
+    if args.two_phase_steps > 0:
+        sc2 = scenes.dam_break_3d(seed=args.seed + rank, l0=args.two_phase_l0)
+        rho_i, nu_i = scenes.two_phase(sc2, rho=(1000.0, 800.0), nu=(1e-6, 5e-6))
+        two_phase = {"workload": f"3D two-phase dam break, l0={args.two_phase_l0} m, densities "
+                                 "1000/800 kg/m^3, nu 1e-6/5e-6 m^2/s (lower / upper half of the "
+                                 "column)", "particles": sc2.n, "fluid": sc2.n_fluid}
+        for name, mode in (("eos", 1), ("ppe", 0)):
+            k2 = args.two_phase_steps
+            sim2 = mps.Simulation(sc2, torch_alloc=True, use_torch_stream=True, precision=1,
+                                  pressure_mode=mode, c0=20.0, rho_i=rho_i, nu_i=nu_i, **common)
+            sim2.step(args.warmup)
+            barrier()
+            ms2, it2, prof2 = timed_steps(sim2, k2, profile=True)
+            barrier()
+            ms2 = max_over_ranks(ms2)
+            sim2.close()
+            two_phase[name] = {"value": world * sc2.n * k2 / (ms2 * 1e-3), "unit": UNIT,
+                               "ms_per_step": ms2 / k2, "steps": k2,
+                               "stage_ms_per_step": {k: prof2["stage_ms"][k] / k2
+                                                     for k in prof2["stage_ms"]}}
+            if mode == 0:
+                two_phase[name]["cg_iters_mean"] = float(np.mean([x[0] for x in it2]))
+        del sc2, rho_i, nu_i
+
     # ---- end to end through the C ABI with host buffers (mixed)
     ke = args.e2e_steps or args.steps
     pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
@@ -379,6 +410,7 @@ def run_gb300(args):
                                            if prof64["stage_calls"][k] else 0.0)
                                        for k in prof64["stage_ms"]}},
         "mixed_over_fp64": value / value64,
+        "two_phase": two_phase,
         "kept_lists": {"list_every": 4, "value": world * n * kk / (ms_k * 1e-3), "unit": UNIT,
                        "ms_per_step": ms_k / kk, "steps": kk,
                        "gathers": int(profk["stage_calls"]["gather"]),

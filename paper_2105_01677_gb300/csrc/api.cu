@@ -366,6 +366,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         MPS_CUDA(c, cudaMemsetAsync(c->nstar, 0, n * sizeof(double), c->stream));
         MPS_CUDA(c, cudaMemsetAsync(c->flag, 0, n, c->stream));
         MPS_CUDA(c, cudaMemsetAsync(c->diag, 0, n * sizeof(double), c->stream));
+        MPS_CUDA(c, cudaMemsetAsync(c->diag32, 0, n * sizeof(float), c->stream));
         MPS_CUDA(c, cudaMemsetAsync(c->bvec, 0, n * sizeof(double), c->stream));
         MPS_CUDA(c, cudaMemsetAsync(c->nb_lap_cnt, 0, n * sizeof(int32_t), c->stream));
         MPS_CUDA(c, cudaMemsetAsync(c->nb_n_cnt, 0, n * sizeof(int32_t), c->stream));
