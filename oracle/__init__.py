@@ -54,7 +54,8 @@ class Params(C.Structure):
                 ("cg_max_iter", C.c_int32), ("clamp_negative_p", C.c_int32),
                 ("cell_skin", C.c_double), ("box_min", C.c_double * 3),
                 ("box_max", C.c_double * 3), ("rho_i", C.POINTER(C.c_double)),
-                ("nu_i", C.POINTER(C.c_double))]
+                ("nu_i", C.POINTER(C.c_double)), ("kernel", C.c_int32), ("grad_form", C.c_int32),
+                ("source", C.c_int32), ("pad0", C.c_int32)]
 
 
 class Report(C.Structure):
@@ -73,16 +74,16 @@ def lib():
     if _lib is None:
         L = C.CDLL(build())
         d, i64, i32, vp = C.POINTER(C.c_double), C.c_int64, C.c_int32, C.c_void_p
-        L.orc_lattice.argtypes = [i32, C.c_double, C.c_double, d, d]
+        L.orc_lattice.argtypes = [i32, C.c_double, C.c_double, d, d, i32]
         L.orc_cell_keys.argtypes = [C.POINTER(Params), i64, d, C.POINTER(C.c_int8),
                                     C.POINTER(C.c_uint32), C.POINTER(C.c_int32)]
         L.orc_neighbors.argtypes = [i32, i64, d, C.POINTER(C.c_int8), C.c_double, i32,
                                     C.POINTER(C.c_int64), C.POINTER(C.c_int32), i64]
-        L.orc_pnd.argtypes = [i32, i64, d, C.POINTER(C.c_int8), C.c_double, i32, d]
+        L.orc_pnd.argtypes = [i32, i64, d, C.POINTER(C.c_int8), C.c_double, i32, d, i32]
         L.orc_laplacian.argtypes = [i32, i64, d, C.POINTER(C.c_int8), C.c_double, C.c_double,
-                                    C.c_double, d, i32, d]
+                                    C.c_double, d, i32, d, i32]
         L.orc_gradient.argtypes = [i32, i64, d, C.POINTER(C.c_int8), C.c_double, C.c_double,
-                                   d, d, d]
+                                   d, d, d, i32, i32]
         L.orc_step.argtypes = [C.POINTER(Params), i64, d, d, C.POINTER(C.c_int8), d, d,
                                C.POINTER(C.c_uint8), C.POINTER(Report), i32, i32]
         L.orc_ppe_system.argtypes = [C.POINTER(Params), i64, d, d, C.POINTER(C.c_int8),
@@ -138,6 +139,11 @@ class StepParams:
     # two-phase flow (Sec. 3.2.1): per-particle density / viscosity in particle order
     rho_i: np.ndarray | None = None
     nu_i: np.ndarray | None = None
+    # numerical options: kernel 0 (Eq. 4) / 1 (cubic WC kernel); gradient 0 (difference
+    # form) / 1 (CMPS, Eq. 18); PPE source 0 (Eq. 13) / 1 (HS, Eq. 21)
+    kernel: int = 0
+    grad_form: int = 0
+    source: int = 0
 
     @property
     def re_n(self):
@@ -161,6 +167,7 @@ class StepParams:
         P.cg_max_iter = self.cg_max_iter if self.cg_max_iter > 0 else 10 * n
         P.clamp_negative_p = self.clamp_negative_p
         P.cell_skin = self.cell_skin
+        P.kernel, P.grad_form, P.source = self.kernel, self.grad_form, self.source
         # the arrays stay referenced by this StepParams while the struct is in use
         for name in ("rho_i", "nu_i"):
             a = getattr(self, name)
@@ -181,9 +188,9 @@ def params_for(scene, **kw) -> StepParams:
     return StepParams(**base)
 
 
-def lattice(dim: int, l0: float, re: float):
+def lattice(dim: int, l0: float, re: float, kernel: int = 0):
     n0, lam = C.c_double(), C.c_double()
-    _check(lib().orc_lattice(dim, l0, re, C.byref(n0), C.byref(lam)), "lattice")
+    _check(lib().orc_lattice(dim, l0, re, C.byref(n0), C.byref(lam), kernel), "lattice")
     return n0.value, lam.value
 
 
@@ -218,36 +225,36 @@ def neighbors(dim, pos, types, re, mode=1):
     return off, ids[: off[-1]]
 
 
-def pnd(dim, pos, types, re, mode=1):
+def pnd(dim, pos, types, re, mode=1, kernel=0):
     pos = _arr(pos, np.float64)
     types = _arr(types, np.int8)
     out = np.empty(len(types), np.float64)
     _check(lib().orc_pnd(dim, len(types), _p(pos, C.c_double), _p(types, C.c_int8), re, mode,
-                         _p(out, C.c_double)), "pnd")
+                         _p(out, C.c_double), kernel), "pnd")
     return out
 
 
-def laplacian(dim, pos, types, re, n0, lam, phi):
+def laplacian(dim, pos, types, re, n0, lam, phi, kernel=0):
     pos = _arr(pos, np.float64)
     types = _arr(types, np.int8)
     phi = _arr(phi, np.float64)
     ncomp = 1 if phi.ndim == 1 else phi.shape[1]
     out = np.empty_like(phi)
     _check(lib().orc_laplacian(dim, len(types), _p(pos, C.c_double), _p(types, C.c_int8), re,
-                               n0, lam, _p(phi, C.c_double), ncomp, _p(out, C.c_double)),
-           "laplacian")
+                               n0, lam, _p(phi, C.c_double), ncomp, _p(out, C.c_double),
+                               kernel), "laplacian")
     return out
 
 
-def gradient(dim, pos, types, re, n0, p, phat):
+def gradient(dim, pos, types, re, n0, p, phat, kernel=0, form=0):
     pos = _arr(pos, np.float64)
     types = _arr(types, np.int8)
     p = _arr(p, np.float64)
     phat = _arr(phat, np.float64)
     out = np.zeros((len(types), dim), np.float64)
     _check(lib().orc_gradient(dim, len(types), _p(pos, C.c_double), _p(types, C.c_int8), re,
-                              n0, _p(p, C.c_double), _p(phat, C.c_double), _p(out, C.c_double)),
-           "gradient")
+                              n0, _p(p, C.c_double), _p(phat, C.c_double), _p(out, C.c_double),
+                              kernel, form), "gradient")
     return out
 
 

@@ -53,6 +53,11 @@ typedef struct {
     /* and kinematic viscosity in particle order, or NULL for the uniform rho and nu.    */
     const double* rho_i;
     const double* nu_i;
+    /* Numerical options of Sec. 3.1 / 3.3:                                               */
+    int32_t kernel;          /* 0: w of Eq. 4 (re/r - 1); 1: the WC kernel (1 - r/re)^3     */
+    int32_t grad_form;       /* 0: difference form with p_hat_i; 1: CMPS, Eq. 18           */
+    int32_t source;          /* PPE source: 0: Eq. 13 (density deviation); 1: HS, Eq. 21   */
+    int32_t pad0;
 } orc_params;
 
 static double rho_of(const orc_params* p, int64_t i) { return p->rho_i ? p->rho_i[i] : p->rho; }
@@ -86,10 +91,16 @@ int orc_get_threads(void) {
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Kernel weight, Eq. 4: w(r) = re/r - 1 for 0 <= r < re, else 0.                       */
+/* Kernel weight, Eq. 4: w(r) = re/r - 1 for 0 <= r < re, else 0 (kernel 0); the       */
+/* kernel the paper recommends with the equation of state (Sec. 3.1):                   */
+/* w(r) = (1 - r/re)^3 for 0 <= r < re, else 0 (kernel 1).                              */
 /* ------------------------------------------------------------------------------------ */
-static double weight(double r, double re) {
+static double weight(double r, double re, int kernel) {
     if (r >= re) return 0.0;
+    if (kernel == 1) {
+        double t = 1.0 - r / re;
+        return t * t * t;
+    }
     return re / r - 1.0;
 }
 
@@ -107,7 +118,8 @@ static double dist2(double dx, double dy, double dz) {
 /* at an interior particle of an unjittered lattice of spacing l0);                     */
 /* lambda = sum w r^2 / sum w over the same offsets (Eq. 7: weighted mean of r_ij^2).   */
 /* ------------------------------------------------------------------------------------ */
-int orc_lattice(int32_t dim, double l0, double re, double* n0_out, double* lambda_out) {
+int orc_lattice(int32_t dim, double l0, double re, double* n0_out, double* lambda_out,
+                int32_t kernel) {
     if ((dim != 2 && dim != 3) || !(l0 > 0.0) || !(re > 0.0)) return ORC_EINVAL;
     int m = (int)ceil(re / l0) + 1;
     int mz = (dim == 3) ? m : 0;
@@ -118,7 +130,7 @@ int orc_lattice(int32_t dim, double l0, double re, double* n0_out, double* lambd
                 if (a == 0 && b == 0 && c == 0) continue;
                 double r2 = dist2(a * l0, b * l0, c * l0);
                 if (!(r2 < re * re)) continue;
-                double w = weight(sqrt(r2), re);
+                double w = weight(sqrt(r2), re, kernel);
                 sw = sw + w;
                 swr2 = swr2 + w * r2;
             }
@@ -346,7 +358,7 @@ int orc_neighbors(int32_t dim, int64_t n, const double* pos, const int8_t* type,
 /* neighbour counted (fluid, wall and dummy alike).                                     */
 /* ------------------------------------------------------------------------------------ */
 static void pnd_from(int dim, int64_t n, const double* pos, const int8_t* type, double re,
-                     const csr_t* nb, double* nd) {
+                     int kernel, const csr_t* nb, double* nd) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         double s = 0.0;
@@ -357,7 +369,7 @@ static void pnd_from(int dim, int64_t n, const double* pos, const int8_t* type, 
                 int64_t j = nb->ids[k];
                 double xj, yj, zj;
                 coords(pos, dim, j, &xj, &yj, &zj);
-                s = s + weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), re);
+                s = s + weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), re, kernel);
             }
         }
         nd[i] = s;
@@ -365,11 +377,11 @@ static void pnd_from(int dim, int64_t n, const double* pos, const int8_t* type, 
 }
 
 int orc_pnd(int32_t dim, int64_t n, const double* pos, const int8_t* type, double re,
-            int32_t mode, double* nd) {
+            int32_t mode, double* nd, int32_t kernel) {
     csr_t nb = {0, 0};
     int rc = neighbors(dim, n, pos, type, re, mode, &nb);
     if (rc) return rc;
-    pnd_from(dim, n, pos, type, re, &nb, nd);
+    pnd_from(dim, n, pos, type, re, kernel, &nb, nd);
     csr_free(&nb);
     return ORC_OK;
 }
@@ -379,8 +391,8 @@ int orc_pnd(int32_t dim, int64_t n, const double* pos, const int8_t* type, doubl
 /* Neighbours j of every non-GHOST kind enter (walls and dummies carry their own phi).  */
 /* ------------------------------------------------------------------------------------ */
 static void laplacian_from(int dim, int64_t n, const double* pos, const int8_t* type, double re,
-                           double n0, double lambda, const csr_t* nb, const double* phi,
-                           int ncomp, double* out) {
+                           int kernel, double n0, double lambda, const csr_t* nb,
+                           const double* phi, int ncomp, double* out) {
     double coef = (2.0 * dim) / (n0 * lambda);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
@@ -393,7 +405,7 @@ static void laplacian_from(int dim, int64_t n, const double* pos, const int8_t* 
                     int64_t j = nb->ids[k];
                     double xj, yj, zj;
                     coords(pos, dim, j, &xj, &yj, &zj);
-                    double w = weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), re);
+                    double w = weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), re, kernel);
                     s = s + (phi[j * ncomp + c] - phi[i * ncomp + c]) * w;
                 }
             }
@@ -403,11 +415,12 @@ static void laplacian_from(int dim, int64_t n, const double* pos, const int8_t* 
 }
 
 int orc_laplacian(int32_t dim, int64_t n, const double* pos, const int8_t* type, double re,
-                  double n0, double lambda, const double* phi, int32_t ncomp, double* out) {
+                  double n0, double lambda, const double* phi, int32_t ncomp, double* out,
+                  int32_t kernel) {
     csr_t nb = {0, 0};
     int rc = neighbors(dim, n, pos, type, re, 1, &nb);
     if (rc) return rc;
-    laplacian_from(dim, n, pos, type, re, n0, lambda, &nb, phi, ncomp, out);
+    laplacian_from(dim, n, pos, type, re, kernel, n0, lambda, &nb, phi, ncomp, out);
     csr_free(&nb);
     return ORC_OK;
 }
@@ -416,11 +429,13 @@ int orc_laplacian(int32_t dim, int64_t n, const double* pos, const int8_t* type,
 /* Pressure gradient, the difference form of Eq. (multi-density gradient, Sec. 3.2.1)   */
 /* with a single density and the minimum-pressure stabilisation p_hat:                   */
 /*   grad p_i = d/n0 sum_{j != i, j not DUMMY} (p_j - p_hat_i) / r_ij^2 * r_ij * w(r_ij) */
-/* with r_ij = r_j - r_i.                                                                */
+/* with r_ij = r_j - r_i (form 0), or the antisymmetric CMPS gradient of Eq. 18 (form   */
+/* 1), whose pair term ((p_i + p_j) - (p_hat_i + p_hat_j)) w / r_ij^2 is symmetric in    */
+/* i, j, so that the pair forces cancel and linear momentum is conserved.               */
 /* ------------------------------------------------------------------------------------ */
 static void gradient_from(int dim, int64_t n, const double* pos, const int8_t* type, double re,
-                          double n0, const csr_t* nb, const double* p, const double* phat,
-                          double* out) {
+                          int kernel, int form, double n0, const csr_t* nb, const double* p,
+                          const double* phat, double* out) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         double s[3] = {0.0, 0.0, 0.0};
@@ -434,8 +449,9 @@ static void gradient_from(int dim, int64_t n, const double* pos, const int8_t* t
                 coords(pos, dim, j, &xj, &yj, &zj);
                 double d[3] = {xj - xi, yj - yi, zj - zi};
                 double r2 = dist2(d[0], d[1], d[2]);
-                double w = weight(sqrt(r2), re);
-                double f = (p[j] - phat[i]) / r2 * w;
+                double w = weight(sqrt(r2), re, kernel);
+                double f = (form == 1) ? ((p[i] + p[j]) - (phat[i] + phat[j])) / r2 * w
+                                       : (p[j] - phat[i]) / r2 * w;
                 for (int a = 0; a < 3; a++) s[a] = s[a] + f * d[a];
             }
         }
@@ -444,11 +460,12 @@ static void gradient_from(int dim, int64_t n, const double* pos, const int8_t* t
 }
 
 int orc_gradient(int32_t dim, int64_t n, const double* pos, const int8_t* type, double re,
-                 double n0, const double* p, const double* phat, double* out) {
+                 double n0, const double* p, const double* phat, double* out, int32_t kernel,
+                 int32_t form) {
     csr_t nb = {0, 0};
     int rc = neighbors(dim, n, pos, type, re, 1, &nb);
     if (rc) return rc;
-    gradient_from(dim, n, pos, type, re, n0, &nb, p, phat, out);
+    gradient_from(dim, n, pos, type, re, kernel, form, n0, &nb, p, phat, out);
     csr_free(&nb);
     return ORC_OK;
 }
@@ -510,7 +527,7 @@ static int assemble_ppe(const orc_params* p, int64_t n, const double* pos, const
             if (type[j] == ORC_DUMMY) continue;
             double xj, yj, zj;
             coords(pos, dim, j, &xj, &yj, &zj);
-            double w = weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), p->re_lap);
+            double w = weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), p->re_lap, p->kernel);
             double c = p->rho_i ? (coef0 * (2.0 / (p->rho_i[i] + p->rho_i[j]))) * w : coef * w;
             diag = diag + c;
             if (in_ppe(type, flags, j)) {
@@ -680,7 +697,8 @@ static int stage_predict(const orc_params* p, int64_t n, const double* pos, cons
     int rc = neighbors(dim, n, pos, type, p->re_lap, nb_mode, &nb);
     if (!rc) rc = check_coincident(dim, n, pos, &nb);
     if (!rc) {
-        laplacian_from(dim, n, pos, type, p->re_lap, R->n0_lap, R->lambda, &nb, vel, dim, lap);
+        laplacian_from(dim, n, pos, type, p->re_lap, p->kernel, R->n0_lap, R->lambda, &nb, vel,
+                       dim, lap);
         for (int64_t i = 0; i < n; i++)
             for (int a = 0; a < dim; a++) {
                 int64_t q = i * dim + a;
@@ -717,7 +735,7 @@ static int stage_density(const orc_params* p, int64_t n, const double* ps, const
     int rc = neighbors(p->dim, n, ps, type, p->re_n, nb_mode, nb_n);
     if (!rc) rc = check_coincident(p->dim, n, ps, nb_n);
     if (rc) return rc;
-    pnd_from(p->dim, n, ps, type, p->re_n, nb_n, nstar);
+    pnd_from(p->dim, n, ps, type, p->re_n, p->kernel, nb_n, nstar);
     R->n_surface = 0;
     R->n_ppe_rows = 0;
     for (int64_t i = 0; i < n; i++) {
@@ -736,10 +754,49 @@ static void ppe_rhs(const orc_params* p, int64_t n, const int8_t* type, const ui
         b[i] = in_ppe(type, flags, i) ? inv_dt2 * ((nstar[i] - n0) / n0) : 0.0;
 }
 
+/* ------------------------------------------------------------------------------------ */
+/* Higher-order source term (MPS-HS), Eq. 21: the PPE source from the time derivative of */
+/* the number density along the predicted motion,                                       */
+/*   (Dn/Dt)*_i = sum_{j != i} w'(r_ij) (r_ij . u_ij) / r_ij = -sum re/r_ij^3 (r_ij . u_ij) */
+/* with r_ij = r*_j - r*_i, u_ij = u*_j - u*_i, over the number-density neighbours       */
+/* (re_n, every non-GHOST kind) of the kernel of Eq. 4.  In the scaling of the PPE here  */
+/* (A = -(1/rho) L + alpha_c/dt^2 I) the right-hand side is b_i = (Dn/Dt)*_i / (n0 dt):   */
+/* positive where the predicted flow compresses the fluid, like Eq. 13's source.        */
+/* ------------------------------------------------------------------------------------ */
+static void hs_rhs(const orc_params* p, int64_t n, const double* ps, const double* us,
+                   const int8_t* type, const uint8_t* flags, const csr_t* nb_n, double n0,
+                   double* b) {
+    int dim = p->dim;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        if (!in_ppe(type, flags, i)) { b[i] = 0.0; continue; }
+        double xi, yi, zi, ui[3] = {0.0, 0.0, 0.0};
+        coords(ps, dim, i, &xi, &yi, &zi);
+        for (int a = 0; a < dim; a++) ui[a] = us[i * dim + a];
+        double s = 0.0;
+        for (int64_t k = nb_n->off[i]; k < nb_n->off[i + 1]; k++) {
+            int64_t j = nb_n->ids[k];
+            double xj, yj, zj;
+            coords(ps, dim, j, &xj, &yj, &zj);
+            double d[3] = {xj - xi, yj - yi, zj - zi};
+            double du[3] = {0.0, 0.0, 0.0};
+            for (int a = 0; a < dim; a++) du[a] = us[j * dim + a] - ui[a];
+            double r2 = dist2(d[0], d[1], d[2]);
+            double r = sqrt(r2);
+            double dot = (d[0] * du[0] + d[1] * du[1]) + d[2] * du[2];
+            s = s + p->re_n / (r2 * r) * dot;
+        }
+        b[i] = -s / (n0 * p->dt);
+    }
+}
+
 static int check_params(const orc_params* p, int64_t n) {
     int dim = p->dim;
     if ((dim != 2 && dim != 3) || n <= 0 || !(p->l0 > 0) || !(p->re_n > 0) || !(p->re_lap > 0) ||
         !(p->rho > 0) || !(p->dt > 0) || !(p->cell_skin >= 0))
+        return ORC_EINVAL;
+    if (p->kernel < 0 || p->kernel > 1 || p->grad_form < 0 || p->grad_form > 1 || p->source < 0 ||
+        p->source > 1 || (p->source == 1 && p->kernel != 0))
         return ORC_EINVAL;
     for (int64_t i = 0; i < n; i++) {
         if (p->rho_i && !(p->rho_i[i] > 0.0 && isfinite(p->rho_i[i]))) return ORC_EINVAL;
@@ -758,8 +815,8 @@ int orc_step(const orc_params* p, int64_t n, double* pos, double* vel, int8_t* t
         if (!isfinite(pos[i]) || !isfinite(vel[i])) return ORC_ENONFINITE;
     orc_report R;
     memset(&R, 0, sizeof R);
-    rc = orc_lattice(dim, p->l0, p->re_n, &R.n0_pnd, NULL);
-    if (!rc) rc = orc_lattice(dim, p->l0, p->re_lap, &R.n0_lap, &R.lambda);
+    rc = orc_lattice(dim, p->l0, p->re_n, &R.n0_pnd, NULL, p->kernel);
+    if (!rc) rc = orc_lattice(dim, p->l0, p->re_lap, &R.n0_lap, &R.lambda, p->kernel);
     if (rc) return rc;
     double n0 = R.n0_pnd;
 
@@ -781,7 +838,8 @@ int orc_step(const orc_params* p, int64_t n, double* pos, double* vel, int8_t* t
         rc = neighbors(dim, n, ps, type, p->re_lap, nb_mode, &nb_l);
         if (!rc) rc = assemble_ppe(p, n, ps, type, flags, &nb_l, R.n0_lap, R.lambda, &A);
         if (rc) goto out;
-        ppe_rhs(p, n, type, flags, nstar, n0, bvec);
+        if (p->source == 1) hs_rhs(p, n, ps, us, type, flags, &nb_n, n0, bvec);
+        else ppe_rhs(p, n, type, flags, nstar, n0, bvec);
         rc = cg_solve(n, &A, bvec, pres, p->cg_tol, p->cg_max_iter, &R.cg_iters, &R.cg_restarts,
                       &R.cg_resid);
         if (rc) goto out;
@@ -803,10 +861,22 @@ int orc_step(const orc_params* p, int64_t n, double* pos, double* vel, int8_t* t
             pres[i] = in_ppe(type, flags, i) ? wc_pressure(p, rho_of(p, i), nstar[i], n0) : 0.0;
             phat[i] = pres[i];
         }
+        /* The CMPS gradient needs p_hat as the neighbourhood minimum on this path too (with */
+        /* p_hat = p its pair term vanishes identically).                                  */
+        if (p->grad_form == 1)
+            for (int64_t i = 0; i < n; i++) {
+                double m = pres[i];
+                for (int64_t k = nb_n.off[i]; k < nb_n.off[i + 1]; k++) {
+                    int64_t j = nb_n.ids[k];
+                    if (type[j] != ORC_DUMMY && pres[j] < m) m = pres[j];
+                }
+                phat[i] = m;
+            }
     }
     if (solve_only) goto out;
 
-    gradient_from(dim, n, ps, type, p->re_n, n0, &nb_n, pres, phat, grad);   /* 6 */
+    gradient_from(dim, n, ps, type, p->re_n, p->kernel, p->grad_form, n0, &nb_n, pres, phat,
+                  grad);                                                /* 6 */
     for (int64_t i = 0; i < n; i++)
         for (int a = 0; a < dim; a++) {
             int64_t q = i * dim + a;
@@ -839,8 +909,8 @@ int orc_ppe_system(const orc_params* p, int64_t n, const double* pos, const doub
     if (rc) return rc;
     orc_report R;
     memset(&R, 0, sizeof R);
-    rc = orc_lattice(dim, p->l0, p->re_n, &R.n0_pnd, NULL);
-    if (!rc) rc = orc_lattice(dim, p->l0, p->re_lap, &R.n0_lap, &R.lambda);
+    rc = orc_lattice(dim, p->l0, p->re_n, &R.n0_pnd, NULL, p->kernel);
+    if (!rc) rc = orc_lattice(dim, p->l0, p->re_lap, &R.n0_lap, &R.lambda, p->kernel);
     if (rc) return rc;
     double* vel_c = malloc(sizeof(double) * (size_t)(n * dim));
     double* ps = malloc(sizeof(double) * (size_t)(n * dim));
@@ -865,7 +935,10 @@ int orc_ppe_system(const orc_params* p, int64_t n, const double* pos, const doub
         memcpy(col, A.col, sizeof(int32_t) * (size_t)A.off[n]);
         memcpy(val, A.val, sizeof(double) * (size_t)A.off[n]);
     }
-    if (b) ppe_rhs(p, n, type, flags, nstar, R.n0_pnd, b);
+    if (b) {
+        if (p->source == 1) hs_rhs(p, n, ps, us, type, flags, &nb_n, R.n0_pnd, b);
+        else ppe_rhs(p, n, type, flags, nstar, R.n0_pnd, b);
+    }
     if (pstar) memcpy(pstar, ps, sizeof(double) * (size_t)(n * dim));
     if (nstar_out) memcpy(nstar_out, nstar, sizeof(double) * (size_t)n);
     if (flags_out) memcpy(flags_out, flags, (size_t)n);
