@@ -96,7 +96,15 @@ typedef struct {
                                * s max(re)/2 from where they were gathered or leaves the grid. *
                                * Neighbour sets stay exact either way (Sec. 5.6.3 runs the    *
                                * paper's fast mode with a refresh every 4 steps).              */
-    int32_t reserved1;        /* must be 0 */
+    int32_t kernel;           /* weight w(r): 0 the kernel of Eq. 4, re/r - 1 (default);       *
+                               * 1 (1 - r/re)^3, the kernel the paper recommends with the      *
+                               * equation of state (Sec. 3.1); n0 and lambda follow it          */
+    int32_t gradient_form;    /* 0 difference form (p_j - p_hat_i) (default); 1 CMPS, Eq. 18: *
+                               * ((p_i + p_j) - (p_hat_i + p_hat_j)), momentum-conserving;     *
+                               * p_hat is then the neighbourhood minimum on both paths         */
+    int32_t source_term;      /* PPE source: 0 Eq. 13, (n* - n0)/(n0 dt^2) (default); 1 HS,    *
+                               * Eq. 21, (Dn/Dt)* / (n0 dt) from the predicted velocities over *
+                               * the number-density neighbours (requires kernel 0)              */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;

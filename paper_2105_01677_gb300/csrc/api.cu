@@ -36,8 +36,10 @@ struct DeviceGuard {
 };
 
 // Reference density and lambda of an ideal lattice (Eq. 5; lambda of Eq. 7): every integer
-// offset o != 0 with |o| l0 < re contributes w = re/(|o| l0) - 1, and w |o|^2 l0^2 to lambda.
-void lattice_constants(int dim, double l0, double re, double* n0, double* lambda, int* count) {
+// offset o != 0 with |o| l0 < re contributes w(|o| l0) — re/r - 1 (Eq. 4), or (1 - r/re)^3
+// for kernel 1 — and w |o|^2 l0^2 to lambda.
+void lattice_constants(int dim, double l0, double re, double* n0, double* lambda, int* count,
+                       int kernel = 0) {
     const int m = (int)std::ceil(re / l0) + 1;
     const int mz = dim == 3 ? m : 0;
     double sw = 0.0, swr2 = 0.0;
@@ -49,7 +51,8 @@ void lattice_constants(int dim, double l0, double re, double* n0, double* lambda
                 if (k == 0) continue;
                 const double r = l0 * std::sqrt((double)k);
                 if (!(r < re)) continue;
-                const double w = re / r - 1.0;
+                const double t = 1.0 - r / re;
+                const double w = kernel == 1 ? t * t * t : re / r - 1.0;
                 sw += w;
                 swr2 += w * r * r;
                 cnt++;
@@ -79,6 +82,9 @@ Radius make_radius(double re, double X) {
     r.re2_h = (float)r.re2;
     r.re2_l = (float)(r.re2 - (double)r.re2_h);
     r.re_l = (float)(re - (double)r.re_f);
+    r.inv_re = 1.0 / re;
+    r.inv_f = (float)r.inv_re;
+    r.inv_l = (float)(r.inv_re - (double)r.inv_f);
     const double tol = 8.0 * (2.0 * re * std::sqrt(3.0) * std::ldexp(X, -46)) +
                        8.0 * std::ldexp(re * re, -45);
     r.ff_tol = (float)tol;
@@ -135,7 +141,13 @@ int check_params(const mps_params* P) {
     if (P->pressure_mode == 0 && !(P->cg_tol > 0)) return MPS_EINVAL;
     if (P->pressure_mode == 1 && !(P->gamma > 0)) return MPS_EINVAL;
     if ((P->alloc == nullptr) != (P->release == nullptr)) return MPS_EINVAL;
-    if (P->list_every < 0 || P->reserved1 != 0) return MPS_EINVAL;
+    if (P->list_every < 0) return MPS_EINVAL;
+    if (P->kernel < 0 || P->kernel > 1 || P->gradient_form < 0 || P->gradient_form > 1 ||
+        P->source_term < 0 || P->source_term > 1 || (P->source_term == 1 && P->kernel != 0))
+        return MPS_EINVAL;
+    // the matrix-free FP32 operator recomputes the coefficients of Eq. 4's kernel only
+    if (P->pressure_mode == 0 && P->precision == 1 && P->ppe_operator == 1 && P->kernel != 0)
+        return MPS_EINVAL;
     if (P->gather_block != 0 && P->gather_block != 32 && P->gather_block != 64 &&
         P->gather_block != 96 && P->gather_block != 128)
         return MPS_EINVAL;
@@ -163,8 +175,8 @@ int setup(Ctx* c) {
     c->dim = dim;
     int cnt_n, cnt_l;
     double lam_n;
-    lattice_constants(dim, P.l0, P.re_n, &c->n0_pnd, &lam_n, &cnt_n);
-    lattice_constants(dim, P.l0, P.re_lap, &c->n0_lap, &c->lambda, &cnt_l);
+    lattice_constants(dim, P.l0, P.re_n, &c->n0_pnd, &lam_n, &cnt_n, P.kernel);
+    lattice_constants(dim, P.l0, P.re_lap, &c->n0_lap, &c->lambda, &cnt_l, P.kernel);
     if (!(c->n0_pnd > 0) || !(c->n0_lap > 0)) return MPS_EINVAL;
     c->coef_lap = (2.0 * dim) / (c->n0_lap * c->lambda);
     c->coef_ppe = (2.0 * dim) / (c->n0_lap * c->lambda * P.rho);
@@ -410,8 +422,8 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         stage_end(c, MPS_STAGE_PPE);
     }
     stage_begin(c, MPS_STAGE_UPDATE);
-    if (P.pressure_mode == 0) {
-        launch_clamp_pmin(c);
+    if (P.pressure_mode == 0 || P.gradient_form == 1) {
+        launch_clamp_pmin(c);   // the equation of state clamps nothing (no PPE solve)
     } else {
         MPS_CUDA(c, cudaMemcpyAsync(c->phat, c->p, sizeof(double) * (size_t)c->n,
                                     cudaMemcpyDeviceToDevice, c->stream));

@@ -206,6 +206,12 @@ __device__ __forceinline__ ff2 ff2_two_over(ff2 x) {
     return {add2(y.h, y.h), add2(y.l, y.l)};
 }
 
+// 1 - a and a^3 of packed float-float values
+__device__ __forceinline__ ff2 ff2_one_minus(ff2 a) {
+    return ff2_add_f({neg2(a.h), neg2(a.l)}, f2(1.0f));
+}
+__device__ __forceinline__ ff2 ff2_cube(ff2 a) { return ff2_mul(ff2_mul(a, a), a); }
+
 __device__ __forceinline__ ff ff2_lo(const ff2& a) { return {a.h.x, a.l.x}; }
 __device__ __forceinline__ ff ff2_hi(const ff2& a) { return {a.h.y, a.l.y}; }
 

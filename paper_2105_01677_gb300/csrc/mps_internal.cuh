@@ -83,7 +83,19 @@ struct Radius {
     float re2_h, re2_l; // re^2 as float-float
     float ff_tol;       // float-float band: |r2_ff - re^2| < ff_tol is decided in binary64
     float re_l;         // re = re_f + re_l (float-float)
+    double inv_re;      // 1/re (the cubic weight (1 - r/re)^3)
+    float inv_f, inv_l; // 1/re as float-float
 };
+
+// Weight of kernel 1, (1 - r/re)^3 for r < re, from r^2 and 1/r (FP32 and binary64)
+__device__ __forceinline__ float cubic_w_f(float r2, float rs, float inv_re) {
+    const float t = fmaf(-(r2 * rs), inv_re, 1.f);
+    return t * t * t;
+}
+__device__ __forceinline__ double cubic_w_d(double r2, double rs, double inv_re) {
+    const double t = fma(-(r2 * rs), inv_re, 1.0);
+    return t * t * t;
+}
 
 // slot of entry k of row i in a SELL-32 array with `cap` entries per row
 __host__ __device__ __forceinline__ size_t sell(int i, int k, int cap) {

@@ -79,6 +79,7 @@ struct PredictArgs {
     const int32_t* rows;    // FLUID slots in slot order
     const uint32_t* nrows;  // their count
     const double* nu_s;     // two-phase: per-slot viscosity (null: nu)
+    int kernel;             // 0: re/r - 1 (Eq. 4); 1: (1 - r/re)^3
     const double4* vel;
     const float4* vel32;
     const int8_t* type;
@@ -125,7 +126,8 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
                     if (!(exact_dist2(pi, a.pos[j]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
                     continue;
                 }
-                const float w = fmaf(a.r.re_f, rsqrtf(r2), -1.f);
+                const float rs = rsqrtf(r2);
+                const float w = a.kernel == 1 ? cubic_w_f(r2, rs, a.r.inv_f) : fmaf(a.r.re_f, rs, -1.f);
                 const float4 uj = a.vel32[j];
                 kahan_add(f0, e0, (uj.x - u32.x) * w);
                 kahan_add(f1, e1, (uj.y - u32.y) * w);
@@ -138,7 +140,8 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
                     atomicOr(&a.st->err, kErrCoincident);
                     continue;
                 }
-                const double w = fma(a.r.re, rsqrt(rr2), -1.0);
+                const double rs = rsqrt(rr2);
+                const double w = a.kernel == 1 ? cubic_w_d(rr2, rs, a.r.inv_re) : fma(a.r.re, rs, -1.0);
                 const double4 uj = a.vel[j];
                 s0 = fma(uj.x - ui.x, w, s0);
                 s1 = fma(uj.y - ui.y, w, s1);
@@ -194,6 +197,10 @@ struct BuildArgs {
     const double* rho_s;
     const float2* rho_ff;
     double coef0, wc_c;     // wc_c = c0^2/gamma
+    int kernel;             // 0: re/r - 1 (Eq. 4); 1: (1 - r/re)^3
+    int source;             // 0: Eq. 13; 1: HS (Eq. 21), from the predicted velocities
+    const double4* vel_star;
+    double dt;
     const int32_t* vcol;
     const int32_t* vcnt;
     const float4* pos32;     // r*
@@ -219,6 +226,16 @@ struct BuildArgs {
     double* p;
 };
 
+// One HS source term (Eq. 21) in binary64: re / r^3 (r_ij . (u*_j - u*_i)) with the offset
+// and 1/r given as float-float (converted by bit moves plus one addition)
+__device__ __forceinline__ double hs_term(ff dx, ff dy, ff dz, ff y, const double4& uj,
+                                          const double4& ui, double re) {
+    const double x = ff_to_double_fast(dx), yy = ff_to_double_fast(dy), z = ff_to_double_fast(dz);
+    const double ry = ff_to_double_fast(y);
+    const double dot = fma(z, uj.z - ui.z, fma(yy, uj.y - ui.y, x * (uj.x - ui.x)));
+    return re * (ry * ry * ry) * dot;
+}
+
 // Entry flags while a PPE row is being assembled (slots are < 2^30)
 constexpr int kEntryN = 1 << 30;   // within re_n: contributes to n*
 constexpr int kEntryL = 1 << 29;   // non-dummy within re_lap: a PPE coefficient
@@ -229,7 +246,9 @@ constexpr int kSlotMask = kEntryL - 1;
 // entries within re_n from the front, PPE-only entries from the back.  The dense pass then
 // evaluates every hit with (nearly) all lanes of the warp busy, accumulates n* and the
 // diagonal, and compacts the PPE coefficients in place to the front of the row.
-template <bool MIXED>
+// KERN, SRC: the weight (0 Eq. 4, 1 cubic) and the PPE source (0 Eq. 13, 1 HS) as
+// compile-time choices, so that the default instantiation carries none of the options' code
+template <bool MIXED, int KERN, int SRC>
 __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
     // FLUID and WALL rows only (the bucket build's list of them): a DUMMY particle's own n*
     // enters no equation (no free-surface test, no PPE row, no gradient), so it is not
@@ -303,7 +322,7 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
             append(j, tl, tn, nb_ok);
         }
         // ---- dense evaluation and in-place compaction (write slot <= read slot)
-        double nd = 0.0, dg = 0.0;
+        double nd = 0.0, dg = 0.0, hs = 0.0;   // hs: sum of the HS source terms
         int out_l = 0;
         const int m_all = m_f + m_b;
         auto slot_of = [&](int t) { return t < m_f ? t : a.cap - m_b + (t - m_f); };
@@ -318,6 +337,9 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
             const ff2 cre = {f2(a.cre_ff.h), f2(a.cre_ff.l)};
             const ff2 ncoef = {f2(a.ncoef_ff.h), f2(a.ncoef_ff.l)};
             const float2 rhoi = a.rho_ff ? a.rho_ff[i] : make_float2(0.f, 0.f);
+            const ff2 coef = {f2(-a.ncoef_ff.h), f2(-a.ncoef_ff.l)};
+            const ff2 invn = {f2(a.rn.inv_f), f2(a.rn.inv_l)}, invl = {f2(a.rl.inv_f), f2(a.rl.inv_l)};
+            const double4 ui = SRC == 1 ? a.vel_star[i] : make_double4(0.0, 0.0, 0.0, 0.0);
             // the entries of the next pair are loaded one iteration ahead (each slot is
             // read before the compaction can write it: writes go to slots <= t + 1)
             int n0 = m_all > 0 ? a.lap_col[sell(i, slot_of(0), a.cap)] : 0;
@@ -332,10 +354,10 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                 const int j0 = e0 & kSlotMask, j1 = e1 & kSlotMask;
                 const float4 h0 = a.pos32[j0], l0 = a.pos32lo[j0];
                 const float4 h1 = a.pos32[j1], l1 = a.pos32lo[j1];
-                const ff2 r2 = ff2_dist2(
-                    ff2_diff(ih.x, il.x, make_float2(h0.x, h1.x), make_float2(l0.x, l1.x)),
-                    ff2_diff(ih.y, il.y, make_float2(h0.y, h1.y), make_float2(l0.y, l1.y)),
-                    ff2_diff(ih.z, il.z, make_float2(h0.z, h1.z), make_float2(l0.z, l1.z)));
+                const ff2 dx = ff2_diff(ih.x, il.x, make_float2(h0.x, h1.x), make_float2(l0.x, l1.x));
+                const ff2 dy = ff2_diff(ih.y, il.y, make_float2(h0.y, h1.y), make_float2(l0.y, l1.y));
+                const ff2 dz = ff2_diff(ih.z, il.z, make_float2(h0.z, h1.z), make_float2(l0.z, l1.z));
+                const ff2 r2 = ff2_dist2(dx, dy, dz);
                 const bool ok0 = r2.h.x > 0.f, ok1 = two && r2.h.y > 0.f;
                 if (!ok0 && !(exact_dist2(pi, a.pos[j0]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
                 if (two && !ok1 && !(exact_dist2(pi, a.pos[j1]) > 0.0))
@@ -344,9 +366,22 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                 const bool tn1 = ok1 && (e1 & kEntryN), tl1 = ok1 && (e1 & kEntryL);
                 const ff2 y = ff2_rsqrt1(r2);
                 ff2 w = {f2(0.f), f2(0.f)};
-                if (tn0 || tn1) w = ff2_add_f(ff2_mul(ren, ff2_rsqrt_step(r2, y)), f2(-1.f));
-                // c = coef (re/r - 1) = (coef re) y - coef
-                ff2 c = ff2_add(ff2_mul(cre, y), ncoef);
+                if (tn0 || tn1) {
+                    const ff2 y2 = ff2_rsqrt_step(r2, y);
+                    w = KERN == 1 ? ff2_cube(ff2_one_minus(ff2_mul(ff2_mul(r2, y2), invn)))
+                                      : ff2_add_f(ff2_mul(ren, y2), f2(-1.f));
+                    if (SRC == 1) {
+                        // HS: re_n / r^3 (r_ij . (u*_j - u*_i)), binary64 from the float-float
+                        // offsets and reciprocal distance
+                        if (tn0) hs += hs_term(ff2_lo(dx), ff2_lo(dy), ff2_lo(dz), ff2_lo(y2),
+                                               a.vel_star[j0], ui, a.rn.re);
+                        if (tn1) hs += hs_term(ff2_hi(dx), ff2_hi(dy), ff2_hi(dz), ff2_hi(y2),
+                                               a.vel_star[j1], ui, a.rn.re);
+                    }
+                }
+                // c = coef (re/r - 1) = (coef re) y - coef, or coef (1 - r/re)^3
+                ff2 c = KERN == 1 ? ff2_mul(coef, ff2_cube(ff2_one_minus(ff2_mul(ff2_mul(r2, y), invl))))
+                                      : ff2_add(ff2_mul(cre, y), ncoef);
                 if (a.rho_ff) {   // two-phase: times 2/(rho_i + rho_j)
                     const float2 q0 = a.rho_ff[j0], q1 = a.rho_ff[j1];
                     c = ff2_mul(c, ff2_two_over(ff2_add({f2(rhoi.x), f2(rhoi.y)},
@@ -384,11 +419,18 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                     continue;
                 }
                 const double rs = rsqrt(rr2);
-                if (tn) nd += fma(a.rn.re, rs, -1.0);
+                if (tn) {
+                    nd += KERN == 1 ? cubic_w_d(rr2, rs, a.rn.inv_re) : fma(a.rn.re, rs, -1.0);
+                    if (SRC == 1) {
+                        const double4 uj = a.vel_star[j], ui = a.vel_star[i];
+                        const double dot = fma(dz, uj.z - ui.z, fma(dy, uj.y - ui.y, dx * (uj.x - ui.x)));
+                        hs += a.rn.re * (rs * rs * rs) * dot;
+                    }
+                }
                 if (tl) {
+                    const double wl = KERN == 1 ? cubic_w_d(rr2, rs, a.rl.inv_re) : fma(a.rl.re, rs, -1.0);
                     const double cd =
-                        a.rho_s ? (a.coef0 * (2.0 / (a.rho_s[i] + a.rho_s[j]))) * fma(a.rl.re, rs, -1.0)
-                                : a.coef_ppe * fma(a.rl.re, rs, -1.0);
+                        a.rho_s ? (a.coef0 * (2.0 / (a.rho_s[i] + a.rho_s[j]))) * wl : a.coef_ppe * wl;
                     dg += cd;
                     const size_t q = sell(i, out_l++, a.cap);
                     a.lap_col[q] = j;
@@ -400,7 +442,9 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
         ppe = !surf;
         a.nstar[i] = nd;
         a.flag[i] = surf ? 1 : 0;
-        a.bvec[i] = ppe ? a.inv_dt2 * ((nd - a.n0) / a.n0) : 0.0;
+        if (!ppe) a.bvec[i] = 0.0;
+        else if (SRC == 1) a.bvec[i] = -hs / (a.n0 * a.dt);   // (Dn/Dt)* / (n0 dt)
+        else a.bvec[i] = a.inv_dt2 * ((nd - a.n0) / a.n0);
         const double dgv = ppe ? dg + a.diag_add : 0.0;
         a.diag[i] = dgv;
         a.diag32[i] = (float)dgv;
@@ -442,6 +486,7 @@ void launch_predict_rows(Ctx* c) {
     a.rows = c->rows_f;
     a.nrows = c->scan_f + c->n;
     a.nu_s = c->nu_s;
+    a.kernel = P.kernel;   // predict
     a.vel = c->vel;
     a.vel32 = c->vel32;
     a.type = c->type;
@@ -479,6 +524,10 @@ void launch_build_rows(Ctx* c) {
     a.rho_s = c->rho_s;
     a.rho_ff = c->rho_ff;
     a.coef0 = c->coef_lap;   // 2d/(n0_lap lambda), the Laplacian's coefficient
+    a.kernel = P.kernel;
+    a.source = P.source_term;
+    a.vel_star = c->vel_star;
+    a.dt = P.dt;
     a.wc_c = P.c0 * P.c0 / P.gamma;
     a.vcol = c->vl_col;
     a.vcnt = c->vl_cnt;
@@ -514,8 +563,16 @@ void launch_build_rows(Ctx* c) {
     a.diag32 = c->diag32;
     a.p = c->p;
     const int grid = (int)((c->n + kBT - 1) / kBT);
-    if (P.precision == 1) k_build<true><<<grid, kBT, 0, c->stream>>>(a);
-    else k_build<false><<<grid, kBT, 0, c->stream>>>(a);
+    const int opt = P.kernel * 2 + P.source_term;   // (1, 1) is rejected by the checks
+    if (P.precision == 1) {
+        if (opt == 0) k_build<true, 0, 0><<<grid, kBT, 0, c->stream>>>(a);
+        else if (opt == 1) k_build<true, 0, 1><<<grid, kBT, 0, c->stream>>>(a);
+        else k_build<true, 1, 0><<<grid, kBT, 0, c->stream>>>(a);
+    } else {
+        if (opt == 0) k_build<false, 0, 0><<<grid, kBT, 0, c->stream>>>(a);
+        else if (opt == 1) k_build<false, 0, 1><<<grid, kBT, 0, c->stream>>>(a);
+        else k_build<false, 1, 0><<<grid, kBT, 0, c->stream>>>(a);
+    }
     c->launches += 1;
 }
 

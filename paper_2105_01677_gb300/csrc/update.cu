@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(kBT)
     double pi = p[i];
     if (clamp) pi = fmax(pi, 0.0);
     double m = pi;
-    if (type[i] == kFluid) {
+    if (type[i] == kFluid || type[i] == kWall) {   // wall p_hat: CMPS pair terms
         const int cnt = ncnt[i];
         for (int k = 0; k < cnt; k++) {
             double pj = p[ncol[sell(i, k, cap_n)]];
@@ -42,6 +42,10 @@ __global__ void __launch_bounds__(kBT) k_clamp_store(int n, double* p) {
 // steps the refresh of the FP32 copies of r, u and r^{k+1} measured against the positions
 // r_b the lists were gathered at.
 struct Keep {
+    int kernel;             // 0: re/r - 1 (Eq. 4); 1: (1 - r/re)^3
+    int form;               // 0: (p_j - p_hat_i); 1: CMPS (Eq. 18)
+    double inv_re;          // 1/re_n
+    float inv_f;
     const double* rho_s;    // two-phase: per-slot density (null: the uniform rho)
     const double4* pos_b;   // null: lists are gathered every step (nothing else is used)
     float4* pos32;
@@ -63,6 +67,7 @@ __device__ __forceinline__ double gradient_row(int i, const int8_t* type, const 
                                                const Keep& kp) {
     const double4 pi = ps[i];
     const double ph = phat[i];
+    const double pp = p[i];
     const int cnt = ncnt[i];
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
     if (MIXED) {
@@ -74,8 +79,9 @@ __device__ __forceinline__ double gradient_row(int i, const int8_t* type, const 
             const float dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             const float rs = rsqrtf(r2);
-            const float w = fmaf(re_f, rs, -1.f);
-            const float f = (float)(p[j] - ph) * (w * rs * rs);
+            const float w = kp.kernel == 1 ? cubic_w_f(r2, rs, kp.inv_f) : fmaf(re_f, rs, -1.f);
+            const double dp = kp.form == 1 ? (pp + p[j]) - (ph + phat[j]) : p[j] - ph;
+            const float f = (float)dp * (w * rs * rs);
             f0 = fmaf(f, dx, f0);
             f1 = fmaf(f, dy, f1);
             f2 = fmaf(f, dz, f2);
@@ -90,8 +96,9 @@ __device__ __forceinline__ double gradient_row(int i, const int8_t* type, const 
             const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
             const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
             const double rs = rsqrt(r2);
-            const double w = fma(re, rs, -1.0);
-            const double f = (p[j] - ph) * (w * rs * rs);
+            const double w = kp.kernel == 1 ? cubic_w_d(r2, rs, kp.inv_re) : fma(re, rs, -1.0);
+            const double dp = kp.form == 1 ? (pp + p[j]) - (ph + phat[j]) : p[j] - ph;
+            const double f = dp * (w * rs * rs);
             g0 = fma(f, dx, g0);
             g1 = fma(f, dy, g1);
             g2 = fma(f, dz, g2);
@@ -239,7 +246,8 @@ __global__ void __launch_bounds__(kBT)
 void launch_clamp_pmin(Ctx* c) {
     const int n = (int)c->n;
     const int nb = (n + kBT - 1) / kBT;
-    const int clamp = c->prm.clamp_negative_p ? 1 : 0;
+    // the clamp belongs to the PPE solution; the equation of state's pressure is kept
+    const int clamp = (c->prm.pressure_mode == 0 && c->prm.clamp_negative_p) ? 1 : 0;
     k_clamp_pmin<<<nb, kBT, 0, c->stream>>>(n, c->type, c->p, c->phat, c->nb_n_col, c->nb_n_cnt,
                                             c->cap_n, clamp);
     if (clamp) k_clamp_store<<<nb, kBT, 0, c->stream>>>(n, c->p);
@@ -251,6 +259,10 @@ void launch_gradient_correct(Ctx* c) {
     const int nb = (n + kBT - 1) / kBT;
     const mps_params& P = c->prm;
     Keep kp;
+    kp.kernel = P.kernel;
+    kp.form = P.gradient_form;
+    kp.inv_re = c->r_n.inv_re;
+    kp.inv_f = c->r_n.inv_f;
     kp.rho_s = c->rho_s;
     kp.pos_b = c->pos_b;
     kp.pos32 = c->pos32;

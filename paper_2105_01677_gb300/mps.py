@@ -36,7 +36,8 @@ class mps_params(C.Structure):
                 ("box_min", C.c_double * 3), ("box_max", C.c_double * 3),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32),
                 ("ppe_operator", C.c_int32), ("device", C.c_int32), ("gather_block", C.c_int32),
-                ("list_every", C.c_int32), ("reserved1", C.c_int32),
+                ("list_every", C.c_int32), ("kernel", C.c_int32), ("gradient_form", C.c_int32),
+                ("source_term", C.c_int32),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
                 ("alloc_user", C.c_void_p)]
 

@@ -60,7 +60,8 @@ int main(void) {
   P(mps_params, precision) P(mps_params, nbr_cap) P(mps_params, cell_skin) P(mps_params, box_min)
   P(mps_params, box_max) P(mps_params, inner_tol) P(mps_params, ppe_operator) P(mps_params, stream)
   P(mps_params, alloc) P(mps_params, release) P(mps_params, alloc_user) P(mps_params, list_every)
-  P(mps_params, gather_block) P(mps_report, list_gathered)
+  P(mps_params, gather_block) P(mps_params, kernel) P(mps_params, source_term)
+  P(mps_report, list_gathered)
   P(mps_report, cg_resid) P(mps_report, n_surface) P(mps_report, max_disp) P(mps_report, lambda)
   P(mps_report, steps_done) P(mps_report, cand_tests) P(mps_report, pairs_pnd)
   return 0;
@@ -104,7 +105,9 @@ def test_invalid_arguments_rejected_before_device_use(L):
     t = np.zeros(3, np.int8)
     h = C.c_void_p()
     for kw in (dict(dim=4), dict(re_n=0.0), dict(dt=-1.0), dict(precision=2),
-               dict(box_max=(0.0, 0.0, 0.0)), dict(list_every=-1), dict(reserved1=1)):
+               dict(box_max=(0.0, 0.0, 0.0)), dict(list_every=-1), dict(kernel=2),
+               dict(gradient_form=3), dict(source_term=1, kernel=1),
+               dict(precision=1, ppe_operator=1, kernel=1)):
         P = mps.mps_params_default(**kw)
         rc = L.mps_create(pos.ctypes.data_as(C.POINTER(C.c_double)), None,
                           t.ctypes.data_as(C.POINTER(C.c_int8)), 3, C.byref(P), C.byref(h))
