@@ -56,7 +56,7 @@ typedef struct {
     /* Numerical options of Sec. 3.1 / 3.3:                                               */
     int32_t kernel;          /* 0: w of Eq. 4 (re/r - 1); 1: the WC kernel (1 - r/re)^3     */
     int32_t grad_form;       /* 0: difference form with p_hat_i; 1: CMPS, Eq. 18           */
-    int32_t source;          /* PPE source: 0: Eq. 13 (density deviation); 1: HS, Eq. 21   */
+    int32_t source;          /* PPE source: 0 Eq. 13; 1 HS, Eq. 21; 2 HS + ECS, Eq. 24-25  */
     int32_t pad0;
 } orc_params;
 
@@ -755,39 +755,89 @@ static void ppe_rhs(const orc_params* p, int64_t n, const int8_t* type, const ui
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Higher-order source term (MPS-HS), Eq. 21: the PPE source from the time derivative of */
-/* the number density along the predicted motion,                                       */
-/*   (Dn/Dt)*_i = sum_{j != i} w'(r_ij) (r_ij . u_ij) / r_ij = -sum re/r_ij^3 (r_ij . u_ij) */
-/* with r_ij = r*_j - r*_i, u_ij = u*_j - u*_i, over the number-density neighbours       */
-/* (re_n, every non-GHOST kind) of the kernel of Eq. 4.  In the scaling of the PPE here  */
-/* (A = -(1/rho) L + alpha_c/dt^2 I) the right-hand side is b_i = (Dn/Dt)*_i / (n0 dt):   */
-/* positive where the predicted flow compresses the fluid, like Eq. 13's source.        */
+/* Time derivative of the number density along a velocity field (the Dn/Dt of Eq. 21    */
+/* and Eq. 24), for the kernel of Eq. 4:                                                 */
+/*   (Dn/Dt)_i = sum_{j != i} w'(r_ij) (r_ij . u_ij) / r_ij = -sum re/r_ij^3 (r_ij . u_ij) */
+/* with r_ij = r_j - r_i, u_ij = u_j - u_i, over the number-density neighbours (re_n,   */
+/* every non-GHOST kind).                                                                */
 /* ------------------------------------------------------------------------------------ */
-static void hs_rhs(const orc_params* p, int64_t n, const double* ps, const double* us,
-                   const int8_t* type, const uint8_t* flags, const csr_t* nb_n, double n0,
-                   double* b) {
+static void dn_dt(const orc_params* p, int64_t n, const double* x, const double* u,
+                  const int8_t* type, const csr_t* nb, double* out) {
     int dim = p->dim;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
-        if (!in_ppe(type, flags, i)) { b[i] = 0.0; continue; }
-        double xi, yi, zi, ui[3] = {0.0, 0.0, 0.0};
-        coords(ps, dim, i, &xi, &yi, &zi);
-        for (int a = 0; a < dim; a++) ui[a] = us[i * dim + a];
         double s = 0.0;
-        for (int64_t k = nb_n->off[i]; k < nb_n->off[i + 1]; k++) {
-            int64_t j = nb_n->ids[k];
-            double xj, yj, zj;
-            coords(ps, dim, j, &xj, &yj, &zj);
-            double d[3] = {xj - xi, yj - yi, zj - zi};
-            double du[3] = {0.0, 0.0, 0.0};
-            for (int a = 0; a < dim; a++) du[a] = us[j * dim + a] - ui[a];
-            double r2 = dist2(d[0], d[1], d[2]);
-            double r = sqrt(r2);
-            double dot = (d[0] * du[0] + d[1] * du[1]) + d[2] * du[2];
-            s = s + p->re_n / (r2 * r) * dot;
+        if (type[i] != ORC_GHOST) {
+            double xi, yi, zi, ui[3] = {0.0, 0.0, 0.0};
+            coords(x, dim, i, &xi, &yi, &zi);
+            for (int a = 0; a < dim; a++) ui[a] = u[i * dim + a];
+            for (int64_t k = nb->off[i]; k < nb->off[i + 1]; k++) {
+                int64_t j = nb->ids[k];
+                double xj, yj, zj;
+                coords(x, dim, j, &xj, &yj, &zj);
+                double d[3] = {xj - xi, yj - yi, zj - zi};
+                double du[3] = {0.0, 0.0, 0.0};
+                for (int a = 0; a < dim; a++) du[a] = u[j * dim + a] - ui[a];
+                double r2 = dist2(d[0], d[1], d[2]);
+                double r = sqrt(r2);
+                double dot = (d[0] * du[0] + d[1] * du[1]) + d[2] * du[2];
+                s = s + p->re_n / (r2 * r) * dot;
+            }
         }
-        b[i] = -s / (n0 * p->dt);
+        out[i] = -s;
     }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Higher-order source term (MPS-HS), Eq. 21, from the predicted motion r*, u*.  In the  */
+/* scaling of the PPE here (A = -(1/rho) L + alpha_c/dt^2 I) the right-hand side is      */
+/*   b_i = (Dn/Dt)*_i / (n0 dt),                                                         */
+/* positive where the predicted flow compresses the fluid, like Eq. 13's source.         */
+/* With the error-compensating source (Eq. 24-25, source 2) the right-hand side adds    */
+/*   ECS_i / dt,  ECS_i = |eps_i| (Dn/Dt)^k_i / n0 + |dt (Dn/Dt)^k_i / n0| eps_i / dt,   */
+/* eps_i = (n^k_i - n0)/n0, number density and its rate at the step's start r^k, u^k.   */
+/* (Eq. 25 prints ECS beside rho/(n0 dt) (Dn/Dt)* without the factor rho/dt its units   */
+/* need; it is taken with that factor, i.e. ECS / dt after the division by rho.)         */
+/* ------------------------------------------------------------------------------------ */
+static void hs_rhs(const orc_params* p, int64_t n, const int8_t* type, const uint8_t* flags,
+                   const double* dstar, const double* nk, const double* dk, double n0,
+                   double* b) {
+    for (int64_t i = 0; i < n; i++) {
+        if (!in_ppe(type, flags, i)) { b[i] = 0.0; continue; }
+        double v = dstar[i] / (n0 * p->dt);
+        if (p->source == 2) {
+            double eps = (nk[i] - n0) / n0;
+            double ecs = fabs(eps) * (dk[i] / n0) + fabs(p->dt * dk[i] / n0) * (eps / p->dt);
+            v = v + ecs / p->dt;
+        }
+        b[i] = v;
+    }
+}
+
+/* The HS / ECS source of every row (steps 3-4 of a step with source 1 or 2).           */
+static int hs_source(const orc_params* p, int64_t n, const double* pos, const double* vel,
+                     const double* ps, const double* us, const int8_t* type,
+                     const uint8_t* flags, const csr_t* nb_n, int nb_mode, double n0,
+                     double* b) {
+    double* dstar = malloc(sizeof(double) * (size_t)n);
+    double* nk = malloc(sizeof(double) * (size_t)n);
+    double* dk = malloc(sizeof(double) * (size_t)n);
+    csr_t nb_k = {0, 0};
+    int rc = ORC_ENOMEM;
+    if (!dstar || !nk || !dk) goto out;
+    dn_dt(p, n, ps, us, type, nb_n, dstar);
+    if (p->source == 2) {
+        rc = neighbors(p->dim, n, pos, type, p->re_n, nb_mode, &nb_k);
+        if (rc) goto out;
+        pnd_from(p->dim, n, pos, type, p->re_n, p->kernel, &nb_k, nk);
+        dn_dt(p, n, pos, vel, type, &nb_k, dk);
+    }
+    hs_rhs(p, n, type, flags, dstar, nk, dk, n0, b);
+    rc = ORC_OK;
+out:
+    free(dstar); free(nk); free(dk);
+    csr_free(&nb_k);
+    return rc;
 }
 
 static int check_params(const orc_params* p, int64_t n) {
@@ -796,7 +846,7 @@ static int check_params(const orc_params* p, int64_t n) {
         !(p->rho > 0) || !(p->dt > 0) || !(p->cell_skin >= 0))
         return ORC_EINVAL;
     if (p->kernel < 0 || p->kernel > 1 || p->grad_form < 0 || p->grad_form > 1 || p->source < 0 ||
-        p->source > 1 || (p->source == 1 && p->kernel != 0))
+        p->source > 2 || (p->source >= 1 && p->kernel != 0))
         return ORC_EINVAL;
     for (int64_t i = 0; i < n; i++) {
         if (p->rho_i && !(p->rho_i[i] > 0.0 && isfinite(p->rho_i[i]))) return ORC_EINVAL;
@@ -838,8 +888,12 @@ int orc_step(const orc_params* p, int64_t n, double* pos, double* vel, int8_t* t
         rc = neighbors(dim, n, ps, type, p->re_lap, nb_mode, &nb_l);
         if (!rc) rc = assemble_ppe(p, n, ps, type, flags, &nb_l, R.n0_lap, R.lambda, &A);
         if (rc) goto out;
-        if (p->source == 1) hs_rhs(p, n, ps, us, type, flags, &nb_n, n0, bvec);
-        else ppe_rhs(p, n, type, flags, nstar, n0, bvec);
+        if (p->source >= 1) {
+            rc = hs_source(p, n, pos, vel, ps, us, type, flags, &nb_n, nb_mode, n0, bvec);
+            if (rc) goto out;
+        } else {
+            ppe_rhs(p, n, type, flags, nstar, n0, bvec);
+        }
         rc = cg_solve(n, &A, bvec, pres, p->cg_tol, p->cg_max_iter, &R.cg_iters, &R.cg_restarts,
                       &R.cg_resid);
         if (rc) goto out;
@@ -936,8 +990,10 @@ int orc_ppe_system(const orc_params* p, int64_t n, const double* pos, const doub
         memcpy(val, A.val, sizeof(double) * (size_t)A.off[n]);
     }
     if (b) {
-        if (p->source == 1) hs_rhs(p, n, ps, us, type, flags, &nb_n, R.n0_pnd, b);
+        if (p->source >= 1) rc = hs_source(p, n, pos, vel_c, ps, us, type, flags, &nb_n, 1,
+                                           R.n0_pnd, b);
         else ppe_rhs(p, n, type, flags, nstar, R.n0_pnd, b);
+        if (rc) goto out;
     }
     if (pstar) memcpy(pstar, ps, sizeof(double) * (size_t)(n * dim));
     if (nstar_out) memcpy(nstar_out, nstar, sizeof(double) * (size_t)n);

@@ -8,7 +8,9 @@
   a free cluster sum to zero (linear momentum is conserved), unlike the difference form;
 - PPE source 1, HS (Eq. 21): the source is (Dn/Dt)*/(n0 dt); it vanishes for a fluid at
   rest, equals the shell-sum closed form for a uniform dilation, and matches a central
-  finite difference of Eq. 5 along the predicted velocity field."""
+  finite difference of Eq. 5 along the predicted velocity field;
+- PPE source 2, HS with the error-compensating source (Eq. 24-25): closed form on a
+  compressed, dilating lattice, whose number density and its rate at r^k are shell sums."""
 import math
 
 import numpy as np
@@ -156,3 +158,44 @@ def test_hs_requires_the_standard_kernel():
     prm = oracle.params_for(sc, source=1, kernel=1)
     with pytest.raises(oracle.OracleError):
         oracle.step(prm, oracle.State.from_scene(sc))
+
+
+def test_ecs_source_closed_form_on_compressed_dilating_lattice():
+    """Lattice at spacing s0 l0 (compressed: n^k > n0) with u = a (r - c): eps, (Dn/Dt)^k at
+    r^k and (Dn/Dt)* at r* are all shell sums, so the HS + ECS source (Eq. 21, 24, 25) has
+    a closed form at interior particles."""
+    l0, s0, a, dt = 0.01, 0.99, 2.0, 1e-4
+    pos, t = lattice_block(2, 21, spacing=s0 * l0)
+    pos = pos + 0.05
+    c = pos.mean(0)
+    vel = a * (pos - c)
+    sc = scenes.Scene(2, l0, pos, vel, t, np.zeros(3), np.array([0.4, 0.4, 0.0]))
+    re_l0 = 2.1
+    sh = _shells()[2]
+    n0, _ = oracle.lattice(2, l0, re_l0 * l0)
+
+    def sums(spacing):   # (sum w, sum re/r) over the shells inside re at this lattice spacing
+        sw = sinv = 0.0
+        for k, cnt in sh.items():
+            r = spacing * math.sqrt(k)
+            if r < re_l0:
+                sw += cnt * (re_l0 / r - 1.0)
+                sinv += cnt * re_l0 / r
+        return sw, sinv
+
+    nk, inv_k = sums(s0)
+    s1 = s0 * (1.0 + a * dt)
+    _, inv_s = sums(s1)
+    dk = -a * inv_k                          # (Dn/Dt)^k = -a sum re/r
+    dstar = -(a / (1.0 + a * dt)) * inv_s
+    eps = (nk - n0) / n0
+    ecs = abs(eps) * dk / n0 + abs(dt * dk / n0) * eps / dt
+    expect = dstar / (n0 * dt) + ecs / dt
+    prm2, b2, ps, fl = _hs_system(sc, vel, dt=dt)
+    prm = oracle.params_for(sc, source=2, nu=0.0, g=(0.0, 0.0, 0.0), dt=dt)
+    st = oracle.State.from_scene(sc)
+    off, col, val, b, ps, ns, fl = oracle.ppe_system(prm, st)
+    inner = interior_mask(pos, 0.03) & (fl == 0)
+    assert inner.sum() > 50 and eps > 0
+    np.testing.assert_allclose(b[inner], expect, rtol=1e-11)
+    np.testing.assert_allclose(b[inner] - b2[inner], ecs / dt, rtol=1e-9)
