@@ -164,7 +164,9 @@ def test_ecs_source_closed_form_on_compressed_dilating_lattice():
     """Lattice at spacing s0 l0 (compressed: n^k > n0) with u = a (r - c): eps, (Dn/Dt)^k at
     r^k and (Dn/Dt)* at r* are all shell sums, so the HS + ECS source (Eq. 21, 24, 25) has
     a closed form at interior particles."""
-    l0, s0, a, dt = 0.01, 0.99, 2.0, 1e-4
+    # compressed (eps > 0) and compressing (a < 0): both ECS terms are positive; with the
+    # opposite signs they cancel, which is how Eq. 24 compensates only same-sign errors
+    l0, s0, a, dt = 0.01, 0.99, -2.0, 1e-4
     pos, t = lattice_block(2, 21, spacing=s0 * l0)
     pos = pos + 0.05
     c = pos.mean(0)
@@ -196,6 +198,6 @@ def test_ecs_source_closed_form_on_compressed_dilating_lattice():
     st = oracle.State.from_scene(sc)
     off, col, val, b, ps, ns, fl = oracle.ppe_system(prm, st)
     inner = interior_mask(pos, 0.03) & (fl == 0)
-    assert inner.sum() > 50 and eps > 0
+    assert inner.sum() > 50 and eps > 0 and ecs > 0
     np.testing.assert_allclose(b[inner], expect, rtol=1e-11)
     np.testing.assert_allclose(b[inner] - b2[inner], ecs / dt, rtol=1e-9)
