@@ -104,7 +104,9 @@ typedef struct {
                                * p_hat is then the neighbourhood minimum on both paths         */
     int32_t source_term;      /* PPE source: 0 Eq. 13, (n* - n0)/(n0 dt^2) (default); 1 HS,    *
                                * Eq. 21, (Dn/Dt)* / (n0 dt) from the predicted velocities over *
-                               * the number-density neighbours (requires kernel 0)              */
+                               * the number-density neighbours; 2 HS plus the error-           *
+                               * compensating source of Eq. 24-25, ECS / dt, from n and Dn/Dt  *
+                               * at the step's start (1 and 2 require kernel 0)                 */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;

@@ -143,7 +143,7 @@ int check_params(const mps_params* P) {
     if ((P->alloc == nullptr) != (P->release == nullptr)) return MPS_EINVAL;
     if (P->list_every < 0) return MPS_EINVAL;
     if (P->kernel < 0 || P->kernel > 1 || P->gradient_form < 0 || P->gradient_form > 1 ||
-        P->source_term < 0 || P->source_term > 1 || (P->source_term == 1 && P->kernel != 0))
+        P->source_term < 0 || P->source_term > 2 || (P->source_term >= 1 && P->kernel != 0))
         return MPS_EINVAL;
     // the matrix-free FP32 operator recomputes the coefficients of Eq. 4's kernel only
     if (P->pressure_mode == 0 && P->precision == 1 && P->ppe_operator == 1 && P->kernel != 0)
@@ -257,6 +257,7 @@ int allocate(Ctx* c) {
         A(cg_r, n) A(cg_d, n) A(cg_q, n)
     }
     if (c->prm.list_every > 1) A(pos_b, n)
+    if (c->prm.pressure_mode == 0 && c->prm.source_term == 2) { A(ecs_nk, n) A(ecs_dk, n) }
     A(key, n) A(key_alt, n) A(perm, n) A(perm_alt, n)
     const int64_t tiles = ((int64_t)n + 2047) / 2048;
     A(hist, 256 * tiles) A(hist_scan, 256 * tiles)
@@ -373,6 +374,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         }
         stage_begin(c, MPS_STAGE_PREDICT);
         launch_predict_rows(c);                                        // 2
+        if (P.pressure_mode == 0 && P.source_term == 2) launch_ecs_rates(c);   // at r^k, u^k
         stage_end(c, MPS_STAGE_PREDICT);
         // per-slot outputs of the build; slots it does not visit (GHOST) keep these zeros
         MPS_CUDA(c, cudaMemsetAsync(c->nstar, 0, n * sizeof(double), c->stream));

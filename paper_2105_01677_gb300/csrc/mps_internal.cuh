@@ -147,6 +147,7 @@ __device__ __forceinline__ void split_rel(double x, double xmin, float* hi, floa
 }
 void launch_unpermute_u32(Ctx* c, const uint32_t* in, uint32_t* out);
 void launch_gather_props(Ctx* c);
+void launch_ecs_rates(Ctx* c);
 
 // ---------------------------------------------------------------- context
 struct Ctx {
@@ -218,6 +219,7 @@ struct Ctx {
     // FLUID or WALL slots (rows_fw); their counts sit after the exclusive scans
     uint32_t *mark_f, *mark_fw, *scan_f, *scan_fw;   // n + 1 each
     int32_t *rows_f, *rows_fw;
+    double *ecs_nk = nullptr, *ecs_dk = nullptr;   // ECS source: n^k, (Dn/Dt)^k per row
     uint32_t* scan_scratch;
     // CG (FP64): x = p, r, d, q ; FP32: r32, d32, q32, x32
     double *cg_r, *cg_d, *cg_q;

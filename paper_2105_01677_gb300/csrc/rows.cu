@@ -201,6 +201,8 @@ struct BuildArgs {
     int source;             // 0: Eq. 13; 1: HS (Eq. 21), from the predicted velocities
     const double4* vel_star;
     double dt;
+    const double* ecs_nk;   // ECS: n^k and (Dn/Dt)^k per row (source 2)
+    const double* ecs_dk;
     const int32_t* vcol;
     const int32_t* vcnt;
     const float4* pos32;     // r*
@@ -246,7 +248,7 @@ constexpr int kSlotMask = kEntryL - 1;
 // entries within re_n from the front, PPE-only entries from the back.  The dense pass then
 // evaluates every hit with (nearly) all lanes of the warp busy, accumulates n* and the
 // diagonal, and compacts the PPE coefficients in place to the front of the row.
-// KERN, SRC: the weight (0 Eq. 4, 1 cubic) and the PPE source (0 Eq. 13, 1 HS) as
+// KERN, SRC: the weight (0 Eq. 4, 1 cubic) and the PPE source (0 Eq. 13, 1 HS, 2 HS + ECS) as
 // compile-time choices, so that the default instantiation carries none of the options' code
 template <bool MIXED, int KERN, int SRC>
 __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
@@ -339,7 +341,7 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
             const float2 rhoi = a.rho_ff ? a.rho_ff[i] : make_float2(0.f, 0.f);
             const ff2 coef = {f2(-a.ncoef_ff.h), f2(-a.ncoef_ff.l)};
             const ff2 invn = {f2(a.rn.inv_f), f2(a.rn.inv_l)}, invl = {f2(a.rl.inv_f), f2(a.rl.inv_l)};
-            const double4 ui = SRC == 1 ? a.vel_star[i] : make_double4(0.0, 0.0, 0.0, 0.0);
+            const double4 ui = SRC >= 1 ? a.vel_star[i] : make_double4(0.0, 0.0, 0.0, 0.0);
             // the entries of the next pair are loaded one iteration ahead (each slot is
             // read before the compaction can write it: writes go to slots <= t + 1)
             int n0 = m_all > 0 ? a.lap_col[sell(i, slot_of(0), a.cap)] : 0;
@@ -370,7 +372,7 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                     const ff2 y2 = ff2_rsqrt_step(r2, y);
                     w = KERN == 1 ? ff2_cube(ff2_one_minus(ff2_mul(ff2_mul(r2, y2), invn)))
                                       : ff2_add_f(ff2_mul(ren, y2), f2(-1.f));
-                    if (SRC == 1) {
+                    if (SRC >= 1) {
                         // HS: re_n / r^3 (r_ij . (u*_j - u*_i)), binary64 from the float-float
                         // offsets and reciprocal distance
                         if (tn0) hs += hs_term(ff2_lo(dx), ff2_lo(dy), ff2_lo(dz), ff2_lo(y2),
@@ -421,7 +423,7 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                 const double rs = rsqrt(rr2);
                 if (tn) {
                     nd += KERN == 1 ? cubic_w_d(rr2, rs, a.rn.inv_re) : fma(a.rn.re, rs, -1.0);
-                    if (SRC == 1) {
+                    if (SRC >= 1) {
                         const double4 uj = a.vel_star[j], ui = a.vel_star[i];
                         const double dot = fma(dz, uj.z - ui.z, fma(dy, uj.y - ui.y, dx * (uj.x - ui.x)));
                         hs += a.rn.re * (rs * rs * rs) * dot;
@@ -443,7 +445,15 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
         a.nstar[i] = nd;
         a.flag[i] = surf ? 1 : 0;
         if (!ppe) a.bvec[i] = 0.0;
-        else if (SRC == 1) a.bvec[i] = -hs / (a.n0 * a.dt);   // (Dn/Dt)* / (n0 dt)
+        else if (SRC >= 1) {
+            double bv = -hs / (a.n0 * a.dt);   // (Dn/Dt)* / (n0 dt)
+            if (SRC == 2) {                    // + ECS / dt (Eq. 24-25)
+                const double dk = a.ecs_dk[i], eps = (a.ecs_nk[i] - a.n0) / a.n0;
+                const double ecs = fabs(eps) * (dk / a.n0) + fabs(a.dt * dk / a.n0) * (eps / a.dt);
+                bv += ecs / a.dt;
+            }
+            a.bvec[i] = bv;
+        }
         else a.bvec[i] = a.inv_dt2 * ((nd - a.n0) / a.n0);
         const double dgv = ppe ? dg + a.diag_add : 0.0;
         a.diag[i] = dgv;
@@ -470,7 +480,88 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
         if (n_pnd) atomicAdd(&a.st->pairs_n, (unsigned long long)n_pnd);
     }
 }
+// ---------------------------------------------------------------- ECS rates at r^k
+// The error-compensating source (Eq. 24) needs, per FLUID / WALL row, the number density
+// n^k and its rate (Dn/Dt)^k = -sum re_n/r^3 (r_ij . u_ij) at the step's start r^k, u^k,
+// over the number-density neighbours (re_n, every non-GHOST kind; the exact predicate as
+// in the build).  Mixed mode: float-float distances, binary64 rate terms.
+struct RatesArgs {
+    int cap_v;
+    const int32_t* vcol;
+    const int32_t* vcnt;
+    const float4* pos32;
+    const float4* pos32lo;
+    const double4* pos;
+    const double4* vel;
+    const int32_t* rows;
+    const uint32_t* nrows;
+    Radius rn;
+    double* nk;
+    double* dk;
+};
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kBT) k_ecs_rates(RatesArgs a) {
+    const int tid = blockIdx.x * kBT + threadIdx.x;
+    if (tid >= (int)*a.nrows) return;
+    const int i = a.rows[tid];
+    const float4 ih = a.pos32[i], il = a.pos32lo[i];
+    const double4 pi = a.pos[i], ui = a.vel[i];
+    const int cnt = a.vcnt[i];
+    ff nf = {0.f, 0.f};
+    double nd = 0.0, dd = 0.0;
+    for (int k = 0; k < cnt; k++) {
+        const int j = a.vcol[sell(i, k, a.cap_v)];
+        const float4 jh = a.pos32[j];
+        const float r2 = dist2_f(ih, jh);
+        int t = tier1(r2, a.rn);
+        if (!t) continue;
+        const float4 jl = a.pos32lo[j];
+        if (t == 2 && !decide_band(pair_r2(ih, il, jh, jl), a.rn, a.pos, pi, j)) continue;
+        const double4 uj = a.vel[j];
+        if (MIXED) {
+            const ff dx = ff_diff(ih.x, il.x, jh.x, jl.x), dy = ff_diff(ih.y, il.y, jh.y, jl.y);
+            const ff dz = ff_diff(ih.z, il.z, jh.z, jl.z);
+            const ff rr = ff_dist2(dx, dy, dz);
+            if (!(rr.h > 0.f)) continue;   // coincident pairs are reported by the prediction
+            const ff y = ff_rsqrt(rr);
+            nf = ff_add(nf, ff_add_f(ff_mul({a.rn.re_f, a.rn.re_l}, y), -1.f));
+            dd += hs_term(dx, dy, dz, y, uj, ui, a.rn.re);
+        } else {
+            const double4 pj = a.pos[j];
+            const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+            const double rr2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            if (!(rr2 > 0.0)) continue;
+            const double rs = rsqrt(rr2);
+            nd += fma(a.rn.re, rs, -1.0);
+            const double dot = fma(dz, uj.z - ui.z, fma(dy, uj.y - ui.y, dx * (uj.x - ui.x)));
+            dd += a.rn.re * (rs * rs * rs) * dot;
+        }
+    }
+    a.nk[i] = MIXED ? ff_to_double_fast(nf) : nd;
+    a.dk[i] = -dd;
+}
 }  // namespace
+
+void launch_ecs_rates(Ctx* c) {
+    RatesArgs a;
+    a.cap_v = c->cap_v;
+    a.vcol = c->vl_col;
+    a.vcnt = c->vl_cnt;
+    a.pos32 = c->pos32;
+    a.pos32lo = c->pos32lo;
+    a.pos = c->pos;
+    a.vel = c->vel;
+    a.rows = c->rows_fw;
+    a.nrows = c->scan_fw + c->n;
+    a.rn = c->r_n;
+    a.nk = c->ecs_nk;
+    a.dk = c->ecs_dk;
+    const int grid = (int)((c->n + kBT - 1) / kBT);
+    if (c->prm.precision == 1) k_ecs_rates<true><<<grid, kBT, 0, c->stream>>>(a);
+    else k_ecs_rates<false><<<grid, kBT, 0, c->stream>>>(a);
+    c->launches += 1;
+}
 
 void launch_predict_rows(Ctx* c) {
     const mps_params& P = c->prm;
@@ -528,6 +619,8 @@ void launch_build_rows(Ctx* c) {
     a.source = P.source_term;
     a.vel_star = c->vel_star;
     a.dt = P.dt;
+    a.ecs_nk = c->ecs_nk;
+    a.ecs_dk = c->ecs_dk;
     a.wc_c = P.c0 * P.c0 / P.gamma;
     a.vcol = c->vl_col;
     a.vcnt = c->vl_cnt;
@@ -563,15 +656,18 @@ void launch_build_rows(Ctx* c) {
     a.diag32 = c->diag32;
     a.p = c->p;
     const int grid = (int)((c->n + kBT - 1) / kBT);
-    const int opt = P.kernel * 2 + P.source_term;   // (1, 1) is rejected by the checks
+    // (kernel, source): (0, 0), (0, 1), (0, 2), (1, 0); the cubic weight with HS is rejected
+    const int src = P.source_term;
     if (P.precision == 1) {
-        if (opt == 0) k_build<true, 0, 0><<<grid, kBT, 0, c->stream>>>(a);
-        else if (opt == 1) k_build<true, 0, 1><<<grid, kBT, 0, c->stream>>>(a);
-        else k_build<true, 1, 0><<<grid, kBT, 0, c->stream>>>(a);
+        if (P.kernel == 1) k_build<true, 1, 0><<<grid, kBT, 0, c->stream>>>(a);
+        else if (src == 0) k_build<true, 0, 0><<<grid, kBT, 0, c->stream>>>(a);
+        else if (src == 1) k_build<true, 0, 1><<<grid, kBT, 0, c->stream>>>(a);
+        else k_build<true, 0, 2><<<grid, kBT, 0, c->stream>>>(a);
     } else {
-        if (opt == 0) k_build<false, 0, 0><<<grid, kBT, 0, c->stream>>>(a);
-        else if (opt == 1) k_build<false, 0, 1><<<grid, kBT, 0, c->stream>>>(a);
-        else k_build<false, 1, 0><<<grid, kBT, 0, c->stream>>>(a);
+        if (P.kernel == 1) k_build<false, 1, 0><<<grid, kBT, 0, c->stream>>>(a);
+        else if (src == 0) k_build<false, 0, 0><<<grid, kBT, 0, c->stream>>>(a);
+        else if (src == 1) k_build<false, 0, 1><<<grid, kBT, 0, c->stream>>>(a);
+        else k_build<false, 0, 2><<<grid, kBT, 0, c->stream>>>(a);
     }
     c->launches += 1;
 }

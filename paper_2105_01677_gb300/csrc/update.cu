@@ -15,13 +15,13 @@ constexpr int kBT = 256;
 
 __global__ void __launch_bounds__(kBT)
     k_clamp_pmin(int n, const int8_t* type, double* p, double* phat, const int32_t* ncol,
-                 const int32_t* ncnt, int cap_n, int clamp) {
+                 const int32_t* ncnt, int cap_n, int clamp, int walls) {
     int i = blockIdx.x * kBT + threadIdx.x;
     if (i >= n) return;
     double pi = p[i];
     if (clamp) pi = fmax(pi, 0.0);
     double m = pi;
-    if (type[i] == kFluid || type[i] == kWall) {   // wall p_hat: CMPS pair terms
+    if (type[i] == kFluid || (walls && type[i] == kWall)) {   // wall p_hat: CMPS pair terms
         const int cnt = ncnt[i];
         for (int k = 0; k < cnt; k++) {
             double pj = p[ncol[sell(i, k, cap_n)]];
@@ -249,7 +249,7 @@ void launch_clamp_pmin(Ctx* c) {
     // the clamp belongs to the PPE solution; the equation of state's pressure is kept
     const int clamp = (c->prm.pressure_mode == 0 && c->prm.clamp_negative_p) ? 1 : 0;
     k_clamp_pmin<<<nb, kBT, 0, c->stream>>>(n, c->type, c->p, c->phat, c->nb_n_col, c->nb_n_cnt,
-                                            c->cap_n, clamp);
+                                            c->cap_n, clamp, c->prm.gradient_form == 1 ? 1 : 0);
     if (clamp) k_clamp_store<<<nb, kBT, 0, c->stream>>>(n, c->p);
     c->launches += clamp ? 2 : 1;
 }

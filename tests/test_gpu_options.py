@@ -1,6 +1,7 @@
 """The paper's numerical options on the GPU against the oracle: the cubic weight of the
-equation-of-state path (Sec. 3.1), the CMPS gradient (Eq. 18) and the HS source (Eq. 21),
-alone and combined, FP64 to the single-step bound and mixed precision to its bound."""
+equation-of-state path (Sec. 3.1), the CMPS gradient (Eq. 18), the HS source (Eq. 21) and
+the error-compensating source (Eq. 24-25), alone and combined, FP64 to the single-step
+bound and mixed precision to its bound."""
 import numpy as np
 import pytest
 
@@ -18,6 +19,8 @@ OPTIONS = [
     dict(source_term=1, pressure_mode=0),
     dict(source_term=1, gradient_form=1, pressure_mode=0),
     dict(kernel=1, gradient_form=1, pressure_mode=1, c0=20.0),
+    dict(source_term=2, pressure_mode=0),
+    dict(source_term=2, gradient_form=1, pressure_mode=0),
 ]
 
 
@@ -55,7 +58,7 @@ def test_option_fp64_2d(opt):
     compare_step(sc, got, ost, prm)
 
 
-@pytest.mark.parametrize("opt", OPTIONS[:3] + OPTIONS[4:5],
+@pytest.mark.parametrize("opt", OPTIONS[:3] + OPTIONS[4:5] + OPTIONS[7:8],
                          ids=lambda o: "-".join(f"{k}{v}" for k, v in o.items()))
 def test_option_fp64_3d_small(opt):
     sc = _moving(small_3d(seed=2))
