@@ -212,6 +212,36 @@ int mps_debug_cells(mps_ctx* ctx, uint32_t* cell_key);
 int mps_debug_neighbors(mps_ctx* ctx, int32_t which, int64_t* offsets, int32_t* ids,
                         int64_t cap);
 
+/* ---------------------------------------------------------------- batched ensemble
+ * Many independent scenes in one context, stepped together by the same kernel launches
+ * (the paper runs one scene at a time; this batching has no counterpart there).  Scene s
+ * has its own particle spacing l0 and cell grid box, in its own coordinates; the radii
+ * scale with l0 (re_n = (params->re_n / params->l0) l0_s, likewise re_lap), and so do
+ * lambda, the PPE and Laplacian coefficients and the cell side; every other parameter
+ * (dt, rho, nu, g, beta, c0, gamma, alpha_c, tolerances, options) is common.  Particles
+ * of different scenes never interact.  Each scene's PPE is solved to cg_tol relative to
+ * its own right-hand side (one CG over the block-diagonal system, stopped when every
+ * scene meets its tolerance).  A step fails with MPS_ESKIN if any particle moves more
+ * than s max(re)/2 of the scene with the smallest spacing. */
+typedef struct {
+    double l0;          /* particle spacing [m] */
+    double box_min[3];  /* cell grid origin of the scene [m] (its own coordinates) */
+    double box_max[3];  /* cell grid extent: outside -> GHOST, as in mps_params */
+} mps_scene;
+
+/* pos, vel, types as mps_create; scene: n scene indices in [0, n_scenes).  params->box_*
+ * are ignored.  mps_debug_cells / mps_debug_neighbors are not available on an ensemble
+ * (MPS_EINVAL); everything else is.
+ * Errors: as mps_create, and MPS_EINVAL for n_scenes < 1 or > 65535, a scene index out of
+ * range, or a scene with l0 <= 0 or an empty box. */
+int mps_create_ensemble(const double* pos, const double* vel, const int8_t* types,
+                        const int32_t* scene, int64_t n, const mps_params* params,
+                        const mps_scene* scenes, int32_t n_scenes, mps_ctx** out);
+
+/* Relative PPE residual ||b_s - A_s p_s|| / ||b_s|| of every scene after the last step
+ * (n_scenes doubles; 0 for a scene with b_s = 0); a single-scene context writes one. */
+int mps_scene_residuals(mps_ctx* ctx, double* out);
+
 /* Derived constants: out[0] n0 at re_n, out[1] n0 at re_lap, out[2] lambda [m^2],
  * out[3] cell side h [m], out[4] cells per axis x, out[5] y, out[6] z, out[7] nbr_cap. */
 int mps_get_constants(mps_ctx* ctx, double* out);

@@ -8,6 +8,7 @@
 #include <new>
 #include <vector>
 
+#include "ff.cuh"
 #include "mps_internal.cuh"
 
 namespace mps {
@@ -169,53 +170,97 @@ int check_host_state(int64_t n, int dim, const double* pos, const double* vel, c
     return MPS_OK;
 }
 
-int setup(Ctx* c) {
+// Constants of one scene with spacing l0 (the radii scale with it) and its own grid box.
+int scene_constants(const mps_params& P, double l0, const double* bmin, const double* bmax,
+                    SceneParams* sp, int* cnt_n, int* cnt_l, int* cnt_h) {
+    const int dim = P.dim;
+    const double re_n = P.re_n / P.l0 * l0, re_lap = P.re_lap / P.l0 * l0;
+    double lam_n, lam, n0h, lamh;
+    lattice_constants(dim, l0, re_n, &sp->n0_pnd, &lam_n, cnt_n, P.kernel);
+    lattice_constants(dim, l0, re_lap, &sp->n0_lap, &lam, cnt_l, P.kernel);
+    if (!(sp->n0_pnd > 0) || !(sp->n0_lap > 0)) return MPS_EINVAL;
+    sp->lambda = lam;
+    sp->coef_lap = (2.0 * dim) / (sp->n0_lap * lam);
+    sp->coef_ppe = (2.0 * dim) / (sp->n0_lap * lam * P.rho);
+    sp->coef_grad = (double)dim / sp->n0_pnd;
+    sp->own_h = std::max(re_n, re_lap) * (1.0 + P.cell_skin);
+    lattice_constants(dim, l0, sp->own_h, &n0h, &lamh, cnt_h);
+    for (int a = 0; a < 3; a++) {
+        if (a < dim) {
+            if (!(bmax[a] > bmin[a]) || !std::isfinite(bmin[a]) || !std::isfinite(bmax[a]))
+                return MPS_EINVAL;
+            sp->own_bmin[a] = bmin[a];
+            const double q = std::floor((bmax[a] - bmin[a]) / sp->own_h) + 1.0;
+            if (q > 16384.0) return MPS_EINVAL;
+            sp->own_ncell[a] = (int)q;
+        } else {
+            sp->own_bmin[a] = 0.0;
+            sp->own_ncell[a] = 1;
+        }
+    }
+    sp->rn.re = re_n;    // completed with the bands once the shared grid is known
+    sp->rl.re = re_lap;
+    sp->pad = 0;
+    return MPS_OK;
+}
+
+int setup(Ctx* c, const mps_scene* scenes, int n_scenes) {
     const mps_params& P = c->prm;
     const int dim = P.dim;
     c->dim = dim;
-    int cnt_n, cnt_l;
-    double lam_n;
-    lattice_constants(dim, P.l0, P.re_n, &c->n0_pnd, &lam_n, &cnt_n, P.kernel);
-    lattice_constants(dim, P.l0, P.re_lap, &c->n0_lap, &c->lambda, &cnt_l, P.kernel);
-    if (!(c->n0_pnd > 0) || !(c->n0_lap > 0)) return MPS_EINVAL;
-    c->coef_lap = (2.0 * dim) / (c->n0_lap * c->lambda);
-    c->coef_ppe = (2.0 * dim) / (c->n0_lap * c->lambda * P.rho);
-    c->coef_grad = (double)dim / c->n0_pnd;
-    c->inv_dt2 = 1.0 / (P.dt * P.dt);
-    c->diag_add = P.alpha_c / (P.dt * P.dt);
+    c->n_scenes = n_scenes;
+    c->scn_host.assign((size_t)n_scenes, SceneParams{});
+    int cnt_n = 0, cnt_l = 0, cnt_h = 0, rc;
+    for (int s = 0; s < n_scenes; s++) {
+        const double l0 = scenes ? scenes[s].l0 : P.l0;
+        if (!(l0 > 0) || !std::isfinite(l0)) return MPS_EINVAL;
+        if ((rc = scene_constants(P, l0, scenes ? scenes[s].box_min : P.box_min,
+                                  scenes ? scenes[s].box_max : P.box_max, &c->scn_host[s], &cnt_n,
+                                  &cnt_l, &cnt_h)))
+            return rc;
+    }
+    // list caps: the neighbour counts depend only on the radii in units of l0 (the same for
+    // every scene)
     c->cap = P.nbr_cap > 0 ? round_up(P.nbr_cap, 32) : round_up((int)std::ceil(1.5 * cnt_l), 32);
     c->cap_n = round_up(std::max((int)std::ceil(1.5 * cnt_n),
                                  (int)std::ceil((double)c->cap * cnt_n / std::max(cnt_l, 1))), 32);
-    {
-        // candidate lists hold every kind within h = max(re)(1 + s): size them from the
-        // ideal-lattice count within h, scaled like the neighbour cap
-        double n0h, lamh;
-        int cnt_h;
-        lattice_constants(dim, P.l0, std::max(P.re_n, P.re_lap) * (1.0 + P.cell_skin), &n0h,
-                          &lamh, &cnt_h);
-        c->cap_v = round_up(std::max((int)std::ceil(1.5 * cnt_h),
-                                     (int)std::ceil((double)c->cap * cnt_h / std::max(cnt_l, 1))), 32);
-    }
+    // candidate lists hold every kind within h = max(re)(1 + s): sized from the
+    // ideal-lattice count within h, scaled like the neighbour cap
+    c->cap_v = round_up(std::max((int)std::ceil(1.5 * cnt_h),
+                                 (int)std::ceil((double)c->cap * cnt_h / std::max(cnt_l, 1))), 32);
     // at least one SELL slot group per list (a radius below l0 has no lattice neighbours)
     c->cap = std::max(c->cap, 32);
     c->cap_n = std::max(c->cap_n, 32);
     c->cap_v = std::max(c->cap_v, 32);
-    // grid
-    const double re_max = std::max(P.re_n, P.re_lap);
-    c->h = re_max * (1.0 + P.cell_skin);
+    // shared grid: cells of the largest scene's side, covering every scene's own grid
     GridDesc& g = c->grid;
     g.dim = dim;
-    g.h = c->h;
+    double hmax = 0.0, skin_half = 1e300;
+    for (const SceneParams& sp : c->scn_host) {
+        hmax = std::max(hmax, sp.own_h);
+        skin_half = std::min(skin_half, 0.5 * P.cell_skin * std::max(sp.rn.re, sp.rl.re));
+    }
+    c->h = hmax;
+    c->skin_half = skin_half;
+    g.h = hmax;
     int maxc = 1;
     double X = 0.0;
     for (int a = 0; a < 3; a++) {
         if (a < dim) {
-            g.bmin[a] = P.box_min[a];
-            const double q = std::floor((P.box_max[a] - P.box_min[a]) / c->h) + 1.0;
+            // one scene: its own grid; an ensemble: enough cells of the largest side to cover
+            // every scene's own grid (each scene's own grid still decides its GHOSTs)
+            double lo = 1e300, hi = -1e300;
+            for (const SceneParams& sp : c->scn_host) {
+                lo = std::min(lo, sp.own_bmin[a]);
+                hi = std::max(hi, sp.own_bmin[a] + sp.own_ncell[a] * sp.own_h);
+            }
+            g.bmin[a] = lo;
+            const double q = n_scenes == 1 ? (double)c->scn_host[0].own_ncell[a]
+                                           : std::max(1.0, std::ceil((hi - lo) / hmax));
             if (q > 16384.0) return MPS_EINVAL;
             g.ncell[a] = (int)q;
             maxc = std::max(maxc, g.ncell[a]);
-            X = std::max(X, (q + 1.0) * c->h);
+            X = std::max(X, (q + 1.0) * hmax);
         } else {
             g.bmin[a] = 0.0;
             g.ncell[a] = 1;
@@ -223,14 +268,44 @@ int setup(Ctx* c) {
     }
     int bits = 1;
     while ((1 << bits) < maxc) bits++;
-    if (dim * bits > 28) return MPS_EINVAL;
+    int sbits = 0;
+    while ((1 << sbits) < n_scenes + 1) sbits++;
+    if (dim * bits > 28 || dim * bits + sbits > 31) return MPS_EINVAL;
     g.bits = bits;
-    g.ghost_key = 1u << (dim * bits);
-    c->ntable = (int64_t)1 << (dim * bits);
-    c->sort_bits = dim * bits + 1;
-    c->r_n = make_radius(P.re_n, X);
-    c->r_lap = make_radius(P.re_lap, X);
+    c->scene_shift = (uint32_t)(dim * bits);
+    g.ghost_key = (uint32_t)n_scenes << c->scene_shift;
+    c->ntable = (int64_t)n_scenes << c->scene_shift;
+    c->sort_bits = dim * bits + sbits;
+    for (SceneParams& sp : c->scn_host) {
+        const double re_n = sp.rn.re, re_lap = sp.rl.re;
+        sp.rn = make_radius(re_n, X);
+        sp.rl = make_radius(re_lap, X);
+        sp.rv = make_radius(sp.own_h, X);
+        const ff cre = ff_from_double(sp.coef_ppe * re_lap), nco = ff_from_double(-sp.coef_ppe);
+        sp.cre_h = cre.h;
+        sp.cre_l = cre.l;
+        sp.ncoef_h = nco.h;
+        sp.ncoef_l = nco.l;
+        const ff cre2 = ff_from_double(sp.coef_lap * re_lap), nco2 = ff_from_double(-sp.coef_lap);
+        sp.cre2_h = cre2.h;
+        sp.cre2_l = cre2.l;
+        sp.ncoef2_h = nco2.h;
+        sp.ncoef2_l = nco2.l;
+    }
+    // scene 0 also in scalars (the single-scene kernels take their constants from these)
+    const SceneParams& s0 = c->scn_host[0];
+    c->n0_pnd = s0.n0_pnd;
+    c->n0_lap = s0.n0_lap;
+    c->lambda = s0.lambda;
+    c->coef_lap = s0.coef_lap;
+    c->coef_ppe = s0.coef_ppe;
+    c->coef_grad = s0.coef_grad;
+    c->inv_dt2 = 1.0 / (P.dt * P.dt);
+    c->diag_add = P.alpha_c / (P.dt * P.dt);
+    c->r_n = s0.rn;
+    c->r_lap = s0.rl;
     c->r_v = make_radius(c->h, X);
+    c->scene_resid.assign((size_t)n_scenes, 0.0);
     return MPS_OK;
 }
 
@@ -257,6 +332,8 @@ int allocate(Ctx* c) {
         A(cg_r, n) A(cg_d, n) A(cg_q, n)
     }
     if (c->prm.list_every > 1) A(pos_b, n)
+    A(scn, (size_t)c->n_scenes) A(scene_sums, 2 * (size_t)c->n_scenes)
+    if (c->n_scenes > 1) { A(sid, n) A(sid_id, n) }
     if (c->prm.pressure_mode == 0 && c->prm.source_term == 2) { A(ecs_nk, n) A(ecs_dk, n) }
     A(key, n) A(key_alt, n) A(perm, n) A(perm_alt, n)
     const int64_t tiles = ((int64_t)n + 2047) / 2048;
@@ -277,6 +354,8 @@ int allocate(Ctx* c) {
     MPS_CUDA(c, cudaMemsetAsync(c->nb_lap_cnt, 0, n * sizeof(int32_t), c->stream));
     MPS_CUDA(c, cudaMemsetAsync(c->nb_n_cnt, 0, n * sizeof(int32_t), c->stream));
     MPS_CUDA(c, cudaMemsetAsync(c->phat, 0, n * sizeof(double), c->stream));
+    MPS_CUDA(c, cudaMemcpyAsync(c->scn, c->scn_host.data(), sizeof(SceneParams) * c->scn_host.size(),
+                                cudaMemcpyHostToDevice, c->stream));
     return MPS_OK;
 }
 
@@ -348,7 +427,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     const mps_params& P = c->prm;
     int rc;
     const bool keep = P.list_every > 1;
-    const double skin_half = 0.5 * P.cell_skin * std::max(P.re_n, P.re_lap);
+    const double skin_half = c->skin_half;
     const size_t n = (size_t)c->n;
     // Candidate lists are gathered at r_b and serve while every particle stays within
     // s max(re)/2 of r_b: a pair closer than re at r^k or r* is then closer than h at r_b.
@@ -511,11 +590,81 @@ int mps_create(const double* pos, const double* vel, const int8_t* types, int64_
         }
         c->own_stream = true;
     }
-    if ((rc = setup(c)) || (rc = allocate(c)) || (rc = upload_state(c, pos, vel, types, false))) {
+    if ((rc = setup(c, nullptr, 1)) || (rc = allocate(c)) ||
+        (rc = upload_state(c, pos, vel, types, false))) {
         mps_destroy(c);
         return rc;
     }
     *out = c;
+    return MPS_OK;
+}
+
+int mps_create_ensemble(const double* pos, const double* vel, const int8_t* types,
+                        const int32_t* scene, int64_t n, const mps_params* params,
+                        const mps_scene* scenes, int32_t n_scenes, mps_ctx** out) {
+    if (!out || !pos || !types || !scene || !scenes || n <= 0 || n >= ((int64_t)1 << 31) ||
+        n_scenes < 1 || n_scenes > 65535)
+        return MPS_EINVAL;
+    if (!params) return MPS_EINVAL;
+    mps_params P = *params;
+    // the common parameters are checked with the first scene's box and spacing
+    P.l0 = params->l0;
+    for (int a = 0; a < 3; a++) {
+        P.box_min[a] = scenes[0].box_min[a];
+        P.box_max[a] = scenes[0].box_max[a];
+    }
+    int rc = check_params(&P);
+    if (rc) return rc;
+    if ((rc = check_host_state(n, P.dim, pos, vel, types))) return rc;
+    std::vector<uint16_t> sid((size_t)n);
+    for (int64_t i = 0; i < n; i++) {
+        if (scene[i] < 0 || scene[i] >= n_scenes) return MPS_EINVAL;
+        sid[(size_t)i] = (uint16_t)scene[i];
+    }
+    DeviceGuard dg(P.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    mps_ctx* c = new (std::nothrow) mps_ctx();
+    if (!c) return MPS_ENOMEM;
+    c->prm = P;
+    c->n = n;
+    c->steps_done = 0;
+    c->last_cg_iters = 8;
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, P.device) != cudaSuccess) {
+        delete c;
+        return MPS_EDEVICE;
+    }
+    if (P.stream) {
+        c->stream = (cudaStream_t)P.stream;
+        c->own_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return MPS_EDEVICE;
+        }
+        c->own_stream = true;
+    }
+    if ((rc = setup(c, scenes, n_scenes)) || (rc = allocate(c))) {
+        mps_destroy(c);
+        return rc;
+    }
+    if (c->sid_id) {
+        if (cudaMemcpyAsync(c->sid_id, sid.data(), sizeof(uint16_t) * sid.size(),
+                            cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+            mps_destroy(c);
+            return MPS_EDEVICE;
+        }
+    }
+    if ((rc = upload_state(c, pos, vel, types, false))) {
+        mps_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return MPS_OK;
+}
+
+int mps_scene_residuals(mps_ctx* c, double* out) {
+    if (!c || !out) return MPS_EINVAL;
+    for (int s = 0; s < c->n_scenes; s++) out[s] = c->scene_resid[(size_t)s];
     return MPS_OK;
 }
 
@@ -628,7 +777,7 @@ int mps_set_fluid_properties(mps_ctx* c, const double* rho, const double* nu) {
 }
 
 int mps_debug_cells(mps_ctx* c, uint32_t* cell_key) {
-    if (!c || !cell_key) return MPS_EINVAL;
+    if (!c || !cell_key || c->n_scenes > 1) return MPS_EINVAL;
     DeviceGuard dg(c->prm.device);
     if (!dg.ok) return MPS_EDEVICE;
     uint32_t* d_out = (uint32_t*)c->stage;
@@ -641,7 +790,7 @@ int mps_debug_cells(mps_ctx* c, uint32_t* cell_key) {
 }
 
 int mps_debug_neighbors(mps_ctx* c, int32_t which, int64_t* offsets, int32_t* ids, int64_t cap) {
-    if (!c || !offsets || (which != 0 && which != 1)) return MPS_EINVAL;
+    if (!c || !offsets || (which != 0 && which != 1) || c->n_scenes > 1) return MPS_EINVAL;
     DeviceGuard dg(c->prm.device);
     if (!dg.ok) return MPS_EDEVICE;
     const int n = (int)c->n;

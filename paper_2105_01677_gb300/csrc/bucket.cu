@@ -3,6 +3,8 @@
 // Per step, at the current positions r^k:
 //   1. cell key of every particle: c = floor((x - box_min)/h) per axis in binary64, Morton
 //      interleave (x in bit 0); a particle outside the grid becomes a GHOST and sorts last;
+//      in an ensemble the key is prefixed by the particle's scene (scene-major order) and
+//      the GHOST test uses the scene's own grid;
 //   2. stable LSD radix sort of (key, slot), 8-bit digits: per-tile digit histogram, a
 //      device-wide exclusive scan of the digit-major histogram table, and a stable scatter
 //      that ranks equal digits with warp match masks;
@@ -22,7 +24,8 @@ constexpr int kDigits = 1 << kRadixBits;
 
 __global__ void __launch_bounds__(kBT)
     k_cell_keys(double4* pos, double4* vel, int8_t* type, uint32_t* key, int32_t* slot, int n,
-                GridDesc g, DevStatus* st, int mutate, uint32_t outside_key) {
+                GridDesc g, DevStatus* st, int mutate, uint32_t outside_key, const uint16_t* sid,
+                const SceneParams* scn, uint32_t shift) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double4 p = pos[i];
@@ -43,8 +46,20 @@ __global__ void __launch_bounds__(kBT)
             if (!(q >= 0.0 && q < (double)g.ncell[a])) inside = false;
             else c[a] = (int)q;
         }
+        uint32_t prefix = 0;
+        if (sid) {
+            // ensemble: inside the scene's own grid (its origin, side and cell counts decide
+            // GHOSTs as for a scene alone), keyed in the shared grid under the scene's prefix
+            const int sc = sid[i];
+            const SceneParams& sp = scn[sc];
+            for (int a = 0; a < g.dim; a++) {
+                const double q = floor(__ddiv_rn(__dsub_rn(xs[a], sp.own_bmin[a]), sp.own_h));
+                if (!(q >= 0.0 && q < (double)sp.own_ncell[a])) inside = false;
+            }
+            prefix = (uint32_t)sc << shift;
+        }
         if (inside) {
-            k = morton_encode(c, g.dim, g.bits);
+            k = prefix | morton_encode(c, g.dim, g.bits);
         } else if (mutate) {
             type[i] = kGhost;
             vel[i] = make_double4(0.0, 0.0, 0.0, 0.0);
@@ -186,7 +201,7 @@ void launch_cell_keys_only(Ctx* c, uint32_t* out_key) {
     // exported keys mark particles outside the grid (and GHOSTs) with 0xFFFFFFFF
     k_cell_keys<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(c->pos, c->vel, c->type, out_key,
                                                              nullptr, n, c->grid, c->st, 0,
-                                                             0xFFFFFFFFu);
+                                                             0xFFFFFFFFu, nullptr, nullptr, 0);
     c->launches += 1;
 }
 
@@ -195,7 +210,8 @@ int bucket_build(Ctx* c, bool mutate) {
     cudaStream_t s = c->stream;
     const int nb1 = (n + kBT - 1) / kBT;
     k_cell_keys<<<nb1, kBT, 0, s>>>(c->pos, c->vel, c->type, c->key, c->perm, n, c->grid, c->st,
-                                    mutate ? 1 : 0, c->grid.ghost_key);
+                                    mutate ? 1 : 0, c->grid.ghost_key, c->sid, c->scn,
+                                    c->scene_shift);
     // LSD radix sort over sort_bits
     const int nt = (n + kTile - 1) / kTile;
     uint32_t* kin = c->key;

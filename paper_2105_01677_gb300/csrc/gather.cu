@@ -42,13 +42,17 @@ __global__ void __launch_bounds__(BT)
     __shared__ int s_cs[27], s_pref[28];
     __shared__ int s_nc;
     const unsigned n_occ = *(volatile const unsigned*)&st->n_occ;
+    // an ensemble's keys carry the scene above the cell's Morton code: neighbour cells are
+    // looked up under the same prefix, so no gather crosses scenes
+    const uint32_t local_mask = (g.dim * g.bits >= 32) ? 0xFFFFFFFFu : ((1u << (g.dim * g.bits)) - 1u);
     for (unsigned ci = blockIdx.x; ci < n_occ; ci += gridDim.x) {
         const uint32_t code = occ[ci];
         const int c0 = cell_start[code], c1 = cell_start[code + 1];
         __syncthreads();   // previous cell's staged data and ranges no longer in use
         if (threadIdx.x == 0) {
             int cc[3];
-            morton_decode(code, g.dim, g.bits, cc);
+            const uint32_t prefix = code & ~local_mask;
+            morton_decode(code & local_mask, g.dim, g.bits, cc);
             int m = 0, pref = 0;
             const int zr = (g.dim == 3) ? 1 : 0;
             for (int dz = -zr; dz <= zr; dz++)
@@ -58,7 +62,7 @@ __global__ void __launch_bounds__(BT)
                         if (nc[0] < 0 || nc[1] < 0 || nc[2] < 0 || nc[0] >= g.ncell[0] ||
                             nc[1] >= g.ncell[1] || nc[2] >= g.ncell[2])
                             continue;
-                        uint32_t k2 = morton_encode(nc, g.dim, g.bits);
+                        uint32_t k2 = prefix | morton_encode(nc, g.dim, g.bits);
                         int s0 = cell_start[k2], s1 = cell_start[k2 + 1];
                         if (s1 > s0) {
                             s_cs[m] = s0;
@@ -152,9 +156,12 @@ struct VerletOp {
     int cap_v;
     int32_t* vcol;
     int32_t* vcnt;
+    const uint16_t* sid;        // ensemble: the scene of every slot (null: one scene)
+    const SceneParams* scn;
 
     struct Center {
         float4 p32;
+        float hv2;      // the candidate bound of the particle's scene
         int cnt;
         int32_t* row;   // entry k of this row at row[32 k] (SELL-32)
     };
@@ -163,7 +170,11 @@ struct VerletOp {
     __device__ void begin(int i, bool act, Center& c) const {
         c.cnt = 0;
         c.row = vcol + sell(i, 0, cap_v);
-        if (act) c.p32 = pos32[i];
+        c.hv2 = hv2;
+        if (act) {
+            c.p32 = pos32[i];
+            if (sid) c.hv2 = scn[sid[i]].rv.hi;
+        }
     }
     // Branch-free append: a predicated store into the row's next slot.  Past the cap every
     // hit rewrites the last slot (the row is then reported as overflowed by finish()).
@@ -181,8 +192,8 @@ struct VerletOp {
         const float2 dy = __fadd2_rn(y, make_float2(-c.p32.y, -c.p32.y));
         const float2 dz = __fadd2_rn(z, make_float2(-c.p32.z, -c.p32.z));
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        push(c, r2.x < hv2 && j.x != i, j.x);
-        push(c, r2.y < hv2 && j.y != i, j.y);
+        push(c, r2.x < c.hv2 && j.x != i, j.x);
+        push(c, r2.y < c.hv2 && j.y != i, j.y);
     }
     __device__ void finish(int i, bool act, const Center& c) const {
         if (!act) return;
@@ -278,6 +289,8 @@ void launch_verlet(Ctx* c) {
     op.cap_v = c->cap_v;
     op.vcol = c->vl_col;
     op.vcnt = c->vl_cnt;
+    op.sid = c->sid;
+    op.scn = c->scn;
     launch_gather<VerletOp>(c, op);
 }
 

@@ -71,7 +71,7 @@ struct GridDesc {
     int ncell[3];
     int bits;
     int dim;
-    uint32_t ghost_key;   // 1 << (dim*bits): sorts after every cell
+    uint32_t ghost_key;   // (number of scenes) << (dim*bits): sorts after every cell
 };
 
 // Precomputed bounds for the FP32 pre-filter of a distance predicate r^2 < re^2:
@@ -85,6 +85,24 @@ struct Radius {
     float re_l;         // re = re_f + re_l (float-float)
     double inv_re;      // 1/re (the cubic weight (1 - r/re)^3)
     float inv_f, inv_l; // 1/re as float-float
+};
+
+// Per-scene constants of a batched ensemble (one entry per scene in device memory; a
+// single-scene context has one).  The cell key of a particle is (scene << dim*bits) |
+// Morton code of its cell in the shared grid, so each scene's particles are contiguous
+// after the sort and the gathers never pair particles of different scenes.
+struct SceneParams {
+    Radius rn, rl, rv;          // predicates at re_n, re_lap and the candidate radius h_s
+    double coef_lap, coef_ppe, coef_grad;
+    double n0_pnd, n0_lap, lambda;
+    float cre_h, cre_l;         // mixed build: coef_ppe re_lap and -coef_ppe as float-float
+    float ncoef_h, ncoef_l;
+    float cre2_h, cre2_l;       // the same with coef_lap (two-phase: the pair factor holds 1/rho)
+    float ncoef2_h, ncoef2_l;
+    double own_bmin[3];         // the scene's own grid (a particle outside it is a GHOST)
+    double own_h;
+    int own_ncell[3];
+    int pad;
 };
 
 // Weight of kernel 1, (1 - r/re)^3 for r < re, from r^2 and 1/r (FP32 and binary64)
@@ -220,6 +238,16 @@ struct Ctx {
     uint32_t *mark_f, *mark_fw, *scan_f, *scan_fw;   // n + 1 each
     int32_t *rows_f, *rows_fw;
     double *ecs_nk = nullptr, *ecs_dk = nullptr;   // ECS source: n^k, (Dn/Dt)^k per row
+    // batched ensemble: scenes, their constants (device table), the scene of every slot
+    // (null for a single scene) and of every original particle, per-scene residuals
+    int n_scenes = 1;
+    std::vector<SceneParams> scn_host;
+    SceneParams* scn = nullptr;
+    uint16_t *sid = nullptr, *sid_id = nullptr;
+    double* scene_sums = nullptr;        // 2 per scene: |r_s|^2, |b_s|^2
+    std::vector<double> scene_resid;
+    uint32_t scene_shift = 0;            // dim * bits
+    double skin_half = 0.0;              // s max(re)/2 of the scene with the smallest spacing
     uint32_t* scan_scratch;
     // CG (FP64): x = p, r, d, q ; FP32: r32, d32, q32, x32
     double *cg_r, *cg_d, *cg_q;

@@ -17,6 +17,7 @@
 //
 // Reductions are deterministic: per-block partials summed in block order by the last block.
 // Convergence is decided on the device; the host polls one flag per chunk of iterations.
+#include <cmath>
 #include <mutex>
 
 #include "ff.cuh"
@@ -434,6 +435,33 @@ __global__ void __launch_bounds__(kBT) k_outer_update(int n, double* x, const fl
     }
 }
 
+// Ensemble: |r_s|^2 and |b_s|^2 of every scene (one block per scene over its contiguous
+// slot range; deterministic order)
+__global__ void __launch_bounds__(kBT) k_scene_sums(const double* r, const double* b,
+                                                    const int32_t* cell_start, uint32_t shift,
+                                                    double* out) {
+    __shared__ double sm[kWarps];
+    const int s = blockIdx.x;
+    const int lo = cell_start[(size_t)s << shift], hi = cell_start[(size_t)(s + 1) << shift];
+    double rr = 0.0, bb = 0.0;
+    for (int i = lo + (int)threadIdx.x; i < hi; i += kBT) {
+        rr = fma(r[i], r[i], rr);
+        bb = fma(b[i], b[i], bb);
+    }
+    rr = block_sum<kBT>(rr, sm);
+    bb = block_sum<kBT>(bb, sm);
+    if (threadIdx.x == 0) {
+        out[2 * s] = rr;
+        out[2 * s + 1] = bb;
+    }
+}
+
+// a tighter recurrence target for the FP64 CG (and whether the current residual meets it)
+__global__ void k_set_stop(CgScalars* cg, double stop2) {
+    cg->stop2 = stop2;
+    cg->done = (cg->rho <= stop2) ? 1 : 0;
+}
+
 __global__ void k_clear_x(int n, double* x) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) x[i] = 0.0;
@@ -507,6 +535,29 @@ static void cg32_chunk(Ctx* c, int chunk) {
     }
 }
 
+// Ensemble: every scene's relative residual from the FP64 residual in cg_r; true when all
+// are within cg_tol.  The worst is returned in *worst.
+static int scenes_converged(Ctx* c, double tol, bool* ok, double* worst) {
+    const int S = c->n_scenes;
+    k_scene_sums<<<S, kBT, 0, c->stream>>>(c->cg_r, c->bvec, c->cell_start, c->scene_shift,
+                                           c->scene_sums);
+    c->launches += 1;
+    std::vector<double> h(2 * (size_t)S);
+    MPS_CUDA(c, cudaMemcpyAsync(h.data(), c->scene_sums, sizeof(double) * h.size(),
+                                cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    double w = 0.0;
+    for (int sc = 0; sc < S; sc++) {
+        const double rr = h[2 * sc], bb = h[2 * sc + 1];
+        const double rel = bb > 0.0 ? std::sqrt(rr / bb) : (rr > 0.0 ? HUGE_VAL : 0.0);
+        c->scene_resid[(size_t)sc] = rel;
+        w = std::max(w, rel);
+    }
+    *ok = w <= tol;
+    *worst = w;
+    return MPS_OK;
+}
+
 int ppe_solve(Ctx* c, mps_report* rep) {
     const int n = (int)c->n;
     const double tol2 = c->prm.cg_tol * c->prm.cg_tol;
@@ -519,9 +570,13 @@ int ppe_solve(Ctx* c, mps_report* rep) {
     c->launches += 1;
     if ((rc = read_scalars(c))) return rc;
     const double bnorm2 = c->cg_host->rr;
-    const double stop2 = c->cg_host->stop2;
+    double stop2 = c->cg_host->stop2;
     int total_iters = 0, outer = 0;
     double rel = 0.0;
+    const bool multi = c->n_scenes > 1;
+    bool sc_ok = true;
+    double sc_worst = 0.0;
+    if (multi) std::fill(c->scene_resid.begin(), c->scene_resid.end(), 0.0);
     if (bnorm2 == 0.0) {
         rep->cg_iters = 0;
         rep->cg_outer = 0;
@@ -540,11 +595,19 @@ int ppe_solve(Ctx* c, mps_report* rep) {
             k_resid64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2, 0, 1);
             if ((rc = read_scalars(c))) return rc;
             rel = sqrt(c->cg_host->rr / bnorm2);
-            if (c->cg_host->rr <= stop2) break;
+            if (c->cg_host->rr <= stop2) {
+                if (!multi) break;
+                // ensemble: every scene to its own tolerance, else a tighter global target
+                if ((rc = scenes_converged(c, c->prm.cg_tol, &sc_ok, &sc_worst))) return rc;
+                if (sc_ok) break;
+                stop2 *= 1e-2;
+                k_set_stop<<<1, 1, 0, c->stream>>>(c->cg, stop2);
+                c->launches += 1;
+            }
             if (total_iters >= max_total) {
                 rep->cg_iters = total_iters;
                 rep->cg_outer = outer;
-                rep->cg_resid = rel;
+                rep->cg_resid = multi ? sc_worst : rel;
                 return MPS_ECG_NOCONV;
             }
             outer++;   // restart with the true residual (done was reset by k_resid64)
@@ -556,11 +619,17 @@ int ppe_solve(Ctx* c, mps_report* rep) {
         const int max_outer = c->prm.max_outer > 0 ? c->prm.max_outer : 30;
         double rr = bnorm2;
         for (;;) {
-            if (rr <= stop2) break;
+            if (rr <= stop2) {
+                if (!multi) break;
+                // ensemble: every scene to its own tolerance, else a tighter global target
+                if ((rc = scenes_converged(c, c->prm.cg_tol, &sc_ok, &sc_worst))) return rc;
+                if (sc_ok) break;
+                stop2 *= 1e-2;
+            }
             if (outer >= max_outer || total_iters >= max_total) {
                 rep->cg_iters = total_iters;
                 rep->cg_outer = outer;
-                rep->cg_resid = sqrt(rr / bnorm2);
+                rep->cg_resid = multi ? sc_worst : sqrt(rr / bnorm2);
                 return MPS_ECG_NOCONV;
             }
             c->launches += 3;
@@ -585,7 +654,8 @@ int ppe_solve(Ctx* c, mps_report* rep) {
     c->last_cg_iters = (c->prm.precision == 0) ? total_iters : std::max(4, total_iters / std::max(outer, 1));
     rep->cg_iters = total_iters;
     rep->cg_outer = outer;
-    rep->cg_resid = rel;
+    rep->cg_resid = multi ? sc_worst : rel;   // ensemble: the worst scene
+    if (!multi) c->scene_resid[0] = rel;
     MPS_CUDA(c, cudaGetLastError());
     return MPS_OK;
 }

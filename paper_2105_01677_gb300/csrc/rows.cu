@@ -80,6 +80,8 @@ struct PredictArgs {
     const uint32_t* nrows;  // their count
     const double* nu_s;     // two-phase: per-slot viscosity (null: nu)
     int kernel;             // 0: re/r - 1 (Eq. 4); 1: (1 - r/re)^3
+    const uint16_t* sid;    // ensemble: scene of every slot
+    const SceneParams* scn;
     const double4* vel;
     const float4* vel32;
     const int8_t* type;
@@ -92,13 +94,21 @@ struct PredictArgs {
     double coef_lap, nu, dt, g0, g1, g2, bmin0, bmin1, bmin2;
 };
 
-template <bool MIXED>
+// MULTI: an ensemble, whose radii and coefficients are those of each row's scene
+template <bool MIXED, bool MULTI>
 __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
     // one thread per FLUID row (the bucket build's list of FLUID slots)
     const int tid = blockIdx.x * kBT + threadIdx.x;
     const int i = tid < (int)*a.nrows ? a.rows[tid] : -1;
     double disp = 0.0;
     if (i >= 0) {
+        Radius R = a.r;
+        double coef_lap = a.coef_lap;
+        if (MULTI) {
+            const SceneParams& sp = a.scn[a.sid[i]];
+            R = sp.rl;
+            coef_lap = sp.coef_lap;
+        }
         const float4 ih = a.pos32[i], il = a.pos32lo[i];
         const double4 pi = a.pos[i];
         const double4 ui = a.vel[i];
@@ -118,8 +128,8 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
             if (k + 1 < cnt) qn = a.pos32[jn];
             if (k + 2 < cnt) jn = a.vcol[sell(i, k + 2, a.cap_v)];
             const float r2 = dist2_f(ih, jh);
-            int t = tier1(r2, a.r);
-            if (t == 2) t = decide_band(pair_r2(ih, il, jh, a.pos32lo[j]), a.r, a.pos, pi, j) ? 1 : 0;
+            int t = tier1(r2, R);
+            if (t == 2) t = decide_band(pair_r2(ih, il, jh, a.pos32lo[j]), R, a.pos, pi, j) ? 1 : 0;
             if (!t) continue;
             if (MIXED) {
                 if (!(r2 > 0.f)) {   // coincident to FP32: decide in binary64
@@ -127,7 +137,7 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
                     continue;
                 }
                 const float rs = rsqrtf(r2);
-                const float w = a.kernel == 1 ? cubic_w_f(r2, rs, a.r.inv_f) : fmaf(a.r.re_f, rs, -1.f);
+                const float w = a.kernel == 1 ? cubic_w_f(r2, rs, R.inv_f) : fmaf(R.re_f, rs, -1.f);
                 const float4 uj = a.vel32[j];
                 kahan_add(f0, e0, (uj.x - u32.x) * w);
                 kahan_add(f1, e1, (uj.y - u32.y) * w);
@@ -141,7 +151,7 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
                     continue;
                 }
                 const double rs = rsqrt(rr2);
-                const double w = a.kernel == 1 ? cubic_w_d(rr2, rs, a.r.inv_re) : fma(a.r.re, rs, -1.0);
+                const double w = a.kernel == 1 ? cubic_w_d(rr2, rs, R.inv_re) : fma(R.re, rs, -1.0);
                 const double4 uj = a.vel[j];
                 s0 = fma(uj.x - ui.x, w, s0);
                 s1 = fma(uj.y - ui.y, w, s1);
@@ -154,7 +164,7 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
             s2 = ff_to_double_fast({f2, -e2});
         }
         // u* = u + dt (nu lap(u) + g); r* = r + dt u*  (one rounding per operation)
-        const double l0 = a.coef_lap * s0, l1 = a.coef_lap * s1, l2 = a.coef_lap * s2;
+        const double l0 = coef_lap * s0, l1 = coef_lap * s1, l2 = coef_lap * s2;
         double4 us, ps;
         const double nu = a.nu_s ? a.nu_s[i] : a.nu;
         us.x = __dadd_rn(ui.x, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(nu, l0), a.g0)));
@@ -203,6 +213,8 @@ struct BuildArgs {
     double dt;
     const double* ecs_nk;   // ECS: n^k and (Dn/Dt)^k per row (source 2)
     const double* ecs_dk;
+    const uint16_t* sid;    // ensemble: scene of every slot
+    const SceneParams* scn;
     const int32_t* vcol;
     const int32_t* vcnt;
     const float4* pos32;     // r*
@@ -250,7 +262,7 @@ constexpr int kSlotMask = kEntryL - 1;
 // diagonal, and compacts the PPE coefficients in place to the front of the row.
 // KERN, SRC: the weight (0 Eq. 4, 1 cubic) and the PPE source (0 Eq. 13, 1 HS, 2 HS + ECS) as
 // compile-time choices, so that the default instantiation carries none of the options' code
-template <bool MIXED, int KERN, int SRC>
+template <bool MIXED, int KERN, int SRC, bool MULTI>
 __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
     // FLUID and WALL rows only (the bucket build's list of them): a DUMMY particle's own n*
     // enters no equation (no free-surface test, no PPE row, no gradient), so it is not
@@ -260,6 +272,19 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
     bool surf = false, ppe = false;
     unsigned n_lap = 0, n_pnd = 0;   // pairs evaluated by this row
     if (i >= 0) {
+        Radius rn = a.rn, rl = a.rl;
+        double coef_ppe = a.coef_ppe, coef0 = a.coef0, n0 = a.n0;
+        ff cre_ff = a.cre_ff, ncoef_ff = a.ncoef_ff;
+        if (MULTI) {   // the row's scene
+            const SceneParams& sp = a.scn[a.sid[i]];
+            rn = sp.rn;
+            rl = sp.rl;
+            coef_ppe = sp.coef_ppe;
+            coef0 = sp.coef_lap;
+            n0 = sp.n0_pnd;
+            cre_ff = a.rho_s ? ff{sp.cre2_h, sp.cre2_l} : ff{sp.cre_h, sp.cre_l};
+            ncoef_ff = a.rho_s ? ff{sp.ncoef2_h, sp.ncoef2_l} : ff{sp.ncoef_h, sp.ncoef_l};
+        }
         const float4 ih = a.pos32[i], il = a.pos32lo[i];
         const double4 pi = a.pos[i];
         const int cnt = a.vcnt[i];
@@ -297,8 +322,8 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
             if (k + 2 < cnt) jn = a.vcol[sell(i, k + 2, a.cap_v)];
             const float r2 = dist2_f(ih, jh);
             const bool nb_ok = kind_of(jh) != kDummy;
-            int tl = (nb_ok && with_ppe) ? tier1(r2, a.rl) : 0;
-            int tn = tier1(r2, a.rn);
+            int tl = (nb_ok && with_ppe) ? tier1(r2, rl) : 0;
+            int tn = tier1(r2, rn);
             if (!tl && !tn) continue;
             if (tl == 2 || tn == 2) {
                 if (np < kPend) {
@@ -306,8 +331,8 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                     continue;
                 }
                 const ff r2f = pair_r2(ih, il, jh, a.pos32lo[j]);
-                if (tl == 2) tl = decide_band(r2f, a.rl, a.pos, pi, j) ? 1 : 0;
-                if (tn == 2) tn = decide_band(r2f, a.rn, a.pos, pi, j) ? 1 : 0;
+                if (tl == 2) tl = decide_band(r2f, rl, a.pos, pi, j) ? 1 : 0;
+                if (tn == 2) tn = decide_band(r2f, rn, a.pos, pi, j) ? 1 : 0;
             }
             append(j, tl, tn, nb_ok);
         }
@@ -316,11 +341,11 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
             const float4 jh = a.pos32[j];
             const float r2 = dist2_f(ih, jh);
             const bool nb_ok = kind_of(jh) != kDummy;
-            int tl = (nb_ok && with_ppe) ? tier1(r2, a.rl) : 0;
-            int tn = tier1(r2, a.rn);
+            int tl = (nb_ok && with_ppe) ? tier1(r2, rl) : 0;
+            int tn = tier1(r2, rn);
             const ff r2f = pair_r2(ih, il, jh, a.pos32lo[j]);
-            if (tl == 2) tl = decide_band(r2f, a.rl, a.pos, pi, j) ? 1 : 0;
-            if (tn == 2) tn = decide_band(r2f, a.rn, a.pos, pi, j) ? 1 : 0;
+            if (tl == 2) tl = decide_band(r2f, rl, a.pos, pi, j) ? 1 : 0;
+            if (tn == 2) tn = decide_band(r2f, rn, a.pos, pi, j) ? 1 : 0;
             append(j, tl, tn, nb_ok);
         }
         // ---- dense evaluation and in-place compaction (write slot <= read slot)
@@ -335,12 +360,12 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
             // entry order into (n*, diagonal) as one packed float-float accumulator; an
             // entry without a term adds an exact zero.
             ff2 acc = {f2(0.f), f2(0.f)};
-            const ff2 ren = {f2(a.rn.re_f), f2(a.rn.re_l)};
-            const ff2 cre = {f2(a.cre_ff.h), f2(a.cre_ff.l)};
-            const ff2 ncoef = {f2(a.ncoef_ff.h), f2(a.ncoef_ff.l)};
+            const ff2 ren = {f2(rn.re_f), f2(rn.re_l)};
+            const ff2 cre = {f2(cre_ff.h), f2(cre_ff.l)};
+            const ff2 ncoef = {f2(ncoef_ff.h), f2(ncoef_ff.l)};
             const float2 rhoi = a.rho_ff ? a.rho_ff[i] : make_float2(0.f, 0.f);
-            const ff2 coef = {f2(-a.ncoef_ff.h), f2(-a.ncoef_ff.l)};
-            const ff2 invn = {f2(a.rn.inv_f), f2(a.rn.inv_l)}, invl = {f2(a.rl.inv_f), f2(a.rl.inv_l)};
+            const ff2 coef = {f2(-ncoef_ff.h), f2(-ncoef_ff.l)};
+            const ff2 invn = {f2(rn.inv_f), f2(rn.inv_l)}, invl = {f2(rl.inv_f), f2(rl.inv_l)};
             const double4 ui = SRC >= 1 ? a.vel_star[i] : make_double4(0.0, 0.0, 0.0, 0.0);
             // the entries of the next pair are loaded one iteration ahead (each slot is
             // read before the compaction can write it: writes go to slots <= t + 1)
@@ -376,9 +401,9 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                         // HS: re_n / r^3 (r_ij . (u*_j - u*_i)), binary64 from the float-float
                         // offsets and reciprocal distance
                         if (tn0) hs += hs_term(ff2_lo(dx), ff2_lo(dy), ff2_lo(dz), ff2_lo(y2),
-                                               a.vel_star[j0], ui, a.rn.re);
+                                               a.vel_star[j0], ui, rn.re);
                         if (tn1) hs += hs_term(ff2_hi(dx), ff2_hi(dy), ff2_hi(dz), ff2_hi(y2),
-                                               a.vel_star[j1], ui, a.rn.re);
+                                               a.vel_star[j1], ui, rn.re);
                     }
                 }
                 // c = coef (re/r - 1) = (coef re) y - coef, or coef (1 - r/re)^3
@@ -422,17 +447,17 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                 }
                 const double rs = rsqrt(rr2);
                 if (tn) {
-                    nd += KERN == 1 ? cubic_w_d(rr2, rs, a.rn.inv_re) : fma(a.rn.re, rs, -1.0);
+                    nd += KERN == 1 ? cubic_w_d(rr2, rs, rn.inv_re) : fma(rn.re, rs, -1.0);
                     if (SRC >= 1) {
                         const double4 uj = a.vel_star[j], ui = a.vel_star[i];
                         const double dot = fma(dz, uj.z - ui.z, fma(dy, uj.y - ui.y, dx * (uj.x - ui.x)));
-                        hs += a.rn.re * (rs * rs * rs) * dot;
+                        hs += rn.re * (rs * rs * rs) * dot;
                     }
                 }
                 if (tl) {
-                    const double wl = KERN == 1 ? cubic_w_d(rr2, rs, a.rl.inv_re) : fma(a.rl.re, rs, -1.0);
+                    const double wl = KERN == 1 ? cubic_w_d(rr2, rs, rl.inv_re) : fma(rl.re, rs, -1.0);
                     const double cd =
-                        a.rho_s ? (a.coef0 * (2.0 / (a.rho_s[i] + a.rho_s[j]))) * wl : a.coef_ppe * wl;
+                        a.rho_s ? (coef0 * (2.0 / (a.rho_s[i] + a.rho_s[j]))) * wl : coef_ppe * wl;
                     dg += cd;
                     const size_t q = sell(i, out_l++, a.cap);
                     a.lap_col[q] = j;
@@ -440,21 +465,21 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                 }
             }
         }
-        surf = nd < a.beta * a.n0;
+        surf = nd < a.beta * n0;
         ppe = !surf;
         a.nstar[i] = nd;
         a.flag[i] = surf ? 1 : 0;
         if (!ppe) a.bvec[i] = 0.0;
         else if (SRC >= 1) {
-            double bv = -hs / (a.n0 * a.dt);   // (Dn/Dt)* / (n0 dt)
+            double bv = -hs / (n0 * a.dt);   // (Dn/Dt)* / (n0 dt)
             if (SRC == 2) {                    // + ECS / dt (Eq. 24-25)
-                const double dk = a.ecs_dk[i], eps = (a.ecs_nk[i] - a.n0) / a.n0;
-                const double ecs = fabs(eps) * (dk / a.n0) + fabs(a.dt * dk / a.n0) * (eps / a.dt);
+                const double dk = a.ecs_dk[i], eps = (a.ecs_nk[i] - n0) / n0;
+                const double ecs = fabs(eps) * (dk / n0) + fabs(a.dt * dk / n0) * (eps / a.dt);
                 bv += ecs / a.dt;
             }
             a.bvec[i] = bv;
         }
-        else a.bvec[i] = a.inv_dt2 * ((nd - a.n0) / a.n0);
+        else a.bvec[i] = a.inv_dt2 * ((nd - n0) / n0);
         const double dgv = ppe ? dg + a.diag_add : 0.0;
         a.diag[i] = dgv;
         a.diag32[i] = (float)dgv;
@@ -463,7 +488,7 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
         if (overflow || out_n > a.cap_n) atomicOr(&a.st->err, kErrCap);
         if (a.pressure_mode == 1) {
             const double k = a.rho_s ? a.rho_s[i] * a.wc_c : a.wc_k;   // rho_i c0^2 / gamma
-            a.p[i] = ppe ? k * (pow(nd / a.n0, a.gamma) - 1.0) : 0.0;
+            a.p[i] = ppe ? k * (pow(nd / n0, a.gamma) - 1.0) : 0.0;
         }
         n_lap = (unsigned)out_l;
         n_pnd = (unsigned)m_f;
@@ -498,6 +523,8 @@ struct RatesArgs {
     Radius rn;
     double* nk;
     double* dk;
+    const uint16_t* sid;
+    const SceneParams* scn;
 };
 
 template <bool MIXED>
@@ -505,6 +532,7 @@ __global__ void __launch_bounds__(kBT) k_ecs_rates(RatesArgs a) {
     const int tid = blockIdx.x * kBT + threadIdx.x;
     if (tid >= (int)*a.nrows) return;
     const int i = a.rows[tid];
+    const Radius rn = a.sid ? a.scn[a.sid[i]].rn : a.rn;
     const float4 ih = a.pos32[i], il = a.pos32lo[i];
     const double4 pi = a.pos[i], ui = a.vel[i];
     const int cnt = a.vcnt[i];
@@ -514,10 +542,10 @@ __global__ void __launch_bounds__(kBT) k_ecs_rates(RatesArgs a) {
         const int j = a.vcol[sell(i, k, a.cap_v)];
         const float4 jh = a.pos32[j];
         const float r2 = dist2_f(ih, jh);
-        int t = tier1(r2, a.rn);
+        int t = tier1(r2, rn);
         if (!t) continue;
         const float4 jl = a.pos32lo[j];
-        if (t == 2 && !decide_band(pair_r2(ih, il, jh, jl), a.rn, a.pos, pi, j)) continue;
+        if (t == 2 && !decide_band(pair_r2(ih, il, jh, jl), rn, a.pos, pi, j)) continue;
         const double4 uj = a.vel[j];
         if (MIXED) {
             const ff dx = ff_diff(ih.x, il.x, jh.x, jl.x), dy = ff_diff(ih.y, il.y, jh.y, jl.y);
@@ -525,17 +553,17 @@ __global__ void __launch_bounds__(kBT) k_ecs_rates(RatesArgs a) {
             const ff rr = ff_dist2(dx, dy, dz);
             if (!(rr.h > 0.f)) continue;   // coincident pairs are reported by the prediction
             const ff y = ff_rsqrt(rr);
-            nf = ff_add(nf, ff_add_f(ff_mul({a.rn.re_f, a.rn.re_l}, y), -1.f));
-            dd += hs_term(dx, dy, dz, y, uj, ui, a.rn.re);
+            nf = ff_add(nf, ff_add_f(ff_mul({rn.re_f, rn.re_l}, y), -1.f));
+            dd += hs_term(dx, dy, dz, y, uj, ui, rn.re);
         } else {
             const double4 pj = a.pos[j];
             const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
             const double rr2 = fma(dz, dz, fma(dy, dy, dx * dx));
             if (!(rr2 > 0.0)) continue;
             const double rs = rsqrt(rr2);
-            nd += fma(a.rn.re, rs, -1.0);
+            nd += fma(rn.re, rs, -1.0);
             const double dot = fma(dz, uj.z - ui.z, fma(dy, uj.y - ui.y, dx * (uj.x - ui.x)));
-            dd += a.rn.re * (rs * rs * rs) * dot;
+            dd += rn.re * (rs * rs * rs) * dot;
         }
     }
     a.nk[i] = MIXED ? ff_to_double_fast(nf) : nd;
@@ -557,6 +585,8 @@ void launch_ecs_rates(Ctx* c) {
     a.rn = c->r_n;
     a.nk = c->ecs_nk;
     a.dk = c->ecs_dk;
+    a.sid = c->sid;
+    a.scn = c->scn;
     const int grid = (int)((c->n + kBT - 1) / kBT);
     if (c->prm.precision == 1) k_ecs_rates<true><<<grid, kBT, 0, c->stream>>>(a);
     else k_ecs_rates<false><<<grid, kBT, 0, c->stream>>>(a);
@@ -597,9 +627,35 @@ void launch_predict_rows(Ctx* c) {
     a.bmin1 = c->grid.bmin[1];
     a.bmin2 = c->grid.bmin[2];
     const int grid = (int)((c->n + kBT - 1) / kBT);
-    if (P.precision == 1) k_predict<true><<<grid, kBT, 0, c->stream>>>(a);
-    else k_predict<false><<<grid, kBT, 0, c->stream>>>(a);
+    a.sid = c->sid;
+    a.scn = c->scn;
+    const bool multi = c->n_scenes > 1;
+    if (P.precision == 1) {
+        if (multi) k_predict<true, true><<<grid, kBT, 0, c->stream>>>(a);
+        else k_predict<true, false><<<grid, kBT, 0, c->stream>>>(a);
+    } else {
+        if (multi) k_predict<false, true><<<grid, kBT, 0, c->stream>>>(a);
+        else k_predict<false, false><<<grid, kBT, 0, c->stream>>>(a);
+    }
     c->launches += 1;
+}
+
+// (kernel, source): (0, 0), (0, 1), (0, 2), (1, 0); the cubic weight with HS is rejected
+template <bool MULTI>
+static void launch_build_t(Ctx* c, const BuildArgs& a, int grid) {
+    const mps_params& P = c->prm;
+    const int src = P.source_term;
+    if (P.precision == 1) {
+        if (P.kernel == 1) k_build<true, 1, 0, MULTI><<<grid, kBT, 0, c->stream>>>(a);
+        else if (src == 0) k_build<true, 0, 0, MULTI><<<grid, kBT, 0, c->stream>>>(a);
+        else if (src == 1) k_build<true, 0, 1, MULTI><<<grid, kBT, 0, c->stream>>>(a);
+        else k_build<true, 0, 2, MULTI><<<grid, kBT, 0, c->stream>>>(a);
+    } else {
+        if (P.kernel == 1) k_build<false, 1, 0, MULTI><<<grid, kBT, 0, c->stream>>>(a);
+        else if (src == 0) k_build<false, 0, 0, MULTI><<<grid, kBT, 0, c->stream>>>(a);
+        else if (src == 1) k_build<false, 0, 1, MULTI><<<grid, kBT, 0, c->stream>>>(a);
+        else k_build<false, 0, 2, MULTI><<<grid, kBT, 0, c->stream>>>(a);
+    }
 }
 
 void launch_build_rows(Ctx* c) {
@@ -656,19 +712,10 @@ void launch_build_rows(Ctx* c) {
     a.diag32 = c->diag32;
     a.p = c->p;
     const int grid = (int)((c->n + kBT - 1) / kBT);
-    // (kernel, source): (0, 0), (0, 1), (0, 2), (1, 0); the cubic weight with HS is rejected
-    const int src = P.source_term;
-    if (P.precision == 1) {
-        if (P.kernel == 1) k_build<true, 1, 0><<<grid, kBT, 0, c->stream>>>(a);
-        else if (src == 0) k_build<true, 0, 0><<<grid, kBT, 0, c->stream>>>(a);
-        else if (src == 1) k_build<true, 0, 1><<<grid, kBT, 0, c->stream>>>(a);
-        else k_build<true, 0, 2><<<grid, kBT, 0, c->stream>>>(a);
-    } else {
-        if (P.kernel == 1) k_build<false, 1, 0><<<grid, kBT, 0, c->stream>>>(a);
-        else if (src == 0) k_build<false, 0, 0><<<grid, kBT, 0, c->stream>>>(a);
-        else if (src == 1) k_build<false, 0, 1><<<grid, kBT, 0, c->stream>>>(a);
-        else k_build<false, 0, 2><<<grid, kBT, 0, c->stream>>>(a);
-    }
+    a.sid = c->sid;
+    a.scn = c->scn;
+    if (c->n_scenes > 1) launch_build_t<true>(c, a, grid);
+    else launch_build_t<false>(c, a, grid);
     c->launches += 1;
 }
 

@@ -47,6 +47,8 @@ struct Keep {
     double inv_re;          // 1/re_n
     float inv_f;
     const double* rho_s;    // two-phase: per-slot density (null: the uniform rho)
+    const uint16_t* sid;    // ensemble: scene of every slot (null: one scene)
+    const SceneParams* scn;
     const double4* pos_b;   // null: lists are gathered every step (nothing else is used)
     float4* pos32;
     float4* pos32lo;
@@ -69,6 +71,16 @@ __device__ __forceinline__ double gradient_row(int i, const int8_t* type, const 
     const double ph = phat[i];
     const double pp = p[i];
     const int cnt = ncnt[i];
+    double inv_re = kp.inv_re;
+    float inv_f = kp.inv_f;
+    if (kp.sid) {   // ensemble: the row's scene
+        const SceneParams& sp = kp.scn[kp.sid[i]];
+        re = sp.rn.re;
+        re_f = sp.rn.re_f;
+        coef_grad = sp.coef_grad;
+        inv_re = sp.rn.inv_re;
+        inv_f = sp.rn.inv_f;
+    }
     double g0 = 0.0, g1 = 0.0, g2 = 0.0;
     if (MIXED) {
         const float4 qi = ps32[i];
@@ -79,7 +91,7 @@ __device__ __forceinline__ double gradient_row(int i, const int8_t* type, const 
             const float dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
             const float rs = rsqrtf(r2);
-            const float w = kp.kernel == 1 ? cubic_w_f(r2, rs, kp.inv_f) : fmaf(re_f, rs, -1.f);
+            const float w = kp.kernel == 1 ? cubic_w_f(r2, rs, inv_f) : fmaf(re_f, rs, -1.f);
             const double dp = kp.form == 1 ? (pp + p[j]) - (ph + phat[j]) : p[j] - ph;
             const float f = (float)dp * (w * rs * rs);
             f0 = fmaf(f, dx, f0);
@@ -96,7 +108,7 @@ __device__ __forceinline__ double gradient_row(int i, const int8_t* type, const 
             const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
             const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
             const double rs = rsqrt(r2);
-            const double w = kp.kernel == 1 ? cubic_w_d(r2, rs, kp.inv_re) : fma(re, rs, -1.0);
+            const double w = kp.kernel == 1 ? cubic_w_d(r2, rs, inv_re) : fma(re, rs, -1.0);
             const double dp = kp.form == 1 ? (pp + p[j]) - (ph + phat[j]) : p[j] - ph;
             const double f = dp * (w * rs * rs);
             g0 = fma(f, dx, g0);
@@ -225,14 +237,17 @@ __global__ void __launch_bounds__(kBT)
     pos32[s] = h;
     pos32lo[s] = l;
 }
-// two-phase properties into slot order (slot s holds particle id[s]); the density also as
-// float-float for the pair factors of the mixed build
+// per-particle properties into slot order (slot s holds particle id[s]): two-phase density
+// (also as float-float for the pair factors of the mixed build) and viscosity, and the
+// scene of an ensemble
 __global__ void __launch_bounds__(kBT)
     k_gather_props(int n, const int32_t* id, const double* rho_id, const double* nu_id,
-                   double* rho_s, double* nu_s, float2* rho_ff) {
+                   double* rho_s, double* nu_s, float2* rho_ff, const uint16_t* sid_id,
+                   uint16_t* sid) {
     int s = blockIdx.x * kBT + threadIdx.x;
     if (s >= n) return;
     const int q = id[s];
+    if (sid_id) sid[s] = sid_id[q];
     if (rho_id) {
         const double r = rho_id[q];
         const float h = (float)r;
@@ -264,6 +279,8 @@ void launch_gradient_correct(Ctx* c) {
     kp.inv_re = c->r_n.inv_re;
     kp.inv_f = c->r_n.inv_f;
     kp.rho_s = c->rho_s;
+    kp.sid = c->sid;
+    kp.scn = c->scn;
     kp.pos_b = c->pos_b;
     kp.pos32 = c->pos32;
     kp.pos32lo = c->pos32lo;
@@ -294,10 +311,11 @@ void launch_unpermute(Ctx* c, double* d_pos, double* d_vel, double* d_p, double*
 }
 
 void launch_gather_props(Ctx* c) {
-    if (!c->rho_id && !c->nu_id) return;
+    if (!c->rho_id && !c->nu_id && !c->sid_id) return;
     const int n = (int)c->n;
     k_gather_props<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(n, c->id, c->rho_id, c->nu_id,
-                                                               c->rho_s, c->nu_s, c->rho_ff);
+                                                               c->rho_s, c->nu_s, c->rho_ff,
+                                                               c->sid_id, c->sid);
     c->launches += 1;
 }
 

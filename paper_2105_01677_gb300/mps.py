@@ -42,6 +42,10 @@ class mps_params(C.Structure):
                 ("alloc_user", C.c_void_p)]
 
 
+class mps_scene(C.Structure):
+    _fields_ = [("l0", C.c_double), ("box_min", C.c_double * 3), ("box_max", C.c_double * 3)]
+
+
 class mps_report(C.Structure):
     _fields_ = [("status", C.c_int32), ("cg_iters", C.c_int32), ("cg_outer", C.c_int32),
                 ("list_gathered", C.c_int32), ("cg_resid", C.c_double), ("n_surface", C.c_int64),
@@ -59,7 +63,8 @@ class mps_report(C.Structure):
 EXPORTS = ("mps_params_default", "mps_create", "mps_step", "mps_solve_ppe", "mps_read_state",
            "mps_write_state", "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants",
            "mps_set_profiling", "mps_get_profile", "mps_ppe_cg_noalloc", "mps_destroy",
-           "mps_strerror", "mps_set_fluid_properties")
+           "mps_strerror", "mps_set_fluid_properties", "mps_create_ensemble",
+           "mps_scene_residuals")
 NOALLOC_MAX_ROWS = 262144
 STAGES = ("bucket", "gather", "predict", "build", "ppe", "update")
 
@@ -91,6 +96,10 @@ def lib(build_if_missing: bool = False):
     L.mps_read_state.argtypes = [C.c_void_p, d, d, d, d, u8, i8]
     L.mps_write_state.argtypes = [C.c_void_p, d, d, i8]
     L.mps_set_fluid_properties.argtypes = [C.c_void_p, d, d]
+    L.mps_create_ensemble.argtypes = [d, d, i8, C.POINTER(C.c_int32), C.c_int64,
+                                      C.POINTER(mps_params), C.POINTER(mps_scene), C.c_int32,
+                                      C.POINTER(C.c_void_p)]
+    L.mps_scene_residuals.argtypes = [C.c_void_p, d]
     L.mps_debug_cells.argtypes = [C.c_void_p, C.POINTER(C.c_uint32)]
     L.mps_debug_neighbors.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int32), C.c_int64]
@@ -106,7 +115,8 @@ def lib(build_if_missing: bool = False):
     L.mps_strerror.restype = C.c_char_p
     for f in ("mps_create", "mps_step", "mps_solve_ppe", "mps_read_state", "mps_write_state",
               "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants", "mps_set_profiling",
-              "mps_get_profile", "mps_ppe_cg_noalloc", "mps_set_fluid_properties"):
+              "mps_get_profile", "mps_ppe_cg_noalloc", "mps_set_fluid_properties",
+              "mps_create_ensemble", "mps_scene_residuals"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -200,6 +210,47 @@ def mps_create(pos, vel, types, params: mps_params, torch_alloc: bool = False,
 
 
 _keepalive = {}
+
+
+def mps_create_ensemble(pos, vel, types, scene, params: mps_params, scenes,
+                        torch_alloc: bool = False, use_torch_stream: bool = False):
+    """Create an ensemble context: scene[i] in [0, len(scenes)); scenes: sequence of
+    (l0, box_min, box_max).  Returns the handle."""
+    L = lib()
+    pos = np.ascontiguousarray(pos, np.float64)
+    vel = None if vel is None else np.ascontiguousarray(vel, np.float64)
+    types = np.ascontiguousarray(types, np.int8)
+    scene = np.ascontiguousarray(scene, np.int32)
+    n = len(types)
+    S = len(scenes)
+    tab = (mps_scene * S)()
+    for s, (l0, bmin, bmax) in enumerate(scenes):
+        tab[s].l0 = float(l0)
+        for a in range(3):
+            tab[s].box_min[a] = float(bmin[a]) if a < len(bmin) else 0.0
+            tab[s].box_max[a] = float(bmax[a]) if a < len(bmax) else 0.0
+    keep = None
+    if torch_alloc or use_torch_stream:
+        import torch
+        dev = int(params.device)
+        if use_torch_stream:
+            params.stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+        if torch_alloc:
+            keep = _TorchAllocator(dev, params.stream)
+            params.alloc = keep.alloc
+            params.release = keep.release
+    h = C.c_void_p()
+    rc = L.mps_create_ensemble(_ptr(pos, C.c_double), _ptr(vel, C.c_double), _ptr(types, C.c_int8),
+                               _ptr(scene, C.c_int32), n, C.byref(params), tab, S, C.byref(h))
+    _check(rc, "mps_create_ensemble")
+    _keepalive[h.value] = (keep, params)
+    return h
+
+
+def mps_scene_residuals(h, n_scenes: int):
+    out = np.zeros(n_scenes, np.float64)
+    _check(lib().mps_scene_residuals(h, _ptr(out, C.c_double)), "mps_scene_residuals")
+    return out
 
 
 def mps_step(h, nsteps: int = 1, check: bool = True):
@@ -314,6 +365,56 @@ def mps_destroy(h):
     if h is not None and h.value:
         lib().mps_destroy(h)
         _keepalive.pop(h.value, None)
+
+
+class Ensemble:
+    """Convenience owner of an ensemble context built from a list of scene-like objects
+    (all of one dimension), concatenated in order; read() returns per-scene states."""
+
+    def __init__(self, scene_list, torch_alloc: bool = False, use_torch_stream: bool = False,
+                 **params):
+        self.scenes = list(scene_list)
+        self.dim = self.scenes[0].dim
+        self.sizes = [sc.n for sc in self.scenes]
+        self.n = int(sum(self.sizes))
+        pos = np.concatenate([sc.pos for sc in self.scenes])
+        vel = np.concatenate([sc.vel for sc in self.scenes])
+        types = np.concatenate([sc.types for sc in self.scenes])
+        scene = np.concatenate([np.full(sc.n, s, np.int32) for s, sc in enumerate(self.scenes)])
+        sc0 = self.scenes[0]
+        g = (0.0, -9.81, 0.0) if self.dim == 2 else (0.0, 0.0, -9.81)
+        base = dict(dim=self.dim, l0=sc0.l0, re_n=2.1 * sc0.l0, re_lap=4.0 * sc0.l0, g=g,
+                    box_min=tuple(sc0.box_min), box_max=tuple(sc0.box_max))
+        base.update(params)
+        self.params = mps_params_default(**base)
+        tab = [(sc.l0, tuple(sc.box_min), tuple(sc.box_max)) for sc in self.scenes]
+        self.h = mps_create_ensemble(pos, vel, types, scene, self.params, tab, torch_alloc,
+                                     use_torch_stream)
+
+    def step(self, nsteps: int = 1, check: bool = True):
+        return mps_step(self.h, nsteps, check)
+
+    def read(self, **kw):
+        st = mps_read_state(self.h, self.n, self.dim, **kw)
+        out, o = [], 0
+        for m in self.sizes:
+            out.append({k: v[o:o + m] for k, v in st.items()})
+            o += m
+        return out
+
+    def residuals(self):
+        return mps_scene_residuals(self.h, len(self.scenes))
+
+    def close(self):
+        mps_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            if self.h is not None:
+                self.close()
+        except Exception:
+            pass
 
 
 class Simulation:

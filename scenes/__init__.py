@@ -166,6 +166,26 @@ def two_phase(scene: Scene, rho=(1000.0, 800.0), nu=(1e-6, 5e-6)):
     return rho_i, nu_i
 
 
+def ensemble_2d(count: int = 256, seed: int = 1, fluid=(500, 20000), aspect=(0.5, 2.0),
+                l0=(0.005, 0.01)) -> list:
+    """Independent 2D dam breaks of seeded sizes: per scene a fluid count, a column aspect
+    (height / width) and a particle spacing drawn uniformly from the given ranges (counter-
+    based SplitMix64 draws of (seed, scene)); the column of nx x ny lattice sites
+    (nx ny ~ fluid count, ny / nx ~ aspect) stands in the corner of a tank 4 nx wide and
+    1.25 ny high (the proportions of the 2D dam break), 2 wall + 2 dummy layers."""
+    out = []
+    for s in range(count):
+        u = splitmix_uniform(seed, np.arange(4 * s, 4 * s + 4, dtype=np.uint64))
+        nf = fluid[0] + u[0] * (fluid[1] - fluid[0])
+        a = aspect[0] + u[1] * (aspect[1] - aspect[0])
+        h = l0[0] + u[2] * (l0[1] - l0[0])
+        nx = max(2, int(round(np.sqrt(nf / a))))
+        ny = max(2, int(round(a * nx)))
+        out.append(tank_scene(2, h, (4 * nx, int(np.ceil(1.25 * ny))), (nx, ny),
+                              seed=seed * 100003 + s, jitter=1e-4))
+    return out
+
+
 def still_tank_2d(l0: float = 0.01, width: float = 0.2, depth: float = 0.2, seed: int = 1,
                   jitter: float = 0.0) -> Scene:
     """Fluid at rest filling the full width of a 2D tank (hydrostatic check)."""
