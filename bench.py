@@ -10,7 +10,8 @@ The headline `value` is the mixed-precision path (FP32 pair terms and inner CG, 
 density, dot products and refinement); the plain FP64 path is timed on the same scene and
 reported under "fp64", and the mixed path with candidate lists kept for up to 4 steps
 under "kept_lists" (exact neighbour sets either way); the two-phase 3D dam break (Sec. 3.2.1,
-l0 = 0.004 m, 1,125,000 fluid particles) under "two_phase".  `e2e` repeats the mixed measurement through the C ABI with host
+l0 = 0.004 m, 1,125,000 fluid particles) under "two_phase"; 256 independent 2D dam breaks
+stepped together in one context under "ensemble".  `e2e` repeats the mixed measurement through the C ABI with host
 buffers: every step uploads positions, velocities and kinds from pinned memory and reads
 back positions, velocities and pressure.
 
@@ -74,7 +75,7 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l0", type=float, default=0.0075, help="particle spacing (testing only)")
-    ap.add_argument("--only", choices=["mixed", "fp64"], default=None,
+    ap.add_argument("--only", choices=["mixed", "fp64", "ensemble"], default=None,
                     help="time one precision only and print its stage profile (profiling runs)")
     ap.add_argument("--list-every", type=int, default=0,
                     help="with --only: keep candidate lists for up to this many steps")
@@ -83,6 +84,9 @@ def parse():
     ap.add_argument("--two-phase-steps", type=int, default=20,
                     help="timed steps of each two-phase path (0: skip)")
     ap.add_argument("--two-phase-l0", type=float, default=0.004)
+    ap.add_argument("--ensemble-steps", type=int, default=20,
+                    help="timed steps of the batched ensemble (0: skip)")
+    ap.add_argument("--ensemble-scenes", type=int, default=256)
     return ap.parse_args()
 
 
@@ -259,6 +263,23 @@ def run_gb300(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    if args.only == "ensemble":
+        E = scenes.ensemble_2d(count=args.ensemble_scenes, seed=args.seed + rank)
+        ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
+                           cg_tol=1e-8)
+        gb = ens.autotune(3)
+        ens.step(args.warmup)
+        barrier()
+        ms, its, prof = timed_steps(ens, args.steps, profile=True)
+        res = ens.residuals()
+        ens.close()
+        if rank == 0:
+            print(json.dumps({"only": "ensemble", "particles": sum(sc.n for sc in E),
+                              "ms_per_step": ms / args.steps, "gather_block": gb,
+                              "value": sum(sc.n for sc in E) * args.steps / (ms * 1e-3),
+                              "cg": [x[:3] for x in its], "worst_resid": float(res.max()),
+                              "profile": prof}), flush=True)
+        return
     if args.only:
         prec = 1 if args.only == "mixed" else 0
         simo = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, precision=prec,
@@ -332,6 +353,34 @@ def run_gb300(args):
             if mode == 0:
                 two_phase[name]["cg_iters_mean"] = float(np.mean([x[0] for x in it2]))
         del sc2, rho_i, nu_i
+
+    # ---- batched ensemble: independent 2D dam breaks of seeded sizes in one context, mixed
+    ensemble = None
+    if args.ensemble_steps > 0:
+        E = scenes.ensemble_2d(count=args.ensemble_scenes, seed=args.seed + rank)
+        ne = sum(sc.n for sc in E)
+        ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
+                           cg_tol=1e-8)
+        gb = ens.autotune(3)
+        ens.step(args.warmup)
+        barrier()
+        ke = args.ensemble_steps
+        launches0 = mps.mps_get_profile(ens.h)["launches"]
+        ms_e, it_e, prof_e = timed_steps(ens, ke, profile=True)
+        barrier()
+        ms_e = max_over_ranks(ms_e)
+        res = ens.residuals()
+        ens.close()
+        ensemble = {"workload": f"{len(E)} independent 2D dam breaks, 500-20,000 fluid particles, "
+                                "column aspect 0.5-2, l0 0.005-0.01 m, dt 1e-4 s",
+                    "scenes": len(E), "particles": ne, "fluid": int(sum(sc.n_fluid for sc in E)),
+                    "value": world * ne * ke / (ms_e * 1e-3), "unit": UNIT,
+                    "ms_per_step": ms_e / ke, "steps": ke, "gather_block": gb,
+                    "cg_iters_mean": float(np.mean([x[0] for x in it_e])),
+                    "worst_scene_resid": float(res.max()),
+                    "launches_per_step": (prof_e["launches"] - launches0) / max(ke, 1),
+                    "stage_ms_per_step": {k: prof_e["stage_ms"][k] / ke for k in prof_e["stage_ms"]}}
+        del E
 
     # ---- end to end through the C ABI with host buffers (mixed)
     ke = args.e2e_steps or args.steps
@@ -411,6 +460,7 @@ def run_gb300(args):
                                        for k in prof64["stage_ms"]}},
         "mixed_over_fp64": value / value64,
         "two_phase": two_phase,
+        "ensemble": ensemble,
         "kept_lists": {"list_every": 4, "value": world * n * kk / (ms_k * 1e-3), "unit": UNIT,
                        "ms_per_step": ms_k / kk, "steps": kk,
                        "gathers": int(profk["stage_calls"]["gather"]),

@@ -83,7 +83,9 @@ typedef struct {
                                * MPS_ESKIN if a particle moves more than s max(re)/2           */
     double box_min[3];        /* cell grid origin [m]; unused axes ignored                    */
     double box_max[3];        /* cell grid extent: ncell = floor((max - min)/h) + 1 per axis  */
-    double inner_tol;         /* mixed: relative residual reduction of each FP32 inner CG      */
+    double inner_tol;         /* mixed: relative residual reduction of an FP32 inner CG that   *
+                               * cannot finish the solve; the sweep that can (the reduction    *
+                               * still needed, with a margin of 2, is >= 1e-6) asks for that   */
     int32_t max_outer;        /* mixed: cap on FP64 refinement sweeps                          */
     int32_t ppe_operator;     /* mixed inner operator: 0 stored FP32 coefficients,             *
                                * 1 matrix-free (coefficients recomputed from positions)        */
@@ -237,6 +239,14 @@ typedef struct {
 int mps_create_ensemble(const double* pos, const double* vel, const int8_t* types,
                         const int32_t* scene, int64_t n, const mps_params* params,
                         const mps_scene* scenes, int32_t n_scenes, mps_ctx** out);
+
+/* Autotuning (a tool of this library; the paper has none): times the candidate gather of
+ * the current state with each block shape (32, 64, 96 and 128 threads per cell block,
+ * `repeats` launches each, CUDA events on the context's stream) and keeps the fastest in
+ * params.gather_block, which *gather_block (nullable) receives.  Candidate lists come out
+ * identical whatever the shape, so results do not change; the state is reordered as by a
+ * step's bucket build.  Errors: MPS_EINVAL (repeats < 1), MPS_EDEVICE. */
+int mps_autotune(mps_ctx* ctx, int32_t repeats, int32_t* gather_block);
 
 /* Relative PPE residual ||b_s - A_s p_s|| / ||b_s|| of every scene after the last step
  * (n_scenes doubles; 0 for a scene with b_s = 0); a single-scene context writes one. */

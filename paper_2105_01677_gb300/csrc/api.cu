@@ -662,6 +662,50 @@ int mps_create_ensemble(const double* pos, const double* vel, const int8_t* type
     return MPS_OK;
 }
 
+int mps_autotune(mps_ctx* c, int32_t repeats, int32_t* gather_block) {
+    if (!c || repeats < 1) return MPS_EINVAL;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    int rc;
+    MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
+    if ((rc = bucket_build(c, true))) return rc;
+    c->need_list = true;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return MPS_EDEVICE;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return MPS_EDEVICE;
+    }
+    const int shapes[4] = {32, 64, 96, 128};
+    int best = c->prm.gather_block;
+    float best_ms = 1e30f;
+    const size_t n = (size_t)c->n;
+    for (int b : shapes) {
+        c->prm.gather_block = b;
+        float ms = 0.f;
+        for (int r = 0; r <= repeats; r++) {   // the first launch warms up
+            cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), c->stream);
+            cudaEventRecord(e0, c->stream);
+            launch_verlet(c);
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (r > 0) ms += t;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = b;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->prm.gather_block = best;
+    if (gather_block) *gather_block = best;
+    MPS_CUDA(c, cudaGetLastError());
+    return MPS_OK;
+}
+
 int mps_scene_residuals(mps_ctx* c, double* out) {
     if (!c || !out) return MPS_EINVAL;
     for (int s = 0; s < c->n_scenes; s++) out[s] = c->scene_resid[(size_t)s];

@@ -28,6 +28,8 @@ namespace mps {
 namespace {
 constexpr int kBT = 256;
 constexpr int kWarps = kBT / 32;
+// smallest relative reduction asked of one FP32 inner solve (its rounding floor is ~1e-7)
+constexpr double kInnerFloor = 1e-6;
 
 // Plain-data view of a row-major PPE operator (the allocation-free entry point's layout).
 struct PpeView {
@@ -558,6 +560,13 @@ static int scenes_converged(Ctx* c, double tol, bool* ok, double* worst) {
     return MPS_OK;
 }
 
+// Factor for the global squared-residual target when the worst scene is at `worst` > tol:
+// the square of the reduction it still needs, with a margin of 2
+static double tighten(double tol, double worst) {
+    const double f = 0.25 * (tol / worst) * (tol / worst);
+    return std::min(0.5, std::max(f, 1e-8));
+}
+
 int ppe_solve(Ctx* c, mps_report* rep) {
     const int n = (int)c->n;
     const double tol2 = c->prm.cg_tol * c->prm.cg_tol;
@@ -600,7 +609,7 @@ int ppe_solve(Ctx* c, mps_report* rep) {
                 // ensemble: every scene to its own tolerance, else a tighter global target
                 if ((rc = scenes_converged(c, c->prm.cg_tol, &sc_ok, &sc_worst))) return rc;
                 if (sc_ok) break;
-                stop2 *= 1e-2;
+                stop2 *= tighten(c->prm.cg_tol, sc_worst);
                 k_set_stop<<<1, 1, 0, c->stream>>>(c->cg, stop2);
                 c->launches += 1;
             }
@@ -615,7 +624,6 @@ int ppe_solve(Ctx* c, mps_report* rep) {
         }
     } else {
         // mixed: x = 0, r = b already.  Loop: inner FP32 solve, x += e, true residual.
-        const double itol2 = c->prm.inner_tol * c->prm.inner_tol;
         const int max_outer = c->prm.max_outer > 0 ? c->prm.max_outer : 30;
         double rr = bnorm2;
         for (;;) {
@@ -624,7 +632,7 @@ int ppe_solve(Ctx* c, mps_report* rep) {
                 // ensemble: every scene to its own tolerance, else a tighter global target
                 if ((rc = scenes_converged(c, c->prm.cg_tol, &sc_ok, &sc_worst))) return rc;
                 if (sc_ok) break;
-                stop2 *= 1e-2;
+                stop2 *= tighten(c->prm.cg_tol, sc_worst);
             }
             if (outer >= max_outer || total_iters >= max_total) {
                 rep->cg_iters = total_iters;
@@ -632,10 +640,15 @@ int ppe_solve(Ctx* c, mps_report* rep) {
                 rep->cg_resid = multi ? sc_worst : sqrt(rr / bnorm2);
                 return MPS_ECG_NOCONV;
             }
+            // inner reduction: exactly what the outer target still needs (with a margin of 2)
+            // when one FP32 solve can reach it, so that the sweep that can finish does so
+            // without overshooting; inner_tol for the sweeps before it
+            const double need = 0.5 * std::sqrt(stop2 / rr);
+            const double itol_k = (need >= kInnerFloor) ? need : c->prm.inner_tol;
             c->launches += 3;
             k_inner_init<<<gv, kBT, 0, c->stream>>>(n, c->cg_r, c->cg_r32, c->cg_d32, c->cg_x32, c->cg,
-                                                    itol2, max_total - total_iters, c->partials,
-                                                    &c->st->counter[3]);
+                                                    itol_k * itol_k, max_total - total_iters,
+                                                    c->partials, &c->st->counter[3]);
             for (;;) {
                 cg32_chunk(c, chunk);
                 if ((rc = read_scalars(c))) return rc;

@@ -64,7 +64,7 @@ EXPORTS = ("mps_params_default", "mps_create", "mps_step", "mps_solve_ppe", "mps
            "mps_write_state", "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants",
            "mps_set_profiling", "mps_get_profile", "mps_ppe_cg_noalloc", "mps_destroy",
            "mps_strerror", "mps_set_fluid_properties", "mps_create_ensemble",
-           "mps_scene_residuals")
+           "mps_scene_residuals", "mps_autotune")
 NOALLOC_MAX_ROWS = 262144
 STAGES = ("bucket", "gather", "predict", "build", "ppe", "update")
 
@@ -100,6 +100,7 @@ def lib(build_if_missing: bool = False):
                                       C.POINTER(mps_params), C.POINTER(mps_scene), C.c_int32,
                                       C.POINTER(C.c_void_p)]
     L.mps_scene_residuals.argtypes = [C.c_void_p, d]
+    L.mps_autotune.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]
     L.mps_debug_cells.argtypes = [C.c_void_p, C.POINTER(C.c_uint32)]
     L.mps_debug_neighbors.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int32), C.c_int64]
@@ -116,7 +117,7 @@ def lib(build_if_missing: bool = False):
     for f in ("mps_create", "mps_step", "mps_solve_ppe", "mps_read_state", "mps_write_state",
               "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants", "mps_set_profiling",
               "mps_get_profile", "mps_ppe_cg_noalloc", "mps_set_fluid_properties",
-              "mps_create_ensemble", "mps_scene_residuals"):
+              "mps_create_ensemble", "mps_scene_residuals", "mps_autotune"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -245,6 +246,13 @@ def mps_create_ensemble(pos, vel, types, scene, params: mps_params, scenes,
     _check(rc, "mps_create_ensemble")
     _keepalive[h.value] = (keep, params)
     return h
+
+
+def mps_autotune(h, repeats: int = 3) -> int:
+    """Pick the fastest gather block shape for the current state; returns it."""
+    b = C.c_int32()
+    _check(lib().mps_autotune(h, int(repeats), C.byref(b)), "mps_autotune")
+    return int(b.value)
 
 
 def mps_scene_residuals(h, n_scenes: int):
@@ -405,6 +413,9 @@ class Ensemble:
     def residuals(self):
         return mps_scene_residuals(self.h, len(self.scenes))
 
+    def autotune(self, repeats: int = 3) -> int:
+        return mps_autotune(self.h, repeats)
+
     def close(self):
         mps_destroy(self.h)
         self.h = None
@@ -450,6 +461,9 @@ class Simulation:
 
     def constants(self):
         return mps_get_constants(self.h)
+
+    def autotune(self, repeats: int = 3) -> int:
+        return mps_autotune(self.h, repeats)
 
     def close(self):
         mps_destroy(self.h)

@@ -108,3 +108,21 @@ def test_ensemble_multi_step_mixed_runs_and_converges():
     assert rep["steps_done"] == 10 and np.all(res <= 1e-8)
     for g in got:
         assert np.all(np.isfinite(g["pos"])) and np.all(np.isfinite(g["p"]))
+
+
+def test_autotune_keeps_results_bitwise():
+    from paper_2105_01677_gb300 import mps
+    E = _ensemble(count=4, seed=7)
+    outs = []
+    for tune in (False, True):
+        ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, cg_tol=1e-10)
+        try:
+            if tune:
+                assert ens.autotune(2) in (32, 64, 96, 128)
+            ens.step(2)
+            outs.append(ens.read())
+        finally:
+            ens.close()
+    for a, b in zip(*outs):
+        for k in ("pos", "vel", "p", "n_star", "flags"):
+            assert np.array_equal(a[k], b[k]), k
