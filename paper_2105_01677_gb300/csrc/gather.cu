@@ -24,7 +24,8 @@ namespace mps {
 
 namespace {
 
-// One block per occupied cell, one thread per particle of the cell.  The particles of the
+// One block per occupied cell (taken in turn from a device counter), one thread per
+// particle of the cell.  The particles of the
 // 3^d surrounding cells (contiguous slot ranges in Morton order) are staged once in shared
 // memory as (x, y, z, slot) and every thread walks the same staged candidates, four per
 // shared-memory load, so each read is a broadcast; one barrier pair per cell (more only when a cell's
@@ -45,7 +46,13 @@ __global__ void __launch_bounds__(BT)
     // an ensemble's keys carry the scene above the cell's Morton code: neighbour cells are
     // looked up under the same prefix, so no gather crosses scenes
     const uint32_t local_mask = (g.dim * g.bits >= 32) ? 0xFFFFFFFFu : ((1u << (g.dim * g.bits)) - 1u);
-    for (unsigned ci = blockIdx.x; ci < n_occ; ci += gridDim.x) {
+    __shared__ unsigned s_ci;
+    for (;;) {
+        __syncthreads();   // s_ci of the previous cell has been read by every thread
+        if (threadIdx.x == 0) s_ci = atomicAdd(&((DevStatus*)st)->gather_next, 1u);
+        __syncthreads();
+        const unsigned ci = s_ci;
+        if (ci >= n_occ) break;
         const uint32_t code = occ[ci];
         const int c0 = cell_start[code], c1 = cell_start[code + 1];
         __syncthreads();   // previous cell's staged data and ranges no longer in use
@@ -253,6 +260,9 @@ __global__ void k_copy_star(int n, const double4* pos, const double4* vel, const
 template <int BT, class Op>
 void launch_gather_bt(Ctx* c, const Op& op, int blocks_per_sm) {
     constexpr int kChunk = 512;
+    // blocks take occupied cells from a counter: cells differ a lot in work (full fluid
+    // cells against sparse wall or surface cells), so a static split leaves SMs idle
+    cudaMemsetAsync(&c->st->gather_next, 0, sizeof(unsigned int), c->stream);
     k_gather<BT, kChunk, Op><<<c->sms * blocks_per_sm, BT, kChunk * 4 * sizeof(float), c->stream>>>(
         op, c->cell_start, c->occ, c->st, c->grid);
 }

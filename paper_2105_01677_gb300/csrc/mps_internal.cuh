@@ -49,6 +49,8 @@ struct DevStatus {
     unsigned long long pairs_lap;       // PPE coefficients evaluated (pairs within re_lap)
     unsigned long long pairs_n;         // number-density terms evaluated (pairs within re_n)
     unsigned long long max_disp_next_bits;   // kept lists: max squared |r^{k+1} - r_b| (as above)
+    unsigned int gather_next;           // next occupied cell of the candidate gather (dynamic)
+    unsigned int pad1;
 };
 
 // Scalars of one CG solve; updated by the last block of each reduction kernel.
