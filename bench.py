@@ -97,6 +97,32 @@ def dist_env():
     return rank, world, local
 
 
+# ------------------------------------------------------------------ replicas over ranks
+# One rank per GPU runs an independent replica of the workload (a single scene does not
+# shard without a halo exchange per CG iteration); the only collectives are the barriers
+# around the timed region and the maximum of the ranks' times.
+def rank_barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def rank_max(x: float, world: int, device=None) -> float:
+    """Largest value of x over the ranks (the slowest rank's time)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(units_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * steps / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -250,18 +276,11 @@ def run_gb300(args):
         return total, iters, prof
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        rank_barrier(world)
         torch.cuda.synchronize(dev)
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(x, world, dev)
 
     if args.only == "ensemble":
         E = scenes.ensemble_2d(count=args.ensemble_scenes, seed=args.seed + rank)
@@ -443,8 +462,8 @@ def run_gb300(args):
                 "model": "matrix-free minimum bytes per particle: 483 + 57 per FP32 inner CG "
                          "iteration + 65 per FP64 residual"}
 
-    value = world * n * args.steps / (ms_mixed * 1e-3)
-    value64 = world * n * k64 / (ms_64 * 1e-3)
+    value = replica_rate(n, args.steps, world, ms_mixed)
+    value64 = replica_rate(n, k64, world, ms_64)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
