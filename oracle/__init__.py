@@ -33,7 +33,14 @@ class OracleError(RuntimeError):
         self.code = code
 
 
+# A test that plants a mistake in the oracle (tests/test_oracle_mutations.py) points this
+# at a library compiled from a mutated copy of the source.
+_OVERRIDE = os.environ.get("MPS_ORACLE_LIB")
+
+
 def build(force: bool = False) -> str:
+    if _OVERRIDE:
+        return _OVERRIDE
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):

@@ -1,0 +1,85 @@
+"""The oracle's pins catch plausible mistakes.  Each case plants one mistake (a dropped term,
+a flipped sign, a wrong operand or index) in a copy of the oracle's C source, compiles it on
+the CPU, and runs the pin suites against it in a subprocess: at least one pin must fail.
+The GB300 library is not involved."""
+import os
+import subprocess
+import sys
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mps_oracle.c")
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_options.py",
+        "tests/test_oracle_two_phase.py"]
+
+MUTATIONS = [
+    ("weight: the -1 of Eq. 4 dropped", "    return re / r - 1.0;\n}", "    return re / r;\n}"),
+    ("squared distance: wrong operand", "    s = s + dz * dz;", "    s = s + dy * dz;"),
+    ("neighbour predicate: r <= re", "    return dist2(xj - xi, yj - yi, zj - zi) < re2;",
+     "    return dist2(xj - xi, yj - yi, zj - zi) <= re2;"),
+    ("lambda: r^4 for r^2", "                swr2 = swr2 + w * r2;",
+     "                swr2 = swr2 + w * r2 * r2;"),
+    ("Laplacian: d for 2d", "    double coef = (2.0 * dim) / (n0 * lambda);",
+     "    double coef = (1.0 * dim) / (n0 * lambda);"),
+    ("Laplacian: flipped difference",
+     "                    s = s + (phi[j * ncomp + c] - phi[i * ncomp + c]) * w;",
+     "                    s = s + (phi[i * ncomp + c] - phi[j * ncomp + c]) * w;"),
+    ("gradient: r_i - r_j",
+     "                double d[3] = {xj - xi, yj - yi, zj - zi};\n"
+     "                double r2 = dist2(d[0], d[1], d[2]);\n"
+     "                double w = weight(sqrt(r2), re, kernel);",
+     "                double d[3] = {xi - xj, yi - yj, zi - zj};\n"
+     "                double r2 = dist2(d[0], d[1], d[2]);\n"
+     "                double w = weight(sqrt(r2), re, kernel);"),
+    ("PPE: diagonal term dropped", "        A->val[k0] = diag + p->alpha_c / (p->dt * p->dt);",
+     "        A->val[k0] = diag;"),
+    ("PPE: off-diagonal sign", "                A->val[k] = -c;", "                A->val[k] = c;"),
+    ("PPE: right-hand side sign",
+     "        b[i] = in_ppe(type, flags, i) ? inv_dt2 * ((nstar[i] - n0) / n0) : 0.0;",
+     "        b[i] = in_ppe(type, flags, i) ? inv_dt2 * ((n0 - nstar[i]) / n0) : 0.0;"),
+    ("predict: gravity dropped",
+     "                    us[q] = vel[q] + p->dt * (nu_of(p, i) * lap[q] + p->g[a]);",
+     "                    us[q] = vel[q] + p->dt * (nu_of(p, i) * lap[q]);"),
+    ("correction: position update without dt", "                pos[q] = ps[q] + p->dt * du;",
+     "                pos[q] = ps[q] + du;"),
+    ("free surface: n* <= beta n0 turned around",
+     "&& nstar[i] < p->beta * R->n0_pnd;", "&& nstar[i] > p->beta * R->n0_pnd;"),
+    ("equation of state: exponent gamma - 1", "(pow(nstar / n0, p->gamma) - 1.0)",
+     "(pow(nstar / n0, p->gamma - 1.0) - 1.0)"),
+    ("two-phase: the row's density for the pair",
+     "(coef0 * (2.0 / (p->rho_i[i] + p->rho_i[j]))) * w", "(coef0 * (1.0 / p->rho_i[i])) * w"),
+    ("cubic kernel: square for cube", "        return t * t * t;", "        return t * t;"),
+    ("CMPS: p_hat_j replaced by p_hat_i", "((p[i] + p[j]) - (phat[i] + phat[j]))",
+     "((p[i] + p[j]) - (phat[i] + phat[i]))"),
+    ("HS: sign of Dn/Dt", "        out[i] = -s;", "        out[i] = s;"),
+    ("ECS: signed density deviation", "            double ecs = fabs(eps) * (dk[i] / n0)",
+     "            double ecs = eps * (dk[i] / n0)"),
+]
+
+
+def _run_mutant(name, old, new, workdir):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"anchor of '{name}' not unique"
+    tag = "".join(ch if ch.isalnum() else "_" for ch in name)[:40]
+    c_path = os.path.join(workdir, f"{tag}.c")
+    so_path = os.path.join(workdir, f"{tag}.so")
+    open(c_path, "w").write(src.replace(old, new))
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                           "-std=c11", "-o", so_path, c_path, "-lm"])
+    env = dict(os.environ, MPS_ORACLE_LIB=so_path, OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "-m", "not gpu"] + PINS, cwd=ROOT, env=env, capture_output=True,
+                       text=True, timeout=900)
+    return name, r.returncode
+
+
+@pytest.mark.slow
+def test_every_planted_mistake_fails_a_pin():
+    with tempfile.TemporaryDirectory() as d:
+        with ThreadPoolExecutor(max_workers=max(1, min(8, (os.cpu_count() or 2) // 2))) as ex:
+            results = list(ex.map(lambda m: _run_mutant(*m, d), MUTATIONS))
+    survived = [name for name, rc in results if rc == 0]
+    assert not survived, f"mistakes no pin catches: {survived}"

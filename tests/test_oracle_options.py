@@ -201,3 +201,21 @@ def test_ecs_source_closed_form_on_compressed_dilating_lattice():
     assert inner.sum() > 50 and eps > 0 and ecs > 0
     np.testing.assert_allclose(b[inner], expect, rtol=1e-11)
     np.testing.assert_allclose(b[inner] - b2[inner], ecs / dt, rtol=1e-9)
+
+
+def test_ecs_terms_cancel_for_an_expanded_compressing_lattice():
+    """Expanded (eps < 0) and compressing ((Dn/Dt)^k > 0): the two terms of Eq. 24 cancel
+    exactly, so the source is the HS term alone."""
+    l0, s0, a, dt = 0.01, 1.01, -2.0, 1e-4
+    pos, t = lattice_block(2, 21, spacing=s0 * l0)
+    pos = pos + 0.05
+    vel = a * (pos - pos.mean(0))
+    sc = scenes.Scene(2, l0, pos, vel, t, np.zeros(3), np.array([0.4, 0.4, 0.0]))
+    prm1, b1, ps, fl = _hs_system(sc, vel, dt=dt)
+    prm = oracle.params_for(sc, source=2, nu=0.0, g=(0.0, 0.0, 0.0), dt=dt)
+    st = oracle.State.from_scene(sc)
+    off, col, val, b2, ps, ns, fl = oracle.ppe_system(prm, st)
+    inner = interior_mask(pos, 0.03) & (fl == 0)
+    assert inner.sum() > 50
+    np.testing.assert_allclose(b2[inner], b1[inner], rtol=1e-12)
+    assert np.all(b1[inner] > 0)

@@ -421,3 +421,27 @@ def test_dam_break_100_steps_sane():
     assert st.nstar[st.types == oracle.FLUID].max() < 1.2 * n0
     assert np.count_nonzero(st.types == oracle.GHOST) == 0
     assert np.count_nonzero(st.types == oracle.FLUID) == 800
+
+
+# ---------------------------------------------------------------- the assembled operator
+@pytest.mark.parametrize("dim", [2, 3])
+def test_ppe_operator_is_minus_laplacian_over_rho_on_quadratics(dim):
+    """On a lattice at rest, rows of the PPE whose whole neighbourhood is in the PPE apply
+    A = -(1/rho) L + alpha_c/dt^2 I: for p = |r|^2 (Laplacian 2d, exact by Eq. 7's
+    construction) (A p)_i - alpha_c/dt^2 p_i = -2d/rho.  Pins the sign and scale of the
+    off-diagonal coefficients and the diagonal sum of the assembly."""
+    m = 21
+    pos, t = lattice_block(dim, m, spacing=0.01)
+    pos = pos + 0.05
+    sc = scenes.Scene(dim, 0.01, pos, np.zeros_like(pos), t, np.zeros(3),
+                      np.full(3, 0.05 + m * 0.01 + 0.1) if dim == 3 else
+                      np.array([0.05 + m * 0.01 + 0.1] * 2 + [0.0]))
+    g0 = (0.0, 0.0, 0.0)
+    prm = oracle.params_for(sc, g=g0, nu=0.0)
+    off, col, val, b, ps, ns, fl = oracle.ppe_system(prm, sc)
+    p = ((pos - pos.mean(0)) ** 2).sum(1)
+    y = np.array([val[off[i]:off[i + 1]] @ p[col[off[i]:off[i + 1]]] for i in range(len(p))])
+    inner = interior_mask(pos, 0.04 + 0.045)   # re_lap plus the surface band
+    assert inner.sum() > 0 and np.all(fl[inner] == 0)
+    diag_add = prm.alpha_c / prm.dt ** 2
+    np.testing.assert_allclose(y[inner] - diag_add * p[inner], -2.0 * dim / prm.rho, rtol=1e-8)
