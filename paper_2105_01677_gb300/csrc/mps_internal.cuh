@@ -250,6 +250,10 @@ struct Ctx {
     std::vector<double> scene_resid;
     uint32_t scene_shift = 0;            // dim * bits
     double skin_half = 0.0;              // s max(re)/2 of the scene with the smallest spacing
+    // Candidate-list skin of the next gather (one scene, lists gathered every step): sized
+    // from the last step's largest displacement, at most cell_skin; X of the FP32 bands.
+    double list_skin = 0.0;
+    double band_x = 0.0;
     uint32_t* scan_scratch;
     // CG (FP64): x = p, r, d, q ; FP32: r32, d32, q32, x32
     double *cg_r, *cg_d, *cg_q;
