@@ -362,9 +362,15 @@ int allocate(Ctx* c) {
 }
 
 // Host data -> device staging (original order) -> state arrays (slot = id).
-int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* types, bool have_state) {
+int read_status(Ctx* c);
+
+// validate: check the staged values on the device first (mps_write_state); the context's
+// state is replaced only if they are finite and of known kinds
+int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* types, bool have_state,
+                 bool validate = false) {
     c->need_list = true;
     const size_t n = (size_t)c->n, dim = (size_t)c->dim;
+    int rc_check;
     uint8_t* base = (uint8_t*)c->stage;
     double* d_pos = (double*)base;
     double* d_vel = d_pos + n * dim;
@@ -378,6 +384,13 @@ int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* typ
     if (vel) MPS_CUDA(c, cudaMemcpyAsync(d_vel, vel, n * dim * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     else if (!have_state) MPS_CUDA(c, cudaMemsetAsync(d_vel, 0, n * dim * sizeof(double), c->stream));
     if (types) MPS_CUDA(c, cudaMemcpyAsync(d_t, types, n, cudaMemcpyHostToDevice, c->stream));
+    if (validate) {
+        MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
+        launch_check_stage(c, d_pos, vel ? d_vel : nullptr, types ? d_t : nullptr);
+        if ((rc_check = read_status(c))) return rc_check;
+        if (c->st_host->err & kErrNonfinite) return MPS_ENONFINITE;
+        if (c->st_host->err & kErrKind) return MPS_EINVAL;
+    }
     launch_ingest(c, d_pos, d_vel, d_t, false, false);
     launch_gather_props(c);   // slot = id again
     MPS_CUDA(c, cudaGetLastError());
@@ -786,11 +799,10 @@ int mps_read_state(mps_ctx* c, double* pos, double* vel, double* p, double* n_st
 
 int mps_write_state(mps_ctx* c, const double* pos, const double* vel, const int8_t* types) {
     if (!c || !pos) return MPS_EINVAL;
-    int rc = check_host_state(c->n, c->dim, pos, vel, types);
-    if (rc) return rc;
     DeviceGuard dg(c->prm.device);
     if (!dg.ok) return MPS_EDEVICE;
-    return upload_state(c, pos, vel, types, true);
+    // the same checks as mps_create, on the device (a restart path uploads every step)
+    return upload_state(c, pos, vel, types, true, true);
 }
 
 int mps_set_fluid_properties(mps_ctx* c, const double* rho, const double* nu) {

@@ -35,6 +35,7 @@ constexpr int kFluid = MPS_FLUID, kWall = MPS_WALL, kDummy = MPS_DUMMY, kGhost =
 
 // device error bits (DevStatus::err)
 constexpr unsigned kErrCoincident = 1u, kErrCap = 2u, kErrNonfinite = 4u, kErrWait = 8u;
+constexpr unsigned kErrKind = 16u;   // a particle kind outside FLUID..GHOST (state upload)
 
 struct DevStatus {
     unsigned int err;
@@ -168,6 +169,7 @@ __device__ __forceinline__ void split_rel(double x, double xmin, float* hi, floa
 void launch_unpermute_u32(Ctx* c, const uint32_t* in, uint32_t* out);
 void launch_gather_props(Ctx* c);
 void launch_ecs_rates(Ctx* c);
+void launch_check_stage(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types);
 
 // ---------------------------------------------------------------- context
 struct Ctx {

@@ -206,6 +206,22 @@ __global__ void __launch_bounds__(kBT) k_unpermute_u32(int n, const int32_t* id,
     if (s < n) out[id[s]] = in[s];
 }
 
+// a staged caller state before it replaces the context's: finite positions and velocities,
+// known kinds (flags in the status word; nothing is written elsewhere)
+__global__ void __launch_bounds__(kBT)
+    k_check_stage(int n, int dim, const double* i_pos, const double* i_vel, const int8_t* i_t,
+                  DevStatus* st) {
+    int s = blockIdx.x * kBT + threadIdx.x;
+    if (s >= n) return;
+    bool fin = true;
+    for (int a = 0; a < dim; a++) {
+        fin = fin && isfinite(i_pos[(size_t)s * dim + a]);
+        if (i_vel) fin = fin && isfinite(i_vel[(size_t)s * dim + a]);
+    }
+    if (!fin) atomicOr(&st->err, kErrNonfinite);
+    if (i_t && (i_t[s] < kFluid || i_t[s] > kGhost)) atomicOr(&st->err, kErrKind);
+}
+
 // state from caller order; slot s = particle s (identity order until the next sort)
 __global__ void __launch_bounds__(kBT)
     k_ingest(int n, int dim, const double* i_pos, const double* i_vel, const int8_t* i_t,
@@ -333,6 +349,12 @@ void launch_ingest(Ctx* c, const double* d_pos, const double* d_vel, const int8_
                                                           c->flag, keep_vel ? 1 : 0,
                                                           keep_types ? 1 : 0, c->grid, c->pos32,
                                                           c->pos32lo);
+    c->launches += 1;
+}
+
+void launch_check_stage(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types) {
+    const int n = (int)c->n;
+    k_check_stage<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(n, c->dim, d_pos, d_vel, d_types, c->st);
     c->launches += 1;
 }
 
