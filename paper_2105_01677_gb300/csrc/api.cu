@@ -445,10 +445,11 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     int rc;
     const bool keep = P.list_every > 1;
     const double re_max = std::max(P.re_n, P.re_lap);
-    // A single scene whose lists are gathered every step gathers them within the skin its
-    // recent motion needs (the grid's cells keep the full skin); a step whose predicted
-    // motion exceeds it is gathered again with the full skin, so the sets stay exact
-    const bool adapt = !keep && c->n_scenes == 1;
+    // A single scene gathers its candidate lists within the skin its recent motion needs
+    // over the lists' lifetime (the grid's cells keep the full skin); a step whose motion
+    // exceeds the skin of the lists in use is gathered again (with the full skin if a
+    // fresh gather already fell short), so the sets stay exact
+    const bool adapt = c->n_scenes == 1;
     const size_t n = (size_t)c->n;
     // Candidate lists are gathered at r_b and serve while every particle stays within
     // s max(re)/2 of r_b: a pair closer than re at r^k or r* is then closer than h at r_b.
@@ -467,7 +468,8 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         }
         launch_copy_state_star(c);
         if (fresh) {
-            if (adapt) c->r_v = make_radius(re_max * (1.0 + c->list_skin), c->band_x);
+            c->gathered_skin = adapt ? c->list_skin : P.cell_skin;
+            if (adapt) c->r_v = make_radius(re_max * (1.0 + c->gathered_skin), c->band_x);
             MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), c->stream));
             stage_begin(c, MPS_STAGE_GATHER);
             launch_verlet(c);                                          // candidates at r_b = r^k
@@ -507,22 +509,24 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         rep->cg_resid = 0.0;
         rep->list_gathered = fresh ? 1 : 0;
         if ((rc = status_error(s))) return rc;
-        const double half = adapt ? 0.5 * c->list_skin * re_max : c->skin_half;
+        const double half = adapt ? 0.5 * c->gathered_skin * re_max : c->skin_half;
         if (rep->max_disp > half) {
-            if (adapt && c->list_skin < P.cell_skin) {
-                c->list_skin = P.cell_skin;                            // the full skin
-                fresh = true;
+            if (!fresh) {                                              // a kept list falls short
+                fresh = true;                                          // gather afresh at r^k
                 continue;
             }
-            if (fresh) return MPS_ESKIN;
-            fresh = true;                                              // gather afresh at r^k
-            continue;
+            if (adapt && c->gathered_skin < P.cell_skin) {
+                c->list_skin = P.cell_skin;                            // the full skin
+                continue;
+            }
+            return MPS_ESKIN;
         }
         break;
     }
     if (adapt) {
-        // next list skin: three times what this step's motion needed, within [0.02, cell_skin]
-        const double need = 2.0 * rep->max_disp / re_max;
+        // next list skin: three times what the motion of the lists' lifetime needs at this
+        // step's displacement, within [0.02, cell_skin]
+        const double need = 2.0 * rep->max_disp / re_max * (keep ? P.list_every : 1);
         c->list_skin = std::min(P.cell_skin, std::max(kMinListSkin, 3.0 * need));
     }
     if (fresh) {
@@ -555,7 +559,8 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     if (keep && advance) {
         const DevStatus& s = *c->st_host;
         c->list_age++;
-        if (s.leave || std::sqrt(bits_to_double(s.max_disp_next_bits)) > c->skin_half) c->need_list = true;
+        const double half = adapt ? 0.5 * c->gathered_skin * re_max : c->skin_half;
+        if (s.leave || std::sqrt(bits_to_double(s.max_disp_next_bits)) > half) c->need_list = true;
     }
     if (advance) c->steps_done++;
     rep->steps_done = c->steps_done;

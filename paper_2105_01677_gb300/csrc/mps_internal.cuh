@@ -255,6 +255,7 @@ struct Ctx {
     // Candidate-list skin of the next gather (one scene, lists gathered every step): sized
     // from the last step's largest displacement, at most cell_skin; X of the FP32 bands.
     double list_skin = 0.0;
+    double gathered_skin = 0.0;          // the skin of the lists in use
     double band_x = 0.0;
     uint32_t* scan_scratch;
     // CG (FP64): x = p, r, d, q ; FP32: r32, d32, q32, x32
