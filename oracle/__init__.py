@@ -99,10 +99,13 @@ def lib():
         L.orc_cg.argtypes = [i64, C.POINTER(C.c_int64), C.POINTER(C.c_int32), d, d, d,
                              C.c_double, i32, C.POINTER(C.c_int32), d]
         L.orc_dense_spd_solve.argtypes = [i64, d, d, d]
+        L.orc_step_vjp.argtypes = [C.POINTER(Params), i64, d, d, C.POINTER(C.c_int8), d, d, d, d,
+                                   d, C.POINTER(Report), i32]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_get_threads.restype = C.c_int
         for f in ("orc_lattice", "orc_cell_keys", "orc_neighbors", "orc_pnd", "orc_laplacian",
-                  "orc_gradient", "orc_step", "orc_ppe_system", "orc_cg", "orc_dense_spd_solve"):
+                  "orc_gradient", "orc_step", "orc_ppe_system", "orc_cg", "orc_dense_spd_solve",
+                  "orc_step_vjp"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -358,3 +361,25 @@ def dense_spd_solve(A, b):
     if rc != 0:
         raise OracleError(-1, "dense_spd_solve: matrix not positive definite")
     return x
+
+
+def step_vjp(prm: StepParams, st, g_pos, g_vel, nb_mode: int = 1):
+    """Vector-Jacobian product of one oracle step at the state `st` (not modified):
+    given dL/dr^{k+1}, dL/du^{k+1} (n x dim), returns (dL/dr^k, dL/du^k, dL/dg[3])."""
+    pos = _arr(st.pos, np.float64)
+    vel = _arr(st.vel, np.float64)
+    types = _arr(st.types, np.int8)
+    g_pos = _arr(g_pos, np.float64)
+    g_vel = _arr(g_vel, np.float64)
+    n = len(types)
+    assert g_pos.shape == pos.shape and g_vel.shape == vel.shape
+    out_r = np.empty_like(pos)
+    out_u = np.empty_like(vel)
+    out_g = np.zeros(3)
+    P = prm.c_struct(n)
+    R = Report()
+    d = C.c_double
+    _check(lib().orc_step_vjp(C.byref(P), n, _p(pos, d), _p(vel, d), _p(types, C.c_int8),
+                              _p(g_pos, d), _p(g_vel, d), _p(out_r, d), _p(out_u, d),
+                              _p(out_g, d), C.byref(R), nb_mode), "step_vjp")
+    return out_r, out_u, out_g

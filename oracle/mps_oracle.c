@@ -1014,3 +1014,273 @@ int orc_cg(int64_t n, const int64_t* off, const int32_t* col, const double* val,
     *iters = it;
     return rc;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Reverse (vector-Jacobian product) of one step, the adjoint of the step map           */
+/*   (r^k, u^k, g) -> (r^{k+1}, u^{k+1})                                                  */
+/* defined by orc_step (PPE or equation-of-state path; kernel of Eq. 4, difference-form */
+/* gradient, source of Eq. 13; one or two phases).  Given the adjoints gr = dL/dr^{k+1}, */
+/* gu = dL/du^{k+1} (n*dim each) it returns dL/dr^k, dL/du^k and dL/dg.                  */
+/* The discrete choices of the step are held fixed: neighbour sets, the GHOST and free- */
+/* surface sets, the clamp's active set and the particle giving p_hat_i (the strict     */
+/* minimum in ascending neighbour order, p_i first).  Within them the step is smooth and */
+/* this is its exact derivative (up to the CG tolerance of the adjoint solve).          */
+/*                                                                                        */
+/* Chain, from the last stage back (x_ij = r_j - r_i, s = |x_ij|, w(s) = re/s - 1,       */
+/* w'(s) = -re/s^2; every pair term adds +X to particle j and -X to particle i):        */
+/*  6. u = u* + u', r = r* + dt u', u' = -(dt/rho_i) G_i, FLUID:                          */
+/*       gu* = gu, gr* = gr, gG_i = -(dt/rho_i)(gu_i + dt gr_i);                           */
+/*     G_i = d/n0 sum_j (p_j - p_hat_i) x w/s^2 over non-dummy j within re_n at r*:      */
+/*       gp_j += d/n0 (x . gG_i) w/s^2, gphat_i -= the same,                              */
+/*       X = d/n0 (p_j - p_hat_i) [q gG_i + (q'/s)(x . gG_i) x],  q = w/s^2;               */
+/*  5. p_hat_i = p_m(i): gp_m(i) += gphat_i; clamp: gp_i = 0 where p_i <= 0 was clamped;  */
+/*     only rows of the PPE (or, for the equation of state, FLUID/WALL rows off the      */
+/*     surface) carry a pressure that depends on the state;                               */
+/*  4. PPE: A p = b with A symmetric, so A lam = gp gives gb = lam and, per coefficient  */
+/*     c_ij (i a PPE row, j a non-dummy neighbour within re_lap; A_ii holds +c_ij and    */
+/*     A_ij holds -c_ij when j is a row), gc_ij = -lam_i (p_i - p_j) with p_j = 0 off    */
+/*     the rows; c_ij = K_ij w(s): X = gc_ij K_ij w'(s) x/s.  gn*_i = lam_i/(n0 dt^2).    */
+/*     Equation of state: gn*_i = gp_i rho_i c0^2 (n*_i/n0)^(gamma-1) / n0;              */
+/*  3. n*_i = sum_j w(s) over every non-GHOST j within re_n at r*: X = gn*_i w'(s) x/s;  */
+/*  2. r* = r + dt u* (FLUID), so gr = gr*, gu* += dt gr*;                                */
+/*     u* = u + dt (nu_i lap(u)_i + g): gu += gu*, gg += dt gu*, and per pair within     */
+/*     re_lap at r^k (k = dt nu_i 2d/(n0_lap lambda)): gu_j += k w gu*_i, gu_i -= the     */
+/*     same, X = k (gu*_i . (u_j - u_i)) w'(s) x/s;                                        */
+/*  1. a particle that becomes a GHOST in this step has its velocity reset: gu = 0.      */
+/* Other kinds: r^{k+1} = r^k, u^{k+1} = u^k (identity) plus their part in pair terms.   */
+/* ------------------------------------------------------------------------------------ */
+static void add_pair(double* out, int dim, int64_t i, int64_t j, const double X[3]) {
+    for (int a = 0; a < dim; a++) {
+        out[j * dim + a] = out[j * dim + a] + X[a];
+        out[i * dim + a] = out[i * dim + a] - X[a];
+    }
+}
+
+int orc_step_vjp(const orc_params* p, int64_t n, const double* pos, const double* vel,
+                 const int8_t* type_in, const double* gr, const double* gu, double* out_r,
+                 double* out_u, double* out_g, orc_report* rep, int32_t nb_mode) {
+    int dim = p->dim;
+    int rc = check_params(p, n);
+    if (rc) return rc;
+    if (p->kernel != 0 || p->grad_form != 0 || p->source != 0) return ORC_EINVAL;
+    for (int64_t i = 0; i < n * dim; i++)
+        if (!isfinite(pos[i]) || !isfinite(vel[i])) return ORC_ENONFINITE;
+    orc_report R;
+    memset(&R, 0, sizeof R);
+    rc = orc_lattice(dim, p->l0, p->re_n, &R.n0_pnd, NULL, 0);
+    if (!rc) rc = orc_lattice(dim, p->l0, p->re_lap, &R.n0_lap, &R.lambda, 0);
+    if (rc) return rc;
+    const double n0 = R.n0_pnd, dt = p->dt;
+    const size_t nv = (size_t)(n * dim);
+
+    double* x0 = malloc(sizeof(double) * nv);      /* r^k */
+    double* u0 = malloc(sizeof(double) * nv);      /* u^k after the grid stage */
+    double* ps = malloc(sizeof(double) * nv);      /* r* */
+    double* us = malloc(sizeof(double) * nv);      /* u* */
+    double* nstar = malloc(sizeof(double) * (size_t)n);
+    double* bvec = malloc(sizeof(double) * (size_t)n);
+    double* ppre = calloc((size_t)n, sizeof(double));   /* PPE solution before the clamp */
+    double* pres = calloc((size_t)n, sizeof(double));
+    int64_t* amin = malloc(sizeof(int64_t) * (size_t)n);
+    double* gG = calloc(nv, sizeof(double));
+    double* gp = calloc((size_t)n, sizeof(double));
+    double* gphat = calloc((size_t)n, sizeof(double));
+    double* lam = calloc((size_t)n, sizeof(double));
+    double* gn = calloc((size_t)n, sizeof(double));
+    double* grs = malloc(sizeof(double) * nv);     /* dL/dr* */
+    double* gus = calloc(nv, sizeof(double));      /* dL/du* */
+    int8_t* type = malloc((size_t)n);
+    uint8_t* flags = calloc((size_t)n, 1);
+    csr_t nb_n = {0, 0}, nb_l = {0, 0}, nb_k = {0, 0};
+    mat_t A = {0, 0, 0};
+    if (!x0 || !u0 || !ps || !us || !nstar || !bvec || !ppre || !pres || !amin || !gG || !gp ||
+        !gphat || !lam || !gn || !grs || !gus || !type || !flags) {
+        rc = ORC_ENOMEM;
+        goto out;
+    }
+    memcpy(x0, pos, sizeof(double) * nv);
+    memcpy(u0, vel, sizeof(double) * nv);
+    memcpy(type, type_in, (size_t)n);
+
+    /* ---- forward, keeping what the reverse needs */
+    rc = stage_grid(p, n, x0, u0, type, &R);
+    if (!rc) rc = stage_predict(p, n, x0, u0, type, nb_mode, ps, us, &R);
+    if (!rc) rc = stage_density(p, n, ps, type, nb_mode, &nb_n, nstar, flags, &R);
+    if (rc) goto out;
+    for (int64_t i = 0; i < n; i++) amin[i] = i;
+    if (p->pressure_mode == 0) {
+        rc = neighbors(dim, n, ps, type, p->re_lap, nb_mode, &nb_l);
+        if (!rc) rc = assemble_ppe(p, n, ps, type, flags, &nb_l, R.n0_lap, R.lambda, &A);
+        if (rc) goto out;
+        ppe_rhs(p, n, type, flags, nstar, n0, bvec);
+        rc = cg_solve(n, &A, bvec, ppre, p->cg_tol, p->cg_max_iter, &R.cg_iters,
+                      &R.cg_restarts, &R.cg_resid);
+        if (rc) goto out;
+        for (int64_t i = 0; i < n; i++) {
+            if (!in_ppe(type, flags, i)) ppre[i] = 0.0;
+            pres[i] = (p->clamp_negative_p && ppre[i] < 0.0) ? 0.0 : ppre[i];
+        }
+        for (int64_t i = 0; i < n; i++) {
+            double m = pres[i];
+            for (int64_t k = nb_n.off[i]; k < nb_n.off[i + 1]; k++) {
+                int64_t j = nb_n.ids[k];
+                if (type[j] != ORC_DUMMY && pres[j] < m) { m = pres[j]; amin[i] = j; }
+            }
+        }
+    } else {
+        for (int64_t i = 0; i < n; i++)
+            pres[i] = in_ppe(type, flags, i) ? wc_pressure(p, rho_of(p, i), nstar[i], n0) : 0.0;
+    }
+
+    /* ---- 6: correction */
+    memcpy(grs, gr, sizeof(double) * nv);
+    for (int64_t i = 0; i < n; i++) {
+        if (type[i] != ORC_FLUID) continue;
+        double k = -(dt / rho_of(p, i));
+        for (int a = 0; a < dim; a++) {
+            int64_t q = i * dim + a;
+            gG[q] = k * (gu[q] + dt * gr[q]);
+            gus[q] = gu[q];
+        }
+    }
+    /* gradient pairs (re_n, non-dummy j, at r*) */
+    const double cg0 = (double)dim / n0;
+    for (int64_t i = 0; i < n; i++) {
+        if (type[i] != ORC_FLUID) continue;
+        double xi, yi, zi;
+        coords(ps, dim, i, &xi, &yi, &zi);
+        double gi[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < dim; a++) gi[a] = gG[i * dim + a];
+        for (int64_t k = nb_n.off[i]; k < nb_n.off[i + 1]; k++) {
+            int64_t j = nb_n.ids[k];
+            if (type[j] == ORC_DUMMY) continue;
+            double xj, yj, zj;
+            coords(ps, dim, j, &xj, &yj, &zj);
+            double d[3] = {xj - xi, yj - yi, zj - zi};
+            double s2 = dist2(d[0], d[1], d[2]);
+            double s = sqrt(s2);
+            double w = p->re_n / s - 1.0;
+            double wd = -p->re_n / s2;
+            double q = w / s2;
+            double qd = wd / s2 - 2.0 * w / (s2 * s);
+            double dg = (d[0] * gi[0] + d[1] * gi[1]) + d[2] * gi[2];
+            gp[j] = gp[j] + cg0 * q * dg;
+            gphat[i] = gphat[i] - cg0 * q * dg;
+            double f = cg0 * (pres[j] - pres[amin[i]]);
+            double X[3];
+            for (int a = 0; a < 3; a++) X[a] = f * (q * gi[a] + (qd / s) * dg * d[a]);
+            add_pair(grs, dim, i, j, X);
+        }
+    }
+    /* ---- 5: p_hat, clamp (p_hat_i = p_i on the equation-of-state path: amin[i] = i) */
+    for (int64_t i = 0; i < n; i++)
+        if (type[i] == ORC_FLUID) gp[amin[i]] = gp[amin[i]] + gphat[i];
+    for (int64_t i = 0; i < n; i++) {
+        if (!in_ppe(type, flags, i)) gp[i] = 0.0;
+        else if (p->pressure_mode == 0 && p->clamp_negative_p && !(ppre[i] > 0.0)) gp[i] = 0.0;
+    }
+    /* ---- 4: pressure */
+    if (p->pressure_mode == 0) {
+        int it = 0, rs = 0;
+        double res = 0.0;
+        rc = cg_solve(n, &A, gp, lam, p->cg_tol, p->cg_max_iter, &it, &rs, &res);
+        if (rc) goto out;
+        const double coef = (2.0 * dim) / (R.n0_lap * R.lambda * p->rho);
+        const double coef0 = (2.0 * dim) / (R.n0_lap * R.lambda);
+        for (int64_t i = 0; i < n; i++) {
+            if (!in_ppe(type, flags, i)) continue;
+            gn[i] = lam[i] / (n0 * dt * dt);
+            double xi, yi, zi;
+            coords(ps, dim, i, &xi, &yi, &zi);
+            for (int64_t k = nb_l.off[i]; k < nb_l.off[i + 1]; k++) {
+                int64_t j = nb_l.ids[k];
+                if (type[j] == ORC_DUMMY) continue;
+                double xj, yj, zj;
+                coords(ps, dim, j, &xj, &yj, &zj);
+                double d[3] = {xj - xi, yj - yi, zj - zi};
+                double s2 = dist2(d[0], d[1], d[2]);
+                double s = sqrt(s2);
+                double K = p->rho_i ? coef0 * (2.0 / (p->rho_i[i] + p->rho_i[j])) : coef;
+                double gc = -lam[i] * (ppre[i] - ppre[j]);
+                double f = gc * K * (-p->re_lap / s2) / s;
+                double X[3] = {f * d[0], f * d[1], f * d[2]};
+                add_pair(grs, dim, i, j, X);
+            }
+        }
+    } else {
+        for (int64_t i = 0; i < n; i++)
+            if (in_ppe(type, flags, i))
+                gn[i] = gp[i] * rho_of(p, i) * p->c0 * p->c0 * pow(nstar[i] / n0, p->gamma - 1.0) / n0;
+    }
+    /* ---- 3: number density (re_n, every non-GHOST neighbour, at r*) */
+    for (int64_t i = 0; i < n; i++) {
+        if (gn[i] == 0.0) continue;
+        double xi, yi, zi;
+        coords(ps, dim, i, &xi, &yi, &zi);
+        for (int64_t k = nb_n.off[i]; k < nb_n.off[i + 1]; k++) {
+            int64_t j = nb_n.ids[k];
+            double xj, yj, zj;
+            coords(ps, dim, j, &xj, &yj, &zj);
+            double d[3] = {xj - xi, yj - yi, zj - zi};
+            double s2 = dist2(d[0], d[1], d[2]);
+            double f = gn[i] * (-p->re_n / s2) / sqrt(s2);
+            double X[3] = {f * d[0], f * d[1], f * d[2]};
+            add_pair(grs, dim, i, j, X);
+        }
+    }
+    /* ---- 2: r* = r + dt u*, u* = u + dt (nu lap(u) + g) */
+    memcpy(out_r, grs, sizeof(double) * nv);
+    for (int a = 0; a < 3; a++) out_g[a] = 0.0;
+    for (int64_t i = 0; i < n; i++)
+        for (int a = 0; a < dim; a++) {
+            int64_t q = i * dim + a;
+            if (type[i] == ORC_FLUID) {
+                gus[q] = gus[q] + dt * grs[q];
+                out_u[q] = gus[q];
+                out_g[a] = out_g[a] + dt * gus[q];
+            } else {
+                out_u[q] = gu[q];
+            }
+        }
+    rc = neighbors(dim, n, x0, type, p->re_lap, nb_mode, &nb_k);
+    if (rc) goto out;
+    const double clap = (2.0 * dim) / (R.n0_lap * R.lambda);
+    for (int64_t i = 0; i < n; i++) {
+        if (type[i] != ORC_FLUID) continue;
+        double xi, yi, zi;
+        coords(x0, dim, i, &xi, &yi, &zi);
+        double k = dt * nu_of(p, i) * clap;
+        for (int64_t kk = nb_k.off[i]; kk < nb_k.off[i + 1]; kk++) {
+            int64_t j = nb_k.ids[kk];
+            double xj, yj, zj;
+            coords(x0, dim, j, &xj, &yj, &zj);
+            double d[3] = {xj - xi, yj - yi, zj - zi};
+            double s2 = dist2(d[0], d[1], d[2]);
+            double s = sqrt(s2);
+            double w = p->re_lap / s - 1.0;
+            double gdu = 0.0;
+            for (int a = 0; a < dim; a++) {
+                double gsa = gus[i * dim + a];
+                out_u[j * dim + a] = out_u[j * dim + a] + k * w * gsa;
+                out_u[i * dim + a] = out_u[i * dim + a] - k * w * gsa;
+                gdu = gdu + gsa * (u0[j * dim + a] - u0[i * dim + a]);
+            }
+            double f = k * gdu * (-p->re_lap / s2) / s;
+            double X[3] = {f * d[0], f * d[1], f * d[2]};
+            add_pair(out_r, dim, i, j, X);
+        }
+    }
+    /* ---- 1: a particle turned GHOST in this step had its velocity reset */
+    for (int64_t i = 0; i < n; i++)
+        if (type[i] == ORC_GHOST && type_in[i] != ORC_GHOST)
+            for (int a = 0; a < dim; a++) out_u[i * dim + a] = 0.0;
+
+out:
+    if (rep) *rep = R;
+    free(x0); free(u0); free(ps); free(us); free(nstar); free(bvec); free(ppre); free(pres);
+    free(amin); free(gG); free(gp); free(gphat); free(lam); free(gn); free(grs); free(gus);
+    free(type); free(flags);
+    csr_free(&nb_n); csr_free(&nb_l); csr_free(&nb_k);
+    mat_free(&A);
+    return rc;
+}

@@ -81,7 +81,7 @@ def _jitter(seed: int, ids: np.ndarray, dim: int, amp: float) -> np.ndarray:
 
 def tank_scene(dim: int, l0: float, interior: tuple, fluid: tuple, *, layers_wall: int = 2,
                layers_dummy: int = 2, wall_height: int | None = None, seed: int = 1,
-               jitter: float = 1e-4, headroom: float = 1.0) -> Scene:
+               jitter: float = 1e-4, headroom: float = 1.0, wall_jitter: float = 0.0) -> Scene:
     """Fluid block in the corner of an open-top tank.
 
     interior: interior lattice counts per axis (last axis is vertical).
@@ -89,6 +89,8 @@ def tank_scene(dim: int, l0: float, interior: tuple, fluid: tuple, *, layers_wal
     Lattice sites sit at (i + 0.5) * l0; boundary sites form `layers_wall` wall layers and
     `layers_dummy` dummy layers (Chebyshev layer index) on every side except the top.
     wall_height: number of lattice rows the side walls reach (default: full interior height).
+    jitter, wall_jitter: uniform offsets of up to that many l0 per axis for the fluid and
+    for the wall and dummy sites (default: walls on the exact lattice).
     """
     assert dim in (2, 3) and len(interior) == dim and len(fluid) == dim
     L = layers_wall + layers_dummy
@@ -118,6 +120,8 @@ def tank_scene(dim: int, l0: float, interior: tuple, fluid: tuple, *, layers_wal
     nf = len(fidx)
     if jitter > 0.0:
         pos[:nf] += _jitter(seed, np.arange(nf), dim, jitter * l0)
+    if wall_jitter > 0.0:
+        pos[nf:] += _jitter(seed + 7919, np.arange(nf, len(pos)), dim, wall_jitter * l0)
     vel = np.zeros_like(pos)
 
     box_min = np.zeros(3)
@@ -127,6 +131,7 @@ def tank_scene(dim: int, l0: float, interior: tuple, fluid: tuple, *, layers_wal
         top = (nint[a] + L + 1) * l0 if a < dim - 1 else (hw + 1) * l0 * (1.0 + headroom)
         box_max[a] = top
     meta = dict(kind="tank", interior=tuple(nint), fluid=tuple(nfl), seed=seed, jitter=jitter,
+                wall_jitter=wall_jitter,
                 layers_wall=layers_wall, layers_dummy=layers_dummy, wall_height=hw)
     return Scene(dim, l0, pos, vel, types, box_min, box_max, meta)
 
@@ -184,6 +189,25 @@ def ensemble_2d(count: int = 256, seed: int = 1, fluid=(500, 20000), aspect=(0.5
         out.append(tank_scene(2, h, (4 * nx, int(np.ceil(1.25 * ny))), (nx, ny),
                               seed=seed * 100003 + s, jitter=1e-4))
     return out
+
+
+def sloshing_3d(seed: int = 1, l0: float = 0.008, tank=(0.5, 0.3, 0.3), fill: float = 0.5,
+                jitter: float = 1e-4) -> Scene:
+    """3D sloshing tank: a 0.5 x 0.3 x 0.3 m open-top tank filled over its whole floor to
+    `fill` of its height (l0 = 0.008: 62 x 37 x 18 = 41,292 fluid, 85,564 particles with the
+    2 wall + 2 dummy layers), fluid at rest."""
+    n = lambda L: int(np.floor(L / l0 + 1e-9))
+    interior = tuple(n(v) for v in tank)
+    column = (interior[0], interior[1], n(fill * tank[2]))
+    return tank_scene(3, l0, interior, column, seed=seed, jitter=jitter)
+
+
+def sloshing_forcing(t, amplitude: float = 0.02, freq: float = 1.2):
+    """Horizontal (x) body acceleration [m/s^2] in the frame of a tank displaced by
+    X(t) = amplitude sin(2 pi freq t): the inertial acceleration -X''(t) =
+    amplitude (2 pi freq)^2 sin(2 pi freq t).  t may be an array."""
+    w = 2.0 * np.pi * freq
+    return amplitude * w * w * np.sin(w * np.asarray(t, dtype=np.float64))
 
 
 def still_tank_2d(l0: float = 0.01, width: float = 0.2, depth: float = 0.2, seed: int = 1,

@@ -13,7 +13,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "mps_oracle.c")
 PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_options.py",
-        "tests/test_oracle_two_phase.py"]
+        "tests/test_oracle_two_phase.py", "tests/test_oracle_adjoint.py"]
 
 MUTATIONS = [
     ("weight: the -1 of Eq. 4 dropped", "    return re / r - 1.0;\n}", "    return re / r;\n}"),
@@ -57,6 +57,36 @@ MUTATIONS = [
     ("HS: sign of Dn/Dt", "        out[i] = -s;", "        out[i] = s;"),
     ("ECS: signed density deviation", "            double ecs = fabs(eps) * (dk[i] / n0)",
      "            double ecs = eps * (dk[i] / n0)"),
+    ("adjoint: sign of the PPE coefficient cotangent",
+     "                double gc = -lam[i] * (ppre[i] - ppre[j]);",
+     "                double gc = lam[i] * (ppre[i] - ppre[j]);"),
+    ("adjoint: viscosity's transpose onto the neighbour dropped",
+     "                out_u[j * dim + a] = out_u[j * dim + a] + k * w * gsa;", ""),
+    ("adjoint: p_hat path dropped",
+     "        if (type[i] == ORC_FLUID) gp[amin[i]] = gp[amin[i]] + gphat[i];", ""),
+    ("adjoint: sign of the number-density derivative",
+     "            double f = gn[i] * (-p->re_n / s2) / sqrt(s2);",
+     "            double f = gn[i] * (p->re_n / s2) / sqrt(s2);"),
+    ("adjoint: clamp mask ignored",
+     "        else if (p->pressure_mode == 0 && p->clamp_negative_p && !(ppre[i] > 0.0)) gp[i] = 0.0;",
+     ""),
+    ("adjoint: equation-of-state exponent gamma for gamma - 1",
+     "pow(nstar[i] / n0, p->gamma - 1.0) / n0;", "pow(nstar[i] / n0, p->gamma) / n0;"),
+    ("adjoint: r* = r + dt u* path dropped",
+     "                gus[q] = gus[q] + dt * grs[q];", ""),
+    ("adjoint: right-hand side scale n0 dt for n0 dt^2",
+     "            gn[i] = lam[i] / (n0 * dt * dt);", "            gn[i] = lam[i] / (n0 * dt);"),
+    ("adjoint: gradient pair term without its radial part",
+     "            for (int a = 0; a < 3; a++) X[a] = f * (q * gi[a] + (qd / s) * dg * d[a]);",
+     "            for (int a = 0; a < 3; a++) X[a] = f * (q * gi[a]);"),
+    ("adjoint: derivative of w/r^2 with r^4 for r^3",
+     "            double qd = wd / s2 - 2.0 * w / (s2 * s);",
+     "            double qd = wd / s2 - 2.0 * w / (s2 * s2);"),
+    ("adjoint: correction cotangent without dt r",
+     "            gG[q] = k * (gu[q] + dt * gr[q]);", "            gG[q] = k * gu[q];"),
+    ("adjoint: viscosity position term sign",
+     "            double f = k * gdu * (-p->re_lap / s2) / s;",
+     "            double f = k * gdu * (p->re_lap / s2) / s;"),
 ]
 
 
