@@ -11,7 +11,9 @@ density, dot products and refinement); the plain FP64 path is timed on the same 
 reported under "fp64", and the mixed path with candidate lists kept for up to 4 steps
 under "kept_lists" (exact neighbour sets either way); the two-phase 3D dam break (Sec. 3.2.1,
 l0 = 0.004 m, 1,125,000 fluid particles) under "two_phase"; 256 independent 2D dam breaks
-stepped together in one context under "ensemble".  `e2e` repeats the mixed measurement through the C ABI with host
+stepped together in one context under "ensemble"; the reverse step (vector-Jacobian
+product, FP64) against the forward step on the 3D sloshing tank (85,564 particles) under
+"adjoint".  `e2e` repeats the mixed measurement through the C ABI with host
 buffers: every step uploads positions, velocities and kinds from pinned memory and reads
 back positions, velocities and pressure.
 
@@ -75,7 +77,7 @@ def parse():
     ap.add_argument("--cpu-sample-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l0", type=float, default=0.0075, help="particle spacing (testing only)")
-    ap.add_argument("--only", choices=["mixed", "fp64", "ensemble"], default=None,
+    ap.add_argument("--only", choices=["mixed", "fp64", "ensemble", "adjoint"], default=None,
                     help="time one precision only and print its stage profile (profiling runs)")
     ap.add_argument("--list-every", type=int, default=0,
                     help="with --only: keep candidate lists for up to this many steps")
@@ -87,6 +89,8 @@ def parse():
     ap.add_argument("--ensemble-steps", type=int, default=20,
                     help="timed steps of the batched ensemble (0: skip)")
     ap.add_argument("--ensemble-scenes", type=int, default=256)
+    ap.add_argument("--adjoint-steps", type=int, default=20,
+                    help="forward and reverse steps timed on the 3D sloshing tank (0: skip)")
     return ap.parse_args()
 
 
@@ -282,6 +286,59 @@ def run_gb300(args):
     def max_over_ranks(x):
         return rank_max(x, world, dev)
 
+    def adjoint_bench(ka):
+        # ---- reverse step (vector-Jacobian product) on the 3D sloshing tank, FP64: forward
+        # steps under the tank-frame forcing, then reverse steps from the reached state (each
+        # repeats its forward step, solves the adjoint PPE and copies the cotangents in and out)
+        sc5 = scenes.sloshing_3d(seed=args.seed + rank)
+        dt5 = 5e-5
+        sim5 = mps.Simulation(sc5, torch_alloc=True, use_torch_stream=True, precision=0,
+                              dt=dt5, cg_tol=1e-8)
+        force = lambda t: (float(scenes.sloshing_forcing(t * dt5)), 0.0, -9.81)
+        for t in range(args.warmup):
+            sim5.set_gravity(force(t))
+            sim5.step(1)
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(2 * ka)]
+        for i in range(ka):
+            sim5.set_gravity(force(args.warmup + i))
+            flush.zero_()
+            ev[i][0].record(stream)
+            sim5.step(1)
+            ev[i][1].record(stream)
+        rng5 = np.random.default_rng(args.seed)
+        ga = rng5.standard_normal((sc5.n, 3))
+        gb_ = rng5.standard_normal((sc5.n, 3))
+        its5 = []
+        for i in range(ka):
+            flush.zero_()
+            ev[ka + i][0].record(stream)
+            _, _, _, _, vrep = sim5.step_vjp(ga, gb_)
+            ev[ka + i][1].record(stream)
+            its5.append(vrep["cg_iters"])
+        torch.cuda.synchronize(dev)
+        ms_f = sum(ev[i][0].elapsed_time(ev[i][1]) for i in range(ka))
+        ms_r = sum(ev[ka + i][0].elapsed_time(ev[ka + i][1]) for i in range(ka))
+        barrier()
+        ms_f, ms_r = max_over_ranks(ms_f), max_over_ranks(ms_r)
+        sim5.close()
+        adjoint = {"workload": "3D sloshing tank 0.5 x 0.3 x 0.3 m half full, l0 0.008 m, "
+                               "forcing 0.02 m at 1.2 Hz as a tank-frame body force, dt 5e-5 s",
+                   "particles": sc5.n, "fluid": sc5.n_fluid, "precision": "fp64",
+                   "forward": {"value": world * sc5.n * ka / (ms_f * 1e-3), "unit": UNIT,
+                               "ms_per_step": ms_f / ka, "steps": ka},
+                   "reverse": {"value": world * sc5.n * ka / (ms_r * 1e-3), "unit": UNIT,
+                               "ms_per_step": ms_r / ka, "steps": ka,
+                               "adjoint_cg_iters_mean": float(np.mean(its5)),
+                               "h2d_bytes_per_step": int(2 * sc5.n * 3 * 8),
+                               "d2h_bytes_per_step": int(2 * sc5.n * 3 * 8 + 24),
+                               "includes": "the repeated forward step, the adjoint solve and "
+                                           "host copies of the cotangents"},
+                   "reverse_over_forward": ms_r / ms_f}
+        return adjoint
+
+
     if args.only == "ensemble":
         E = scenes.ensemble_2d(count=args.ensemble_scenes, seed=args.seed + rank)
         ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
@@ -298,6 +355,11 @@ def run_gb300(args):
                               "value": sum(sc.n for sc in E) * args.steps / (ms * 1e-3),
                               "cg": [x[:3] for x in its], "worst_resid": float(res.max()),
                               "profile": prof}), flush=True)
+        return
+    if args.only == "adjoint":
+        res = adjoint_bench(args.steps)
+        if rank == 0:
+            print(json.dumps({"only": "adjoint", **res}), flush=True)
         return
     if args.only:
         prec = 1 if args.only == "mixed" else 0
@@ -401,6 +463,8 @@ def run_gb300(args):
                     "stage_ms_per_step": {k: prof_e["stage_ms"][k] / ke for k in prof_e["stage_ms"]}}
         del E
 
+    adjoint = adjoint_bench(args.adjoint_steps) if args.adjoint_steps > 0 else None
+
     # ---- end to end through the C ABI with host buffers (mixed)
     ke = args.e2e_steps or args.steps
     pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
@@ -480,6 +544,7 @@ def run_gb300(args):
         "mixed_over_fp64": value / value64,
         "two_phase": two_phase,
         "ensemble": ensemble,
+        "adjoint": adjoint,
         "kept_lists": {"list_every": 4, "value": world * n * kk / (ms_k * 1e-3), "unit": UNIT,
                        "ms_per_step": ms_k / kk, "steps": kk,
                        "gathers": int(profk["stage_calls"]["gather"]),

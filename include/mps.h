@@ -186,6 +186,42 @@ int mps_read_state(mps_ctx* ctx, double* pos, double* vel, double* p, double* n_
  * them).  Same checks as mps_create.  Used to restart from a saved state. */
 int mps_write_state(mps_ctx* ctx, const double* pos, const double* vel, const int8_t* types);
 
+/* Set the external acceleration g [m/s^2] (3 doubles; the unused axis of 2D is ignored)
+ * for the following steps.  A time-dependent body force -- for instance the inertial
+ * acceleration -X''(t) of a tank shaken by X(t), in the tank's frame -- is applied by
+ * setting it before each step.  Errors: MPS_EINVAL (NULL or not finite). */
+int mps_set_gravity(mps_ctx* ctx, const double* g);
+
+/* ---------------------------------------------------------------- reverse step
+ * Vector-Jacobian product of one step (the reverse mode of the step map; the paper has no
+ * counterpart).  The step is the map (r^k, u^k, g) -> (r^{k+1}, u^{k+1}) that mps_step
+ * would apply to the context's current state.  Its discrete choices are held at their
+ * values in that step: neighbour sets, GHOST and free-surface sets (Eq. 15), the clamp's
+ * active set and the neighbour giving p_hat_i.  Within them the step is smooth and this
+ * is its exact derivative.  The PPE path solves the adjoint system A lam = dL/dp on the
+ * step's own symmetric matrix (Eq. 13 as assembled in Listing 2 of Sec. 4.3) with the same
+ * solver, precision and cg_tol; the equation-of-state path differentiates Eq. 16.
+ *   g_pos, g_vel    dL/dr^{k+1}, dL/du^{k+1}: n*dim doubles each (original order);
+ *   out_pos, out_vel dL/dr^k, dL/du^k: n*dim doubles each (caller-allocated);
+ *   out_g           dL/dg: 3 doubles (nullable; 0 on the unused axis of 2D).
+ * GHOST particles carry their cotangents through, except that a particle turned GHOST
+ * by this step (its velocity is reset) gets dL/du^k = 0.
+ * The state is not advanced: afterwards positions and velocities are unchanged and
+ * mps_read_state returns p, n* and flags of the step (as after mps_solve_ppe).
+ * Supported: one scene, kernel 0, gradient_form 0, source_term 0 (one or two phases,
+ * either precision, either pressure mode); otherwise MPS_EINVAL.
+ * Errors: as mps_step (forward) and MPS_ECG_NOCONV of the adjoint solve. */
+typedef struct {
+    int32_t status;          /* MPS_OK or the error                                         */
+    int32_t cg_iters;        /* adjoint PPE solve: CG iterations (mixed: FP32 inner ones)   */
+    int32_t cg_outer;        /* adjoint PPE solve: refinement sweeps                         */
+    int32_t pad;
+    double cg_resid;         /* adjoint PPE solve: relative residual at exit               */
+    mps_report forward;      /* the repeated forward step                                   */
+} mps_vjp_report;
+int mps_step_vjp(mps_ctx* ctx, const double* g_pos, const double* g_vel, double* out_pos,
+                 double* out_vel, double* out_g, mps_vjp_report* report);
+
 /* Two-phase (multi-density, multi-viscosity) flow of Sec. 3.2.1: a density rho_i [kg/m^3]
  * and a kinematic viscosity nu_i [m^2/s] per particle, n doubles each in the original
  * particle order (copied; the caller keeps its arrays).  NULL leaves that property uniform

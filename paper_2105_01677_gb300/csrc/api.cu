@@ -540,6 +540,9 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         stage_end(c, MPS_STAGE_PPE);
     }
     stage_begin(c, MPS_STAGE_UPDATE);
+    if (c->vjp && P.pressure_mode == 0)   // the reverse step needs p before the clamp
+        MPS_CUDA(c, cudaMemcpyAsync(c->adj.ppre, c->p, n * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, c->stream));
     if (P.pressure_mode == 0 || P.gradient_form == 1) {
         launch_clamp_pmin(c);   // the equation of state clamps nothing (no PPE solve)
     } else {
@@ -564,6 +567,24 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     }
     if (advance) c->steps_done++;
     rep->steps_done = c->steps_done;
+    return MPS_OK;
+}
+
+int alloc_adjoint(Ctx* c) {
+    AdjBuffers& a = c->adj;
+    if (a.ready) return MPS_OK;
+    const size_t n = (size_t)c->n;
+    int rc;
+    if ((rc = alloc_dev(c, &a.gr, n)) || (rc = alloc_dev(c, &a.gu, n)) ||
+        (rc = alloc_dev(c, &a.gG, n)) || (rc = alloc_dev(c, &a.grs, n)) ||
+        (rc = alloc_dev(c, &a.gus, n)) || (rc = alloc_dev(c, &a.out_r, n)) ||
+        (rc = alloc_dev(c, &a.out_u, n)) || (rc = alloc_dev(c, &a.gphat, n)) ||
+        (rc = alloc_dev(c, &a.pbar, n)) || (rc = alloc_dev(c, &a.lam, n)) ||
+        (rc = alloc_dev(c, &a.gn, n)) || (rc = alloc_dev(c, &a.ppre, n)) ||
+        (rc = alloc_dev(c, &a.amin, n)) || (rc = alloc_dev(c, &a.was_ghost, n)) ||
+        (rc = alloc_dev(c, &a.gsum, 4)))
+        return rc;
+    a.ready = true;
     return MPS_OK;
 }
 
@@ -774,6 +795,75 @@ int mps_solve_ppe(mps_ctx* c, mps_report* out) {
     rep.status = rc;
     if (out) *out = rep;
     return rc;
+}
+
+int mps_set_gravity(mps_ctx* c, const double* g) {
+    if (!c || !g) return MPS_EINVAL;
+    for (int a = 0; a < 3; a++)
+        if (!std::isfinite(g[a])) return MPS_EINVAL;
+    for (int a = 0; a < 3; a++) c->prm.g[a] = g[a];
+    return MPS_OK;
+}
+
+
+int mps_step_vjp(mps_ctx* c, const double* g_pos, const double* g_vel, double* out_pos,
+                 double* out_vel, double* out_g, mps_vjp_report* out) {
+    if (!c || !g_pos || !g_vel || !out_pos || !out_vel) return MPS_EINVAL;
+    const mps_params& P = c->prm;
+    if (c->n_scenes > 1 || P.kernel != 0 || P.gradient_form != 0 || P.source_term != 0)
+        return MPS_EINVAL;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    mps_vjp_report vr;
+    std::memset(&vr, 0, sizeof vr);
+    int rc = alloc_adjoint(c);
+    if (rc) return rc;
+    const size_t n = (size_t)c->n, dim = (size_t)c->dim;
+    // the forward step from the current state, kept for the reverse: fresh candidate lists
+    // (DUMMY rows included), the PPE solution before the clamp
+    launch_adj_mark(c);
+    c->vjp = true;
+    c->need_list = true;
+    rc = do_step(c, false, &vr.forward);
+    c->vjp = false;
+    c->need_list = true;   // the next step gathers its own lists (without DUMMY rows)
+    vr.forward.status = rc;
+    if (rc) {
+        vr.status = rc;
+        if (out) *out = vr;
+        return rc;
+    }
+    double* d_a = (double*)c->stage;
+    double* d_b = d_a + n * dim;
+    MPS_CUDA(c, cudaMemcpyAsync(d_a, g_pos, n * dim * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    MPS_CUDA(c, cudaMemcpyAsync(d_b, g_vel, n * dim * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    launch_adj_load(c, d_a, d_b);
+    launch_adj_front(c);
+    if (P.pressure_mode == 0) {
+        mps_report ar;
+        std::memset(&ar, 0, sizeof ar);
+        rc = ppe_solve_rhs(c, c->adj.lam, c->adj.pbar, &ar);
+        vr.cg_iters = ar.cg_iters;
+        vr.cg_outer = ar.cg_outer;
+        vr.cg_resid = ar.cg_resid;
+        if (rc) {
+            vr.status = rc;
+            if (out) *out = vr;
+            return rc;
+        }
+    }
+    launch_adj_back(c, c->adj.gsum);
+    launch_adj_store(c, d_a, d_b);
+    MPS_CUDA(c, cudaGetLastError());
+    MPS_CUDA(c, cudaMemcpyAsync(out_pos, d_a, n * dim * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaMemcpyAsync(out_vel, d_b, n * dim * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    double gs[3] = {0.0, 0.0, 0.0};
+    MPS_CUDA(c, cudaMemcpyAsync(gs, c->adj.gsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (out_g)
+        for (int a = 0; a < 3; a++) out_g[a] = a < c->dim ? gs[a] : 0.0;
+    if (out) *out = vr;
+    return MPS_OK;
 }
 
 int mps_read_state(mps_ctx* c, double* pos, double* vel, double* p, double* n_star,

@@ -165,6 +165,7 @@ struct VerletOp {
     int32_t* vcnt;
     const uint16_t* sid;        // ensemble: the scene of every slot (null: one scene)
     const SceneParams* scn;
+    int dummies;                // also give DUMMY particles a list (the reverse step)
 
     struct Center {
         float4 p32;
@@ -172,8 +173,12 @@ struct VerletOp {
         int cnt;
         int32_t* row;   // entry k of this row at row[32 k] (SELL-32)
     };
-    // DUMMY particles only ever appear as neighbours: they get no candidate list
-    __device__ bool active(int i) const { const int t = type[i]; return t == kFluid || t == kWall; }
+    // DUMMY particles only ever appear as neighbours: they get no candidate list (unless
+    // the reverse step asks for one: their positions enter the number densities)
+    __device__ bool active(int i) const {
+        const int t = type[i];
+        return t == kFluid || t == kWall || (dummies && t == kDummy);
+    }
     __device__ void begin(int i, bool act, Center& c) const {
         c.cnt = 0;
         c.row = vcol + sell(i, 0, cap_v);
@@ -301,6 +306,7 @@ void launch_verlet(Ctx* c) {
     op.vcnt = c->vl_cnt;
     op.sid = c->sid;
     op.scn = c->scn;
+    op.dummies = c->vjp ? 1 : 0;
     launch_gather<VerletOp>(c, op);
 }
 

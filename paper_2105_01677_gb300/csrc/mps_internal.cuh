@@ -151,6 +151,16 @@ void launch_build_rows(Ctx* c);
 
 // ---------------------------------------------------------------- ppe.cu
 int ppe_solve(Ctx* c, mps_report* rep);
+// the same solver on A x = b for another right-hand side (the adjoint solve); leaves the
+// context's record of the step's PPE solve (iteration heuristic, residual) untouched
+int ppe_solve_rhs(Ctx* c, double* x, const double* b, mps_report* rep);
+
+// ---------------------------------------------------------------- adjoint.cu
+void launch_adj_mark(Ctx* c);
+void launch_adj_load(Ctx* c, const double* d_gpos, const double* d_gvel);
+void launch_adj_front(Ctx* c);
+void launch_adj_back(Ctx* c, double* d_gsum);
+void launch_adj_store(Ctx* c, double* d_out_r, double* d_out_u);
 
 // ---------------------------------------------------------------- update.cu
 void launch_clamp_pmin(Ctx* c);
@@ -172,6 +182,20 @@ void launch_ecs_rates(Ctx* c);
 void launch_check_stage(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types);
 
 // ---------------------------------------------------------------- context
+// Work arrays of the reverse step (slot order unless noted), allocated on first use.
+struct AdjBuffers {
+    bool ready = false;
+    double4 *gr = nullptr, *gu = nullptr;     // cotangents of r^{k+1}, u^{k+1}
+    double4 *gG = nullptr;                    // of the pressure gradient (FLUID rows)
+    double4 *grs = nullptr, *gus = nullptr;   // of r*, u*
+    double4 *out_r = nullptr, *out_u = nullptr;
+    double *gphat = nullptr, *pbar = nullptr, *lam = nullptr, *gn = nullptr;
+    double* ppre = nullptr;                   // the PPE solution before the clamp
+    int32_t* amin = nullptr;                  // slot giving p_hat of each FLUID row
+    uint8_t* was_ghost = nullptr;             // by particle id: GHOST before the step
+    double* gsum = nullptr;                   // dL/dg (3)
+};
+
 struct Ctx {
     mps_params prm;
     int64_t n;
@@ -202,6 +226,10 @@ struct Ctx {
     int list_age = 0;
     bool need_list = true;
     int64_t n_ghost_last = 0;
+    // reverse step: the forward it repeats gathers candidate lists for DUMMY rows too and
+    // keeps the PPE solution before the clamp
+    bool vjp = false;
+    AdjBuffers adj;
 
     // state (sorted order) and double buffers
     double4 *pos, *vel, *pos_alt, *vel_alt;

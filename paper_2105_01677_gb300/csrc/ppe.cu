@@ -475,7 +475,7 @@ __global__ void k_clear_x(int n, double* x) {
 // uneven rows (dummy and surface rows are empty) across the SMs.
 static int row_grid(const Ctx* c) { return (int)std::min<int64_t>((c->n + kBT - 1) / kBT, 4096); }
 
-static SellView sell_view(Ctx* c) {
+static SellView sell_view(Ctx* c, const double* b) {
     SellView v;
     v.n = (int)c->n;
     v.cap = c->cap;
@@ -486,7 +486,7 @@ static SellView sell_view(Ctx* c) {
     v.vlo = c->nb_lap_vlo;
     v.diag = c->diag;
     v.diag32 = c->diag32;
-    v.bvec = c->bvec;
+    v.bvec = b;
     v.pos32s = c->pos32_star;
     v.partials = c->partials;
     v.counter = c->st->counter;
@@ -508,29 +508,28 @@ static int set_cg_limits(Ctx* c, int max_iters) {
 }
 
 // Launch up to `chunk` iterations of FP64 CG (extra launches exit at once once done).
-static void cg64_chunk(Ctx* c, int chunk) {
+static void cg64_chunk(Ctx* c, int chunk, double* x, const double* b) {
     const int n = (int)c->n;
     const int gv = vec_grid(c), gs = row_grid(c);
-    double* x = c->p;
     c->launches += 3 * chunk;
     for (int k = 0; k < chunk; k++) {
-        k_spmv64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->cg_d, c->cg_q, c->cg);
+        k_spmv64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), c->cg_d, c->cg_q, c->cg);
         k_xr64<<<gv, kBT, 0, c->stream>>>(n, x, c->cg_r, c->cg_d, c->cg_q, c->cg, c->partials,
                                           &c->st->counter[2]);
         k_d64<<<gv, kBT, 0, c->stream>>>(n, c->cg_r, c->cg_d, c->cg);
     }
 }
 
-static void cg32_chunk(Ctx* c, int chunk) {
+static void cg32_chunk(Ctx* c, int chunk, const double* b) {
     const int n = (int)c->n;
     const int gv = vec_grid(c), gs = row_grid(c);
     const float coef = (float)c->coef_ppe, re_f = (float)c->r_lap.re;
     c->launches += 3 * chunk;
     for (int k = 0; k < chunk; k++) {
         if (c->prm.ppe_operator == 1)
-            k_spmv32_t<true><<<gs, kBT, 0, c->stream>>>(sell_view(c), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+            k_spmv32_t<true><<<gs, kBT, 0, c->stream>>>(sell_view(c, b), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
         else
-            k_spmv32_t<false><<<gs, kBT, 0, c->stream>>>(sell_view(c), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+            k_spmv32_t<false><<<gs, kBT, 0, c->stream>>>(sell_view(c, b), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
         k_xr32<<<gv, kBT, 0, c->stream>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_q32, c->cg,
                                           c->partials, &c->st->counter[2]);
         k_d32<<<gv, kBT, 0, c->stream>>>(n, c->cg_r32, c->cg_d32, c->cg);
@@ -539,9 +538,9 @@ static void cg32_chunk(Ctx* c, int chunk) {
 
 // Ensemble: every scene's relative residual from the FP64 residual in cg_r; true when all
 // are within cg_tol.  The worst is returned in *worst.
-static int scenes_converged(Ctx* c, double tol, bool* ok, double* worst) {
+static int scenes_converged(Ctx* c, const double* b, double tol, bool* ok, double* worst) {
     const int S = c->n_scenes;
-    k_scene_sums<<<S, kBT, 0, c->stream>>>(c->cg_r, c->bvec, c->cell_start, c->scene_shift,
+    k_scene_sums<<<S, kBT, 0, c->stream>>>(c->cg_r, b, c->cell_start, c->scene_shift,
                                            c->scene_sums);
     c->launches += 1;
     std::vector<double> h(2 * (size_t)S);
@@ -567,7 +566,9 @@ static double tighten(double tol, double worst) {
     return std::min(0.5, std::max(f, 1e-8));
 }
 
-int ppe_solve(Ctx* c, mps_report* rep) {
+// A x = b; primary: the step's own PPE (x = p, b = the source), whose iteration count and
+// residual the context keeps for the next solve and for mps_scene_residuals
+static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool primary) {
     const int n = (int)c->n;
     const double tol2 = c->prm.cg_tol * c->prm.cg_tol;
     const int max_total = c->prm.cg_max_iter > 0 ? c->prm.cg_max_iter : (int)std::min<int64_t>(10 * c->n, 1 << 30);
@@ -575,7 +576,7 @@ int ppe_solve(Ctx* c, mps_report* rep) {
     int rc;
     if ((rc = set_cg_limits(c, max_total))) return rc;
     // x = 0, r = b, d = b, rho = |b|^2, stop2 = tol^2 |b|^2
-    k_start64<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2, c->cg_xhl);
+    k_start64<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), x, c->cg_r, c->cg_d, c->cg, tol2, c->cg_xhl);
     c->launches += 1;
     if ((rc = read_scalars(c))) return rc;
     const double bnorm2 = c->cg_host->rr;
@@ -595,19 +596,19 @@ int ppe_solve(Ctx* c, mps_report* rep) {
     int chunk = std::max(4, c->last_cg_iters + 1);
     if (c->prm.precision == 0) {
         for (;;) {
-            cg64_chunk(c, chunk);
+            cg64_chunk(c, chunk, x, b);
             if ((rc = read_scalars(c))) return rc;
             if (!c->cg_host->done) { chunk = std::max(4, chunk / 2); continue; }
             total_iters = c->cg_host->iters;
             // true residual; restart from it if the recurrence drifted
             c->launches += 1;
-            k_resid64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_r, c->cg_d, c->cg, tol2, 0, 1);
+            k_resid64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), x, c->cg_r, c->cg_d, c->cg, tol2, 0, 1);
             if ((rc = read_scalars(c))) return rc;
             rel = sqrt(c->cg_host->rr / bnorm2);
             if (c->cg_host->rr <= stop2) {
                 if (!multi) break;
                 // ensemble: every scene to its own tolerance, else a tighter global target
-                if ((rc = scenes_converged(c, c->prm.cg_tol, &sc_ok, &sc_worst))) return rc;
+                if ((rc = scenes_converged(c, b, c->prm.cg_tol, &sc_ok, &sc_worst))) return rc;
                 if (sc_ok) break;
                 stop2 *= tighten(c->prm.cg_tol, sc_worst);
                 k_set_stop<<<1, 1, 0, c->stream>>>(c->cg, stop2);
@@ -630,7 +631,7 @@ int ppe_solve(Ctx* c, mps_report* rep) {
             if (rr <= stop2) {
                 if (!multi) break;
                 // ensemble: every scene to its own tolerance, else a tighter global target
-                if ((rc = scenes_converged(c, c->prm.cg_tol, &sc_ok, &sc_worst))) return rc;
+                if ((rc = scenes_converged(c, b, c->prm.cg_tol, &sc_ok, &sc_worst))) return rc;
                 if (sc_ok) break;
                 stop2 *= tighten(c->prm.cg_tol, sc_worst);
             }
@@ -650,27 +651,34 @@ int ppe_solve(Ctx* c, mps_report* rep) {
                                                     itol_k * itol_k, max_total - total_iters,
                                                     c->partials, &c->st->counter[3]);
             for (;;) {
-                cg32_chunk(c, chunk);
+                cg32_chunk(c, chunk, b);
                 if ((rc = read_scalars(c))) return rc;
                 if (c->cg_host->done) break;
                 chunk = std::max(4, chunk / 2);
             }
             total_iters += c->cg_host->iters;
-            k_outer_update<<<gv, kBT, 0, c->stream>>>(n, c->p, c->cg_x32, rr, c->cg_xhl);
-            k_resid_ff_t<<<gs, kBT, 0, c->stream>>>(sell_view(c), c->p, c->cg_xhl, c->cg_r, c->cg);
+            k_outer_update<<<gv, kBT, 0, c->stream>>>(n, x, c->cg_x32, rr, c->cg_xhl);
+            k_resid_ff_t<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), x, c->cg_xhl, c->cg_r, c->cg);
             if ((rc = read_scalars(c))) return rc;
             rr = c->cg_host->rr;
             outer++;
         }
         rel = sqrt(rr / bnorm2);
     }
-    c->last_cg_iters = (c->prm.precision == 0) ? total_iters : std::max(4, total_iters / std::max(outer, 1));
+    if (primary)
+        c->last_cg_iters = (c->prm.precision == 0) ? total_iters : std::max(4, total_iters / std::max(outer, 1));
     rep->cg_iters = total_iters;
     rep->cg_outer = outer;
     rep->cg_resid = multi ? sc_worst : rel;   // ensemble: the worst scene
-    if (!multi) c->scene_resid[0] = rel;
+    if (!multi && primary) c->scene_resid[0] = rel;
     MPS_CUDA(c, cudaGetLastError());
     return MPS_OK;
+}
+
+int ppe_solve(Ctx* c, mps_report* rep) { return solve(c, c->p, c->bvec, rep, true); }
+
+int ppe_solve_rhs(Ctx* c, double* x, const double* b, mps_report* rep) {
+    return solve(c, x, b, rep, false);
 }
 
 }  // namespace mps

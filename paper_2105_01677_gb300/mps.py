@@ -60,11 +60,20 @@ class mps_report(C.Structure):
         return d
 
 
+class mps_vjp_report(C.Structure):
+    _fields_ = [("status", C.c_int32), ("cg_iters", C.c_int32), ("cg_outer", C.c_int32),
+                ("pad", C.c_int32), ("cg_resid", C.c_double), ("forward", mps_report)]
+
+    def as_dict(self) -> dict:
+        return dict(status=self.status, cg_iters=self.cg_iters, cg_outer=self.cg_outer,
+                    cg_resid=self.cg_resid, forward=self.forward.as_dict())
+
+
 EXPORTS = ("mps_params_default", "mps_create", "mps_step", "mps_solve_ppe", "mps_read_state",
            "mps_write_state", "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants",
            "mps_set_profiling", "mps_get_profile", "mps_ppe_cg_noalloc", "mps_destroy",
            "mps_strerror", "mps_set_fluid_properties", "mps_create_ensemble",
-           "mps_scene_residuals", "mps_autotune")
+           "mps_scene_residuals", "mps_autotune", "mps_set_gravity", "mps_step_vjp")
 NOALLOC_MAX_ROWS = 262144
 STAGES = ("bucket", "gather", "predict", "build", "ppe", "update")
 
@@ -96,6 +105,8 @@ def lib(build_if_missing: bool = False):
     L.mps_read_state.argtypes = [C.c_void_p, d, d, d, d, u8, i8]
     L.mps_write_state.argtypes = [C.c_void_p, d, d, i8]
     L.mps_set_fluid_properties.argtypes = [C.c_void_p, d, d]
+    L.mps_set_gravity.argtypes = [C.c_void_p, d]
+    L.mps_step_vjp.argtypes = [C.c_void_p, d, d, d, d, d, C.POINTER(mps_vjp_report)]
     L.mps_create_ensemble.argtypes = [d, d, i8, C.POINTER(C.c_int32), C.c_int64,
                                       C.POINTER(mps_params), C.POINTER(mps_scene), C.c_int32,
                                       C.POINTER(C.c_void_p)]
@@ -117,7 +128,8 @@ def lib(build_if_missing: bool = False):
     for f in ("mps_create", "mps_step", "mps_solve_ppe", "mps_read_state", "mps_write_state",
               "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants", "mps_set_profiling",
               "mps_get_profile", "mps_ppe_cg_noalloc", "mps_set_fluid_properties",
-              "mps_create_ensemble", "mps_scene_residuals", "mps_autotune"):
+              "mps_create_ensemble", "mps_scene_residuals", "mps_autotune", "mps_set_gravity",
+              "mps_step_vjp"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -319,6 +331,32 @@ def mps_set_fluid_properties(h, rho=None, nu=None, check: bool = True):
     return rc
 
 
+def mps_set_gravity(h, g):
+    """External acceleration g (3 values; the unused axis of 2D is ignored) for the next steps."""
+    ga = np.zeros(3, np.float64)
+    ga[: len(g)] = np.asarray(g, np.float64)
+    _check(lib().mps_set_gravity(h, _ptr(ga, C.c_double)), "mps_set_gravity")
+
+
+def mps_step_vjp(h, g_pos, g_vel, check: bool = True):
+    """Reverse of the step from the current state: given dL/dr^{k+1}, dL/du^{k+1} ((n, dim)
+    float64, original order) returns (rc, dL/dr^k, dL/du^k, dL/dg[3], report dict)."""
+    g_pos = np.ascontiguousarray(g_pos, np.float64)
+    g_vel = np.ascontiguousarray(g_vel, np.float64)
+    if g_pos.shape != g_vel.shape:
+        raise ValueError("g_pos and g_vel must have the same shape (n, dim)")
+    out_r = np.empty_like(g_pos)
+    out_u = np.empty_like(g_vel)
+    out_g = np.zeros(3, np.float64)
+    rep = mps_vjp_report()
+    rc = lib().mps_step_vjp(h, _ptr(g_pos, C.c_double), _ptr(g_vel, C.c_double),
+                            _ptr(out_r, C.c_double), _ptr(out_u, C.c_double),
+                            _ptr(out_g, C.c_double), C.byref(rep))
+    if check:
+        _check(rc, "mps_step_vjp")
+    return rc, out_r, out_u, out_g, rep.as_dict()
+
+
 def mps_debug_cells(h, n: int):
     out = np.empty(n, np.uint32)
     _check(lib().mps_debug_cells(h, _ptr(out, C.c_uint32)), "mps_debug_cells")
@@ -452,6 +490,13 @@ class Simulation:
 
     def solve_ppe(self, check: bool = True):
         return mps_solve_ppe(self.h, check)
+
+    def set_gravity(self, g):
+        mps_set_gravity(self.h, g)
+
+    def step_vjp(self, g_pos, g_vel, check: bool = True):
+        """(rc, dL/dr, dL/du, dL/dg, report) of the step from the current state."""
+        return mps_step_vjp(self.h, g_pos, g_vel, check)
 
     def read(self, **kw):
         return mps_read_state(self.h, self.n, self.dim, **kw)

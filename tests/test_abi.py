@@ -56,6 +56,7 @@ def _c_layout():
 int main(void) {
   printf("mps_params size %zu\n", sizeof(mps_params));
   printf("mps_report size %zu\n", sizeof(mps_report));
+  printf("mps_vjp_report size %zu\n", sizeof(mps_vjp_report));
   P(mps_params, dim) P(mps_params, l0) P(mps_params, g) P(mps_params, cg_max_iter)
   P(mps_params, precision) P(mps_params, nbr_cap) P(mps_params, cell_skin) P(mps_params, box_min)
   P(mps_params, box_max) P(mps_params, inner_tol) P(mps_params, ppe_operator) P(mps_params, stream)
@@ -64,6 +65,7 @@ int main(void) {
   P(mps_report, list_gathered)
   P(mps_report, cg_resid) P(mps_report, n_surface) P(mps_report, max_disp) P(mps_report, lambda)
   P(mps_report, steps_done) P(mps_report, cand_tests) P(mps_report, pairs_pnd)
+  P(mps_vjp_report, cg_iters) P(mps_vjp_report, cg_resid) P(mps_vjp_report, forward)
   return 0;
 }
 '''
@@ -84,10 +86,13 @@ def test_struct_layout_matches_binding():
     lay = _c_layout()
     assert lay[("mps_params", "size")] == C.sizeof(mps.mps_params)
     assert lay[("mps_report", "size")] == C.sizeof(mps.mps_report)
+    assert lay[("mps_vjp_report", "size")] == C.sizeof(mps.mps_vjp_report)
+    classes = {"mps_params": mps.mps_params, "mps_report": mps.mps_report,
+               "mps_vjp_report": mps.mps_vjp_report}
     for (s, f), off in lay.items():
         if f == "size":
             continue
-        cls = mps.mps_params if s == "mps_params" else mps.mps_report
+        cls = classes[s]
         name = "lambda_" if f == "lambda" else f
         assert getattr(cls, name).offset == off, (s, f)
 
@@ -124,6 +129,9 @@ def test_invalid_arguments_rejected_before_device_use(L):
                       t2.ctypes.data_as(C.POINTER(C.c_int8)), 3, C.byref(P), C.byref(h))
     assert rc == mps.EINVAL
     assert L.mps_step(None, 1, None) == mps.EINVAL
+    assert L.mps_step_vjp(None, None, None, None, None, None, None) == mps.EINVAL
+    g = np.zeros(3)
+    assert L.mps_set_gravity(None, g.ctypes.data_as(C.POINTER(C.c_double))) == mps.EINVAL
 
 
 def test_strerror_names_every_code(L):
