@@ -88,9 +88,8 @@ __global__ void __launch_bounds__(kBT) k_adj_grad(AdjArgs a) {
         for (int t = 0; t < cnt; t++) {
             const int j = a.ncol[sell(i, t, a.cap_n)];
             const double4 x = sub4(a.ps[j], pi);
-            const double s2 = dot3(x, x);
-            const double s = sqrt(s2);
-            const double q = (a.rn.re / s - 1.0) / s2;
+            const double rs = rsqrt(dot3(x, x));
+            const double q = fma(a.rn.re, rs, -1.0) * (rs * rs);   // w / s^2
             S = axpy4(q, x, S);
             if (a.ppe) {
                 const double pj = a.p[j];
@@ -123,9 +122,8 @@ __global__ void __launch_bounds__(kBT) k_adj_pbar(AdjArgs a) {
             const int i = a.ncol[sell(j, t, a.cap_n)];
             if (a.type[i] != kFluid) continue;
             const double4 x = sub4(pj, a.ps[i]);   // r_j - r_i for the pair (i, j) of row i
-            const double s2 = dot3(x, x);
-            const double s = sqrt(s2);
-            const double q = (a.rn.re / s - 1.0) / s2;
+            const double rs = rsqrt(dot3(x, x));
+            const double q = fma(a.rn.re, rs, -1.0) * (rs * rs);
             pb = fma(a.coef_grad * q, dot3(x, a.gG[i]), pb);
             if (a.amin[i] == j) pb += a.gphat[i];
         }
@@ -172,28 +170,30 @@ __global__ void __launch_bounds__(kBT) k_adj_star(AdjArgs a) {
             const bool in_l = a.ppe && ndk && ndj && in_radius(r2f, a.rl, a.ps, k, j, xk);
             if (!in_n && !in_l) continue;
             const double4 x = sub4(a.ps[j], xk);
-            const double s2 = dot3(x, x);
-            const double s = sqrt(s2);
-            const double is3 = 1.0 / (s2 * s);
+            // every power of 1/s from one reciprocal square root
+            const double rs = rsqrt(dot3(x, x));
+            const double rs2 = rs * rs;
+            const double is3 = rs2 * rs;
             if (in_n) {
                 // n*_k and n*_j both hold w(s): -(gn_k + gn_j) w'(s) x/s
                 acc = axpy4((gnk + gn_of(a, j)) * a.rn.re * is3, x, acc);
                 if (ndk && ndj) {
-                    const double w = a.rn.re / s - 1.0;
-                    const double q = w / s2;
-                    const double qd = -a.rn.re / (s2 * s2) - 2.0 * w * is3;
+                    const double w = fma(a.rn.re, rs, -1.0);
+                    const double q = w * rs2;
+                    // (d/ds (w/s^2)) / s = -re/s^5 - 2 w/s^4
+                    const double qds = -rs2 * rs2 * fma(a.rn.re, rs, 2.0 * w);
                     if (fk) {   // pair (k, j) of row k's gradient: -X
                         const double dg = dot3(x, gGk);
                         const double f = a.coef_grad * (a.p[j] - phk);
                         acc = axpy4(-f * q, gGk, acc);
-                        acc = axpy4(-f * (qd / s) * dg, x, acc);
+                        acc = axpy4(-f * qds * dg, x, acc);
                     }
                     if (tj == kFluid) {   // pair (j, k) of row j's gradient: +X
                         const double4 gGj = a.gG[j];
                         const double dg = dot3(x, gGj);
                         const double f = a.coef_grad * (pk - a.phat[j]);
                         acc = axpy4(f * q, gGj, acc);
-                        acc = axpy4(f * (qd / s) * dg, x, acc);
+                        acc = axpy4(f * qds * dg, x, acc);
                     }
                 }
             }
@@ -233,10 +233,9 @@ __global__ void __launch_bounds__(kBT) k_adj_visc(AdjArgs a) {
         const int j = a.vcol[sell(k, t, a.cap_v)];
         if (!in_radius(dist2_f(qk, a.pos32[j]), a.rl, a.pos, k, j, xk)) continue;
         const double4 x = sub4(a.pos[j], xk);
-        const double s2 = dot3(x, x);
-        const double s = sqrt(s2);
-        const double w = a.rl.re / s - 1.0;
-        const double wd_s = -a.rl.re / (s2 * s);   // w'(s)/s
+        const double rs = rsqrt(dot3(x, x));
+        const double w = fma(a.rl.re, rs, -1.0);
+        const double wd_s = -a.rl.re * (rs * rs * rs);   // w'(s)/s
         const double4 uj = a.vel[j];
         if (fk) {   // row k's Laplacian: u_k enters with -w, positions through w
             ou = axpy4(-kk * w, gsk, ou);
@@ -255,13 +254,12 @@ __global__ void __launch_bounds__(kBT) k_adj_visc(AdjArgs a) {
     a.out_u[k] = ou;
 }
 
-// dL/dg = dt sum over FLUID rows of gu* (one block, fixed order)
-__global__ void __launch_bounds__(256) k_adj_gsum(int n, const int8_t* type, const double4* gus,
-                                                  double dt, double* out) {
+// dL/dg = dt sum over FLUID rows of gu*: per-block partial sums (gus is zero off FLUID
+// rows), then one block adds them in block order
+__global__ void __launch_bounds__(256) k_adj_gpart(int n, const double4* gus, double* part) {
     __shared__ double sm[8];
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int i = threadIdx.x; i < n; i += 256) {
-        if (type[i] != kFluid) continue;
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256) {
         const double4 v = gus[i];
         s0 += v.x;
         s1 += v.y;
@@ -271,9 +269,20 @@ __global__ void __launch_bounds__(256) k_adj_gsum(int n, const int8_t* type, con
     s1 = block_sum<256>(s1, sm);
     s2 = block_sum<256>(s2, sm);
     if (threadIdx.x == 0) {
-        out[0] = dt * s0;
-        out[1] = dt * s1;
-        out[2] = dt * s2;
+        part[3 * blockIdx.x] = s0;
+        part[3 * blockIdx.x + 1] = s1;
+        part[3 * blockIdx.x + 2] = s2;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_adj_gsum(int nb, const double* part, double dt, double* out) {
+    __shared__ double sm[8];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nb; b += 256)
+        for (int a = 0; a < 3; a++) s[a] += part[3 * b + a];
+    for (int a = 0; a < 3; a++) {
+        const double t = block_sum<256>(s[a], sm);
+        if (threadIdx.x == 0) out[a] = dt * t;
     }
 }
 
@@ -397,8 +406,10 @@ void launch_adj_back(Ctx* c, double* d_gsum) {
     const int g = blocks(c->n, kBT);
     k_adj_star<<<g, kBT, 0, c->stream>>>(a);
     k_adj_visc<<<g, kBT, 0, c->stream>>>(a);
-    k_adj_gsum<<<1, 256, 0, c->stream>>>((int)c->n, c->type, c->adj.gus, c->prm.dt, d_gsum);
-    c->launches += 3;
+    const int nb = std::min<int>(blocks(c->n, 256), 1024);   // c->partials holds 4096 doubles
+    k_adj_gpart<<<nb, 256, 0, c->stream>>>((int)c->n, c->adj.gus, c->partials);
+    k_adj_gsum<<<1, 256, 0, c->stream>>>(nb, c->partials, c->prm.dt, d_gsum);
+    c->launches += 4;
 }
 
 void launch_adj_store(Ctx* c, double* d_out_r, double* d_out_u) {
