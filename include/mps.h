@@ -109,6 +109,11 @@ typedef struct {
                                * the number-density neighbours; 2 HS plus the error-           *
                                * compensating source of Eq. 24-25, ECS / dt, from n and Dn/Dt  *
                                * at the step's start (1 and 2 require kernel 0)                 */
+    int32_t ppe_host_loop;    /* mixed PPE of one scene: 0 (default) runs the refinement and   *
+                               * inner CG loops on the device as one CUDA graph with           *
+                               * conditional nodes (one launch and one read per solve); 1     *
+                               * drives them from the host, polling per chunk of iterations.  *
+                               * Results are identical.                                        */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;

@@ -143,6 +143,7 @@ int check_params(const mps_params* P) {
     if (P->pressure_mode == 1 && !(P->gamma > 0)) return MPS_EINVAL;
     if ((P->alloc == nullptr) != (P->release == nullptr)) return MPS_EINVAL;
     if (P->list_every < 0) return MPS_EINVAL;
+    if (P->ppe_host_loop != 0 && P->ppe_host_loop != 1) return MPS_EINVAL;
     if (P->kernel < 0 || P->kernel > 1 || P->gradient_form < 0 || P->gradient_form > 1 ||
         P->source_term < 0 || P->source_term > 2 || (P->source_term >= 1 && P->kernel != 0))
         return MPS_EINVAL;
@@ -1065,6 +1066,7 @@ void mps_destroy(mps_ctx* c) {
         if (c->stream) cudaStreamSynchronize(c->stream);
         for (int k = 0; k < 2 * MPS_NSTAGES; k++)
             if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+        ppe_graphs_destroy(c);
         free_all(c);
         if (c->st_host) cudaFreeHost(c->st_host);
         if (c->cg_host) cudaFreeHost(c->cg_host);

@@ -66,6 +66,14 @@ struct CgScalars {
     int iters;         // iterations executed by this solve
     int max_iters;
     int pad;
+    // device-driven mixed solve (one CUDA graph with conditional WHILE nodes): the outer
+    // target, the refinement sweeps and inner iterations so far, their caps, the inner
+    // tolerance, and loop guards that end either loop whatever the CG does
+    double ostop2;
+    double bb;         // |b|^2
+    double inner_tol;
+    int outer, total, max_outer, max_total;
+    int guard_in, guard_out;
 };
 
 struct GridDesc {
@@ -154,6 +162,7 @@ int ppe_solve(Ctx* c, mps_report* rep);
 // the same solver on A x = b for another right-hand side (the adjoint solve); leaves the
 // context's record of the step's PPE solve (iteration heuristic, residual) untouched
 int ppe_solve_rhs(Ctx* c, double* x, const double* b, mps_report* rep);
+void ppe_graphs_destroy(Ctx* c);
 
 // ---------------------------------------------------------------- adjoint.cu
 void launch_adj_mark(Ctx* c);
@@ -182,6 +191,15 @@ void launch_ecs_rates(Ctx* c);
 void launch_check_stage(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types);
 
 // ---------------------------------------------------------------- context
+// The mixed PPE solve captured as one CUDA graph (outer refinement loop around the inner
+// FP32 CG loop, both conditional WHILE nodes set by the kernels), one per buffer that the
+// solution p can live in (the bucket build swaps p with its alternate buffer).
+struct PpeGraph {
+    const double* x = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 // Work arrays of the reverse step (slot order unless noted), allocated on first use.
 struct AdjBuffers {
     bool ready = false;
@@ -230,6 +248,7 @@ struct Ctx {
     // keeps the PPE solution before the clamp
     bool vjp = false;
     AdjBuffers adj;
+    PpeGraph ppe_graph[2];
 
     // state (sorted order) and double buffers
     double4 *pos, *vel, *pos_alt, *vel_alt;

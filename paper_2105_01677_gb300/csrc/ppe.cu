@@ -144,11 +144,16 @@ __global__ void __launch_bounds__(kBT) k_d64(int n, const double* r, double* d, 
 }
 
 // ------------------------------------------------------------------ FP32 inner kernels
-// r32 = r64 / |r64|, d32 = r32, x32 = 0; rho = r32.r32; stop2 = itol2 * rho
+// r32 = r64 / |r64|, d32 = r32, x32 = 0; rho = r32.r32; stop2 = itol2 * rho.
+// itol2 < 0 (the device-driven solve): the inner tolerance and iteration cap are taken on
+// the device, as the host loop takes them: the reduction the outer target still needs
+// (with a margin of 2) when one FP32 solve can reach it, else inner_tol; h_in (nonzero) is
+// the conditional of the inner loop, set to run it unless the inner solve is already done.
 __global__ void __launch_bounds__(kBT) k_inner_init(int n, const double* r64, float* r32, float* d32,
                                                     float* x32, CgScalars* cg, double itol2,
                                                     int max_iters, double* partials,
-                                                    unsigned int* counter) {
+                                                    unsigned int* counter,
+                                                    cudaGraphConditionalHandle h_in) {
     __shared__ double sm[kWarps];
     const double scale = 1.0 / sqrt(cg->rr);
     double part = 0.0;
@@ -162,12 +167,22 @@ __global__ void __launch_bounds__(kBT) k_inner_init(int n, const double* r64, fl
     double tot;
     part = block_sum<kBT>(part, sm);
     if (grid_sum<kBT>(part, partials, counter, &tot, sm) && threadIdx.x == 0) {
+        if (itol2 < 0.0) {
+            const double need = 0.5 * sqrt(cg->ostop2 / cg->rr);
+            const double itol = (need >= kInnerFloor) ? need : cg->inner_tol;
+            itol2 = itol * itol;
+            max_iters = cg->max_total - cg->total;
+        }
         cg->rho = tot;
         cg->rho0 = tot;
         cg->stop2 = itol2 * tot;
         cg->iters = 0;
         cg->max_iters = max_iters;
         cg->done = (tot > 0.0 && max_iters > 0) ? 0 : 1;
+        if (h_in) {
+            cg->guard_in = 0;
+            cudaGraphSetConditional(h_in, cg->done ? 0u : 1u);
+        }
     }
 }
 
@@ -193,7 +208,15 @@ __global__ void __launch_bounds__(kBT) k_xr32(int n, float* x, float* r, const f
     }
 }
 
-__global__ void __launch_bounds__(kBT) k_d32(int n, const float* r, float* d, const CgScalars* cg) {
+// d = r + beta d.  h_in (nonzero): the inner loop's conditional, set first by one thread
+// (run again unless done; never more than max_total + 2 times in one inner solve)
+__global__ void __launch_bounds__(kBT) k_d32(int n, const float* r, float* d, CgScalars* cg,
+                                             cudaGraphConditionalHandle h_in) {
+    if (h_in && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int g = ++cg->guard_in;
+        const bool more = !*(volatile const int*)&cg->done && g < cg->max_total + 2;
+        cudaGraphSetConditional(h_in, more ? 1u : 0u);
+    }
     if (*(volatile const int*)&cg->done) return;
     const float beta = (float)cg->beta;
     for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) d[i] = fmaf(beta, d[i], r[i]);
@@ -287,8 +310,12 @@ __global__ void __launch_bounds__(kBT) k_resid64_t(SellView c, const double* x, 
 // x as float-float (xh + xl) beside its binary64 value: each product and the row sum are
 // formed with error-free transformations on the FP32 pipes (~2^-46 relative per term), the
 // row result is combined with b and the diagonal in binary64.
+// h_out (nonzero, the device-driven solve): the sweep's inner iterations are added to the
+// total and the refinement loop's conditional is set: another sweep while the residual is
+// above the outer target and within the caps (never more than max_outer + 2 sweeps).
 __global__ void __launch_bounds__(kBT) k_resid_ff_t(SellView c, const double* x, const float2* xhl,
-                                                    double* r, CgScalars* cg) {
+                                                    double* r, CgScalars* cg,
+                                                    cudaGraphConditionalHandle h_out) {
     __shared__ double sm[kWarps];
     double part = 0.0;
     for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT) {
@@ -338,12 +365,25 @@ __global__ void __launch_bounds__(kBT) k_resid_ff_t(SellView c, const double* x,
     }
     double tot;
     part = block_sum<kBT>(part, sm);
-    if (grid_sum<kBT>(part, c.partials, &c.counter[0], &tot, sm) && threadIdx.x == 0) cg->rr = tot;
+    if (grid_sum<kBT>(part, c.partials, &c.counter[0], &tot, sm) && threadIdx.x == 0) {
+        cg->rr = tot;
+        if (h_out) {
+            cg->total += cg->iters;
+            cg->outer += 1;
+            cg->guard_out += 1;
+            const bool more = tot > cg->ostop2 && cg->outer < cg->max_outer &&
+                              cg->total < cg->max_total && cg->guard_out < cg->max_outer + 2;
+            cudaGraphSetConditional(h_out, more ? 1u : 0u);
+        }
+    }
 }
 
 // start of a solve from x = 0: x = 0, r = b, d = b, rr = rho = b.b, stop2 = tol2 b.b
+// h_out (nonzero, the device-driven mixed solve): also the outer target and counters, and
+// the refinement loop's conditional (run unless b = 0)
 __global__ void __launch_bounds__(kBT) k_start64(SellView c, double* x, double* r, double* d,
-                                                 CgScalars* cg, double tol2, float2* xhl) {
+                                                 CgScalars* cg, double tol2, float2* xhl,
+                                                 cudaGraphConditionalHandle h_out) {
     __shared__ double sm[kWarps];
     double part = 0.0;
     for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT) {
@@ -362,6 +402,14 @@ __global__ void __launch_bounds__(kBT) k_start64(SellView c, double* x, double* 
         cg->rho = tot;
         cg->rho0 = tot;
         cg->done = (tot <= cg->stop2) ? 1 : 0;
+        cg->bb = tot;
+        if (h_out) {
+            cg->ostop2 = tol2 * tot;
+            cg->outer = 0;
+            cg->total = 0;
+            cg->guard_out = 0;
+            cudaGraphSetConditional(h_out, tot > cg->ostop2 ? 1u : 0u);
+        }
     }
 }
 
@@ -426,9 +474,11 @@ __global__ void __launch_bounds__(kBT) k_spmv32_t(SellView c, const float* d, fl
 
 // x64 += |r64| x32   (|r64| = sqrt(rr) of the residual that started the inner solve); the
 // float-float copy of x for the next outer residual is refreshed at the same time
+// scale_rr < 0 (the device-driven solve): |r64|^2 is read from the scalars (cg->rr still
+// holds the residual that started the inner solve)
 __global__ void __launch_bounds__(kBT) k_outer_update(int n, double* x, const float* e, double scale_rr,
-                                                      float2* xhl) {
-    const double s = sqrt(scale_rr);
+                                                      float2* xhl, const CgScalars* cg) {
+    const double s = sqrt(scale_rr < 0.0 ? cg->rr : scale_rr);
     for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) {
         const double v = fma(s, (double)e[i], x[i]);
         x[i] = v;
@@ -532,7 +582,7 @@ static void cg32_chunk(Ctx* c, int chunk, const double* b) {
             k_spmv32_t<false><<<gs, kBT, 0, c->stream>>>(sell_view(c, b), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
         k_xr32<<<gv, kBT, 0, c->stream>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_q32, c->cg,
                                           c->partials, &c->st->counter[2]);
-        k_d32<<<gv, kBT, 0, c->stream>>>(n, c->cg_r32, c->cg_d32, c->cg);
+        k_d32<<<gv, kBT, 0, c->stream>>>(n, c->cg_r32, c->cg_d32, c->cg, 0);
     }
 }
 
@@ -566,6 +616,126 @@ static double tighten(double tol, double worst) {
     return std::min(0.5, std::max(f, 1e-8));
 }
 
+// ---------------------------------------------------------------- device-driven mixed solve
+// The mixed solve of one scene as one CUDA graph:
+//   start (x = 0, r = b, outer target)  ->  WHILE (sweeps) {
+//       inner init (r32 = r/|r|, tolerance)  ->  WHILE (inner) { A d, x/r update, d update }
+//       ->  x += |r| e  ->  r = b - A x (float-float) }
+// Both conditions are set by the kernels (one thread each, every iteration), so the solve
+// is one launch and one read of the scalars instead of a host poll per chunk of iterations
+// and per sweep; the kernels and their arithmetic are those of the host-driven loop, so
+// the results are identical.
+static cudaGraphNode_t only_node(cudaGraph_t g) {
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> v(nn);
+    if (nn) cudaGraphGetNodes(g, v.data(), &nn);
+    return nn == 1 ? v[0] : nullptr;
+}
+
+static int add_while(Ctx* c, cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h,
+                     cudaGraphNode_t* node, cudaGraph_t* body) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    MPS_CUDA(c, cudaGraphAddNode(node, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &cp));
+    *body = cp.conditional.phGraph_out[0];
+    return MPS_OK;
+}
+
+static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
+    const int n = (int)c->n;
+    const int gs = row_grid(c), gv = vec_grid(c);
+    const double tol2 = c->prm.cg_tol * c->prm.cg_tol;
+    const float coef = (float)c->coef_ppe, re_f = (float)c->r_lap.re;
+    const SellView sv = sell_view(c, c->bvec);
+    cudaStream_t s = c->stream;
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    MPS_CUDA(c, cudaStreamSynchronize(s));
+    cudaGraph_t G = nullptr, B = nullptr, Bi = nullptr, tmp = nullptr;
+    cudaGraphConditionalHandle h_out = 0, h_in = 0;
+    cudaGraphNode_t n_start, n_outer, n_init, n_inner;
+    MPS_CUDA(c, cudaGraphCreate(&G, 0));
+    pg->graph = G;
+    MPS_CUDA(c, cudaGraphConditionalHandleCreate(&h_out, G, 0, cudaGraphCondAssignDefault));
+    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, G, nullptr, nullptr, 0, mode));
+    k_start64<<<gs, kBT, 0, s>>>(sv, x, c->cg_r, c->cg_d, c->cg, tol2, c->cg_xhl, h_out);
+    MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+    if (!(n_start = only_node(G))) return MPS_EDEVICE;
+    int rc;
+    if ((rc = add_while(c, G, n_start, h_out, &n_outer, &B))) return rc;
+    MPS_CUDA(c, cudaGraphConditionalHandleCreate(&h_in, B, 0, cudaGraphCondAssignDefault));
+    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, B, nullptr, nullptr, 0, mode));
+    k_inner_init<<<gv, kBT, 0, s>>>(n, c->cg_r, c->cg_r32, c->cg_d32, c->cg_x32, c->cg, -1.0, 0,
+                                    c->partials, &c->st->counter[3], h_in);
+    MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+    if (!(n_init = only_node(B))) return MPS_EDEVICE;
+    if ((rc = add_while(c, B, n_init, h_in, &n_inner, &Bi))) return rc;
+    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, Bi, nullptr, nullptr, 0, mode));
+    if (c->prm.ppe_operator == 1)
+        k_spmv32_t<true><<<gs, kBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+    else
+        k_spmv32_t<false><<<gs, kBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+    k_xr32<<<gv, kBT, 0, s>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_q32, c->cg, c->partials,
+                              &c->st->counter[2]);
+    k_d32<<<gv, kBT, 0, s>>>(n, c->cg_r32, c->cg_d32, c->cg, h_in);
+    MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, B, &n_inner, nullptr, 1, mode));
+    k_outer_update<<<gv, kBT, 0, s>>>(n, x, c->cg_x32, -1.0, c->cg_xhl, c->cg);
+    k_resid_ff_t<<<gs, kBT, 0, s>>>(sv, x, c->cg_xhl, c->cg_r, c->cg, h_out);
+    MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+    MPS_CUDA(c, cudaGraphInstantiate(&pg->exec, G, 0));
+    pg->x = x;
+    return MPS_OK;
+}
+
+void ppe_graphs_destroy(Ctx* c) {
+    for (PpeGraph& pg : c->ppe_graph) {
+        if (pg.exec) cudaGraphExecDestroy(pg.exec);
+        if (pg.graph) cudaGraphDestroy(pg.graph);
+        pg = PpeGraph{};
+    }
+}
+
+static int mixed_graph_solve(Ctx* c, double* x, mps_report* rep, int max_total) {
+    PpeGraph* pg = nullptr;
+    for (PpeGraph& g : c->ppe_graph)
+        if (g.exec && g.x == x) pg = &g;
+    if (!pg) {
+        for (PpeGraph& g : c->ppe_graph)
+            if (!g.exec) { pg = &g; break; }
+        if (!pg) return MPS_EDEVICE;   // a third buffer: not expected
+        int rc = build_mixed_graph(c, x, pg);
+        if (rc) {
+            if (pg->graph) cudaGraphDestroy(pg->graph);
+            *pg = PpeGraph{};
+            return rc;
+        }
+    }
+    CgScalars init{};
+    init.max_iters = max_total;
+    init.max_total = max_total;
+    init.max_outer = c->prm.max_outer > 0 ? c->prm.max_outer : 30;
+    init.inner_tol = c->prm.inner_tol;
+    MPS_CUDA(c, cudaMemcpyAsync(c->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream));
+    MPS_CUDA(c, cudaGraphLaunch(pg->exec, c->stream));
+    int rc;
+    if ((rc = read_scalars(c))) return rc;
+    const CgScalars& h = *c->cg_host;
+    // kernels the graph ran: start, per sweep init + update + residual, per inner iteration 3
+    c->launches += 1 + 3 * (int64_t)h.outer + 3 * (int64_t)h.total;
+    const double rel = h.bb > 0.0 ? sqrt(h.rr / h.bb) : 0.0;
+    rep->cg_iters = h.total;
+    rep->cg_outer = h.outer;
+    rep->cg_resid = rel;
+    c->scene_resid[0] = rel;
+    c->last_cg_iters = std::max(4, h.total / std::max(h.outer, 1));
+    if (!(h.rr <= h.ostop2)) return MPS_ECG_NOCONV;
+    return MPS_OK;
+}
+
 // A x = b; primary: the step's own PPE (x = p, b = the source), whose iteration count and
 // residual the context keeps for the next solve and for mps_scene_residuals
 static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool primary) {
@@ -574,9 +744,11 @@ static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool prima
     const int max_total = c->prm.cg_max_iter > 0 ? c->prm.cg_max_iter : (int)std::min<int64_t>(10 * c->n, 1 << 30);
     const int gs = row_grid(c), gv = vec_grid(c);
     int rc;
+    if (primary && c->prm.precision == 1 && c->n_scenes == 1 && c->prm.ppe_host_loop == 0)
+        return mixed_graph_solve(c, x, rep, max_total);
     if ((rc = set_cg_limits(c, max_total))) return rc;
     // x = 0, r = b, d = b, rho = |b|^2, stop2 = tol^2 |b|^2
-    k_start64<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), x, c->cg_r, c->cg_d, c->cg, tol2, c->cg_xhl);
+    k_start64<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), x, c->cg_r, c->cg_d, c->cg, tol2, c->cg_xhl, 0);
     c->launches += 1;
     if ((rc = read_scalars(c))) return rc;
     const double bnorm2 = c->cg_host->rr;
@@ -649,7 +821,7 @@ static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool prima
             c->launches += 3;
             k_inner_init<<<gv, kBT, 0, c->stream>>>(n, c->cg_r, c->cg_r32, c->cg_d32, c->cg_x32, c->cg,
                                                     itol_k * itol_k, max_total - total_iters,
-                                                    c->partials, &c->st->counter[3]);
+                                                    c->partials, &c->st->counter[3], 0);
             for (;;) {
                 cg32_chunk(c, chunk, b);
                 if ((rc = read_scalars(c))) return rc;
@@ -657,8 +829,8 @@ static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool prima
                 chunk = std::max(4, chunk / 2);
             }
             total_iters += c->cg_host->iters;
-            k_outer_update<<<gv, kBT, 0, c->stream>>>(n, x, c->cg_x32, rr, c->cg_xhl);
-            k_resid_ff_t<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), x, c->cg_xhl, c->cg_r, c->cg);
+            k_outer_update<<<gv, kBT, 0, c->stream>>>(n, x, c->cg_x32, rr, c->cg_xhl, c->cg);
+            k_resid_ff_t<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), x, c->cg_xhl, c->cg_r, c->cg, 0);
             if ((rc = read_scalars(c))) return rc;
             rr = c->cg_host->rr;
             outer++;

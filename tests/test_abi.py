@@ -62,6 +62,7 @@ int main(void) {
   P(mps_params, box_max) P(mps_params, inner_tol) P(mps_params, ppe_operator) P(mps_params, stream)
   P(mps_params, alloc) P(mps_params, release) P(mps_params, alloc_user) P(mps_params, list_every)
   P(mps_params, gather_block) P(mps_params, kernel) P(mps_params, source_term)
+  P(mps_params, ppe_host_loop)
   P(mps_report, list_gathered)
   P(mps_report, cg_resid) P(mps_report, n_surface) P(mps_report, max_disp) P(mps_report, lambda)
   P(mps_report, steps_done) P(mps_report, cand_tests) P(mps_report, pairs_pnd)
