@@ -62,6 +62,10 @@ FLOPS_PER_PPE_PAIR = 133.0
 FLOPS_PER_PND_PAIR = 62.0
 # FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one FP32 SpMV launch per PPE coefficient, from the ncu
+# capture in profiles/kernels_dam_break_3d_227k_mixed.md (259.8 + 3.7 MB for 25.19 M
+# coefficients on the 227,136-particle case); traffic scales with the coefficients
+SPMV_TRAFFIC_PER_COEF = (259.8e6 + 3.7e6) / 25.19e6
 
 
 def parse():
@@ -89,6 +93,8 @@ def parse():
     ap.add_argument("--ensemble-steps", type=int, default=20,
                     help="timed steps of the batched ensemble (0: skip)")
     ap.add_argument("--ensemble-scenes", type=int, default=256)
+    ap.add_argument("--ppe-host-loop", action="store_true",
+                    help="drive the mixed PPE solve from the host (profiling: identical results)")
     ap.add_argument("--adjoint-steps", type=int, default=20,
                     help="forward and reverse steps timed on the 3D sloshing tank (0: skip)")
     return ap.parse_args()
@@ -257,7 +263,9 @@ def run_gb300(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
-    common = dict(dt=5e-5, cg_tol=1e-8)
+    # --ppe-host-loop: the mixed PPE solve driven from the host instead of one CUDA graph
+    # (identical results; ncu cannot profile the kernels of a graph with conditional nodes)
+    common = dict(dt=5e-5, cg_tol=1e-8, ppe_host_loop=1 if args.ppe_host_loop else 0)
 
     def timed_steps(sim, k, profile=False):
         if profile:
@@ -368,11 +376,19 @@ def run_gb300(args):
         simo.step(args.warmup)
         barrier()
         ms, its, prof = timed_steps(simo, args.steps, profile=True)
+        # the PPE's SpMV (and the float-float residual) timed alone, outside the graph
+        kern = {}
+        for name, which in (("spmv32", mps.KERNEL_SPMV32), ("resid_ff", mps.KERNEL_RESID_FF),
+                            ("spmv64", mps.KERNEL_SPMV64)):
+            if (which == mps.KERNEL_SPMV64) == (prec == 0):
+                kms, kby = mps.mps_time_kernel(simo.h, which, 5)
+                kern[name] = {"ms_per_launch": kms, "bytes_per_launch": kby,
+                              "gbs": kby / (kms * 1e-3) / 1e9}
         simo.close()
         if rank == 0:
             print(json.dumps({"only": args.only, "particles": n, "ms_per_step": ms / args.steps,
-                              "value": n * args.steps / (ms * 1e-3), "cg": its, "profile": prof}),
-                  flush=True)
+                              "value": n * args.steps / (ms * 1e-3), "cg": its, "profile": prof,
+                              "kernels": kern}), flush=True)
         return
 
     # ---- mixed (headline)
@@ -384,6 +400,13 @@ def run_gb300(args):
     barrier()
     clk = clocks.stop()
     ms_mixed = max_over_ranks(ms_mixed)
+    # The dominant kernel of the step is the FP32 SpMV of the inner CG (the launch list's
+    # largest share).  The solve launches it inside the graph's conditional loops, where CUDA
+    # events cannot bracket single launches, so it is timed alone right after the timed
+    # region, on the system of the last timed step, with CUDA events on the library's stream
+    # (coefficients 441 MB, larger than L2); likewise the float-float outer residual.
+    spmv_ms, spmv_bytes = mps.mps_time_kernel(sim.h, mps.KERNEL_SPMV32, 20)
+    resid_ms, resid_bytes = mps.mps_time_kernel(sim.h, mps.KERNEL_RESID_FF, 10)
     sim.close()
 
     # ---- plain FP64 on the same scene
@@ -513,12 +536,23 @@ def run_gb300(args):
     else:
         flops = FLOPS_PER_PPE_PAIR * ppe_pairs + FLOPS_PER_PND_PAIR * pnd_pairs
     achieved = flops / (per_call[top] * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": single[top], "achieved": achieved,
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                "traffic": None, "work": {"cand_tests": tests, "pairs_ppe": ppe_pairs,
-                                          "pairs_pnd": pnd_pairs},
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "stage_ms_per_step": {k: per_call[k] for k in per_call}}
+    roofline_build = {"bound": "alu", "kernel": single[top], "achieved": achieved,
+                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                      "work": {"cand_tests": tests, "pairs_ppe": ppe_pairs, "pairs_pnd": pnd_pairs},
+                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                      "stage_ms_per_step": {k: per_call[k] for k in per_call}}
+    spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_spmv32_t (FP32 SpMV of the inner CG)",
+                "achieved": spmv_gbs, "peak": hbm, "unit": "GB/s", "frac": spmv_gbs / hbm,
+                "traffic": SPMV_TRAFFIC_PER_COEF * ppe_pairs if SPMV_TRAFFIC_PER_COEF else None,
+                "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms,
+                "launches_per_step": inner,
+                "timing": "timed alone after the timed region (CUDA events, 20 launches)",
+                "peak_source": hbm_src + " (burst copy)",
+                "resid_ff": {"achieved": resid_bytes / (resid_ms * 1e-3) / 1e9,
+                             "frac": resid_bytes / (resid_ms * 1e-3) / 1e9 / hbm,
+                             "bytes_per_launch": resid_bytes, "ms_per_launch": resid_ms}}
     step_bytes = n * (STEP_BYTES_FIXED[1] + 57.0 * inner + 65.0 * (outer + 1))
     step_hbm = {"bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms_mixed / args.steps * 1e-3) / 1e9,
                 "peak_gbs": hbm, "frac": step_bytes / (ms_mixed / args.steps * 1e-3) / 1e9 / hbm,
@@ -555,6 +589,7 @@ def run_gb300(args):
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(prof["launches"]),
         "roofline": roofline,
+        "roofline_build": roofline_build,
         "step_hbm": step_hbm,
         "cpu_baseline": cpu,
         "clocks": clk,

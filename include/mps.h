@@ -312,6 +312,25 @@ int mps_set_profiling(mps_ctx* ctx, int32_t on);
  * launches: kernels launched since the last reset.  Any pointer may be NULL. */
 int mps_get_profile(mps_ctx* ctx, double* stage_ms, int64_t* stage_calls, int64_t* launches);
 
+/* Kernel timing (a tool of this library): after a step or solve of a PPE context, launch
+ * one kernel of the PPE solve `repeats` times on the system that step built (CUDA events
+ * on the context's stream, one launch at a time) and report its mean duration [ms] and its
+ * algorithmic bytes per launch (per row of the system the stored coefficients and the
+ * row's own vector entries, per other row its diagonal read and output write; gathers of
+ * neighbour entries, which stay in cache, are not counted).  Only scratch vectors change:
+ * the state, p, n* and flags stay as the step left them.
+ *   MPS_KERNEL_SPMV32   the FP32 SpMV of the mixed inner CG (column + FP32 value: 8 B per
+ *                       coefficient);
+ *   MPS_KERNEL_RESID_FF the mixed float-float residual (12 B per coefficient);
+ *   MPS_KERNEL_SPMV64   the FP64 SpMV (12 B per coefficient).
+ * Errors: MPS_EINVAL (equation-of-state context, repeats < 1, or a kernel of the other
+ * precision), MPS_EDEVICE. */
+#define MPS_KERNEL_SPMV32 0
+#define MPS_KERNEL_RESID_FF 1
+#define MPS_KERNEL_SPMV64 2
+int mps_time_kernel(mps_ctx* ctx, int32_t which, int32_t repeats, double* ms_per_launch,
+                    double* bytes_per_launch);
+
 /* Solve A x = b by FP64 conjugate gradients WITHOUT ALLOCATING any memory.
  * No counterpart in the paper: this is an entry point for callers that are not allowed to
  * call cudaMalloc -- for instance a host application whose device memory is entirely

@@ -1049,6 +1049,14 @@ int mps_set_profiling(mps_ctx* c, int32_t on) {
     return MPS_OK;
 }
 
+int mps_time_kernel(mps_ctx* c, int32_t which, int32_t repeats, double* ms_per_launch,
+                    double* bytes_per_launch) {
+    if (!c || !ms_per_launch || !bytes_per_launch) return MPS_EINVAL;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    return ppe_time_kernel(c, which, repeats, ms_per_launch, bytes_per_launch);
+}
+
 int mps_get_profile(mps_ctx* c, double* stage_ms, int64_t* stage_calls, int64_t* launches) {
     if (!c) return MPS_EINVAL;
     for (int s = 0; s < MPS_NSTAGES; s++) {

@@ -163,6 +163,7 @@ int ppe_solve(Ctx* c, mps_report* rep);
 // context's record of the step's PPE solve (iteration heuristic, residual) untouched
 int ppe_solve_rhs(Ctx* c, double* x, const double* b, mps_report* rep);
 void ppe_graphs_destroy(Ctx* c);
+int ppe_time_kernel(Ctx* c, int which, int repeats, double* ms, double* bytes);
 
 // ---------------------------------------------------------------- adjoint.cu
 void launch_adj_mark(Ctx* c);

@@ -736,6 +736,72 @@ static int mixed_graph_solve(Ctx* c, double* x, mps_report* rep, int max_total) 
     return MPS_OK;
 }
 
+// ---------------------------------------------------------------- kernel timing
+// Algorithmic bytes of one launch of the PPE kernels on the current system, summed on the
+// device (integers: exact): per row of the system (diag != 0) the stored coefficients and
+// the row's own vector entries; per other row the diagonal read and the output write.
+__global__ void k_ppe_bytes(int n, const int32_t* cnt, const double* diag, int which,
+                            unsigned long long* out) {
+    unsigned long long b = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool row = diag[i] != 0.0;
+        const unsigned long long k = row ? (unsigned long long)cnt[i] : 0ull;
+        if (which == 0) b += row ? 8ull * k + 12ull : 8ull;        // col + v32; diag32, d_i, q_i
+        else if (which == 1) b += row ? 12ull * k + 32ull : 16ull; // col + v32 + vlo; diag, x_i, b_i, r_i
+        else b += row ? 12ull * k + 24ull : 16ull;                 // col + v64; diag, d_i, q_i
+    }
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(out, b);
+}
+
+int ppe_time_kernel(Ctx* c, int which, int repeats, double* ms, double* bytes) {
+    const mps_params& P = c->prm;
+    if (P.pressure_mode != 0 || repeats < 1 || which < 0 || which > 2) return MPS_EINVAL;
+    if ((which < 2) != (P.precision == 1)) return MPS_EINVAL;
+    const int n = (int)c->n;
+    const int gs = row_grid(c);
+    const SellView sv = sell_view(c, c->bvec);
+    cudaStream_t s = c->stream;
+    unsigned long long* d_b = (unsigned long long*)c->partials;   // scratch: one word
+    MPS_CUDA(c, cudaMemsetAsync(d_b, 0, sizeof(unsigned long long), s));
+    k_ppe_bytes<<<c->sms * 4, 256, 0, s>>>(n, c->nb_lap_cnt, c->diag, which, d_b);
+    unsigned long long hb = 0;
+    MPS_CUDA(c, cudaMemcpyAsync(&hb, d_b, sizeof hb, cudaMemcpyDeviceToHost, s));
+    cudaEvent_t e0, e1;
+    MPS_CUDA(c, cudaEventCreate(&e0));
+    MPS_CUDA(c, cudaEventCreate(&e1));
+    const float coef = (float)c->coef_ppe, re_f = (float)c->r_lap.re;
+    float total = 0.f;
+    for (int k = 0; k < repeats; k++) {
+        // the kernels skip their work once a solve is done: clear the flag (scratch only;
+        // the step's results are not touched)
+        MPS_CUDA(c, cudaMemsetAsync(&c->cg->done, 0, sizeof(int), s));
+        cudaEventRecord(e0, s);
+        if (which == 0) {
+            if (P.ppe_operator == 1)
+                k_spmv32_t<true><<<gs, kBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+            else
+                k_spmv32_t<false><<<gs, kBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+        } else if (which == 1) {
+            k_resid_ff_t<<<gs, kBT, 0, s>>>(sv, c->p, c->cg_xhl, c->cg_r, c->cg, 0);
+        } else {
+            k_spmv64_t<<<gs, kBT, 0, s>>>(sv, c->cg_d, c->cg_q, c->cg);
+        }
+        cudaEventRecord(e1, s);
+        MPS_CUDA(c, cudaEventSynchronize(e1));
+        float m = 0.f;
+        cudaEventElapsedTime(&m, e0, e1);
+        total += m;
+    }
+    c->launches += repeats + 1;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    MPS_CUDA(c, cudaGetLastError());
+    *ms = total / repeats;
+    *bytes = (double)hb;
+    return MPS_OK;
+}
+
 // A x = b; primary: the step's own PPE (x = p, b = the source), whose iteration count and
 // residual the context keeps for the next solve and for mps_scene_residuals
 static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool primary) {

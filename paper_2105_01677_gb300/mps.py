@@ -73,7 +73,8 @@ EXPORTS = ("mps_params_default", "mps_create", "mps_step", "mps_solve_ppe", "mps
            "mps_write_state", "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants",
            "mps_set_profiling", "mps_get_profile", "mps_ppe_cg_noalloc", "mps_destroy",
            "mps_strerror", "mps_set_fluid_properties", "mps_create_ensemble",
-           "mps_scene_residuals", "mps_autotune", "mps_set_gravity", "mps_step_vjp")
+           "mps_scene_residuals", "mps_autotune", "mps_set_gravity", "mps_step_vjp",
+           "mps_time_kernel")
 NOALLOC_MAX_ROWS = 262144
 STAGES = ("bucket", "gather", "predict", "build", "ppe", "update")
 
@@ -106,6 +107,7 @@ def lib(build_if_missing: bool = False):
     L.mps_write_state.argtypes = [C.c_void_p, d, d, i8]
     L.mps_set_fluid_properties.argtypes = [C.c_void_p, d, d]
     L.mps_set_gravity.argtypes = [C.c_void_p, d]
+    L.mps_time_kernel.argtypes = [C.c_void_p, C.c_int32, C.c_int32, d, d]
     L.mps_step_vjp.argtypes = [C.c_void_p, d, d, d, d, d, C.POINTER(mps_vjp_report)]
     L.mps_create_ensemble.argtypes = [d, d, i8, C.POINTER(C.c_int32), C.c_int64,
                                       C.POINTER(mps_params), C.POINTER(mps_scene), C.c_int32,
@@ -129,7 +131,7 @@ def lib(build_if_missing: bool = False):
               "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants", "mps_set_profiling",
               "mps_get_profile", "mps_ppe_cg_noalloc", "mps_set_fluid_properties",
               "mps_create_ensemble", "mps_scene_residuals", "mps_autotune", "mps_set_gravity",
-              "mps_step_vjp"):
+              "mps_step_vjp", "mps_time_kernel"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -355,6 +357,19 @@ def mps_step_vjp(h, g_pos, g_vel, check: bool = True):
     if check:
         _check(rc, "mps_step_vjp")
     return rc, out_r, out_u, out_g, rep.as_dict()
+
+
+KERNEL_SPMV32, KERNEL_RESID_FF, KERNEL_SPMV64 = 0, 1, 2
+
+
+def mps_time_kernel(h, which: int, repeats: int = 10):
+    """(mean ms per launch, algorithmic bytes per launch) of one PPE kernel on the system
+    of the last step."""
+    ms = C.c_double()
+    by = C.c_double()
+    _check(lib().mps_time_kernel(h, int(which), int(repeats), C.byref(ms), C.byref(by)),
+           "mps_time_kernel")
+    return ms.value, by.value
 
 
 def mps_debug_cells(h, n: int):

@@ -65,3 +65,29 @@ def test_graph_solve_iteration_cap_and_recovery():
     reps, st = _run(sc, 2, 0, cg_tol=1e-8)
     assert all(r["cg_resid"] <= 1e-8 for r in reps)
     assert np.all(np.isfinite(st["p"]))
+
+
+def test_time_kernel_leaves_the_state_and_counts_bytes():
+    from paper_2105_01677_gb300 import mps
+    sc = small_3d(seed=3)
+    sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
+                         **gpu_params(sc, precision=1, dt=5e-5))
+    try:
+        rc, rep = sim.step(1)
+        before = sim.read()
+        ms, by = mps.mps_time_kernel(sim.h, mps.KERNEL_SPMV32, 3)
+        ms2, by2 = mps.mps_time_kernel(sim.h, mps.KERNEL_RESID_FF, 2)
+        after = sim.read()
+        with pytest.raises(mps.MPSError):
+            mps.mps_time_kernel(sim.h, mps.KERNEL_SPMV64, 1)   # FP64 kernel of a mixed context
+        sim.step(1)                                           # still steps afterwards
+    finally:
+        sim.close()
+    for k in before:
+        assert np.array_equal(before[k], after[k]), k
+    # 8 bytes per stored coefficient of the system's rows (free-surface rows, whose
+    # coefficients are stored but not in the system, are a large share of this small scene),
+    # 12 for the float-float residual
+    assert ms > 0 and ms2 > 0
+    assert 8 * rep["pairs_ppe"] * 0.4 <= by <= 8 * rep["pairs_ppe"] + 12 * sc.n
+    assert abs(by2 / by - 1.5) < 0.1
