@@ -945,6 +945,7 @@ int mps_set_fluid_properties(mps_ctx* c, const double* rho, const double* nu) {
     launch_gather_props(c);
     MPS_CUDA(c, cudaGetLastError());
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    bucket_graphs_destroy(c);   // the captured builds gather the properties that were set
     return MPS_OK;
 }
 
@@ -1075,6 +1076,7 @@ void mps_destroy(mps_ctx* c) {
         for (int k = 0; k < 2 * MPS_NSTAGES; k++)
             if (c->ev[k]) cudaEventDestroy(c->ev[k]);
         ppe_graphs_destroy(c);
+        bucket_graphs_destroy(c);
         free_all(c);
         if (c->st_host) cudaFreeHost(c->st_host);
         if (c->cg_host) cudaFreeHost(c->cg_host);

@@ -11,6 +11,8 @@
 //   3. per-cell counts and their exclusive scan give cell_start (a cell's particles are
 //      contiguous in Morton order); occupied cells are collected for the gathers;
 //   4. every per-particle array is permuted into the new order (slot s <- old slot perm[s]).
+#include <cstring>
+
 #include "mps_internal.cuh"
 
 namespace mps {
@@ -205,7 +207,90 @@ void launch_cell_keys_only(Ctx* c, uint32_t* out_key) {
     c->launches += 1;
 }
 
+static int bucket_launches(Ctx* c, bool mutate);
+
+// The bucket build is ~25 short dependent kernels whose launch gaps cost more than their
+// work, so the stepping path replays it as one CUDA graph.  Every build swaps the state with
+// its alternate buffers (and the radix sort's keys and permutation with theirs when it
+// takes an odd number of passes), so there are two graphs, keyed by the position buffer
+// the build starts from; each remembers the buffer assignment its build leaves behind.
+namespace {
+struct BucketPtrs {
+    uint32_t *key, *key_alt;
+    int32_t *perm, *perm_alt;
+    double4 *pos, *pos_alt, *vel, *vel_alt;
+    int8_t *type, *type_alt;
+    int32_t *id, *id_alt;
+    double *p, *p_alt;
+};
+BucketPtrs save_ptrs(const Ctx* c) {
+    return {c->key, c->key_alt, c->perm, c->perm_alt, c->pos, c->pos_alt, c->vel, c->vel_alt,
+            c->type, c->type_alt, c->id, c->id_alt, c->p, c->p_alt};
+}
+void load_ptrs(Ctx* c, const BucketPtrs& b) {
+    c->key = b.key; c->key_alt = b.key_alt; c->perm = b.perm; c->perm_alt = b.perm_alt;
+    c->pos = b.pos; c->pos_alt = b.pos_alt; c->vel = b.vel; c->vel_alt = b.vel_alt;
+    c->type = b.type; c->type_alt = b.type_alt; c->id = b.id; c->id_alt = b.id_alt;
+    c->p = b.p; c->p_alt = b.p_alt;
+}
+}  // namespace
+
 int bucket_build(Ctx* c, bool mutate) {
+    if (!mutate) return bucket_launches(c, false);
+    BucketGraph* bg = nullptr;
+    for (BucketGraph& g : c->bucket_graph)
+        if (g.exec && g.pos == c->pos) bg = &g;
+    if (!bg) {
+        for (BucketGraph& g : c->bucket_graph)
+            if (!g.exec) { bg = &g; break; }
+        if (!bg) return bucket_launches(c, true);   // not expected: more than two parities
+        const double4* start = c->pos;
+        const BucketPtrs before = save_ptrs(c);
+        const int64_t l0 = c->launches;
+        MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+        MPS_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
+        int rc = bucket_launches(c, true);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            load_ptrs(c, before);
+            c->launches = l0;
+            return rc ? rc : cuda_fail(c, e, "bucket graph capture");
+        }
+        e = cudaGraphInstantiate(&bg->exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            load_ptrs(c, before);
+            c->launches = l0;
+            return cuda_fail(c, e, "bucket graph instantiate");
+        }
+        bg->graph = g;
+        bg->pos = start;
+        bg->launches = c->launches - l0;
+        BucketPtrs after = save_ptrs(c);
+        static_assert(sizeof(BucketPtrs) <= sizeof(bg->after), "pointer record too small");
+        std::memcpy(bg->after, &after, sizeof after);
+        c->launches = l0;   // counted at the replay below
+        load_ptrs(c, before);
+    }
+    MPS_CUDA(c, cudaGraphLaunch(bg->exec, c->stream));
+    BucketPtrs after;
+    std::memcpy(&after, bg->after, sizeof after);
+    load_ptrs(c, after);
+    c->launches += bg->launches;
+    return MPS_OK;
+}
+
+void bucket_graphs_destroy(Ctx* c) {
+    for (BucketGraph& g : c->bucket_graph) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        g = BucketGraph{};
+    }
+}
+
+static int bucket_launches(Ctx* c, bool mutate) {
     const int n = (int)c->n;
     cudaStream_t s = c->stream;
     const int nb1 = (n + kBT - 1) / kBT;

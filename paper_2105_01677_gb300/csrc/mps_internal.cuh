@@ -138,6 +138,7 @@ struct Ctx;
 
 // ---------------------------------------------------------------- bucket.cu
 int bucket_build(Ctx* c, bool mutate);            // keys, sort, cell table, permute
+void bucket_graphs_destroy(Ctx* c);
 void launch_cell_keys_only(Ctx* c, uint32_t* out_key);
 
 // ---------------------------------------------------------------- scan.cu
@@ -201,6 +202,16 @@ struct PpeGraph {
     cudaGraphExec_t exec = nullptr;
 };
 
+// The stepping bucket build captured as a CUDA graph, one per starting state buffer, with
+// the buffer assignment it leaves behind (a record of pointers, see bucket.cu).
+struct BucketGraph {
+    const double4* pos = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+    void* after[16] = {};
+};
+
 // Work arrays of the reverse step (slot order unless noted), allocated on first use.
 struct AdjBuffers {
     bool ready = false;
@@ -250,6 +261,7 @@ struct Ctx {
     bool vjp = false;
     AdjBuffers adj;
     PpeGraph ppe_graph[2];
+    BucketGraph bucket_graph[2];
 
     // state (sorted order) and double buffers
     double4 *pos, *vel, *pos_alt, *vel_alt;
