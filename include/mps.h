@@ -227,6 +227,17 @@ typedef struct {
 int mps_step_vjp(mps_ctx* ctx, const double* g_pos, const double* g_vel, double* out_pos,
                  double* out_vel, double* out_g, mps_vjp_report* report);
 
+/* Device-memory variants: the same calls with the caller's particle arrays (every pointer
+ * argument except out_g and report) in device memory of the context's device, in the same
+ * original-order layouts; no host copies are made.  Work runs on the context's stream and
+ * the calls are synchronous at return like the host ones.  For callers whose data already
+ * lives on the GPU (PyTorch tensors, a rollout's checkpoints). */
+int mps_read_state_device(mps_ctx* ctx, double* pos, double* vel, double* p, double* n_star,
+                          uint8_t* flags, int8_t* types);
+int mps_write_state_device(mps_ctx* ctx, const double* pos, const double* vel, const int8_t* types);
+int mps_step_vjp_device(mps_ctx* ctx, const double* g_pos, const double* g_vel, double* out_pos,
+                        double* out_vel, double* out_g, mps_vjp_report* report);
+
 /* Two-phase (multi-density, multi-viscosity) flow of Sec. 3.2.1: a density rho_i [kg/m^3]
  * and a kinematic viscosity nu_i [m^2/s] per particle, n doubles each in the original
  * particle order (copied; the caller keeps its arrays).  NULL leaves that property uniform

@@ -6,8 +6,11 @@ trajectory checkpointed every ``checkpoint_every`` steps and recomputed segment 
 The inputs are the initial positions and velocities (n x dim) and the external
 acceleration of every step (T x 3): a time-dependent body force such as the inertial
 acceleration of a shaken tank in its own frame.  Gradients flow to all three.  Particle
-kinds are those of the simulation's state when the rollout starts.  Argument marshalling
-only: the steps and their reverse run in the library's kernels.
+kinds are those of the simulation's state when the rollout starts.
+
+With CUDA tensors the states, checkpoints and cotangents stay in device memory (the
+library's device-memory calls); with CPU tensors they pass through host memory.  Argument
+marshalling only: the steps and their reverse run in the library's kernels.
 """
 from __future__ import annotations
 
@@ -19,9 +22,78 @@ def _torch():
     return torch
 
 
-def _state(sim):
-    st = sim.read(want=("pos", "vel", "types"))
-    return st["pos"].copy(), st["vel"].copy(), st["types"].copy()
+class _HostIO:
+    """State and cotangents as numpy arrays through the host calls."""
+
+    def __init__(self, sim):
+        self.sim = sim
+
+    def types(self):
+        return self.sim.read(want=("types",))["types"].copy()
+
+    def from_tensor(self, t):
+        return t.detach().to("cpu", _torch().float64).numpy().copy()
+
+    def read(self):
+        st = self.sim.read(want=("pos", "vel", "types"))
+        return st["pos"].copy(), st["vel"].copy(), st["types"].copy()
+
+    def write(self, x, u, types):
+        self.sim.write(x, u, types)
+
+    def vjp(self, gr, gu):
+        _, r, u, g, _ = self.sim.step_vjp(gr, gu)
+        return r, u, g
+
+    def zeros_like(self, x):
+        return np.zeros_like(x)
+
+    def to_tensor(self, a, device):
+        return _torch().from_numpy(a).to(device)
+
+
+class _DeviceIO:
+    """State and cotangents as CUDA tensors through the device-memory calls."""
+
+    def __init__(self, sim, device):
+        self.sim = sim
+        self.device = device
+        torch = _torch()
+        self.shape = (sim.n, sim.dim)
+        self._f64 = dict(dtype=torch.float64, device=device)
+
+    def types(self):
+        torch = _torch()
+        t = torch.empty(self.sim.n, dtype=torch.int8, device=self.device)
+        self.sim.read_device(types=t)
+        return t
+
+    def from_tensor(self, t):
+        return t.detach().to(self.device, _torch().float64).contiguous().clone()
+
+    def read(self):
+        torch = _torch()
+        x = torch.empty(self.shape, **self._f64)
+        u = torch.empty(self.shape, **self._f64)
+        t = torch.empty(self.sim.n, dtype=torch.int8, device=self.device)
+        self.sim.read_device(pos=x, vel=u, types=t)
+        return x, u, t
+
+    def write(self, x, u, types):
+        self.sim.write_device(x, u, types)
+
+    def vjp(self, gr, gu):
+        torch = _torch()
+        r = torch.empty_like(gr)
+        u = torch.empty_like(gu)
+        _, g, _ = self.sim.step_vjp_device(gr, gu, r, u)
+        return r, u, g
+
+    def zeros_like(self, x):
+        return _torch().zeros_like(x)
+
+    def to_tensor(self, a, device):
+        return a if a.device == device else a.to(device)
 
 
 def _make_function():
@@ -31,51 +103,50 @@ def _make_function():
         @staticmethod
         def forward(ctx, pos, vel, forcing, sim, checkpoint_every):
             K = max(1, int(checkpoint_every))
+            io = _DeviceIO(sim, pos.device) if pos.is_cuda else _HostIO(sim)
             f = forcing.detach().to("cpu", torch.float64).numpy().copy()
-            types = sim.read(want=("types",))["types"].copy()
-            x = pos.detach().to("cpu", torch.float64).numpy()
-            u = vel.detach().to("cpu", torch.float64).numpy()
+            types = io.types()
+            x, u = io.from_tensor(pos), io.from_tensor(vel)
             ckpts = []
             for t in range(f.shape[0]):
                 if t % K == 0:
                     # every segment starts from a state written afresh, so that its
                     # recomputation in backward repeats it bit for bit
                     if t > 0:
-                        x, u, types = _state(sim)
-                    ckpts.append((x.copy(), u.copy(), types.copy()))
-                    sim.write(x, u, types)
+                        x, u, types = io.read()
+                    ckpts.append((x, u, types))
+                    io.write(x, u, types)
                 sim.set_gravity(f[t])
                 sim.step(1)
-            xT, uT, _ = _state(sim)
-            ctx.sim, ctx.K, ctx.ckpts, ctx.f = sim, K, ckpts, f
+            xT, uT, _ = io.read()
+            ctx.sim, ctx.K, ctx.ckpts, ctx.f, ctx.io = sim, K, ckpts, f, io
             ctx.dev = pos.device
-            return (torch.from_numpy(xT).to(pos.device), torch.from_numpy(uT).to(pos.device))
+            return io.to_tensor(xT, pos.device), io.to_tensor(uT, pos.device)
 
         @staticmethod
         def backward(ctx, g_pos, g_vel):
-            sim, K, f = ctx.sim, ctx.K, ctx.f
+            sim, K, f, io = ctx.sim, ctx.K, ctx.f, ctx.io
             n_steps = f.shape[0]
             x0 = ctx.ckpts[0][0]
-            gr = np.zeros_like(x0) if g_pos is None else g_pos.detach().to("cpu", torch.float64).numpy().copy()
-            gu = np.zeros_like(x0) if g_vel is None else g_vel.detach().to("cpu", torch.float64).numpy().copy()
+            gr = io.zeros_like(x0) if g_pos is None else io.from_tensor(g_pos)
+            gu = io.zeros_like(x0) if g_vel is None else io.from_tensor(g_vel)
             gf = np.zeros_like(f)
             for s in reversed(range(len(ctx.ckpts))):
                 t0, t1 = s * K, min(n_steps, (s + 1) * K)
                 x, u, types = ctx.ckpts[s]
-                sim.write(x, u, types)
+                io.write(x, u, types)
                 states = [(x, u, types)]
                 for t in range(t0, t1 - 1):
                     sim.set_gravity(f[t])
                     sim.step(1)
-                    states.append(_state(sim))
+                    states.append(io.read())
                 for t in reversed(range(t0, t1)):
                     xs, us, ts = states[t - t0]
-                    sim.write(xs, us, ts)
+                    io.write(xs, us, ts)
                     sim.set_gravity(f[t])
-                    _, gr, gu, gg, _ = sim.step_vjp(gr, gu)
-                    gf[t] = gg
+                    gr, gu, gf[t] = io.vjp(gr, gu)
             dev = ctx.dev
-            return (torch.from_numpy(gr).to(dev), torch.from_numpy(gu).to(dev),
+            return (io.to_tensor(gr, dev), io.to_tensor(gu, dev),
                     torch.from_numpy(gf).to(dev), None, None)
 
     return Rollout

@@ -367,8 +367,10 @@ int read_status(Ctx* c);
 
 // validate: check the staged values on the device first (mps_write_state); the context's
 // state is replaced only if they are finite and of known kinds
+// device: the caller's arrays are in device memory (copies device to device)
 int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* types, bool have_state,
-                 bool validate = false) {
+                 bool validate = false, bool device = false) {
+    const cudaMemcpyKind in = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     c->need_list = true;
     const size_t n = (size_t)c->n, dim = (size_t)c->dim;
     int rc_check;
@@ -381,10 +383,10 @@ int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* typ
         launch_unpermute(c, nullptr, vel ? nullptr : d_vel, nullptr, nullptr, nullptr,
                          types ? nullptr : d_t);
     }
-    MPS_CUDA(c, cudaMemcpyAsync(d_pos, pos, n * dim * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    if (vel) MPS_CUDA(c, cudaMemcpyAsync(d_vel, vel, n * dim * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    MPS_CUDA(c, cudaMemcpyAsync(d_pos, pos, n * dim * sizeof(double), in, c->stream));
+    if (vel) MPS_CUDA(c, cudaMemcpyAsync(d_vel, vel, n * dim * sizeof(double), in, c->stream));
     else if (!have_state) MPS_CUDA(c, cudaMemsetAsync(d_vel, 0, n * dim * sizeof(double), c->stream));
-    if (types) MPS_CUDA(c, cudaMemcpyAsync(d_t, types, n, cudaMemcpyHostToDevice, c->stream));
+    if (types) MPS_CUDA(c, cudaMemcpyAsync(d_t, types, n, in, c->stream));
     if (validate) {
         MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
         launch_check_stage(c, d_pos, vel ? d_vel : nullptr, types ? d_t : nullptr);
@@ -807,9 +809,12 @@ int mps_set_gravity(mps_ctx* c, const double* g) {
 }
 
 
-int mps_step_vjp(mps_ctx* c, const double* g_pos, const double* g_vel, double* out_pos,
-                 double* out_vel, double* out_g, mps_vjp_report* out) {
+namespace {
+int step_vjp(Ctx* c, const double* g_pos, const double* g_vel, double* out_pos, double* out_vel,
+             double* out_g, mps_vjp_report* out, bool device) {
     if (!c || !g_pos || !g_vel || !out_pos || !out_vel) return MPS_EINVAL;
+    const cudaMemcpyKind in = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind back = device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const mps_params& P = c->prm;
     if (c->n_scenes > 1 || P.kernel != 0 || P.gradient_form != 0 || P.source_term != 0)
         return MPS_EINVAL;
@@ -836,8 +841,8 @@ int mps_step_vjp(mps_ctx* c, const double* g_pos, const double* g_vel, double* o
     }
     double* d_a = (double*)c->stage;
     double* d_b = d_a + n * dim;
-    MPS_CUDA(c, cudaMemcpyAsync(d_a, g_pos, n * dim * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    MPS_CUDA(c, cudaMemcpyAsync(d_b, g_vel, n * dim * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    MPS_CUDA(c, cudaMemcpyAsync(d_a, g_pos, n * dim * sizeof(double), in, c->stream));
+    MPS_CUDA(c, cudaMemcpyAsync(d_b, g_vel, n * dim * sizeof(double), in, c->stream));
     launch_adj_load(c, d_a, d_b);
     launch_adj_front(c);
     if (P.pressure_mode == 0) {
@@ -856,8 +861,8 @@ int mps_step_vjp(mps_ctx* c, const double* g_pos, const double* g_vel, double* o
     launch_adj_back(c, c->adj.gsum);
     launch_adj_store(c, d_a, d_b);
     MPS_CUDA(c, cudaGetLastError());
-    MPS_CUDA(c, cudaMemcpyAsync(out_pos, d_a, n * dim * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    MPS_CUDA(c, cudaMemcpyAsync(out_vel, d_b, n * dim * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaMemcpyAsync(out_pos, d_a, n * dim * sizeof(double), back, c->stream));
+    MPS_CUDA(c, cudaMemcpyAsync(out_vel, d_b, n * dim * sizeof(double), back, c->stream));
     double gs[3] = {0.0, 0.0, 0.0};
     MPS_CUDA(c, cudaMemcpyAsync(gs, c->adj.gsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -866,9 +871,21 @@ int mps_step_vjp(mps_ctx* c, const double* g_pos, const double* g_vel, double* o
     if (out) *out = vr;
     return MPS_OK;
 }
+}  // namespace
 
-int mps_read_state(mps_ctx* c, double* pos, double* vel, double* p, double* n_star,
-                   uint8_t* flags, int8_t* types) {
+int mps_step_vjp(mps_ctx* c, const double* g_pos, const double* g_vel, double* out_pos,
+                 double* out_vel, double* out_g, mps_vjp_report* out) {
+    return step_vjp(c, g_pos, g_vel, out_pos, out_vel, out_g, out, false);
+}
+
+int mps_step_vjp_device(mps_ctx* c, const double* g_pos, const double* g_vel, double* out_pos,
+                        double* out_vel, double* out_g, mps_vjp_report* out) {
+    return step_vjp(c, g_pos, g_vel, out_pos, out_vel, out_g, out, true);
+}
+
+namespace {
+int read_state(Ctx* c, double* pos, double* vel, double* p, double* n_star, uint8_t* flags,
+               int8_t* types, cudaMemcpyKind out) {
     if (!c) return MPS_EINVAL;
     DeviceGuard dg(c->prm.device);
     if (!dg.ok) return MPS_EDEVICE;
@@ -883,14 +900,25 @@ int mps_read_state(mps_ctx* c, double* pos, double* vel, double* p, double* n_st
     launch_unpermute(c, pos ? d_pos : nullptr, vel ? d_vel : nullptr, p ? d_p : nullptr,
                      n_star ? d_n : nullptr, flags ? d_f : nullptr, types ? d_t : nullptr);
     MPS_CUDA(c, cudaGetLastError());
-    if (pos) MPS_CUDA(c, cudaMemcpyAsync(pos, d_pos, n * dim * 8, cudaMemcpyDeviceToHost, c->stream));
-    if (vel) MPS_CUDA(c, cudaMemcpyAsync(vel, d_vel, n * dim * 8, cudaMemcpyDeviceToHost, c->stream));
-    if (p) MPS_CUDA(c, cudaMemcpyAsync(p, d_p, n * 8, cudaMemcpyDeviceToHost, c->stream));
-    if (n_star) MPS_CUDA(c, cudaMemcpyAsync(n_star, d_n, n * 8, cudaMemcpyDeviceToHost, c->stream));
-    if (flags) MPS_CUDA(c, cudaMemcpyAsync(flags, d_f, n, cudaMemcpyDeviceToHost, c->stream));
-    if (types) MPS_CUDA(c, cudaMemcpyAsync(types, d_t, n, cudaMemcpyDeviceToHost, c->stream));
+    if (pos) MPS_CUDA(c, cudaMemcpyAsync(pos, d_pos, n * dim * 8, out, c->stream));
+    if (vel) MPS_CUDA(c, cudaMemcpyAsync(vel, d_vel, n * dim * 8, out, c->stream));
+    if (p) MPS_CUDA(c, cudaMemcpyAsync(p, d_p, n * 8, out, c->stream));
+    if (n_star) MPS_CUDA(c, cudaMemcpyAsync(n_star, d_n, n * 8, out, c->stream));
+    if (flags) MPS_CUDA(c, cudaMemcpyAsync(flags, d_f, n, out, c->stream));
+    if (types) MPS_CUDA(c, cudaMemcpyAsync(types, d_t, n, out, c->stream));
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
     return MPS_OK;
+}
+}  // namespace
+
+int mps_read_state(mps_ctx* c, double* pos, double* vel, double* p, double* n_star,
+                   uint8_t* flags, int8_t* types) {
+    return read_state(c, pos, vel, p, n_star, flags, types, cudaMemcpyDeviceToHost);
+}
+
+int mps_read_state_device(mps_ctx* c, double* pos, double* vel, double* p, double* n_star,
+                          uint8_t* flags, int8_t* types) {
+    return read_state(c, pos, vel, p, n_star, flags, types, cudaMemcpyDeviceToDevice);
 }
 
 int mps_write_state(mps_ctx* c, const double* pos, const double* vel, const int8_t* types) {
@@ -899,6 +927,13 @@ int mps_write_state(mps_ctx* c, const double* pos, const double* vel, const int8
     if (!dg.ok) return MPS_EDEVICE;
     // the same checks as mps_create, on the device (a restart path uploads every step)
     return upload_state(c, pos, vel, types, true, true);
+}
+
+int mps_write_state_device(mps_ctx* c, const double* pos, const double* vel, const int8_t* types) {
+    if (!c || !pos) return MPS_EINVAL;
+    DeviceGuard dg(c->prm.device);
+    if (!dg.ok) return MPS_EDEVICE;
+    return upload_state(c, pos, vel, types, true, true, true);
 }
 
 int mps_set_fluid_properties(mps_ctx* c, const double* rho, const double* nu) {

@@ -74,7 +74,8 @@ EXPORTS = ("mps_params_default", "mps_create", "mps_step", "mps_solve_ppe", "mps
            "mps_set_profiling", "mps_get_profile", "mps_ppe_cg_noalloc", "mps_destroy",
            "mps_strerror", "mps_set_fluid_properties", "mps_create_ensemble",
            "mps_scene_residuals", "mps_autotune", "mps_set_gravity", "mps_step_vjp",
-           "mps_time_kernel")
+           "mps_time_kernel", "mps_read_state_device", "mps_write_state_device",
+           "mps_step_vjp_device")
 NOALLOC_MAX_ROWS = 262144
 STAGES = ("bucket", "gather", "predict", "build", "ppe", "update")
 
@@ -109,6 +110,10 @@ def lib(build_if_missing: bool = False):
     L.mps_set_gravity.argtypes = [C.c_void_p, d]
     L.mps_time_kernel.argtypes = [C.c_void_p, C.c_int32, C.c_int32, d, d]
     L.mps_step_vjp.argtypes = [C.c_void_p, d, d, d, d, d, C.POINTER(mps_vjp_report)]
+    vp = C.c_void_p
+    L.mps_read_state_device.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    L.mps_write_state_device.argtypes = [vp, vp, vp, vp]
+    L.mps_step_vjp_device.argtypes = [vp, vp, vp, vp, vp, d, C.POINTER(mps_vjp_report)]
     L.mps_create_ensemble.argtypes = [d, d, i8, C.POINTER(C.c_int32), C.c_int64,
                                       C.POINTER(mps_params), C.POINTER(mps_scene), C.c_int32,
                                       C.POINTER(C.c_void_p)]
@@ -131,7 +136,8 @@ def lib(build_if_missing: bool = False):
               "mps_debug_cells", "mps_debug_neighbors", "mps_get_constants", "mps_set_profiling",
               "mps_get_profile", "mps_ppe_cg_noalloc", "mps_set_fluid_properties",
               "mps_create_ensemble", "mps_scene_residuals", "mps_autotune", "mps_set_gravity",
-              "mps_step_vjp", "mps_time_kernel"):
+              "mps_step_vjp", "mps_time_kernel", "mps_read_state_device",
+              "mps_write_state_device", "mps_step_vjp_device"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -359,6 +365,46 @@ def mps_step_vjp(h, g_pos, g_vel, check: bool = True):
     return rc, out_r, out_u, out_g, rep.as_dict()
 
 
+def _dptr(t, dtype_name, shape=None):
+    """Device address of a contiguous CUDA tensor (None passes through)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous() or str(t.dtype) != f"torch.{dtype_name}":
+        raise ValueError(f"expected a contiguous CUDA tensor of {dtype_name}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {shape}, got {tuple(t.shape)}")
+    return C.c_void_p(t.data_ptr())
+
+
+def mps_read_state_device(h, n: int, dim: int, pos=None, vel=None, p=None, n_star=None,
+                          flags=None, types=None):
+    """Read the state into preallocated CUDA tensors (float64 (n, dim) / (n,), uint8 flags,
+    int8 types); any may be None."""
+    _check(lib().mps_read_state_device(h, _dptr(pos, "float64", (n, dim)),
+                                       _dptr(vel, "float64", (n, dim)), _dptr(p, "float64", (n,)),
+                                       _dptr(n_star, "float64", (n,)), _dptr(flags, "uint8", (n,)),
+                                       _dptr(types, "int8", (n,))), "mps_read_state_device")
+
+
+def mps_write_state_device(h, pos, vel=None, types=None):
+    _check(lib().mps_write_state_device(h, _dptr(pos, "float64"), _dptr(vel, "float64"),
+                                        _dptr(types, "int8")), "mps_write_state_device")
+
+
+def mps_step_vjp_device(h, g_pos, g_vel, out_pos, out_vel, check: bool = True):
+    """Reverse of the step with CUDA tensors: g_pos, g_vel in; out_pos, out_vel (same shape)
+    out; returns (rc, dL/dg[3] as numpy, report dict)."""
+    out_g = np.zeros(3, np.float64)
+    rep = mps_vjp_report()
+    rc = lib().mps_step_vjp_device(h, _dptr(g_pos, "float64"), _dptr(g_vel, "float64"),
+                                   _dptr(out_pos, "float64", tuple(g_pos.shape)),
+                                   _dptr(out_vel, "float64", tuple(g_vel.shape)),
+                                   _ptr(out_g, C.c_double), C.byref(rep))
+    if check:
+        _check(rc, "mps_step_vjp_device")
+    return rc, out_g, rep.as_dict()
+
+
 KERNEL_SPMV32, KERNEL_RESID_FF, KERNEL_SPMV64 = 0, 1, 2
 
 
@@ -512,6 +558,16 @@ class Simulation:
     def step_vjp(self, g_pos, g_vel, check: bool = True):
         """(rc, dL/dr, dL/du, dL/dg, report) of the step from the current state."""
         return mps_step_vjp(self.h, g_pos, g_vel, check)
+
+    # device-memory variants (CUDA tensors in original order)
+    def read_device(self, pos=None, vel=None, p=None, n_star=None, flags=None, types=None):
+        mps_read_state_device(self.h, self.n, self.dim, pos, vel, p, n_star, flags, types)
+
+    def write_device(self, pos, vel=None, types=None):
+        mps_write_state_device(self.h, pos, vel, types)
+
+    def step_vjp_device(self, g_pos, g_vel, out_pos, out_vel, check: bool = True):
+        return mps_step_vjp_device(self.h, g_pos, g_vel, out_pos, out_vel, check)
 
     def read(self, **kw):
         return mps_read_state(self.h, self.n, self.dim, **kw)

@@ -261,3 +261,71 @@ def test_rollout_forcing_gradient_matches_central_differences():
         sim.close()
     adj = float((gf * v).sum())
     assert abs(fd - adj) <= 1e-6 * abs(adj), (fd, adj)
+
+
+def test_device_memory_calls_equal_host_calls():
+    """read / write / reverse step with CUDA tensors give the host calls' results bit for bit."""
+    import torch
+    from paper_2105_01677_gb300 import mps
+    sc = _scene(3, seed=11)
+    a, b = _cotangents(sc, seed=12)
+    sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, **gpu_params(sc, cg_tol=CG))
+    try:
+        sim.step(2)
+        host = sim.read()
+        dev = torch.device("cuda", 0)
+        x = torch.empty((sc.n, 3), dtype=torch.float64, device=dev)
+        u = torch.empty_like(x)
+        p = torch.empty(sc.n, dtype=torch.float64, device=dev)
+        t = torch.empty(sc.n, dtype=torch.int8, device=dev)
+        sim.read_device(pos=x, vel=u, p=p, types=t)
+        assert np.array_equal(x.cpu().numpy(), host["pos"])
+        assert np.array_equal(u.cpu().numpy(), host["vel"])
+        assert np.array_equal(p.cpu().numpy(), host["p"])
+        assert np.array_equal(t.cpu().numpy(), host["types"])
+        _, gr_h, gu_h, gg_h, _ = sim.step_vjp(a, b)
+        ga, gb = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+        ro, uo = torch.empty_like(ga), torch.empty_like(gb)
+        _, gg_d, rep = sim.step_vjp_device(ga, gb, ro, uo)
+        assert np.array_equal(ro.cpu().numpy(), gr_h) and np.array_equal(uo.cpu().numpy(), gu_h)
+        assert np.array_equal(gg_d, gg_h)
+        # write from device memory, then a step equals a step after the host write
+        sim.write_device(x, u, t)
+        sim.step(1)
+        s1 = sim.read()
+        sim.write(host["pos"], host["vel"], host["types"])
+        sim.step(1)
+        s2 = sim.read()
+        for k in ("pos", "vel", "p"):
+            assert np.array_equal(s1[k], s2[k]), k
+    finally:
+        sim.close()
+
+
+def test_rollout_on_cuda_tensors_equals_host_rollout():
+    import torch
+    from paper_2105_01677_gb300 import autograd, mps
+    sc = _scene(2, seed=13)
+    T = 5
+    forcing = np.zeros((T, 3))
+    forcing[:, 0] = 0.3
+    forcing[:, 1] = -9.81
+    a, b = _cotangents(sc, seed=14)
+    grads = []
+    for device in ("cpu", "cuda"):
+        sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
+                             **gpu_params(sc, cg_tol=CG))
+        try:
+            x = torch.tensor(sc.pos, dtype=torch.float64, device=device, requires_grad=True)
+            u = torch.tensor(sc.vel, dtype=torch.float64, device=device, requires_grad=True)
+            f = torch.tensor(forcing, dtype=torch.float64, device=device, requires_grad=True)
+            xT, uT = autograd.rollout(sim, x, u, f, checkpoint_every=2)
+            assert xT.device.type == device
+            loss = (xT * torch.from_numpy(a).to(device)).sum() + (uT * torch.from_numpy(b).to(device)).sum()
+            loss.backward()
+            grads.append((xT.detach().cpu().numpy(), x.grad.cpu().numpy(), u.grad.cpu().numpy(),
+                          f.grad.cpu().numpy()))
+        finally:
+            sim.close()
+    for h, d in zip(*grads):
+        assert np.array_equal(h, d)
