@@ -18,10 +18,11 @@
 //           rows whose minimum is p_j, zero where p_j is not a function of the state (off
 //           the PPE, or clamped); the equation of state turns it into gn*_j directly;
 //   adjoint CG           A lam = gp on the same symmetric matrix (the PPE path);
-//   star    (all kinds)   gr*_k: number density (every non-GHOST pair within re_n at r*),
-//           PPE coefficients c_ij = K_ij w (non-dummy pairs within re_lap, gc_ij =
-//           -lam_i (p_i - p_j) with the solution before the clamp) and the gradient's pair
-//           terms; gu*_k = gu_k + dt gr*_k;
+//   star    (all kinds)   gr*_k: number density (every non-GHOST pair within re_n at r*)
+//           and the gradient's pair terms over the candidate list; PPE coefficients
+//           c_ij = K_ij w (non-dummy pairs within re_lap, gc_ij = -lam_i (p_i - p_j) with
+//           the solution before the clamp) over the step's stored PPE rows, whose stored
+//           c_ij give K re/s^3 = (c + K)^3/(K re)^2; gu*_k = gu_k + dt gr*_k;
 //   visc    (all kinds)   the prediction u* = u + dt (nu lap(u) + g) at r^k: the
 //           Laplacian's transpose onto the velocities and its derivative in positions.
 // All arithmetic is binary64.  Neighbour sets are decided by the same exact predicate as
@@ -56,6 +57,9 @@ struct AdjArgs {
     const double *p, *phat, *ppre, *nstar, *diag;
     const uint8_t* flag;
     const int32_t *vcol, *vcnt, *ncol, *ncnt;
+    const int32_t *lcol, *lcnt;        // the step's PPE rows: non-dummy j within re_lap at r*
+    const double* lv64;                // with c_ij in binary64 (FP64 mode) or
+    const float *lv32, *lvlo;          //   as float-float hi + lo (mixed mode)
     const double *rho_s, *nu_s;        // two-phase (null: uniform)
     Radius rn, rl;
     double n0, coef_grad, coef_ppe, coef_lap, rho, nu, dt, c0, gamma;
@@ -144,7 +148,7 @@ __device__ __forceinline__ double gn_of(const AdjArgs& a, int i) {
 }
 
 // cotangent of r* (and u* of FLUID rows): number density, PPE coefficients, gradient pairs
-__global__ void __launch_bounds__(kBT) k_adj_star(AdjArgs a) {
+__global__ void __launch_bounds__(kBT) k_adj_star(AdjArgs a, double inv_kre2) {
     const int k = blockIdx.x * kBT + threadIdx.x;
     if (k >= a.n) return;
     const int tk = a.type[k];
@@ -152,58 +156,66 @@ __global__ void __launch_bounds__(kBT) k_adj_star(AdjArgs a) {
     if (tk != kGhost) {
         const bool fk = tk == kFluid, ndk = tk != kDummy;
         const double gnk = gn_of(a, k);
-        const bool rk = a.ppe && a.diag[k] != 0.0;
-        const double lamk = rk ? a.lam[k] : 0.0, ppk = rk ? a.ppre[k] : 0.0;
         const double pk = a.p[k], phk = a.phat[k];
         const double4 gGk = a.gG[k];
         const double4 xk = a.ps[k];
         const float4 qk = a.ps32[k];
-        const double K0 = a.coef_lap, Kppe = a.coef_ppe;
-        const double rhok = a.rho_s ? a.rho_s[k] : 0.0;
+        // number-density and gradient pairs (re_n): the candidate list, exact predicate
         const int cnt = a.vcnt[k];
         for (int t = 0; t < cnt; t++) {
             const int j = a.vcol[sell(k, t, a.cap_v)];
+            if (!in_radius(dist2_f(qk, a.ps32[j]), a.rn, a.ps, k, j, xk)) continue;
             const int tj = a.type[j];
-            const float r2f = dist2_f(qk, a.ps32[j]);
-            const bool ndj = tj != kDummy;
-            const bool in_n = in_radius(r2f, a.rn, a.ps, k, j, xk);
-            const bool in_l = a.ppe && ndk && ndj && in_radius(r2f, a.rl, a.ps, k, j, xk);
-            if (!in_n && !in_l) continue;
             const double4 x = sub4(a.ps[j], xk);
             // every power of 1/s from one reciprocal square root
             const double rs = rsqrt(dot3(x, x));
             const double rs2 = rs * rs;
             const double is3 = rs2 * rs;
-            if (in_n) {
-                // n*_k and n*_j both hold w(s): -(gn_k + gn_j) w'(s) x/s
-                acc = axpy4((gnk + gn_of(a, j)) * a.rn.re * is3, x, acc);
-                if (ndk && ndj) {
-                    const double w = fma(a.rn.re, rs, -1.0);
-                    const double q = w * rs2;
-                    // (d/ds (w/s^2)) / s = -re/s^5 - 2 w/s^4
-                    const double qds = -rs2 * rs2 * fma(a.rn.re, rs, 2.0 * w);
-                    if (fk) {   // pair (k, j) of row k's gradient: -X
-                        const double dg = dot3(x, gGk);
-                        const double f = a.coef_grad * (a.p[j] - phk);
-                        acc = axpy4(-f * q, gGk, acc);
-                        acc = axpy4(-f * qds * dg, x, acc);
-                    }
-                    if (tj == kFluid) {   // pair (j, k) of row j's gradient: +X
-                        const double4 gGj = a.gG[j];
-                        const double dg = dot3(x, gGj);
-                        const double f = a.coef_grad * (pk - a.phat[j]);
-                        acc = axpy4(f * q, gGj, acc);
-                        acc = axpy4(f * qds * dg, x, acc);
-                    }
+            // n*_k and n*_j both hold w(s): -(gn_k + gn_j) w'(s) x/s
+            acc = axpy4((gnk + gn_of(a, j)) * a.rn.re * is3, x, acc);
+            if (ndk && tj != kDummy) {
+                const double w = fma(a.rn.re, rs, -1.0);
+                const double q = w * rs2;
+                // (d/ds (w/s^2)) / s = -re/s^5 - 2 w/s^4
+                const double qds = -rs2 * rs2 * fma(a.rn.re, rs, 2.0 * w);
+                if (fk) {   // pair (k, j) of row k's gradient: -X
+                    const double dg = dot3(x, gGk);
+                    const double f = a.coef_grad * (a.p[j] - phk);
+                    acc = axpy4(-f * q, gGk, acc);
+                    acc = axpy4(-f * qds * dg, x, acc);
+                }
+                if (tj == kFluid) {   // pair (j, k) of row j's gradient: +X
+                    const double4 gGj = a.gG[j];
+                    const double dg = dot3(x, gGj);
+                    const double f = a.coef_grad * (pk - a.phat[j]);
+                    acc = axpy4(f * q, gGj, acc);
+                    acc = axpy4(f * qds * dg, x, acc);
                 }
             }
-            if (in_l) {
+        }
+        // PPE coefficient pairs (non-dummy j within re_lap): the row's stored coefficients.
+        // -(gc_kj + gc_jk) K w'(s) x/s = (p_k - p_j)(lam_j - lam_k) K re/s^3 x, and with
+        // c = K (re/s - 1) stored, K re/s^3 = (c + K)^3 / (K re)^2: no square root
+        if (a.ppe && (fk || tk == kWall)) {
+            const bool rk = a.diag[k] != 0.0;
+            const double lamk = rk ? a.lam[k] : 0.0, ppk = rk ? a.ppre[k] : 0.0;
+            const double rhok = a.rho_s ? a.rho_s[k] : 0.0;
+            const int m = a.lcnt[k];
+            for (int t = 0; t < m; t++) {
+                const size_t q = sell(k, t, a.cap);
+                const int j = a.lcol[q];
+                const double c = a.lv64 ? a.lv64[q] : (double)a.lv32[q] + (double)a.lvlo[q];
                 const bool rj = a.diag[j] != 0.0;
                 const double lamj = rj ? a.lam[j] : 0.0, ppj = rj ? a.ppre[j] : 0.0;
-                const double cb = -lamk * (ppk - ppj) - lamj * (ppj - ppk);
-                const double K = a.rho_s ? K0 * (2.0 / (rhok + a.rho_s[j])) : Kppe;
-                // -(gc_kj + gc_jk) K w'(s) x/s
-                acc = axpy4(cb * K * a.rl.re * is3, x, acc);
+                double K = a.coef_ppe, ik = inv_kre2;
+                if (a.rho_s) {   // two-phase pair factor
+                    K = a.coef_lap * (2.0 / (rhok + a.rho_s[j]));
+                    const double kre = K * a.rl.re;
+                    ik = 1.0 / (kre * kre);
+                }
+                const double u = c + K;
+                const double f = (ppk - ppj) * (lamj - lamk) * (u * u * u * ik);
+                acc = axpy4(f, sub4(a.ps[j], xk), acc);
             }
         }
     }
@@ -347,6 +359,11 @@ AdjArgs adj_args(Ctx* c) {
     a.vcnt = c->vl_cnt;
     a.ncol = c->nb_n_col;
     a.ncnt = c->nb_n_cnt;
+    a.lcol = c->nb_lap_col;
+    a.lcnt = c->nb_lap_cnt;
+    a.lv64 = c->prm.precision == 0 ? c->nb_lap_v64 : nullptr;
+    a.lv32 = c->nb_lap_v32;
+    a.lvlo = c->nb_lap_vlo;
     a.rho_s = c->rho_s;
     a.nu_s = c->nu_s;
     a.rn = c->r_n;
@@ -404,7 +421,8 @@ void launch_adj_front(Ctx* c) {
 void launch_adj_back(Ctx* c, double* d_gsum) {
     const AdjArgs a = adj_args(c);
     const int g = blocks(c->n, kBT);
-    k_adj_star<<<g, kBT, 0, c->stream>>>(a);
+    const double kre = c->coef_ppe * c->r_lap.re;
+    k_adj_star<<<g, kBT, 0, c->stream>>>(a, 1.0 / (kre * kre));
     k_adj_visc<<<g, kBT, 0, c->stream>>>(a);
     const int nb = std::min<int>(blocks(c->n, 256), 1024);   // c->partials holds 4096 doubles
     k_adj_gpart<<<nb, 256, 0, c->stream>>>((int)c->n, c->adj.gus, c->partials);
