@@ -508,6 +508,47 @@ __global__ void __launch_bounds__(kBT) k_scene_sums(const double* r, const doubl
     }
 }
 
+// Device-driven mixed solve of an ensemble, after each sweep's residual and per-scene sums:
+// every scene is checked against cg_tol relative to its own right-hand side once the global
+// residual meets the global target; if one is still above, the target is tightened by
+// what the worst scene needs (squared, with a margin of 2, within [1e-8, 0.5]); then the
+// refinement loop's conditional is set as k_resid_ff_t sets it for a single scene.
+__global__ void k_scene_decide(CgScalars* cg, const double* sums, int n_scenes, double tol,
+                               cudaGraphConditionalHandle h_out) {
+    __shared__ double s_worst[kBT];
+    double w = 0.0;
+    for (int s = threadIdx.x; s < n_scenes; s += kBT) {
+        const double rr = sums[2 * s], bb = sums[2 * s + 1];
+        const double rel = bb > 0.0 ? sqrt(rr / bb) : (rr > 0.0 ? HUGE_VAL : 0.0);
+        w = fmax(w, rel);
+    }
+    s_worst[threadIdx.x] = w;
+    __syncthreads();
+    for (int o = kBT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s_worst[threadIdx.x] = fmax(s_worst[threadIdx.x], s_worst[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double worst = s_worst[0];
+    cg->total += cg->iters;
+    cg->outer += 1;
+    cg->guard_out += 1;
+    bool more;
+    if (cg->rr > cg->ostop2) {
+        more = true;
+    } else if (worst <= tol) {
+        more = false;
+    } else {
+        const double f = 0.25 * (tol / worst) * (tol / worst);
+        cg->ostop2 *= fmin(0.5, fmax(f, 1e-8));
+        more = true;
+    }
+    more = more && cg->outer < cg->max_outer && cg->total < cg->max_total &&
+           cg->guard_out < cg->max_outer + 2;
+    cg->done = more ? 0 : 1;   // 1: the solve ended (converged or capped)
+    cudaGraphSetConditional(h_out, more ? 1u : 0u);
+}
+
 // a tighter recurrence target for the FP64 CG (and whether the current residual meets it)
 __global__ void k_set_stop(CgScalars* cg, double stop2) {
     cg->stop2 = stop2;
@@ -684,7 +725,13 @@ static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
     MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, B, &n_inner, nullptr, 1, mode));
     k_outer_update<<<gv, kBT, 0, s>>>(n, x, c->cg_x32, -1.0, c->cg_xhl, c->cg);
-    k_resid_ff_t<<<gs, kBT, 0, s>>>(sv, x, c->cg_xhl, c->cg_r, c->cg, h_out);
+    const bool multi = c->n_scenes > 1;
+    k_resid_ff_t<<<gs, kBT, 0, s>>>(sv, x, c->cg_xhl, c->cg_r, c->cg, multi ? 0 : h_out);
+    if (multi) {   // every scene to its own tolerance, decided on the device
+        k_scene_sums<<<c->n_scenes, kBT, 0, s>>>(c->cg_r, c->bvec, c->cell_start, c->scene_shift,
+                                                  c->scene_sums);
+        k_scene_decide<<<1, kBT, 0, s>>>(c->cg, c->scene_sums, c->n_scenes, c->prm.cg_tol, h_out);
+    }
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
     MPS_CUDA(c, cudaGraphInstantiate(&pg->exec, G, 0));
     pg->x = x;
@@ -723,16 +770,36 @@ static int mixed_graph_solve(Ctx* c, double* x, mps_report* rep, int max_total) 
     MPS_CUDA(c, cudaGraphLaunch(pg->exec, c->stream));
     int rc;
     if ((rc = read_scalars(c))) return rc;
-    const CgScalars& h = *c->cg_host;
-    // kernels the graph ran: start, per sweep init + update + residual, per inner iteration 3
-    c->launches += 1 + 3 * (int64_t)h.outer + 3 * (int64_t)h.total;
-    const double rel = h.bb > 0.0 ? sqrt(h.rr / h.bb) : 0.0;
+    const CgScalars h = *c->cg_host;
+    const bool multi = c->n_scenes > 1;
+    // kernels the graph ran: start, per sweep init + update + residual (+ the per-scene sums
+    // and decision of an ensemble), per inner iteration 3
+    c->launches += 1 + (multi ? 5 : 3) * (int64_t)h.outer + 3 * (int64_t)h.total;
     rep->cg_iters = h.total;
     rep->cg_outer = h.outer;
-    rep->cg_resid = rel;
-    c->scene_resid[0] = rel;
     c->last_cg_iters = std::max(4, h.total / std::max(h.outer, 1));
-    if (!(h.rr <= h.ostop2)) return MPS_ECG_NOCONV;
+    if (!multi) {
+        const double rel = h.bb > 0.0 ? sqrt(h.rr / h.bb) : 0.0;
+        rep->cg_resid = rel;
+        c->scene_resid[0] = rel;
+        if (!(h.rr <= h.ostop2)) return MPS_ECG_NOCONV;
+        return MPS_OK;
+    }
+    // ensemble: every scene's residual from the last sweep's per-scene sums
+    const int S = c->n_scenes;
+    std::vector<double> hs(2 * (size_t)S);
+    MPS_CUDA(c, cudaMemcpyAsync(hs.data(), c->scene_sums, sizeof(double) * hs.size(),
+                                cudaMemcpyDeviceToHost, c->stream));
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    double worst = 0.0;
+    for (int sc = 0; sc < S; sc++) {
+        const double rr = hs[2 * sc], bb = hs[2 * sc + 1];
+        const double rel = bb > 0.0 ? std::sqrt(rr / bb) : (rr > 0.0 ? HUGE_VAL : 0.0);
+        c->scene_resid[(size_t)sc] = h.outer > 0 ? rel : 0.0;
+        worst = std::max(worst, c->scene_resid[(size_t)sc]);
+    }
+    rep->cg_resid = worst;
+    if (!(worst <= c->prm.cg_tol)) return MPS_ECG_NOCONV;
     return MPS_OK;
 }
 
@@ -810,7 +877,7 @@ static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool prima
     const int max_total = c->prm.cg_max_iter > 0 ? c->prm.cg_max_iter : (int)std::min<int64_t>(10 * c->n, 1 << 30);
     const int gs = row_grid(c), gv = vec_grid(c);
     int rc;
-    if (primary && c->prm.precision == 1 && c->n_scenes == 1 && c->prm.ppe_host_loop == 0)
+    if (primary && c->prm.precision == 1 && c->prm.ppe_host_loop == 0)
         return mixed_graph_solve(c, x, rep, max_total);
     if ((rc = set_cg_limits(c, max_total))) return rc;
     // x = 0, r = b, d = b, rho = |b|^2, stop2 = tol^2 |b|^2

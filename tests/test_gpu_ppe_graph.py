@@ -91,3 +91,26 @@ def test_time_kernel_leaves_the_state_and_counts_bytes():
     assert ms > 0 and ms2 > 0
     assert 8 * rep["pairs_ppe"] * 0.4 <= by <= 8 * rep["pairs_ppe"] + 12 * sc.n
     assert abs(by2 / by - 1.5) < 0.1
+
+
+def test_graph_solve_equals_host_loop_ensemble():
+    """An ensemble's per-scene convergence decided on the device inside the graph: the
+    same sweeps, iterations, per-scene residuals and states as the host-driven loop."""
+    from paper_2105_01677_gb300 import mps
+    E = scenes.ensemble_2d(count=6, seed=4, fluid=(150, 1500))
+    out = []
+    for host_loop in (0, 1):
+        ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1,
+                           cg_tol=1e-9, ppe_host_loop=host_loop)
+        try:
+            reps = [ens.step(1)[1] for _ in range(4)]
+            out.append((reps, ens.read(), ens.residuals()))
+        finally:
+            ens.close()
+    (rg, sg, resg), (rh, sh, resh) = out
+    for a, b in zip(rg, rh):
+        assert (a["cg_iters"], a["cg_outer"], a["cg_resid"]) == (b["cg_iters"], b["cg_outer"], b["cg_resid"])
+    assert np.array_equal(resg, resh) and np.all(resg <= 1e-9)
+    for a, b in zip(sg, sh):
+        for k in ("pos", "vel", "p", "n_star", "flags"):
+            assert np.array_equal(a[k], b[k]), k
