@@ -19,10 +19,11 @@
 //           the PPE, or clamped); the equation of state turns it into gn*_j directly;
 //   adjoint CG           A lam = gp on the same symmetric matrix (the PPE path);
 //   star    (all kinds)   gr*_k: number density (every non-GHOST pair within re_n at r*)
-//           and the gradient's pair terms over the candidate list; PPE coefficients
-//           c_ij = K_ij w (non-dummy pairs within re_lap, gc_ij = -lam_i (p_i - p_j) with
-//           the solution before the clamp) over the step's stored PPE rows, whose stored
-//           c_ij give K re/s^3 = (c + K)^3/(K re)^2; gu*_k = gu_k + dt gr*_k;
+//           and the gradient's pair terms over the step's gradient lists (DUMMY neighbours
+//           from the candidate walk); PPE coefficients c_ij = K_ij w (non-dummy pairs
+//           within re_lap, gc_ij = -lam_i (p_i - p_j) with the solution before the clamp)
+//           over the step's stored PPE rows, whose stored c_ij give K re/s^3 =
+//           (c + K)^3/(K re)^2; gu*_k = gu_k + dt gr*_k;
 //   visc    (all kinds)   the prediction u* = u + dt (nu lap(u) + g) at r^k: the
 //           Laplacian's transpose onto the velocities and its derivative in positions.
 // All arithmetic is binary64.  Neighbour sets are decided by the same exact predicate as
@@ -147,80 +148,118 @@ __device__ __forceinline__ double gn_of(const AdjArgs& a, int i) {
     return a.diag[i] != 0.0 ? a.lam[i] / (a.n0 * a.dt * a.dt) : 0.0;
 }
 
-// cotangent of r* (and u* of FLUID rows): number density, PPE coefficients, gradient pairs
-__global__ void __launch_bounds__(kBT) k_adj_star(AdjArgs a, double inv_kre2) {
-    const int k = blockIdx.x * kBT + threadIdx.x;
-    if (k >= a.n) return;
-    const int tk = a.type[k];
+// cotangent of r* (and u* of FLUID rows): number density, PPE coefficients, gradient pairs.
+// On GB300 an FP64 warp instruction costs the same whatever the number of active lanes, so
+// the pair loops run over dense lists wherever the forward step stored them: FLUID / WALL
+// rows (the bucket build's list of them, one thread each) take their non-dummy neighbours
+// within re_n from the gradient list and their PPE pairs from the PPE rows; only the DUMMY
+// neighbours (number density alone) come from the candidate walk.
+__global__ void __launch_bounds__(kBT) k_adj_star_fw(AdjArgs a, const int32_t* rows,
+                                                     const uint32_t* nrows, double inv_kre2) {
+    const int tid = blockIdx.x * kBT + threadIdx.x;
+    if (tid >= (int)*nrows) return;
+    const int k = rows[tid];
+    const bool fk = a.type[k] == kFluid;
     double4 acc = a.gr[k];
-    if (tk != kGhost) {
-        const bool fk = tk == kFluid, ndk = tk != kDummy;
-        const double gnk = gn_of(a, k);
-        const double pk = a.p[k], phk = a.phat[k];
-        const double4 gGk = a.gG[k];
-        const double4 xk = a.ps[k];
+    const double gnk = gn_of(a, k);
+    const double pk = a.p[k], phk = a.phat[k];
+    const double4 gGk = a.gG[k];
+    const double4 xk = a.ps[k];
+    // non-dummy pairs within re_n: number density and the gradient's pair terms
+    const int cn = a.ncnt[k];
+    for (int t = 0; t < cn; t++) {
+        const int j = a.ncol[sell(k, t, a.cap_n)];
+        const double4 x = sub4(a.ps[j], xk);
+        // every power of 1/s from one reciprocal square root
+        const double rs = rsqrt(dot3(x, x));
+        const double rs2 = rs * rs;
+        const double is3 = rs2 * rs;
+        // n*_k and n*_j both hold w(s): -(gn_k + gn_j) w'(s) x/s
+        acc = axpy4((gnk + gn_of(a, j)) * a.rn.re * is3, x, acc);
+        const double w = fma(a.rn.re, rs, -1.0);
+        const double q = w * rs2;
+        // (d/ds (w/s^2)) / s = -re/s^5 - 2 w/s^4
+        const double qds = -rs2 * rs2 * fma(a.rn.re, rs, 2.0 * w);
+        if (fk) {   // pair (k, j) of row k's gradient: -X
+            const double dg = dot3(x, gGk);
+            const double f = a.coef_grad * (a.p[j] - phk);
+            acc = axpy4(-f * q, gGk, acc);
+            acc = axpy4(-f * qds * dg, x, acc);
+        }
+        if (a.type[j] == kFluid) {   // pair (j, k) of row j's gradient: +X
+            const double4 gGj = a.gG[j];
+            const double dg = dot3(x, gGj);
+            const double f = a.coef_grad * (pk - a.phat[j]);
+            acc = axpy4(f * q, gGj, acc);
+            acc = axpy4(f * qds * dg, x, acc);
+        }
+    }
+    // DUMMY neighbours within re_n (their n* enters no equation): -gn_k w'(s) x/s
+    if (gnk != 0.0) {
         const float4 qk = a.ps32[k];
-        // number-density and gradient pairs (re_n): the candidate list, exact predicate
         const int cnt = a.vcnt[k];
         for (int t = 0; t < cnt; t++) {
             const int j = a.vcol[sell(k, t, a.cap_v)];
+            if (a.type[j] != kDummy) continue;
             if (!in_radius(dist2_f(qk, a.ps32[j]), a.rn, a.ps, k, j, xk)) continue;
-            const int tj = a.type[j];
             const double4 x = sub4(a.ps[j], xk);
-            // every power of 1/s from one reciprocal square root
             const double rs = rsqrt(dot3(x, x));
-            const double rs2 = rs * rs;
-            const double is3 = rs2 * rs;
-            // n*_k and n*_j both hold w(s): -(gn_k + gn_j) w'(s) x/s
-            acc = axpy4((gnk + gn_of(a, j)) * a.rn.re * is3, x, acc);
-            if (ndk && tj != kDummy) {
-                const double w = fma(a.rn.re, rs, -1.0);
-                const double q = w * rs2;
-                // (d/ds (w/s^2)) / s = -re/s^5 - 2 w/s^4
-                const double qds = -rs2 * rs2 * fma(a.rn.re, rs, 2.0 * w);
-                if (fk) {   // pair (k, j) of row k's gradient: -X
-                    const double dg = dot3(x, gGk);
-                    const double f = a.coef_grad * (a.p[j] - phk);
-                    acc = axpy4(-f * q, gGk, acc);
-                    acc = axpy4(-f * qds * dg, x, acc);
-                }
-                if (tj == kFluid) {   // pair (j, k) of row j's gradient: +X
-                    const double4 gGj = a.gG[j];
-                    const double dg = dot3(x, gGj);
-                    const double f = a.coef_grad * (pk - a.phat[j]);
-                    acc = axpy4(f * q, gGj, acc);
-                    acc = axpy4(f * qds * dg, x, acc);
-                }
-            }
+            acc = axpy4(gnk * a.rn.re * (rs * rs * rs), x, acc);
         }
-        // PPE coefficient pairs (non-dummy j within re_lap): the row's stored coefficients.
-        // -(gc_kj + gc_jk) K w'(s) x/s = (p_k - p_j)(lam_j - lam_k) K re/s^3 x, and with
-        // c = K (re/s - 1) stored, K re/s^3 = (c + K)^3 / (K re)^2: no square root
-        if (a.ppe && (fk || tk == kWall)) {
-            const bool rk = a.diag[k] != 0.0;
-            const double lamk = rk ? a.lam[k] : 0.0, ppk = rk ? a.ppre[k] : 0.0;
-            const double rhok = a.rho_s ? a.rho_s[k] : 0.0;
-            const int m = a.lcnt[k];
-            for (int t = 0; t < m; t++) {
-                const size_t q = sell(k, t, a.cap);
-                const int j = a.lcol[q];
-                const double c = a.lv64 ? a.lv64[q] : (double)a.lv32[q] + (double)a.lvlo[q];
-                const bool rj = a.diag[j] != 0.0;
-                const double lamj = rj ? a.lam[j] : 0.0, ppj = rj ? a.ppre[j] : 0.0;
-                double K = a.coef_ppe, ik = inv_kre2;
-                if (a.rho_s) {   // two-phase pair factor
-                    K = a.coef_lap * (2.0 / (rhok + a.rho_s[j]));
-                    const double kre = K * a.rl.re;
-                    ik = 1.0 / (kre * kre);
-                }
-                const double u = c + K;
-                const double f = (ppk - ppj) * (lamj - lamk) * (u * u * u * ik);
-                acc = axpy4(f, sub4(a.ps[j], xk), acc);
+    }
+    // PPE coefficient pairs (non-dummy j within re_lap): the row's stored coefficients.
+    // -(gc_kj + gc_jk) K w'(s) x/s = (p_k - p_j)(lam_j - lam_k) K re/s^3 x, and with
+    // c = K (re/s - 1) stored, K re/s^3 = (c + K)^3 / (K re)^2: no square root
+    if (a.ppe) {
+        const bool rk = a.diag[k] != 0.0;
+        const double lamk = rk ? a.lam[k] : 0.0, ppk = rk ? a.ppre[k] : 0.0;
+        const double rhok = a.rho_s ? a.rho_s[k] : 0.0;
+        const int m = a.lcnt[k];
+        for (int t = 0; t < m; t++) {
+            const size_t q = sell(k, t, a.cap);
+            const int j = a.lcol[q];
+            const double c = a.lv64 ? a.lv64[q] : (double)a.lv32[q] + (double)a.lvlo[q];
+            const bool rj = a.diag[j] != 0.0;
+            const double lamj = rj ? a.lam[j] : 0.0, ppj = rj ? a.ppre[j] : 0.0;
+            double K = a.coef_ppe, ik = inv_kre2;
+            if (a.rho_s) {   // two-phase pair factor
+                K = a.coef_lap * (2.0 / (rhok + a.rho_s[j]));
+                const double kre = K * a.rl.re;
+                ik = 1.0 / (kre * kre);
             }
+            const double u = c + K;
+            const double f = (ppk - ppj) * (lamj - lamk) * (u * u * u * ik);
+            acc = axpy4(f, sub4(a.ps[j], xk), acc);
         }
     }
     a.grs[k] = acc;
-    a.gus[k] = tk == kFluid ? axpy4(a.dt, acc, a.gu[k]) : make_double4(0.0, 0.0, 0.0, 0.0);
+    a.gus[k] = fk ? axpy4(a.dt, acc, a.gu[k]) : make_double4(0.0, 0.0, 0.0, 0.0);
+}
+
+// DUMMY rows (number density of their FLUID / WALL neighbours within re_n) and GHOST rows
+// (carried through); FLUID / WALL slots are left to k_adj_star_fw
+__global__ void __launch_bounds__(kBT) k_adj_star_other(AdjArgs a) {
+    const int k = blockIdx.x * kBT + threadIdx.x;
+    if (k >= a.n) return;
+    const int tk = a.type[k];
+    if (tk == kFluid || tk == kWall) return;
+    double4 acc = a.gr[k];
+    if (tk == kDummy) {
+        const double4 xk = a.ps[k];
+        const float4 qk = a.ps32[k];
+        const int cnt = a.vcnt[k];
+        for (int t = 0; t < cnt; t++) {
+            const int j = a.vcol[sell(k, t, a.cap_v)];
+            const double gnj = gn_of(a, j);
+            if (gnj == 0.0) continue;
+            if (!in_radius(dist2_f(qk, a.ps32[j]), a.rn, a.ps, k, j, xk)) continue;
+            const double4 x = sub4(a.ps[j], xk);
+            const double rs = rsqrt(dot3(x, x));
+            acc = axpy4(gnj * a.rn.re * (rs * rs * rs), x, acc);
+        }
+    }
+    a.grs[k] = acc;
+    a.gus[k] = make_double4(0.0, 0.0, 0.0, 0.0);
 }
 
 // prediction at r^k: the Laplacian's transpose and its position derivative; final cotangents
@@ -422,12 +461,13 @@ void launch_adj_back(Ctx* c, double* d_gsum) {
     const AdjArgs a = adj_args(c);
     const int g = blocks(c->n, kBT);
     const double kre = c->coef_ppe * c->r_lap.re;
-    k_adj_star<<<g, kBT, 0, c->stream>>>(a, 1.0 / (kre * kre));
+    k_adj_star_fw<<<g, kBT, 0, c->stream>>>(a, c->rows_fw, c->scan_fw + c->n, 1.0 / (kre * kre));
+    k_adj_star_other<<<g, kBT, 0, c->stream>>>(a);
     k_adj_visc<<<g, kBT, 0, c->stream>>>(a);
     const int nb = std::min<int>(blocks(c->n, 256), 1024);   // c->partials holds 4096 doubles
     k_adj_gpart<<<nb, 256, 0, c->stream>>>((int)c->n, c->adj.gus, c->partials);
     k_adj_gsum<<<1, 256, 0, c->stream>>>(nb, c->partials, c->prm.dt, d_gsum);
-    c->launches += 4;
+    c->launches += 5;
 }
 
 void launch_adj_store(Ctx* c, double* d_out_r, double* d_out_u) {
