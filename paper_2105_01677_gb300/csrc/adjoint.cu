@@ -64,6 +64,7 @@ struct AdjArgs {
     const double *rho_s, *nu_s;        // two-phase (null: uniform)
     Radius rn, rl;
     double n0, coef_grad, coef_ppe, coef_lap, rho, nu, dt, c0, gamma;
+    double inv_n0dt2;                  // 1 / (n0 dt^2)
     // cotangents and work arrays (slot order)
     const double4 *gr, *gu;            // of r^{k+1}, u^{k+1}
     double4 *gG, *grs, *gus, *out_r, *out_u;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kBT) k_adj_pbar(AdjArgs a) {
 // the PPE path's number-density cotangent from the adjoint solution
 __device__ __forceinline__ double gn_of(const AdjArgs& a, int i) {
     if (!a.ppe) return a.gn[i];
-    return a.diag[i] != 0.0 ? a.lam[i] / (a.n0 * a.dt * a.dt) : 0.0;
+    return a.diag[i] != 0.0 ? a.lam[i] * a.inv_n0dt2 : 0.0;
 }
 
 // cotangent of r* (and u* of FLUID rows): number density, PPE coefficients, gradient pairs.
@@ -250,9 +251,9 @@ __global__ void __launch_bounds__(kBT) k_adj_star_other(AdjArgs a) {
         const int cnt = a.vcnt[k];
         for (int t = 0; t < cnt; t++) {
             const int j = a.vcol[sell(k, t, a.cap_v)];
+            if (!in_radius(dist2_f(qk, a.ps32[j]), a.rn, a.ps, k, j, xk)) continue;
             const double gnj = gn_of(a, j);
             if (gnj == 0.0) continue;
-            if (!in_radius(dist2_f(qk, a.ps32[j]), a.rn, a.ps, k, j, xk)) continue;
             const double4 x = sub4(a.ps[j], xk);
             const double rs = rsqrt(dot3(x, x));
             acc = axpy4(gnj * a.rn.re * (rs * rs * rs), x, acc);
@@ -262,44 +263,73 @@ __global__ void __launch_bounds__(kBT) k_adj_star_other(AdjArgs a) {
     a.gus[k] = make_double4(0.0, 0.0, 0.0, 0.0);
 }
 
-// prediction at r^k: the Laplacian's transpose and its position derivative; final cotangents
-__global__ void __launch_bounds__(kBT) k_adj_visc(AdjArgs a) {
-    const int k = blockIdx.x * kBT + threadIdx.x;
-    if (k >= a.n) return;
-    const int tk = a.type[k];
-    if (tk == kGhost) {
-        a.out_r[k] = a.gr[k];
-        a.out_u[k] = a.was_ghost[a.id[k]] ? a.gu[k] : make_double4(0.0, 0.0, 0.0, 0.0);
-        return;
+// prediction at r^k: the Laplacian's transpose and its position derivative; final
+// cotangents.  Only pairs with a FLUID end carry viscosity terms, so FLUID rows (the bucket
+// build's list of them) and the other rows run as two kernels, and the other rows skip
+// non-FLUID candidates before any binary64 work.
+//   pair (k, j), x = r_j - r_k, a_k = dt nu_k 2d/(n0 lambda) gu*_k (0 unless k is FLUID):
+//   gu_k += w (a_j - a_k),  gr_k -= w'(s)/s ((a_k - a_j) . (u_j - u_k)) x
+__device__ __forceinline__ void visc_pair(const AdjArgs& a, int j, const double4& xk,
+                                          const double4& uk, const double4& ak, double4& orr,
+                                          double4& ou) {
+    const double4 x = sub4(a.pos[j], xk);
+    const double rs = rsqrt(dot3(x, x));
+    const double w = fma(a.rl.re, rs, -1.0);
+    const double wd_s = -a.rl.re * (rs * rs * rs);   // w'(s)/s
+    double4 aj = make_double4(0.0, 0.0, 0.0, 0.0);
+    if (a.type[j] == kFluid) {
+        const double kj = a.dt * nu_of(a, j) * a.coef_lap;
+        const double4 gsj = a.gus[j];
+        aj = make_double4(kj * gsj.x, kj * gsj.y, kj * gsj.z, 0.0);
     }
-    const bool fk = tk == kFluid;
+    const double4 da = sub4(aj, ak);
+    ou = axpy4(w, da, ou);
+    orr = axpy4(wd_s * dot3(da, sub4(a.vel[j], uk)), x, orr);
+}
+
+__global__ void __launch_bounds__(kBT) k_adj_visc_f(AdjArgs a, const int32_t* rows,
+                                                    const uint32_t* nrows) {
+    const int tid = blockIdx.x * kBT + threadIdx.x;
+    if (tid >= (int)*nrows) return;
+    const int k = rows[tid];
     double4 orr = a.grs[k];
-    double4 ou = fk ? a.gus[k] : a.gu[k];
     const double4 gsk = a.gus[k];
-    const double kk = fk ? a.dt * nu_of(a, k) * a.coef_lap : 0.0;
+    double4 ou = gsk;
+    const double kk = a.dt * nu_of(a, k) * a.coef_lap;
+    const double4 ak = make_double4(kk * gsk.x, kk * gsk.y, kk * gsk.z, 0.0);
     const double4 xk = a.pos[k], uk = a.vel[k];
     const float4 qk = a.pos32[k];
     const int cnt = a.vcnt[k];
     for (int t = 0; t < cnt; t++) {
         const int j = a.vcol[sell(k, t, a.cap_v)];
         if (!in_radius(dist2_f(qk, a.pos32[j]), a.rl, a.pos, k, j, xk)) continue;
-        const double4 x = sub4(a.pos[j], xk);
-        const double rs = rsqrt(dot3(x, x));
-        const double w = fma(a.rl.re, rs, -1.0);
-        const double wd_s = -a.rl.re * (rs * rs * rs);   // w'(s)/s
-        const double4 uj = a.vel[j];
-        if (fk) {   // row k's Laplacian: u_k enters with -w, positions through w
-            ou = axpy4(-kk * w, gsk, ou);
-            const double f = kk * dot3(gsk, sub4(uj, uk)) * wd_s;
-            orr = axpy4(-f, x, orr);
-        }
-        if (a.type[j] == kFluid) {   // row j's Laplacian: u_k enters with +w
-            const double kj = a.dt * nu_of(a, j) * a.coef_lap;
-            const double4 gsj = a.gus[j];
-            ou = axpy4(kj * w, gsj, ou);
-            const double f = kj * dot3(gsj, sub4(uk, uj)) * wd_s;   // X of pair (j, k) with r_k - r_j
-            orr = axpy4(-f, x, orr);
-        }
+        visc_pair(a, j, xk, uk, ak, orr, ou);
+    }
+    a.out_r[k] = orr;
+    a.out_u[k] = ou;
+}
+
+__global__ void __launch_bounds__(kBT) k_adj_visc_other(AdjArgs a) {
+    const int k = blockIdx.x * kBT + threadIdx.x;
+    if (k >= a.n) return;
+    const int tk = a.type[k];
+    if (tk == kFluid) return;
+    if (tk == kGhost) {
+        a.out_r[k] = a.gr[k];
+        a.out_u[k] = a.was_ghost[a.id[k]] ? a.gu[k] : make_double4(0.0, 0.0, 0.0, 0.0);
+        return;
+    }
+    double4 orr = a.grs[k];
+    double4 ou = a.gu[k];
+    const double4 ak = make_double4(0.0, 0.0, 0.0, 0.0);
+    const double4 xk = a.pos[k], uk = a.vel[k];
+    const float4 qk = a.pos32[k];
+    const int cnt = a.vcnt[k];
+    for (int t = 0; t < cnt; t++) {
+        const int j = a.vcol[sell(k, t, a.cap_v)];
+        if (a.type[j] != kFluid) continue;
+        if (!in_radius(dist2_f(qk, a.pos32[j]), a.rl, a.pos, k, j, xk)) continue;
+        visc_pair(a, j, xk, uk, ak, orr, ou);
     }
     a.out_r[k] = orr;
     a.out_u[k] = ou;
@@ -416,6 +446,7 @@ AdjArgs adj_args(Ctx* c) {
     a.dt = P.dt;
     a.c0 = P.c0;
     a.gamma = P.gamma;
+    a.inv_n0dt2 = 1.0 / (c->n0_pnd * P.dt * P.dt);
     a.gr = c->adj.gr;
     a.gu = c->adj.gu;
     a.gG = c->adj.gG;
@@ -463,11 +494,12 @@ void launch_adj_back(Ctx* c, double* d_gsum) {
     const double kre = c->coef_ppe * c->r_lap.re;
     k_adj_star_fw<<<g, kBT, 0, c->stream>>>(a, c->rows_fw, c->scan_fw + c->n, 1.0 / (kre * kre));
     k_adj_star_other<<<g, kBT, 0, c->stream>>>(a);
-    k_adj_visc<<<g, kBT, 0, c->stream>>>(a);
+    k_adj_visc_f<<<g, kBT, 0, c->stream>>>(a, c->rows_f, c->scan_f + c->n);
+    k_adj_visc_other<<<g, kBT, 0, c->stream>>>(a);
     const int nb = std::min<int>(blocks(c->n, 256), 1024);   // c->partials holds 4096 doubles
     k_adj_gpart<<<nb, 256, 0, c->stream>>>((int)c->n, c->adj.gus, c->partials);
     k_adj_gsum<<<1, 256, 0, c->stream>>>(nb, c->partials, c->prm.dt, d_gsum);
-    c->launches += 5;
+    c->launches += 6;
 }
 
 void launch_adj_store(Ctx* c, double* d_out_r, double* d_out_u) {
