@@ -236,13 +236,15 @@ int setup(Ctx* c, const mps_scene* scenes, int n_scenes) {
     // shared grid: cells of the largest scene's side, covering every scene's own grid
     GridDesc& g = c->grid;
     g.dim = dim;
-    double hmax = 0.0, skin_half = 1e300;
+    double hmax = 0.0, skin_half = 1e300, re_skin = 1e300;
     for (const SceneParams& sp : c->scn_host) {
         hmax = std::max(hmax, sp.own_h);
         skin_half = std::min(skin_half, 0.5 * P.cell_skin * std::max(sp.rn.re, sp.rl.re));
+        re_skin = std::min(re_skin, std::max(sp.rn.re, sp.rl.re));
     }
     c->h = hmax;
     c->skin_half = skin_half;
+    c->re_skin = re_skin;
     g.h = hmax;
     int maxc = 1;
     double X = 0.0;
@@ -447,12 +449,15 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     const mps_params& P = c->prm;
     int rc;
     const bool keep = P.list_every > 1;
-    const double re_max = std::max(P.re_n, P.re_lap);
-    // A single scene gathers its candidate lists within the skin its recent motion needs
-    // over the lists' lifetime (the grid's cells keep the full skin); a step whose motion
-    // exceeds the skin of the lists in use is gathered again (with the full skin if a
-    // fresh gather already fell short), so the sets stay exact
-    const bool adapt = c->n_scenes == 1;
+    // the radius the skin is measured against: max(re) (of the scene with the smallest
+    // spacing in an ensemble)
+    const double re_max = c->re_skin;
+    // Candidate lists are gathered within the skin the recent motion needs over the lists'
+    // lifetime (the grid's cells keep the full skin); a step whose motion exceeds the skin
+    // of the lists in use is gathered again (with the full skin if a fresh gather already
+    // fell short), so the sets stay exact.  In an ensemble every scene's candidate radius
+    // is its own max(re) times (1 + that skin).
+    const bool adapt = true;
     const size_t n = (size_t)c->n;
     // Candidate lists are gathered at r_b and serve while every particle stays within
     // s max(re)/2 of r_b: a pair closer than re at r^k or r* is then closer than h at r_b.
@@ -472,7 +477,17 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         launch_copy_state_star(c);
         if (fresh) {
             c->gathered_skin = adapt ? c->list_skin : P.cell_skin;
-            if (adapt) c->r_v = make_radius(re_max * (1.0 + c->gathered_skin), c->band_x);
+            if (c->n_scenes == 1) {
+                c->r_v = make_radius(re_max * (1.0 + c->gathered_skin), c->band_x);
+            } else if (c->gathered_skin != c->scn_skin) {
+                for (SceneParams& sp : c->scn_host)
+                    sp.rv = make_radius(std::max(sp.rn.re, sp.rl.re) * (1.0 + c->gathered_skin),
+                                        c->band_x);
+                MPS_CUDA(c, cudaMemcpyAsync(c->scn, c->scn_host.data(),
+                                            sizeof(SceneParams) * c->scn_host.size(),
+                                            cudaMemcpyHostToDevice, c->stream));
+                c->scn_skin = c->gathered_skin;
+            }
             MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), c->stream));
             stage_begin(c, MPS_STAGE_GATHER);
             launch_verlet(c);                                          // candidates at r_b = r^k

@@ -312,8 +312,10 @@ struct Ctx {
     std::vector<double> scene_resid;
     uint32_t scene_shift = 0;            // dim * bits
     double skin_half = 0.0;              // s max(re)/2 of the scene with the smallest spacing
-    // Candidate-list skin of the next gather (one scene, lists gathered every step): sized
-    // from the last step's largest displacement, at most cell_skin; X of the FP32 bands.
+    double re_skin = 0.0;                // max(re) of the scene with the smallest spacing
+    double scn_skin = -1.0;              // ensemble: the list skin of the device scene table
+    // Candidate-list skin of the next gather: sized from the last step's largest
+    // displacement, at most cell_skin; X of the FP32 bands.
     double list_skin = 0.0;
     double gathered_skin = 0.0;          // the skin of the lists in use
     double band_x = 0.0;
