@@ -246,6 +246,7 @@ int setup(Ctx* c, const mps_scene* scenes, int n_scenes) {
     c->skin_half = skin_half;
     c->re_skin = re_skin;
     g.h = hmax;
+    g.inv_h = 1.0 / hmax;
     int maxc = 1;
     double X = 0.0;
     for (int a = 0; a < 3; a++) {

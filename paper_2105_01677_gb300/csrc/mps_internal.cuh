@@ -79,6 +79,7 @@ struct CgScalars {
 struct GridDesc {
     double bmin[3];
     double h;
+    double inv_h;      // 1/h in binary64 (cell_floor)
     int ncell[3];
     int bits;
     int dim;
@@ -364,6 +365,18 @@ __host__ __device__ inline void morton_decode(uint32_t key, int dim, int bits, i
     c[0] = c[1] = c[2] = 0;
     for (int k = 0; k < bits; k++)
         for (int a = 0; a < dim; a++) c[a] |= (int)((key >> (k * dim + a)) & 1u) << k;
+}
+
+// floor(fl(d / h)) -- the cell coordinate of the binary64 definition -- mostly without the
+// division: q = fl(d fl(1/h)) differs from fl(d/h) by at most ~3 ulp of |d/h|, so the two
+// have the same floor unless q lies within 4 ulp of an integer, and only there is the
+// quotient formed by the (slow) binary64 division.
+__device__ __forceinline__ double cell_floor(double d, double h, double inv_h) {
+    const double q = d * inv_h;
+    const double f = floor(q);
+    const double gap = fmin(q - f, (f + 1.0) - q);
+    if (gap > 4.0 * 2.220446049250313e-16 * fmax(fabs(q), 1.0)) return f;
+    return floor(__ddiv_rn(d, h));
 }
 
 // Squared distance in binary64 with one rounding per operation and the fixed order
