@@ -256,8 +256,8 @@ constexpr int kEntryL = 1 << 29;   // non-dummy within re_lap: a PPE coefficient
 constexpr int kSlotMask = kEntryL - 1;
 
 // Two passes per row.  Classification walks the candidate list, decides the predicates
-// (FP32 / float-float / binary64 tiers) and writes the hits into the row's PPE slots: the
-// entries within re_n from the front, PPE-only entries from the back.  The dense pass then
+// (FP32 / float-float / binary64 tiers) and writes the hits into the row's PPE slots in
+// candidate order (band pairs, decided after the walk, last).  The dense pass then
 // evaluates every hit with (nearly) all lanes of the warp busy, accumulates n* and the
 // diagonal, and compacts the PPE coefficients in place to the front of the row.
 // KERN, SRC: the weight (0 Eq. 4, 1 cubic) and the PPE source (0 Eq. 13, 1 HS, 2 HS + ECS) as
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
         const double4 pi = a.pos[i];
         const int cnt = a.vcnt[i];
         const bool with_ppe = (a.pressure_mode == 0);
-        int m_f = 0, m_b = 0, out_n = 0;
+        int m_f = 0, out_n = 0;
         bool overflow = false;
         // a decided pair: into the gradient list and the row's PPE slots
         auto append = [&](int j, bool tl, bool tn, bool nb_ok) {
@@ -298,12 +298,14 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
                 if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j;
                 out_n++;
             }
-            if (m_f + m_b >= a.cap) {
+            if (m_f >= a.cap) {
                 overflow = true;
                 return;
             }
-            if (tn) a.lap_col[sell(i, m_f++, a.cap)] = j | kEntryN | (tl ? kEntryL : 0);
-            else a.lap_col[sell(i, a.cap - 1 - m_b++, a.cap)] = j | kEntryL;
+            // every hit in candidate order: the rows of a slice (neighbouring particles, one
+            // candidate sequence) then hold nearby particles at the same entry, which keeps
+            // the solver's gathers of x[col] within few cache lines per warp
+            a.lap_col[sell(i, m_f++, a.cap)] = j | (tn ? kEntryN : 0) | (tl ? kEntryL : 0);
         };
         // band pairs are set aside and decided after the walk, so that the lanes of a warp
         // take the float-float and binary64 tiers together rather than one by one
@@ -351,8 +353,8 @@ __global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
         // ---- dense evaluation and in-place compaction (write slot <= read slot)
         double nd = 0.0, dg = 0.0, hs = 0.0;   // hs: sum of the HS source terms
         int out_l = 0;
-        const int m_all = m_f + m_b;
-        auto slot_of = [&](int t) { return t < m_f ? t : a.cap - m_b + (t - m_f); };
+        const int m_all = m_f;
+        auto slot_of = [&](int t) { return t; };
         if (MIXED) {
             // Two entries per iteration, their pair terms in packed FP32x2 float-float.
             // 1/r: one Newton step (~1e-13) serves the PPE coefficient; n* takes a second
