@@ -313,12 +313,13 @@ __global__ void __launch_bounds__(kBT) k_resid64_t(SellView c, const double* x, 
 // h_out (nonzero, the device-driven solve): the sweep's inner iterations are added to the
 // total and the refinement loop's conditional is set: another sweep while the residual is
 // above the outer target and within the caps (never more than max_outer + 2 sweeps).
-__global__ void __launch_bounds__(kBT) k_resid_ff_t(SellView c, const double* x, const float2* xhl,
+template <int BT = kBT>
+__global__ void __launch_bounds__(BT) k_resid_ff_t(SellView c, const double* x, const float2* xhl,
                                                     double* r, CgScalars* cg,
                                                     cudaGraphConditionalHandle h_out) {
-    __shared__ double sm[kWarps];
+    __shared__ double sm[BT / 32];
     double part = 0.0;
-    for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT) {
+    for (int i = blockIdx.x * BT + threadIdx.x; i < c.n; i += gridDim.x * BT) {
         const double dg = c.diag[i];
         double ri = 0.0;
         if (dg != 0.0) {
@@ -364,8 +365,8 @@ __global__ void __launch_bounds__(kBT) k_resid_ff_t(SellView c, const double* x,
         part = fma(ri, ri, part);
     }
     double tot;
-    part = block_sum<kBT>(part, sm);
-    if (grid_sum<kBT>(part, c.partials, &c.counter[0], &tot, sm) && threadIdx.x == 0) {
+    part = block_sum<BT>(part, sm);
+    if (grid_sum<BT>(part, c.partials, &c.counter[0], &tot, sm) && threadIdx.x == 0) {
         cg->rr = tot;
         if (h_out) {
             cg->total += cg->iters;
@@ -414,12 +415,13 @@ __global__ void __launch_bounds__(kBT) k_start64(SellView c, double* x, double* 
 }
 
 // q = A d, alpha = rho / (d.q)
-__global__ void __launch_bounds__(kBT) k_spmv64_t(SellView c, const double* d, double* q,
+template <int BT = kBT>
+__global__ void __launch_bounds__(BT) k_spmv64_t(SellView c, const double* d, double* q,
                                                   CgScalars* cg) {
     if (*(volatile int*)&cg->done) return;
-    __shared__ double sm[kWarps];
+    __shared__ double sm[BT / 32];
     double part = 0.0;
-    for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT) {
+    for (int i = blockIdx.x * BT + threadIdx.x; i < c.n; i += gridDim.x * BT) {
         const double dg = c.diag[i];
         double qi = 0.0;
         if (dg != 0.0) qi = dg * d[i] - sell_dot64(c, i, d);
@@ -427,21 +429,21 @@ __global__ void __launch_bounds__(kBT) k_spmv64_t(SellView c, const double* d, d
         part = fma(d[i], qi, part);
     }
     double tot;
-    part = block_sum<kBT>(part, sm);
-    if (grid_sum<kBT>(part, c.partials, &c.counter[1], &tot, sm) && threadIdx.x == 0) {
+    part = block_sum<BT>(part, sm);
+    if (grid_sum<BT>(part, c.partials, &c.counter[1], &tot, sm) && threadIdx.x == 0) {
         cg->dq = tot;
         cg->alpha = (tot > 0.0) ? cg->rho / tot : 0.0;
     }
 }
 
 // FP32 operator: stored FP32 coefficients, or recomputed from the FP32 positions at r*
-template <bool MATRIX_FREE>
-__global__ void __launch_bounds__(kBT) k_spmv32_t(SellView c, const float* d, float* q,
-                                                  CgScalars* cg, float coef, float re_f) {
+template <bool MATRIX_FREE, int BT = kBT>
+__global__ void __launch_bounds__(BT) k_spmv32_t(SellView c, const float* d, float* q,
+                                                 CgScalars* cg, float coef, float re_f) {
     if (*(volatile int*)&cg->done) return;
-    __shared__ double sm[kWarps];
+    __shared__ double sm[BT / 32];
     double part = 0.0;
-    for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT) {
+    for (int i = blockIdx.x * BT + threadIdx.x; i < c.n; i += gridDim.x * BT) {
         const float dg = c.diag32[i];
         float qi = 0.f;
         if (dg != 0.f) {
@@ -465,8 +467,8 @@ __global__ void __launch_bounds__(kBT) k_spmv32_t(SellView c, const float* d, fl
         part = fma((double)d[i], (double)qi, part);
     }
     double tot;
-    part = block_sum<kBT>(part, sm);
-    if (grid_sum<kBT>(part, c.partials, &c.counter[1], &tot, sm) && threadIdx.x == 0) {
+    part = block_sum<BT>(part, sm);
+    if (grid_sum<BT>(part, c.partials, &c.counter[1], &tot, sm) && threadIdx.x == 0) {
         cg->dq = tot;
         cg->alpha = (tot > 0.0) ? cg->rho / tot : 0.0;
     }
@@ -598,13 +600,31 @@ static int set_cg_limits(Ctx* c, int max_iters) {
     return MPS_OK;
 }
 
+// The FP32 SpMV runs 512-thread blocks: a block's rows are 512 consecutive slots
+// (neighbouring particles) that share most of their neighbours, so the gathers of x[col]
+// find them in the SM's L1 (256-thread blocks: 5% slower, 128: 25%, 1024: 40%, measured
+// on the 3D dam break).  The float-float residual and the FP64 SpMV, with more registers
+// and bytes per entry, are faster at 256 (512: 18% and 9% slower).
+constexpr int kSpmvBT = 512;
+static int spmv_grid(const Ctx* c) {
+    return (int)std::min<int64_t>((c->n + kSpmvBT - 1) / kSpmvBT, 4096);
+}
+
+static void launch_spmv32(Ctx* c, cudaStream_t s, const SellView& sv) {
+    const float coef = (float)c->coef_ppe, re_f = (float)c->r_lap.re;
+    if (c->prm.ppe_operator == 1)
+        k_spmv32_t<true, kSpmvBT><<<spmv_grid(c), kSpmvBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+    else
+        k_spmv32_t<false, kSpmvBT><<<spmv_grid(c), kSpmvBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+}
+
 // Launch up to `chunk` iterations of FP64 CG (extra launches exit at once once done).
 static void cg64_chunk(Ctx* c, int chunk, double* x, const double* b) {
     const int n = (int)c->n;
     const int gv = vec_grid(c), gs = row_grid(c);
     c->launches += 3 * chunk;
     for (int k = 0; k < chunk; k++) {
-        k_spmv64_t<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), c->cg_d, c->cg_q, c->cg);
+        k_spmv64_t<kBT><<<row_grid(c), kBT, 0, c->stream>>>(sell_view(c, b), c->cg_d, c->cg_q, c->cg);
         k_xr64<<<gv, kBT, 0, c->stream>>>(n, x, c->cg_r, c->cg_d, c->cg_q, c->cg, c->partials,
                                           &c->st->counter[2]);
         k_d64<<<gv, kBT, 0, c->stream>>>(n, c->cg_r, c->cg_d, c->cg);
@@ -614,13 +634,9 @@ static void cg64_chunk(Ctx* c, int chunk, double* x, const double* b) {
 static void cg32_chunk(Ctx* c, int chunk, const double* b) {
     const int n = (int)c->n;
     const int gv = vec_grid(c), gs = row_grid(c);
-    const float coef = (float)c->coef_ppe, re_f = (float)c->r_lap.re;
     c->launches += 3 * chunk;
     for (int k = 0; k < chunk; k++) {
-        if (c->prm.ppe_operator == 1)
-            k_spmv32_t<true><<<gs, kBT, 0, c->stream>>>(sell_view(c, b), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
-        else
-            k_spmv32_t<false><<<gs, kBT, 0, c->stream>>>(sell_view(c, b), c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+        launch_spmv32(c, c->stream, sell_view(c, b));
         k_xr32<<<gv, kBT, 0, c->stream>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_q32, c->cg,
                                           c->partials, &c->st->counter[2]);
         k_d32<<<gv, kBT, 0, c->stream>>>(n, c->cg_r32, c->cg_d32, c->cg, 0);
@@ -690,7 +706,6 @@ static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
     const int n = (int)c->n;
     const int gs = row_grid(c), gv = vec_grid(c);
     const double tol2 = c->prm.cg_tol * c->prm.cg_tol;
-    const float coef = (float)c->coef_ppe, re_f = (float)c->r_lap.re;
     const SellView sv = sell_view(c, c->bvec);
     cudaStream_t s = c->stream;
     const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
@@ -715,10 +730,7 @@ static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
     if (!(n_init = only_node(B))) return MPS_EDEVICE;
     if ((rc = add_while(c, B, n_init, h_in, &n_inner, &Bi))) return rc;
     MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, Bi, nullptr, nullptr, 0, mode));
-    if (c->prm.ppe_operator == 1)
-        k_spmv32_t<true><<<gs, kBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
-    else
-        k_spmv32_t<false><<<gs, kBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+    launch_spmv32(c, s, sv);
     k_xr32<<<gv, kBT, 0, s>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_q32, c->cg, c->partials,
                               &c->st->counter[2]);
     k_d32<<<gv, kBT, 0, s>>>(n, c->cg_r32, c->cg_d32, c->cg, h_in);
@@ -726,7 +738,7 @@ static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
     MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, B, &n_inner, nullptr, 1, mode));
     k_outer_update<<<gv, kBT, 0, s>>>(n, x, c->cg_x32, -1.0, c->cg_xhl, c->cg);
     const bool multi = c->n_scenes > 1;
-    k_resid_ff_t<<<gs, kBT, 0, s>>>(sv, x, c->cg_xhl, c->cg_r, c->cg, multi ? 0 : h_out);
+    k_resid_ff_t<kBT><<<row_grid(c), kBT, 0, s>>>(sv, x, c->cg_xhl, c->cg_r, c->cg, multi ? 0 : h_out);
     if (multi) {   // every scene to its own tolerance, decided on the device
         k_scene_sums<<<c->n_scenes, kBT, 0, s>>>(c->cg_r, c->bvec, c->cell_start, c->scene_shift,
                                                   c->scene_sums);
@@ -837,7 +849,6 @@ int ppe_time_kernel(Ctx* c, int which, int repeats, double* ms, double* bytes) {
     cudaEvent_t e0, e1;
     MPS_CUDA(c, cudaEventCreate(&e0));
     MPS_CUDA(c, cudaEventCreate(&e1));
-    const float coef = (float)c->coef_ppe, re_f = (float)c->r_lap.re;
     float total = 0.f;
     for (int k = 0; k < repeats; k++) {
         // the kernels skip their work once a solve is done: clear the flag (scratch only;
@@ -845,14 +856,11 @@ int ppe_time_kernel(Ctx* c, int which, int repeats, double* ms, double* bytes) {
         MPS_CUDA(c, cudaMemsetAsync(&c->cg->done, 0, sizeof(int), s));
         cudaEventRecord(e0, s);
         if (which == 0) {
-            if (P.ppe_operator == 1)
-                k_spmv32_t<true><<<gs, kBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
-            else
-                k_spmv32_t<false><<<gs, kBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+            launch_spmv32(c, s, sv);
         } else if (which == 1) {
-            k_resid_ff_t<<<gs, kBT, 0, s>>>(sv, c->p, c->cg_xhl, c->cg_r, c->cg, 0);
+            k_resid_ff_t<kBT><<<row_grid(c), kBT, 0, s>>>(sv, c->p, c->cg_xhl, c->cg_r, c->cg, 0);
         } else {
-            k_spmv64_t<<<gs, kBT, 0, s>>>(sv, c->cg_d, c->cg_q, c->cg);
+            k_spmv64_t<kBT><<<row_grid(c), kBT, 0, s>>>(sv, c->cg_d, c->cg_q, c->cg);
         }
         cudaEventRecord(e1, s);
         MPS_CUDA(c, cudaEventSynchronize(e1));
@@ -963,7 +971,7 @@ static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool prima
             }
             total_iters += c->cg_host->iters;
             k_outer_update<<<gv, kBT, 0, c->stream>>>(n, x, c->cg_x32, rr, c->cg_xhl, c->cg);
-            k_resid_ff_t<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), x, c->cg_xhl, c->cg_r, c->cg, 0);
+            k_resid_ff_t<kBT><<<row_grid(c), kBT, 0, c->stream>>>(sell_view(c, b), x, c->cg_xhl, c->cg_r, c->cg, 0);
             if ((rc = read_scalars(c))) return rc;
             rr = c->cg_host->rr;
             outer++;
