@@ -32,6 +32,9 @@ namespace mps {
 
 namespace {
 constexpr int kBT = 128;
+// the build's blocks: 256 rows of neighbouring particles share more of their candidates in
+// L1 (5% faster than 128 on the 3D dam break; the prediction is faster at 128)
+constexpr int kBuildBT = 256;
 
 __device__ __forceinline__ float dist2_f(const float4& a, const float4& b) {
     float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
@@ -263,11 +266,11 @@ constexpr int kSlotMask = kEntryL - 1;
 // KERN, SRC: the weight (0 Eq. 4, 1 cubic) and the PPE source (0 Eq. 13, 1 HS, 2 HS + ECS) as
 // compile-time choices, so that the default instantiation carries none of the options' code
 template <bool MIXED, int KERN, int SRC, bool MULTI>
-__global__ void __launch_bounds__(kBT) k_build(BuildArgs a) {
+__global__ void __launch_bounds__(kBuildBT) k_build(BuildArgs a) {
     // FLUID and WALL rows only (the bucket build's list of them): a DUMMY particle's own n*
     // enters no equation (no free-surface test, no PPE row, no gradient), so it is not
     // evaluated (reported as 0)
-    const int tid = blockIdx.x * kBT + threadIdx.x;
+    const int tid = blockIdx.x * kBuildBT + threadIdx.x;
     const int i = tid < (int)*a.nrows ? a.rows[tid] : -1;
     bool surf = false, ppe = false;
     unsigned n_lap = 0, n_pnd = 0;   // pairs evaluated by this row
@@ -648,15 +651,15 @@ static void launch_build_t(Ctx* c, const BuildArgs& a, int grid) {
     const mps_params& P = c->prm;
     const int src = P.source_term;
     if (P.precision == 1) {
-        if (P.kernel == 1) k_build<true, 1, 0, MULTI><<<grid, kBT, 0, c->stream>>>(a);
-        else if (src == 0) k_build<true, 0, 0, MULTI><<<grid, kBT, 0, c->stream>>>(a);
-        else if (src == 1) k_build<true, 0, 1, MULTI><<<grid, kBT, 0, c->stream>>>(a);
-        else k_build<true, 0, 2, MULTI><<<grid, kBT, 0, c->stream>>>(a);
+        if (P.kernel == 1) k_build<true, 1, 0, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
+        else if (src == 0) k_build<true, 0, 0, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
+        else if (src == 1) k_build<true, 0, 1, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
+        else k_build<true, 0, 2, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
     } else {
-        if (P.kernel == 1) k_build<false, 1, 0, MULTI><<<grid, kBT, 0, c->stream>>>(a);
-        else if (src == 0) k_build<false, 0, 0, MULTI><<<grid, kBT, 0, c->stream>>>(a);
-        else if (src == 1) k_build<false, 0, 1, MULTI><<<grid, kBT, 0, c->stream>>>(a);
-        else k_build<false, 0, 2, MULTI><<<grid, kBT, 0, c->stream>>>(a);
+        if (P.kernel == 1) k_build<false, 1, 0, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
+        else if (src == 0) k_build<false, 0, 0, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
+        else if (src == 1) k_build<false, 0, 1, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
+        else k_build<false, 0, 2, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
     }
 }
 
@@ -713,7 +716,7 @@ void launch_build_rows(Ctx* c) {
     a.diag = c->diag;
     a.diag32 = c->diag32;
     a.p = c->p;
-    const int grid = (int)((c->n + kBT - 1) / kBT);
+    const int grid = (int)((c->n + kBuildBT - 1) / kBuildBT);
     a.sid = c->sid;
     a.scn = c->scn;
     if (c->n_scenes > 1) launch_build_t<true>(c, a, grid);
