@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kBuildBT) k_build(BuildArgs a) {
         const double4 pi = a.pos[i];
         const int cnt = a.vcnt[i];
         const bool with_ppe = (a.pressure_mode == 0);
-        int m_f = 0, out_n = 0;
+        int m_f = 0, out_n = 0, m_n = 0;   // m_n: entries within re_n (number density)
         bool overflow = false;
         // a decided pair: into the gradient list and the row's PPE slots
         auto append = [&](int j, bool tl, bool tn, bool nb_ok) {
@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(kBuildBT) k_build(BuildArgs a) {
             // candidate sequence) then hold nearby particles at the same entry, which keeps
             // the solver's gathers of x[col] within few cache lines per warp
             a.lap_col[sell(i, m_f++, a.cap)] = j | (tn ? kEntryN : 0) | (tl ? kEntryL : 0);
+            m_n += tn ? 1 : 0;
         };
         // band pairs are set aside and decided after the walk, so that the lanes of a warp
         // take the float-float and binary64 tiers together rather than one by one
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(kBuildBT) k_build(BuildArgs a) {
             a.p[i] = ppe ? k * (pow(nd / n0, a.gamma) - 1.0) : 0.0;
         }
         n_lap = (unsigned)out_l;
-        n_pnd = (unsigned)m_f;
+        n_pnd = (unsigned)m_n;
     }
     const unsigned bs = __ballot_sync(0xffffffffu, surf), bp = __ballot_sync(0xffffffffu, ppe);
     for (int o = 16; o > 0; o >>= 1) {

@@ -293,3 +293,22 @@ def test_mixed_precision_drift_over_100_steps():
     dp = np.linalg.norm(out[1]["p"][f] - out[0]["p"][f]) / np.linalg.norm(out[0]["p"][f])
     print(f"mixed vs FP64 after 100 steps: max |dx| = {dx:.3e} l0, relative L2 of p = {dp:.3e}")
     assert dx < 1e-2 and dp < 1e-2
+
+
+def test_work_counters_match_oracle_sets():
+    """The report's work counters (the bench's roofline work) count the pairs the method
+    defines: number-density terms = neighbours of every kind within re_n at r* of the
+    FLUID / WALL particles; PPE coefficients = their non-dummy neighbours within re_lap."""
+    sc = scenes.dam_break_2d(seed=5)
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc, cg_tol=1e-10))
+    prm = oracle_params(sc, cg_tol=1e-10)
+    _, _, _, _, pstar, _, _ = oracle.ppe_system(prm, sc)
+    fw = (sc.types == scenes.FLUID) | (sc.types == scenes.WALL)
+    off_n, ids_n = oracle.neighbors(2, pstar, sc.types, prm.re_n, mode=0)
+    off_l, ids_l = oracle.neighbors(2, pstar, sc.types, prm.re_lap, mode=0)
+    rows_n = np.repeat(np.arange(sc.n), np.diff(off_n))
+    rows_l = np.repeat(np.arange(sc.n), np.diff(off_l))
+    pnd = int(np.count_nonzero(fw[rows_n]))
+    ppe = int(np.count_nonzero(fw[rows_l] & (sc.types[ids_l] != scenes.DUMMY)))
+    assert rep["pairs_pnd"] == pnd
+    assert rep["pairs_ppe"] == ppe
