@@ -276,7 +276,7 @@ def test_default_allocator_and_own_stream():
 
 
 def test_mixed_precision_drift_over_100_steps():
-    """The mixed path's N-step drift against the FP64 path (SURVEY: reported, not bounded
+    """The mixed path's N-step drift against the FP64 path (reported, not bounded
     by the paper): 100 steps of the 2D dam break (10 ms of flow).  Printed for the record;
     the assertion is only a sanity bound far above the single-step error."""
     sc = scenes.dam_break_2d(seed=3)
