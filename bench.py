@@ -62,10 +62,11 @@ FLOPS_PER_PPE_PAIR = 133.0
 FLOPS_PER_PND_PAIR = 62.0
 # FP32 peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one FP32 SpMV launch per PPE coefficient, from the ncu
-# capture in profiles/kernels_dam_break_3d_227k_mixed.md (259.8 + 3.7 MB for 25.19 M
-# coefficients on the 227,136-particle case); traffic scales with the coefficients
-SPMV_TRAFFIC_PER_COEF = (259.8e6 + 3.7e6) / 25.19e6
+# DRAM bytes (read + write) of one FP32 SpMV launch (512-thread blocks) per PPE
+# coefficient, from the ncu capture in profiles/kernels_dam_break_3d_227k_mixed.md
+# (259.9 + 3.5 MB for 25.19 M coefficients on the 227,136-particle case); traffic scales
+# with the coefficients
+SPMV_TRAFFIC_PER_COEF = (259.9e6 + 3.5e6) / 25.19e6
 
 
 def parse():
