@@ -16,7 +16,10 @@
 // matrix-free), FP64 dot products.
 //
 // Reductions are deterministic: per-block partials summed in block order by the last block.
-// Convergence is decided on the device; the host polls one flag per chunk of iterations.
+// Convergence is decided on the device.  The mixed solve (one scene or an ensemble) runs as
+// one CUDA graph whose conditional WHILE nodes the kernels drive (build_mixed_graph below);
+// the FP64 solve, the adjoint solve and ppe_host_loop = 1 poll one flag per chunk of
+// iterations from the host.
 #include <cmath>
 #include <mutex>
 
