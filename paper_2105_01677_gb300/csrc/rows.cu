@@ -5,9 +5,11 @@
 // the number of active lanes.
 //
 // The candidate list of particle i holds every j whose FP32 distance at r^k is below
-// h = max(re_n, re_lap)(1 + s) (plus the FP32 rounding margin).  A pair closer than re_lap
-// at r^k, or closer than max(re) at r* = r^k + dt u*, is in it as long as no particle moves
-// more than s max(re)/2 in the step (checked; MPS_ESKIN otherwise).
+// max(re_n, re_lap)(1 + s') (plus the FP32 rounding margin), s' <= s the list skin the
+// recent motion needs (the cells keep the full skin s).  A pair closer than re_lap at r^k,
+// or closer than max(re) at r* = r^k + dt u*, is in it as long as no particle moves more
+// than s' max(re)/2 in the step (checked: the step is gathered again with the full skin,
+// and MPS_ESKIN past that).
 //
 // Exact predicate r^2 < re^2 of the binary64 definition, in three tiers: the FP32 squared
 // distance decides outside a band of its rounding error; inside it, a float-float distance
