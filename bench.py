@@ -4,7 +4,9 @@
 Workload: 0.40 x 0.60 x 0.30 m water column in a 1.6 x 0.6 x 0.6 m open-top tank,
 l0 = 0.0075 m, 2 wall + 2 dummy layers to full height: 169,600 fluid + 270,432 wall/dummy
 = 440,032 particles; re_n = 2.1 l0, re_lap = 4 l0, dt = 5e-5 s, PPE by CG to a relative
-FP64 residual of 1e-8.  Synthetic seeded lattice with 1e-4 l0 jitter.
+FP64 residual of 1e-8, started from the previous step's solution (--cg-x0 1; the mixed step
+started from zero is reported under "other_x0").  Synthetic seeded lattice with 1e-4 l0
+jitter.
 
 The headline `value` is the mixed-precision path (FP32 pair terms and inner CG, FP64 number
 density, dot products and refinement); the plain FP64 path is timed on the same scene and
@@ -15,7 +17,7 @@ stepped together in one context under "ensemble"; the reverse step (vector-Jacob
 product, FP64) against the forward step on the 3D sloshing tank (85,564 particles) under
 "adjoint".  `e2e` repeats the mixed measurement through the C ABI with host
 buffers: every step uploads positions, velocities and kinds from pinned memory and reads
-back positions, velocities and pressure.
+back positions, velocities and pressure (a written state starts its solve from zero).
 
 --impl reference times the FP64 CPU oracle on the host cores on the same workload (one
 oracle step per bench step).
@@ -43,6 +45,8 @@ import scenes  # noqa: E402
 
 METRIC = "particle-steps/s (3D ~200k dam break) FP64 vs mixed at PPE resid 1e-8; % HBM peak"
 UNIT = "particle-steps/s"
+# the PPE's initial guess (cg_x0); the stop rule is the same FP64 residual either way
+X0_NAMES = {0: "zero", 1: "previous step's solution (before the clamp)"}
 WORKLOAD = "3D dam break, 0.40x0.60x0.30 m column in 1.6x0.6x0.6 m tank, l0=0.0075 m"
 
 # Whole-step algorithmic bytes per particle (matrix-free minimum: every array read or
@@ -96,6 +100,9 @@ def parse():
     ap.add_argument("--ensemble-scenes", type=int, default=256)
     ap.add_argument("--ppe-host-loop", action="store_true",
                     help="drive the mixed PPE solve from the host (profiling: identical results)")
+    ap.add_argument("--cg-x0", type=int, default=1, choices=[0, 1],
+                    help="PPE initial guess: 1 the previous step's solution (default), 0 zero; "
+                         "the full run also times the mixed step with the other one")
     ap.add_argument("--adjoint-steps", type=int, default=20,
                     help="forward and reverse steps timed on the 3D sloshing tank (0: skip)")
     return ap.parse_args()
@@ -228,7 +235,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles": sc.n, "fluid": sc.n_fluid, "dt": 5e-5,
-                   "cg_tol": 1e-8, "l2": "inputs larger than L2"},
+                   "cg_tol": 1e-8, "ppe_x0": X0_NAMES[0], "l2": "inputs larger than L2"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(),
                          "kind": "oracle",
                          "sample": f"{args.steps} oracle steps of the full workload after {args.warmup} warm-up steps"},
@@ -266,7 +273,8 @@ def run_gb300(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
     # --ppe-host-loop: the mixed PPE solve driven from the host instead of one CUDA graph
     # (identical results; ncu cannot profile the kernels of a graph with conditional nodes)
-    common = dict(dt=5e-5, cg_tol=1e-8, ppe_host_loop=1 if args.ppe_host_loop else 0)
+    common = dict(dt=5e-5, cg_tol=1e-8, ppe_host_loop=1 if args.ppe_host_loop else 0,
+                  cg_x0=args.cg_x0)
 
     def timed_steps(sim, k, profile=False):
         if profile:
@@ -424,6 +432,17 @@ def run_gb300(args):
     spmv_ms, spmv_bytes = mps.mps_time_kernel(sim.h, mps.KERNEL_SPMV32, 20)
     resid_ms, resid_bytes = mps.mps_time_kernel(sim.h, mps.KERNEL_RESID_FF, 10)
     sim.close()
+
+    # ---- the same mixed step with the other PPE initial guess
+    other_x0 = 1 - args.cg_x0
+    simz = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, precision=1,
+                          **{**common, "cg_x0": other_x0})
+    simz.step(args.warmup)
+    barrier()
+    ms_z, it_z, _ = timed_steps(simz, args.steps)
+    barrier()
+    ms_z = max_over_ranks(ms_z)
+    simz.close()
 
     # ---- plain FP64 on the same scene
     k64 = args.fp64_steps or args.steps
@@ -584,6 +603,7 @@ def run_gb300(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64 mixed", "data": "synthetic",
         "config": {"workload": WORKLOAD, "particles": n, "fluid": sc.n_fluid, "dt": 5e-5,
                    "cg_tol": 1e-8, "precision": "mixed", "parallelism": f"replicas{world}",
+                   "ppe_x0": X0_NAMES[args.cg_x0],
                    "l2": "flushed (512 MiB write) before every timed step",
                    "fluid_particle_steps_per_s": world * sc.n_fluid * args.steps / (ms_mixed * 1e-3)},
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms_64 / k64, "steps": k64,
@@ -592,6 +612,11 @@ def run_gb300(args):
                                            if prof64["stage_calls"][k] else 0.0)
                                        for k in prof64["stage_ms"]}},
         "mixed_over_fp64": value / value64,
+        "other_x0": {"cg_x0": other_x0, "ppe_x0": X0_NAMES[other_x0],
+                     "value": world * n * args.steps / (ms_z * 1e-3), "unit": UNIT,
+                     "ms_per_step": ms_z / args.steps, "steps": args.steps,
+                     "cg_inner_iters_mean": float(np.mean([x[0] for x in it_z])),
+                     "cg_outer_mean": float(np.mean([x[1] for x in it_z]))},
         "two_phase": two_phase,
         "ensemble": ensemble,
         "adjoint": adjoint,
@@ -602,7 +627,9 @@ def run_gb300(args):
         "cg": {"inner_iters_mean": inner, "outer_mean": outer,
                "resid_max": float(max(x[2] for x in it_mixed))},
         "e2e": {"value": world * n * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h),
+                "ppe_x0": "zero: every step solves from a state written from host memory"
+                          if args.cg_x0 else X0_NAMES[0]},
         "gpu_launches": int(prof["launches"]),
         "roofline": roofline,
         "roofline_build": roofline_build,

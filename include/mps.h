@@ -114,6 +114,12 @@ typedef struct {
                                * conditional nodes (one launch and one read per solve); 1     *
                                * drives them from the host, polling per chunk of iterations.  *
                                * Results are identical.                                        */
+    int32_t cg_x0;            /* PPE initial guess: 0 (default) x0 = 0; 1 the previous solve's *
+                               * solution before the clamp (carried with the particles; zero  *
+                               * before the first solve and after mps_write_state).  The stop *
+                               * rule is unchanged (FP64 ||b - A p|| / ||b|| <= cg_tol); a    *
+                               * step then depends on the previous step's solve at the level  *
+                               * of the tolerance                                               */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;
@@ -147,7 +153,7 @@ typedef struct mps_ctx mps_ctx;
 /* Fill *p with the defaults: dim 2, l0 0.01, re_n 2.1 l0, re_lap 4 l0, rho 1000, nu 1e-6,
  * dt 1e-4, beta 0.97, g (0, -9.81, 0), c0 20, gamma 7, alpha_c 1e-7, cg_tol 1e-8,
  * cg_max_iter 0, precision 0, clamp 1, nbr_cap 0, cell_skin 0.1, box [0,1]^dim,
- * inner_tol 1e-4, max_outer 30, ppe_operator 0, device 0, no stream, no hooks. */
+ * inner_tol 1e-4, max_outer 30, ppe_operator 0, device 0, cg_x0 0, no stream, no hooks. */
 void mps_params_default(mps_params* p);
 
 /* Create a context from n particles (the problem statement of Sec. 3 and the particle kinds

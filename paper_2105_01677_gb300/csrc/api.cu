@@ -144,6 +144,7 @@ int check_params(const mps_params* P) {
     if ((P->alloc == nullptr) != (P->release == nullptr)) return MPS_EINVAL;
     if (P->list_every < 0) return MPS_EINVAL;
     if (P->ppe_host_loop != 0 && P->ppe_host_loop != 1) return MPS_EINVAL;
+    if (P->cg_x0 != 0 && P->cg_x0 != 1) return MPS_EINVAL;
     if (P->kernel < 0 || P->kernel > 1 || P->gradient_form < 0 || P->gradient_form > 1 ||
         P->source_term < 0 || P->source_term > 2 || (P->source_term >= 1 && P->kernel != 0))
         return MPS_EINVAL;
@@ -336,6 +337,10 @@ int allocate(Ctx* c) {
             A(nb_lap_v64, sl)
         }
         A(cg_r, n) A(cg_d, n) A(cg_q, n)
+        if (c->prm.cg_x0 == 1) {
+            A(p0, n) A(p0_alt, n)
+            MPS_CUDA(c, cudaMemsetAsync(c->p0, 0, n * sizeof(double), c->stream));
+        }
     }
     if (c->prm.list_every > 1) A(pos_b, n)
     A(scn, (size_t)c->n_scenes) A(scene_sums, 2 * (size_t)c->n_scenes)
@@ -399,6 +404,7 @@ int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* typ
     }
     launch_ingest(c, d_pos, d_vel, d_t, false, false);
     launch_gather_props(c);   // slot = id again
+    if (c->p0) MPS_CUDA(c, cudaMemsetAsync(c->p0, 0, n * sizeof(double), c->stream));   // cold start
     MPS_CUDA(c, cudaGetLastError());
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
     return MPS_OK;
@@ -556,6 +562,9 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     if (P.pressure_mode == 0) {                                    // 4, 5
         stage_begin(c, MPS_STAGE_PPE);
         if ((rc = ppe_solve(c, rep))) return rc;
+        if (c->p0)   // the next solve starts from this one (cg_x0 = 1)
+            MPS_CUDA(c, cudaMemcpyAsync(c->p0, c->p, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                        c->stream));
         stage_end(c, MPS_STAGE_PPE);
     }
     stage_begin(c, MPS_STAGE_UPDATE);

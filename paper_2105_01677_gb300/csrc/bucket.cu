@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(kBT)
 __global__ void __launch_bounds__(kBT)
     k_permute(const int32_t* perm, int n, const double4* pos, const double4* vel,
               const int8_t* type, const int32_t* id, const double* p, double4* pos_o,
-              double4* vel_o, int8_t* type_o, int32_t* id_o, double* p_o, float4* pos32,
-              float4* pos32lo, float4* vel32, GridDesc g) {
+              double4* vel_o, int8_t* type_o, int32_t* id_o, double* p_o, const double* p0,
+              double* p0_o, float4* pos32, float4* pos32lo, float4* vel32, GridDesc g) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int j = perm[s];
@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(kBT)
     type_o[s] = t;
     id_o[s] = id[j];
     p_o[s] = p[j];
+    if (p0) p0_o[s] = p0[j];   // the PPE's initial guess follows its particle
     float4 h, l;
     split_rel(x.x, g.bmin[0], &h.x, &l.x);
     split_rel(x.y, g.bmin[1], &h.y, &l.y);
@@ -222,16 +223,18 @@ struct BucketPtrs {
     int8_t *type, *type_alt;
     int32_t *id, *id_alt;
     double *p, *p_alt;
+    double *p0, *p0_alt;
 };
 BucketPtrs save_ptrs(const Ctx* c) {
     return {c->key, c->key_alt, c->perm, c->perm_alt, c->pos, c->pos_alt, c->vel, c->vel_alt,
-            c->type, c->type_alt, c->id, c->id_alt, c->p, c->p_alt};
+            c->type, c->type_alt, c->id, c->id_alt, c->p, c->p_alt, c->p0, c->p0_alt};
 }
 void load_ptrs(Ctx* c, const BucketPtrs& b) {
     c->key = b.key; c->key_alt = b.key_alt; c->perm = b.perm; c->perm_alt = b.perm_alt;
     c->pos = b.pos; c->pos_alt = b.pos_alt; c->vel = b.vel; c->vel_alt = b.vel_alt;
     c->type = b.type; c->type_alt = b.type_alt; c->id = b.id; c->id_alt = b.id_alt;
     c->p = b.p; c->p_alt = b.p_alt;
+    c->p0 = b.p0; c->p0_alt = b.p0_alt;
 }
 }  // namespace
 
@@ -322,13 +325,14 @@ static int bucket_launches(Ctx* c, bool mutate) {
     k_occupied<<<nb1, kBT, 0, s>>>(c->key, n, c->grid.ghost_key, c->occ, c->st);
     // permute the state into the new order
     k_permute<<<nb1, kBT, 0, s>>>(c->perm, n, c->pos, c->vel, c->type, c->id, c->p, c->pos_alt,
-                                  c->vel_alt, c->type_alt, c->id_alt, c->p_alt, c->pos32,
-                                  c->pos32lo, c->vel32, c->grid);
+                                  c->vel_alt, c->type_alt, c->id_alt, c->p_alt, c->p0,
+                                  c->p0_alt, c->pos32, c->pos32lo, c->vel32, c->grid);
     std::swap(c->pos, c->pos_alt);
     std::swap(c->vel, c->vel_alt);
     std::swap(c->type, c->type_alt);
     std::swap(c->id, c->id_alt);
     std::swap(c->p, c->p_alt);
+    std::swap(c->p0, c->p0_alt);
     // FLUID rows and FLUID / WALL rows in slot order, for the per-row kernels
     k_mark_rows<<<nb1, kBT, 0, s>>>(n, c->type, c->mark_f, c->mark_fw);
     c->launches += 2 + scan_exclusive(c->mark_f, c->scan_f, n, true, c->scan_scratch, s);

@@ -199,6 +199,8 @@ void launch_check_stage(Ctx* c, const double* d_pos, const double* d_vel, const 
 // solution p can live in (the bucket build swaps p with its alternate buffer).
 struct PpeGraph {
     const double* x = nullptr;
+    const double* x0 = nullptr;   // the initial guess (cg_x0 = 1), or null: x0 = 0
+    bool guess = false;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -269,6 +271,7 @@ struct Ctx {
     int8_t *type, *type_alt;
     int32_t *id, *id_alt;
     double *p, *p_alt;
+    double *p0 = nullptr, *p0_alt = nullptr;   // cg_x0 = 1: the last solve before the clamp
     float4 *pos32, *pos32lo;
     // step buffers
     double4 *pos_star, *vel_star;

@@ -417,6 +417,44 @@ __global__ void __launch_bounds__(kBT) k_start64(SellView c, double* x, double* 
     }
 }
 
+// start of a solve from a given guess (cg_x0 = 1), first kernel: bb = b.b and the targets
+// tol2 bb of the recurrence and of the refinement; the counters of the device-driven solve
+// start one below zero, so that the residual of the guess (the next kernels) is no sweep
+__global__ void __launch_bounds__(kBT) k_bnorm64(SellView c, CgScalars* cg, double tol2) {
+    __shared__ double sm[kWarps];
+    double part = 0.0;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < c.n; i += gridDim.x * kBT)
+        part = fma(c.bvec[i], c.bvec[i], part);
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, c.partials, &c.counter[0], &tot, sm) && threadIdx.x == 0) {
+        cg->bb = tot;
+        cg->stop2 = tol2 * tot;
+        cg->ostop2 = tol2 * tot;
+        cg->iters = 0;
+        cg->outer = -1;
+        cg->total = 0;
+        cg->guard_out = -1;
+    }
+}
+
+// second kernel: x = x0 on the rows of the system, 0 elsewhere (and everywhere when b = 0,
+// whose solution is 0), with its float-float copy; r = b - A x follows (k_resid64_t or
+// k_resid_ff_t)
+__global__ void __launch_bounds__(kBT) k_guess(int n, double* x, const double* x0,
+                                               const double* diag, float2* xhl,
+                                               const CgScalars* cg) {
+    const bool any = cg->bb > 0.0;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) {
+        const double v = (any && diag[i] != 0.0) ? x0[i] : 0.0;
+        x[i] = v;
+        if (xhl) {
+            const float h = (float)v;
+            xhl[i] = make_float2(h, (float)(v - (double)h));
+        }
+    }
+}
+
 // q = A d, alpha = rho / (d.q)
 template <int BT = kBT>
 __global__ void __launch_bounds__(BT) k_spmv64_t(SellView c, const double* d, double* q,
@@ -719,10 +757,34 @@ static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
     MPS_CUDA(c, cudaGraphCreate(&G, 0));
     pg->graph = G;
     MPS_CUDA(c, cudaGraphConditionalHandleCreate(&h_out, G, 0, cudaGraphCondAssignDefault));
+    const bool multi = c->n_scenes > 1;
     MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, G, nullptr, nullptr, 0, mode));
-    k_start64<<<gs, kBT, 0, s>>>(sv, x, c->cg_r, c->cg_d, c->cg, tol2, c->cg_xhl, h_out);
+    if (pg->guess) {
+        // from the previous solution: b.b, x = x0, r = b - A x and the refinement loop's
+        // conditional as after a sweep (per scene in an ensemble)
+        k_bnorm64<<<gs, kBT, 0, s>>>(sv, c->cg, tol2);
+        k_guess<<<gv, kBT, 0, s>>>(n, x, c->p0, c->diag, c->cg_xhl, c->cg);
+        k_resid_ff_t<kBT><<<row_grid(c), kBT, 0, s>>>(sv, x, c->cg_xhl, c->cg_r, c->cg,
+                                                      multi ? 0 : h_out);
+        if (multi) {
+            k_scene_sums<<<c->n_scenes, kBT, 0, s>>>(c->cg_r, c->bvec, c->cell_start,
+                                                      c->scene_shift, c->scene_sums);
+            k_scene_decide<<<1, kBT, 0, s>>>(c->cg, c->scene_sums, c->n_scenes, c->prm.cg_tol,
+                                             h_out);
+        }
+    } else {
+        k_start64<<<gs, kBT, 0, s>>>(sv, x, c->cg_r, c->cg_d, c->cg, tol2, c->cg_xhl, h_out);
+    }
+    {
+        // the last node of the start sequence
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        MPS_CUDA(c, cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+        n_start = (nd == 1) ? deps[0] : nullptr;
+    }
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
-    if (!(n_start = only_node(G))) return MPS_EDEVICE;
+    if (!n_start) return MPS_EDEVICE;
     int rc;
     if ((rc = add_while(c, G, n_start, h_out, &n_outer, &B))) return rc;
     MPS_CUDA(c, cudaGraphConditionalHandleCreate(&h_in, B, 0, cudaGraphCondAssignDefault));
@@ -740,7 +802,6 @@ static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
     MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, B, &n_inner, nullptr, 1, mode));
     k_outer_update<<<gv, kBT, 0, s>>>(n, x, c->cg_x32, -1.0, c->cg_xhl, c->cg);
-    const bool multi = c->n_scenes > 1;
     k_resid_ff_t<kBT><<<row_grid(c), kBT, 0, s>>>(sv, x, c->cg_xhl, c->cg_r, c->cg, multi ? 0 : h_out);
     if (multi) {   // every scene to its own tolerance, decided on the device
         k_scene_sums<<<c->n_scenes, kBT, 0, s>>>(c->cg_r, c->bvec, c->cell_start, c->scene_shift,
@@ -762,13 +823,17 @@ void ppe_graphs_destroy(Ctx* c) {
 }
 
 static int mixed_graph_solve(Ctx* c, double* x, mps_report* rep, int max_total) {
+    // keyed by the solution buffer and the guess buffer (both alternate with the bucket build)
+    const double* x0 = c->p0;
     PpeGraph* pg = nullptr;
     for (PpeGraph& g : c->ppe_graph)
-        if (g.exec && g.x == x) pg = &g;
+        if (g.exec && g.x == x && g.x0 == x0) pg = &g;
     if (!pg) {
         for (PpeGraph& g : c->ppe_graph)
             if (!g.exec) { pg = &g; break; }
-        if (!pg) return MPS_EDEVICE;   // a third buffer: not expected
+        if (!pg) return MPS_EDEVICE;   // a third buffer pair: not expected
+        pg->x0 = x0;
+        pg->guess = x0 != nullptr;
         int rc = build_mixed_graph(c, x, pg);
         if (rc) {
             if (pg->graph) cudaGraphDestroy(pg->graph);
@@ -789,7 +854,8 @@ static int mixed_graph_solve(Ctx* c, double* x, mps_report* rep, int max_total) 
     const bool multi = c->n_scenes > 1;
     // kernels the graph ran: start, per sweep init + update + residual (+ the per-scene sums
     // and decision of an ensemble), per inner iteration 3
-    c->launches += 1 + (multi ? 5 : 3) * (int64_t)h.outer + 3 * (int64_t)h.total;
+    c->launches += (pg->guess ? (multi ? 5 : 3) : 1) + (multi ? 5 : 3) * (int64_t)h.outer +
+                   3 * (int64_t)h.total;
     rep->cg_iters = h.total;
     rep->cg_outer = h.outer;
     c->last_cg_iters = std::max(4, h.total / std::max(h.outer, 1));
@@ -810,7 +876,7 @@ static int mixed_graph_solve(Ctx* c, double* x, mps_report* rep, int max_total) 
     for (int sc = 0; sc < S; sc++) {
         const double rr = hs[2 * sc], bb = hs[2 * sc + 1];
         const double rel = bb > 0.0 ? std::sqrt(rr / bb) : (rr > 0.0 ? HUGE_VAL : 0.0);
-        c->scene_resid[(size_t)sc] = h.outer > 0 ? rel : 0.0;
+        c->scene_resid[(size_t)sc] = (h.outer > 0 || pg->guess) ? rel : 0.0;
         worst = std::max(worst, c->scene_resid[(size_t)sc]);
     }
     rep->cg_resid = worst;
@@ -891,11 +957,25 @@ static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool prima
     if (primary && c->prm.precision == 1 && c->prm.ppe_host_loop == 0)
         return mixed_graph_solve(c, x, rep, max_total);
     if ((rc = set_cg_limits(c, max_total))) return rc;
-    // x = 0, r = b, d = b, rho = |b|^2, stop2 = tol^2 |b|^2
-    k_start64<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), x, c->cg_r, c->cg_d, c->cg, tol2, c->cg_xhl, 0);
-    c->launches += 1;
+    // the step's own solve may start from the previous solution (cg_x0 = 1)
+    const bool guess = primary && c->p0 != nullptr;
+    if (guess) {
+        // bb = |b|^2, stop2 = tol^2 bb; x = x0; r = b - A x (and d = r, rho = |r|^2 in FP64)
+        const SellView sv = sell_view(c, b);
+        k_bnorm64<<<gs, kBT, 0, c->stream>>>(sv, c->cg, tol2);
+        k_guess<<<gv, kBT, 0, c->stream>>>(n, x, c->p0, c->diag, c->cg_xhl, c->cg);
+        if (c->prm.precision == 0)
+            k_resid64_t<<<gs, kBT, 0, c->stream>>>(sv, x, c->cg_r, c->cg_d, c->cg, tol2, 0, 1);
+        else
+            k_resid_ff_t<kBT><<<gs, kBT, 0, c->stream>>>(sv, x, c->cg_xhl, c->cg_r, c->cg, 0);
+        c->launches += 3;
+    } else {
+        // x = 0, r = b, d = b, rho = |b|^2, stop2 = tol^2 |b|^2
+        k_start64<<<gs, kBT, 0, c->stream>>>(sell_view(c, b), x, c->cg_r, c->cg_d, c->cg, tol2, c->cg_xhl, 0);
+        c->launches += 1;
+    }
     if ((rc = read_scalars(c))) return rc;
-    const double bnorm2 = c->cg_host->rr;
+    const double bnorm2 = guess ? c->cg_host->bb : c->cg_host->rr;
     double stop2 = c->cg_host->stop2;
     int total_iters = 0, outer = 0;
     double rel = 0.0;
@@ -940,9 +1020,10 @@ static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool prima
             chunk = 4;
         }
     } else {
-        // mixed: x = 0, r = b already.  Loop: inner FP32 solve, x += e, true residual.
+        // mixed: x = 0, r = b (or x = x0, r = b - A x0) already.  Loop: inner FP32 solve,
+        // x += e, true residual.
         const int max_outer = c->prm.max_outer > 0 ? c->prm.max_outer : 30;
-        double rr = bnorm2;
+        double rr = guess ? c->cg_host->rr : bnorm2;
         for (;;) {
             if (rr <= stop2) {
                 if (!multi) break;

@@ -38,7 +38,7 @@ class mps_params(C.Structure):
                 ("ppe_operator", C.c_int32), ("device", C.c_int32), ("gather_block", C.c_int32),
                 ("list_every", C.c_int32), ("kernel", C.c_int32), ("gradient_form", C.c_int32),
                 ("source_term", C.c_int32), ("ppe_host_loop", C.c_int32),
-                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
+                ("cg_x0", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
                 ("alloc_user", C.c_void_p)]
 
 

@@ -62,7 +62,7 @@ int main(void) {
   P(mps_params, box_max) P(mps_params, inner_tol) P(mps_params, ppe_operator) P(mps_params, stream)
   P(mps_params, alloc) P(mps_params, release) P(mps_params, alloc_user) P(mps_params, list_every)
   P(mps_params, gather_block) P(mps_params, kernel) P(mps_params, source_term)
-  P(mps_params, ppe_host_loop)
+  P(mps_params, ppe_host_loop) P(mps_params, cg_x0)
   P(mps_report, list_gathered)
   P(mps_report, cg_resid) P(mps_report, n_surface) P(mps_report, max_disp) P(mps_report, lambda)
   P(mps_report, steps_done) P(mps_report, cand_tests) P(mps_report, pairs_pnd)
@@ -113,7 +113,7 @@ def test_invalid_arguments_rejected_before_device_use(L):
     for kw in (dict(dim=4), dict(re_n=0.0), dict(dt=-1.0), dict(precision=2),
                dict(box_max=(0.0, 0.0, 0.0)), dict(list_every=-1), dict(kernel=2),
                dict(gradient_form=3), dict(source_term=1, kernel=1), dict(source_term=3),
-               dict(precision=1, ppe_operator=1, kernel=1)):
+               dict(precision=1, ppe_operator=1, kernel=1), dict(cg_x0=2), dict(ppe_host_loop=2)):
         P = mps.mps_params_default(**kw)
         rc = L.mps_create(pos.ctypes.data_as(C.POINTER(C.c_double)), None,
                           t.ctypes.data_as(C.POINTER(C.c_int8)), 3, C.byref(P), C.byref(h))
