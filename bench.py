@@ -374,7 +374,7 @@ def run_gb300(args):
     if args.only == "ensemble":
         E = scenes.ensemble_2d(count=args.ensemble_scenes, seed=args.seed + rank)
         ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
-                           cg_tol=1e-8)
+                           cg_tol=1e-8, cg_x0=args.cg_x0)
         gb = ens.autotune(3)
         ens.step(args.warmup)
         barrier()
@@ -499,7 +499,7 @@ def run_gb300(args):
         E = scenes.ensemble_2d(count=args.ensemble_scenes, seed=args.seed + rank)
         ne = sum(sc.n for sc in E)
         ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
-                           cg_tol=1e-8)
+                           cg_tol=1e-8, cg_x0=args.cg_x0)
         gb = ens.autotune(3)
         ens.step(args.warmup)
         barrier()
@@ -513,6 +513,7 @@ def run_gb300(args):
         ensemble = {"workload": f"{len(E)} independent 2D dam breaks, 500-20,000 fluid particles, "
                                 "column aspect 0.5-2, l0 0.005-0.01 m, dt 1e-4 s",
                     "scenes": len(E), "particles": ne, "fluid": int(sum(sc.n_fluid for sc in E)),
+                    "ppe_x0": X0_NAMES[args.cg_x0],
                     "value": world * ne * ke / (ms_e * 1e-3), "unit": UNIT,
                     "ms_per_step": ms_e / ke, "steps": ke, "gather_block": gb,
                     "cg_iters_mean": float(np.mean([x[0] for x in it_e])),
