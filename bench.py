@@ -71,6 +71,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (259.9 + 3.5 MB for 25.19 M coefficients on the 227,136-particle case); traffic scales
 # with the coefficients
 SPMV_TRAFFIC_PER_COEF = (259.9e6 + 3.5e6) / 25.19e6
+# the same for one launch of the mixed build kernel (256-thread blocks): 549.1 + 510.5 MB
+# for 25.19 M PPE coefficients (its lists and row outputs scale with them)
+BUILD_TRAFFIC_PER_COEF = (549.1e6 + 510.5e6) / 25.19e6
 
 
 def parse():
@@ -564,31 +567,49 @@ def run_gb300(args):
     mean = lambda idx: float(np.mean([x[idx] for x in it_mixed]))
     inner, outer = mean(0), mean(1)
     tests, ppe_pairs, pnd_pairs = mean(3), mean(4), mean(5)
-    # the two single-kernel stages that dominate the step
-    single = {"gather": "k_gather<VerletOp>", "build": "k_build<mixed>"}
-    top = max(single, key=lambda k: per_call[k])
-    if top == "gather":
-        flops = FLOPS_PER_TEST * tests
-    else:
-        flops = FLOPS_PER_PPE_PAIR * ppe_pairs + FLOPS_PER_PND_PAIR * pnd_pairs
-    achieved = flops / (per_call[top] * 1e-3) / 1e12
-    roofline_build = {"bound": "alu", "kernel": single[top], "achieved": achieved,
-                      "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                      "work": {"cand_tests": tests, "pairs_ppe": ppe_pairs, "pairs_pnd": pnd_pairs},
-                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                      "stage_ms_per_step": {k: per_call[k] for k in per_call}}
+    # Rooflines of the step's largest kernels, each from live CUDA-event times: the build
+    # and the gather by their stage timers (one kernel each), the FP32 SpMV and the
+    # float-float residual timed alone after the timed region (they run inside the graph's
+    # conditional loops, where events cannot bracket single launches) times their launches
+    # per step.  `roofline` is the one with the most device time per step.
+    def alu_roofline(kernel, flops, ms):
+        achieved = flops / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": kernel, "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "ms_per_launch": ms, "launches_per_step": 1.0, "ms_per_step": ms}
+    roof_build = alu_roofline("k_build<mixed> (number density, flags, PPE rows)",
+                              FLOPS_PER_PPE_PAIR * ppe_pairs + FLOPS_PER_PND_PAIR * pnd_pairs,
+                              per_call["build"])
+    roof_build["traffic"] = BUILD_TRAFFIC_PER_COEF * ppe_pairs
+    roof_build["work"] = {"pairs_ppe": ppe_pairs, "pairs_pnd": pnd_pairs}
+    roof_gather = alu_roofline("k_gather<VerletOp> (candidate lists)", FLOPS_PER_TEST * tests,
+                               per_call["gather"])
+    roof_gather["traffic"] = None
+    roof_gather["work"] = {"cand_tests": tests}
     spmv_gbs = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_spmv32_t (FP32 SpMV of the inner CG)",
-                "achieved": spmv_gbs, "peak": hbm, "unit": "GB/s", "frac": spmv_gbs / hbm,
-                "traffic": SPMV_TRAFFIC_PER_COEF * ppe_pairs if SPMV_TRAFFIC_PER_COEF else None,
-                "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms,
-                "launches_per_step": inner,
-                "timing": "timed alone after the timed region (CUDA events, 20 launches)",
-                "peak_source": hbm_src + " (burst copy)",
-                "resid_ff": {"achieved": resid_bytes / (resid_ms * 1e-3) / 1e9,
-                             "frac": resid_bytes / (resid_ms * 1e-3) / 1e9 / hbm,
-                             "bytes_per_launch": resid_bytes, "ms_per_launch": resid_ms}}
+    roof_spmv = {"bound": "hbm", "kernel": "k_spmv32_t (FP32 SpMV of the inner CG)",
+                 "achieved": spmv_gbs, "peak": hbm, "unit": "GB/s", "frac": spmv_gbs / hbm,
+                 "traffic": SPMV_TRAFFIC_PER_COEF * ppe_pairs if SPMV_TRAFFIC_PER_COEF else None,
+                 "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms,
+                 "launches_per_step": inner, "ms_per_step": spmv_ms * inner,
+                 "timing": "timed alone after the timed region (CUDA events, 20 launches)",
+                 "peak_source": hbm_src + " (burst copy)"}
+    resid_gbs = resid_bytes / (resid_ms * 1e-3) / 1e9
+    roof_resid = {"bound": "hbm", "kernel": "k_resid_ff_t (float-float FP64 residual)",
+                  "achieved": resid_gbs, "peak": hbm, "unit": "GB/s", "frac": resid_gbs / hbm,
+                  "traffic": None, "bytes_per_launch": resid_bytes, "ms_per_launch": resid_ms,
+                  "launches_per_step": outer + (1 if args.cg_x0 else 0),
+                  "ms_per_step": resid_ms * (outer + (1 if args.cg_x0 else 0)),
+                  "timing": "timed alone after the timed region (CUDA events, 10 launches)",
+                  "peak_source": hbm_src + " (burst copy)"}
+    rooflines = sorted([roof_build, roof_spmv, roof_gather, roof_resid],
+                       key=lambda r: -r["ms_per_step"])
+    step_ms = ms_mixed / args.steps
+    for r in rooflines:
+        r["share_of_step"] = r["ms_per_step"] / step_ms
+    roofline = dict(rooflines[0])
+    roofline["dominant"] = "largest device time per step among the step's kernels"
     step_bytes = n * (STEP_BYTES_FIXED[1] + 57.0 * inner + 65.0 * (outer + 1))
     step_hbm = {"bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms_mixed / args.steps * 1e-3) / 1e9,
                 "peak_gbs": hbm, "frac": step_bytes / (ms_mixed / args.steps * 1e-3) / 1e9 / hbm,
@@ -633,7 +654,8 @@ def run_gb300(args):
                           if args.cg_x0 else X0_NAMES[0]},
         "gpu_launches": int(prof["launches"]),
         "roofline": roofline,
-        "roofline_build": roofline_build,
+        "rooflines": rooflines[1:],
+        "stage_ms_per_step": {k: per_call[k] for k in per_call},
         "step_hbm": step_hbm,
         "cpu_baseline": cpu,
         "clocks": clk,
