@@ -4,9 +4,9 @@
 Workload: 0.40 x 0.60 x 0.30 m water column in a 1.6 x 0.6 x 0.6 m open-top tank,
 l0 = 0.0075 m, 2 wall + 2 dummy layers to full height: 169,600 fluid + 270,432 wall/dummy
 = 440,032 particles; re_n = 2.1 l0, re_lap = 4 l0, dt = 5e-5 s, PPE by CG to a relative
-FP64 residual of 1e-8, started from the previous step's solution (--cg-x0 1; the mixed step
-started from zero is reported under "other_x0").  Synthetic seeded lattice with 1e-4 l0
-jitter.
+FP64 residual of 1e-8, started from the quadratic extrapolation of the last three steps'
+solutions (--cg-x0 3; the mixed step with the other starts, zero included, is reported
+under "other_x0").  Synthetic seeded lattice with 1e-4 l0 jitter.
 
 The headline `value` is the mixed-precision path (FP32 pair terms and inner CG, FP64 number
 density, dot products and refinement); the plain FP64 path is timed on the same scene and
@@ -46,7 +46,9 @@ import scenes  # noqa: E402
 METRIC = "particle-steps/s (3D ~200k dam break) FP64 vs mixed at PPE resid 1e-8; % HBM peak"
 UNIT = "particle-steps/s"
 # the PPE's initial guess (cg_x0); the stop rule is the same FP64 residual either way
-X0_NAMES = {0: "zero", 1: "previous step's solution (before the clamp)"}
+X0_NAMES = {0: "zero", 1: "previous step's solution (before the clamp)",
+            2: "linear extrapolation of the last 2 solutions",
+            3: "quadratic extrapolation of the last 3 solutions"}
 WORKLOAD = "3D dam break, 0.40x0.60x0.30 m column in 1.6x0.6x0.6 m tank, l0=0.0075 m"
 
 # Whole-step algorithmic bytes per particle (matrix-free minimum: every array read or
@@ -103,9 +105,10 @@ def parse():
     ap.add_argument("--ensemble-scenes", type=int, default=256)
     ap.add_argument("--ppe-host-loop", action="store_true",
                     help="drive the mixed PPE solve from the host (profiling: identical results)")
-    ap.add_argument("--cg-x0", type=int, default=1, choices=[0, 1],
-                    help="PPE initial guess: 1 the previous step's solution (default), 0 zero; "
-                         "the full run also times the mixed step with the other one")
+    ap.add_argument("--cg-x0", type=int, default=3, choices=[0, 1, 2, 3],
+                    help="PPE initial guess: 0 zero, 1 the previous step's solution, 2 / 3 "
+                         "its linear / quadratic extrapolation (default 3); the full run also "
+                         "times the mixed step with each of the others")
     ap.add_argument("--adjoint-steps", type=int, default=20,
                     help="forward and reverse steps timed on the 3D sloshing tank (0: skip)")
     return ap.parse_args()
@@ -437,15 +440,22 @@ def run_gb300(args):
     sim.close()
 
     # ---- the same mixed step with the other PPE initial guess
-    other_x0 = 1 - args.cg_x0
-    simz = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, precision=1,
-                          **{**common, "cg_x0": other_x0})
-    simz.step(args.warmup)
-    barrier()
-    ms_z, it_z, _ = timed_steps(simz, args.steps)
-    barrier()
-    ms_z = max_over_ranks(ms_z)
-    simz.close()
+    # the same mixed step with the other PPE initial guesses
+    x0_runs = {}
+    for x0 in (v for v in sorted(X0_NAMES) if v != args.cg_x0):
+        simz = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, precision=1,
+                              **{**common, "cg_x0": x0})
+        simz.step(args.warmup)
+        barrier()
+        ms_z, it_z, _ = timed_steps(simz, args.steps)
+        barrier()
+        ms_z = max_over_ranks(ms_z)
+        simz.close()
+        x0_runs[x0] = {"cg_x0": x0, "ppe_x0": X0_NAMES[x0],
+                       "value": world * n * args.steps / (ms_z * 1e-3), "unit": UNIT,
+                       "ms_per_step": ms_z / args.steps, "steps": args.steps,
+                       "cg_inner_iters_mean": float(np.mean([x[0] for x in it_z])),
+                       "cg_outer_mean": float(np.mean([x[1] for x in it_z]))}
 
     # ---- plain FP64 on the same scene
     k64 = args.fp64_steps or args.steps
@@ -634,11 +644,7 @@ def run_gb300(args):
                                            if prof64["stage_calls"][k] else 0.0)
                                        for k in prof64["stage_ms"]}},
         "mixed_over_fp64": value / value64,
-        "other_x0": {"cg_x0": other_x0, "ppe_x0": X0_NAMES[other_x0],
-                     "value": world * n * args.steps / (ms_z * 1e-3), "unit": UNIT,
-                     "ms_per_step": ms_z / args.steps, "steps": args.steps,
-                     "cg_inner_iters_mean": float(np.mean([x[0] for x in it_z])),
-                     "cg_outer_mean": float(np.mean([x[1] for x in it_z]))},
+        "other_x0": [x0_runs[k] for k in sorted(x0_runs)],
         "two_phase": two_phase,
         "ensemble": ensemble,
         "adjoint": adjoint,

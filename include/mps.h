@@ -114,12 +114,14 @@ typedef struct {
                                * conditional nodes (one launch and one read per solve); 1     *
                                * drives them from the host, polling per chunk of iterations.  *
                                * Results are identical.                                        */
-    int32_t cg_x0;            /* PPE initial guess: 0 (default) x0 = 0; 1 the previous solve's *
-                               * solution before the clamp (carried with the particles; zero  *
-                               * before the first solve and after mps_write_state).  The stop *
-                               * rule is unchanged (FP64 ||b - A p|| / ||b|| <= cg_tol); a    *
-                               * step then depends on the previous step's solve at the level  *
-                               * of the tolerance                                               */
+    int32_t cg_x0;            /* PPE initial guess from the previous steps' solutions before  *
+                               * the clamp (carried with the particles): 0 (default) x0 = 0;  *
+                               * 1 the previous solution; 2 its linear, 3 its quadratic       *
+                               * extrapolation in time from the last 2 or 3 solutions (lower  *
+                               * orders while fewer exist; none before the first solve and    *
+                               * after mps_write_state).  The stop rule is unchanged (FP64    *
+                               * ||b - A p|| / ||b|| <= cg_tol); a step then depends on the   *
+                               * previous steps' solves at the level of the tolerance          */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;

@@ -144,7 +144,7 @@ int check_params(const mps_params* P) {
     if ((P->alloc == nullptr) != (P->release == nullptr)) return MPS_EINVAL;
     if (P->list_every < 0) return MPS_EINVAL;
     if (P->ppe_host_loop != 0 && P->ppe_host_loop != 1) return MPS_EINVAL;
-    if (P->cg_x0 != 0 && P->cg_x0 != 1) return MPS_EINVAL;
+    if (P->cg_x0 < 0 || P->cg_x0 > 3) return MPS_EINVAL;
     if (P->kernel < 0 || P->kernel > 1 || P->gradient_form < 0 || P->gradient_form > 1 ||
         P->source_term < 0 || P->source_term > 2 || (P->source_term >= 1 && P->kernel != 0))
         return MPS_EINVAL;
@@ -337,9 +337,12 @@ int allocate(Ctx* c) {
             A(nb_lap_v64, sl)
         }
         A(cg_r, n) A(cg_d, n) A(cg_q, n)
-        if (c->prm.cg_x0 == 1) {
-            A(p0, n) A(p0_alt, n)
-            MPS_CUDA(c, cudaMemsetAsync(c->p0, 0, n * sizeof(double), c->stream));
+        // the guess history: the last cg_x0 solutions (none valid yet)
+        c->guess_m = std::min(c->prm.cg_x0, Ctx::kGuessMax);
+        c->guess_n = 0;
+        for (int k = 0; k < c->guess_m; k++) {
+            A(ph[k], n) A(ph_alt[k], n)
+            MPS_CUDA(c, cudaMemsetAsync(c->ph[k], 0, n * sizeof(double), c->stream));
         }
     }
     if (c->prm.list_every > 1) A(pos_b, n)
@@ -404,7 +407,7 @@ int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* typ
     }
     launch_ingest(c, d_pos, d_vel, d_t, false, false);
     launch_gather_props(c);   // slot = id again
-    if (c->p0) MPS_CUDA(c, cudaMemsetAsync(c->p0, 0, n * sizeof(double), c->stream));   // cold start
+    c->guess_n = 0;   // a written state starts its solve from zero
     MPS_CUDA(c, cudaGetLastError());
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
     return MPS_OK;
@@ -562,9 +565,15 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     if (P.pressure_mode == 0) {                                    // 4, 5
         stage_begin(c, MPS_STAGE_PPE);
         if ((rc = ppe_solve(c, rep))) return rc;
-        if (c->p0)   // the next solve starts from this one (cg_x0 = 1)
-            MPS_CUDA(c, cudaMemcpyAsync(c->p0, c->p, n * sizeof(double), cudaMemcpyDeviceToDevice,
-                                        c->stream));
+        if (c->guess_m > 0) {
+            // the next solve starts from this one (and the ones before it): shift the history
+            for (int k = c->guess_m - 1; k > 0; k--)
+                MPS_CUDA(c, cudaMemcpyAsync(c->ph[k], c->ph[k - 1], n * sizeof(double),
+                                            cudaMemcpyDeviceToDevice, c->stream));
+            MPS_CUDA(c, cudaMemcpyAsync(c->ph[0], c->p, n * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->stream));
+            c->guess_n = std::min(c->guess_n + 1, c->guess_m);
+        }
         stage_end(c, MPS_STAGE_PPE);
     }
     stage_begin(c, MPS_STAGE_UPDATE);

@@ -151,11 +151,18 @@ __global__ void __launch_bounds__(kBT)
     }
 }
 
+// the previous PPE solutions (cg_x0 >= 1) follow their particles
+struct GuessPerm {
+    const double* in[3];
+    double* out[3];
+    int m;
+};
+
 __global__ void __launch_bounds__(kBT)
     k_permute(const int32_t* perm, int n, const double4* pos, const double4* vel,
               const int8_t* type, const int32_t* id, const double* p, double4* pos_o,
-              double4* vel_o, int8_t* type_o, int32_t* id_o, double* p_o, const double* p0,
-              double* p0_o, float4* pos32, float4* pos32lo, float4* vel32, GridDesc g) {
+              double4* vel_o, int8_t* type_o, int32_t* id_o, double* p_o, GuessPerm gp,
+              float4* pos32, float4* pos32lo, float4* vel32, GridDesc g) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int j = perm[s];
@@ -168,7 +175,7 @@ __global__ void __launch_bounds__(kBT)
     type_o[s] = t;
     id_o[s] = id[j];
     p_o[s] = p[j];
-    if (p0) p0_o[s] = p0[j];   // the PPE's initial guess follows its particle
+    for (int k = 0; k < gp.m; k++) gp.out[k][s] = gp.in[k][j];   // the PPE guess history
     float4 h, l;
     split_rel(x.x, g.bmin[0], &h.x, &l.x);
     split_rel(x.y, g.bmin[1], &h.y, &l.y);
@@ -223,18 +230,22 @@ struct BucketPtrs {
     int8_t *type, *type_alt;
     int32_t *id, *id_alt;
     double *p, *p_alt;
-    double *p0, *p0_alt;
+    double *ph[Ctx::kGuessMax], *ph_alt[Ctx::kGuessMax];
 };
 BucketPtrs save_ptrs(const Ctx* c) {
     return {c->key, c->key_alt, c->perm, c->perm_alt, c->pos, c->pos_alt, c->vel, c->vel_alt,
-            c->type, c->type_alt, c->id, c->id_alt, c->p, c->p_alt, c->p0, c->p0_alt};
+            c->type, c->type_alt, c->id, c->id_alt, c->p, c->p_alt,
+            {c->ph[0], c->ph[1], c->ph[2]}, {c->ph_alt[0], c->ph_alt[1], c->ph_alt[2]}};
 }
 void load_ptrs(Ctx* c, const BucketPtrs& b) {
     c->key = b.key; c->key_alt = b.key_alt; c->perm = b.perm; c->perm_alt = b.perm_alt;
     c->pos = b.pos; c->pos_alt = b.pos_alt; c->vel = b.vel; c->vel_alt = b.vel_alt;
     c->type = b.type; c->type_alt = b.type_alt; c->id = b.id; c->id_alt = b.id_alt;
     c->p = b.p; c->p_alt = b.p_alt;
-    c->p0 = b.p0; c->p0_alt = b.p0_alt;
+    for (int k = 0; k < Ctx::kGuessMax; k++) {
+        c->ph[k] = b.ph[k];
+        c->ph_alt[k] = b.ph_alt[k];
+    }
 }
 }  // namespace
 
@@ -324,15 +335,21 @@ static int bucket_launches(Ctx* c, bool mutate) {
                                       c->scan_scratch, s);
     k_occupied<<<nb1, kBT, 0, s>>>(c->key, n, c->grid.ghost_key, c->occ, c->st);
     // permute the state into the new order
+    GuessPerm gp{};
+    gp.m = c->guess_m;
+    for (int k = 0; k < c->guess_m; k++) {
+        gp.in[k] = c->ph[k];
+        gp.out[k] = c->ph_alt[k];
+    }
     k_permute<<<nb1, kBT, 0, s>>>(c->perm, n, c->pos, c->vel, c->type, c->id, c->p, c->pos_alt,
-                                  c->vel_alt, c->type_alt, c->id_alt, c->p_alt, c->p0,
-                                  c->p0_alt, c->pos32, c->pos32lo, c->vel32, c->grid);
+                                  c->vel_alt, c->type_alt, c->id_alt, c->p_alt, gp, c->pos32,
+                                  c->pos32lo, c->vel32, c->grid);
     std::swap(c->pos, c->pos_alt);
     std::swap(c->vel, c->vel_alt);
     std::swap(c->type, c->type_alt);
     std::swap(c->id, c->id_alt);
     std::swap(c->p, c->p_alt);
-    std::swap(c->p0, c->p0_alt);
+    for (int k = 0; k < c->guess_m; k++) std::swap(c->ph[k], c->ph_alt[k]);
     // FLUID rows and FLUID / WALL rows in slot order, for the per-row kernels
     k_mark_rows<<<nb1, kBT, 0, s>>>(n, c->type, c->mark_f, c->mark_fw);
     c->launches += 2 + scan_exclusive(c->mark_f, c->scan_f, n, true, c->scan_scratch, s);

@@ -74,6 +74,7 @@ struct CgScalars {
     double inner_tol;
     int outer, total, max_outer, max_total;
     int guard_in, guard_out;
+    double gw[3];      // initial guess x0 = sum_k gw[k] ph[k] (cg_x0 >= 1)
 };
 
 struct GridDesc {
@@ -212,7 +213,7 @@ struct BucketGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t launches = 0;
-    void* after[16] = {};
+    void* after[24] = {};
 };
 
 // Work arrays of the reverse step (slot order unless noted), allocated on first use.
@@ -271,7 +272,12 @@ struct Ctx {
     int8_t *type, *type_alt;
     int32_t *id, *id_alt;
     double *p, *p_alt;
-    double *p0 = nullptr, *p0_alt = nullptr;   // cg_x0 = 1: the last solve before the clamp
+    // cg_x0 >= 1: the last guess_m solutions before the clamp (ph[0] the latest), of which
+    // guess_n are valid (0 before the first solve and after a written state)
+    static constexpr int kGuessMax = 3;
+    double* ph[kGuessMax] = {};
+    double* ph_alt[kGuessMax] = {};
+    int guess_m = 0, guess_n = 0;
     float4 *pos32, *pos32lo;
     // step buffers
     double4 *pos_star, *vel_star;

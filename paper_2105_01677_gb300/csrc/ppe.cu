@@ -440,13 +440,22 @@ __global__ void __launch_bounds__(kBT) k_bnorm64(SellView c, CgScalars* cg, doub
 
 // second kernel: x = x0 on the rows of the system, 0 elsewhere (and everywhere when b = 0,
 // whose solution is 0), with its float-float copy; r = b - A x follows (k_resid64_t or
-// k_resid_ff_t)
-__global__ void __launch_bounds__(kBT) k_guess(int n, double* x, const double* x0,
+// k_resid_ff_t).  x0 = sum_k gw[k] h_k over the previous solutions h_0 (latest), h_1, h_2:
+// the previous one (weights 1), or its linear (2, -1) or quadratic (3, -3, 1) extrapolation
+// in time; a zero weight reads nothing
+__global__ void __launch_bounds__(kBT) k_guess(int n, double* x, const double* h0,
+                                               const double* h1, const double* h2,
                                                const double* diag, float2* xhl,
                                                const CgScalars* cg) {
     const bool any = cg->bb > 0.0;
+    const double w0 = cg->gw[0], w1 = cg->gw[1], w2 = cg->gw[2];
     for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) {
-        const double v = (any && diag[i] != 0.0) ? x0[i] : 0.0;
+        double v = 0.0;
+        if (any && diag[i] != 0.0) {
+            if (w0 != 0.0) v = w0 * h0[i];
+            if (w1 != 0.0) v = fma(w1, h1[i], v);
+            if (w2 != 0.0) v = fma(w2, h2[i], v);
+        }
         x[i] = v;
         if (xhl) {
             const float h = (float)v;
@@ -634,9 +643,19 @@ static int read_scalars(Ctx* c) {
     return MPS_OK;
 }
 
+// Weights of the initial guess over the previous solutions: the highest order the valid
+// history allows, up to cg_x0 (1 previous solution, 2 linear, 3 quadratic extrapolation)
+static void guess_weights(const Ctx* c, double* w) {
+    static const double kW[4][3] = {{0.0, 0.0, 0.0}, {1.0, 0.0, 0.0}, {2.0, -1.0, 0.0},
+                                     {3.0, -3.0, 1.0}};
+    const int m = std::min(c->guess_n, c->guess_m);
+    for (int k = 0; k < 3; k++) w[k] = kW[m][k];
+}
+
 static int set_cg_limits(Ctx* c, int max_iters) {
     CgScalars init{};
     init.max_iters = max_iters;
+    guess_weights(c, init.gw);
     MPS_CUDA(c, cudaMemcpyAsync(c->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream));
     return MPS_OK;
 }
@@ -763,7 +782,8 @@ static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
         // from the previous solution: b.b, x = x0, r = b - A x and the refinement loop's
         // conditional as after a sweep (per scene in an ensemble)
         k_bnorm64<<<gs, kBT, 0, s>>>(sv, c->cg, tol2);
-        k_guess<<<gv, kBT, 0, s>>>(n, x, c->p0, c->diag, c->cg_xhl, c->cg);
+        k_guess<<<gv, kBT, 0, s>>>(n, x, c->ph[0], c->ph[1], c->ph[2], c->diag, c->cg_xhl,
+                                   c->cg);
         k_resid_ff_t<kBT><<<row_grid(c), kBT, 0, s>>>(sv, x, c->cg_xhl, c->cg_r, c->cg,
                                                       multi ? 0 : h_out);
         if (multi) {
@@ -823,8 +843,8 @@ void ppe_graphs_destroy(Ctx* c) {
 }
 
 static int mixed_graph_solve(Ctx* c, double* x, mps_report* rep, int max_total) {
-    // keyed by the solution buffer and the guess buffer (both alternate with the bucket build)
-    const double* x0 = c->p0;
+    // keyed by the solution buffer and the guess buffers (all alternate with the bucket build)
+    const double* x0 = c->ph[0];
     PpeGraph* pg = nullptr;
     for (PpeGraph& g : c->ppe_graph)
         if (g.exec && g.x == x && g.x0 == x0) pg = &g;
@@ -846,6 +866,7 @@ static int mixed_graph_solve(Ctx* c, double* x, mps_report* rep, int max_total) 
     init.max_total = max_total;
     init.max_outer = c->prm.max_outer > 0 ? c->prm.max_outer : 30;
     init.inner_tol = c->prm.inner_tol;
+    guess_weights(c, init.gw);
     MPS_CUDA(c, cudaMemcpyAsync(c->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream));
     MPS_CUDA(c, cudaGraphLaunch(pg->exec, c->stream));
     int rc;
@@ -958,12 +979,13 @@ static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool prima
         return mixed_graph_solve(c, x, rep, max_total);
     if ((rc = set_cg_limits(c, max_total))) return rc;
     // the step's own solve may start from the previous solution (cg_x0 = 1)
-    const bool guess = primary && c->p0 != nullptr;
+    const bool guess = primary && c->guess_m > 0;
     if (guess) {
         // bb = |b|^2, stop2 = tol^2 bb; x = x0; r = b - A x (and d = r, rho = |r|^2 in FP64)
         const SellView sv = sell_view(c, b);
         k_bnorm64<<<gs, kBT, 0, c->stream>>>(sv, c->cg, tol2);
-        k_guess<<<gv, kBT, 0, c->stream>>>(n, x, c->p0, c->diag, c->cg_xhl, c->cg);
+        k_guess<<<gv, kBT, 0, c->stream>>>(n, x, c->ph[0], c->ph[1], c->ph[2], c->diag,
+                                           c->cg_xhl, c->cg);
         if (c->prm.precision == 0)
             k_resid64_t<<<gs, kBT, 0, c->stream>>>(sv, x, c->cg_r, c->cg_d, c->cg, tol2, 0, 1);
         else

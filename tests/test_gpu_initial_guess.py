@@ -1,6 +1,8 @@
-"""The PPE started from the previous solve (cg_x0 = 1): the same solution as a cold start to
-the tolerance, oracle parity along a short trajectory, fewer iterations, identical results
-from the device-driven and host-driven loops, and a written state that restarts cold."""
+"""The PPE started from the previous solves (cg_x0 = 1: the previous solution; 2, 3: its
+linear and quadratic extrapolation): the same solution as a cold start to the tolerance,
+oracle parity along a short trajectory, fewer iterations, the lower orders while the
+history is short, identical results from the device-driven and host-driven loops, and a
+written state that restarts cold."""
 import numpy as np
 import pytest
 
@@ -48,16 +50,17 @@ def test_first_step_is_the_cold_start_bitwise(host_loop):
         assert np.array_equal(s0[k], s1[k]), k
 
 
-@pytest.mark.parametrize("scene", ["2d", "3d"])
-def test_guess_trajectory_matches_oracle(scene):
-    """FP64, three steps at the parity tolerance: the second and third solves start from the
-    previous solution; the oracle starts every solve from zero.  The bound is the oracle's
-    own sensitivity to one-ulp changes of the positions over the same steps."""
+@pytest.mark.parametrize("scene,x0", [("2d", 1), ("3d", 1), ("2d", 3), ("3d", 2)])
+def test_guess_trajectory_matches_oracle(scene, x0):
+    """FP64, four steps at the parity tolerance: every solve after the first starts from the
+    previous solutions (or their extrapolation); the oracle starts every solve from zero.
+    The bound is the oracle's own sensitivity to one-ulp changes of the positions over the
+    same steps."""
     sc = _scene(scene)
-    nsteps = 3
+    nsteps = 4
     dt = 1e-4 if sc.dim == 2 else 5e-5
     kw = dict(cg_tol=PARITY_CG_TOL, dt=dt)
-    rc, rep, got, _ = run_gpu(sc, nsteps=nsteps, **gpu_params(sc, cg_x0=1, **kw))
+    rc, rep, got, _ = run_gpu(sc, nsteps=nsteps, **gpu_params(sc, cg_x0=x0, **kw))
     orep, ost, prm = run_oracle(sc, nsteps=nsteps, **kw)
     sens = ulp_sensitivity(sc, nsteps, **kw)
     tol = max(FP64_TOL, 10.0 * max(sens.values()))
@@ -65,12 +68,12 @@ def test_guess_trajectory_matches_oracle(scene):
     assert rep["cg_resid"] <= PARITY_CG_TOL
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_guess_agrees_with_cold_start_and_cuts_iterations(precision):
+@pytest.mark.parametrize("precision,x0", [(0, 1), (1, 1), (1, 2), (1, 3), (0, 3)])
+def test_guess_agrees_with_cold_start_and_cuts_iterations(precision, x0):
     sc = small_3d(seed=3)
     kw = dict(precision=precision, dt=5e-5, cg_tol=1e-8)
     rc_, sc_ = _steps(sc, 6, cg_x0=0, **kw)
-    rw_, sw_ = _steps(sc, 6, cg_x0=1, **kw)
+    rw_, sw_ = _steps(sc, 6, cg_x0=x0, **kw)
     assert all(r["cg_resid"] <= 1e-8 for r in rc_ + rw_)
     cold = sum(r["cg_iters"] for r in rc_[1:])
     warm = sum(r["cg_iters"] for r in rw_[1:])
@@ -81,11 +84,11 @@ def test_guess_agrees_with_cold_start_and_cuts_iterations(precision):
     assert np.array_equal(sw_["flags"], sc_["flags"])
 
 
-@pytest.mark.parametrize("scene,nsteps", [("2d", 5), ("3d", 3)])
-def test_graph_equals_host_loop_with_guess(scene, nsteps):
+@pytest.mark.parametrize("scene,nsteps,x0", [("2d", 5, 1), ("3d", 3, 1), ("2d", 5, 3)])
+def test_graph_equals_host_loop_with_guess(scene, nsteps, x0):
     sc = _scene(scene)
     dt = 1e-4 if sc.dim == 2 else 5e-5
-    out = [_steps(sc, nsteps, precision=1, dt=dt, cg_x0=1, ppe_host_loop=h) for h in (0, 1)]
+    out = [_steps(sc, nsteps, precision=1, dt=dt, cg_x0=x0, ppe_host_loop=h) for h in (0, 1)]
     (rg, sg), (rh, sh) = out
     for a, b in zip(rg, rh):
         assert (a["cg_iters"], a["cg_outer"], a["cg_resid"]) == (b["cg_iters"], b["cg_outer"], b["cg_resid"])
@@ -99,7 +102,7 @@ def test_graph_equals_host_loop_with_guess_ensemble():
     out = []
     for host_loop in (0, 1):
         ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1,
-                           cg_tol=1e-9, ppe_host_loop=host_loop, cg_x0=1)
+                           cg_tol=1e-9, ppe_host_loop=host_loop, cg_x0=2)
         try:
             reps = [ens.step(1)[1] for _ in range(4)]
             out.append((reps, ens.read(), ens.residuals()))
@@ -120,7 +123,7 @@ def test_written_state_restarts_cold():
     from paper_2105_01677_gb300 import mps
     sc = _scene("2d")
     sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
-                         **gpu_params(sc, precision=1, cg_x0=1))
+                         **gpu_params(sc, precision=1, cg_x0=3))
     try:
         sim.step(3)
         s = sim.read()
@@ -135,3 +138,20 @@ def test_written_state_restarts_cold():
     assert (ra["cg_iters"], ra["cg_resid"]) == (rb["cg_iters"], rb["cg_resid"])
     for k in ("pos", "vel", "p", "n_star", "flags"):
         assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_short_history_uses_the_lower_orders(precision):
+    """With k solutions in the history the guess is of order min(k, cg_x0): the first two
+    steps of cg_x0 = 2 are those of cg_x0 = 1 and the first three of cg_x0 = 3 are those of
+    cg_x0 = 2, bit for bit (the same weights over the same buffers); the next step differs."""
+    sc = small_3d(seed=4)
+    kw = dict(precision=precision, dt=5e-5)
+    runs = {x0: _steps(sc, k, cg_x0=x0, **kw) for x0, k in ((1, 3), (2, 4), (3, 4))}
+    for lo, hi, same in ((1, 2, 2), (2, 3, 3)):
+        a, b = runs[lo][0], runs[hi][0]
+        for t in range(same):
+            assert (a[t]["cg_iters"], a[t]["cg_resid"]) == (b[t]["cg_iters"], b[t]["cg_resid"]), (lo, hi, t)
+    # one more step: the higher order changes the iterate path (not the solution's tolerance)
+    a, b = runs[1][0][2], runs[2][0][2]
+    assert a["cg_resid"] != b["cg_resid"]
