@@ -248,6 +248,7 @@ int setup(Ctx* c, const mps_scene* scenes, int n_scenes) {
     c->re_skin = re_skin;
     g.h = hmax;
     g.inv_h = 1.0 / hmax;
+    g.inv_hf = (float)g.inv_h;
     int maxc = 1;
     double X = 0.0;
     for (int a = 0; a < 3; a++) {

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kBT)
         const double xs[3] = {p.x, p.y, p.z};
         bool inside = true;
         for (int a = 0; a < g.dim; a++) {
-            double q = cell_floor(__dsub_rn(xs[a], g.bmin[a]), g.h, g.inv_h);
+            double q = cell_floor(__dsub_rn(xs[a], g.bmin[a]), g.h, g.inv_h, g.inv_hf);
             if (!(q >= 0.0 && q < (double)g.ncell[a])) inside = false;
             else c[a] = (int)q;
         }

@@ -81,6 +81,7 @@ struct GridDesc {
     double bmin[3];
     double h;
     double inv_h;      // 1/h in binary64 (cell_floor)
+    float inv_hf;      // 1/h rounded to binary32 (cell_floor's first tier)
     int ncell[3];
     int bits;
     int dim;
@@ -376,11 +377,21 @@ __host__ __device__ inline void morton_decode(uint32_t key, int dim, int bits, i
         for (int a = 0; a < dim; a++) c[a] |= (int)((key >> (k * dim + a)) & 1u) << k;
 }
 
-// floor(fl(d / h)) -- the cell coordinate of the binary64 definition -- mostly without the
-// division: q = fl(d fl(1/h)) differs from fl(d/h) by at most ~3 ulp of |d/h|, so the two
-// have the same floor unless q lies within 4 ulp of an integer, and only there is the
-// quotient formed by the (slow) binary64 division.
-__device__ __forceinline__ double cell_floor(double d, double h, double inv_h) {
+// floor(fl(d / h)) -- the cell coordinate of the binary64 definition -- mostly without
+// binary64 arithmetic, in three tiers:
+//   1. binary32: qf = fl32(fl32(d) fl32(1/h)) carries three binary32 roundings, so
+//      |qf - d/h| <= ~3 2^-24 |d/h| (1.8e-7 relative) and fl(d/h) is within 2^-53 of d/h:
+//      both have the same floor unless qf lies within that of an integer (a margin of 2.7x:
+//      4.8e-7 max(|qf|, 1)); qf - floor(qf) and floor(qf) + 1 - qf are exact;
+//   2. binary64 q = fl(d fl(1/h)), within ~3 ulp of d/h: decided unless q lies within
+//      4 ulp of an integer;
+//   3. the (slow) binary64 division itself.
+// Non-finite inputs fail both comparisons and reach the division.
+__device__ __forceinline__ double cell_floor(double d, double h, double inv_h, float inv_hf) {
+    const float qf = __fmul_rn(__double2float_rn(d), inv_hf);
+    const float ff = floorf(qf);
+    const float gapf = fminf(qf - ff, (ff + 1.0f) - qf);
+    if (gapf > 4.8e-7f * fmaxf(fabsf(qf), 1.0f)) return (double)ff;
     const double q = d * inv_h;
     const double f = floor(q);
     const double gap = fmin(q - f, (f + 1.0) - q);

@@ -139,7 +139,7 @@ __device__ __forceinline__ double gradient_row(int i, const int8_t* type, const 
     const double xs[3] = {xn.x, xn.y, xn.z};
     bool inside = isfinite(un.x) && isfinite(un.y) && isfinite(un.z);
     for (int a = 0; a < g.dim; a++) {
-        const double q = cell_floor(__dsub_rn(xs[a], g.bmin[a]), g.h, g.inv_h);
+        const double q = cell_floor(__dsub_rn(xs[a], g.bmin[a]), g.h, g.inv_h, g.inv_hf);
         if (!(q >= 0.0 && q < (double)g.ncell[a])) inside = false;
     }
     if (!inside) atomicAdd(&kp.st->leave, 1u);

@@ -55,10 +55,20 @@ def _key_scenes():
     sc.pos[30:40, 1] = sc.box_max[1] + 0.01
     sc.pos[40:50, 2] = sc.box_min[2] - 1e-12
     out.append(sc)
+    # coordinates a relative 1e-10 ... 1e-5 of a cell side either side of cell faces: the
+    # binary32 first tier of the cell floor decides the far ones, binary64 the near ones
+    sc = scenes.random_cloud(3000, 3, seed=6)
+    h = 4.0 * sc.l0 * 1.1
+    rng = np.random.default_rng(6)
+    m = 2400
+    face = rng.integers(0, 8, size=(m, 3))
+    rel = 10.0 ** rng.uniform(-10, -5, size=(m, 3)) * rng.choice([-1.0, 1.0], size=(m, 3))
+    sc.pos[:m] = sc.box_min + (face + rel) * h
+    out.append(sc)
     return out
 
 
-@pytest.mark.parametrize("idx", range(6))
+@pytest.mark.parametrize("idx", range(7))
 def test_cell_keys_bit_exact(idx):
     sc = _key_scenes()[idx]
     mps = _mps()
