@@ -1,7 +1,8 @@
 // bucket.cu -- bucket build of the cell-linked list (Sec. 4.1).
 //
 // Per step, at the current positions r^k:
-//   1. cell key of every particle: c = floor((x - box_min)/h) per axis in binary64, Morton
+//   1. cell key of every particle: c = floor((x - box_min)/h) per axis as in binary64
+//      (decided in binary32 where its error bound allows, see cell_floor), Morton
 //      interleave (x in bit 0); a particle outside the grid becomes a GHOST and sorts last;
 //      in an ensemble the key is prefixed by the particle's scene (scene-major order) and
 //      the GHOST test uses the scene's own grid;
