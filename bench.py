@@ -61,9 +61,10 @@ STEP_BYTES_FIXED = {0: 182.0 + 97.0 + 42.0 + 146.0, 1: 182.0 + 113.0 + 42.0 + 14
 # Algorithmic FP32 flops (fused multiply-add = 2) of the ALU-bound kernels, per unit of
 # work counted live by the library:
 #   candidate gather: 8 per distance test (3 differences, 1 square, 2 fused squares);
-#   build (mixed): 133 per PPE coefficient in float-float (distance 70, one Newton step
-#   for 1/r 31, coefficient and diagonal sum 32) and 62 more per number-density term
-#   (second Newton step 31, weight and sum 31).
+#   build (mixed): 8 per candidate-list entry classified at r* (the distance test, as in
+#   the gather), 133 per PPE coefficient in float-float (distance 70, one Newton step for
+#   1/r 31, coefficient and diagonal sum 32) and 62 more per number-density term (second
+#   Newton step 31, weight and sum 31).
 FLOPS_PER_TEST = 8.0
 FLOPS_PER_PPE_PAIR = 133.0
 FLOPS_PER_PND_PAIR = 62.0
@@ -296,7 +297,7 @@ def run_gb300(args):
             rc, rep = sim.step(1)
             e_ev[i].record(stream)
             iters.append((rep["cg_iters"], rep["cg_outer"], rep["cg_resid"], rep["cand_tests"],
-                          rep["pairs_ppe"], rep["pairs_pnd"]))
+                          rep["pairs_ppe"], rep["pairs_pnd"], rep["list_tests"]))
         torch.cuda.synchronize(dev)
         for i in range(k):
             total += s_ev[i].elapsed_time(e_ev[i])
@@ -594,7 +595,7 @@ def run_gb300(args):
     per_call = {k: (st_ms[k] / st_calls[k] if st_calls[k] else 0.0) for k in st_ms}
     mean = lambda idx: float(np.mean([x[idx] for x in it_mixed]))
     inner, outer = mean(0), mean(1)
-    tests, ppe_pairs, pnd_pairs = mean(3), mean(4), mean(5)
+    tests, ppe_pairs, pnd_pairs, list_tests = mean(3), mean(4), mean(5), mean(6)
     # Rooflines of the step's largest kernels, each from live CUDA-event times: the build
     # and the gather by their stage timers (one kernel each), the FP32 SpMV and the
     # float-float residual timed alone after the timed region (they run inside the graph's
@@ -607,10 +608,11 @@ def run_gb300(args):
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                 "ms_per_launch": ms, "launches_per_step": 1.0, "ms_per_step": ms}
     roof_build = alu_roofline("k_build<mixed> (number density, flags, PPE rows)",
-                              FLOPS_PER_PPE_PAIR * ppe_pairs + FLOPS_PER_PND_PAIR * pnd_pairs,
-                              per_call["build"])
+                              FLOPS_PER_PPE_PAIR * ppe_pairs + FLOPS_PER_PND_PAIR * pnd_pairs +
+                              FLOPS_PER_TEST * list_tests, per_call["build"])
     roof_build["traffic"] = BUILD_TRAFFIC_PER_COEF * ppe_pairs
-    roof_build["work"] = {"pairs_ppe": ppe_pairs, "pairs_pnd": pnd_pairs}
+    roof_build["work"] = {"pairs_ppe": ppe_pairs, "pairs_pnd": pnd_pairs,
+                          "list_tests": list_tests}
     roof_gather = alu_roofline("k_gather<VerletOp> (candidate lists)", FLOPS_PER_TEST * tests,
                                per_call["gather"])
     roof_gather["traffic"] = None

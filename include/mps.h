@@ -147,6 +147,8 @@ typedef struct {
     int64_t cand_tests;       /* distance tests of the cell gather (candidate lists)          */
     int64_t pairs_ppe;        /* PPE coefficients evaluated (non-dummy pairs within re_lap)   */
     int64_t pairs_pnd;        /* number-density terms evaluated (pairs within re_n)           */
+    int64_t list_tests;       /* candidate-list entries classified at r* (distance tests of  *
+                               * the number-density / PPE assembly)                           */
 } mps_report;
 
 /* Opaque context: device buffers, stream and derived constants of one particle system. */

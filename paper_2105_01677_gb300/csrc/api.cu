@@ -531,6 +531,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         rep->cand_tests = (int64_t)s.cand_tests;
         rep->pairs_ppe = (int64_t)s.pairs_lap;
         rep->pairs_pnd = (int64_t)s.pairs_n;
+        rep->list_tests = (int64_t)s.list_tests;
         rep->n0_pnd = c->n0_pnd;
         rep->n0_lap = c->n0_lap;
         rep->lambda = c->lambda;

@@ -52,6 +52,7 @@ struct DevStatus {
     unsigned long long max_disp_next_bits;   // kept lists: max squared |r^{k+1} - r_b| (as above)
     unsigned int gather_next;           // next occupied cell of the candidate gather (dynamic)
     unsigned int pad1;
+    unsigned long long list_tests;      // candidate-list entries classified by the build (at r*)
 };
 
 // Scalars of one CG solve; updated by the last block of each reduction kernel.

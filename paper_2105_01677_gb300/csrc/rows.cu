@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(kBuildBT) k_build(BuildArgs a) {
     const int i = tid < (int)*a.nrows ? a.rows[tid] : -1;
     bool surf = false, ppe = false;
     unsigned n_lap = 0, n_pnd = 0;   // pairs evaluated by this row
+    unsigned n_cand = 0;             // candidate-list entries it classified
     if (i >= 0) {
         Radius rn = a.rn, rl = a.rl;
         double coef_ppe = a.coef_ppe, coef0 = a.coef0, n0 = a.n0;
@@ -500,13 +501,16 @@ __global__ void __launch_bounds__(kBuildBT) k_build(BuildArgs a) {
         }
         n_lap = (unsigned)out_l;
         n_pnd = (unsigned)m_n;
+        n_cand = (unsigned)cnt;
     }
     const unsigned bs = __ballot_sync(0xffffffffu, surf), bp = __ballot_sync(0xffffffffu, ppe);
     for (int o = 16; o > 0; o >>= 1) {
         n_lap += __shfl_xor_sync(0xffffffffu, n_lap, o);
         n_pnd += __shfl_xor_sync(0xffffffffu, n_pnd, o);
+        n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
     }
     if ((threadIdx.x & 31) == 0) {
+        if (n_cand) atomicAdd(&a.st->list_tests, (unsigned long long)n_cand);
         if (bs) atomicAdd(&a.st->n_surface, (unsigned)__popc(bs));
         if (bp) atomicAdd(&a.st->n_ppe, (unsigned)__popc(bp));
         if (n_lap) atomicAdd(&a.st->pairs_lap, (unsigned long long)n_lap);

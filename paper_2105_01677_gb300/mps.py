@@ -52,7 +52,7 @@ class mps_report(C.Structure):
                 ("n_ghost", C.c_int64), ("n_ppe_rows", C.c_int64), ("max_disp", C.c_double),
                 ("n0_pnd", C.c_double), ("n0_lap", C.c_double), ("lambda_", C.c_double),
                 ("steps_done", C.c_int64), ("cand_tests", C.c_int64), ("pairs_ppe", C.c_int64),
-                ("pairs_pnd", C.c_int64)]
+                ("pairs_pnd", C.c_int64), ("list_tests", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

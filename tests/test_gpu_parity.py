@@ -322,3 +322,8 @@ def test_work_counters_match_oracle_sets():
     ppe = int(np.count_nonzero(fw[rows_l] & (sc.types[ids_l] != scenes.DUMMY)))
     assert rep["pairs_pnd"] == pnd
     assert rep["pairs_ppe"] == ppe
+    # the build classifies every FLUID / WALL row's candidate list: a superset of each row's
+    # neighbours within max(re) at r*, within what the gather's tests produced
+    off_h, ids_h = oracle.neighbors(2, pstar, sc.types, prm.re_lap, mode=0)
+    within = int(np.count_nonzero(fw[np.repeat(np.arange(sc.n), np.diff(off_h))]))
+    assert within <= rep["list_tests"] <= rep["cand_tests"]
