@@ -260,15 +260,22 @@ constexpr int kEntryN = 1 << 30;   // within re_n: contributes to n*
 constexpr int kEntryL = 1 << 29;   // non-dummy within re_lap: a PPE coefficient
 constexpr int kSlotMask = kEntryL - 1;
 
-// Two passes per row.  Classification walks the candidate list, decides the predicates
-// (FP32 / float-float / binary64 tiers) and writes the hits into the row's PPE slots in
-// candidate order (band pairs, decided after the walk, last).  The dense pass then
-// evaluates every hit with (nearly) all lanes of the warp busy, accumulates n* and the
-// diagonal, and compacts the PPE coefficients in place to the front of the row.
+// Mixed precision: one walk per row over the candidate list, two candidates at a time in
+// packed float-float: the squared distance decides membership (float-float outside a band
+// of its error around re^2, binary64 inside it), n* and the diagonal are accumulated and
+// the PPE coefficients and gradient neighbours written in candidate order.  Nine in ten
+// candidates are members, so evaluating every candidate wastes little.
+// FP64: two passes.  Classification decides the predicates (FP32 / float-float / binary64
+// tiers) and writes the hits into the row's PPE slots in candidate order (band pairs,
+// decided after the walk, last); the dense pass evaluates every hit with (nearly) all
+// lanes busy and compacts the PPE coefficients in place to the front of the row.
+// Registers: the default mixed and the FP64 instantiations fit 64 (four 256-thread blocks
+// per SM); the options and the ensemble's take up to 85 (three).
 // KERN, SRC: the weight (0 Eq. 4, 1 cubic) and the PPE source (0 Eq. 13, 1 HS, 2 HS + ECS) as
 // compile-time choices, so that the default instantiation carries none of the options' code
 template <bool MIXED, int KERN, int SRC, bool MULTI>
-__global__ void __launch_bounds__(kBuildBT) k_build(BuildArgs a) {
+__global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && SRC == 0))) ? 4 : 3)
+    k_build(BuildArgs a) {
     // FLUID and WALL rows only (the bucket build's list of them): a DUMMY particle's own n*
     // enters no equation (no free-surface test, no PPE row, no gradient), so it is not
     // evaluated (reported as 0)
@@ -314,8 +321,10 @@ __global__ void __launch_bounds__(kBuildBT) k_build(BuildArgs a) {
             a.lap_col[sell(i, m_f++, a.cap)] = j | (tn ? kEntryN : 0) | (tl ? kEntryL : 0);
             m_n += tn ? 1 : 0;
         };
-        // band pairs are set aside and decided after the walk, so that the lanes of a warp
-        // take the float-float and binary64 tiers together rather than one by one
+        // FP64 path: classification first (the mixed path decides membership inside its
+        // single walk below).  Band pairs are set aside and decided after the walk, so that
+        // the lanes of a warp take the float-float and binary64 tiers together
+        if (!MIXED) {
         constexpr int kPend = 16;
         int pend[kPend];
         int np = 0;
@@ -357,6 +366,7 @@ __global__ void __launch_bounds__(kBuildBT) k_build(BuildArgs a) {
             if (tn == 2) tn = decide_band(r2f, rn, a.pos, pi, j) ? 1 : 0;
             append(j, tl, tn, nb_ok);
         }
+        }
         // ---- dense evaluation and in-place compaction (write slot <= read slot)
         double nd = 0.0, dg = 0.0, hs = 0.0;   // hs: sum of the HS source terms
         int out_l = 0;
@@ -376,30 +386,62 @@ __global__ void __launch_bounds__(kBuildBT) k_build(BuildArgs a) {
             const ff2 coef = {f2(-ncoef_ff.h), f2(-ncoef_ff.l)};
             const ff2 invn = {f2(rn.inv_f), f2(rn.inv_l)}, invl = {f2(rl.inv_f), f2(rl.inv_l)};
             const double4 ui = SRC >= 1 ? a.vel_star[i] : make_double4(0.0, 0.0, 0.0, 0.0);
-            // the entries of the next pair are loaded one iteration ahead (each slot is
-            // read before the compaction can write it: writes go to slots <= t + 1)
-            int n0 = m_all > 0 ? a.lap_col[sell(i, slot_of(0), a.cap)] : 0;
-            int n1 = m_all > 1 ? a.lap_col[sell(i, slot_of(1), a.cap)] : n0;
-            for (int t = 0; t < m_all; t += 2) {
-                const bool two = t + 1 < m_all;
-                const int e0 = n0, e1 = n1;
-                if (t + 2 < m_all) {
-                    n0 = a.lap_col[sell(i, slot_of(t + 2), a.cap)];
-                    n1 = t + 3 < m_all ? a.lap_col[sell(i, slot_of(t + 3), a.cap)] : n0;
+            // One walk over the candidate list, two candidates per iteration: the float-float
+            // squared distance decides membership (the second tier of the exact predicate:
+            // outside the ff_tol band around re^2, binary64 inside it) and the members' terms
+            // are evaluated at once, in candidate order.  The slots of the next pair are
+            // loaded one iteration ahead.
+            int s0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
+            int s1 = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : s0;
+            for (int t = 0; t < cnt; t += 2) {
+                const bool two = t + 1 < cnt;
+                const int j0 = s0, j1 = s1;
+                if (t + 2 < cnt) {
+                    s0 = a.vcol[sell(i, t + 2, a.cap_v)];
+                    s1 = t + 3 < cnt ? a.vcol[sell(i, t + 3, a.cap_v)] : s0;
                 }
-                const int j0 = e0 & kSlotMask, j1 = e1 & kSlotMask;
                 const float4 h0 = a.pos32[j0], l0 = a.pos32lo[j0];
                 const float4 h1 = a.pos32[j1], l1 = a.pos32lo[j1];
                 const ff2 dx = ff2_diff(ih.x, il.x, make_float2(h0.x, h1.x), make_float2(l0.x, l1.x));
                 const ff2 dy = ff2_diff(ih.y, il.y, make_float2(h0.y, h1.y), make_float2(l0.y, l1.y));
                 const ff2 dz = ff2_diff(ih.z, il.z, make_float2(h0.z, h1.z), make_float2(l0.z, l1.z));
                 const ff2 r2 = ff2_dist2(dx, dy, dz);
+                // membership: d = r^2 - re^2 in float-float, decided outside [-ff_tol, ff_tol]
+                const float2 dn = add2(sub2(r2.h, f2(rn.re2_h)), sub2(r2.l, f2(rn.re2_l)));
+                bool tn0 = dn.x <= -rn.ff_tol ||
+                           (dn.x < rn.ff_tol && exact_dist2(pi, a.pos[j0]) < rn.re2);
+                bool tn1 = two && (dn.y <= -rn.ff_tol ||
+                                   (dn.y < rn.ff_tol && exact_dist2(pi, a.pos[j1]) < rn.re2));
+                const bool nb0 = kind_of(h0) != kDummy, nb1 = kind_of(h1) != kDummy;
+                bool tl0 = false, tl1 = false;
+                if (with_ppe) {
+                    const float2 dl = add2(sub2(r2.h, f2(rl.re2_h)), sub2(r2.l, f2(rl.re2_l)));
+                    tl0 = nb0 && (dl.x <= -rl.ff_tol ||
+                                  (dl.x < rl.ff_tol && exact_dist2(pi, a.pos[j0]) < rl.re2));
+                    tl1 = two && nb1 && (dl.y <= -rl.ff_tol ||
+                                         (dl.y < rl.ff_tol && exact_dist2(pi, a.pos[j1]) < rl.re2));
+                }
+                // a member at zero distance (coincident to float-float) is an error unless
+                // binary64 separates it; either way it adds no term
                 const bool ok0 = r2.h.x > 0.f, ok1 = two && r2.h.y > 0.f;
-                if (!ok0 && !(exact_dist2(pi, a.pos[j0]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
-                if (two && !ok1 && !(exact_dist2(pi, a.pos[j1]) > 0.0))
+                if ((tn0 || tl0) && !ok0 && !(exact_dist2(pi, a.pos[j0]) > 0.0))
                     atomicOr(&a.st->err, kErrCoincident);
-                const bool tn0 = ok0 && (e0 & kEntryN), tl0 = ok0 && (e0 & kEntryL);
-                const bool tn1 = ok1 && (e1 & kEntryN), tl1 = ok1 && (e1 & kEntryL);
+                if ((tn1 || tl1) && !ok1 && !(exact_dist2(pi, a.pos[j1]) > 0.0))
+                    atomicOr(&a.st->err, kErrCoincident);
+                // the gradient list: non-dummy members within re_n, in candidate order
+                if (tn0 && nb0) {
+                    if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j0;
+                    out_n++;
+                }
+                if (tn1 && nb1) {
+                    if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j1;
+                    out_n++;
+                }
+                m_n += (tn0 ? 1 : 0) + (tn1 ? 1 : 0);
+                tn0 = tn0 && ok0;
+                tn1 = tn1 && ok1;
+                tl0 = tl0 && ok0;
+                tl1 = tl1 && ok1;
                 const ff2 y = ff2_rsqrt1(r2);
                 ff2 w = {f2(0.f), f2(0.f)};
                 if (tn0 || tn1) {
@@ -428,16 +470,24 @@ __global__ void __launch_bounds__(kBuildBT) k_build(BuildArgs a) {
                 acc = ff2_add(acc, {make_float2(tn1 ? w.h.y : 0.f, tl1 ? c.h.y : 0.f),
                                     make_float2(tn1 ? w.l.y : 0.f, tl1 ? c.l.y : 0.f)});
                 if (tl0) {
-                    const size_t q = sell(i, out_l++, a.cap);
-                    a.lap_col[q] = j0;
-                    a.lap_v32[q] = c.h.x;
-                    a.lap_vlo[q] = c.l.x;
+                    if (out_l < a.cap) {
+                        const size_t q = sell(i, out_l++, a.cap);
+                        a.lap_col[q] = j0;
+                        a.lap_v32[q] = c.h.x;
+                        a.lap_vlo[q] = c.l.x;
+                    } else {
+                        overflow = true;
+                    }
                 }
                 if (tl1) {
-                    const size_t q = sell(i, out_l++, a.cap);
-                    a.lap_col[q] = j1;
-                    a.lap_v32[q] = c.h.y;
-                    a.lap_vlo[q] = c.l.y;
+                    if (out_l < a.cap) {
+                        const size_t q = sell(i, out_l++, a.cap);
+                        a.lap_col[q] = j1;
+                        a.lap_v32[q] = c.h.y;
+                        a.lap_vlo[q] = c.l.y;
+                    } else {
+                        overflow = true;
+                    }
                 }
             }
             nd = ff_to_double_fast(ff2_lo(acc));
