@@ -75,9 +75,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # (259.9 + 3.5 MB for 25.19 M coefficients on the 227,136-particle case); traffic scales
 # with the coefficients
 SPMV_TRAFFIC_PER_COEF = (259.9e6 + 3.5e6) / 25.19e6
-# the same for one launch of the mixed build kernel (256-thread blocks): 549.1 + 510.5 MB
-# for 25.19 M PPE coefficients (its lists and row outputs scale with them)
-BUILD_TRAFFIC_PER_COEF = (549.1e6 + 510.5e6) / 25.19e6
+# the same for one launch of the mixed build kernel (one walk per row, 256-thread blocks):
+# 478.6 + 557.3 MB for 25.19 M PPE coefficients (its lists and row outputs scale with them)
+BUILD_TRAFFIC_PER_COEF = (478.6e6 + 557.3e6) / 25.19e6
 
 
 def parse():
