@@ -115,8 +115,14 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
             coef_lap = sp.coef_lap;
         }
         const float4 ih = a.pos32[i], il = a.pos32lo[i];
-        const double4 pi = a.pos[i];
-        const double4 ui = a.vel[i];
+        // the binary64 state of i: held through the walk on the FP64 path; the mixed path
+        // reads it in the rare binary64 tier and after the walk, which leaves it registers
+        // for the neighbour's velocity in flight
+        double4 pi = make_double4(0.0, 0.0, 0.0, 0.0), ui = pi;
+        if (!MIXED) {
+            pi = a.pos[i];
+            ui = a.vel[i];
+        }
         const float4 u32 = a.vel32[i];
         const int cnt = a.vcnt[i];
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
@@ -126,24 +132,32 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
         int jn = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : 0;
         int j0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
         float4 qn = a.pos32[j0];
+        // mixed: the FP32 velocity of k+1 is in flight with its position (nearly every
+        // candidate is a member)
+        float4 vn = MIXED ? a.vel32[j0] : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int k = 0; k < cnt; k++) {
             const int j = j0;
             const float4 jh = qn;
+            const float4 vj = vn;
             j0 = jn;
-            if (k + 1 < cnt) qn = a.pos32[jn];
+            if (k + 1 < cnt) {
+                qn = a.pos32[jn];
+                if (MIXED) vn = a.vel32[jn];
+            }
             if (k + 2 < cnt) jn = a.vcol[sell(i, k + 2, a.cap_v)];
             const float r2 = dist2_f(ih, jh);
             int t = tier1(r2, R);
-            if (t == 2) t = decide_band(pair_r2(ih, il, jh, a.pos32lo[j]), R, a.pos, pi, j) ? 1 : 0;
+            if (t == 2)
+                t = decide_band(pair_r2(ih, il, jh, a.pos32lo[j]), R, a.pos, MIXED ? a.pos[i] : pi, j) ? 1 : 0;
             if (!t) continue;
             if (MIXED) {
                 if (!(r2 > 0.f)) {   // coincident to FP32: decide in binary64
-                    if (!(exact_dist2(pi, a.pos[j]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
+                    if (!(exact_dist2(a.pos[i], a.pos[j]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
                     continue;
                 }
                 const float rs = rsqrtf(r2);
                 const float w = a.kernel == 1 ? cubic_w_f(r2, rs, R.inv_f) : fmaf(R.re_f, rs, -1.f);
-                const float4 uj = a.vel32[j];
+                const float4 uj = vj;
                 kahan_add(f0, e0, (uj.x - u32.x) * w);
                 kahan_add(f1, e1, (uj.y - u32.y) * w);
                 kahan_add(f2, e2, (uj.z - u32.z) * w);
@@ -167,6 +181,8 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
             s0 = ff_to_double_fast({f0, -e0});
             s1 = ff_to_double_fast({f1, -e1});
             s2 = ff_to_double_fast({f2, -e2});
+            pi = a.pos[i];
+            ui = a.vel[i];
         }
         // u* = u + dt (nu lap(u) + g); r* = r + dt u*  (one rounding per operation)
         const double l0 = coef_lap * s0, l1 = coef_lap * s1, l2 = coef_lap * s2;
