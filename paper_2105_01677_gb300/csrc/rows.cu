@@ -276,11 +276,13 @@ constexpr int kEntryN = 1 << 30;   // within re_n: contributes to n*
 constexpr int kEntryL = 1 << 29;   // non-dummy within re_lap: a PPE coefficient
 constexpr int kSlotMask = kEntryL - 1;
 
-// Mixed precision: one walk per row over the candidate list, two candidates at a time in
-// packed float-float: the squared distance decides membership (float-float outside a band
-// of its error around re^2, binary64 inside it), n* and the diagonal are accumulated and
-// the PPE coefficients and gradient neighbours written in candidate order.  Nine in ten
-// candidates are members, so evaluating every candidate wastes little.
+// Mixed precision with the PPE: one walk per row over the candidate list, two candidates at
+// a time in packed float-float: the squared distance decides membership (float-float
+// outside a band of its error around re^2, binary64 inside it), n* and the diagonal are
+// accumulated and the PPE coefficients and gradient neighbours written in candidate order.
+// Nine in ten candidates are members, so evaluating every candidate wastes little.  With
+// the equation of state only the number-density neighbours (one in seven) are members: the
+// members are classified and staged first, as on the FP64 path, and only they evaluated.
 // FP64: two passes.  Classification decides the predicates (FP32 / float-float / binary64
 // tiers) and writes the hits into the row's PPE slots in candidate order (band pairs,
 // decided after the walk, last); the dense pass evaluates every hit with (nearly) all
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
         // FP64 path: classification first (the mixed path decides membership inside its
         // single walk below).  Band pairs are set aside and decided after the walk, so that
         // the lanes of a warp take the float-float and binary64 tiers together
-        if (!MIXED) {
+        if (!MIXED || !with_ppe) {
         constexpr int kPend = 16;
         int pend[kPend];
         int np = 0;
@@ -402,62 +404,10 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
             const ff2 coef = {f2(-ncoef_ff.h), f2(-ncoef_ff.l)};
             const ff2 invn = {f2(rn.inv_f), f2(rn.inv_l)}, invl = {f2(rl.inv_f), f2(rl.inv_l)};
             const double4 ui = SRC >= 1 ? a.vel_star[i] : make_double4(0.0, 0.0, 0.0, 0.0);
-            // One walk over the candidate list, two candidates per iteration: the float-float
-            // squared distance decides membership (the second tier of the exact predicate:
-            // outside the ff_tol band around re^2, binary64 inside it) and the members' terms
-            // are evaluated at once, in candidate order.  The slots of the next pair are
-            // loaded one iteration ahead.
-            int s0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
-            int s1 = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : s0;
-            for (int t = 0; t < cnt; t += 2) {
-                const bool two = t + 1 < cnt;
-                const int j0 = s0, j1 = s1;
-                if (t + 2 < cnt) {
-                    s0 = a.vcol[sell(i, t + 2, a.cap_v)];
-                    s1 = t + 3 < cnt ? a.vcol[sell(i, t + 3, a.cap_v)] : s0;
-                }
-                const float4 h0 = a.pos32[j0], l0 = a.pos32lo[j0];
-                const float4 h1 = a.pos32[j1], l1 = a.pos32lo[j1];
-                const ff2 dx = ff2_diff(ih.x, il.x, make_float2(h0.x, h1.x), make_float2(l0.x, l1.x));
-                const ff2 dy = ff2_diff(ih.y, il.y, make_float2(h0.y, h1.y), make_float2(l0.y, l1.y));
-                const ff2 dz = ff2_diff(ih.z, il.z, make_float2(h0.z, h1.z), make_float2(l0.z, l1.z));
-                const ff2 r2 = ff2_dist2(dx, dy, dz);
-                // membership: d = r^2 - re^2 in float-float, decided outside [-ff_tol, ff_tol]
-                const float2 dn = add2(sub2(r2.h, f2(rn.re2_h)), sub2(r2.l, f2(rn.re2_l)));
-                bool tn0 = dn.x <= -rn.ff_tol ||
-                           (dn.x < rn.ff_tol && exact_dist2(pi, a.pos[j0]) < rn.re2);
-                bool tn1 = two && (dn.y <= -rn.ff_tol ||
-                                   (dn.y < rn.ff_tol && exact_dist2(pi, a.pos[j1]) < rn.re2));
-                const bool nb0 = kind_of(h0) != kDummy, nb1 = kind_of(h1) != kDummy;
-                bool tl0 = false, tl1 = false;
-                if (with_ppe) {
-                    const float2 dl = add2(sub2(r2.h, f2(rl.re2_h)), sub2(r2.l, f2(rl.re2_l)));
-                    tl0 = nb0 && (dl.x <= -rl.ff_tol ||
-                                  (dl.x < rl.ff_tol && exact_dist2(pi, a.pos[j0]) < rl.re2));
-                    tl1 = two && nb1 && (dl.y <= -rl.ff_tol ||
-                                         (dl.y < rl.ff_tol && exact_dist2(pi, a.pos[j1]) < rl.re2));
-                }
-                // a member at zero distance (coincident to float-float) is an error unless
-                // binary64 separates it; either way it adds no term
-                const bool ok0 = r2.h.x > 0.f, ok1 = two && r2.h.y > 0.f;
-                if ((tn0 || tl0) && !ok0 && !(exact_dist2(pi, a.pos[j0]) > 0.0))
-                    atomicOr(&a.st->err, kErrCoincident);
-                if ((tn1 || tl1) && !ok1 && !(exact_dist2(pi, a.pos[j1]) > 0.0))
-                    atomicOr(&a.st->err, kErrCoincident);
-                // the gradient list: non-dummy members within re_n, in candidate order
-                if (tn0 && nb0) {
-                    if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j0;
-                    out_n++;
-                }
-                if (tn1 && nb1) {
-                    if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j1;
-                    out_n++;
-                }
-                m_n += (tn0 ? 1 : 0) + (tn1 ? 1 : 0);
-                tn0 = tn0 && ok0;
-                tn1 = tn1 && ok1;
-                tl0 = tl0 && ok0;
-                tl1 = tl1 && ok1;
+            // the members' terms of a pair of candidates (lane x: j0, lane y: j1), shared by
+            // the single walk and the walk over staged entries
+            auto terms = [&](int j0, int j1, const ff2& dx, const ff2& dy, const ff2& dz,
+                             const ff2& r2, bool tn0, bool tl0, bool tn1, bool tl1) {
                 const ff2 y = ff2_rsqrt1(r2);
                 ff2 w = {f2(0.f), f2(0.f)};
                 if (tn0 || tn1) {
@@ -504,6 +454,87 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                     } else {
                         overflow = true;
                     }
+                }
+            };
+            if (!with_ppe) {
+                // equation of state: one in seven candidates is a member (within re_n), so
+                // the classification above staged the members and only they are evaluated
+                for (int t = 0; t < m_all; t += 2) {
+                    const bool two = t + 1 < m_all;
+                    const int e0 = a.lap_col[sell(i, t, a.cap)];
+                    const int e1 = two ? a.lap_col[sell(i, t + 1, a.cap)] : e0;
+                    const int j0 = e0 & kSlotMask, j1 = e1 & kSlotMask;
+                    const float4 h0 = a.pos32[j0], l0 = a.pos32lo[j0];
+                    const float4 h1 = a.pos32[j1], l1 = a.pos32lo[j1];
+                    const ff2 dx = ff2_diff(ih.x, il.x, make_float2(h0.x, h1.x), make_float2(l0.x, l1.x));
+                    const ff2 dy = ff2_diff(ih.y, il.y, make_float2(h0.y, h1.y), make_float2(l0.y, l1.y));
+                    const ff2 dz = ff2_diff(ih.z, il.z, make_float2(h0.z, h1.z), make_float2(l0.z, l1.z));
+                    const ff2 r2 = ff2_dist2(dx, dy, dz);
+                    const bool ok0 = r2.h.x > 0.f, ok1 = two && r2.h.y > 0.f;
+                    if (!ok0 && !(exact_dist2(pi, a.pos[j0]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
+                    if (two && !ok1 && !(exact_dist2(pi, a.pos[j1]) > 0.0))
+                        atomicOr(&a.st->err, kErrCoincident);
+                    terms(j0, j1, dx, dy, dz, r2, ok0 && (e0 & kEntryN), false,
+                          ok1 && (e1 & kEntryN), false);
+                }
+            } else {
+                // One walk over the candidate list, two candidates per iteration: the float-float
+                // squared distance decides membership (the second tier of the exact predicate:
+                // outside the ff_tol band around re^2, binary64 inside it) and the members' terms
+                // are evaluated at once, in candidate order.  The slots of the next pair are
+                // loaded one iteration ahead.
+                int s0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
+                int s1 = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : s0;
+                for (int t = 0; t < cnt; t += 2) {
+                    const bool two = t + 1 < cnt;
+                    const int j0 = s0, j1 = s1;
+                    if (t + 2 < cnt) {
+                        s0 = a.vcol[sell(i, t + 2, a.cap_v)];
+                        s1 = t + 3 < cnt ? a.vcol[sell(i, t + 3, a.cap_v)] : s0;
+                    }
+                    const float4 h0 = a.pos32[j0], l0 = a.pos32lo[j0];
+                    const float4 h1 = a.pos32[j1], l1 = a.pos32lo[j1];
+                    const ff2 dx = ff2_diff(ih.x, il.x, make_float2(h0.x, h1.x), make_float2(l0.x, l1.x));
+                    const ff2 dy = ff2_diff(ih.y, il.y, make_float2(h0.y, h1.y), make_float2(l0.y, l1.y));
+                    const ff2 dz = ff2_diff(ih.z, il.z, make_float2(h0.z, h1.z), make_float2(l0.z, l1.z));
+                    const ff2 r2 = ff2_dist2(dx, dy, dz);
+                    // membership: d = r^2 - re^2 in float-float, decided outside [-ff_tol, ff_tol]
+                    const float2 dn = add2(sub2(r2.h, f2(rn.re2_h)), sub2(r2.l, f2(rn.re2_l)));
+                    bool tn0 = dn.x <= -rn.ff_tol ||
+                               (dn.x < rn.ff_tol && exact_dist2(pi, a.pos[j0]) < rn.re2);
+                    bool tn1 = two && (dn.y <= -rn.ff_tol ||
+                                       (dn.y < rn.ff_tol && exact_dist2(pi, a.pos[j1]) < rn.re2));
+                    const bool nb0 = kind_of(h0) != kDummy, nb1 = kind_of(h1) != kDummy;
+                    bool tl0 = false, tl1 = false;
+                    if (with_ppe) {
+                        const float2 dl = add2(sub2(r2.h, f2(rl.re2_h)), sub2(r2.l, f2(rl.re2_l)));
+                        tl0 = nb0 && (dl.x <= -rl.ff_tol ||
+                                      (dl.x < rl.ff_tol && exact_dist2(pi, a.pos[j0]) < rl.re2));
+                        tl1 = two && nb1 && (dl.y <= -rl.ff_tol ||
+                                             (dl.y < rl.ff_tol && exact_dist2(pi, a.pos[j1]) < rl.re2));
+                    }
+                    // a member at zero distance (coincident to float-float) is an error unless
+                    // binary64 separates it; either way it adds no term
+                    const bool ok0 = r2.h.x > 0.f, ok1 = two && r2.h.y > 0.f;
+                    if ((tn0 || tl0) && !ok0 && !(exact_dist2(pi, a.pos[j0]) > 0.0))
+                        atomicOr(&a.st->err, kErrCoincident);
+                    if ((tn1 || tl1) && !ok1 && !(exact_dist2(pi, a.pos[j1]) > 0.0))
+                        atomicOr(&a.st->err, kErrCoincident);
+                    // the gradient list: non-dummy members within re_n, in candidate order
+                    if (tn0 && nb0) {
+                        if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j0;
+                        out_n++;
+                    }
+                    if (tn1 && nb1) {
+                        if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j1;
+                        out_n++;
+                    }
+                    m_n += (tn0 ? 1 : 0) + (tn1 ? 1 : 0);
+                    tn0 = tn0 && ok0;
+                    tn1 = tn1 && ok1;
+                    tl0 = tl0 && ok0;
+                    tl1 = tl1 && ok1;
+                    terms(j0, j1, dx, dy, dz, r2, tn0, tl0, tn1, tl1);
                 }
             }
             nd = ff_to_double_fast(ff2_lo(acc));
