@@ -76,8 +76,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # with the coefficients
 SPMV_TRAFFIC_PER_COEF = (259.9e6 + 3.5e6) / 25.19e6
 # the same for one launch of the mixed build kernel (one walk per row, 256-thread blocks):
-# 478.6 + 557.3 MB for 25.19 M PPE coefficients (its lists and row outputs scale with them)
-BUILD_TRAFFIC_PER_COEF = (478.6e6 + 557.3e6) / 25.19e6
+# 477.7 + 556.8 MB for 25.19 M PPE coefficients (its lists and row outputs scale with them)
+BUILD_TRAFFIC_PER_COEF = (477.7e6 + 556.8e6) / 25.19e6
 
 
 def parse():
