@@ -1111,6 +1111,7 @@ namespace {
 constexpr int64_t kNoAllocMaxRows = MPS_NOALLOC_MAX_ROWS;
 constexpr size_t kNoAllocHead = 512;                       // CgScalars + reduction tickets
 constexpr size_t kNoAllocPartials = 4096;                  // per-block partial sums
+constexpr int kNoAllocMaxRestarts = 30;                    // true-residual restarts per call
 constexpr size_t kNoAllocBytes = kNoAllocHead + kNoAllocPartials * sizeof(double) +
                                  3 * (size_t)kNoAllocMaxRows * sizeof(double);
 static_assert(sizeof(CgScalars) <= 256, "CgScalars must fit the scratch header");
@@ -1155,6 +1156,9 @@ extern "C" int mps_ppe_cg_noalloc(int64_t n, int32_t cap, const int32_t* col, co
     if (n <= 0 || n > kNoAllocMaxRows || cap <= 0 || !col || !cnt || !val || !diag || !b || !x ||
         !(tol > 0.0))
         return MPS_EINVAL;
+    // a launch error left pending by the caller's earlier work is not this call's: report
+    // it without clearing it, before launching anything
+    if (cudaPeekAtLastError() != cudaSuccess) return MPS_EDEVICE;
     void* base = nullptr;
     int rc = noalloc_base(&base);
     if (rc) return rc;
@@ -1172,7 +1176,9 @@ extern "C" int mps_ppe_cg_noalloc(int64_t n, int32_t cap, const int32_t* col, co
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return MPS_EDEVICE;
-    const int gs = sms * 8, gv = sms * 4;
+    // one partial sum per block: the grids never exceed the partials region
+    const int gs = std::min(sms * 8, (int)kNoAllocPartials);
+    const int gv = std::min(sms * 4, (int)kNoAllocPartials);
     // the array keeps the previous call's contents: scalars and tickets restart from zero
     CgScalars init{};
     init.max_iters = max_total;
@@ -1199,9 +1205,11 @@ extern "C" int mps_ppe_cg_noalloc(int64_t n, int32_t cap, const int32_t* col, co
     const double bnorm2 = h.rr, stop2 = h.stop2;
     double rel = 0.0;
     int iters = 0;
+    int restarts = 0;
     if (bnorm2 > 0.0) {
         int chunk = 8;
         for (;;) {
+            if (cudaGetLastError() != cudaSuccess) return MPS_EDEVICE;
             for (int k = 0; k < chunk; k++) {
                 k_spmv64<<<gs, kBT, 0, s>>>(v, d, q, cg);
                 k_xr64<<<gv, kBT, 0, s>>>(ni, x, r, d, q, cg, partials, &counters[2]);
@@ -1214,7 +1222,9 @@ extern "C" int mps_ppe_cg_noalloc(int64_t n, int32_t cap, const int32_t* col, co
             if ((rc = noalloc_read(&h, cg, s))) return rc;
             rel = sqrt(h.rr / bnorm2);
             if (h.rr <= stop2) break;
-            if (iters >= max_total) {
+            // the recurrence met the target but the true residual did not: restart from it,
+            // a bounded number of times (a tolerance below what FP64 can attain ends here)
+            if (iters >= max_total || ++restarts > kNoAllocMaxRestarts) {
                 rc = MPS_ECG_NOCONV;
                 break;
             }
