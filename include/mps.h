@@ -352,6 +352,25 @@ int mps_get_profile(mps_ctx* ctx, double* stage_ms, int64_t* stage_calls, int64_
 int mps_time_kernel(mps_ctx* ctx, int32_t which, int32_t repeats, double* ms_per_launch,
                     double* bytes_per_launch);
 
+/* Measured arithmetic peak of a device (a measuring tool of this library; the paper has no
+ * counterpart): the pair sums of the step are bound by FP32 arithmetic in the mixed path
+ * and by FP64 arithmetic in the FP64 path, and their rooflines are taken against these
+ * rates.  Launches `repeats` timed kernels (after two untimed ones) of independent chains
+ * of fused multiply-adds over whole waves of the device's SMs, timed with CUDA events on
+ * `stream` (cudaStream_t, NULL: the legacy default stream), and returns the rate in
+ * TFLOP/s (one fused multiply-add = 2 flops) and the mean launch time [ms] (nullable).
+ *   MPS_PEAK_FFMA   scalar FP32 FFMA;
+ *   MPS_PEAK_FFMA2  packed two-lane FP32 FFMA (one instruction, two fused multiply-adds);
+ *   MPS_PEAK_DFMA   FP64 DFMA.
+ * The device is made current for the call and the previous one restored.  Synchronous.
+ * Errors: MPS_EINVAL (unknown `which`, repeats < 1, tflops NULL), MPS_EDEVICE (a CUDA call
+ * failed, or a launch error was already pending on entry, which is left pending). */
+#define MPS_PEAK_FFMA 0
+#define MPS_PEAK_FFMA2 1
+#define MPS_PEAK_DFMA 2
+int mps_measure_peak(int32_t device, int32_t which, int32_t repeats, void* stream, double* tflops,
+                     double* ms_per_launch);
+
 /* Solve A x = b by FP64 conjugate gradients WITHOUT ALLOCATING any memory.
  * No counterpart in the paper: this is an entry point for callers that are not allowed to
  * call cudaMalloc -- for instance a host application whose device memory is entirely
@@ -361,15 +380,17 @@ int mps_time_kernel(mps_ctx* ctx, int32_t which, int32_t repeats, double* ms_per
  * vectors, partial sums and scalars live in one fixed array of device memory that belongs
  * to the loaded library (about 6.3 MB on every GPU that loads it, held until process exit).
  *
- * The system uses the row layout of the library's PPE operator (Eq. 13 as assembled in the
- * PPE listing (Listing 2) of Sec. 4.3):
+ * The system uses the row layout of the library's PPE operator:
  *   (A x)_i = diag[i] x_i - sum_{k < cnt[i]} val[i*cap + k] x[col[i*cap + k]]  if diag[i] != 0,
  *   and rows with diag[i] == 0 are outside the system (x_i = 0, b_i must be 0).
  * A must be symmetric positive definite on its rows.  col, cnt, val, diag, b and x are
  * device pointers owned by the caller (col/val: n*cap entries, the others n); x is
  * overwritten with the solution.  CG starts from x = 0 and stops when the recomputed true
- * residual satisfies ||b - A x|| <= tol ||b|| (restarting from it if the recurrence drifted),
- * or after max_iter iterations in total (<= 0: 10 n) with MPS_ECG_NOCONV.
+ * residual satisfies ||b - A x|| <= tol ||b|| (restarting from it if the recurrence drifted,
+ * at most 30 times), or with MPS_ECG_NOCONV after max_iter iterations in total (<= 0: 10 n)
+ * or 30 restarts (a tol below what FP64 can attain on the system).
+ * A CUDA launch error already pending in the calling thread on entry is reported as
+ * MPS_EDEVICE and left pending (not cleared) for its owner; nothing is launched then.
  * stream: cudaStream_t (NULL: the legacy default stream); the call is synchronous.
  * iters_out, resid_out (nullable): iterations and final relative residual.
  * Limits: 1 <= n <= MPS_NOALLOC_MAX_ROWS, else MPS_EINVAL.

@@ -75,7 +75,7 @@ EXPORTS = ("mps_params_default", "mps_create", "mps_step", "mps_solve_ppe", "mps
            "mps_strerror", "mps_set_fluid_properties", "mps_create_ensemble",
            "mps_scene_residuals", "mps_autotune", "mps_set_gravity", "mps_step_vjp",
            "mps_time_kernel", "mps_read_state_device", "mps_write_state_device",
-           "mps_step_vjp_device")
+           "mps_step_vjp_device", "mps_measure_peak")
 NOALLOC_MAX_ROWS = 262144
 STAGES = ("bucket", "gather", "predict", "build", "ppe", "update")
 
@@ -128,6 +128,7 @@ def lib(build_if_missing: bool = False):
     L.mps_ppe_cg_noalloc.argtypes = [C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
                                      C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
+    L.mps_measure_peak.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, d, d]
     L.mps_destroy.argtypes = [C.c_void_p]
     L.mps_destroy.restype = None
     L.mps_strerror.argtypes = [C.c_int]
@@ -137,7 +138,7 @@ def lib(build_if_missing: bool = False):
               "mps_get_profile", "mps_ppe_cg_noalloc", "mps_set_fluid_properties",
               "mps_create_ensemble", "mps_scene_residuals", "mps_autotune", "mps_set_gravity",
               "mps_step_vjp", "mps_time_kernel", "mps_read_state_device",
-              "mps_write_state_device", "mps_step_vjp_device"):
+              "mps_write_state_device", "mps_step_vjp_device", "mps_measure_peak"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -180,14 +181,19 @@ def mps_params_default(**kw) -> mps_params:
 class _TorchAllocator:
     """Device memory hooks backed by torch.cuda's caching allocator."""
 
-    def __init__(self, device: int, stream_ptr):
+    def __init__(self, device: int, stream_ptr, limit: int | None = None):
         import torch
         self._torch = torch
         self.device = device
         self.stream = stream_ptr
         self._live = {}
+        # optional byte budget: beyond it an allocation fails (returns NULL) as a full
+        # device would, so that callers can exercise the library's MPS_ENOMEM path
+        self.limit = limit
 
         def _alloc(nbytes, user):
+            if self.limit is not None and self.live_bytes() + int(nbytes) > self.limit:
+                return None
             try:
                 ptr = torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device)
             except Exception:
@@ -203,9 +209,12 @@ class _TorchAllocator:
         self.alloc = ALLOC_FN(_alloc)
         self.release = RELEASE_FN(_release)
 
+    def live_bytes(self) -> int:
+        return int(sum(self._live.values()))
+
 
 def mps_create(pos, vel, types, params: mps_params, torch_alloc: bool = False,
-               use_torch_stream: bool = False):
+               use_torch_stream: bool = False, alloc_limit: int | None = None):
     """Create a context; returns an opaque handle (c_void_p).  pos/vel: (n, dim) float64."""
     L = lib()
     pos = np.ascontiguousarray(pos, np.float64)
@@ -219,7 +228,7 @@ def mps_create(pos, vel, types, params: mps_params, torch_alloc: bool = False,
         if use_torch_stream:
             params.stream = C.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
         if torch_alloc:
-            keep = _TorchAllocator(dev, params.stream)
+            keep = _TorchAllocator(dev, params.stream, alloc_limit)
             params.alloc = keep.alloc
             params.release = keep.release
     h = C.c_void_p()
@@ -418,6 +427,19 @@ def mps_time_kernel(h, which: int, repeats: int = 10):
     return ms.value, by.value
 
 
+PEAK_FFMA, PEAK_FFMA2, PEAK_DFMA = 0, 1, 2
+
+
+def mps_measure_peak(which: int, device: int = 0, repeats: int = 5, stream: int = 0):
+    """(TFLOP/s, ms per launch) of the device's fused multiply-add rate: PEAK_FFMA (FP32),
+    PEAK_FFMA2 (packed two-lane FP32) or PEAK_DFMA (FP64)."""
+    tf = C.c_double()
+    ms = C.c_double()
+    _check(lib().mps_measure_peak(int(device), int(which), int(repeats), stream or None,
+                                  C.byref(tf), C.byref(ms)), "mps_measure_peak")
+    return tf.value, ms.value
+
+
 def mps_debug_cells(h, n: int):
     out = np.empty(n, np.uint32)
     _check(lib().mps_debug_cells(h, _ptr(out, C.c_uint32)), "mps_debug_cells")
@@ -531,7 +553,7 @@ class Simulation:
     """Convenience owner of one context built from a scene-like object."""
 
     def __init__(self, scene, torch_alloc: bool = False, use_torch_stream: bool = False,
-                 rho_i=None, nu_i=None, **params):
+                 rho_i=None, nu_i=None, alloc_limit: int | None = None, **params):
         self.n, self.dim = scene.n, scene.dim
         g = (0.0, -9.81, 0.0) if scene.dim == 2 else (0.0, 0.0, -9.81)
         base = dict(dim=scene.dim, l0=scene.l0, re_n=2.1 * scene.l0, re_lap=4.0 * scene.l0, g=g,
@@ -539,7 +561,7 @@ class Simulation:
         base.update(params)
         self.params = mps_params_default(**base)
         self.h = mps_create(scene.pos, scene.vel, scene.types, self.params, torch_alloc,
-                            use_torch_stream)
+                            use_torch_stream, alloc_limit)
         if rho_i is not None or nu_i is not None:
             self.set_fluid_properties(rho_i, nu_i)
 
