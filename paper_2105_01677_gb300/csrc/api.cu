@@ -621,8 +621,14 @@ int alloc_adjoint(Ctx* c) {
         (rc = alloc_dev(c, &a.pbar, n)) || (rc = alloc_dev(c, &a.lam, n)) ||
         (rc = alloc_dev(c, &a.gn, n)) || (rc = alloc_dev(c, &a.ppre, n)) ||
         (rc = alloc_dev(c, &a.amin, n)) || (rc = alloc_dev(c, &a.was_ghost, n)) ||
-        (rc = alloc_dev(c, &a.gsum, 4)))
+        (rc = alloc_dev(c, &a.gsum, 4))) {
+        // all or none: hand back what was taken, so that a retry starts clean
+        void* bufs[] = {a.gr, a.gu, a.gG, a.grs, a.gus, a.out_r, a.out_u, a.gphat, a.pbar,
+                        a.lam, a.gn, a.ppre, a.amin, a.was_ghost, a.gsum};
+        for (void* b : bufs) free_one(c, b);
+        a = AdjBuffers{};
         return rc;
+    }
     a.ready = true;
     return MPS_OK;
 }
@@ -988,11 +994,21 @@ int mps_set_fluid_properties(mps_ctx* c, const double* rho, const double* nu) {
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
     const size_t bytes = (size_t)n * sizeof(double);
     int rc;
+    // the buffers are taken all or none: a context never sees half of a property's set
     if (rho) {
         if (!c->rho_id) {
-            if ((rc = alloc_dev(c, &c->rho_id, (size_t)n)) || (rc = alloc_dev(c, &c->rho_s, (size_t)n)) ||
-                (rc = alloc_dev(c, &c->rho_ff, (size_t)n)))
+            double *a = nullptr, *b = nullptr;
+            float2* f = nullptr;
+            if ((rc = alloc_dev(c, &a, (size_t)n)) || (rc = alloc_dev(c, &b, (size_t)n)) ||
+                (rc = alloc_dev(c, &f, (size_t)n))) {
+                free_one(c, a);
+                free_one(c, b);
+                free_one(c, f);
                 return rc;
+            }
+            c->rho_id = a;
+            c->rho_s = b;
+            c->rho_ff = f;
         }
         MPS_CUDA(c, cudaMemcpyAsync(c->rho_id, rho, bytes, cudaMemcpyHostToDevice, c->stream));
     } else if (c->rho_id) {
@@ -1004,8 +1020,14 @@ int mps_set_fluid_properties(mps_ctx* c, const double* rho, const double* nu) {
     }
     if (nu) {
         if (!c->nu_id) {
-            if ((rc = alloc_dev(c, &c->nu_id, (size_t)n)) || (rc = alloc_dev(c, &c->nu_s, (size_t)n)))
+            double *a = nullptr, *b = nullptr;
+            if ((rc = alloc_dev(c, &a, (size_t)n)) || (rc = alloc_dev(c, &b, (size_t)n))) {
+                free_one(c, a);
+                free_one(c, b);
                 return rc;
+            }
+            c->nu_id = a;
+            c->nu_s = b;
         }
         MPS_CUDA(c, cudaMemcpyAsync(c->nu_id, nu, bytes, cudaMemcpyHostToDevice, c->stream));
     } else if (c->nu_id) {

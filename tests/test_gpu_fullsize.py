@@ -71,3 +71,72 @@ def test_fullsize_step_mixed_bound(scene, oracle_step):
     assert np.array_equal(got["flags"], ost.flags)
     rows = ost.types <= oracle.WALL
     assert rel_err(got["n_star"][rows], ost.nstar[rows]) <= 1e-12
+
+
+# ------------------------------------------------------------------ the bench's trajectory
+TRAJ_STEPS = 5
+
+
+@pytest.fixture(scope="module")
+def oracle_trajectory(scene):
+    """The oracle's first five steps (PPE from zero to 1e-13), a copy after each."""
+    prm = oracle_params(scene, dt=5e-5, cg_tol=PARITY_CG_TOL)
+    st = oracle.State.from_scene(scene)
+    out = []
+    for _ in range(TRAJ_STEPS):
+        oracle.step(prm, st)
+        out.append(st.copy())
+    return prm, out
+
+
+def _gpu_trajectory(scene, **kw):
+    from paper_2105_01677_gb300 import mps
+    sim = mps.Simulation(scene, torch_alloc=True, use_torch_stream=True,
+                         **gpu_params(scene, dt=5e-5, **kw))
+    states, reps = [], []
+    try:
+        for _ in range(TRAJ_STEPS):
+            _, rep = sim.step(1)
+            reps.append(rep)
+            states.append(sim.read())
+    finally:
+        sim.close()
+    return states, reps
+
+
+def test_fullsize_mixed_trajectory_with_quadratic_guess(scene, oracle_trajectory):
+    """The headline configuration over five steps: mixed precision, PPE started from the
+    extrapolation of the previous solutions (cg_x0 = 3), true FP64 residual <= 1e-8 each
+    step; every step's state within the mixed bound of the oracle's trajectory."""
+    prm, ref = oracle_trajectory
+    got, reps = _gpu_trajectory(scene, precision=1, cg_tol=1e-8, cg_x0=3)
+    f = scene.types == scenes.FLUID
+    n0, _ = oracle.lattice(3, scene.l0, 2.1 * scene.l0)
+    for k in range(TRAJ_STEPS):
+        assert reps[k]["cg_resid"] <= 1e-8
+        ep = np.linalg.norm(got[k]["p"][f] - ref[k].p[f]) / np.linalg.norm(ref[k].p[f])
+        ex = np.abs(got[k]["pos"] - ref[k].pos).max() / scene.l0
+        assert ep <= 1e-5, (k, ep)
+        assert ex <= 1e-6, (k, ex)
+        # after the first step the positions differ at the mixed bound, so n* may too:
+        # flags agree outside a band of 1e-7 n0 around the threshold
+        band = np.abs(ref[k].nstar - prm.beta * n0) <= 1e-7 * n0
+        assert np.array_equal(got[k]["flags"][~band], ref[k].flags[~band]), k
+    # the guess is used from the second step on: fewer inner iterations than the cold start
+    assert min(r["cg_iters"] for r in reps[2:]) < reps[0]["cg_iters"]
+
+
+def test_fullsize_fp64_trajectory_with_quadratic_guess(scene, oracle_trajectory):
+    """FP64 with cg_x0 = 3 over five steps against the oracle (which starts every solve
+    from zero) at max(1e-10, 4x the oracle's own one-ulp sensitivity over those steps)."""
+    from _parity import ulp_sensitivity
+    prm, ref = oracle_trajectory
+    got, reps = _gpu_trajectory(scene, precision=0, cg_tol=PARITY_CG_TOL, cg_x0=3)
+    sens = ulp_sensitivity(scene, TRAJ_STEPS, dt=5e-5, cg_tol=PARITY_CG_TOL)
+    for name, key in (("p", "p"), ("vel", "vel")):
+        tol = max(FP64_TOL, 4.0 * sens[name])
+        err = rel_err(got[-1][key], getattr(ref[-1], name))
+        assert err <= tol, (name, err, tol)
+    for k in range(TRAJ_STEPS):
+        assert np.array_equal(got[k]["flags"], ref[k].flags), k
+        assert np.array_equal(got[k]["types"], ref[k].types), k
