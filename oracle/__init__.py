@@ -100,7 +100,7 @@ def lib():
                              C.c_double, i32, C.POINTER(C.c_int32), d]
         L.orc_dense_spd_solve.argtypes = [i64, d, d, d]
         L.orc_step_vjp.argtypes = [C.POINTER(Params), i64, d, d, C.POINTER(C.c_int8), d, d, d, d,
-                                   d, C.POINTER(Report), i32]
+                                   d, d, C.POINTER(Report), i32]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_get_threads.restype = C.c_int
         for f in ("orc_lattice", "orc_cell_keys", "orc_neighbors", "orc_pnd", "orc_laplacian",
@@ -363,9 +363,11 @@ def dense_spd_solve(A, b):
     return x
 
 
-def step_vjp(prm: StepParams, st, g_pos, g_vel, nb_mode: int = 1):
+def step_vjp(prm: StepParams, st, g_pos, g_vel, nb_mode: int = 1, with_nu: bool = False):
     """Vector-Jacobian product of one oracle step at the state `st` (not modified):
-    given dL/dr^{k+1}, dL/du^{k+1} (n x dim), returns (dL/dr^k, dL/du^k, dL/dg[3])."""
+    given dL/dr^{k+1}, dL/du^{k+1} (n x dim), returns (dL/dr^k, dL/du^k, dL/dg[3]), and
+    with `with_nu` also dL/dnu_i (n values: the viscosity of every particle; with one
+    viscosity for all, dL/dnu is their sum)."""
     pos = _arr(st.pos, np.float64)
     vel = _arr(st.vel, np.float64)
     types = _arr(st.types, np.int8)
@@ -376,10 +378,14 @@ def step_vjp(prm: StepParams, st, g_pos, g_vel, nb_mode: int = 1):
     out_r = np.empty_like(pos)
     out_u = np.empty_like(vel)
     out_g = np.zeros(3)
+    out_nu = np.zeros(n) if with_nu else None
     P = prm.c_struct(n)
     R = Report()
     d = C.c_double
     _check(lib().orc_step_vjp(C.byref(P), n, _p(pos, d), _p(vel, d), _p(types, C.c_int8),
                               _p(g_pos, d), _p(g_vel, d), _p(out_r, d), _p(out_u, d),
-                              _p(out_g, d), C.byref(R), nb_mode), "step_vjp")
+                              _p(out_g, d), None if out_nu is None else _p(out_nu, d),
+                              C.byref(R), nb_mode), "step_vjp")
+    if with_nu:
+        return out_r, out_u, out_g, out_nu
     return out_r, out_u, out_g

@@ -1046,6 +1046,9 @@ int orc_cg(int64_t n, const int64_t* off, const int32_t* col, const double* val,
 /*     u* = u + dt (nu_i lap(u)_i + g): gu += gu*, gg += dt gu*, and per pair within     */
 /*     re_lap at r^k (k = dt nu_i 2d/(n0_lap lambda)): gu_j += k w gu*_i, gu_i -= the     */
 /*     same, X = k (gu*_i . (u_j - u_i)) w'(s) x/s;                                        */
+/*     The viscosity nu_i enters only u*_i (FLUID), linearly: dL/dnu_i = dt gu*_i .       */
+/*     lap(u)_i = dt 2d/(n0_lap lambda) sum_j w(s) (gu*_i . (u_j - u_i)) (out_nu, n      */
+/*     values; 0 off FLUID; with one viscosity for all, dL/dnu is their sum);            */
 /*  1. a particle that becomes a GHOST in this step has its velocity reset: gu = 0.      */
 /* Other kinds: r^{k+1} = r^k, u^{k+1} = u^k (identity) plus their part in pair terms.   */
 /* ------------------------------------------------------------------------------------ */
@@ -1058,7 +1061,8 @@ static void add_pair(double* out, int dim, int64_t i, int64_t j, const double X[
 
 int orc_step_vjp(const orc_params* p, int64_t n, const double* pos, const double* vel,
                  const int8_t* type_in, const double* gr, const double* gu, double* out_r,
-                 double* out_u, double* out_g, orc_report* rep, int32_t nb_mode) {
+                 double* out_u, double* out_g, double* out_nu, orc_report* rep,
+                 int32_t nb_mode) {
     int dim = p->dim;
     int rc = check_params(p, n);
     if (rc) return rc;
@@ -1245,11 +1249,14 @@ int orc_step_vjp(const orc_params* p, int64_t n, const double* pos, const double
     rc = neighbors(dim, n, x0, type, p->re_lap, nb_mode, &nb_k);
     if (rc) goto out;
     const double clap = (2.0 * dim) / (R.n0_lap * R.lambda);
+    if (out_nu)
+        for (int64_t i = 0; i < n; i++) out_nu[i] = 0.0;
     for (int64_t i = 0; i < n; i++) {
         if (type[i] != ORC_FLUID) continue;
         double xi, yi, zi;
         coords(x0, dim, i, &xi, &yi, &zi);
         double k = dt * nu_of(p, i) * clap;
+        double gnu = 0.0;   /* sum_j w (gu*_i . (u_j - u_i)) */
         for (int64_t kk = nb_k.off[i]; kk < nb_k.off[i + 1]; kk++) {
             int64_t j = nb_k.ids[kk];
             double xj, yj, zj;
@@ -1268,7 +1275,9 @@ int orc_step_vjp(const orc_params* p, int64_t n, const double* pos, const double
             double f = k * gdu * (-p->re_lap / s2) / s;
             double X[3] = {f * d[0], f * d[1], f * d[2]};
             add_pair(out_r, dim, i, j, X);
+            gnu = gnu + w * gdu;
         }
+        if (out_nu) out_nu[i] = dt * clap * gnu;
     }
     /* ---- 1: a particle turned GHOST in this step had its velocity reset */
     for (int64_t i = 0; i < n; i++)

@@ -156,3 +156,63 @@ def test_vjp_rejects_options_without_a_reverse():
     for kw in (dict(kernel=1, pressure_mode=1), dict(grad_form=1), dict(source=1)):
         with pytest.raises(oracle.OracleError):
             oracle.step_vjp(oracle.params_for(sc, **kw), st, z, z)
+
+
+# ------------------------------------------------------------------ the viscosity
+def _forward_nu(prm, sc, nu=None, nu_i=None):
+    kw = dict(prm.__dict__)
+    if nu is not None:
+        kw["nu"] = float(nu)
+    if nu_i is not None:
+        kw["nu_i"] = np.ascontiguousarray(nu_i, dtype=np.float64)
+    return _forward(oracle.StepParams(**kw), sc, sc.pos, sc.vel)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_vjp_viscosity_matches_central_differences(dim, mode):
+    """dL/dnu (Eq. 7's viscosity in the prediction, one value for all): the sum of the
+    per-particle cotangents against (F(nu + h) - F(nu - h)) / 2h, PPE and EOS paths."""
+    sc = _scene(dim, seed=10 + dim)
+    nu = 0.05
+    prm = oracle.params_for(sc, cg_tol=1e-14, pressure_mode=mode, c0=20.0, nu=nu)
+    rng = np.random.default_rng(11)
+    gpos = rng.standard_normal(sc.pos.shape)
+    gvel = rng.standard_normal(sc.vel.shape)
+    _, _, _, gnu = oracle.step_vjp(prm, oracle.State.from_scene(sc), gpos, gvel, with_nu=True)
+    assert np.all(gnu[sc.types != scenes.FLUID] == 0.0)
+    h = 1e-6 * nu
+    fp = _forward_nu(prm, sc, nu=nu + h)
+    fm = _forward_nu(prm, sc, nu=nu - h)
+    fd = float(((fp[0] - fm[0]) * gpos + (fp[1] - fm[1]) * gvel).sum()) / (2.0 * h)
+    adj = float(gnu.sum())
+    assert abs(fd - adj) <= TOL * abs(adj), (fd, adj, abs(fd - adj) / abs(adj))
+
+
+def test_vjp_per_particle_viscosity_matches_central_differences():
+    """Two phases: dL/dnu_i along a random direction of the per-particle viscosities."""
+    sc = _scene(2, seed=12)
+    rho, nu = scenes.two_phase(sc, rho=(1000.0, 600.0), nu=(0.05, 0.3))
+    prm = oracle.params_for(sc, cg_tol=1e-14, rho_i=rho, nu_i=nu)
+    rng = np.random.default_rng(13)
+    gpos = rng.standard_normal(sc.pos.shape)
+    gvel = rng.standard_normal(sc.vel.shape)
+    _, _, _, gnu = oracle.step_vjp(prm, oracle.State.from_scene(sc), gpos, gvel, with_nu=True)
+    v = rng.uniform(0.5, 1.5, size=sc.n) * 0.05   # one sign: no cancellation in the sum
+    h = 1e-6
+    fp = _forward_nu(prm, sc, nu_i=nu + h * v)
+    fm = _forward_nu(prm, sc, nu_i=nu - h * v)
+    fd = float(((fp[0] - fm[0]) * gpos + (fp[1] - fm[1]) * gvel).sum()) / (2.0 * h)
+    adj = float(gnu @ v)
+    assert abs(fd - adj) <= TOL * abs(adj), (fd, adj, abs(fd - adj) / abs(adj))
+
+
+def test_vjp_viscosity_of_a_fluid_at_rest_is_zero():
+    """With u = 0 the Laplacian of the velocity vanishes: dL/dnu = 0 exactly."""
+    sc = _scene(2, seed=14)
+    sc.vel[:] = 0.0
+    prm = oracle.params_for(sc, cg_tol=1e-14, nu=0.05)
+    rng = np.random.default_rng(15)
+    g = rng.standard_normal(sc.pos.shape)
+    _, _, _, gnu = oracle.step_vjp(prm, oracle.State.from_scene(sc), g, g, with_nu=True)
+    assert np.all(gnu == 0.0)
