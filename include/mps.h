@@ -218,7 +218,11 @@ int mps_set_gravity(mps_ctx* ctx, const double* g);
  * solver, precision and cg_tol; the equation-of-state path differentiates Eq. 16.
  *   g_pos, g_vel    dL/dr^{k+1}, dL/du^{k+1}: n*dim doubles each (original order);
  *   out_pos, out_vel dL/dr^k, dL/du^k: n*dim doubles each (caller-allocated);
- *   out_g           dL/dg: 3 doubles (nullable; 0 on the unused axis of 2D).
+ *   out_g           dL/dg: 3 doubles (nullable; 0 on the unused axis of 2D);
+ *   out_nu          dL/dnu_i: n doubles (nullable; original order), the cotangent of every
+ *                   particle's kinematic viscosity in the prediction u* = u + dt (nu_i
+ *                   lap(u)_i + g) (Eq. 7): dt lap(u)_i . dL/du*_i for FLUID particles, 0 for
+ *                   the others.  With one viscosity for all (params.nu), dL/dnu is their sum.
  * GHOST particles carry their cotangents through, except that a particle turned GHOST
  * by this step (its velocity is reset) gets dL/du^k = 0.
  * The state is not advanced: afterwards positions and velocities are unchanged and
@@ -235,7 +239,7 @@ typedef struct {
     mps_report forward;      /* the repeated forward step                                   */
 } mps_vjp_report;
 int mps_step_vjp(mps_ctx* ctx, const double* g_pos, const double* g_vel, double* out_pos,
-                 double* out_vel, double* out_g, mps_vjp_report* report);
+                 double* out_vel, double* out_g, double* out_nu, mps_vjp_report* report);
 
 /* Device-memory variants: the same calls with the caller's particle arrays (every pointer
  * argument except out_g and report) in device memory of the context's device, in the same
@@ -246,7 +250,7 @@ int mps_read_state_device(mps_ctx* ctx, double* pos, double* vel, double* p, dou
                           uint8_t* flags, int8_t* types);
 int mps_write_state_device(mps_ctx* ctx, const double* pos, const double* vel, const int8_t* types);
 int mps_step_vjp_device(mps_ctx* ctx, const double* g_pos, const double* g_vel, double* out_pos,
-                        double* out_vel, double* out_g, mps_vjp_report* report);
+                        double* out_vel, double* out_g, double* out_nu, mps_vjp_report* report);
 
 /* Two-phase (multi-density, multi-viscosity) flow of Sec. 3.2.1: a density rho_i [kg/m^3]
  * and a kinematic viscosity nu_i [m^2/s] per particle, n doubles each in the original

@@ -71,6 +71,7 @@ struct AdjArgs {
     double *gphat, *pbar, *lam, *gn;
     int32_t* amin;
     const uint8_t* was_ghost;          // by particle id
+    double* gnu;                       // dL/dnu of every slot
 };
 
 __device__ __forceinline__ double rho_of(const AdjArgs& a, int i) { return a.rho_s ? a.rho_s[i] : a.rho; }
@@ -269,9 +270,11 @@ __global__ void __launch_bounds__(kBT) k_adj_star_other(AdjArgs a) {
 // non-FLUID candidates before any binary64 work.
 //   pair (k, j), x = r_j - r_k, a_k = dt nu_k 2d/(n0 lambda) gu*_k (0 unless k is FLUID):
 //   gu_k += w (a_j - a_k),  gr_k -= w'(s)/s ((a_k - a_j) . (u_j - u_k)) x
-__device__ __forceinline__ void visc_pair(const AdjArgs& a, int j, const double4& xk,
-                                          const double4& uk, const double4& ak, double4& orr,
-                                          double4& ou) {
+// The viscosity enters u*_k linearly: dL/dnu_k = dt 2d/(n0 lambda) sum_j w (gu*_k . (u_j - u_k))
+// for FLUID k; FLUID rows return w to sum it.
+__device__ __forceinline__ double visc_pair(const AdjArgs& a, int j, const double4& xk,
+                                            const double4& uk, const double4& ak, double4& orr,
+                                            double4& ou) {
     const double4 x = sub4(a.pos[j], xk);
     const double rs = rsqrt(dot3(x, x));
     const double w = fma(a.rl.re, rs, -1.0);
@@ -285,6 +288,7 @@ __device__ __forceinline__ void visc_pair(const AdjArgs& a, int j, const double4
     const double4 da = sub4(aj, ak);
     ou = axpy4(w, da, ou);
     orr = axpy4(wd_s * dot3(da, sub4(a.vel[j], uk)), x, orr);
+    return w;
 }
 
 __global__ void __launch_bounds__(kBT) k_adj_visc_f(AdjArgs a, const int32_t* rows,
@@ -300,13 +304,16 @@ __global__ void __launch_bounds__(kBT) k_adj_visc_f(AdjArgs a, const int32_t* ro
     const double4 xk = a.pos[k], uk = a.vel[k];
     const float4 qk = a.pos32[k];
     const int cnt = a.vcnt[k];
+    double lap = 0.0;   // sum_j w (gu*_k . (u_j - u_k))
     for (int t = 0; t < cnt; t++) {
         const int j = a.vcol[sell(k, t, a.cap_v)];
         if (!in_radius(dist2_f(qk, a.pos32[j]), a.rl, a.pos, k, j, xk)) continue;
-        visc_pair(a, j, xk, uk, ak, orr, ou);
+        const double w = visc_pair(a, j, xk, uk, ak, orr, ou);
+        lap = fma(w, dot3(gsk, sub4(a.vel[j], uk)), lap);
     }
     a.out_r[k] = orr;
     a.out_u[k] = ou;
+    a.gnu[k] = a.dt * a.coef_lap * lap;
 }
 
 __global__ void __launch_bounds__(kBT) k_adj_visc_other(AdjArgs a) {
@@ -314,6 +321,7 @@ __global__ void __launch_bounds__(kBT) k_adj_visc_other(AdjArgs a) {
     if (k >= a.n) return;
     const int tk = a.type[k];
     if (tk == kFluid) return;
+    a.gnu[k] = 0.0;   // the viscosity acts on FLUID particles only
     if (tk == kGhost) {
         a.out_r[k] = a.gr[k];
         a.out_u[k] = a.was_ghost[a.id[k]] ? a.gu[k] : make_double4(0.0, 0.0, 0.0, 0.0);
@@ -389,9 +397,10 @@ __global__ void k_adj_load(int n, int dim, const int32_t* id, const double* gpos
 }
 
 __global__ void k_adj_store(int n, int dim, const int32_t* id, const double4* r, const double4* u,
-                            double* o_r, double* o_u) {
+                            const double* gnu, double* o_r, double* o_u, double* o_nu) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
+    if (o_nu) o_nu[id[s]] = gnu[s];
     const size_t i = (size_t)id[s] * dim;
     const double4 a = r[s], b = u[s];
     const double ra[3] = {a.x, a.y, a.z}, ua[3] = {b.x, b.y, b.z};
@@ -460,6 +469,7 @@ AdjArgs adj_args(Ctx* c) {
     a.gn = c->adj.gn;
     a.amin = c->adj.amin;
     a.was_ghost = c->adj.was_ghost;
+    a.gnu = c->adj.gnu;
     return a;
 }
 
@@ -502,10 +512,11 @@ void launch_adj_back(Ctx* c, double* d_gsum) {
     c->launches += 6;
 }
 
-void launch_adj_store(Ctx* c, double* d_out_r, double* d_out_u) {
+void launch_adj_store(Ctx* c, double* d_out_r, double* d_out_u, double* d_out_nu) {
     const int n = (int)c->n;
     k_adj_store<<<blocks(n, 256), 256, 0, c->stream>>>(n, c->dim, c->id, c->adj.out_r,
-                                                        c->adj.out_u, d_out_r, d_out_u);
+                                                        c->adj.out_u, c->adj.gnu, d_out_r,
+                                                        d_out_u, d_out_nu);
     c->launches += 1;
 }
 

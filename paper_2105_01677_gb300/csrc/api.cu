@@ -621,10 +621,10 @@ int alloc_adjoint(Ctx* c) {
         (rc = alloc_dev(c, &a.pbar, n)) || (rc = alloc_dev(c, &a.lam, n)) ||
         (rc = alloc_dev(c, &a.gn, n)) || (rc = alloc_dev(c, &a.ppre, n)) ||
         (rc = alloc_dev(c, &a.amin, n)) || (rc = alloc_dev(c, &a.was_ghost, n)) ||
-        (rc = alloc_dev(c, &a.gsum, 4))) {
+        (rc = alloc_dev(c, &a.gsum, 4)) || (rc = alloc_dev(c, &a.gnu, n))) {
         // all or none: hand back what was taken, so that a retry starts clean
         void* bufs[] = {a.gr, a.gu, a.gG, a.grs, a.gus, a.out_r, a.out_u, a.gphat, a.pbar,
-                        a.lam, a.gn, a.ppre, a.amin, a.was_ghost, a.gsum};
+                        a.lam, a.gn, a.ppre, a.amin, a.was_ghost, a.gsum, a.gnu};
         for (void* b : bufs) free_one(c, b);
         a = AdjBuffers{};
         return rc;
@@ -853,7 +853,7 @@ int mps_set_gravity(mps_ctx* c, const double* g) {
 
 namespace {
 int step_vjp(Ctx* c, const double* g_pos, const double* g_vel, double* out_pos, double* out_vel,
-             double* out_g, mps_vjp_report* out, bool device) {
+             double* out_g, double* out_nu, mps_vjp_report* out, bool device) {
     if (!c || !g_pos || !g_vel || !out_pos || !out_vel) return MPS_EINVAL;
     const cudaMemcpyKind in = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const cudaMemcpyKind back = device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -901,10 +901,14 @@ int step_vjp(Ctx* c, const double* g_pos, const double* g_vel, double* out_pos, 
         }
     }
     launch_adj_back(c, c->adj.gsum);
-    launch_adj_store(c, d_a, d_b);
+    double* d_nu = out_nu ? (device ? out_nu : d_b + n * dim) : nullptr;
+    launch_adj_store(c, d_a, d_b, d_nu);
     MPS_CUDA(c, cudaGetLastError());
     MPS_CUDA(c, cudaMemcpyAsync(out_pos, d_a, n * dim * sizeof(double), back, c->stream));
     MPS_CUDA(c, cudaMemcpyAsync(out_vel, d_b, n * dim * sizeof(double), back, c->stream));
+    if (out_nu && !device)
+        MPS_CUDA(c, cudaMemcpyAsync(out_nu, d_nu, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
     double gs[3] = {0.0, 0.0, 0.0};
     MPS_CUDA(c, cudaMemcpyAsync(gs, c->adj.gsum, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -916,13 +920,13 @@ int step_vjp(Ctx* c, const double* g_pos, const double* g_vel, double* out_pos, 
 }  // namespace
 
 int mps_step_vjp(mps_ctx* c, const double* g_pos, const double* g_vel, double* out_pos,
-                 double* out_vel, double* out_g, mps_vjp_report* out) {
-    return step_vjp(c, g_pos, g_vel, out_pos, out_vel, out_g, out, false);
+                 double* out_vel, double* out_g, double* out_nu, mps_vjp_report* out) {
+    return step_vjp(c, g_pos, g_vel, out_pos, out_vel, out_g, out_nu, out, false);
 }
 
 int mps_step_vjp_device(mps_ctx* c, const double* g_pos, const double* g_vel, double* out_pos,
-                        double* out_vel, double* out_g, mps_vjp_report* out) {
-    return step_vjp(c, g_pos, g_vel, out_pos, out_vel, out_g, out, true);
+                        double* out_vel, double* out_g, double* out_nu, mps_vjp_report* out) {
+    return step_vjp(c, g_pos, g_vel, out_pos, out_vel, out_g, out_nu, out, true);
 }
 
 namespace {

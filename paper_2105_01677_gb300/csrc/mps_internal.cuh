@@ -175,7 +175,7 @@ void launch_adj_mark(Ctx* c);
 void launch_adj_load(Ctx* c, const double* d_gpos, const double* d_gvel);
 void launch_adj_front(Ctx* c);
 void launch_adj_back(Ctx* c, double* d_gsum);
-void launch_adj_store(Ctx* c, double* d_out_r, double* d_out_u);
+void launch_adj_store(Ctx* c, double* d_out_r, double* d_out_u, double* d_out_nu);
 
 // ---------------------------------------------------------------- update.cu
 void launch_clamp_pmin(Ctx* c);
@@ -230,6 +230,7 @@ struct AdjBuffers {
     int32_t* amin = nullptr;                  // slot giving p_hat of each FLUID row
     uint8_t* was_ghost = nullptr;             // by particle id: GHOST before the step
     double* gsum = nullptr;                   // dL/dg (3)
+    double* gnu = nullptr;                    // dL/dnu of every slot (0 off FLUID)
 };
 
 struct Ctx {

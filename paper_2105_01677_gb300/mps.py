@@ -109,11 +109,11 @@ def lib(build_if_missing: bool = False):
     L.mps_set_fluid_properties.argtypes = [C.c_void_p, d, d]
     L.mps_set_gravity.argtypes = [C.c_void_p, d]
     L.mps_time_kernel.argtypes = [C.c_void_p, C.c_int32, C.c_int32, d, d]
-    L.mps_step_vjp.argtypes = [C.c_void_p, d, d, d, d, d, C.POINTER(mps_vjp_report)]
+    L.mps_step_vjp.argtypes = [C.c_void_p, d, d, d, d, d, d, C.POINTER(mps_vjp_report)]
     vp = C.c_void_p
     L.mps_read_state_device.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.mps_write_state_device.argtypes = [vp, vp, vp, vp]
-    L.mps_step_vjp_device.argtypes = [vp, vp, vp, vp, vp, d, C.POINTER(mps_vjp_report)]
+    L.mps_step_vjp_device.argtypes = [vp, vp, vp, vp, vp, d, vp, C.POINTER(mps_vjp_report)]
     L.mps_create_ensemble.argtypes = [d, d, i8, C.POINTER(C.c_int32), C.c_int64,
                                       C.POINTER(mps_params), C.POINTER(mps_scene), C.c_int32,
                                       C.POINTER(C.c_void_p)]
@@ -355,9 +355,10 @@ def mps_set_gravity(h, g):
     _check(lib().mps_set_gravity(h, _ptr(ga, C.c_double)), "mps_set_gravity")
 
 
-def mps_step_vjp(h, g_pos, g_vel, check: bool = True):
+def mps_step_vjp(h, g_pos, g_vel, check: bool = True, want_nu: bool = False):
     """Reverse of the step from the current state: given dL/dr^{k+1}, dL/du^{k+1} ((n, dim)
-    float64, original order) returns (rc, dL/dr^k, dL/du^k, dL/dg[3], report dict)."""
+    float64, original order) returns (rc, dL/dr^k, dL/du^k, dL/dg[3], report dict); with
+    `want_nu` (rc, dL/dr^k, dL/du^k, dL/dg[3], dL/dnu_i[n], report dict)."""
     g_pos = np.ascontiguousarray(g_pos, np.float64)
     g_vel = np.ascontiguousarray(g_vel, np.float64)
     if g_pos.shape != g_vel.shape:
@@ -365,12 +366,15 @@ def mps_step_vjp(h, g_pos, g_vel, check: bool = True):
     out_r = np.empty_like(g_pos)
     out_u = np.empty_like(g_vel)
     out_g = np.zeros(3, np.float64)
+    out_nu = np.zeros(g_pos.shape[0], np.float64) if want_nu else None
     rep = mps_vjp_report()
     rc = lib().mps_step_vjp(h, _ptr(g_pos, C.c_double), _ptr(g_vel, C.c_double),
                             _ptr(out_r, C.c_double), _ptr(out_u, C.c_double),
-                            _ptr(out_g, C.c_double), C.byref(rep))
+                            _ptr(out_g, C.c_double), _ptr(out_nu, C.c_double), C.byref(rep))
     if check:
         _check(rc, "mps_step_vjp")
+    if want_nu:
+        return rc, out_r, out_u, out_g, out_nu, rep.as_dict()
     return rc, out_r, out_u, out_g, rep.as_dict()
 
 
@@ -400,15 +404,17 @@ def mps_write_state_device(h, pos, vel=None, types=None):
                                         _dptr(types, "int8")), "mps_write_state_device")
 
 
-def mps_step_vjp_device(h, g_pos, g_vel, out_pos, out_vel, check: bool = True):
+def mps_step_vjp_device(h, g_pos, g_vel, out_pos, out_vel, check: bool = True, out_nu=None):
     """Reverse of the step with CUDA tensors: g_pos, g_vel in; out_pos, out_vel (same shape)
-    out; returns (rc, dL/dg[3] as numpy, report dict)."""
+    and optionally out_nu (float64 (n,): dL/dnu_i) out; returns (rc, dL/dg[3] as numpy,
+    report dict)."""
     out_g = np.zeros(3, np.float64)
     rep = mps_vjp_report()
     rc = lib().mps_step_vjp_device(h, _dptr(g_pos, "float64"), _dptr(g_vel, "float64"),
                                    _dptr(out_pos, "float64", tuple(g_pos.shape)),
                                    _dptr(out_vel, "float64", tuple(g_vel.shape)),
-                                   _ptr(out_g, C.c_double), C.byref(rep))
+                                   _ptr(out_g, C.c_double),
+                                   _dptr(out_nu, "float64", (g_pos.shape[0],)), C.byref(rep))
     if check:
         _check(rc, "mps_step_vjp_device")
     return rc, out_g, rep.as_dict()
@@ -562,11 +568,16 @@ class Simulation:
         self.params = mps_params_default(**base)
         self.h = mps_create(scene.pos, scene.vel, scene.types, self.params, torch_alloc,
                             use_torch_stream, alloc_limit)
+        self.rho_i = self.nu_i = None
         if rho_i is not None or nu_i is not None:
             self.set_fluid_properties(rho_i, nu_i)
 
     def set_fluid_properties(self, rho=None, nu=None, check: bool = True):
-        return mps_set_fluid_properties(self.h, rho, nu, check)
+        rc = mps_set_fluid_properties(self.h, rho, nu, check)
+        if rc == OK:
+            self.rho_i = None if rho is None else np.array(rho, np.float64)
+            self.nu_i = None if nu is None else np.array(nu, np.float64)
+        return rc
 
     def step(self, nsteps: int = 1, check: bool = True):
         return mps_step(self.h, nsteps, check)
@@ -577,9 +588,10 @@ class Simulation:
     def set_gravity(self, g):
         mps_set_gravity(self.h, g)
 
-    def step_vjp(self, g_pos, g_vel, check: bool = True):
-        """(rc, dL/dr, dL/du, dL/dg, report) of the step from the current state."""
-        return mps_step_vjp(self.h, g_pos, g_vel, check)
+    def step_vjp(self, g_pos, g_vel, check: bool = True, want_nu: bool = False):
+        """(rc, dL/dr, dL/du, dL/dg, report) of the step from the current state; with
+        `want_nu` (rc, dL/dr, dL/du, dL/dg, dL/dnu_i, report)."""
+        return mps_step_vjp(self.h, g_pos, g_vel, check, want_nu)
 
     # device-memory variants (CUDA tensors in original order)
     def read_device(self, pos=None, vel=None, p=None, n_star=None, flags=None, types=None):
@@ -588,8 +600,8 @@ class Simulation:
     def write_device(self, pos, vel=None, types=None):
         mps_write_state_device(self.h, pos, vel, types)
 
-    def step_vjp_device(self, g_pos, g_vel, out_pos, out_vel, check: bool = True):
-        return mps_step_vjp_device(self.h, g_pos, g_vel, out_pos, out_vel, check)
+    def step_vjp_device(self, g_pos, g_vel, out_pos, out_vel, check: bool = True, out_nu=None):
+        return mps_step_vjp_device(self.h, g_pos, g_vel, out_pos, out_vel, check, out_nu)
 
     def read(self, **kw):
         return mps_read_state(self.h, self.n, self.dim, **kw)

@@ -131,7 +131,7 @@ def test_invalid_arguments_rejected_before_device_use(L):
                       t2.ctypes.data_as(C.POINTER(C.c_int8)), 3, C.byref(P), C.byref(h))
     assert rc == mps.EINVAL
     assert L.mps_step(None, 1, None) == mps.EINVAL
-    assert L.mps_step_vjp(None, None, None, None, None, None, None) == mps.EINVAL
+    assert L.mps_step_vjp(None, None, None, None, None, None, None, None) == mps.EINVAL
     g = np.zeros(3)
     assert L.mps_set_gravity(None, g.ctypes.data_as(C.POINTER(C.c_double))) == mps.EINVAL
 

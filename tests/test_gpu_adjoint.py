@@ -329,3 +329,83 @@ def test_rollout_on_cuda_tensors_equals_host_rollout():
             sim.close()
     for h, d in zip(*grads):
         assert np.array_equal(h, d)
+
+
+# ------------------------------------------------------------------ the viscosity
+@pytest.mark.parametrize("case", ["2d-ppe", "2d-eos-viscous", "3d-ppe", "two-phase"])
+def test_vjp_viscosity_cotangent_matches_oracle(case):
+    """dL/dnu_i of one step (the prediction's viscosity, Eq. 7) against the oracle's."""
+    from paper_2105_01677_gb300 import mps
+    nu_i = rho_i = None
+    if case == "2d-ppe":
+        sc, kw = _scene(2, seed=21), dict(cg_tol=CG, nu=0.05)
+    elif case == "2d-eos-viscous":
+        sc, kw = _scene(2, seed=22), dict(pressure_mode=1, c0=20.0, nu=0.5)
+    elif case == "3d-ppe":
+        sc, kw = _scene(3, seed=23), dict(cg_tol=CG, nu=0.05)
+    else:
+        sc, kw = _scene(2, seed=24), dict(cg_tol=CG)
+        rho_i, nu_i = scenes.two_phase(sc, rho=(1000.0, 600.0), nu=(0.05, 0.3))
+    gpos, gvel = _cotangents(sc, seed=25)
+    sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, rho_i=rho_i, nu_i=nu_i,
+                         **gpu_params(sc, **kw))
+    try:
+        _, gr, gu, gg, gnu, _ = sim.step_vjp(gpos, gvel, want_nu=True)
+    finally:
+        sim.close()
+    okw = dict(kw)
+    if rho_i is not None:
+        okw.update(rho_i=rho_i, nu_i=nu_i)
+    ogr, ogu, ogg, ognu = oracle.step_vjp(oracle_params(sc, **okw), oracle.State.from_scene(sc),
+                                          gpos, gvel, with_nu=True)
+    _close(gnu, ognu, what="dL/dnu")
+    _close(gu, ogu, what="dL/du")
+    assert np.all(gnu[sc.types != scenes.FLUID] == 0.0)
+
+
+def test_rollout_viscosity_gradient_matches_chained_oracle_and_differences():
+    """A 6-step rollout (checkpoint every 4) with the viscosity as a differentiable 0-d
+    tensor: d(kinetic energy)/dnu against the oracle's per-step dL/dnu summed along its
+    trajectory, and against central differences of the GPU rollout in nu."""
+    import torch
+    from paper_2105_01677_gb300 import autograd, mps
+    sc = _scene(2, seed=26)
+    T, nu0 = 6, 0.05
+    forcing = np.zeros((T, 3))
+    forcing[:, 1] = -9.81
+    sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
+                         **gpu_params(sc, cg_tol=1e-14, nu=nu0))
+    try:
+        def loss_of(nu_value, grad=False):
+            x = torch.tensor(sc.pos, dtype=torch.float64)
+            u = torch.tensor(sc.vel, dtype=torch.float64, requires_grad=grad)
+            f = torch.tensor(forcing, dtype=torch.float64)
+            nu = torch.tensor(nu_value, dtype=torch.float64, requires_grad=grad)
+            xT, uT = autograd.rollout(sim, x, u, f, checkpoint_every=4, nu=nu)
+            loss = autograd.kinetic_energy(uT, sc.types)
+            if grad:
+                loss.backward()
+                return float(loss.detach()), float(nu.grad), u.grad.numpy(), uT.detach().numpy()
+            return float(loss)
+        L0, g_nu, g_u0, uT = loss_of(nu0, grad=True)
+        h = 1e-6 * nu0
+        fd = (loss_of(nu0 + h) - loss_of(nu0 - h)) / (2.0 * h)
+    finally:
+        sim.close()
+    assert abs(fd - g_nu) <= 1e-6 * abs(g_nu), (fd, g_nu)
+    # the chained oracle reverse: KE's cotangent at the final state is u_T on FLUID rows
+    st = oracle.State.from_scene(sc)
+    states = []
+    for t in range(T):
+        prm = oracle_params(sc, cg_tol=CG, nu=nu0, g=tuple(forcing[t]))
+        states.append((st.copy(), prm))
+        oracle.step(prm, st)
+    f = (sc.types == scenes.FLUID)[:, None]
+    gr, gu = np.zeros_like(sc.pos), st.vel * f
+    onu = 0.0
+    for t in reversed(range(T)):
+        s, prm = states[t]
+        gr, gu, _, gn = oracle.step_vjp(prm, s, gr, gu, with_nu=True)
+        onu += gn.sum()
+    assert abs(g_nu - onu) <= 1e-7 * abs(onu), (g_nu, onu)
+    _close(g_u0, gu, tol=1e-7, what="dKE/du0")
