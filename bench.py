@@ -120,6 +120,8 @@ def parse():
                          "times the mixed step with each of the others")
     ap.add_argument("--stiff-steps", type=int, default=10,
                     help="timed steps of the stiff PPE (alpha_c = 0) comparison (0: skip)")
+    ap.add_argument("--rollout-steps", type=int, default=200,
+                    help="steps of the timed differentiable sloshing rollout (0: skip)")
     ap.add_argument("--adjoint-steps", type=int, default=20,
                     help="forward and reverse steps timed on the 3D sloshing tank (0: skip)")
     return ap.parse_args()
@@ -384,6 +386,39 @@ def run_gb300(args):
         barrier()
         ms_f, ms_r, ms_rh = max_over_ranks(ms_f), max_over_ranks(ms_r), max_over_ranks(ms_rh)
         sim5.close()
+        # the differentiable rollout: args.rollout_steps steps from rest with a checkpoint every
+        # 20, then d(kinetic energy)/d(nu, u0) through torch.autograd (the backward recomputes
+        # each segment from its checkpoint and runs the reverse steps); wall clock on the host
+        # around each pass with the device synchronised, CUDA tensors throughout
+        roll = None
+        if args.rollout_steps > 0:
+            from paper_2105_01677_gb300 import autograd
+            TR = args.rollout_steps
+            simr = mps.Simulation(sc5, torch_alloc=True, use_torch_stream=True, precision=0,
+                                  dt=dt5, cg_tol=1e-8)
+            fr = torch.tensor([force(t) for t in range(TR)], dtype=torch.float64)
+            x0 = torch.tensor(sc5.pos, dtype=torch.float64, device=dev)
+            times = []
+            for rep_i in range(2):   # the first pass captures the graphs: the second is timed
+                u0 = torch.zeros((sc5.n, 3), dtype=torch.float64, device=dev, requires_grad=True)
+                nu = torch.tensor(1e-6, dtype=torch.float64, requires_grad=True)
+                barrier()
+                t0 = time.perf_counter()
+                xT, uT = autograd.rollout(simr, x0, u0, fr, checkpoint_every=20, nu=nu)
+                ke = autograd.kinetic_energy(uT, sc5.types)
+                torch.cuda.synchronize(dev)
+                t1 = time.perf_counter()
+                ke.backward()
+                torch.cuda.synchronize(dev)
+                t2 = time.perf_counter()
+                times.append((t1 - t0, t2 - t1))
+            simr.close()
+            tf_, tb_ = max_over_ranks(times[-1][0]), max_over_ranks(times[-1][1])
+            roll = {"steps": TR, "checkpoint_every": 20, "loss": "final kinetic energy",
+                    "wrt": ["nu", "u0"], "precision": "fp64", "cg_tol": 1e-8,
+                    "forward_s": tf_, "backward_s": tb_,
+                    "value": world * sc5.n * TR / (tf_ + tb_), "unit": UNIT,
+                    "timing": "host wall clock with the device synchronised (second pass)"}
         adjoint = {"workload": "3D sloshing tank 0.5 x 0.3 x 0.3 m half full, l0 0.008 m, "
                                "forcing 0.02 m at 1.2 Hz as a tank-frame body force, dt 5e-5 s",
                    "particles": sc5.n, "fluid": sc5.n_fluid, "precision": "fp64",
@@ -399,7 +434,8 @@ def run_gb300(args):
                                     "h2d_bytes_per_step": int(2 * sc5.n * 3 * 8),
                                     "d2h_bytes_per_step": int(2 * sc5.n * 3 * 8 + 24),
                                     "cotangents": "pageable host buffers (mps_step_vjp)"},
-                   "reverse_over_forward": ms_r / ms_f}
+                   "reverse_over_forward": ms_r / ms_f,
+                   "rollout": roll}
         return adjoint
 
 

@@ -1,0 +1,149 @@
+"""The differentiable rollout at full size: 200 steps of the 3D sloshing tank (85,564
+particles, l0 = 0.008 m, forcing 0.02 m at 1.2 Hz as a tank-frame body force, dt = 5e-5 s,
+FP64), checkpointed every 20 steps.  Losses of the final state: the fluid's kinetic energy
+and the mean height of its free-surface particles.  Their gradients with respect to the
+kinematic viscosity (one value for all particles) and to a seeded initial velocity field
+(along a seeded direction) are checked against
+
+  - central differences of the GPU rollout itself, and
+  - the oracle's reverse steps chained along the oracle's own 200-step trajectory (the FP64
+    CPU reference gradient), for a combination of both losses (one chain covers both: the
+    reverse steps are linear in the cotangent).
+
+Steps of the central differences.  The equation-of-state path is smooth in every input and
+takes h = 1e-6 (m^2/s for nu, m/s along the unit-RMS direction for the velocity field); its
+differences agree to ~1e-8.  The PPE path is only piecewise smooth over 200 steps: the clamp
+max(p, 0) and the minimum p_hat have kinks, and a particle whose number density crosses the
+free-surface threshold (Eq. 15) switches its PPE row to p = 0, a jump.  Along the velocity
+field the differences then stay ~2-3e-4 away from the adjoint for h = 1e-7 ... 1e-6 (the
+jumps crossed grow with h while their weight falls as 1/h) and grow beyond (1.6e-3 at 1e-5),
+so that check is bounded at 1e-3; the exact comparison of the PPE path is the chained oracle
+below (1e-4).  In the viscosity, h = 1e-8 m^2/s (1% of nu) agrees to ~1e-7.  Both sides run
+their PPE solves to 1e-13."""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+import scenes
+from _parity import gpu_params, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+DT, T, K = 5e-5, 200, 20
+NU = 1e-6
+CG = 1e-13
+FD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available()
+    __graft_entry__.build()
+    oracle.set_threads(0)
+
+
+def _forcing():
+    return np.array([(float(scenes.sloshing_forcing(t * DT)), 0.0, -9.81) for t in range(T)])
+
+
+@pytest.fixture(scope="module")
+def setup():
+    sc = scenes.sloshing_3d()
+    assert sc.n == 85564
+    f = sc.types == scenes.FLUID
+    rng = np.random.default_rng(5)
+    u0 = np.zeros_like(sc.vel)
+    u0[f] = 0.01 * rng.standard_normal((int(f.sum()), 3))   # the seeded initial velocity field
+    v = np.zeros_like(sc.vel)
+    v[f] = rng.standard_normal((int(f.sum()), 3))           # the direction of its derivative
+    return sc, u0, v
+
+
+def _rollout(sim, sc, u0, nu_value, grad=None):
+    """(KE, H) of the final state, or with grad in {"ke", "h"} (loss, dL/dnu, dL/du0, flags)."""
+    import torch
+    from paper_2105_01677_gb300 import autograd
+    dev = torch.device("cuda", 0)
+    x = torch.tensor(sc.pos, dtype=torch.float64, device=dev)
+    u = torch.tensor(u0, dtype=torch.float64, device=dev, requires_grad=grad is not None)
+    nu = torch.tensor(nu_value, dtype=torch.float64, requires_grad=grad is not None)
+    xT, uT = autograd.rollout(sim, x, u, torch.tensor(_forcing()), checkpoint_every=K, nu=nu)
+    flags = sim.read(want=("flags",))["flags"].copy()
+    ke = autograd.kinetic_energy(uT, sc.types)
+    hh = autograd.mean_surface_height(xT, flags, sc.types)
+    if grad is None:
+        return float(ke.detach()), float(hh.detach())
+    loss = ke if grad == "ke" else hh
+    loss.backward()
+    return (float(loss.detach()), float(nu.grad), u.grad.detach().cpu().numpy(), flags,
+            xT.detach().cpu().numpy(), uT.detach().cpu().numpy())
+
+
+@pytest.mark.parametrize("path", ["ppe", "eos"])
+def test_rollout_gradients_match_central_differences(setup, path):
+    from paper_2105_01677_gb300 import mps
+    sc, u0, v = setup
+    kw = dict(dt=DT, cg_tol=CG) if path == "ppe" else dict(dt=DT, pressure_mode=1, c0=20.0)
+    h_nu, h_u = (1e-8, 1e-7) if path == "ppe" else (1e-6, 1e-6)
+    sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, **gpu_params(sc, **kw))
+    try:
+        adj = {}
+        for loss in ("ke", "h"):
+            _, g_nu, g_u, *_ = _rollout(sim, sc, u0, NU, grad=loss)
+            adj[loss] = (g_nu, float((g_u * v).sum()))
+        p_nu, m_nu = _rollout(sim, sc, u0, NU + h_nu), _rollout(sim, sc, u0, NU - h_nu)
+        p_u, m_u = _rollout(sim, sc, u0 + h_u * v, NU), _rollout(sim, sc, u0 - h_u * v, NU)
+    finally:
+        sim.close()
+    for i, loss in enumerate(("ke", "h")):
+        fd_nu = (p_nu[i] - m_nu[i]) / (2.0 * h_nu)
+        fd_u = (p_u[i] - m_u[i]) / (2.0 * h_u)
+        a_nu, a_u = adj[loss]
+        assert abs(fd_nu - a_nu) <= FD_TOL * abs(a_nu), (path, loss, "nu", fd_nu, a_nu)
+        tol_u = FD_TOL if path == "eos" else 1e-3   # the PPE path's jumps (docstring)
+        assert abs(fd_u - a_u) <= tol_u * abs(a_u), (path, loss, "u0", fd_u, a_u)
+
+
+def test_rollout_gradients_match_the_chained_oracle(setup):
+    """PPE path: the GPU gradients of KE + lam H (lam scales H to KE's size) against the
+    oracle's 200 reverse steps chained along its own trajectory from the same inputs."""
+    from paper_2105_01677_gb300 import mps
+    sc, u0, v = setup
+    sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
+                         **gpu_params(sc, dt=DT, cg_tol=CG))
+    try:
+        ke, gnu_ke, gu_ke, flags, xT, uT = _rollout(sim, sc, u0, NU, grad="ke")
+        hh, gnu_h, gu_h, *_ = _rollout(sim, sc, u0, NU, grad="h")
+    finally:
+        sim.close()
+    lam = ke / hh
+    g_nu = gnu_ke + lam * gnu_h
+    g_u = gu_ke + lam * gu_h
+    # the oracle's own trajectory from the same initial state
+    forcing = _forcing()
+    st = oracle.State.from_scene(sc)
+    st.vel = u0.copy()
+    states = []
+    for t in range(T):
+        prm = oracle_params(sc, dt=DT, cg_tol=CG, nu=NU, g=tuple(forcing[t]))
+        states.append((st.copy(), prm))
+        oracle.step(prm, st)
+    assert np.abs(st.pos - xT).max() <= 1e-8 * sc.l0
+    f = st.types == scenes.FLUID
+    surf = f & ((st.flags & 1) != 0)
+    assert np.array_equal(surf, f & ((flags & 1) != 0))      # the same free-surface set
+    gr = np.zeros_like(st.pos)
+    gr[surf, 2] = lam / surf.sum()
+    gu = st.vel * f[:, None]
+    onu = 0.0
+    for t in reversed(range(T)):
+        s, prm = states[t]
+        gr, gu, _, gn = oracle.step_vjp(prm, s, gr, gu, with_nu=True)
+        onu += gn.sum()
+    assert abs(g_nu - onu) <= FD_TOL * abs(onu), (g_nu, onu)
+    d_gpu, d_ora = float((g_u * v).sum()), float((gu * v).sum())
+    assert abs(d_gpu - d_ora) <= FD_TOL * abs(d_ora), (d_gpu, d_ora)
+    scale = np.abs(gu).max()
+    assert np.abs(g_u - gu).max() <= 1e-3 * scale
