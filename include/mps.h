@@ -122,6 +122,11 @@ typedef struct {
                                * after mps_write_state).  The stop rule is unchanged (FP64    *
                                * ||b - A p|| / ||b|| <= cg_tol); a step then depends on the   *
                                * previous steps' solves at the level of the tolerance          */
+    int32_t step_graph;       /* 1 (default): a step on the mixed path (device-driven PPE) or  *
+                               * the equation-of-state path, with candidate lists gathered    *
+                               * every step and the stage timers off, runs as one CUDA graph: *
+                               * one launch and one synchronisation; 0: launch by launch.     *
+                               * Results are identical.                                        */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;
@@ -149,6 +154,8 @@ typedef struct {
     int64_t pairs_pnd;        /* number-density terms evaluated (pairs within re_n)           */
     int64_t list_tests;       /* candidate-list entries classified at r* (distance tests of  *
                                * the number-density / PPE assembly)                           */
+    int32_t step_graph;       /* 1 if the step ran as one CUDA graph launch                    */
+    int32_t pad;
 } mps_report;
 
 /* Opaque context: device buffers, stream and derived constants of one particle system. */
@@ -157,7 +164,8 @@ typedef struct mps_ctx mps_ctx;
 /* Fill *p with the defaults: dim 2, l0 0.01, re_n 2.1 l0, re_lap 4 l0, rho 1000, nu 1e-6,
  * dt 1e-4, beta 0.97, g (0, -9.81, 0), c0 20, gamma 7, alpha_c 1e-7, cg_tol 1e-8,
  * cg_max_iter 0, precision 0, clamp 1, nbr_cap 0, cell_skin 0.1, box [0,1]^dim,
- * inner_tol 1e-4, max_outer 30, ppe_operator 0, device 0, cg_x0 0, no stream, no hooks. */
+ * inner_tol 1e-4, max_outer 30, ppe_operator 0, device 0, cg_x0 0, step_graph 1, no stream,
+ * no hooks. */
 void mps_params_default(mps_params* p);
 
 /* Create a context from n particles (the problem statement of Sec. 3 and the particle kinds

@@ -63,6 +63,8 @@ void lattice_constants(int dim, double l0, double re, double* n0, double* lambda
     *count = cnt;
 }
 
+}  // namespace
+
 // FP32 pre-filter band for r^2 < re^2 (see gather.cu).  Coordinates are stored relative to
 // the grid origin, so |x| <= X; each is rounded once to FP32 (error <= 2^-24 X), the
 // difference and the squares add a few more roundings.
@@ -91,6 +93,8 @@ Radius make_radius(double re, double X) {
     r.ff_tol = (float)tol;
     return r;
 }
+
+namespace {
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -459,6 +463,8 @@ constexpr double kMinListSkin = 0.02;
 int do_step(Ctx* c, bool advance, mps_report* rep) {
     const mps_params& P = c->prm;
     int rc;
+    if (step_graph_eligible(c, advance)) return step_graph_step(c, rep);
+    rep->step_graph = 0;
     const bool keep = P.list_every > 1;
     // the radius the skin is measured against: max(re) (of the scene with the smallest
     // spacing in an ensemble)
@@ -664,6 +670,7 @@ void mps_params_default(mps_params* p) {
     p->box_max[0] = p->box_max[1] = p->box_max[2] = 1.0;
     p->inner_tol = 1e-4;
     p->max_outer = 30;
+    p->step_graph = 1;
 }
 
 int mps_create(const double* pos, const double* vel, const int8_t* types, int64_t n,
@@ -806,6 +813,7 @@ int mps_autotune(mps_ctx* c, int32_t repeats, int32_t* gather_block) {
     cudaEventDestroy(e1);
     c->prm.gather_block = best;
     if (gather_block) *gather_block = best;
+    step_graphs_destroy(c);   // they captured the gather with its block shape
     MPS_CUDA(c, cudaGetLastError());
     return MPS_OK;
 }
@@ -1043,6 +1051,7 @@ int mps_set_fluid_properties(mps_ctx* c, const double* rho, const double* nu) {
     MPS_CUDA(c, cudaGetLastError());
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
     bucket_graphs_destroy(c);   // the captured builds gather the properties that were set
+    step_graphs_destroy(c);
     return MPS_OK;
 }
 
@@ -1174,6 +1183,10 @@ void mps_destroy(mps_ctx* c) {
             if (c->ev[k]) cudaEventDestroy(c->ev[k]);
         ppe_graphs_destroy(c);
         bucket_graphs_destroy(c);
+        step_graphs_destroy(c);
+        if (c->ctl_host) cudaFreeHost(c->ctl_host);
+        if (c->rv_var_host) cudaFreeHost(c->rv_var_host);
+        if (c->scene_sums_host) cudaFreeHost(c->scene_sums_host);
         free_all(c);
         if (c->st_host) cudaFreeHost(c->st_host);
         if (c->cg_host) cudaFreeHost(c->cg_host);

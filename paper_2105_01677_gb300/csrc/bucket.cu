@@ -250,6 +250,20 @@ void load_ptrs(Ctx* c, const BucketPtrs& b) {
 }
 }  // namespace
 
+int bucket_capture_launches(Ctx* c) { return bucket_launches(c, true); }
+
+void state_ptrs_save(const Ctx* c, void* rec) {
+    static_assert(sizeof(BucketPtrs) <= kPtrRecord, "pointer record too small");
+    const BucketPtrs b = save_ptrs(c);
+    std::memcpy(rec, &b, sizeof b);
+}
+
+void state_ptrs_load(Ctx* c, const void* rec) {
+    BucketPtrs b;
+    std::memcpy(&b, rec, sizeof b);
+    load_ptrs(c, b);
+}
+
 int bucket_build(Ctx* c, bool mutate) {
     if (!mutate) return bucket_launches(c, false);
     BucketGraph* bg = nullptr;

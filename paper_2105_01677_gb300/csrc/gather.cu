@@ -160,6 +160,7 @@ struct VerletOp {
     const int8_t* type;
     DevStatus* st;
     float hv2;
+    const float* hv2_dev;   // non-null: the bound is read here (a step graph's control block)
     int cap_v;
     int32_t* vcol;
     int32_t* vcnt;
@@ -182,7 +183,7 @@ struct VerletOp {
     __device__ void begin(int i, bool act, Center& c) const {
         c.cnt = 0;
         c.row = vcol + sell(i, 0, cap_v);
-        c.hv2 = hv2;
+        c.hv2 = hv2_dev ? *hv2_dev : hv2;
         if (act) {
             c.p32 = pos32[i];
             if (sid) c.hv2 = scn[sid[i]].rv.hi;
@@ -301,6 +302,7 @@ void launch_verlet(Ctx* c) {
     op.type = c->type;
     op.st = c->st;
     op.hv2 = c->r_v.hi;
+    op.hv2_dev = c->capture_ctl ? &c->capture_ctl->hv2_live : nullptr;
     op.cap_v = c->cap_v;
     op.vcol = c->vl_col;
     op.vcnt = c->vl_cnt;

@@ -178,6 +178,22 @@ void launch_adj_back(Ctx* c, double* d_gsum);
 void launch_adj_store(Ctx* c, double* d_out_r, double* d_out_u, double* d_out_nu);
 
 // ---------------------------------------------------------------- update.cu
+// the mixed solve's nodes appended to a graph (ppe.cu), its start scalars and kernel count
+int add_mixed_solve(Ctx* c, cudaGraph_t G, cudaGraphNode_t dep, double* x, bool guess,
+                    cudaGraphNode_t* last);
+void mixed_init_scalars(Ctx* c, CgScalars* init);
+int64_t mixed_solve_launches(Ctx* c, bool guess, const CgScalars& h);
+// the stepping bucket build's launches and the state buffer assignment (bucket.cu)
+int bucket_capture_launches(Ctx* c);
+constexpr size_t kPtrRecord = 24 * sizeof(void*);
+void state_ptrs_save(const Ctx* c, void* rec);
+void state_ptrs_load(Ctx* c, const void* rec);
+// the candidate and predicate bands of radius re for coordinates up to X (api.cu)
+Radius make_radius(double re, double X);
+// whole steps as CUDA graphs (stepgraph.cu)
+bool step_graph_eligible(const Ctx* c, bool advance);
+int step_graph_step(Ctx* c, mps_report* rep);
+void step_graphs_destroy(Ctx* c);
 void launch_clamp_pmin(Ctx* c);
 void launch_gradient_correct(Ctx* c);
 void launch_unpermute(Ctx* c, double* d_pos, double* d_vel, double* d_p, double* d_nstar,
@@ -215,6 +231,31 @@ struct BucketGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t launches = 0;
+    void* after[24] = {};
+};
+
+// Per-step control block of a step run as one CUDA graph (stepgraph.cu): written by the
+// host into pinned memory and copied to the device before each launch (the host part), then
+// updated by the graph's own kernels (the device part).
+struct StepCtl {
+    CgScalars cg_init;   // host: start values of the mixed solve's scalars
+    double g[3];         // host: external acceleration of this step
+    double half[2];      // host: s' max(re)/2 of the adaptive list skin s' (0) and of cell_skin (1)
+    float hv2[2];        // host: single scene: the candidate bound of the two skins
+    int can_retry;       // host: the adaptive skin is below cell_skin
+    int attempt;         // device: 0, or 1 after a retry with the full skin
+    int skin_err;        // device: a particle outran the full skin (MPS_ESKIN)
+    float hv2_live;      // device: the bound the gather reads
+};
+
+// One step as a CUDA graph, one per starting state buffer (the bucket build alternates the
+// buffers), with the buffer assignment it leaves behind and its kernel counts.
+struct StepGraph {
+    const double4* pos = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches_pre = 0, launches_attempt = 0, launches_post = 0;
+    bool guess = false;
     void* after[24] = {};
 };
 
@@ -269,6 +310,20 @@ struct Ctx {
     AdjBuffers adj;
     PpeGraph ppe_graph[2];
     BucketGraph bucket_graph[2];
+    // the candidate and predicate bands of radius re for coordinates up to X (api.cu)
+Radius make_radius(double re, double X);
+// whole steps as CUDA graphs (stepgraph.cu): the control block (device and pinned host
+    // mirror), the two scene tables of an ensemble (adaptive and full list skin), the pinned
+    // copy of the per-scene residual sums, and the control block kernels read while a step
+    // is being captured (null otherwise)
+    StepGraph step_graph[2];
+    StepCtl* ctl = nullptr;
+    StepCtl* ctl_host = nullptr;
+    Radius* rv_var = nullptr;          // ensemble: candidate radius of every scene, 2 skins
+    Radius* rv_var_host = nullptr;     // pinned staging of the adaptive half
+    double* scene_sums_host = nullptr;
+    double rv_var_skin = -1.0;         // the adaptive skin the device table holds
+    StepCtl* capture_ctl = nullptr;
 
     // state (sorted order) and double buffers
     double4 *pos, *vel, *pos_alt, *vel_alt;

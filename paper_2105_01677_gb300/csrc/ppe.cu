@@ -762,23 +762,26 @@ static int add_while(Ctx* c, cudaGraph_t g, cudaGraphNode_t dep, cudaGraphCondit
     return MPS_OK;
 }
 
-static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
+// The mixed solve's nodes appended to graph G after node dep (null: at its root): the start
+// sequence, then the WHILE of the refinement sweeps with the WHILE of the inner CG inside.
+// *last receives the outer WHILE node.  The scalars (c->cg) must hold their start values
+// (mixed_init_scalars) when the nodes run.
+int add_mixed_solve(Ctx* c, cudaGraph_t G, cudaGraphNode_t dep, double* x, bool guess,
+                    cudaGraphNode_t* last) {
     const int n = (int)c->n;
     const int gs = row_grid(c), gv = vec_grid(c);
     const double tol2 = c->prm.cg_tol * c->prm.cg_tol;
     const SellView sv = sell_view(c, c->bvec);
     cudaStream_t s = c->stream;
     const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
-    MPS_CUDA(c, cudaStreamSynchronize(s));
-    cudaGraph_t G = nullptr, B = nullptr, Bi = nullptr, tmp = nullptr;
+    cudaGraph_t B = nullptr, Bi = nullptr, tmp = nullptr;
     cudaGraphConditionalHandle h_out = 0, h_in = 0;
     cudaGraphNode_t n_start, n_outer, n_init, n_inner;
-    MPS_CUDA(c, cudaGraphCreate(&G, 0));
-    pg->graph = G;
     MPS_CUDA(c, cudaGraphConditionalHandleCreate(&h_out, G, 0, cudaGraphCondAssignDefault));
     const bool multi = c->n_scenes > 1;
-    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, G, nullptr, nullptr, 0, mode));
-    if (pg->guess) {
+    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, G, dep ? &dep : nullptr, nullptr, dep ? 1 : 0,
+                                              mode));
+    if (guess) {
         // from the previous solution: b.b, x = x0, r = b - A x and the refinement loop's
         // conditional as after a sweep (per scene in an ensemble)
         k_bnorm64<<<gs, kBT, 0, s>>>(sv, c->cg, tol2);
@@ -829,10 +832,43 @@ static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
         k_scene_decide<<<1, kBT, 0, s>>>(c->cg, c->scene_sums, c->n_scenes, c->prm.cg_tol, h_out);
     }
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+    *last = n_outer;
+    return MPS_OK;
+}
+
+// Start values of the scalars of a device-driven mixed solve: caps, inner tolerance and the
+// weights of the initial guess.
+void mixed_init_scalars(Ctx* c, CgScalars* init) {
+    const int max_total = c->prm.cg_max_iter > 0 ? c->prm.cg_max_iter
+                                                 : (int)std::min<int64_t>(10 * c->n, 1 << 30);
+    *init = CgScalars{};
+    init->max_iters = max_total;
+    init->max_total = max_total;
+    init->max_outer = c->prm.max_outer > 0 ? c->prm.max_outer : 30;
+    init->inner_tol = c->prm.inner_tol;
+    guess_weights(c, init->gw);
+}
+
+// Kernels one mixed solve ran (counted like the host loop's launches)
+int64_t mixed_solve_launches(Ctx* c, bool guess, const CgScalars& h) {
+    const bool multi = c->n_scenes > 1;
+    return (guess ? (multi ? 5 : 3) : 1) + (multi ? 5 : 3) * (int64_t)h.outer + 3 * (int64_t)h.total;
+}
+
+namespace {
+static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    cudaGraph_t G = nullptr;
+    MPS_CUDA(c, cudaGraphCreate(&G, 0));
+    pg->graph = G;
+    cudaGraphNode_t last = nullptr;
+    int rc = add_mixed_solve(c, G, nullptr, x, pg->guess, &last);
+    if (rc) return rc;
     MPS_CUDA(c, cudaGraphInstantiate(&pg->exec, G, 0));
     pg->x = x;
     return MPS_OK;
 }
+}  // namespace
 
 void ppe_graphs_destroy(Ctx* c) {
     for (PpeGraph& pg : c->ppe_graph) {
@@ -861,12 +897,9 @@ static int mixed_graph_solve(Ctx* c, double* x, mps_report* rep, int max_total) 
             return rc;
         }
     }
-    CgScalars init{};
-    init.max_iters = max_total;
-    init.max_total = max_total;
-    init.max_outer = c->prm.max_outer > 0 ? c->prm.max_outer : 30;
-    init.inner_tol = c->prm.inner_tol;
-    guess_weights(c, init.gw);
+    CgScalars init;
+    mixed_init_scalars(c, &init);
+    init.max_iters = init.max_total = max_total;
     MPS_CUDA(c, cudaMemcpyAsync(c->cg, &init, sizeof(CgScalars), cudaMemcpyHostToDevice, c->stream));
     MPS_CUDA(c, cudaGraphLaunch(pg->exec, c->stream));
     int rc;
@@ -875,8 +908,7 @@ static int mixed_graph_solve(Ctx* c, double* x, mps_report* rep, int max_total) 
     const bool multi = c->n_scenes > 1;
     // kernels the graph ran: start, per sweep init + update + residual (+ the per-scene sums
     // and decision of an ensemble), per inner iteration 3
-    c->launches += (pg->guess ? (multi ? 5 : 3) : 1) + (multi ? 5 : 3) * (int64_t)h.outer +
-                   3 * (int64_t)h.total;
+    c->launches += mixed_solve_launches(c, pg->guess, h);
     rep->cg_iters = h.total;
     rep->cg_outer = h.outer;
     c->last_cg_iters = std::max(4, h.total / std::max(h.outer, 1));

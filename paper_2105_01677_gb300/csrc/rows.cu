@@ -97,6 +97,7 @@ struct PredictArgs {
     DevStatus* st;
     Radius r;
     double coef_lap, nu, dt, g0, g1, g2, bmin0, bmin1, bmin2;
+    const double* g_dev;    // non-null: the acceleration is read here (a step graph's control block)
 };
 
 // MULTI: an ensemble, whose radii and coefficients are those of each row's scene
@@ -188,9 +189,11 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
         const double l0 = coef_lap * s0, l1 = coef_lap * s1, l2 = coef_lap * s2;
         double4 us, ps;
         const double nu = a.nu_s ? a.nu_s[i] : a.nu;
-        us.x = __dadd_rn(ui.x, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(nu, l0), a.g0)));
-        us.y = __dadd_rn(ui.y, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(nu, l1), a.g1)));
-        us.z = __dadd_rn(ui.z, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(nu, l2), a.g2)));
+        const double g0 = a.g_dev ? a.g_dev[0] : a.g0, g1 = a.g_dev ? a.g_dev[1] : a.g1,
+                     g2 = a.g_dev ? a.g_dev[2] : a.g2;
+        us.x = __dadd_rn(ui.x, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(nu, l0), g0)));
+        us.y = __dadd_rn(ui.y, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(nu, l1), g1)));
+        us.z = __dadd_rn(ui.z, __dmul_rn(a.dt, __dadd_rn(__dmul_rn(nu, l2), g2)));
         us.w = 0.0;
         ps.x = __dadd_rn(pi.x, __dmul_rn(a.dt, us.x));
         ps.y = __dadd_rn(pi.y, __dmul_rn(a.dt, us.y));
@@ -732,6 +735,7 @@ void launch_predict_rows(Ctx* c) {
     a.g0 = P.g[0];
     a.g1 = P.g[1];
     a.g2 = c->dim == 3 ? P.g[2] : 0.0;
+    a.g_dev = c->capture_ctl ? c->capture_ctl->g : nullptr;
     a.bmin0 = c->grid.bmin[0];
     a.bmin1 = c->grid.bmin[1];
     a.bmin2 = c->grid.bmin[2];

@@ -38,7 +38,7 @@ class mps_params(C.Structure):
                 ("ppe_operator", C.c_int32), ("device", C.c_int32), ("gather_block", C.c_int32),
                 ("list_every", C.c_int32), ("kernel", C.c_int32), ("gradient_form", C.c_int32),
                 ("source_term", C.c_int32), ("ppe_host_loop", C.c_int32),
-                ("cg_x0", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
+                ("cg_x0", C.c_int32), ("step_graph", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
                 ("alloc_user", C.c_void_p)]
 
 
@@ -52,11 +52,13 @@ class mps_report(C.Structure):
                 ("n_ghost", C.c_int64), ("n_ppe_rows", C.c_int64), ("max_disp", C.c_double),
                 ("n0_pnd", C.c_double), ("n0_lap", C.c_double), ("lambda_", C.c_double),
                 ("steps_done", C.c_int64), ("cand_tests", C.c_int64), ("pairs_ppe", C.c_int64),
-                ("pairs_pnd", C.c_int64), ("list_tests", C.c_int64)]
+                ("pairs_pnd", C.c_int64), ("list_tests", C.c_int64), ("step_graph", C.c_int32),
+                ("pad", C.c_int32)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["lambda"] = d.pop("lambda_")
+        d.pop("pad")
         return d
 
 

@@ -1,0 +1,147 @@
+"""Whole steps as one CUDA graph (step_graph = 1, the default) against the same steps launched
+one by one (step_graph = 0): the kernels are the same, so every field must agree bit for
+bit, over several steps (which exercises both state-buffer parities of the graph, the guess
+history and the adaptive list skin), for one scene and for an ensemble, on the mixed PPE
+path and the equation-of-state path; the retry with the full skin, MPS_ESKIN and the device
+errors must come out as on the host-driven path.  The parity of either path with the oracle
+is covered by the other GPU tests, which run the graph by default."""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import scenes
+from _parity import gpu_params, small_3d
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("pos", "vel", "p", "n_star", "flags", "types")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available()
+    __graft_entry__.build()
+
+
+def _run(sc, steps, step_graph, **kw):
+    from paper_2105_01677_gb300 import mps
+    sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
+                         **gpu_params(sc, step_graph=step_graph, **kw))
+    reps, states = [], []
+    try:
+        for _ in range(steps):
+            rc, rep = sim.step(1)
+            reps.append(rep)
+            states.append(sim.read())
+    finally:
+        sim.close()
+    return reps, states
+
+
+def _same(a, b):
+    for k in FIELDS:
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("case", ["2d-mixed", "3d-mixed-guess", "2d-eos-mixed", "3d-eos-fp64",
+                                  "2d-mixed-two-phase"])
+def test_step_graph_equals_launch_by_launch(case):
+    kw = {}
+    rho_i = nu_i = None
+    if case == "2d-mixed":
+        sc, kw = scenes.dam_break_2d(seed=1), dict(precision=1)
+    elif case == "3d-mixed-guess":
+        sc, kw = small_3d(seed=2), dict(precision=1, dt=5e-5, cg_x0=3)
+    elif case == "2d-eos-mixed":
+        sc, kw = scenes.dam_break_2d(seed=3), dict(precision=1, pressure_mode=1, c0=20.0)
+    elif case == "3d-eos-fp64":
+        sc, kw = small_3d(seed=4), dict(precision=0, pressure_mode=1, c0=20.0, dt=5e-5)
+    else:
+        sc = scenes.dam_break_2d(seed=5)
+        kw = dict(precision=1, cg_x0=2)
+    if case == "2d-mixed-two-phase":
+        rho_i, nu_i = scenes.two_phase(sc, rho=(1000.0, 800.0), nu=(1e-6, 5e-6))
+        kw.update(rho_i=rho_i, nu_i=nu_i)
+    rg, sg = _run(sc, 6, 1, **kw)
+    rh, sh = _run(sc, 6, 0, **kw)
+    assert all(r["step_graph"] == 1 for r in rg)
+    assert all(r["step_graph"] == 0 for r in rh)
+    for k in range(6):
+        _same(sg[k], sh[k])
+        for f in ("cg_iters", "cg_outer", "cg_resid", "n_surface", "n_ppe_rows", "max_disp",
+                  "cand_tests", "pairs_ppe", "pairs_pnd", "list_tests"):
+            assert rg[k][f] == rh[k][f], (k, f)
+
+
+def test_step_graph_ensemble_equals_launch_by_launch():
+    from paper_2105_01677_gb300 import mps
+    E = scenes.ensemble_2d(count=12, seed=3, fluid=(500, 3000))
+    out = []
+    for sgflag in (1, 0):
+        ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
+                           cg_tol=1e-8, cg_x0=3, step_graph=sgflag)
+        try:
+            reps, states, res = [], [], []
+            for _ in range(5):
+                rc, rep = ens.step(1)
+                reps.append(rep)
+                states.append(ens.read())
+                res.append(ens.residuals())
+        finally:
+            ens.close()
+        out.append((reps, states, res))
+    (rg, sg, qg), (rh, sh, qh) = out
+    assert all(r["step_graph"] == 1 for r in rg) and all(r["step_graph"] == 0 for r in rh)
+    for k in range(5):
+        assert np.array_equal(qg[k], qh[k])
+        assert rg[k]["cg_iters"] == rh[k]["cg_iters"]
+        for a, b in zip(sg[k], sh[k]):
+            _same(a, b)
+
+
+def test_step_graph_retries_with_the_full_skin():
+    """A calm first step leaves a small adaptive list skin; the state is then given velocities
+    that move particles beyond it but within the full cell skin: both paths gather again with
+    the full skin, and agree bit for bit."""
+    from paper_2105_01677_gb300 import mps
+    sc = scenes.dam_break_2d(seed=6)
+    f = sc.types == scenes.FLUID
+    rng = np.random.default_rng(7)
+    kick = np.zeros_like(sc.vel)
+    # up to 1.4 mm in one 1e-4 s step: past half a list skin of 0.02 (0.4 mm at
+    # re = 0.04 m), within half the full skin of 0.1 (2 mm)
+    kick[f] = rng.uniform(-1.0, 1.0, size=(int(f.sum()), 2)) * 10.0
+    states = []
+    for sgflag in (1, 0):
+        sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
+                             **gpu_params(sc, precision=1, step_graph=sgflag))
+        try:
+            sim.step(2)
+            st = sim.read()
+            sim.write(st["pos"], kick, st["types"])
+            rc, rep = sim.step(1)
+            assert rc == 0 and rep["max_disp"] > 0.4e-3, rep["max_disp"]
+            states.append(sim.read())
+        finally:
+            sim.close()
+    _same(states[0], states[1])
+
+
+def test_step_graph_reports_skin_and_coincidence_errors():
+    from paper_2105_01677_gb300 import mps
+    sc = scenes.dam_break_2d(seed=8)
+    f = np.flatnonzero(sc.types == scenes.FLUID)
+    fast = sc.copy()
+    fast.vel[f[10]] = [300.0, 0.0]     # 3 cm in one step: beyond any skin
+    coinc = sc.copy()
+    coinc.pos[f[1]] = coinc.pos[f[0]]
+    for sgflag in (1, 0):
+        for scene, code in ((fast, mps.ESKIN), (coinc, mps.ECOINCIDENT)):
+            sim = mps.Simulation(scene, torch_alloc=True, use_torch_stream=True,
+                                 **gpu_params(scene, precision=1, step_graph=sgflag))
+            try:
+                rc, rep = sim.step(1, check=False)
+                assert rc == code, (sgflag, rc, code)
+            finally:
+                sim.close()
