@@ -127,6 +127,10 @@ typedef struct {
                                * every step and the stage timers off, runs as one CUDA graph: *
                                * one launch and one synchronisation; 0: launch by launch.     *
                                * Results are identical.                                        */
+    int32_t inner_cg;         /* mixed inner CG of the device-driven solve: 0 (default) three  *
+                               * kernels per iteration; 1 two (fused: the recurrences of      *
+                               * Chronopoulos and Gear; rounds differently, same stop rule)    */
+    int32_t spmv_block;       /* threads per block of the FP32 SpMV: 256 or 512; 0: 512         */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;
@@ -314,13 +318,31 @@ int mps_create_ensemble(const double* pos, const double* vel, const int8_t* type
                         const int32_t* scene, int64_t n, const mps_params* params,
                         const mps_scene* scenes, int32_t n_scenes, mps_ctx** out);
 
-/* Autotuning (a tool of this library; the paper has none): times the candidate gather of
- * the current state with each block shape (32, 64, 96 and 128 threads per cell block,
- * `repeats` launches each, CUDA events on the context's stream) and keeps the fastest in
- * params.gather_block, which *gather_block (nullable) receives.  Candidate lists come out
- * identical whatever the shape, so results do not change; the state is reordered as by a
- * step's bucket build.  Errors: MPS_EINVAL (repeats < 1), MPS_EDEVICE. */
-int mps_autotune(mps_ctx* ctx, int32_t repeats, int32_t* gather_block);
+/* Autotuning (a tool of this library; the paper has none): times the launch shapes and the
+ * inner solver's form on the current state with CUDA events on the context's stream
+ * (`repeats` timed runs each after one untimed run) and keeps the fastest:
+ *   - the candidate gather's cell block: 32, 64, 96 or 128 threads (params.gather_block);
+ *   - mixed PPE only, on the system of a solve at the current state: the FP32 SpMV's block,
+ *     256 or 512 threads, and the inner CG as three kernels per iteration (SpMV; x, r
+ *     update; direction update) or two (the recurrences of Chronopoulos and Gear: SpMV of
+ *     the residual; one pass updating direction, A-direction, x and r), the latter for the
+ *     device-driven solve only.
+ * Candidate lists and the solve's stop rule are the same whatever the choice; the fused CG
+ * rounds differently, so a solve's result changes within its tolerance.  Afterwards the
+ * state is reordered as by a step's bucket build and p, n* and flags are those of a solve at
+ * the current state (positions and velocities are not advanced).  *out (nullable) receives
+ * the choice and its times.  Errors: MPS_EINVAL (repeats < 1), MPS_EDEVICE, and the errors
+ * of the solve. */
+typedef struct {
+    int32_t gather_block;   /* threads per cell block of the candidate gather                */
+    int32_t spmv_block;     /* threads per block of the FP32 SpMV of the mixed inner CG      */
+    int32_t cg_fused;       /* 1: the inner CG in two kernels per iteration, 0: three        */
+    int32_t pad;
+    double gather_ms;       /* the chosen gather's time [ms]                                 */
+    double spmv_ms;         /* the chosen SpMV's time [ms] (0 without a mixed PPE)            */
+    double solve_ms;        /* a mixed solve's time with the chosen form [ms] (0 without)     */
+} mps_tuning;
+int mps_autotune(mps_ctx* ctx, int32_t repeats, mps_tuning* out);
 
 /* Relative PPE residual ||b_s - A_s p_s|| / ||b_s|| of every scene after the last step
  * (n_scenes doubles; 0 for a scene with b_s = 0); a single-scene context writes one. */

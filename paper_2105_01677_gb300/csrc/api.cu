@@ -149,6 +149,8 @@ int check_params(const mps_params* P) {
     if (P->list_every < 0) return MPS_EINVAL;
     if (P->ppe_host_loop != 0 && P->ppe_host_loop != 1) return MPS_EINVAL;
     if (P->cg_x0 < 0 || P->cg_x0 > 3) return MPS_EINVAL;
+    if (P->inner_cg < 0 || P->inner_cg > 1) return MPS_EINVAL;
+    if (P->spmv_block != 0 && P->spmv_block != 256 && P->spmv_block != 512) return MPS_EINVAL;
     if (P->kernel < 0 || P->kernel > 1 || P->gradient_form < 0 || P->gradient_form > 1 ||
         P->source_term < 0 || P->source_term > 2 || (P->source_term >= 1 && P->kernel != 0))
         return MPS_EINVAL;
@@ -337,7 +339,7 @@ int allocate(Ctx* c) {
     if (c->prm.pressure_mode == 0) {
         if (c->prm.precision == 1) {
             A(nb_lap_v32, sl) A(nb_lap_vlo, sl)
-            A(cg_r32, n) A(cg_d32, n) A(cg_q32, n) A(cg_x32, n) A(cg_xhl, n)
+            A(cg_r32, n) A(cg_d32, n) A(cg_q32, n) A(cg_x32, n) A(cg_xhl, n) A(cg_s32, n)
         } else {
             A(nb_lap_v64, sl)
         }
@@ -686,6 +688,8 @@ int mps_create(const double* pos, const double* vel, const int8_t* types, int64_
     c->prm = *params;
     c->n = n;
     c->steps_done = 0;
+    c->cg_fused = params->inner_cg == 1;
+    c->spmv_block = params->spmv_block ? params->spmv_block : 512;
     c->last_cg_iters = 8;
     if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, params->device) != cudaSuccess) {
         delete c;
@@ -737,6 +741,8 @@ int mps_create_ensemble(const double* pos, const double* vel, const int8_t* type
     mps_ctx* c = new (std::nothrow) mps_ctx();
     if (!c) return MPS_ENOMEM;
     c->prm = P;
+    c->cg_fused = P.inner_cg == 1;
+    c->spmv_block = P.spmv_block ? P.spmv_block : 512;
     c->n = n;
     c->steps_done = 0;
     c->last_cg_iters = 8;
@@ -773,48 +779,121 @@ int mps_create_ensemble(const double* pos, const double* vel, const int8_t* type
     return MPS_OK;
 }
 
-int mps_autotune(mps_ctx* c, int32_t repeats, int32_t* gather_block) {
+int mps_autotune(mps_ctx* c, int32_t repeats, mps_tuning* out) {
     if (!c || repeats < 1) return MPS_EINVAL;
     DeviceGuard dg(c->prm.device);
     if (!dg.ok) return MPS_EDEVICE;
     int rc;
-    MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
-    if ((rc = bucket_build(c, true))) return rc;
-    c->need_list = true;
+    mps_tuning t;
+    std::memset(&t, 0, sizeof t);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return MPS_EDEVICE;
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
         return MPS_EDEVICE;
     }
-    const int shapes[4] = {32, 64, 96, 128};
-    int best = c->prm.gather_block;
-    float best_ms = 1e30f;
-    const size_t n = (size_t)c->n;
-    for (int b : shapes) {
-        c->prm.gather_block = b;
-        float ms = 0.f;
-        for (int r = 0; r <= repeats; r++) {   // the first launch warms up
-            cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), c->stream);
+    // mean time of `repeats` runs of f after one untimed run
+    auto time_of = [&](auto&& f, float* ms) -> int {
+        float total = 0.f;
+        for (int r = 0; r <= repeats; r++) {
             cudaEventRecord(e0, c->stream);
-            launch_verlet(c);
+            int frc = f();
             cudaEventRecord(e1, c->stream);
-            cudaEventSynchronize(e1);
-            float t = 0.f;
-            cudaEventElapsedTime(&t, e0, e1);
-            if (r > 0) ms += t;
+            if (frc) return frc;
+            if (cudaEventSynchronize(e1) != cudaSuccess) return MPS_EDEVICE;
+            float m = 0.f;
+            cudaEventElapsedTime(&m, e0, e1);
+            if (r > 0) total += m;
         }
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = b;
+        *ms = total / repeats;
+        return MPS_OK;
+    };
+    const size_t n = (size_t)c->n;
+    // ---- the candidate gather's block shape, on the current state
+    rc = [&]() -> int {
+        MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
+        int r2 = bucket_build(c, true);
+        if (r2) return r2;
+        c->need_list = true;
+        const int shapes[4] = {32, 64, 96, 128};
+        int best = c->prm.gather_block;
+        float best_ms = 1e30f;
+        for (int b : shapes) {
+            c->prm.gather_block = b;
+            float ms = 0.f;
+            r2 = time_of([&]() -> int {
+                MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), c->stream));
+                launch_verlet(c);
+                return MPS_OK;
+            }, &ms);
+            if (r2) return r2;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = b;
+            }
         }
+        c->prm.gather_block = best;
+        t.gather_block = best;
+        t.gather_ms = best_ms;
+        return MPS_OK;
+    }();
+    // ---- the mixed PPE: the FP32 SpMV's block size and the inner CG's form, on the system
+    // of a solve at the current state (the state is not advanced)
+    if (!rc && c->prm.pressure_mode == 0 && c->prm.precision == 1) {
+        rc = [&]() -> int {
+            mps_report rep;
+            std::memset(&rep, 0, sizeof rep);
+            int r2 = do_step(c, false, &rep);
+            if (r2 && r2 != MPS_ECG_NOCONV) return r2;
+            float best_ms = 1e30f;
+            int best = c->spmv_block;
+            for (int b : {256, 512}) {
+                c->spmv_block = b;
+                double ms = 0.0, bytes = 0.0;
+                if ((r2 = ppe_time_kernel(c, 0, repeats, &ms, &bytes))) return r2;
+                if (ms < best_ms) {
+                    best_ms = (float)ms;
+                    best = b;
+                }
+            }
+            c->spmv_block = best;
+            t.spmv_block = best;
+            t.spmv_ms = best_ms;
+            if (c->prm.ppe_host_loop != 0) return MPS_OK;   // the fused form is device-driven only
+            best_ms = 1e30f;
+            bool best_f = c->cg_fused;
+            for (bool f : {false, true}) {
+                c->cg_fused = f;
+                ppe_graphs_destroy(c);
+                float ms = 0.f;
+                r2 = time_of([&]() -> int {
+                    mps_report pr;
+                    std::memset(&pr, 0, sizeof pr);
+                    int r3 = ppe_solve(c, &pr);
+                    return (r3 == MPS_ECG_NOCONV) ? MPS_OK : r3;
+                }, &ms);
+                if (r2) return r2;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_f = f;
+                }
+            }
+            c->cg_fused = best_f;
+            ppe_graphs_destroy(c);
+            t.cg_fused = best_f ? 1 : 0;
+            t.solve_ms = best_ms;
+            return MPS_OK;
+        }();
+    } else {
+        t.spmv_block = c->spmv_block;
+        t.cg_fused = c->cg_fused ? 1 : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->prm.gather_block = best;
-    if (gather_block) *gather_block = best;
-    step_graphs_destroy(c);   // they captured the gather with its block shape
+    step_graphs_destroy(c);   // they captured the tuned kernels' launch shapes
+    if (rc) return rc;
     MPS_CUDA(c, cudaGetLastError());
+    if (out) *out = t;
     return MPS_OK;
 }
 

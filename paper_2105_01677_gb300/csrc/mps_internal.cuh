@@ -391,6 +391,10 @@ Radius make_radius(double re, double X);
     // CG (FP64): x = p, r, d, q ; FP32: r32, d32, q32, x32
     double *cg_r, *cg_d, *cg_q;
     float *cg_r32, *cg_d32, *cg_q32, *cg_x32;
+    float* cg_s32 = nullptr;   // the fused inner CG's A p (its A r is kept in cg_q32)
+    // tuned by mps_autotune: the FP32 SpMV's block size and the inner CG's form
+    int spmv_block = 512;
+    bool cg_fused = false;
     float2* cg_xhl;         // mixed: the FP64 iterate as float-float (hi, lo) for the outer residual
     double* partials;       // per-block partial sums
     CgScalars* cg;          // device

@@ -524,6 +524,96 @@ __global__ void __launch_bounds__(BT) k_spmv32_t(SellView c, const float* d, flo
     }
 }
 
+// ------------------------------------------------------------------ fused inner CG
+// The inner CG in two kernels per iteration instead of three, by the recurrences of
+// Chronopoulos and Gear (s-step CG, 1989): with w = A r computed from the residual itself,
+//   delta_k = (A r_k) . r_k,  beta_k = gamma_k / gamma_{k-1},
+//   alpha_k = gamma_k / (delta_k - beta_k gamma_k / alpha_{k-1})   (alpha_0 = gamma_0/delta_0),
+//   p_k = r_k + beta_k p_{k-1},  s_k = w_k + beta_k s_{k-1}  (= A p_k),
+//   x += alpha_k p_k,  r_{k+1} = r_k - alpha_k s_k,  gamma_{k+1} = r_{k+1} . r_{k+1}.
+// The iterates are those of the textbook CG in exact arithmetic; the vector bytes per
+// iteration are the same, one launch and one pass fewer.  p lives in d32, w in q32.
+// K1: w = A r and delta; its last block forms alpha (and ends a solve that broke down).
+template <bool MATRIX_FREE, int BT = kBT>
+__global__ void __launch_bounds__(BT) k_spmv32_cg(SellView c, const float* r, float* w,
+                                                  CgScalars* cg, float coef, float re_f) {
+    if (*(volatile int*)&cg->done) return;
+    __shared__ double sm[BT / 32];
+    double part = 0.0;
+    for (int i = blockIdx.x * BT + threadIdx.x; i < c.n; i += gridDim.x * BT) {
+        const float dg = c.diag32[i];
+        float wi = 0.f;
+        if (dg != 0.f) {
+            const int cnt = c.cnt[i];
+            float acc = 0.f;
+            if (MATRIX_FREE) {
+                const float4 pi = c.pos32s[i];
+                for (int k = 0; k < cnt; k++) {
+                    const int j = c.col[sell(i, k, c.cap)];
+                    const float4 pj = c.pos32s[j];
+                    const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
+                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+                    acc = fmaf(coef * fmaf(re_f, rsqrtf(r2), -1.f), r[j], acc);
+                }
+            } else {
+                acc = sell_dot32(c.col + sell(i, 0, c.cap), c.v32 + sell(i, 0, c.cap), cnt, r);
+            }
+            wi = dg * r[i] - acc;
+        }
+        w[i] = wi;
+        part = fma((double)r[i], (double)wi, part);
+    }
+    double tot;
+    part = block_sum<BT>(part, sm);
+    if (grid_sum<BT>(part, c.partials, &c.counter[1], &tot, sm) && threadIdx.x == 0) {
+        const bool first = cg->iters == 0;
+        const double den = first ? tot : tot - cg->beta * cg->rho / cg->alpha;
+        cg->dq = den;
+        cg->alpha = (den > 0.0) ? cg->rho / den : 0.0;
+        if (!(den > 0.0)) cg->done = 1;
+    }
+}
+
+// K2: p, s, x and r updated in one pass, gamma of the new residual; its last block forms
+// beta and the stop decision.  h_in (nonzero): the inner loop's conditional, set by the last
+// block (run again unless done; never more than max_total + 2 times in one inner solve).
+__global__ void __launch_bounds__(kBT) k_vec32_cg(int n, float* x, float* r, float* p, float* s,
+                                                  const float* w, CgScalars* cg, double* partials,
+                                                  unsigned int* counter,
+                                                  cudaGraphConditionalHandle h_in) {
+    if (*(volatile int*)&cg->done) {
+        if (h_in && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_in, 0u);
+        return;
+    }
+    __shared__ double sm[kWarps];
+    const bool first = cg->iters == 0;
+    const float alpha = (float)cg->alpha, beta = first ? 0.f : (float)cg->beta;
+    double part = 0.0;
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) {
+        const float ri = r[i], wi = w[i];
+        const float pi = first ? ri : fmaf(beta, p[i], ri);
+        const float si = first ? wi : fmaf(beta, s[i], wi);
+        p[i] = pi;
+        s[i] = si;
+        x[i] = fmaf(alpha, pi, x[i]);
+        const float rn = fmaf(-alpha, si, ri);
+        r[i] = rn;
+        part += (double)rn * (double)rn;
+    }
+    double tot;
+    part = block_sum<kBT>(part, sm);
+    if (grid_sum<kBT>(part, partials, counter, &tot, sm) && threadIdx.x == 0) {
+        cg->beta = (cg->rho > 0.0) ? tot / cg->rho : 0.0;
+        cg->rho = tot;
+        cg->iters += 1;
+        if (tot <= cg->stop2 || cg->iters >= cg->max_iters) cg->done = 1;
+        if (h_in) {
+            const int g = ++cg->guard_in;
+            cudaGraphSetConditional(h_in, (!cg->done && g < cg->max_total + 2) ? 1u : 0u);
+        }
+    }
+}
+
 // x64 += |r64| x32   (|r64| = sqrt(rr) of the residual that started the inner solve); the
 // float-float copy of x for the next outer residual is refreshed at the same time
 // scale_rr < 0 (the device-driven solve): |r64|^2 is read from the scalars (cg->rr still
@@ -665,17 +755,27 @@ static int set_cg_limits(Ctx* c, int max_iters) {
 // find them in the SM's L1 (256-thread blocks: 5% slower, 128: 25%, 1024: 40%, measured
 // on the 3D dam break).  The float-float residual and the FP64 SpMV, with more registers
 // and bytes per entry, are faster at 256 (512: 18% and 9% slower).
-constexpr int kSpmvBT = 512;
-static int spmv_grid(const Ctx* c) {
-    return (int)std::min<int64_t>((c->n + kSpmvBT - 1) / kSpmvBT, 4096);
+static int spmv_grid(const Ctx* c, int bt) {
+    return (int)std::min<int64_t>((c->n + bt - 1) / bt, 4096);
 }
 
-static void launch_spmv32(Ctx* c, cudaStream_t s, const SellView& sv) {
+// FP32 SpMV of the inner CG, in the block size the autotuner chose (512: the rows of a block
+// are neighbouring particles whose neighbours overlap in L1; 256 on smaller systems)
+template <bool MF, int BT>
+static void spmv32_bt(Ctx* c, cudaStream_t s, const SellView& sv, bool fused) {
     const float coef = (float)c->coef_ppe, re_f = (float)c->r_lap.re;
-    if (c->prm.ppe_operator == 1)
-        k_spmv32_t<true, kSpmvBT><<<spmv_grid(c), kSpmvBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+    if (fused)
+        k_spmv32_cg<MF, BT><<<spmv_grid(c, BT), BT, 0, s>>>(sv, c->cg_r32, c->cg_q32, c->cg, coef, re_f);
     else
-        k_spmv32_t<false, kSpmvBT><<<spmv_grid(c), kSpmvBT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+        k_spmv32_t<MF, BT><<<spmv_grid(c, BT), BT, 0, s>>>(sv, c->cg_d32, c->cg_q32, c->cg, coef, re_f);
+}
+
+static void launch_spmv32(Ctx* c, cudaStream_t s, const SellView& sv, bool fused = false) {
+    const bool mf = c->prm.ppe_operator == 1;
+    if (c->spmv_block == 256)
+        mf ? spmv32_bt<true, 256>(c, s, sv, fused) : spmv32_bt<false, 256>(c, s, sv, fused);
+    else
+        mf ? spmv32_bt<true, 512>(c, s, sv, fused) : spmv32_bt<false, 512>(c, s, sv, fused);
 }
 
 // Launch up to `chunk` iterations of FP64 CG (extra launches exit at once once done).
@@ -818,10 +918,16 @@ int add_mixed_solve(Ctx* c, cudaGraph_t G, cudaGraphNode_t dep, double* x, bool 
     if (!(n_init = only_node(B))) return MPS_EDEVICE;
     if ((rc = add_while(c, B, n_init, h_in, &n_inner, &Bi))) return rc;
     MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, Bi, nullptr, nullptr, 0, mode));
-    launch_spmv32(c, s, sv);
-    k_xr32<<<gv, kBT, 0, s>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_q32, c->cg, c->partials,
-                              &c->st->counter[2]);
-    k_d32<<<gv, kBT, 0, s>>>(n, c->cg_r32, c->cg_d32, c->cg, h_in);
+    if (c->cg_fused) {
+        launch_spmv32(c, s, sv, true);
+        k_vec32_cg<<<gv, kBT, 0, s>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_s32, c->cg_q32,
+                                      c->cg, c->partials, &c->st->counter[2], h_in);
+    } else {
+        launch_spmv32(c, s, sv);
+        k_xr32<<<gv, kBT, 0, s>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_q32, c->cg,
+                                  c->partials, &c->st->counter[2]);
+        k_d32<<<gv, kBT, 0, s>>>(n, c->cg_r32, c->cg_d32, c->cg, h_in);
+    }
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
     MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, B, &n_inner, nullptr, 1, mode));
     k_outer_update<<<gv, kBT, 0, s>>>(n, x, c->cg_x32, -1.0, c->cg_xhl, c->cg);
@@ -852,7 +958,8 @@ void mixed_init_scalars(Ctx* c, CgScalars* init) {
 // Kernels one mixed solve ran (counted like the host loop's launches)
 int64_t mixed_solve_launches(Ctx* c, bool guess, const CgScalars& h) {
     const bool multi = c->n_scenes > 1;
-    return (guess ? (multi ? 5 : 3) : 1) + (multi ? 5 : 3) * (int64_t)h.outer + 3 * (int64_t)h.total;
+    return (guess ? (multi ? 5 : 3) : 1) + (multi ? 5 : 3) * (int64_t)h.outer +
+           (c->cg_fused ? 2 : 3) * (int64_t)h.total;
 }
 
 namespace {

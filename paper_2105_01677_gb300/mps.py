@@ -38,7 +38,8 @@ class mps_params(C.Structure):
                 ("ppe_operator", C.c_int32), ("device", C.c_int32), ("gather_block", C.c_int32),
                 ("list_every", C.c_int32), ("kernel", C.c_int32), ("gradient_form", C.c_int32),
                 ("source_term", C.c_int32), ("ppe_host_loop", C.c_int32),
-                ("cg_x0", C.c_int32), ("step_graph", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
+                ("cg_x0", C.c_int32), ("step_graph", C.c_int32), ("inner_cg", C.c_int32),
+                ("spmv_block", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
                 ("alloc_user", C.c_void_p)]
 
 
@@ -58,6 +59,17 @@ class mps_report(C.Structure):
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["lambda"] = d.pop("lambda_")
+        d.pop("pad")
+        return d
+
+
+class mps_tuning(C.Structure):
+    _fields_ = [("gather_block", C.c_int32), ("spmv_block", C.c_int32), ("cg_fused", C.c_int32),
+                ("pad", C.c_int32), ("gather_ms", C.c_double), ("spmv_ms", C.c_double),
+                ("solve_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
         d.pop("pad")
         return d
 
@@ -120,7 +132,7 @@ def lib(build_if_missing: bool = False):
                                       C.POINTER(mps_params), C.POINTER(mps_scene), C.c_int32,
                                       C.POINTER(C.c_void_p)]
     L.mps_scene_residuals.argtypes = [C.c_void_p, d]
-    L.mps_autotune.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]
+    L.mps_autotune.argtypes = [C.c_void_p, C.c_int32, C.POINTER(mps_tuning)]
     L.mps_debug_cells.argtypes = [C.c_void_p, C.POINTER(C.c_uint32)]
     L.mps_debug_neighbors.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int32), C.c_int64]
@@ -279,11 +291,12 @@ def mps_create_ensemble(pos, vel, types, scene, params: mps_params, scenes,
     return h
 
 
-def mps_autotune(h, repeats: int = 3) -> int:
-    """Pick the fastest gather block shape for the current state; returns it."""
-    b = C.c_int32()
-    _check(lib().mps_autotune(h, int(repeats), C.byref(b)), "mps_autotune")
-    return int(b.value)
+def mps_autotune(h, repeats: int = 3) -> dict:
+    """Pick the fastest gather block shape, FP32 SpMV block and inner-CG form for the current
+    state; returns the choice and its times (mps_tuning as a dict)."""
+    t = mps_tuning()
+    _check(lib().mps_autotune(h, int(repeats), C.byref(t)), "mps_autotune")
+    return t.as_dict()
 
 
 def mps_scene_residuals(h, n_scenes: int):
@@ -542,7 +555,7 @@ class Ensemble:
     def residuals(self):
         return mps_scene_residuals(self.h, len(self.scenes))
 
-    def autotune(self, repeats: int = 3) -> int:
+    def autotune(self, repeats: int = 3) -> dict:
         return mps_autotune(self.h, repeats)
 
     def close(self):
@@ -614,7 +627,7 @@ class Simulation:
     def constants(self):
         return mps_get_constants(self.h)
 
-    def autotune(self, repeats: int = 3) -> int:
+    def autotune(self, repeats: int = 3) -> dict:
         return mps_autotune(self.h, repeats)
 
     def close(self):

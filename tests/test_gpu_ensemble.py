@@ -118,7 +118,7 @@ def test_autotune_keeps_results_bitwise():
         ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, cg_tol=1e-10)
         try:
             if tune:
-                assert ens.autotune(2) in (32, 64, 96, 128)
+                assert ens.autotune(2)["gather_block"] in (32, 64, 96, 128)
             ens.step(2)
             outs.append(ens.read())
         finally:

@@ -1,0 +1,109 @@
+"""The tunable forms of the mixed PPE solve and the autotuner that picks them.
+
+- The fused inner CG (inner_cg = 1: two kernels per iteration by the recurrences of
+  Chronopoulos and Gear) and the 256-thread FP32 SpMV round differently from the defaults,
+  so they are held to the mixed-precision bound against the FP64 oracle (p: relative L2 over
+  fluid <= 1e-5, positions <= 1e-6 l0), on the regularised and on the stiff PPE, one scene
+  and an ensemble, and must reach the same FP64 residual.
+- mps_autotune returns a valid choice with its times, and an ensemble stepped after tuning
+  keeps every scene within its tolerance and within the mixed bound of the oracle."""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+import scenes
+from _parity import PARITY_CG_TOL, gpu_params, oracle_params, run_gpu, run_oracle, small_3d
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available()
+    __graft_entry__.build()
+    oracle.set_threads(0)
+
+
+def _mixed_bound(sc, got, ref):
+    f = sc.types == scenes.FLUID
+    ep = np.linalg.norm(got["p"][f] - ref.p[f]) / np.linalg.norm(ref.p[f])
+    ex = np.abs(got["pos"] - ref.pos).max() / sc.l0
+    assert ep <= 1e-5, ep
+    assert ex <= 1e-6, ex
+
+
+@pytest.mark.parametrize("form", [dict(inner_cg=1), dict(spmv_block=256),
+                                  dict(inner_cg=1, spmv_block=256)])
+@pytest.mark.parametrize("case", ["2d", "3d", "2d-stiff"])
+def test_tunable_forms_within_the_mixed_bound(case, form):
+    if case == "2d":
+        sc, kw = scenes.dam_break_2d(seed=1), {}
+    elif case == "3d":
+        sc, kw = small_3d(seed=2), dict(dt=5e-5)
+    else:
+        sc, kw = scenes.dam_break_2d(seed=3), dict(alpha_c=0.0, clamp_negative_p=0)
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc, precision=1, cg_tol=1e-8, cg_x0=0, **kw,
+                                               **form))
+    orep, ost, prm = run_oracle(sc, cg_tol=PARITY_CG_TOL, **kw)
+    assert rc == 0 and rep["cg_resid"] <= 1e-8
+    _mixed_bound(sc, got, ost)
+    assert np.array_equal(got["flags"], ost.flags)
+
+
+def test_fused_cg_along_a_trajectory_with_the_guess():
+    """Five steps of the 3D small dam break with the quadratic guess: the fused inner CG
+    and the default reach the same residual and stay within the mixed bound of each other."""
+    sc = small_3d(seed=4)
+    outs = []
+    for form in (0, 1):
+        from paper_2105_01677_gb300 import mps
+        sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
+                             **gpu_params(sc, precision=1, dt=5e-5, cg_x0=3, inner_cg=form))
+        try:
+            reps = [sim.step(1)[1] for _ in range(5)]
+            outs.append((reps, sim.read()))
+        finally:
+            sim.close()
+    (r0, s0), (r1, s1) = outs
+    assert all(r["cg_resid"] <= 1e-8 for r in r0 + r1)
+    f = sc.types == scenes.FLUID
+    assert np.linalg.norm(s1["p"][f] - s0["p"][f]) / np.linalg.norm(s0["p"][f]) <= 1e-5
+    assert np.abs(s1["pos"] - s0["pos"]).max() / sc.l0 <= 1e-6
+
+
+def test_autotune_mixed_ensemble():
+    from paper_2105_01677_gb300 import mps
+    E = scenes.ensemble_2d(count=8, seed=9, fluid=(500, 3000))
+    ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
+                       cg_tol=1e-8, cg_x0=3)
+    try:
+        ens.step(2)
+        t = ens.autotune(2)
+        assert t["gather_block"] in (32, 64, 96, 128)
+        assert t["spmv_block"] in (256, 512)
+        assert t["cg_fused"] in (0, 1)
+        assert t["gather_ms"] > 0 and t["spmv_ms"] > 0 and t["solve_ms"] > 0
+        for _ in range(3):
+            rc, rep = ens.step(1)
+            assert rc == 0 and rep["step_graph"] == 1
+            assert np.all(ens.residuals() <= 1e-8)
+        got = ens.read()
+        before = [sc.copy() for sc in E]
+    finally:
+        ens.close()
+    # every scene's state after tuning within the mixed bound of the oracle run on that scene
+    # alone for the same five steps (two before tuning, three after)
+    for k in (0, len(E) - 1):
+        sc = E[k]
+        prm = oracle_params(sc, dt=1e-4, cg_tol=PARITY_CG_TOL)
+        st = oracle.State.from_scene(sc)
+        for _ in range(5):
+            oracle.step(prm, st)
+        f = sc.types == scenes.FLUID
+        ep = np.linalg.norm(got[k]["p"][f] - st.p[f]) / np.linalg.norm(st.p[f])
+        ex = np.abs(got[k]["pos"] - st.pos).max() / sc.l0
+        assert ep <= 1e-4, (k, ep)     # five steps of drift at the mixed bound
+        assert ex <= 1e-6, (k, ex)
+    del before
