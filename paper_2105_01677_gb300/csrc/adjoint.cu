@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kBT) k_adj_grad(AdjArgs a) {
         double4 S = make_double4(0.0, 0.0, 0.0, 0.0);
         const int cnt = a.ncnt[i];
         for (int t = 0; t < cnt; t++) {
-            const int j = a.ncol[sell(i, t, a.cap_n)];
+            const int j = a.ncol[sell8(i, t, a.cap_n)];
             const double4 x = sub4(a.ps[j], pi);
             const double rs = rsqrt(dot3(x, x));
             const double q = fma(a.rn.re, rs, -1.0) * (rs * rs);   // w / s^2
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kBT) k_adj_pbar(AdjArgs a) {
         const double4 pj = a.ps[j];
         const int cnt = a.ncnt[j];
         for (int t = 0; t < cnt; t++) {
-            const int i = a.ncol[sell(j, t, a.cap_n)];
+            const int i = a.ncol[sell8(j, t, a.cap_n)];
             if (a.type[i] != kFluid) continue;
             const double4 x = sub4(pj, a.ps[i]);   // r_j - r_i for the pair (i, j) of row i
             const double rs = rsqrt(dot3(x, x));
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kBT) k_adj_star_fw(AdjArgs a, const int32_t* r
     // non-dummy pairs within re_n: number density and the gradient's pair terms
     const int cn = a.ncnt[k];
     for (int t = 0; t < cn; t++) {
-        const int j = a.ncol[sell(k, t, a.cap_n)];
+        const int j = a.ncol[sell8(k, t, a.cap_n)];
         const double4 x = sub4(a.ps[j], xk);
         // every power of 1/s from one reciprocal square root
         const double rs = rsqrt(dot3(x, x));
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kBT) k_adj_star_fw(AdjArgs a, const int32_t* r
         const double rhok = a.rho_s ? a.rho_s[k] : 0.0;
         const int m = a.lcnt[k];
         for (int t = 0; t < m; t++) {
-            const size_t q = sell(k, t, a.cap);
+            const size_t q = sell8(k, t, a.cap);
             const int j = a.lcol[q];
             const double c = a.lv64 ? a.lv64[q] : (double)a.lv32[q] + (double)a.lvlo[q];
             const bool rj = a.diag[j] != 0.0;

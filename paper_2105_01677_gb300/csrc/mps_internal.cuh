@@ -134,6 +134,17 @@ __device__ __forceinline__ double cubic_w_d(double r2, double rs, double inv_re)
 __host__ __device__ __forceinline__ size_t sell(int i, int k, int cap) {
     return ((size_t)(i >> 5) * (size_t)cap + (size_t)k) * 32 + (size_t)(i & 31);
 }
+// The PPE and gradient rows (the build's outputs) in slices of 32 rows whose entries come in
+// groups of 8 per row: entry k of row i at slice (i / 32), group (k / 8), row (i % 32),
+// position (k % 8).  A row's group is one 32-byte sector, written whole by its thread and
+// read with two 16-byte loads; the 32 rows' group g is 1 KB contiguous.  cap is a multiple
+// of 8.
+__host__ __device__ __forceinline__ size_t sell8(int i, int k, int cap) {
+    return ((size_t)(i >> 5) * (size_t)cap + (size_t)(k & ~7)) * 32 + (size_t)(i & 31) * 8 +
+           (size_t)(k & 7);
+}
+// the first entry of row i (group g of the row sits 256 entries after group g - 1)
+__host__ __device__ __forceinline__ size_t sell8_row(int i, int cap) { return sell8(i, 0, cap); }
 __host__ __device__ __forceinline__ size_t sell_size(int64_t n, int cap) {
     return (size_t)((n + 31) / 32) * 32 * (size_t)cap;
 }

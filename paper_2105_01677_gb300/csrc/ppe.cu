@@ -247,37 +247,36 @@ __device__ __forceinline__ double sell_dot64(const SellView& c, int i, const dou
     const int cnt = c.cnt[i];
     double acc = 0.0;
     for (int k = 0; k < cnt; k++) {
-        const size_t q = sell(i, k, c.cap);
+        const size_t q = sell8(i, k, c.cap);
         acc = fma(c.v64[q], x[c.col[q]], acc);
     }
     return acc;
 }
 
-// sum_k v_k x_{col_k} over one SELL-32 row (entry k at offset 32 k), in entry order; the
-// loads of eight entries are issued before their products so that each thread keeps
-// several independent gathers in flight
+// sum_k v_k x_{col_k} over one row of the grouped layout (sell8), in entry order: a group's
+// 8 columns and 8 coefficients come in as two 16-byte loads each, and the 8 gathers of x
+// are issued before their products.  The mixed build pads a row's last group with zero
+// coefficients on the row's own column, which add exact zeros.
 __device__ __forceinline__ float sell_dot32(const int32_t* __restrict__ cp, const float* __restrict__ vp,
                                             int cnt, const float* __restrict__ x) {
     float acc = 0.f;
-    int k = 0;
-    for (; k + 8 <= cnt; k += 8) {
-        int j[8];
-        float v[8], y[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) j[u] = cp[32 * u];
-#pragma unroll
-        for (int u = 0; u < 8; u++) v[u] = vp[32 * u];
-#pragma unroll
-        for (int u = 0; u < 8; u++) y[u] = x[j[u]];
-#pragma unroll
-        for (int u = 0; u < 8; u++) acc = fmaf(v[u], y[u], acc);
+    const int ng = (cnt + 7) >> 3;
+#pragma unroll 2
+    for (int g = 0; g < ng; g++) {
+        const int4 c0 = *(const int4*)cp, c1 = *(const int4*)(cp + 4);
+        const float4 v0 = *(const float4*)vp, v1 = *(const float4*)(vp + 4);
+        const float y0 = x[c0.x], y1 = x[c0.y], y2 = x[c0.z], y3 = x[c0.w];
+        const float y4 = x[c1.x], y5 = x[c1.y], y6 = x[c1.z], y7 = x[c1.w];
+        acc = fmaf(v0.x, y0, acc);
+        acc = fmaf(v0.y, y1, acc);
+        acc = fmaf(v0.z, y2, acc);
+        acc = fmaf(v0.w, y3, acc);
+        acc = fmaf(v1.x, y4, acc);
+        acc = fmaf(v1.y, y5, acc);
+        acc = fmaf(v1.z, y6, acc);
+        acc = fmaf(v1.w, y7, acc);
         cp += 256;
         vp += 256;
-    }
-    for (; k < cnt; k++) {
-        acc = fmaf(*vp, x[*cp], acc);
-        cp += 32;
-        vp += 32;
     }
     return acc;
 }
@@ -328,7 +327,7 @@ __global__ void __launch_bounds__(BT) k_resid_ff_t(SellView c, const double* x, 
         if (dg != 0.0) {
             const int cnt = c.cnt[i];
             ff acc = {0.f, 0.f};
-            const size_t q0 = sell(i, 0, c.cap);
+            const size_t q0 = sell8(i, 0, c.cap);
             const int32_t* cp = c.col + q0;
             const float* hp = c.v32 + q0;
             const float* lp = c.vlo + q0;
@@ -337,30 +336,26 @@ __global__ void __launch_bounds__(BT) k_resid_ff_t(SellView c, const double* x, 
                 p.l = fmaf(ch, y.y, fmaf(cl, y.x, p.l));
                 acc = ff_add(acc, p);
             };
-            int k = 0;
-            for (; k + 4 <= cnt; k += 4) {   // loads of four entries ahead of their products
-                int j[4];
-                float ch[4], cl[4];
-                float2 y[4];
-#pragma unroll
-                for (int u = 0; u < 4; u++) j[u] = cp[32 * u];
-#pragma unroll
-                for (int u = 0; u < 4; u++) ch[u] = hp[32 * u];
-#pragma unroll
-                for (int u = 0; u < 4; u++) cl[u] = lp[32 * u];
-#pragma unroll
-                for (int u = 0; u < 4; u++) y[u] = xhl[j[u]];
-#pragma unroll
-                for (int u = 0; u < 4; u++) term(ch[u], cl[u], y[u]);
-                cp += 128;
-                hp += 128;
-                lp += 128;
-            }
-            for (; k < cnt; k++) {
-                term(*hp, *lp, xhl[*cp]);
-                cp += 32;
-                hp += 32;
-                lp += 32;
+            // whole groups of 8 (the last one padded with zeros by the build): columns and
+            // both coefficient parts in 16-byte loads, the 8 gathers before their products
+            const int ng = (cnt + 7) >> 3;
+            for (int g = 0; g < ng; g++) {
+                const int4 c0 = *(const int4*)cp, c1 = *(const int4*)(cp + 4);
+                const float4 h0 = *(const float4*)hp, h1 = *(const float4*)(hp + 4);
+                const float4 l0 = *(const float4*)lp, l1 = *(const float4*)(lp + 4);
+                const float2 y0 = xhl[c0.x], y1 = xhl[c0.y], y2 = xhl[c0.z], y3 = xhl[c0.w];
+                const float2 y4 = xhl[c1.x], y5 = xhl[c1.y], y6 = xhl[c1.z], y7 = xhl[c1.w];
+                term(h0.x, l0.x, y0);
+                term(h0.y, l0.y, y1);
+                term(h0.z, l0.z, y2);
+                term(h0.w, l0.w, y3);
+                term(h1.x, l1.x, y4);
+                term(h1.y, l1.y, y5);
+                term(h1.z, l1.z, y6);
+                term(h1.w, l1.w, y7);
+                cp += 256;
+                hp += 256;
+                lp += 256;
             }
             ri = c.bvec[i] - (dg * x[i] - ff_to_double_fast(acc));
         }
@@ -502,14 +497,14 @@ __global__ void __launch_bounds__(BT) k_spmv32_t(SellView c, const float* d, flo
             if (MATRIX_FREE) {
                 const float4 pi = c.pos32s[i];
                 for (int k = 0; k < cnt; k++) {
-                    const int j = c.col[sell(i, k, c.cap)];
+                    const int j = c.col[sell8(i, k, c.cap)];
                     const float4 pj = c.pos32s[j];
                     const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     acc = fmaf(coef * fmaf(re_f, rsqrtf(r2), -1.f), d[j], acc);
                 }
             } else {
-                acc = sell_dot32(c.col + sell(i, 0, c.cap), c.v32 + sell(i, 0, c.cap), cnt, d);
+                acc = sell_dot32(c.col + sell8(i, 0, c.cap), c.v32 + sell8(i, 0, c.cap), cnt, d);
             }
             qi = dg * d[i] - acc;
         }
@@ -549,14 +544,14 @@ __global__ void __launch_bounds__(BT) k_spmv32_cg(SellView c, const float* r, fl
             if (MATRIX_FREE) {
                 const float4 pi = c.pos32s[i];
                 for (int k = 0; k < cnt; k++) {
-                    const int j = c.col[sell(i, k, c.cap)];
+                    const int j = c.col[sell8(i, k, c.cap)];
                     const float4 pj = c.pos32s[j];
                     const float dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                     acc = fmaf(coef * fmaf(re_f, rsqrtf(r2), -1.f), r[j], acc);
                 }
             } else {
-                acc = sell_dot32(c.col + sell(i, 0, c.cap), c.v32 + sell(i, 0, c.cap), cnt, r);
+                acc = sell_dot32(c.col + sell8(i, 0, c.cap), c.v32 + sell8(i, 0, c.cap), cnt, r);
             }
             wi = dg * r[i] - acc;
         }

@@ -274,6 +274,21 @@ __device__ __forceinline__ double hs_term(ff dx, ff dy, ff dz, ff y, const doubl
     return re * (ry * ry * ry) * dot;
 }
 
+// Staging of the mixed build's row outputs: each thread collects the next 8 entries of its
+// PPE row (column, FP32 coefficient, low part) and of its gradient row in shared memory and
+// writes each group of 8 as whole 32-byte sectors (the grouped row layout, sell8), so that
+// no partially written sector has to be filled from DRAM.  Entry-major: thread t's entry e
+// sits at [e][t], consecutive threads in consecutive banks.
+template <bool ON, int BT>
+struct RowStage {
+    int32_t col[8][BT];
+    float hi[8][BT];
+    float lo[8][BT];
+    int32_t ncol[8][BT];
+};
+template <int BT>
+struct RowStage<false, BT> {};
+
 // Entry flags while a PPE row is being assembled (slots are < 2^30)
 constexpr int kEntryN = 1 << 30;   // within re_n: contributes to n*
 constexpr int kEntryL = 1 << 29;   // non-dummy within re_lap: a PPE coefficient
@@ -302,6 +317,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
     // evaluated (reported as 0)
     const int tid = blockIdx.x * kBuildBT + threadIdx.x;
     const int i = tid < (int)*a.nrows ? a.rows[tid] : -1;
+    __shared__ RowStage<MIXED, kBuildBT> stage;
     bool surf = false, ppe = false;
     unsigned n_lap = 0, n_pnd = 0;   // pairs evaluated by this row
     unsigned n_cand = 0;             // candidate-list entries it classified
@@ -329,7 +345,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
         auto append = [&](int j, bool tl, bool tn, bool nb_ok) {
             if (!tl && !tn) return;
             if (tn && nb_ok) {
-                if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j;
+                if (out_n < a.cap_n) a.n_col[sell8(i, out_n, a.cap_n)] = j;
                 out_n++;
             }
             if (m_f >= a.cap) {
@@ -339,7 +355,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
             // every hit in candidate order: the rows of a slice (neighbouring particles, one
             // candidate sequence) then hold nearby particles at the same entry, which keeps
             // the solver's gathers of x[col] within few cache lines per warp
-            a.lap_col[sell(i, m_f++, a.cap)] = j | (tn ? kEntryN : 0) | (tl ? kEntryL : 0);
+            a.lap_col[sell8(i, m_f++, a.cap)] = j | (tn ? kEntryN : 0) | (tl ? kEntryL : 0);
             m_n += tn ? 1 : 0;
         };
         // FP64 path: classification first (the mixed path decides membership inside its
@@ -393,7 +409,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
         int out_l = 0;
         const int m_all = m_f;
         auto slot_of = [&](int t) { return t; };
-        if (MIXED) {
+        if constexpr (MIXED) {
             // Two entries per iteration, their pair terms in packed FP32x2 float-float.
             // 1/r: one Newton step (~1e-13) serves the PPE coefficient; n* takes a second
             // (~1e-15) so that it stays far inside the flag band.  The terms are summed in
@@ -407,6 +423,50 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
             const ff2 coef = {f2(-ncoef_ff.h), f2(-ncoef_ff.l)};
             const ff2 invn = {f2(rn.inv_f), f2(rn.inv_l)}, invl = {f2(rl.inv_f), f2(rl.inv_l)};
             const double4 ui = SRC >= 1 ? a.vel_star[i] : make_double4(0.0, 0.0, 0.0, 0.0);
+            // the row's outputs, staged 8 entries at a time (RowStage above)
+            const int t_ = threadIdx.x;
+            auto flush_lap = [&](int g) {
+                const size_t q = sell8(i, 8 * g, a.cap);
+                *(int4*)(a.lap_col + q) = make_int4(stage.col[0][t_], stage.col[1][t_],
+                                                    stage.col[2][t_], stage.col[3][t_]);
+                *(int4*)(a.lap_col + q + 4) = make_int4(stage.col[4][t_], stage.col[5][t_],
+                                                        stage.col[6][t_], stage.col[7][t_]);
+                *(float4*)(a.lap_v32 + q) = make_float4(stage.hi[0][t_], stage.hi[1][t_],
+                                                        stage.hi[2][t_], stage.hi[3][t_]);
+                *(float4*)(a.lap_v32 + q + 4) = make_float4(stage.hi[4][t_], stage.hi[5][t_],
+                                                            stage.hi[6][t_], stage.hi[7][t_]);
+                *(float4*)(a.lap_vlo + q) = make_float4(stage.lo[0][t_], stage.lo[1][t_],
+                                                        stage.lo[2][t_], stage.lo[3][t_]);
+                *(float4*)(a.lap_vlo + q + 4) = make_float4(stage.lo[4][t_], stage.lo[5][t_],
+                                                            stage.lo[6][t_], stage.lo[7][t_]);
+            };
+            auto put_lap = [&](int j, float h, float l) {
+                if (out_l < a.cap) {
+                    const int e = out_l & 7;
+                    stage.col[e][t_] = j;
+                    stage.hi[e][t_] = h;
+                    stage.lo[e][t_] = l;
+                    if (e == 7) flush_lap(out_l >> 3);
+                    out_l++;
+                } else {
+                    overflow = true;
+                }
+            };
+            auto flush_n = [&](int g) {
+                const size_t q = sell8(i, 8 * g, a.cap_n);
+                *(int4*)(a.n_col + q) = make_int4(stage.ncol[0][t_], stage.ncol[1][t_],
+                                                  stage.ncol[2][t_], stage.ncol[3][t_]);
+                *(int4*)(a.n_col + q + 4) = make_int4(stage.ncol[4][t_], stage.ncol[5][t_],
+                                                      stage.ncol[6][t_], stage.ncol[7][t_]);
+            };
+            auto put_n = [&](int j) {
+                if (out_n < a.cap_n) {
+                    const int e = out_n & 7;
+                    stage.ncol[e][t_] = j;
+                    if (e == 7) flush_n(out_n >> 3);
+                }
+                out_n++;
+            };
             // the members' terms of a pair of candidates (lane x: j0, lane y: j1), shared by
             // the single walk and the walk over staged entries
             auto terms = [&](int j0, int j1, const ff2& dx, const ff2& dy, const ff2& dz,
@@ -438,34 +498,16 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                                     make_float2(tn0 ? w.l.x : 0.f, tl0 ? c.l.x : 0.f)});
                 acc = ff2_add(acc, {make_float2(tn1 ? w.h.y : 0.f, tl1 ? c.h.y : 0.f),
                                     make_float2(tn1 ? w.l.y : 0.f, tl1 ? c.l.y : 0.f)});
-                if (tl0) {
-                    if (out_l < a.cap) {
-                        const size_t q = sell(i, out_l++, a.cap);
-                        a.lap_col[q] = j0;
-                        a.lap_v32[q] = c.h.x;
-                        a.lap_vlo[q] = c.l.x;
-                    } else {
-                        overflow = true;
-                    }
-                }
-                if (tl1) {
-                    if (out_l < a.cap) {
-                        const size_t q = sell(i, out_l++, a.cap);
-                        a.lap_col[q] = j1;
-                        a.lap_v32[q] = c.h.y;
-                        a.lap_vlo[q] = c.l.y;
-                    } else {
-                        overflow = true;
-                    }
-                }
+                if (tl0) put_lap(j0, c.h.x, c.l.x);
+                if (tl1) put_lap(j1, c.h.y, c.l.y);
             };
             if (!with_ppe) {
                 // equation of state: one in seven candidates is a member (within re_n), so
                 // the classification above staged the members and only they are evaluated
                 for (int t = 0; t < m_all; t += 2) {
                     const bool two = t + 1 < m_all;
-                    const int e0 = a.lap_col[sell(i, t, a.cap)];
-                    const int e1 = two ? a.lap_col[sell(i, t + 1, a.cap)] : e0;
+                    const int e0 = a.lap_col[sell8(i, t, a.cap)];
+                    const int e1 = two ? a.lap_col[sell8(i, t + 1, a.cap)] : e0;
                     const int j0 = e0 & kSlotMask, j1 = e1 & kSlotMask;
                     const float4 h0 = a.pos32[j0], l0 = a.pos32lo[j0];
                     const float4 h1 = a.pos32[j1], l1 = a.pos32lo[j1];
@@ -524,14 +566,8 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                     if ((tn1 || tl1) && !ok1 && !(exact_dist2(pi, a.pos[j1]) > 0.0))
                         atomicOr(&a.st->err, kErrCoincident);
                     // the gradient list: non-dummy members within re_n, in candidate order
-                    if (tn0 && nb0) {
-                        if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j0;
-                        out_n++;
-                    }
-                    if (tn1 && nb1) {
-                        if (out_n < a.cap_n) a.n_col[sell(i, out_n, a.cap_n)] = j1;
-                        out_n++;
-                    }
+                    if (tn0 && nb0) put_n(j0);
+                    if (tn1 && nb1) put_n(j1);
                     m_n += (tn0 ? 1 : 0) + (tn1 ? 1 : 0);
                     tn0 = tn0 && ok0;
                     tn1 = tn1 && ok1;
@@ -539,12 +575,27 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                     tl1 = tl1 && ok1;
                     terms(j0, j1, dx, dy, dz, r2, tn0, tl0, tn1, tl1);
                 }
+                // the last, partial groups: the PPE row padded with zero coefficients on the
+                // row's own column (the solver reads whole groups), the gradient row as is
+                if (out_l & 7) {
+                    for (int e = out_l & 7; e < 8; e++) {
+                        stage.col[e][t_] = i;
+                        stage.hi[e][t_] = 0.f;
+                        stage.lo[e][t_] = 0.f;
+                    }
+                    flush_lap(out_l >> 3);
+                }
+                const int mn = min(out_n, a.cap_n);
+                if (mn & 7) {
+                    for (int e = mn & 7; e < 8; e++) stage.ncol[e][t_] = i;
+                    flush_n(mn >> 3);
+                }
             }
             nd = ff_to_double_fast(ff2_lo(acc));
             dg = ff_to_double_fast(ff2_hi(acc));
         } else {
             for (int t = 0; t < m_all; t++) {
-                const int e = a.lap_col[sell(i, slot_of(t), a.cap)];
+                const int e = a.lap_col[sell8(i, slot_of(t), a.cap)];
                 const int j = e & kSlotMask;
                 const bool tn = (e & kEntryN) != 0, tl = (e & kEntryL) != 0;
                 const double4 pj = a.pos[j];
@@ -568,7 +619,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                     const double cd =
                         a.rho_s ? (coef0 * (2.0 / (a.rho_s[i] + a.rho_s[j]))) * wl : coef_ppe * wl;
                     dg += cd;
-                    const size_t q = sell(i, out_l++, a.cap);
+                    const size_t q = sell8(i, out_l++, a.cap);
                     a.lap_col[q] = j;
                     a.lap_v64[q] = cd;
                 }

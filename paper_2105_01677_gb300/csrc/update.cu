@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kBT)
     if (type[i] == kFluid || (walls && type[i] == kWall)) {   // wall p_hat: CMPS pair terms
         const int cnt = ncnt[i];
         for (int k = 0; k < cnt; k++) {
-            double pj = p[ncol[sell(i, k, cap_n)]];
+            double pj = p[ncol[sell8(i, k, cap_n)]];
             if (clamp) pj = fmax(pj, 0.0);
             m = fmin(m, pj);
         }
@@ -86,7 +86,7 @@ __device__ __forceinline__ double gradient_row(int i, const int8_t* type, const 
         const float4 qi = ps32[i];
         float f0 = 0.f, f1 = 0.f, f2 = 0.f;
         for (int k = 0; k < cnt; k++) {
-            const int j = ncol[sell(i, k, cap_n)];
+            const int j = ncol[sell8(i, k, cap_n)];
             const float4 qj = ps32[j];
             const float dx = qj.x - qi.x, dy = qj.y - qi.y, dz = qj.z - qi.z;
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
@@ -103,7 +103,7 @@ __device__ __forceinline__ double gradient_row(int i, const int8_t* type, const 
         g2 = f2;
     } else {
         for (int k = 0; k < cnt; k++) {
-            const int j = ncol[sell(i, k, cap_n)];
+            const int j = ncol[sell8(i, k, cap_n)];
             const double4 pj = ps[j];
             const double dx = pj.x - pi.x, dy = pj.y - pi.y, dz = pj.z - pi.z;
             const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
