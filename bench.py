@@ -77,14 +77,13 @@ ISSUED_FLOPS_LIST_TEST, ISSUED_FLOPS_PPE_PAIR, ISSUED_FLOPS_PND_PAIR = 8.0, 133.
 # list entry its slot read (4 B); per particle r* (hi and lo float4: 32 B) read and n*,
 # flag, diagonal (FP64 and FP32), right-hand side and the two list counts written (37 B).
 BUILD_BYTES_PER_COEF, BUILD_BYTES_PER_LIST_ENTRY, BUILD_BYTES_PER_PARTICLE = 12.0, 4.0, 69.0
-# DRAM bytes (read + write) of one FP32 SpMV launch (512-thread blocks) per PPE
-# coefficient, from the ncu capture in profiles/kernels_dam_break_3d_227k_mixed.md
-# (259.9 + 3.5 MB for 25.19 M coefficients on the 227,136-particle case); traffic scales
-# with the coefficients
-SPMV_TRAFFIC_PER_COEF = (259.9e6 + 3.5e6) / 25.19e6
-# the same for one launch of the mixed build kernel (one walk per row, 256-thread blocks):
-# 477.7 + 556.8 MB for 25.19 M PPE coefficients (its lists and row outputs scale with them)
-BUILD_TRAFFIC_PER_COEF = (477.7e6 + 556.8e6) / 25.19e6
+# DRAM bytes (read + write) per PPE coefficient of one launch, from the ncu capture in
+# profiles/kernels_dam_break_3d_227k_mixed.md (227,136-particle case, 25.19 M coefficients,
+# rows grouped 8 entries per row): FP32 SpMV 202.1 + 0.5 MB, build 203.0 + 289.2 MB,
+# float-float residual 306.5 + 1.2 MB.  The rows and lists scale with the coefficients.
+SPMV_TRAFFIC_PER_COEF = (202.06e6 + 0.48e6) / 25.19e6
+BUILD_TRAFFIC_PER_COEF = (202.98e6 + 289.20e6) / 25.19e6
+RESID_TRAFFIC_PER_COEF = (306.47e6 + 1.18e6) / 25.19e6
 
 
 def parse():
@@ -112,6 +111,9 @@ def parse():
     ap.add_argument("--ensemble-steps", type=int, default=20,
                     help="timed steps of the batched ensemble (0: skip)")
     ap.add_argument("--ensemble-scenes", type=int, default=256)
+    ap.add_argument("--no-step-graph", action="store_true",
+                    help="launch kernel by kernel instead of one CUDA graph per step "
+                         "(profiling: identical results)")
     ap.add_argument("--ppe-host-loop", action="store_true",
                     help="drive the mixed PPE solve from the host (profiling: identical results)")
     ap.add_argument("--cg-x0", type=int, default=3, choices=[0, 1, 2, 3],
@@ -308,7 +310,7 @@ def run_gb300(args):
     # --ppe-host-loop: the mixed PPE solve driven from the host instead of one CUDA graph
     # (identical results; ncu cannot profile the kernels of a graph with conditional nodes)
     common = dict(dt=5e-5, cg_tol=1e-8, ppe_host_loop=1 if args.ppe_host_loop else 0,
-                  cg_x0=args.cg_x0)
+                  cg_x0=args.cg_x0, step_graph=0 if args.no_step_graph else 1)
 
     def timed_steps(sim, k, profile=False, profile_steps=20):
         """CUDA-event time of k steps with the stage timers off (a step then runs as one CUDA
@@ -752,7 +754,8 @@ def run_gb300(args):
                       bytes_per_launch=spmv_bytes,
                       timing="timed alone after the timed region (CUDA events, 20 launches)")
     roof_resid = bound("k_resid_ff_t (float-float FP64 residual)", resid_ms, resid_launches,
-                       nbytes=resid_bytes, traffic=None, bytes_per_launch=resid_bytes,
+                       nbytes=resid_bytes, traffic=RESID_TRAFFIC_PER_COEF * ppe_pairs,
+                       bytes_per_launch=resid_bytes,
                        timing="timed alone after the timed region (CUDA events, 10 launches)")
     rooflines = sorted([roof_build, roof_spmv, roof_gather, roof_resid],
                        key=lambda r: -r["ms_per_step"])
