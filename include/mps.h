@@ -48,7 +48,8 @@ extern "C" {
 #define MPS_ENOMEM -2       /* device or host allocation failed                              */
 #define MPS_ECG_NOCONV -3   /* CG did not reach cg_tol within cg_max_iter (report filled)    */
 #define MPS_ENONFINITE -4   /* NaN or Inf in a position or velocity                          */
-#define MPS_ESKIN -5        /* a particle moved more than half the cell skin within a step   */
+#define MPS_ESKIN -5        /* more than max(64, n/256) particles moved more than half the   *
+                             * cell skin within a step (fewer: their lists are completed)     */
 #define MPS_ECOINCIDENT -6  /* two neighbouring particles at distance 0 (w infinite, Eq. 4)  */
 #define MPS_ECAP -7         /* a caller buffer or the per-particle neighbour cap is too small */
 #define MPS_EDEVICE -8      /* a CUDA call failed or a device-side wait gave up              */
@@ -159,7 +160,8 @@ typedef struct {
     int64_t list_tests;       /* candidate-list entries classified at r* (distance tests of  *
                                * the number-density / PPE assembly)                           */
     int32_t step_graph;       /* 1 if the step ran as one CUDA graph launch                    */
-    int32_t pad;
+    int32_t n_fast;           /* FLUID particles that moved more than half the cell skin: their *
+                               * candidate lists were completed by a direct search at r*      */
 } mps_report;
 
 /* Opaque context: device buffers, stream and derived constants of one particle system. */

@@ -710,6 +710,13 @@ static int stage_predict(const orc_params* p, int64_t n, const double* pos, cons
                     ps[q] = pos[q];
                 }
             }
+        /* The neighbour sets at r* below are searched afresh at r*, so they are exact     */
+        /* whatever the motion.  The library's candidate lists, gathered at r^k, need a     */
+        /* direct search for every particle that moves more than half the cell skin; it    */
+        /* gives up (MPS_ESKIN) beyond max(64, n/256) such particles, and so does this.     */
+        double re = p->re_n > p->re_lap ? p->re_n : p->re_lap;
+        const double half = 0.5 * p->cell_skin * re;
+        int64_t n_fast = 0;
         R->max_disp = 0.0;
         for (int64_t i = 0; i < n; i++) {
             if (type[i] != ORC_FLUID) continue;
@@ -719,11 +726,9 @@ static int stage_predict(const orc_params* p, int64_t n, const double* pos, cons
                 d2 = d2 + d * d;
             }
             if (sqrt(d2) > R->max_disp) R->max_disp = sqrt(d2);
+            if (sqrt(d2) > half) n_fast++;
         }
-        /* The cell grid is built at r^k and reused at r*; it stays a complete candidate  */
-        /* filter while no particle moves more than half the skin.                        */
-        double re = p->re_n > p->re_lap ? p->re_n : p->re_lap;
-        if (R->max_disp > 0.5 * p->cell_skin * re) rc = ORC_ESKIN;
+        if (n_fast > (n / 256 > 64 ? n / 256 : 64)) rc = ORC_ESKIN;
     }
     csr_free(&nb);
     free(lap);

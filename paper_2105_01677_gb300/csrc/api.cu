@@ -365,6 +365,7 @@ int allocate(Ctx* c) {
                                 scan_scratch_words((int64_t)n + 1));
     A(scan_scratch, sw)
     A(partials, 4096) A(cg, 1) A(st, 1)
+    A(fast_idx, (size_t)skin_patch_cap(c))
     c->stage_bytes = n * (3 * 8 * 2 + 8 + 8 + 4 + 2) + 1024;
     { uint8_t* s8 = nullptr; if ((rc = alloc_dev(c, &s8, c->stage_bytes))) return rc; c->stage = s8; }
 #undef A
@@ -459,14 +460,17 @@ void stage_collect(Ctx* c, const bool* used) {
     }
 }
 
-// One step (advance) or steps 1-5 only (solve).
 constexpr double kMinListSkin = 0.02;
+}  // namespace
+
+// One step (advance) or steps 1-5 only (solve).
 
 int do_step(Ctx* c, bool advance, mps_report* rep) {
     const mps_params& P = c->prm;
     int rc;
     if (step_graph_eligible(c, advance)) return step_graph_step(c, rep);
     rep->step_graph = 0;
+    rep->n_fast = 0;
     const bool keep = P.list_every > 1;
     // the radius the skin is measured against: max(re) (of the scene with the smallest
     // spacing in an ensemble)
@@ -483,6 +487,8 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     // A kept list that fails the check for r* is gathered afresh at r^k and the step
     // restarts (r^k, u^k are untouched until the update).
     bool fresh = !keep || c->need_list || c->list_age >= P.list_every;
+    // particles beyond the full skin: their pairs found by a direct search at r* (one scene)
+    bool patch = false, patched = false;
     for (;;) {
         MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
         if (fresh) {
@@ -516,6 +522,15 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         launch_predict_rows(c);                                        // 2
         if (P.pressure_mode == 0 && P.source_term == 2) launch_ecs_rates(c);   // at r^k, u^k
         stage_end(c, MPS_STAGE_PREDICT);
+        if (patch) {
+            launch_fast_mark(c, 0.5 * P.cell_skin * re_max);
+            if ((rc = read_status(c))) return rc;
+            const int n_fast = (int)c->st_host->n_fast;
+            rep->n_fast = n_fast;
+            if (n_fast > skin_patch_cap(c)) return MPS_ESKIN;
+            if ((rc = launch_fast_patch(c, n_fast, c->r_v.hi))) return rc;
+            patched = true;
+        }
         // per-slot outputs of the build; slots it does not visit (GHOST) keep these zeros
         MPS_CUDA(c, cudaMemsetAsync(c->nstar, 0, n * sizeof(double), c->stream));
         MPS_CUDA(c, cudaMemsetAsync(c->flag, 0, n, c->stream));
@@ -548,13 +563,17 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         rep->list_gathered = fresh ? 1 : 0;
         if ((rc = status_error(s))) return rc;
         const double half = adapt ? 0.5 * c->gathered_skin * re_max : c->skin_half;
-        if (rep->max_disp > half) {
+        if (rep->max_disp > half && !patched) {
             if (!fresh) {                                              // a kept list falls short
                 fresh = true;                                          // gather afresh at r^k
                 continue;
             }
             if (adapt && c->gathered_skin < P.cell_skin) {
                 c->list_skin = P.cell_skin;                            // the full skin
+                continue;
+            }
+            if (c->n_scenes == 1) {                                    // complete the lists of
+                patch = true;                                          // the particles beyond it
                 continue;
             }
             return MPS_ESKIN;
@@ -617,6 +636,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     return MPS_OK;
 }
 
+namespace {
 int alloc_adjoint(Ctx* c) {
     AdjBuffers& a = c->adj;
     if (a.ready) return MPS_OK;

@@ -53,6 +53,8 @@ struct DevStatus {
     unsigned int gather_next;           // next occupied cell of the candidate gather (dynamic)
     unsigned int pad1;
     unsigned long long list_tests;      // candidate-list entries classified by the build (at r*)
+    unsigned int n_fast;                // particles beyond half the full skin (skinpatch.cu)
+    unsigned int pad2;
 };
 
 // Scalars of one CG solve; updated by the last block of each reduction kernel.
@@ -201,9 +203,14 @@ void state_ptrs_save(const Ctx* c, void* rec);
 void state_ptrs_load(Ctx* c, const void* rec);
 // the candidate and predicate bands of radius re for coordinates up to X (api.cu)
 Radius make_radius(double re, double X);
+// candidate lists completed for particles beyond the full skin (skinpatch.cu)
+int skin_patch_cap(const Ctx* c);
+void launch_fast_mark(Ctx* c, double half);
+int launch_fast_patch(Ctx* c, int n_fast, float hv2);
 // whole steps as CUDA graphs (stepgraph.cu)
 bool step_graph_eligible(const Ctx* c, bool advance);
 int step_graph_step(Ctx* c, mps_report* rep);
+int do_step(Ctx* c, bool advance, mps_report* rep);   // api.cu: the host-driven step
 void step_graphs_destroy(Ctx* c);
 void launch_clamp_pmin(Ctx* c);
 void launch_gradient_correct(Ctx* c);
@@ -323,6 +330,10 @@ struct Ctx {
     BucketGraph bucket_graph[2];
     // the candidate and predicate bands of radius re for coordinates up to X (api.cu)
 Radius make_radius(double re, double X);
+// candidate lists completed for particles beyond the full skin (skinpatch.cu)
+int skin_patch_cap(const Ctx* c);
+void launch_fast_mark(Ctx* c, double half);
+int launch_fast_patch(Ctx* c, int n_fast, float hv2);
 // whole steps as CUDA graphs (stepgraph.cu): the control block (device and pinned host
     // mirror), the two scene tables of an ensemble (adaptive and full list skin), the pinned
     // copy of the per-scene residual sums, and the control block kernels read while a step
@@ -335,6 +346,10 @@ Radius make_radius(double re, double X);
     double* scene_sums_host = nullptr;
     double rv_var_skin = -1.0;         // the adaptive skin the device table holds
     StepCtl* capture_ctl = nullptr;
+    // particles that outran the full skin in this step (skinpatch.cu), and whether the step
+    // runs launch by launch (a step graph hands such a step to the host-driven path)
+    int32_t* fast_idx = nullptr;
+    bool force_host = false;
 
     // state (sorted order) and double buffers
     double4 *pos, *vel, *pos_alt, *vel_alt;

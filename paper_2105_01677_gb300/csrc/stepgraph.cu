@@ -275,7 +275,8 @@ int build_step_graph(Ctx* c, StepGraph* sg) {
 
 bool step_graph_eligible(const Ctx* c, bool advance) {
     const mps_params& P = c->prm;
-    return P.step_graph != 0 && advance && !c->vjp && !c->profiling && P.list_every <= 1 &&
+    return P.step_graph != 0 && advance && !c->vjp && !c->profiling && !c->force_host &&
+           P.list_every <= 1 &&
            (P.pressure_mode == 1 || (P.precision == 1 && P.ppe_host_loop == 0));
 }
 
@@ -363,6 +364,7 @@ int step_graph_step(Ctx* c, mps_report* rep) {
     rep->cg_resid = 0.0;
     rep->list_gathered = 1;
     rep->step_graph = 1;
+    rep->n_fast = 0;
     c->launches += sg->launches_pre + attempts * sg->launches_attempt;
     c->list_age = 0;
     c->need_list = false;
@@ -372,7 +374,15 @@ int step_graph_step(Ctx* c, mps_report* rep) {
         if (st.err & kErrCap) return MPS_ECAP;
         return MPS_EDEVICE;
     }
-    if (h.skin_err) return MPS_ESKIN;
+    if (h.skin_err) {
+        if (S > 1) return MPS_ESKIN;
+        // a particle outran the full skin: the host-driven step completes the lists of such
+        // particles by a direct search (skinpatch.cu) and repeats the step (nothing advanced)
+        c->force_host = true;
+        rc = do_step(c, true, rep);
+        c->force_host = false;
+        return rc;
+    }
     // next list skin: three times what this step's displacement needs, within
     // [0.02, cell_skin] (as the host-driven step)
     c->list_skin = std::min(P.cell_skin, std::max(0.02, 3.0 * (2.0 * rep->max_disp / re_max)));

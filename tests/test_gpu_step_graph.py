@@ -133,7 +133,8 @@ def test_step_graph_reports_skin_and_coincidence_errors():
     sc = scenes.dam_break_2d(seed=8)
     f = np.flatnonzero(sc.types == scenes.FLUID)
     fast = sc.copy()
-    fast.vel[f[10]] = [300.0, 0.0]     # 3 cm in one step: beyond any skin
+    fast.vel[f[:65]] = [300.0, 0.0]    # 65 particles beyond the skin: more than the direct
+                                       # search completes (max(64, n/256))
     coinc = sc.copy()
     coinc.pos[f[1]] = coinc.pos[f[0]]
     for sgflag in (1, 0):

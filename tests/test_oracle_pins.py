@@ -445,3 +445,31 @@ def test_ppe_operator_is_minus_laplacian_over_rho_on_quadratics(dim):
     assert inner.sum() > 0 and np.all(fl[inner] == 0)
     diag_add = prm.alpha_c / prm.dt ** 2
     np.testing.assert_allclose(y[inner] - diag_add * p[inner], -2.0 * dim / prm.rho, rtol=1e-8)
+
+
+def test_particles_beyond_the_skin_keep_exact_sets_up_to_the_limit():
+    """The neighbour sets at r* are searched at r*: a few particles moving farther than half
+    the cell skin in one step change nothing (the step equals the one with a skin so large
+    that nobody outruns it, bit for bit); more than max(64, n/256) such particles is
+    MPS_ESKIN, the limit of the library's direct search."""
+    sc = scenes.dam_break_2d(seed=4)
+    f = np.flatnonzero(sc.types == scenes.FLUID)
+    kicked = sc.copy()
+    kicked.vel[f[[5, 300, 700]]] = [[40.0, 0.0], [0.0, 35.0], [-30.0, 20.0]]   # 3-4 mm/step
+    out = []
+    for skin in (0.1, 2.0):
+        st = oracle.State.from_scene(kicked)
+        rc, rep = oracle.step(oracle.params_for(kicked, cell_skin=skin), st, check=False)
+        assert rc == 0 and rep["max_disp"] > 0.5 * 0.1 * 4.0 * sc.l0
+        out.append(st)
+    for k in ("pos", "vel", "p", "nstar", "flags"):
+        assert np.array_equal(getattr(out[0], k), getattr(out[1], k)), k
+    many = sc.copy()
+    many.vel[f[:65]] = [30.0, 0.0]
+    rc, _ = oracle.step(oracle.params_for(many, cell_skin=0.1), oracle.State.from_scene(many),
+                        check=False)
+    assert rc == -5
+    many.vel[f[64]] = [0.0, 0.0]
+    rc, _ = oracle.step(oracle.params_for(many, cell_skin=0.1), oracle.State.from_scene(many),
+                        check=False)
+    assert rc == 0
