@@ -25,15 +25,23 @@ namespace mps {
 namespace {
 
 // One block per occupied cell (taken in turn from a device counter), one thread per
-// particle of the cell.  The particles of the
-// 3^d surrounding cells (contiguous slot ranges in Morton order) are staged once in shared
-// memory as (x, y, z, slot) and every thread walks the same staged candidates, four per
-// shared-memory load, so each read is a broadcast; one barrier pair per cell (more only when a cell's
-// neighbourhood exceeds CHUNK candidates).
+// particle of the cell.  The particles of the 3^d surrounding cells (contiguous slot ranges
+// in Morton order) are staged in shared memory as (x, y, z, slot) and every thread walks
+// the same staged candidates, four per shared-memory load, so each read is a broadcast.
+// Staging keeps only candidates within the candidate bound of the block's own cell box (no
+// particle of the cell can pair with the others: about a quarter of the 3^d neighbourhood
+// in 3D, mostly in the edge and corner cells).  Each warp filters a contiguous part of the
+// candidate range into its own segment of the staging buffer (ballot compaction, no block
+// barrier), in candidate order, so the lists come out in a fixed order.  One barrier pair
+// per cell, more only when the neighbourhood exceeds a chunk.
 template <int BT, int CHUNK, class Op>
 __global__ void __launch_bounds__(BT)
     k_gather(Op op, const int32_t* __restrict__ cell_start, const uint32_t* __restrict__ occ,
              const DevStatus* st, GridDesc g) {
+    constexpr int NW = BT / 32;
+    constexpr int WCAP = CHUNK / NW;     // staged entries per warp segment (a multiple of 4)
+    constexpr int WRAW = WCAP - 4;       // raw candidates a warp filters per chunk (room for padding)
+    static_assert(WCAP % 4 == 0 && WRAW > 0, "chunk too small for the block");
     // staged candidates, structure of arrays: x, y, z relative to the grid origin, slot
     extern __shared__ __align__(16) float s_buf[];
     float* s_x = s_buf;
@@ -42,11 +50,14 @@ __global__ void __launch_bounds__(BT)
     int* s_j = (int*)(s_buf + 3 * CHUNK);
     __shared__ int s_cs[27], s_pref[28];
     __shared__ int s_nc;
+    __shared__ int s_cnt[NW];
+    __shared__ float s_box[7];           // the cell box (lo xyz, hi xyz) and the bound
     const unsigned n_occ = *(volatile const unsigned*)&st->n_occ;
     // an ensemble's keys carry the scene above the cell's Morton code: neighbour cells are
     // looked up under the same prefix, so no gather crosses scenes
     const uint32_t local_mask = (g.dim * g.bits >= 32) ? 0xFFFFFFFFu : ((1u << (g.dim * g.bits)) - 1u);
     __shared__ unsigned s_ci;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         __syncthreads();   // s_ci of the previous cell has been read by every thread
         if (threadIdx.x == 0) s_ci = atomicAdd(&((DevStatus*)st)->gather_next, 1u);
@@ -80,33 +91,68 @@ __global__ void __launch_bounds__(BT)
                     }
             s_pref[m] = pref;
             s_nc = m;
+            // the cell box in the FP32 coordinates relative to the grid origin, widened by
+            // several roundings of the largest coordinate (a particle's FP32 position may lie
+            // just outside its binary64 cell)
+            double ext = 0.0;
+            for (int a = 0; a < g.dim; a++) ext = fmax(ext, g.ncell[a] * g.h);
+            const float eps = (float)(ext * 4.8e-7) + 1e-30f;
+            for (int a = 0; a < 3; a++) {
+                const bool used = a < g.dim;
+                s_box[a] = used ? (float)(cc[a] * g.h) - eps : -eps;
+                s_box[3 + a] = used ? (float)((cc[a] + 1) * g.h) + eps : eps;
+            }
+            s_box[6] = op.block_bound2(c0) * 1.00001f;
         }
         __syncthreads();
         const int ncand = s_pref[s_nc];
-        const int ncells = s_nc;
-        const bool once = ncand <= CHUNK;   // whole neighbourhood staged once for the cell
-        // copy candidates [base, base + len) cell by cell (coalesced slot ranges)
-        // (padded with up to three sentinels at infinity, so that the walk below reads four
-        // candidates per shared-memory load and needs no tail)
+        const float4 blo = make_float4(s_box[0], s_box[1], s_box[2], 0.f);
+        const float4 bhi = make_float4(s_box[3], s_box[4], s_box[5], 0.f);
+        const float bound2 = s_box[6];
+        const bool once = ncand <= NW * WRAW;   // whole neighbourhood staged once for the cell
+        // filter raw candidates [base, base + len): warp w takes a contiguous part and
+        // appends the candidates near the cell box to its segment (padded with sentinels at
+        // infinity to a multiple of four, so that the walk needs no tail)
         auto stage = [&](int base, int len) {
-            for (int m = 0; m < ncells; m++) {
-                const int a = max(s_pref[m], base), b = min(s_pref[m + 1], base + len);
-                const int off = s_cs[m] - s_pref[m];
-                for (int f = a + (int)threadIdx.x; f < b; f += BT) {
-                    const float4 q = op.pos32[f + off];
-                    s_x[f - base] = q.x;
-                    s_y[f - base] = q.y;
-                    s_z[f - base] = q.z;
-                    s_j[f - base] = f + off;
+            const int per = (len + NW - 1) / NW;
+            const int f0 = base + warp * per, f1 = min(base + len, f0 + per);
+            float* sx = s_x + warp * WCAP;
+            float* sy = s_y + warp * WCAP;
+            float* sz = s_z + warp * WCAP;
+            int* sj = s_j + warp * WCAP;
+            int cnt = 0, m = 0;
+            for (int fb = f0; fb < f1; fb += 32) {
+                const int f = fb + lane;
+                bool keep = false;
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                int slot = -1;
+                if (f < f1) {
+                    while (f >= s_pref[m + 1]) m++;
+                    slot = f + s_cs[m] - s_pref[m];
+                    q = op.pos32[slot];
+                    const float dx = fmaxf(fmaxf(blo.x - q.x, q.x - bhi.x), 0.f);
+                    const float dy = fmaxf(fmaxf(blo.y - q.y, q.y - bhi.y), 0.f);
+                    const float dz = fmaxf(fmaxf(blo.z - q.z, q.z - bhi.z), 0.f);
+                    keep = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < bound2;
                 }
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int k = cnt + __popc(bal & ((1u << lane) - 1u));
+                    sx[k] = q.x;
+                    sy[k] = q.y;
+                    sz[k] = q.z;
+                    sj[k] = slot;
+                }
+                cnt += __popc(bal);
             }
-            const int pad = len + (int)threadIdx.x;
-            if (pad < ((len + 3) & ~3)) {
-                s_x[pad] = __int_as_float(0x7f800000);
-                s_y[pad] = 0.f;
-                s_z[pad] = 0.f;
-                s_j[pad] = -1;
+            const int padded = (cnt + 3) & ~3;
+            if (lane < padded - cnt) {
+                sx[cnt + lane] = __int_as_float(0x7f800000);
+                sy[cnt + lane] = 0.f;
+                sz[cnt + lane] = 0.f;
+                sj[cnt + lane] = -1;
             }
+            if (lane == 0) s_cnt[warp] = padded;
         };
         if (once) {
             stage(0, ncand);
@@ -116,26 +162,37 @@ __global__ void __launch_bounds__(BT)
             const int i = ib + threadIdx.x;
             const bool act = (i < c1) && op.active(i);
             const int nact = __syncthreads_count(act);
-            if (threadIdx.x == 0 && nact)
-                atomicAdd(&((DevStatus*)st)->cand_tests, (unsigned long long)nact * (unsigned long long)ncand);
             typename Op::Center ctr;
             op.begin(i, act, ctr);
-            for (int base = 0; base < ncand; base += CHUNK) {
-                const int len = min(CHUNK, ncand - base);
+            for (int base = 0; base < ncand; base += NW * WRAW) {
+                const int len = min(NW * WRAW, ncand - base);
                 if (!once) {
                     if (base > 0 || ib > c0) __syncthreads();   // buffer reuse
                     stage(base, len);
                     __syncthreads();
                 }
+                if (threadIdx.x == 0 && nact) {
+                    int staged = 0;
+                    for (int w2 = 0; w2 < NW; w2++) staged += s_cnt[w2];
+                    atomicAdd(&((DevStatus*)st)->cand_tests,
+                              (unsigned long long)nact * (unsigned long long)staged);
+                }
                 if (act) {
-                    for (int k = 0; k < len; k += 4) {
-                        const float4 x4 = *(const float4*)&s_x[k], y4 = *(const float4*)&s_y[k];
-                        const float4 z4 = *(const float4*)&s_z[k];
-                        const int4 j4 = *(const int4*)&s_j[k];
-                        op.visit2(ctr, i, make_float2(x4.x, x4.y), make_float2(y4.x, y4.y),
-                                  make_float2(z4.x, z4.y), make_int2(j4.x, j4.y));
-                        op.visit2(ctr, i, make_float2(x4.z, x4.w), make_float2(y4.z, y4.w),
-                                  make_float2(z4.z, z4.w), make_int2(j4.z, j4.w));
+                    for (int w2 = 0; w2 < NW; w2++) {
+                        const int mcnt = s_cnt[w2];
+                        const float* sx = s_x + w2 * WCAP;
+                        const float* sy = s_y + w2 * WCAP;
+                        const float* sz = s_z + w2 * WCAP;
+                        const int* sj = s_j + w2 * WCAP;
+                        for (int k = 0; k < mcnt; k += 4) {
+                            const float4 x4 = *(const float4*)&sx[k], y4 = *(const float4*)&sy[k];
+                            const float4 z4 = *(const float4*)&sz[k];
+                            const int4 j4 = *(const int4*)&sj[k];
+                            op.visit2(ctr, i, make_float2(x4.x, x4.y), make_float2(y4.x, y4.y),
+                                      make_float2(z4.x, z4.y), make_int2(j4.x, j4.y));
+                            op.visit2(ctr, i, make_float2(x4.z, x4.w), make_float2(y4.z, y4.w),
+                                      make_float2(z4.z, z4.w), make_int2(j4.z, j4.w));
+                        }
                     }
                 }
             }
@@ -213,6 +270,11 @@ struct VerletOp {
         vcnt[i] = min(c.cnt, cap_v);
         if (c.cnt > cap_v) atomicOr(&st->err, kErrCap);
     }
+    // the candidate bound of the cell's particles (all of one scene), for the staging filter
+    __device__ float block_bound2(int i) const {
+        if (sid) return scn[sid[i]].rv.hi;
+        return hv2_dev ? *hv2_dev : hv2;
+    }
 };
 
 // ------------------------------------------------------------------------------ debug
@@ -250,6 +312,7 @@ struct NbrOp {
     __device__ void finish(int i, bool act, const Center& c) const {
         if (act && !row_off) out_cnt[i] = c.cnt;
     }
+    __device__ float block_bound2(int) const { return r.hi; }
 };
 
 __global__ void k_copy_star(int n, const double4* pos, const double4* vel, const float4* pos32,
@@ -265,7 +328,8 @@ __global__ void k_copy_star(int n, const double4* pos, const double4* vel, const
 
 template <int BT, class Op>
 void launch_gather_bt(Ctx* c, const Op& op, int blocks_per_sm) {
-    constexpr int kChunk = 512;
+    // staged candidates per chunk: 512, split evenly over the block's warps (528 for three)
+    constexpr int kChunk = (BT == 96) ? 528 : 512;
     // blocks take occupied cells from a counter: cells differ a lot in work (full fluid
     // cells against sparse wall or surface cells), so a static split leaves SMs idle
     cudaMemsetAsync(&c->st->gather_next, 0, sizeof(unsigned int), c->stream);
