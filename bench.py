@@ -639,7 +639,7 @@ def run_gb300(args):
         ne = sum(sc.n for sc in E)
         ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
                            cg_tol=1e-8, cg_x0=args.cg_x0)
-        tuning = ens.autotune(3)
+        tuning_e = ens.autotune(3)
         ens.step(args.warmup)
         barrier()
         ke = args.ensemble_steps
@@ -653,7 +653,7 @@ def run_gb300(args):
                     "scenes": len(E), "particles": ne, "fluid": int(sum(sc.n_fluid for sc in E)),
                     "ppe_x0": X0_NAMES[args.cg_x0],
                     "value": world * ne * ke / (ms_e * 1e-3), "unit": UNIT,
-                    "ms_per_step": ms_e / ke, "steps": ke, "tuning": tuning,
+                    "ms_per_step": ms_e / ke, "steps": ke, "tuning": tuning_e,
                     "cg_iters_mean": float(np.mean([x[0] for x in it_e])),
                     "worst_scene_resid": float(res.max()),
                     "launches_per_step": prof_e["launches"] / max(ke, 1),
