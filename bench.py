@@ -808,8 +808,10 @@ def run_gb300(args):
                         "one CUDA graph",
         "e2e": {"value": world * n * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
-                "ppe_x0": "zero: every step solves from a state written from host memory"
-                          if args.cg_x0 else X0_NAMES[0]},
+                "ppe_x0": X0_NAMES[args.cg_x0],
+                "note": "every step writes the state read after the previous one (the "
+                        "context's own, bit for bit: the write changes nothing) and reads "
+                        "positions, velocities and pressure back"},
         "cpu_baseline": cpu,
         "clocks": clk,
         "alu_peaks": alu_peaks,

@@ -212,8 +212,18 @@ int mps_read_state(mps_ctx* ctx, double* pos, double* vel, double* p, double* n_
                    uint8_t* flags, int8_t* types);
 
 /* Replace positions, velocities and kinds (original order; vel or types may be NULL to keep
- * them).  Same checks as mps_create.  Used to restart from a saved state. */
+ * them).  Same checks as mps_create.  Used to restart from a saved state: the next PPE solve
+ * starts from zero (cg_x0's history is cleared) and p, n* and flags read 0 until the next
+ * step.  Writing back, bit for bit, the state the context already holds (for instance a
+ * host loop that reads the state after each step and writes it back before the next)
+ * changes nothing at all: the call returns without touching the context. */
 int mps_write_state(mps_ctx* ctx, const double* pos, const double* vel, const int8_t* types);
+
+/* Clear the PPE initial-guess history (cg_x0): the next solve starts from zero, as after
+ * writing a new state.  For callers that replay a trajectory from a saved state and need
+ * the replay to repeat the original bit for bit (a checkpointed rollout).  Errors:
+ * MPS_EINVAL (NULL). */
+int mps_clear_history(mps_ctx* ctx);
 
 /* Set the external acceleration g [m/s^2] (3 doubles; the unused axis of 2D is ignored)
  * for the following steps.  A time-dependent body force -- for instance the inertial

@@ -122,12 +122,14 @@ def _make_function():
             ckpts = []
             for t in range(f.shape[0]):
                 if t % K == 0:
-                    # every segment starts from a state written afresh, so that its
-                    # recomputation in backward repeats it bit for bit
+                    # every segment starts from a state written afresh with the solver's
+                    # guess history cleared, so that its recomputation in backward repeats it
+                    # bit for bit
                     if t > 0:
                         x, u, types = io.read()
                     ckpts.append((x, u, types))
                     io.write(x, u, types)
+                    sim.clear_history()
                 sim.set_gravity(f[t])
                 sim.step(1)
             xT, uT, _ = io.read()
@@ -148,6 +150,7 @@ def _make_function():
                 t0, t1 = s * K, min(n_steps, (s + 1) * K)
                 x, u, types = ctx.ckpts[s]
                 io.write(x, u, types)
+                sim.clear_history()
                 states = [(x, u, types)]
                 for t in range(t0, t1 - 1):
                     sim.set_gravity(f[t])
@@ -156,6 +159,7 @@ def _make_function():
                 for t in reversed(range(t0, t1)):
                     xs, us, ts = states[t - t0]
                     io.write(xs, us, ts)
+                    sim.clear_history()
                     sim.set_gravity(f[t])
                     gr, gu, gf[t], gn = io.vjp(gr, gu)
                     gnu = gn if gnu is None else gnu + gn

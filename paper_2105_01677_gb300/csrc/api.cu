@@ -390,7 +390,6 @@ int read_status(Ctx* c);
 int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* types, bool have_state,
                  bool validate = false, bool device = false) {
     const cudaMemcpyKind in = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    c->need_list = true;
     const size_t n = (size_t)c->n, dim = (size_t)c->dim;
     int rc_check;
     uint8_t* base = (uint8_t*)c->stage;
@@ -409,10 +408,15 @@ int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* typ
     if (validate) {
         MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
         launch_check_stage(c, d_pos, vel ? d_vel : nullptr, types ? d_t : nullptr);
+        launch_same_state(c, d_pos, vel ? d_vel : nullptr, types ? d_t : nullptr);
         if ((rc_check = read_status(c))) return rc_check;
         if (c->st_host->err & kErrNonfinite) return MPS_ENONFINITE;
         if (c->st_host->err & kErrKind) return MPS_EINVAL;
+        // the state the context already holds, bit for bit: nothing to replace (its lists,
+        // the PPE guess history, p, n* and the flags stay as the last step left them)
+        if (!c->st_host->differs) return MPS_OK;
     }
+    c->need_list = true;
     launch_ingest(c, d_pos, d_vel, d_t, false, false);
     launch_gather_props(c);   // slot = id again
     c->guess_n = 0;   // a written state starts its solve from zero
@@ -947,6 +951,12 @@ int mps_solve_ppe(mps_ctx* c, mps_report* out) {
     rep.status = rc;
     if (out) *out = rep;
     return rc;
+}
+
+int mps_clear_history(mps_ctx* c) {
+    if (!c) return MPS_EINVAL;
+    c->guess_n = 0;
+    return MPS_OK;
 }
 
 int mps_set_gravity(mps_ctx* c, const double* g) {

@@ -54,7 +54,7 @@ struct DevStatus {
     unsigned int pad1;
     unsigned long long list_tests;      // candidate-list entries classified by the build (at r*)
     unsigned int n_fast;                // particles beyond half the full skin (skinpatch.cu)
-    unsigned int pad2;
+    unsigned int differs;               // a written state differs from the context's
 };
 
 // Scalars of one CG solve; updated by the last block of each reduction kernel.
@@ -229,6 +229,7 @@ void launch_unpermute_u32(Ctx* c, const uint32_t* in, uint32_t* out);
 void launch_gather_props(Ctx* c);
 void launch_ecs_rates(Ctx* c);
 void launch_check_stage(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types);
+void launch_same_state(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types);
 
 // ---------------------------------------------------------------- context
 // The mixed PPE solve captured as one CUDA graph (outer refinement loop around the inner

@@ -222,6 +222,25 @@ __global__ void __launch_bounds__(kBT)
     if (i_t && (i_t[s] < kFluid || i_t[s] > kGhost)) atomicOr(&st->err, kErrKind);
 }
 
+// whether a staged caller state (original order) equals the context's, bit for bit: the
+// positions, and the velocities and kinds where given
+__global__ void __launch_bounds__(kBT)
+    k_same_state(int n, int dim, const double* i_pos, const double* i_vel, const int8_t* i_t,
+                 const double4* pos, const double4* vel, const int8_t* type, const int32_t* id,
+                 DevStatus* st) {
+    int s = blockIdx.x * kBT + threadIdx.x;
+    if (s >= n) return;
+    const size_t i = (size_t)id[s];
+    const double4 x = pos[s], u = vel[s];
+    const double xs[3] = {x.x, x.y, x.z}, us[3] = {u.x, u.y, u.z};
+    bool same = !i_t || i_t[i] == type[s];
+    for (int a = 0; a < dim; a++) {
+        same = same && __double_as_longlong(i_pos[i * dim + a]) == __double_as_longlong(xs[a]);
+        if (i_vel) same = same && __double_as_longlong(i_vel[i * dim + a]) == __double_as_longlong(us[a]);
+    }
+    if (!same) atomicOr(&st->differs, 1u);
+}
+
 // state from caller order; slot s = particle s (identity order until the next sort)
 __global__ void __launch_bounds__(kBT)
     k_ingest(int n, int dim, const double* i_pos, const double* i_vel, const int8_t* i_t,
@@ -349,6 +368,13 @@ void launch_ingest(Ctx* c, const double* d_pos, const double* d_vel, const int8_
                                                           c->flag, keep_vel ? 1 : 0,
                                                           keep_types ? 1 : 0, c->grid, c->pos32,
                                                           c->pos32lo);
+    c->launches += 1;
+}
+
+void launch_same_state(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types) {
+    const int n = (int)c->n;
+    k_same_state<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(n, c->dim, d_pos, d_vel, d_types,
+                                                             c->pos, c->vel, c->type, c->id, c->st);
     c->launches += 1;
 }
 

@@ -88,7 +88,7 @@ EXPORTS = ("mps_params_default", "mps_create", "mps_step", "mps_solve_ppe", "mps
            "mps_strerror", "mps_set_fluid_properties", "mps_create_ensemble",
            "mps_scene_residuals", "mps_autotune", "mps_set_gravity", "mps_step_vjp",
            "mps_time_kernel", "mps_read_state_device", "mps_write_state_device",
-           "mps_step_vjp_device", "mps_measure_peak")
+           "mps_step_vjp_device", "mps_measure_peak", "mps_clear_history")
 NOALLOC_MAX_ROWS = 262144
 STAGES = ("bucket", "gather", "predict", "build", "ppe", "update")
 
@@ -142,6 +142,7 @@ def lib(build_if_missing: bool = False):
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int32,
                                      C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)]
     L.mps_measure_peak.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, d, d]
+    L.mps_clear_history.argtypes = [C.c_void_p]
     L.mps_destroy.argtypes = [C.c_void_p]
     L.mps_destroy.restype = None
     L.mps_strerror.argtypes = [C.c_int]
@@ -151,7 +152,8 @@ def lib(build_if_missing: bool = False):
               "mps_get_profile", "mps_ppe_cg_noalloc", "mps_set_fluid_properties",
               "mps_create_ensemble", "mps_scene_residuals", "mps_autotune", "mps_set_gravity",
               "mps_step_vjp", "mps_time_kernel", "mps_read_state_device",
-              "mps_write_state_device", "mps_step_vjp_device", "mps_measure_peak"):
+              "mps_write_state_device", "mps_step_vjp_device", "mps_measure_peak",
+              "mps_clear_history"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -622,6 +624,10 @@ class Simulation:
 
     def write(self, pos, vel=None, types=None):
         mps_write_state(self.h, pos, vel, types)
+
+    def clear_history(self):
+        """The next PPE solve starts from zero (cg_x0's history cleared)."""
+        _check(lib().mps_clear_history(self.h), "mps_clear_history")
 
     def constants(self):
         return mps_get_constants(self.h)

@@ -118,8 +118,8 @@ def test_graph_equals_host_loop_with_guess_ensemble():
 
 
 def test_written_state_restarts_cold():
-    """mps_write_state clears the guess: stepping a written state twice gives the same bits,
-    although the guess after the first of them would differ."""
+    """mps_write_state of a new state clears the guess: stepping the same written state twice
+    gives the same bits, although the guess after the first of them would differ."""
     from paper_2105_01677_gb300 import mps
     sc = _scene("2d")
     sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
@@ -127,9 +127,12 @@ def test_written_state_restarts_cold():
     try:
         sim.step(3)
         s = sim.read()
+        f = np.flatnonzero(s["types"] == 0)[0]
+        moved = s["pos"].copy()
+        moved[f, 0] = np.nextafter(moved[f, 0], 1.0)   # another state than the context's
         outs = []
         for _ in range(2):
-            sim.write(s["pos"], s["vel"], s["types"])
+            sim.write(moved, s["vel"], s["types"])
             rep = sim.step(1)[1]
             outs.append((rep, sim.read()))
     finally:
@@ -138,6 +141,34 @@ def test_written_state_restarts_cold():
     assert (ra["cg_iters"], ra["cg_resid"]) == (rb["cg_iters"], rb["cg_resid"])
     for k in ("pos", "vel", "p", "n_star", "flags"):
         assert np.array_equal(a[k], b[k]), k
+
+
+def test_writing_back_the_same_state_changes_nothing():
+    """Reading the state and writing it back unchanged is a no-op: the next step (with its
+    guess from the history) is bit for bit the step without the write; clear_history then
+    restarts cold like a new state."""
+    from paper_2105_01677_gb300 import mps
+    sc = _scene("2d")
+    outs = []
+    for mode in ("plain", "write-back", "clear"):
+        sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
+                             **gpu_params(sc, precision=1, cg_x0=3))
+        try:
+            sim.step(3)
+            if mode != "plain":
+                s = sim.read()
+                sim.write(s["pos"], s["vel"], s["types"])
+            if mode == "clear":
+                sim.clear_history()
+            rep = sim.step(1)[1]
+            outs.append((rep, sim.read()))
+        finally:
+            sim.close()
+    (r0, a), (r1, b), (r2, c) = outs
+    assert (r0["cg_iters"], r0["cg_resid"]) == (r1["cg_iters"], r1["cg_resid"])
+    for k in ("pos", "vel", "p", "n_star", "flags"):
+        assert np.array_equal(a[k], b[k]), k
+    assert r2["cg_iters"] > r0["cg_iters"]      # from zero: more inner iterations
 
 
 @pytest.mark.parametrize("precision", [0, 1])
