@@ -91,8 +91,9 @@ typedef struct {
     int32_t ppe_operator;     /* mixed inner operator: 0 stored FP32 coefficients,             *
                                * 1 matrix-free (coefficients recomputed from positions)        */
     int32_t device;           /* CUDA device ordinal                                           */
-    int32_t gather_block;     /* threads per cell block of the candidate gather: 32, 64, 96 or *
-                               * 128; 0 chooses by dimension (tuning only, results identical)  */
+    int32_t gather_block;     /* threads per cell block of the candidate gather (warps that   *
+                               * share a cell's candidates): 32, 64, 96 or 128; 0 chooses by   *
+                               * dimension (tuning only, results identical)                    */
     int32_t list_every;       /* candidate lists (cell gather within h): 0 or 1 gathers them  *
                                * every step; K > 1 keeps them for up to K steps, gathering    *
                                * afresh earlier as soon as a particle has moved more than     *

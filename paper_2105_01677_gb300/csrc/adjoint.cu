@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kBT) k_adj_star_fw(AdjArgs a, const int32_t* r
         const float4 qk = a.ps32[k];
         const int cnt = a.vcnt[k];
         for (int t = 0; t < cnt; t++) {
-            const int j = a.vcol[sell(k, t, a.cap_v)];
+            const int j = a.vcol[sell8(k, t, a.cap_v)];
             if (a.type[j] != kDummy) continue;
             if (!in_radius(dist2_f(qk, a.ps32[j]), a.rn, a.ps, k, j, xk)) continue;
             const double4 x = sub4(a.ps[j], xk);
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kBT) k_adj_star_other(AdjArgs a) {
         const float4 qk = a.ps32[k];
         const int cnt = a.vcnt[k];
         for (int t = 0; t < cnt; t++) {
-            const int j = a.vcol[sell(k, t, a.cap_v)];
+            const int j = a.vcol[sell8(k, t, a.cap_v)];
             if (!in_radius(dist2_f(qk, a.ps32[j]), a.rn, a.ps, k, j, xk)) continue;
             const double gnj = gn_of(a, j);
             if (gnj == 0.0) continue;
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kBT) k_adj_visc_f(AdjArgs a, const int32_t* ro
     const int cnt = a.vcnt[k];
     double lap = 0.0;   // sum_j w (gu*_k . (u_j - u_k))
     for (int t = 0; t < cnt; t++) {
-        const int j = a.vcol[sell(k, t, a.cap_v)];
+        const int j = a.vcol[sell8(k, t, a.cap_v)];
         if (!in_radius(dist2_f(qk, a.pos32[j]), a.rl, a.pos, k, j, xk)) continue;
         const double w = visc_pair(a, j, xk, uk, ak, orr, ou);
         lap = fma(w, dot3(gsk, sub4(a.vel[j], uk)), lap);
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kBT) k_adj_visc_other(AdjArgs a) {
     const float4 qk = a.pos32[k];
     const int cnt = a.vcnt[k];
     for (int t = 0; t < cnt; t++) {
-        const int j = a.vcol[sell(k, t, a.cap_v)];
+        const int j = a.vcol[sell8(k, t, a.cap_v)];
         if (a.type[j] != kFluid) continue;
         if (!in_radius(dist2_f(qk, a.pos32[j]), a.rl, a.pos, k, j, xk)) continue;
         visc_pair(a, j, xk, uk, ak, orr, ou);

@@ -22,6 +22,15 @@ int cuda_fail(Ctx* c, cudaError_t e, const char* what) {
     return MPS_EDEVICE;
 }
 
+void abort_capture(Ctx* c) {
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(c->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        cudaGraph_t tmp = nullptr;
+        cudaStreamEndCapture(c->stream, &tmp);   // the captured-into graph or null: not used
+    }
+    cudaGetLastError();
+}
+
 namespace {
 
 struct DeviceGuard {

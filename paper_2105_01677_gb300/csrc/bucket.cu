@@ -266,6 +266,7 @@ void state_ptrs_load(Ctx* c, const void* rec) {
 
 int bucket_build(Ctx* c, bool mutate) {
     if (!mutate) return bucket_launches(c, false);
+    if (c->graphs_off) return bucket_launches(c, true);
     BucketGraph* bg = nullptr;
     for (BucketGraph& g : c->bucket_graph)
         if (g.exec && g.pos == c->pos) bg = &g;
@@ -283,6 +284,8 @@ int bucket_build(Ctx* c, bool mutate) {
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (rc || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            c->graphs_off = true;
             load_ptrs(c, before);
             c->launches = l0;
             return rc ? rc : cuda_fail(c, e, "bucket graph capture");

@@ -24,181 +24,223 @@ namespace mps {
 
 namespace {
 
-// One block per occupied cell (taken in turn from a device counter), one thread per
-// particle of the cell.  The particles of the 3^d surrounding cells (contiguous slot ranges
-// in Morton order) are staged in shared memory as (x, y, z, slot) and every thread walks
-// the same staged candidates, four per shared-memory load, so each read is a broadcast.
-// Staging keeps only candidates within the candidate bound of the block's own cell box (no
-// particle of the cell can pair with the others: about a quarter of the 3^d neighbourhood
-// in 3D, mostly in the edge and corner cells).  Each warp filters a contiguous part of the
-// candidate range into its own segment of the staging buffer (ballot compaction, no block
-// barrier), in candidate order, so the lists come out in a fixed order.  One barrier pair
-// per cell, more only when the neighbourhood exceeds a chunk.
-template <int BT, int CHUNK, class Op>
-__global__ void __launch_bounds__(BT)
+// One block per occupied cell (taken in turn from a device counter).  The cell's particles
+// that get a list ("active": no DUMMY or GHOST slots; the dummy layers behind the walls fill
+// many cells) are compacted, up to NA at a time, with their FP32 positions.  The particles of
+// the 3^d surrounding cells (contiguous slot ranges in Morton order) are staged in shared
+// memory as (x, y, z, slot), each warp filtering a contiguous part of the candidate range
+// into its own segment (ballot compaction, candidate order kept); a candidate is kept only
+// within the candidate bound of the bounding box of the compacted actives (taken in the same
+// FP32 coordinates as the tests, so no candidate that any of them accepts is dropped: about
+// a quarter of the 3^d neighbourhood in full cells, more in thin wall layers and at the free
+// surface).  Then the lanes are the candidates: each warp takes pairs of actives in turn and
+// tests 32 staged candidates at a time against both (packed FP32x2 arithmetic); the hits of
+// each, ranked by a ballot, are appended to its list as one run of consecutive entries in
+// candidate order -- with the lists in groups of 8 entries per row (sell8) such a run fills
+// whole 32-byte sectors, where one entry per store would write a sector each.
+template <int NW, int WCAP, class Op>
+__global__ void __launch_bounds__(32 * NW)
     k_gather(Op op, const int32_t* __restrict__ cell_start, const uint32_t* __restrict__ occ,
              const DevStatus* st, GridDesc g) {
-    constexpr int NW = BT / 32;
-    constexpr int WCAP = CHUNK / NW;     // staged entries per warp segment (a multiple of 4)
-    constexpr int WRAW = WCAP - 4;       // raw candidates a warp filters per chunk (room for padding)
-    static_assert(WCAP % 4 == 0 && WRAW > 0, "chunk too small for the block");
-    // staged candidates, structure of arrays: x, y, z relative to the grid origin, slot
-    extern __shared__ __align__(16) float s_buf[];
-    float* s_x = s_buf;
-    float* s_y = s_buf + CHUNK;
-    float* s_z = s_buf + 2 * CHUNK;
-    int* s_j = (int*)(s_buf + 3 * CHUNK);
+    constexpr int NA = 128;              // actives per pass
+    constexpr int WRAW = WCAP - 32;      // raw candidates a warp filters per chunk (room for padding)
+    static_assert(WRAW >= 128 && WCAP % 32 == 0, "staging segment too small");
+    extern __shared__ __align__(16) float4 s_stage[];   // NW segments of WCAP entries
+    __shared__ float4 s_ctr[NA];         // the actives: FP32 position, slot in w
+    __shared__ int s_len[NA];            // their list lengths so far
     __shared__ int s_cs[27], s_pref[28];
-    __shared__ int s_nc;
-    __shared__ int s_cnt[NW];
-    __shared__ float s_box[7];           // the cell box (lo xyz, hi xyz) and the bound
+    __shared__ int s_seg[NW], s_kept[NW];   // each segment's padded and kept lengths
+    __shared__ float s_box[6];
+    __shared__ int s_nact, s_next, s_ncand;
+    __shared__ unsigned s_ci[2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lane_lt = (1u << lane) - 1u;
     const unsigned n_occ = *(volatile const unsigned*)&st->n_occ;
     // an ensemble's keys carry the scene above the cell's Morton code: neighbour cells are
     // looked up under the same prefix, so no gather crosses scenes
     const uint32_t local_mask = (g.dim * g.bits >= 32) ? 0xFFFFFFFFu : ((1u << (g.dim * g.bits)) - 1u);
-    __shared__ unsigned s_ci;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (;;) {
-        __syncthreads();   // s_ci of the previous cell has been read by every thread
-        if (threadIdx.x == 0) s_ci = atomicAdd(&((DevStatus*)st)->gather_next, 1u);
-        __syncthreads();
-        const unsigned ci = s_ci;
+    if (threadIdx.x == 0) s_ci[0] = atomicAdd(&((DevStatus*)st)->gather_next, 1u);
+    unsigned long long tests = 0;   // candidate tests of this block (counted by thread 0)
+    for (int par = 0;; par ^= 1) {
+        __syncthreads();   // the cell index is in place; every thread is done with the previous cell
+        const unsigned ci = s_ci[par];
         if (ci >= n_occ) break;
         const uint32_t code = occ[ci];
         const int c0 = cell_start[code], c1 = cell_start[code + 1];
-        __syncthreads();   // previous cell's staged data and ranges no longer in use
-        if (threadIdx.x == 0) {
+        if (warp == NW - 1) {
+            // the next cell, fetched while this one is worked on
+            if (lane == 0) s_ci[par ^ 1] = atomicAdd(&((DevStatus*)st)->gather_next, 1u);
+            // the 3^d neighbour cells, one per lane in the order (dz, dy, dx) = (-1..1)^d,
+            // their slot ranges loaded at once; a warp scan gives the staging offsets of the
+            // non-empty ones (the same order and offsets as a serial walk over the cells)
             int cc[3];
             const uint32_t prefix = code & ~local_mask;
             morton_decode(code & local_mask, g.dim, g.bits, cc);
-            int m = 0, pref = 0;
-            const int zr = (g.dim == 3) ? 1 : 0;
-            for (int dz = -zr; dz <= zr; dz++)
-                for (int dy = -1; dy <= 1; dy++)
-                    for (int dx = -1; dx <= 1; dx++) {
-                        int nc[3] = {cc[0] + dx, cc[1] + dy, cc[2] + dz};
-                        if (nc[0] < 0 || nc[1] < 0 || nc[2] < 0 || nc[0] >= g.ncell[0] ||
-                            nc[1] >= g.ncell[1] || nc[2] >= g.ncell[2])
-                            continue;
-                        uint32_t k2 = prefix | morton_encode(nc, g.dim, g.bits);
-                        int s0 = cell_start[k2], s1 = cell_start[k2 + 1];
-                        if (s1 > s0) {
-                            s_cs[m] = s0;
-                            s_pref[m] = pref;
-                            pref += s1 - s0;
-                            m++;
-                        }
+            const int ncells_max = (g.dim == 3) ? 27 : 9;
+            int s0 = 0, cnt = 0;
+            if (lane < ncells_max) {
+                const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = (g.dim == 3) ? lane / 9 - 1 : 0;
+                int nc[3] = {cc[0] + dx, cc[1] + dy, cc[2] + dz};
+                const bool inside = nc[0] >= 0 && nc[1] >= 0 && nc[2] >= 0 && nc[0] < g.ncell[0] &&
+                                    nc[1] < g.ncell[1] && nc[2] < g.ncell[2];
+                if (inside) {
+                    const uint32_t k2 = prefix | morton_encode(nc, g.dim, g.bits);
+                    s0 = cell_start[k2];
+                    cnt = cell_start[k2 + 1] - s0;
+                }
+            }
+            const bool nonempty = cnt > 0;
+            const unsigned bal = __ballot_sync(0xffffffffu, nonempty);
+            int incl = cnt;   // inclusive scan of the counts
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            if (nonempty) {
+                const int m = __popc(bal & lane_lt);
+                s_cs[m] = s0;
+                s_pref[m] = incl - cnt;
+            }
+            if (lane == 31) {
+                s_pref[__popc(bal)] = incl;
+                s_ncand = incl;
+            }
+        }
+        const float bound2 = op.block_bound2(c0) * 1.00001f;   // the cell's particles share a scene
+        for (int a0 = c0; a0 < c1;) {
+            if (a0 > c0) __syncthreads();   // the previous pass's actives are no longer read
+            if (warp == 0) {
+                // compact up to NA active slots of [a0, c1), bounding their FP32 positions
+                int nact = 0, a = a0;
+                float lx = INFINITY, ly = INFINITY, lz = INFINITY;
+                float hx = -INFINITY, hy = -INFINITY, hz = -INFINITY;
+                while (a < c1 && nact <= NA - 32) {
+                    const int i = a + lane;
+                    const bool on = i < c1 && op.active(i);
+                    const unsigned bal = __ballot_sync(0xffffffffu, on);
+                    if (on) {
+                        const float4 q = op.pos32[i];
+                        const int k = nact + __popc(bal & lane_lt);
+                        s_ctr[k] = make_float4(q.x, q.y, q.z, __int_as_float(i));
+                        s_len[k] = 0;
+                        lx = fminf(lx, q.x); ly = fminf(ly, q.y); lz = fminf(lz, q.z);
+                        hx = fmaxf(hx, q.x); hy = fmaxf(hy, q.y); hz = fmaxf(hz, q.z);
                     }
-            s_pref[m] = pref;
-            s_nc = m;
-            // the cell box in the FP32 coordinates relative to the grid origin, widened by
-            // several roundings of the largest coordinate (a particle's FP32 position may lie
-            // just outside its binary64 cell)
-            double ext = 0.0;
-            for (int a = 0; a < g.dim; a++) ext = fmax(ext, g.ncell[a] * g.h);
-            const float eps = (float)(ext * 4.8e-7) + 1e-30f;
-            for (int a = 0; a < 3; a++) {
-                const bool used = a < g.dim;
-                s_box[a] = used ? (float)(cc[a] * g.h) - eps : -eps;
-                s_box[3 + a] = used ? (float)((cc[a] + 1) * g.h) + eps : eps;
-            }
-            s_box[6] = op.block_bound2(c0) * 1.00001f;
-        }
-        __syncthreads();
-        const int ncand = s_pref[s_nc];
-        const float4 blo = make_float4(s_box[0], s_box[1], s_box[2], 0.f);
-        const float4 bhi = make_float4(s_box[3], s_box[4], s_box[5], 0.f);
-        const float bound2 = s_box[6];
-        const bool once = ncand <= NW * WRAW;   // whole neighbourhood staged once for the cell
-        // filter raw candidates [base, base + len): warp w takes a contiguous part and
-        // appends the candidates near the cell box to its segment (padded with sentinels at
-        // infinity to a multiple of four, so that the walk needs no tail)
-        auto stage = [&](int base, int len) {
-            const int per = (len + NW - 1) / NW;
-            const int f0 = base + warp * per, f1 = min(base + len, f0 + per);
-            float* sx = s_x + warp * WCAP;
-            float* sy = s_y + warp * WCAP;
-            float* sz = s_z + warp * WCAP;
-            int* sj = s_j + warp * WCAP;
-            int cnt = 0, m = 0;
-            for (int fb = f0; fb < f1; fb += 32) {
-                const int f = fb + lane;
-                bool keep = false;
-                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-                int slot = -1;
-                if (f < f1) {
-                    while (f >= s_pref[m + 1]) m++;
-                    slot = f + s_cs[m] - s_pref[m];
-                    q = op.pos32[slot];
-                    const float dx = fmaxf(fmaxf(blo.x - q.x, q.x - bhi.x), 0.f);
-                    const float dy = fmaxf(fmaxf(blo.y - q.y, q.y - bhi.y), 0.f);
-                    const float dz = fmaxf(fmaxf(blo.z - q.z, q.z - bhi.z), 0.f);
-                    keep = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < bound2;
+                    nact += __popc(bal);
+                    a += 32;
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, keep);
-                if (keep) {
-                    const int k = cnt + __popc(bal & ((1u << lane) - 1u));
-                    sx[k] = q.x;
-                    sy[k] = q.y;
-                    sz[k] = q.z;
-                    sj[k] = slot;
+                for (int o = 16; o > 0; o >>= 1) {
+                    lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+                    ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+                    lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+                    hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+                    hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+                    hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
                 }
-                cnt += __popc(bal);
+                if (lane == 0) {
+                    s_nact = nact;
+                    s_next = a;
+                    s_box[0] = lx; s_box[1] = ly; s_box[2] = lz;
+                    s_box[3] = hx; s_box[4] = hy; s_box[5] = hz;
+                }
             }
-            const int padded = (cnt + 3) & ~3;
-            if (lane < padded - cnt) {
-                sx[cnt + lane] = __int_as_float(0x7f800000);
-                sy[cnt + lane] = 0.f;
-                sz[cnt + lane] = 0.f;
-                sj[cnt + lane] = -1;
-            }
-            if (lane == 0) s_cnt[warp] = padded;
-        };
-        if (once) {
-            stage(0, ncand);
-            __syncthreads();
-        }
-        for (int ib = c0; ib < c1; ib += BT) {
-            const int i = ib + threadIdx.x;
-            const bool act = (i < c1) && op.active(i);
-            const int nact = __syncthreads_count(act);
-            typename Op::Center ctr;
-            op.begin(i, act, ctr);
+            __syncthreads();   // actives, box and neighbourhood are in place
+            const int nact = s_nact, ncand = s_ncand;
+            a0 = s_next;
+            if (nact == 0) continue;   // block-uniform
+            const float lx = s_box[0], ly = s_box[1], lz = s_box[2];
+            const float hx = s_box[3], hy = s_box[4], hz = s_box[5];
             for (int base = 0; base < ncand; base += NW * WRAW) {
-                const int len = min(NW * WRAW, ncand - base);
-                if (!once) {
-                    if (base > 0 || ib > c0) __syncthreads();   // buffer reuse
-                    stage(base, len);
-                    __syncthreads();
-                }
-                if (threadIdx.x == 0 && nact) {
-                    int staged = 0;
-                    for (int w2 = 0; w2 < NW; w2++) staged += s_cnt[w2];
-                    atomicAdd(&((DevStatus*)st)->cand_tests,
-                              (unsigned long long)nact * (unsigned long long)staged);
-                }
-                if (act) {
-                    for (int w2 = 0; w2 < NW; w2++) {
-                        const int mcnt = s_cnt[w2];
-                        const float* sx = s_x + w2 * WCAP;
-                        const float* sy = s_y + w2 * WCAP;
-                        const float* sz = s_z + w2 * WCAP;
-                        const int* sj = s_j + w2 * WCAP;
-                        for (int k = 0; k < mcnt; k += 4) {
-                            const float4 x4 = *(const float4*)&sx[k], y4 = *(const float4*)&sy[k];
-                            const float4 z4 = *(const float4*)&sz[k];
-                            const int4 j4 = *(const int4*)&sj[k];
-                            op.visit2(ctr, i, make_float2(x4.x, x4.y), make_float2(y4.x, y4.y),
-                                      make_float2(z4.x, z4.y), make_int2(j4.x, j4.y));
-                            op.visit2(ctr, i, make_float2(x4.z, x4.w), make_float2(y4.z, y4.w),
-                                      make_float2(z4.z, z4.w), make_int2(j4.z, j4.w));
+                if (base > 0) __syncthreads();   // the previous chunk has been walked
+                {
+                    // warp w filters the raw candidates [f0, f1) into its segment, four per
+                    // lane in flight
+                    const int len = min(NW * WRAW, ncand - base);
+                    const int per = (len + NW - 1) / NW;
+                    const int f0 = base + warp * per, f1 = min(base + len, f0 + per);
+                    float4* seg = s_stage + warp * WCAP;
+                    int cnt = 0, m = 0;
+                    for (int gb = f0; gb < f1; gb += 128) {
+                        float4 q[4];
+                        int slot[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int f = gb + 32 * u + lane;
+                            slot[u] = -1;
+                            if (f < f1) {
+                                while (f >= s_pref[m + 1]) m++;
+                                slot[u] = f + s_cs[m] - s_pref[m];
+                                q[u] = op.pos32[slot[u]];
+                            }
                         }
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            bool keep = false;
+                            if (slot[u] >= 0) {
+                                const float dx = fmaxf(fmaxf(lx - q[u].x, q[u].x - hx), 0.f);
+                                const float dy = fmaxf(fmaxf(ly - q[u].y, q[u].y - hy), 0.f);
+                                const float dz = fmaxf(fmaxf(lz - q[u].z, q[u].z - hz), 0.f);
+                                keep = fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < bound2;
+                            }
+                            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                            if (keep)
+                                seg[cnt + __popc(bal & lane_lt)] =
+                                    make_float4(q[u].x, q[u].y, q[u].z, __int_as_float(slot[u]));
+                            cnt += __popc(bal);
+                        }
+                    }
+                    // padded with sentinels at infinity (no hits) to a multiple of 32 lanes
+                    const int padded = (cnt + 31) & ~31;
+                    if (cnt + lane < padded)
+                        seg[cnt + lane] = make_float4(INFINITY, 0.f, 0.f, __int_as_float(-1));
+                    if (lane == 0) {
+                        s_seg[warp] = padded;
+                        s_kept[warp] = cnt;
+                    }
+                }
+                __syncthreads();   // the chunk is staged
+                if (threadIdx.x == 0) {
+                    int kept = 0;
+                    for (int w2 = 0; w2 < NW; w2++) kept += s_kept[w2];
+                    tests += (unsigned long long)nact * (unsigned long long)kept;
+                }
+                // warp w takes the pairs (p, p + 1), p = 2 w, 2 w + 2 NW, ...
+                for (int p = 2 * warp; p < nact; p += 2 * NW) {
+                    const bool two = p + 1 < nact;
+                    const typename Op::Center ca = op.center(s_ctr[p], true);
+                    const typename Op::Center cb = op.center(s_ctr[two ? p + 1 : p], two);
+                    int la = s_len[p], lb = two ? s_len[p + 1] : 0;
+                    for (int w2 = 0; w2 < NW; w2++) {
+                        const float4* seg = s_stage + w2 * WCAP;
+                        const int padded = s_seg[w2];
+#pragma unroll 2
+                        for (int gk = 0; gk < padded; gk += 32) {
+                            const float4 qc = seg[gk + lane];
+                            const int j = __float_as_int(qc.w);
+                            bool ha, hb;
+                            op.test2(ca, cb, qc, j, ha, hb);
+                            const unsigned ma = __ballot_sync(0xffffffffu, ha);
+                            const unsigned mb = __ballot_sync(0xffffffffu, hb);
+                            if (ma | mb) {   // warp-uniform: most groups miss one center or both
+                                if (ha) op.put(ca, la + __popc(ma & lane_lt), j);
+                                if (hb) op.put(cb, lb + __popc(mb & lane_lt), j);
+                                la += __popc(ma);
+                                lb += __popc(mb);
+                            }
+                        }
+                    }
+                    if (lane == 0) {
+                        s_len[p] = la;
+                        if (two) s_len[p + 1] = lb;
                     }
                 }
             }
-            op.finish(i, act, ctr);
+            __syncthreads();   // the lengths are final
+            for (int k = threadIdx.x; k < nact; k += 32 * NW)
+                op.finish(__float_as_int(s_ctr[k].w), s_len[k]);
         }
     }
+    if (threadIdx.x == 0 && tests) atomicAdd(&((DevStatus*)st)->cand_tests, tests);
 }
 
 __device__ __forceinline__ float dist2_f(const float4& a, const float4& b) {
@@ -211,7 +253,7 @@ __device__ __forceinline__ int kind_of(const float4& q) { return __float_as_int(
 // ------------------------------------------------------------------------------ Verlet
 // Candidate list of every FLUID and WALL particle: all j != i with FP32 squared distance
 // below the candidate radius h^2 plus its rounding margin (a superset of the exact set
-// within h), written as SELL-32 rows.
+// within h), written as sell8 rows in candidate order.
 struct VerletOp {
     const float4* pos32;
     const int8_t* type;
@@ -226,10 +268,10 @@ struct VerletOp {
     int dummies;                // also give DUMMY particles a list (the reverse step)
 
     struct Center {
-        float4 p32;
-        float hv2;      // the candidate bound of the particle's scene
-        int cnt;
-        int32_t* row;   // entry k of this row at row[32 k] (SELL-32)
+        float px, py, pz;
+        float hv2;      // the candidate bound of the particle's scene (negative: no hits)
+        int i;
+        size_t row;     // sell8 offset of the row's first entry
     };
     // DUMMY particles only ever appear as neighbours: they get no candidate list (unless
     // the reverse step asks for one: their positions enter the number densities)
@@ -237,38 +279,34 @@ struct VerletOp {
         const int t = type[i];
         return t == kFluid || t == kWall || (dummies && t == kDummy);
     }
-    __device__ void begin(int i, bool act, Center& c) const {
-        c.cnt = 0;
-        c.row = vcol + sell(i, 0, cap_v);
-        c.hv2 = hv2_dev ? *hv2_dev : hv2;
-        if (act) {
-            c.p32 = pos32[i];
-            if (sid) c.hv2 = scn[sid[i]].rv.hi;
-        }
+    __device__ Center center(const float4& c, bool act) const {
+        Center r;
+        r.px = c.x;
+        r.py = c.y;
+        r.pz = c.z;
+        r.i = __float_as_int(c.w);
+        r.row = sell8(r.i, 0, cap_v);
+        r.hv2 = !act ? -1.f : sid ? scn[sid[r.i]].rv.hi : (hv2_dev ? *hv2_dev : hv2);
+        return r;
     }
-    // Branch-free append: a predicated store into the row's next slot.  Past the cap every
-    // hit rewrites the last slot (the row is then reported as overflowed by finish()).
-    __device__ __forceinline__ void push(Center& c, bool hit, int j) const {
-        int32_t* dst = c.row + (size_t)min(c.cnt, cap_v - 1) * 32;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p st.global.u32 [%0], %1;\n\t}"
-            :: "l"(dst), "r"(j), "r"((unsigned)hit));
-        c.cnt += hit ? 1 : 0;
-    }
-    // two candidates with packed FP32x2 arithmetic (each lane of the pair rounds like the
-    // scalar dx*dx + dy*dy + dz*dz with fused multiply-adds)
-    __device__ __forceinline__ void visit2(Center& c, int i, float2 x, float2 y, float2 z, int2 j) const {
-        const float2 dx = __fadd2_rn(x, make_float2(-c.p32.x, -c.p32.x));
-        const float2 dy = __fadd2_rn(y, make_float2(-c.p32.y, -c.p32.y));
-        const float2 dz = __fadd2_rn(z, make_float2(-c.p32.z, -c.p32.z));
+    // one candidate against two centers with packed FP32x2 arithmetic (each half rounds like
+    // the scalar dx*dx + dy*dy + dz*dz with fused multiply-adds, dx = x_j - x_i)
+    __device__ __forceinline__ void test2(const Center& a, const Center& b, const float4& q, int j,
+                                          bool& ha, bool& hb) const {
+        const float2 dx = __fadd2_rn(make_float2(q.x, q.x), make_float2(-a.px, -b.px));
+        const float2 dy = __fadd2_rn(make_float2(q.y, q.y), make_float2(-a.py, -b.py));
+        const float2 dz = __fadd2_rn(make_float2(q.z, q.z), make_float2(-a.pz, -b.pz));
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
-        push(c, r2.x < c.hv2 && j.x != i, j.x);
-        push(c, r2.y < c.hv2 && j.y != i, j.y);
+        ha = r2.x < a.hv2 && j != a.i;
+        hb = r2.y < b.hv2 && j != b.i;
     }
-    __device__ void finish(int i, bool act, const Center& c) const {
-        if (!act) return;
-        vcnt[i] = min(c.cnt, cap_v);
-        if (c.cnt > cap_v) atomicOr(&st->err, kErrCap);
+    // entry k of the row (past the cap the row is reported as overflowed by finish())
+    __device__ __forceinline__ void put(const Center& c, int k, int j) const {
+        if (k < cap_v) vcol[c.row + (size_t)((k & ~7) * 32 + (k & 7))] = j;
+    }
+    __device__ void finish(int i, int len) const {
+        vcnt[i] = min(len, cap_v);
+        if (len > cap_v) atomicOr(&st->err, kErrCap);
     }
     // the candidate bound of the cell's particles (all of one scene), for the staging filter
     __device__ float block_bound2(int i) const {
@@ -278,6 +316,8 @@ struct VerletOp {
 };
 
 // ------------------------------------------------------------------------------ debug
+// exact neighbour sets at r^k (the FP32 band decided in binary64), as global ids in
+// candidate order
 struct NbrOp {
     const float4* pos32;
     const double4* pos;
@@ -290,27 +330,32 @@ struct NbrOp {
     struct Center {
         double4 p;
         float4 p32;
-        int cnt;
+        int i;
+        bool act;
     };
     __device__ bool active(int i) const { return type[i] != kGhost; }
-    __device__ void begin(int i, bool act, Center& c) const {
-        c.cnt = 0;
-        if (!act) return;
-        c.p = pos[i];
-        c.p32 = pos32[i];
+    __device__ Center center(const float4& c, bool act) const {
+        Center r_;
+        r_.i = __float_as_int(c.w);
+        r_.act = act;
+        r_.p32 = make_float4(c.x, c.y, c.z, 0.f);
+        r_.p = pos[r_.i];
+        return r_;
     }
-    __device__ void visit(Center& c, int i, int j, const float4& q) const {
-        if (j == i) return;
-        if (!in_radius(dist2_f(c.p32, q), r, pos, i, j, c.p)) return;
-        if (row_off) out_ids[row_off[i] + c.cnt] = id[j];
-        c.cnt++;
+    __device__ bool test(const Center& c, const float4& q, int j) const {
+        if (!c.act || j < 0 || j == c.i) return false;
+        return in_radius(dist2_f(c.p32, q), r, pos, c.i, j, c.p);
     }
-    __device__ void visit2(Center& c, int i, float2 x, float2 y, float2 z, int2 j) const {
-        if (j.x >= 0) visit(c, i, j.x, make_float4(x.x, y.x, z.x, 0.f));
-        if (j.y >= 0) visit(c, i, j.y, make_float4(x.y, y.y, z.y, 0.f));
+    __device__ void test2(const Center& a, const Center& b, const float4& q, int j, bool& ha,
+                          bool& hb) const {
+        ha = test(a, q, j);
+        hb = test(b, q, j);
     }
-    __device__ void finish(int i, bool act, const Center& c) const {
-        if (act && !row_off) out_cnt[i] = c.cnt;
+    __device__ void put(const Center& c, int k, int j) const {
+        if (row_off) out_ids[row_off[c.i] + k] = id[j];
+    }
+    __device__ void finish(int i, int len) const {
+        if (!row_off) out_cnt[i] = len;
     }
     __device__ float block_bound2(int) const { return r.hi; }
 };
@@ -326,27 +371,29 @@ __global__ void k_copy_star(int n, const double4* pos, const double4* vel, const
     p32los[i] = pos32lo[i];
 }
 
-template <int BT, class Op>
-void launch_gather_bt(Ctx* c, const Op& op, int blocks_per_sm) {
-    // staged candidates per chunk: 512, split evenly over the block's warps (528 for three)
-    constexpr int kChunk = (BT == 96) ? 528 : 512;
+template <int NW, class Op>
+void launch_gather_nw(Ctx* c, const Op& op, int blocks_per_sm) {
+    // each warp stages up to 480 candidates per chunk in its 512-entry segment (8 KB)
+    constexpr int kWCAP = 512;
+    static_assert(NW * kWCAP * sizeof(float4) <= 48 * 1024, "within the default dynamic shared memory");
     // blocks take occupied cells from a counter: cells differ a lot in work (full fluid
     // cells against sparse wall or surface cells), so a static split leaves SMs idle
     cudaMemsetAsync(&c->st->gather_next, 0, sizeof(unsigned int), c->stream);
-    k_gather<BT, kChunk, Op><<<c->sms * blocks_per_sm, BT, kChunk * 4 * sizeof(float), c->stream>>>(
+    k_gather<NW, kWCAP, Op><<<c->sms * blocks_per_sm, 32 * NW, NW * kWCAP * sizeof(float4), c->stream>>>(
         op, c->cell_start, c->occ, c->st, c->grid);
 }
 
+// params.gather_block: threads per cell block (1 to 4 warps)
 template <class Op>
 void launch_gather(Ctx* c, const Op& op) {
     c->launches += 1;
     int bt = c->prm.gather_block;
-    if (bt == 0) bt = (c->dim == 3) ? 128 : 32;   // measured best on the 3D dam break
+    if (bt == 0) bt = (c->dim == 3) ? 128 : 64;
     switch (bt) {
-        case 32: launch_gather_bt<32>(c, op, 24); break;
-        case 64: launch_gather_bt<64>(c, op, 20); break;
-        case 128: launch_gather_bt<128>(c, op, 12); break;
-        default: launch_gather_bt<96>(c, op, 16); break;
+        case 32: launch_gather_nw<1>(c, op, 24); break;
+        case 64: launch_gather_nw<2>(c, op, 14); break;
+        case 96: launch_gather_nw<3>(c, op, 10); break;
+        default: launch_gather_nw<4>(c, op, 8); break;
     }
 }
 

@@ -6,15 +6,17 @@
 //   type            int8, id int32 (caller's particle id of slot s)
 //   pos_star/vel_star double4, pos32_star float4   predicted r*, u* of the step
 //   pos32lo         float4 low parts: x - xmin = pos32.x + pos32lo.x to ~48 bits (float-float)
-//   vl              SELL-32 rows of `cap_v` int32 slots: candidates within h at r^k (superset)
+//   vl              sell8 rows of `cap_v` int32 slots: candidates within h at r^k (superset)
 //   vel32           float4 velocities (mixed-precision viscosity terms)
-//   nb_lap          SELL-32 rows of `cap` int32 slots: non-dummy neighbours within re_lap at
+//   nb_lap          sell8 rows of `cap` int32 slots: non-dummy neighbours within re_lap at
 //                   r*, with the PPE coefficients c_ij: binary64 (v64, FP64 mode) or
 //                   float-float hi/lo (v32/vlo, mixed mode; v32 is the FP32 coefficient)
-//   nb_n            SELL-32 rows of `cap_n` int32 slots: non-dummy neighbours within re_n at r*
-//   SELL-32: the rows of 32 consecutive slots form a slice; entry k of row i sits at
-//   ((i / 32) cap + k) 32 + i % 32, so a warp (one row per lane) reads entry k of its 32
-//   rows in one coalesced 128-byte access.
+//   nb_n            sell8 rows of `cap_n` int32 slots: non-dummy neighbours within re_n at r*
+//   sell8: the rows of 32 consecutive slots form a slice, and a row's entries come in groups
+//   of 8 (one 32-byte sector): entry k of row i sits at ((i / 32) cap + 8 (k / 8)) 32 +
+//   8 (i % 32) + k % 8, so the 32 rows' group g is 1 KB contiguous, a row's run of
+//   consecutive entries fills whole sectors, and a warp (one row per lane) reads a group of
+//   its 32 rows with two 16-byte loads per lane.
 //   cell_start      int32[2^(dim*bits) + 1], indexed by Morton code: exclusive scan of
 //                   per-cell counts, so cell m holds slots [cell_start[m], cell_start[m+1])
 #pragma once
@@ -132,15 +134,11 @@ __device__ __forceinline__ double cubic_w_d(double r2, double rs, double inv_re)
     return t * t * t;
 }
 
-// slot of entry k of row i in a SELL-32 array with `cap` entries per row
-__host__ __device__ __forceinline__ size_t sell(int i, int k, int cap) {
-    return ((size_t)(i >> 5) * (size_t)cap + (size_t)k) * 32 + (size_t)(i & 31);
-}
-// The PPE and gradient rows (the build's outputs) in slices of 32 rows whose entries come in
-// groups of 8 per row: entry k of row i at slice (i / 32), group (k / 8), row (i % 32),
-// position (k % 8).  A row's group is one 32-byte sector, written whole by its thread and
-// read with two 16-byte loads; the 32 rows' group g is 1 KB contiguous.  cap is a multiple
-// of 8.
+// The candidate lists and the PPE and gradient rows, in slices of 32 rows whose entries come
+// in groups of 8 per row: entry k of row i at slice (i / 32), group (k / 8), row (i % 32),
+// position (k % 8).  A row's group is one 32-byte sector (written whole by the build's
+// thread, or as a run of consecutive entries by the gather's warp) and is read with two
+// 16-byte loads; the 32 rows' group g is 1 KB contiguous.  cap is a multiple of 8.
 __host__ __device__ __forceinline__ size_t sell8(int i, int k, int cap) {
     return ((size_t)(i >> 5) * (size_t)cap + (size_t)(k & ~7)) * 32 + (size_t)(i & 31) * 8 +
            (size_t)(k & 7);
@@ -156,6 +154,8 @@ struct Ctx;
 // ---------------------------------------------------------------- bucket.cu
 int bucket_build(Ctx* c, bool mutate);            // keys, sort, cell table, permute
 void bucket_graphs_destroy(Ctx* c);
+// end a stream capture left open by a failed capture (its result is discarded)
+void abort_capture(Ctx* c);
 void launch_cell_keys_only(Ctx* c, uint32_t* out_key);
 
 // ---------------------------------------------------------------- scan.cu
@@ -351,6 +351,10 @@ int launch_fast_patch(Ctx* c, int n_fast, float hv2);
     // runs launch by launch (a step graph hands such a step to the host-driven path)
     int32_t* fast_idx = nullptr;
     bool force_host = false;
+    // a graph capture failed (a launch refused inside it): every later step runs launch by
+    // launch, and the graph of the failed capture is left alone (not destroyed: the runtime
+    // may have dropped the body it was capturing into)
+    bool graphs_off = false;
 
     // state (sorted order) and double buffers
     double4 *pos, *vel, *pos_alt, *vel_alt;

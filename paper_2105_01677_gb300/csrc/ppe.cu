@@ -1,7 +1,7 @@
 // ppe.cu -- conjugate-gradient solve of the PPE A p = b (Eq. 13 assembled as in the CUDA
 // PPE listing (Listing 2) of Sec. 4.3; the paper solves it by (IC)CG, Sec. 3.1.2 and Sec. 4.3).
 //
-// A is applied from the per-step neighbour lists built at r* (SELL-32 rows, one thread per
+// A is applied from the per-step neighbour lists built at r* (sell8 rows, one thread per
 // row; the allocation-free entry point below takes caller rows in plain row-major layout):
 //   (A x)_i = diag_i x_i - sum_{j in nb_lap(i)} c_ij x_j   for rows of the PPE (diag_i > 0),
 //   (A x)_i = 0 elsewhere,
@@ -225,9 +225,9 @@ __global__ void __launch_bounds__(kBT) k_d32(int n, const float* r, float* d, Cg
     for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) d[i] = fmaf(beta, d[i], r[i]);
 }
 
-// ------------------------------------------------------------------ thread-per-row (SELL-32)
-// The step's PPE rows are SELL-32: each thread owns a row, a warp reads entry k of 32 rows
-// with one coalesced access, and every FP64 operation runs with all lanes busy.
+// ------------------------------------------------------------------ thread-per-row (sell8)
+// The step's PPE rows are sell8: each thread owns a row, a warp reads a group of 8 entries
+// of its 32 rows as 1 KB contiguous, and every FP64 operation runs with all lanes busy.
 struct SellView {
     int n, cap;
     const int32_t* col;
@@ -965,7 +965,10 @@ static int build_mixed_graph(Ctx* c, double* x, PpeGraph* pg) {
     pg->graph = G;
     cudaGraphNode_t last = nullptr;
     int rc = add_mixed_solve(c, G, nullptr, x, pg->guess, &last);
-    if (rc) return rc;
+    if (rc) {
+        abort_capture(c);
+        return rc;
+    }
     MPS_CUDA(c, cudaGraphInstantiate(&pg->exec, G, 0));
     pg->x = x;
     return MPS_OK;
@@ -994,8 +997,8 @@ static int mixed_graph_solve(Ctx* c, double* x, mps_report* rep, int max_total) 
         pg->guess = x0 != nullptr;
         int rc = build_mixed_graph(c, x, pg);
         if (rc) {
-            if (pg->graph) cudaGraphDestroy(pg->graph);
-            *pg = PpeGraph{};
+            *pg = PpeGraph{};   // the graph of the failed capture is left alone
+            c->graphs_off = true;
             return rc;
         }
     }
@@ -1109,7 +1112,7 @@ static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool prima
     const int max_total = c->prm.cg_max_iter > 0 ? c->prm.cg_max_iter : (int)std::min<int64_t>(10 * c->n, 1 << 30);
     const int gs = row_grid(c), gv = vec_grid(c);
     int rc;
-    if (primary && c->prm.precision == 1 && c->prm.ppe_host_loop == 0)
+    if (primary && c->prm.precision == 1 && c->prm.ppe_host_loop == 0 && !c->graphs_off)
         return mixed_graph_solve(c, x, rep, max_total);
     if ((rc = set_cg_limits(c, max_total))) return rc;
     // the step's own solve may start from the previous solution (cg_x0 = 1)

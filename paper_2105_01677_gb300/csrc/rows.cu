@@ -1,6 +1,6 @@
 // rows.cu -- per-particle pair sums over the step's candidate (Verlet) lists, one thread per
-// particle.  Lists are SELL-32, so a warp reads entry k of its 32 rows in one access, and
-// every per-particle FP64 operation (the state update, the PPE row) runs with all lanes of
+// particle.  Lists are sell8 (a row's entries in 32-byte groups, the 32 rows of a warp's
+// slice side by side), and every per-particle FP64 operation (the state update, the PPE row) runs with all lanes of
 // the warp busy: on GB300 an FP64 warp instruction costs the FP64 pipe ~64 cycles whatever
 // the number of active lanes.
 //
@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
         // FP32 terms in compensated (Kahan) FP32 sums: value f, running correction e
         float f0 = 0.f, f1 = 0.f, f2 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f;
         // two-stage software pipeline: the slot of k+2 and the position of k+1 are in flight
-        int jn = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : 0;
-        int j0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
+        int jn = cnt > 1 ? a.vcol[sell8(i, 1, a.cap_v)] : 0;
+        int j0 = cnt > 0 ? a.vcol[sell8(i, 0, a.cap_v)] : 0;
         float4 qn = a.pos32[j0];
         // mixed: the FP32 velocity of k+1 is in flight with its position (nearly every
         // candidate is a member)
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
                 qn = a.pos32[jn];
                 if (MIXED) vn = a.vel32[jn];
             }
-            if (k + 2 < cnt) jn = a.vcol[sell(i, k + 2, a.cap_v)];
+            if (k + 2 < cnt) jn = a.vcol[sell8(i, k + 2, a.cap_v)];
             const float r2 = dist2_f(ih, jh);
             int t = tier1(r2, R);
             if (t == 2)
@@ -366,15 +366,15 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
         int pend[kPend];
         int np = 0;
         // ---- classification
-        int jn = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : 0;
-        int j0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
+        int jn = cnt > 1 ? a.vcol[sell8(i, 1, a.cap_v)] : 0;
+        int j0 = cnt > 0 ? a.vcol[sell8(i, 0, a.cap_v)] : 0;
         float4 qn = a.pos32[j0];
         for (int k = 0; k < cnt; k++) {
             const int j = j0;
             const float4 jh = qn;
             j0 = jn;
             if (k + 1 < cnt) qn = a.pos32[jn];
-            if (k + 2 < cnt) jn = a.vcol[sell(i, k + 2, a.cap_v)];
+            if (k + 2 < cnt) jn = a.vcol[sell8(i, k + 2, a.cap_v)];
             const float r2 = dist2_f(ih, jh);
             const bool nb_ok = kind_of(jh) != kDummy;
             int tl = (nb_ok && with_ppe) ? tier1(r2, rl) : 0;
@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
             append(j, tl, tn, nb_ok);
         }
         for (int q = 0; q < np; q++) {
-            const int j = a.vcol[sell(i, pend[q], a.cap_v)];
+            const int j = a.vcol[sell8(i, pend[q], a.cap_v)];
             const float4 jh = a.pos32[j];
             const float r2 = dist2_f(ih, jh);
             const bool nb_ok = kind_of(jh) != kDummy;
@@ -528,14 +528,14 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                 // outside the ff_tol band around re^2, binary64 inside it) and the members' terms
                 // are evaluated at once, in candidate order.  The slots of the next pair are
                 // loaded one iteration ahead.
-                int s0 = cnt > 0 ? a.vcol[sell(i, 0, a.cap_v)] : 0;
-                int s1 = cnt > 1 ? a.vcol[sell(i, 1, a.cap_v)] : s0;
+                int s0 = cnt > 0 ? a.vcol[sell8(i, 0, a.cap_v)] : 0;
+                int s1 = cnt > 1 ? a.vcol[sell8(i, 1, a.cap_v)] : s0;
                 for (int t = 0; t < cnt; t += 2) {
                     const bool two = t + 1 < cnt;
                     const int j0 = s0, j1 = s1;
                     if (t + 2 < cnt) {
-                        s0 = a.vcol[sell(i, t + 2, a.cap_v)];
-                        s1 = t + 3 < cnt ? a.vcol[sell(i, t + 3, a.cap_v)] : s0;
+                        s0 = a.vcol[sell8(i, t + 2, a.cap_v)];
+                        s1 = t + 3 < cnt ? a.vcol[sell8(i, t + 3, a.cap_v)] : s0;
                     }
                     const float4 h0 = a.pos32[j0], l0 = a.pos32lo[j0];
                     const float4 h1 = a.pos32[j1], l1 = a.pos32lo[j1];
@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(kBT) k_ecs_rates(RatesArgs a) {
     ff nf = {0.f, 0.f};
     double nd = 0.0, dd = 0.0;
     for (int k = 0; k < cnt; k++) {
-        const int j = a.vcol[sell(i, k, a.cap_v)];
+        const int j = a.vcol[sell8(i, k, a.cap_v)];
         const float4 jh = a.pos32[j];
         const float r2 = dist2_f(ih, jh);
         int t = tier1(r2, rn);

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kBT) k_fast_mark(int n, const int32_t* rows, c
 
 __device__ __forceinline__ bool in_list(const int32_t* vcol, int row, int cnt, int cap_v, int j) {
     for (int k = 0; k < cnt; k++)
-        if (vcol[sell(row, k, cap_v)] == j) return true;
+        if (vcol[sell8(row, k, cap_v)] == j) return true;
     return false;
 }
 
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kBT) k_fast_patch(int n, const int32_t* fast, 
         // i's own list (only this block writes it)
         if (!in_list(vcol, i, cnt_i, cap_v, j)) {
             const int s = atomicAdd(&vcnt[i], 1);
-            if (s < cap_v) vcol[sell(i, s, cap_v)] = j;
+            if (s < cap_v) vcol[sell8(i, s, cap_v)] = j;
             else atomicOr(&st->err, kErrCap);
         }
         // j's list, unless j is fast itself (its own block enters i) or has no list
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kBT) k_fast_patch(int n, const int32_t* fast, 
         const int cnt_j = min(cnt0[j], cap_v);
         if (!in_list(vcol, j, cnt_j, cap_v, i)) {
             const int s = atomicAdd(&vcnt[j], 1);
-            if (s < cap_v) vcol[sell(j, s, cap_v)] = i;
+            if (s < cap_v) vcol[sell8(j, s, cap_v)] = i;
             else atomicOr(&st->err, kErrCap);
         }
     }

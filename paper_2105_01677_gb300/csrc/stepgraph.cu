@@ -258,11 +258,7 @@ int build_step_graph(Ctx* c, StepGraph* sg) {
     int rc = capture_step(c, sg, G);
     c->capture_ctl = nullptr;
     if (rc) {
-        cudaStreamCaptureStatus cs;
-        cudaGraph_t tmp = nullptr;
-        if (cudaStreamIsCapturing(c->stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
-            cudaStreamEndCapture(c->stream, &tmp);   // tmp is G itself: freed by the caller
-        cudaGetLastError();
+        abort_capture(c);
     } else {
         state_ptrs_save(c, sg->after);   // the assignment a replay leaves behind
     }
@@ -276,6 +272,7 @@ int build_step_graph(Ctx* c, StepGraph* sg) {
 bool step_graph_eligible(const Ctx* c, bool advance) {
     const mps_params& P = c->prm;
     return P.step_graph != 0 && advance && !c->vjp && !c->profiling && !c->force_host &&
+           !c->graphs_off &&
            P.list_every <= 1 &&
            (P.pressure_mode == 1 || (P.precision == 1 && P.ppe_host_loop == 0));
 }
@@ -304,8 +301,8 @@ int step_graph_step(Ctx* c, mps_report* rep) {
         const double4* start = c->pos;
         rc = build_step_graph(c, sg);
         if (rc) {
-            if (sg->graph) cudaGraphDestroy(sg->graph);
-            *sg = StepGraph{};
+            *sg = StepGraph{};   // the graph of the failed capture is left alone
+            c->graphs_off = true;
             return rc;
         }
         sg->pos = start;
