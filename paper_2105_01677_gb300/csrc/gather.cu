@@ -204,34 +204,43 @@ __global__ void __launch_bounds__(32 * NW)
                     for (int w2 = 0; w2 < NW; w2++) kept += s_kept[w2];
                     tests += (unsigned long long)nact * (unsigned long long)kept;
                 }
-                // warp w takes the pairs (p, p + 1), p = 2 w, 2 w + 2 NW, ...
-                for (int p = 2 * warp; p < nact; p += 2 * NW) {
-                    const bool two = p + 1 < nact;
-                    const typename Op::Center ca = op.center(s_ctr[p], true);
-                    const typename Op::Center cb = op.center(s_ctr[two ? p + 1 : p], two);
-                    int la = s_len[p], lb = two ? s_len[p + 1] : 0;
+                // warp w takes the actives p .. p + 3, p = 4 w, 4 w + 4 NW, ...: one staged
+                // candidate per lane, tested against two pairs of them
+                for (int p = 4 * warp; p < nact; p += 4 * NW) {
+                    typename Op::Center cn[4];
+                    int ln[4];
+#pragma unroll
+                    for (int t = 0; t < 4; t++) {
+                        const bool on = p + t < nact;
+                        cn[t] = op.center(s_ctr[on ? p + t : p], on);
+                        ln[t] = on ? s_len[p + t] : 0;
+                    }
                     for (int w2 = 0; w2 < NW; w2++) {
                         const float4* seg = s_stage + w2 * WCAP;
                         const int padded = s_seg[w2];
-#pragma unroll 2
                         for (int gk = 0; gk < padded; gk += 32) {
                             const float4 qc = seg[gk + lane];
                             const int j = __float_as_int(qc.w);
-                            bool ha, hb;
-                            op.test2(ca, cb, qc, j, ha, hb);
-                            const unsigned ma = __ballot_sync(0xffffffffu, ha);
-                            const unsigned mb = __ballot_sync(0xffffffffu, hb);
-                            if (ma | mb) {   // warp-uniform: most groups miss one center or both
-                                if (ha) op.put(ca, la + __popc(ma & lane_lt), j);
-                                if (hb) op.put(cb, lb + __popc(mb & lane_lt), j);
-                                la += __popc(ma);
-                                lb += __popc(mb);
+                            bool hit[4];
+                            op.test2(cn[0], cn[1], qc, j, hit[0], hit[1]);
+                            op.test2(cn[2], cn[3], qc, j, hit[2], hit[3]);
+#pragma unroll
+                            for (int t = 0; t < 4; t++) {
+                                const unsigned mt = __ballot_sync(0xffffffffu, hit[t]);
+                                if (mt) {   // warp-uniform: a center misses most groups
+                                    if (hit[t]) op.put(cn[t], ln[t] + __popc(mt & lane_lt), j);
+                                    ln[t] += __popc(mt);
+                                }
                             }
                         }
                     }
-                    if (lane == 0) {
-                        s_len[p] = la;
-                        if (two) s_len[p + 1] = lb;
+                    if (lane < 4 && p + lane < nact) {
+                        // lane t stores center t's length (registers indexed by a constant)
+                        int lv = ln[0];
+                        if (lane == 1) lv = ln[1];
+                        if (lane == 2) lv = ln[2];
+                        if (lane == 3) lv = ln[3];
+                        s_len[p + lane] = lv;
                     }
                 }
             }
