@@ -341,7 +341,7 @@ int allocate(Ctx* c) {
                  sn = sell_size(c->n, c->cap_n);
     A(pos, n) A(vel, n) A(pos_alt, n) A(vel_alt, n) A(type, n) A(type_alt, n) A(id, n) A(id_alt, n)
     A(p, n) A(p_alt, n) A(pos32, n) A(pos32lo, n) A(pos_star, n) A(vel_star, n) A(pos32_star, n)
-    A(pos32lo_star, n) A(nstar, n) A(flag, n) A(bvec, n) A(diag, n) A(diag32, n) A(phat, n)
+    A(pff_star, 2 * n) A(nstar, n) A(flag, n) A(bvec, n) A(diag, n) A(diag32, n) A(phat, n)
     A(vl_col, sv) A(vl_cnt, n) A(vel32, n)
     // nb_lap_col also stages the number-density entries of a row while it is assembled
     A(nb_n_col, sn) A(nb_n_cnt, n) A(nb_lap_cnt, n) A(nb_lap_col, sl)

@@ -371,13 +371,15 @@ struct NbrOp {
 
 __global__ void k_copy_star(int n, const double4* pos, const double4* vel, const float4* pos32,
                             const float4* pos32lo, double4* ps, double4* vs, float4* p32s,
-                            float4* p32los) {
+                            float4* pff) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     ps[i] = pos[i];
     vs[i] = vel[i];
-    p32s[i] = pos32[i];
-    p32los[i] = pos32lo[i];
+    const float4 h = pos32[i];
+    p32s[i] = h;
+    pff[2 * i] = h;
+    pff[2 * i + 1] = pos32lo[i];
 }
 
 template <int NW, class Op>
@@ -412,7 +414,7 @@ void launch_copy_state_star(Ctx* c) {
     int n = (int)c->n;
     k_copy_star<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->pos, c->vel, c->pos32, c->pos32lo,
                                                          c->pos_star, c->vel_star, c->pos32_star,
-                                                         c->pos32lo_star);
+                                                         c->pff_star);
     c->launches += 1;
 }
 

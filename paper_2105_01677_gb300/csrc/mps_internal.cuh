@@ -5,6 +5,8 @@
 //   pos32           float4 (x-xmin, y-ymin, z-zmin, kind bits)   FP32 copy for filtering
 //   type            int8, id int32 (caller's particle id of slot s)
 //   pos_star/vel_star double4, pos32_star float4   predicted r*, u* of the step
+//   pff_star        float4[2n]: r* as float-float, slot i's hi at 2 i and lo at 2 i + 1 (one
+//                   32-byte sector per particle for the build's gathers)
 //   pos32lo         float4 low parts: x - xmin = pos32.x + pos32lo.x to ~48 bits (float-float)
 //   vl              sell8 rows of `cap_v` int32 slots: candidates within h at r^k (superset)
 //   vel32           float4 velocities (mixed-precision viscosity terms)
@@ -370,7 +372,7 @@ int launch_fast_patch(Ctx* c, int n_fast, float hv2);
     float4 *pos32, *pos32lo;
     // step buffers
     double4 *pos_star, *vel_star;
-    float4 *pos32_star, *pos32lo_star;
+    float4 *pos32_star, *pff_star;   // r* in FP32, and as (hi, lo) pairs (slot i at 2 i, 2 i + 1)
     float4* vel32;
     double* nstar;
     uint8_t* flag;

@@ -35,8 +35,10 @@ namespace mps {
 namespace {
 constexpr int kBT = 128;
 // the build's blocks: 256 rows of neighbouring particles share more of their candidates in
-// L1 (5% faster than 128 on the 3D dam break; the prediction is faster at 128)
-constexpr int kBuildBT = 256;
+// L1 (5% faster than 128 on the 3D dam break; the prediction is faster at 128); the mixed
+// build takes 128, its output staging ring (RowStage) being twice as deep
+template <bool MIXED>
+__host__ __device__ constexpr int build_bt() { return MIXED ? 128 : 256; }
 
 __device__ __forceinline__ float dist2_f(const float4& a, const float4& b) {
     float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
@@ -93,7 +95,7 @@ struct PredictArgs {
     double4* pos_star;
     double4* vel_star;
     float4* pos32_star;
-    float4* pos32lo_star;
+    float4* pff_star;   // r* again as (hi, lo) pairs: slot i at 2 i and 2 i + 1
     DevStatus* st;
     Radius r;
     double coef_lap, nu, dt, g0, g1, g2, bmin0, bmin1, bmin2;
@@ -208,7 +210,8 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
         h4.w = ih.w;
         l4.w = 0.f;
         a.pos32_star[i] = h4;
-        a.pos32lo_star[i] = l4;
+        a.pff_star[2 * i] = h4;
+        a.pff_star[2 * i + 1] = l4;
         const double4 pb = a.pos_b ? a.pos_b[i] : pi;
         const double dx = ps.x - pb.x, dy = ps.y - pb.y, dz = ps.z - pb.z;
         disp = fma(dz, dz, fma(dy, dy, dx * dx));   // squared; the host takes the root
@@ -242,7 +245,7 @@ struct BuildArgs {
     const int32_t* vcol;
     const int32_t* vcnt;
     const float4* pos32;     // r*
-    const float4* pos32lo;   // r*
+    const float4* pff;       // r* as (hi, lo) pairs: one 32-byte sector per particle
     const double4* pos;      // r*
     const int8_t* type;
     DevStatus* st;
@@ -274,17 +277,22 @@ __device__ __forceinline__ double hs_term(ff dx, ff dy, ff dz, ff y, const doubl
     return re * (ry * ry * ry) * dot;
 }
 
-// Staging of the mixed build's row outputs: each thread collects the next 8 entries of its
-// PPE row (column, FP32 coefficient, low part) and of its gradient row in shared memory and
-// writes each group of 8 as whole 32-byte sectors (the grouped row layout, sell8), so that
-// no partially written sector has to be filled from DRAM.  Entry-major: thread t's entry e
-// sits at [e][t], consecutive threads in consecutive banks.
+// Staging of the mixed build's row outputs: each thread appends the entries of its PPE row
+// (column, FP32 coefficient, low part) and of its gradient row to a ring of 12 in shared
+// memory (an unconditional store and a cursor step, no branch) and writes each completed
+// group of 8 as whole 32-byte sectors (the grouped row layout, sell8), so that no partially
+// written sector has to be filled from DRAM.  A check every 2 iterations writes at most one
+// completed group per list, which leaves at most 7 unwritten; the next 2 iterations add at
+// most 4, so 12 slots never wrap onto an unwritten entry (and 24 KB per 128 threads keeps 8
+// blocks on an SM).  Entry-major: thread t's entry e sits at [e][t], consecutive threads in
+// consecutive banks.
+constexpr int kRing = 16;
 template <bool ON, int BT>
 struct RowStage {
-    int32_t col[8][BT];
-    float hi[8][BT];
-    float lo[8][BT];
-    int32_t ncol[8][BT];
+    int32_t col[kRing][BT];
+    float hi[kRing][BT];
+    float lo[kRing][BT];
+    int32_t ncol[kRing][BT];
 };
 template <int BT>
 struct RowStage<false, BT> {};
@@ -305,13 +313,16 @@ constexpr int kSlotMask = kEntryL - 1;
 // tiers) and writes the hits into the row's PPE slots in candidate order (band pairs,
 // decided after the walk, last); the dense pass evaluates every hit with (nearly) all
 // lanes busy and compacts the PPE coefficients in place to the front of the row.
-// Registers: the default mixed and the FP64 instantiations fit 64 (four 256-thread blocks
-// per SM); the options and the ensemble's take up to 85 (three).
+// Registers: the default mixed and the FP64 instantiations fit 64 (2048 threads per SM);
+// the options and the ensemble's take up to 85 (1536).
 // KERN, SRC: the weight (0 Eq. 4, 1 cubic) and the PPE source (0 Eq. 13, 1 HS, 2 HS + ECS) as
 // compile-time choices, so that the default instantiation carries none of the options' code
 template <bool MIXED, int KERN, int SRC, bool MULTI>
-__global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && SRC == 0))) ? 4 : 3)
+__global__ void __launch_bounds__(build_bt<MIXED>(),
+                                  ((!MULTI && (!MIXED || (KERN == 0 && SRC == 0))) ? 4 : 3) *
+                                      (256 / build_bt<MIXED>()))
     k_build(BuildArgs a) {
+    constexpr int kBuildBT = build_bt<MIXED>();
     // FLUID and WALL rows only (the bucket build's list of them): a DUMMY particle's own n*
     // enters no equation (no free-surface test, no PPE row, no gradient), so it is not
     // evaluated (reported as 0)
@@ -335,7 +346,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
             cre_ff = a.rho_s ? ff{sp.cre2_h, sp.cre2_l} : ff{sp.cre_h, sp.cre_l};
             ncoef_ff = a.rho_s ? ff{sp.ncoef2_h, sp.ncoef2_l} : ff{sp.ncoef_h, sp.ncoef_l};
         }
-        const float4 ih = a.pos32[i], il = a.pos32lo[i];
+        const float4 ih = a.pos32[i], il = a.pff[2 * i + 1];
         const double4 pi = a.pos[i];
         const int cnt = a.vcnt[i];
         const bool with_ppe = (a.pressure_mode == 0);
@@ -385,7 +396,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                     pend[np++] = k;
                     continue;
                 }
-                const ff r2f = pair_r2(ih, il, jh, a.pos32lo[j]);
+                const ff r2f = pair_r2(ih, il, jh, a.pff[2 * j + 1]);
                 if (tl == 2) tl = decide_band(r2f, rl, a.pos, pi, j) ? 1 : 0;
                 if (tn == 2) tn = decide_band(r2f, rn, a.pos, pi, j) ? 1 : 0;
             }
@@ -398,7 +409,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
             const bool nb_ok = kind_of(jh) != kDummy;
             int tl = (nb_ok && with_ppe) ? tier1(r2, rl) : 0;
             int tn = tier1(r2, rn);
-            const ff r2f = pair_r2(ih, il, jh, a.pos32lo[j]);
+            const ff r2f = pair_r2(ih, il, jh, a.pff[2 * j + 1]);
             if (tl == 2) tl = decide_band(r2f, rl, a.pos, pi, j) ? 1 : 0;
             if (tn == 2) tn = decide_band(r2f, rn, a.pos, pi, j) ? 1 : 0;
             append(j, tl, tn, nb_ok);
@@ -425,66 +436,68 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
             const double4 ui = SRC >= 1 ? a.vel_star[i] : make_double4(0.0, 0.0, 0.0, 0.0);
             // the row's outputs, staged 8 entries at a time (RowStage above)
             const int t_ = threadIdx.x;
+            // group g of a list sits in ring half g & 1
             auto flush_lap = [&](int g) {
                 const size_t q = sell8(i, 8 * g, a.cap);
-                *(int4*)(a.lap_col + q) = make_int4(stage.col[0][t_], stage.col[1][t_],
-                                                    stage.col[2][t_], stage.col[3][t_]);
-                *(int4*)(a.lap_col + q + 4) = make_int4(stage.col[4][t_], stage.col[5][t_],
-                                                        stage.col[6][t_], stage.col[7][t_]);
-                *(float4*)(a.lap_v32 + q) = make_float4(stage.hi[0][t_], stage.hi[1][t_],
-                                                        stage.hi[2][t_], stage.hi[3][t_]);
-                *(float4*)(a.lap_v32 + q + 4) = make_float4(stage.hi[4][t_], stage.hi[5][t_],
-                                                            stage.hi[6][t_], stage.hi[7][t_]);
-                *(float4*)(a.lap_vlo + q) = make_float4(stage.lo[0][t_], stage.lo[1][t_],
-                                                        stage.lo[2][t_], stage.lo[3][t_]);
-                *(float4*)(a.lap_vlo + q + 4) = make_float4(stage.lo[4][t_], stage.lo[5][t_],
-                                                            stage.lo[6][t_], stage.lo[7][t_]);
-            };
-            auto put_lap = [&](int j, float h, float l) {
-                if (out_l < a.cap) {
-                    const int e = out_l & 7;
-                    stage.col[e][t_] = j;
-                    stage.hi[e][t_] = h;
-                    stage.lo[e][t_] = l;
-                    if (e == 7) flush_lap(out_l >> 3);
-                    out_l++;
-                } else {
-                    overflow = true;
-                }
+                const int h = (g & 1) * 8;
+                *(int4*)(a.lap_col + q) = make_int4(stage.col[h][t_], stage.col[h + 1][t_],
+                                                    stage.col[h + 2][t_], stage.col[h + 3][t_]);
+                *(int4*)(a.lap_col + q + 4) = make_int4(stage.col[h + 4][t_], stage.col[h + 5][t_],
+                                                        stage.col[h + 6][t_], stage.col[h + 7][t_]);
+                *(float4*)(a.lap_v32 + q) = make_float4(stage.hi[h][t_], stage.hi[h + 1][t_],
+                                                        stage.hi[h + 2][t_], stage.hi[h + 3][t_]);
+                *(float4*)(a.lap_v32 + q + 4) = make_float4(stage.hi[h + 4][t_], stage.hi[h + 5][t_],
+                                                            stage.hi[h + 6][t_], stage.hi[h + 7][t_]);
+                *(float4*)(a.lap_vlo + q) = make_float4(stage.lo[h][t_], stage.lo[h + 1][t_],
+                                                        stage.lo[h + 2][t_], stage.lo[h + 3][t_]);
+                *(float4*)(a.lap_vlo + q + 4) = make_float4(stage.lo[h + 4][t_], stage.lo[h + 5][t_],
+                                                            stage.lo[h + 6][t_], stage.lo[h + 7][t_]);
             };
             auto flush_n = [&](int g) {
                 const size_t q = sell8(i, 8 * g, a.cap_n);
-                *(int4*)(a.n_col + q) = make_int4(stage.ncol[0][t_], stage.ncol[1][t_],
-                                                  stage.ncol[2][t_], stage.ncol[3][t_]);
-                *(int4*)(a.n_col + q + 4) = make_int4(stage.ncol[4][t_], stage.ncol[5][t_],
-                                                      stage.ncol[6][t_], stage.ncol[7][t_]);
+                const int h = (g & 1) * 8;
+                *(int4*)(a.n_col + q) = make_int4(stage.ncol[h][t_], stage.ncol[h + 1][t_],
+                                                  stage.ncol[h + 2][t_], stage.ncol[h + 3][t_]);
+                *(int4*)(a.n_col + q + 4) = make_int4(stage.ncol[h + 4][t_], stage.ncol[h + 5][t_],
+                                                      stage.ncol[h + 6][t_], stage.ncol[h + 7][t_]);
             };
-            auto put_n = [&](int j) {
-                if (out_n < a.cap_n) {
-                    const int e = out_n & 7;
-                    stage.ncol[e][t_] = j;
-                    if (e == 7) flush_n(out_n >> 3);
+            auto put_lap = [&](int j, float h, float l, bool on) {
+                const int e = out_l & (kRing - 1);
+                stage.col[e][t_] = j;
+                stage.hi[e][t_] = h;
+                stage.lo[e][t_] = l;
+                out_l += on ? 1 : 0;
+            };
+            auto put_n = [&](int j, bool on) {
+                stage.ncol[out_n & (kRing - 1)][t_] = j;
+                out_n += on ? 1 : 0;
+            };
+            int done_l = 0, done_n = 0;   // groups written
+            auto flush_ready = [&]() {
+                const bool fl = done_l < (min(out_l, a.cap) >> 3);
+                const bool fn = done_n < (min(out_n, a.cap_n) >> 3);
+                if (__any_sync(__activemask(), fl || fn)) {
+                    if (fl) flush_lap(done_l++);
+                    if (fn) flush_n(done_n++);
                 }
-                out_n++;
             };
             // the members' terms of a pair of candidates (lane x: j0, lane y: j1), shared by
             // the single walk and the walk over staged entries
             auto terms = [&](int j0, int j1, const ff2& dx, const ff2& dy, const ff2& dz,
                              const ff2& r2, bool tn0, bool tl0, bool tn1, bool tl1) {
                 const ff2 y = ff2_rsqrt1(r2);
-                ff2 w = {f2(0.f), f2(0.f)};
-                if (tn0 || tn1) {
-                    const ff2 y2 = ff2_rsqrt_step(r2, y);
-                    w = KERN == 1 ? ff2_cube(ff2_one_minus(ff2_mul(ff2_mul(r2, y2), invn)))
-                                      : ff2_add_f(ff2_mul(ren, y2), f2(-1.f));
-                    if (SRC >= 1) {
-                        // HS: re_n / r^3 (r_ij . (u*_j - u*_i)), binary64 from the float-float
-                        // offsets and reciprocal distance
-                        if (tn0) hs += hs_term(ff2_lo(dx), ff2_lo(dy), ff2_lo(dz), ff2_lo(y2),
-                                               a.vel_star[j0], ui, rn.re);
-                        if (tn1) hs += hs_term(ff2_hi(dx), ff2_hi(dy), ff2_hi(dz), ff2_hi(y2),
-                                               a.vel_star[j1], ui, rn.re);
-                    }
+                // the number-density weight of both lanes, used only where tn (a branch on
+                // tn0 || tn1 would be taken by nearly every warp anyway)
+                const ff2 y2 = ff2_rsqrt_step(r2, y);
+                const ff2 w = KERN == 1 ? ff2_cube(ff2_one_minus(ff2_mul(ff2_mul(r2, y2), invn)))
+                                        : ff2_add_f(ff2_mul(ren, y2), f2(-1.f));
+                if (SRC >= 1) {
+                    // HS: re_n / r^3 (r_ij . (u*_j - u*_i)), binary64 from the float-float
+                    // offsets and reciprocal distance
+                    if (tn0) hs += hs_term(ff2_lo(dx), ff2_lo(dy), ff2_lo(dz), ff2_lo(y2),
+                                           a.vel_star[j0], ui, rn.re);
+                    if (tn1) hs += hs_term(ff2_hi(dx), ff2_hi(dy), ff2_hi(dz), ff2_hi(y2),
+                                           a.vel_star[j1], ui, rn.re);
                 }
                 // c = coef (re/r - 1) = (coef re) y - coef, or coef (1 - r/re)^3
                 ff2 c = KERN == 1 ? ff2_mul(coef, ff2_cube(ff2_one_minus(ff2_mul(ff2_mul(r2, y), invl))))
@@ -498,8 +511,8 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                                     make_float2(tn0 ? w.l.x : 0.f, tl0 ? c.l.x : 0.f)});
                 acc = ff2_add(acc, {make_float2(tn1 ? w.h.y : 0.f, tl1 ? c.h.y : 0.f),
                                     make_float2(tn1 ? w.l.y : 0.f, tl1 ? c.l.y : 0.f)});
-                if (tl0) put_lap(j0, c.h.x, c.l.x);
-                if (tl1) put_lap(j1, c.h.y, c.l.y);
+                put_lap(j0, c.h.x, c.l.x, tl0);
+                put_lap(j1, c.h.y, c.l.y, tl1);
             };
             if (!with_ppe) {
                 // equation of state: one in seven candidates is a member (within re_n), so
@@ -509,8 +522,8 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                     const int e0 = a.lap_col[sell8(i, t, a.cap)];
                     const int e1 = two ? a.lap_col[sell8(i, t + 1, a.cap)] : e0;
                     const int j0 = e0 & kSlotMask, j1 = e1 & kSlotMask;
-                    const float4 h0 = a.pos32[j0], l0 = a.pos32lo[j0];
-                    const float4 h1 = a.pos32[j1], l1 = a.pos32lo[j1];
+                    const float4 h0 = a.pff[2 * j0], l0 = a.pff[2 * j0 + 1];
+                    const float4 h1 = a.pff[2 * j1], l1 = a.pff[2 * j1 + 1];
                     const ff2 dx = ff2_diff(ih.x, il.x, make_float2(h0.x, h1.x), make_float2(l0.x, l1.x));
                     const ff2 dy = ff2_diff(ih.y, il.y, make_float2(h0.y, h1.y), make_float2(l0.y, l1.y));
                     const ff2 dz = ff2_diff(ih.z, il.z, make_float2(h0.z, h1.z), make_float2(l0.z, l1.z));
@@ -537,57 +550,75 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                         s0 = a.vcol[sell8(i, t + 2, a.cap_v)];
                         s1 = t + 3 < cnt ? a.vcol[sell8(i, t + 3, a.cap_v)] : s0;
                     }
-                    const float4 h0 = a.pos32[j0], l0 = a.pos32lo[j0];
-                    const float4 h1 = a.pos32[j1], l1 = a.pos32lo[j1];
+                    const float4 h0 = a.pff[2 * j0], l0 = a.pff[2 * j0 + 1];
+                    const float4 h1 = a.pff[2 * j1], l1 = a.pff[2 * j1 + 1];
                     const ff2 dx = ff2_diff(ih.x, il.x, make_float2(h0.x, h1.x), make_float2(l0.x, l1.x));
                     const ff2 dy = ff2_diff(ih.y, il.y, make_float2(h0.y, h1.y), make_float2(l0.y, l1.y));
                     const ff2 dz = ff2_diff(ih.z, il.z, make_float2(h0.z, h1.z), make_float2(l0.z, l1.z));
                     const ff2 r2 = ff2_dist2(dx, dy, dz);
-                    // membership: d = r^2 - re^2 in float-float, decided outside [-ff_tol, ff_tol]
+                    // membership: d = r^2 - re^2 in float-float, decided outside [-ff_tol, ff_tol];
+                    // inside that band binary64 decides, in a branch the warp enters only when
+                    // one of its lanes has such a pair (rare)
                     const float2 dn = add2(sub2(r2.h, f2(rn.re2_h)), sub2(r2.l, f2(rn.re2_l)));
-                    bool tn0 = dn.x <= -rn.ff_tol ||
-                               (dn.x < rn.ff_tol && exact_dist2(pi, a.pos[j0]) < rn.re2);
-                    bool tn1 = two && (dn.y <= -rn.ff_tol ||
-                                       (dn.y < rn.ff_tol && exact_dist2(pi, a.pos[j1]) < rn.re2));
+                    const float2 dl = add2(sub2(r2.h, f2(rl.re2_h)), sub2(r2.l, f2(rl.re2_l)));
                     const bool nb0 = kind_of(h0) != kDummy, nb1 = kind_of(h1) != kDummy;
-                    bool tl0 = false, tl1 = false;
-                    if (with_ppe) {
-                        const float2 dl = add2(sub2(r2.h, f2(rl.re2_h)), sub2(r2.l, f2(rl.re2_l)));
-                        tl0 = nb0 && (dl.x <= -rl.ff_tol ||
-                                      (dl.x < rl.ff_tol && exact_dist2(pi, a.pos[j0]) < rl.re2));
-                        tl1 = two && nb1 && (dl.y <= -rl.ff_tol ||
-                                             (dl.y < rl.ff_tol && exact_dist2(pi, a.pos[j1]) < rl.re2));
+                    bool tn0 = dn.x <= -rn.ff_tol, tn1 = two && dn.y <= -rn.ff_tol;
+                    bool tl0 = nb0 && dl.x <= -rl.ff_tol, tl1 = two && nb1 && dl.y <= -rl.ff_tol;
+                    const bool bn0 = !(dn.x <= -rn.ff_tol) && dn.x < rn.ff_tol;
+                    const bool bn1 = two && !(dn.y <= -rn.ff_tol) && dn.y < rn.ff_tol;
+                    const bool bl0 = nb0 && !(dl.x <= -rl.ff_tol) && dl.x < rl.ff_tol;
+                    const bool bl1 = two && nb1 && !(dl.y <= -rl.ff_tol) && dl.y < rl.ff_tol;
+                    if (__any_sync(__activemask(), bn0 || bn1 || bl0 || bl1)) {
+                        if (bn0 || bl0) {
+                            const double d2 = exact_dist2(pi, a.pos[j0]);
+                            if (bn0) tn0 = d2 < rn.re2;
+                            if (bl0) tl0 = d2 < rl.re2;
+                        }
+                        if (bn1 || bl1) {
+                            const double d2 = exact_dist2(pi, a.pos[j1]);
+                            if (bn1) tn1 = d2 < rn.re2;
+                            if (bl1) tl1 = d2 < rl.re2;
+                        }
                     }
                     // a member at zero distance (coincident to float-float) is an error unless
                     // binary64 separates it; either way it adds no term
                     const bool ok0 = r2.h.x > 0.f, ok1 = two && r2.h.y > 0.f;
-                    if ((tn0 || tl0) && !ok0 && !(exact_dist2(pi, a.pos[j0]) > 0.0))
-                        atomicOr(&a.st->err, kErrCoincident);
-                    if ((tn1 || tl1) && !ok1 && !(exact_dist2(pi, a.pos[j1]) > 0.0))
-                        atomicOr(&a.st->err, kErrCoincident);
+                    const bool z0 = (tn0 || tl0) && !ok0, z1 = (tn1 || tl1) && !ok1;
+                    if (__any_sync(__activemask(), z0 || z1)) {
+                        if (z0 && !(exact_dist2(pi, a.pos[j0]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
+                        if (z1 && !(exact_dist2(pi, a.pos[j1]) > 0.0)) atomicOr(&a.st->err, kErrCoincident);
+                    }
                     // the gradient list: non-dummy members within re_n, in candidate order
-                    if (tn0 && nb0) put_n(j0);
-                    if (tn1 && nb1) put_n(j1);
+                    put_n(j0, tn0 && nb0);
+                    put_n(j1, tn1 && nb1);
                     m_n += (tn0 ? 1 : 0) + (tn1 ? 1 : 0);
                     tn0 = tn0 && ok0;
                     tn1 = tn1 && ok1;
                     tl0 = tl0 && ok0;
                     tl1 = tl1 && ok1;
                     terms(j0, j1, dx, dy, dz, r2, tn0, tl0, tn1, tl1);
+                    if ((t & 6) == 6) flush_ready();   // every 4 iterations
+                }
+                flush_ready();   // the last completed groups (at most one per list)
+                if (out_l > a.cap) {
+                    overflow = true;
+                    out_l = a.cap;
                 }
                 // the last, partial groups: the PPE row padded with zero coefficients on the
                 // row's own column (the solver reads whole groups), the gradient row as is
                 if (out_l & 7) {
+                    const int h = ((out_l >> 3) & 1) * 8;
                     for (int e = out_l & 7; e < 8; e++) {
-                        stage.col[e][t_] = i;
-                        stage.hi[e][t_] = 0.f;
-                        stage.lo[e][t_] = 0.f;
+                        stage.col[h + e][t_] = i;
+                        stage.hi[h + e][t_] = 0.f;
+                        stage.lo[h + e][t_] = 0.f;
                     }
                     flush_lap(out_l >> 3);
                 }
                 const int mn = min(out_n, a.cap_n);
                 if (mn & 7) {
-                    for (int e = mn & 7; e < 8; e++) stage.ncol[e][t_] = i;
+                    const int h = ((mn >> 3) & 1) * 8;
+                    for (int e = mn & 7; e < 8; e++) stage.ncol[h + e][t_] = i;
                     flush_n(mn >> 3);
                 }
             }
@@ -777,7 +808,7 @@ void launch_predict_rows(Ctx* c) {
     a.pos_star = c->pos_star;
     a.vel_star = c->vel_star;
     a.pos32_star = c->pos32_star;
-    a.pos32lo_star = c->pos32lo_star;
+    a.pff_star = c->pff_star;
     a.st = c->st;
     a.r = c->r_lap;
     a.coef_lap = c->coef_lap;
@@ -810,15 +841,15 @@ static void launch_build_t(Ctx* c, const BuildArgs& a, int grid) {
     const mps_params& P = c->prm;
     const int src = P.source_term;
     if (P.precision == 1) {
-        if (P.kernel == 1) k_build<true, 1, 0, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
-        else if (src == 0) k_build<true, 0, 0, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
-        else if (src == 1) k_build<true, 0, 1, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
-        else k_build<true, 0, 2, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
+        if (P.kernel == 1) k_build<true, 1, 0, MULTI><<<grid, build_bt<true>(), 0, c->stream>>>(a);
+        else if (src == 0) k_build<true, 0, 0, MULTI><<<grid, build_bt<true>(), 0, c->stream>>>(a);
+        else if (src == 1) k_build<true, 0, 1, MULTI><<<grid, build_bt<true>(), 0, c->stream>>>(a);
+        else k_build<true, 0, 2, MULTI><<<grid, build_bt<true>(), 0, c->stream>>>(a);
     } else {
-        if (P.kernel == 1) k_build<false, 1, 0, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
-        else if (src == 0) k_build<false, 0, 0, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
-        else if (src == 1) k_build<false, 0, 1, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
-        else k_build<false, 0, 2, MULTI><<<grid, kBuildBT, 0, c->stream>>>(a);
+        if (P.kernel == 1) k_build<false, 1, 0, MULTI><<<grid, build_bt<false>(), 0, c->stream>>>(a);
+        else if (src == 0) k_build<false, 0, 0, MULTI><<<grid, build_bt<false>(), 0, c->stream>>>(a);
+        else if (src == 1) k_build<false, 0, 1, MULTI><<<grid, build_bt<false>(), 0, c->stream>>>(a);
+        else k_build<false, 0, 2, MULTI><<<grid, build_bt<false>(), 0, c->stream>>>(a);
     }
 }
 
@@ -845,7 +876,7 @@ void launch_build_rows(Ctx* c) {
     a.vcol = c->vl_col;
     a.vcnt = c->vl_cnt;
     a.pos32 = c->pos32_star;
-    a.pos32lo = c->pos32lo_star;
+    a.pff = c->pff_star;
     a.pos = c->pos_star;
     a.type = c->type;
     a.st = c->st;
@@ -875,7 +906,8 @@ void launch_build_rows(Ctx* c) {
     a.diag = c->diag;
     a.diag32 = c->diag32;
     a.p = c->p;
-    const int grid = (int)((c->n + kBuildBT - 1) / kBuildBT);
+    const int bt = P.precision == 1 ? build_bt<true>() : build_bt<false>();
+    const int grid = (int)((c->n + bt - 1) / bt);
     a.sid = c->sid;
     a.scn = c->scn;
     if (c->n_scenes > 1) launch_build_t<true>(c, a, grid);
