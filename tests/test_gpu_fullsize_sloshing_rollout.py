@@ -14,12 +14,14 @@ Steps of the central differences.  The equation-of-state path is smooth in every
 takes h = 1e-6 (m^2/s for nu, m/s along the unit-RMS direction for the velocity field); its
 differences agree to ~1e-8.  The PPE path is only piecewise smooth over 200 steps: the clamp
 max(p, 0) and the minimum p_hat have kinks, and a particle whose number density crosses the
-free-surface threshold (Eq. 15) switches its PPE row to p = 0, a jump.  Along the velocity
-field the differences then stay ~2-3e-4 away from the adjoint for h = 1e-7 ... 1e-6 (the
-jumps crossed grow with h while their weight falls as 1/h) and grow beyond (1.6e-3 at 1e-5),
-so that check is bounded at 1e-3; the exact comparison of the PPE path is the chained oracle
-below (1e-4).  In the viscosity, h = 1e-8 m^2/s (1% of nu) agrees to ~1e-7.  Both sides run
-their PPE solves to 1e-13."""
+free-surface threshold (Eq. 15) switches its PPE row to p = 0, a jump.  Below, the losses
+themselves are reproducible only to ~2e-13 m across perturbed runs (200 solves to a relative
+residual of 1e-13), which alone puts a difference at h = 1e-7 ~3e-3 away from the adjoint
+(measured: mean surface height, -3.6731e-4 against -3.6853e-4); at h = 1e-6 that floor is
+~3e-4, and beyond the jumps crossed take over (1.6e-3 at 1e-5).  So the velocity field takes
+h = 1e-6 and that check is bounded at 1e-3; the exact comparison of the PPE path is the
+chained oracle below (1e-4).  In the viscosity, h = 1e-8 m^2/s (1% of nu) agrees to ~1e-7.
+Both sides run their PPE solves to 1e-13."""
 import numpy as np
 import pytest
 
@@ -86,7 +88,7 @@ def test_rollout_gradients_match_central_differences(setup, path):
     from paper_2105_01677_gb300 import mps
     sc, u0, v = setup
     kw = dict(dt=DT, cg_tol=CG) if path == "ppe" else dict(dt=DT, pressure_mode=1, c0=20.0)
-    h_nu, h_u = (1e-8, 1e-7) if path == "ppe" else (1e-6, 1e-6)
+    h_nu, h_u = (1e-8, 1e-6) if path == "ppe" else (1e-6, 1e-6)
     sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True, **gpu_params(sc, **kw))
     try:
         adj = {}
