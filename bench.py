@@ -79,11 +79,13 @@ ISSUED_FLOPS_LIST_TEST, ISSUED_FLOPS_PPE_PAIR, ISSUED_FLOPS_PND_PAIR = 8.0, 133.
 BUILD_BYTES_PER_COEF, BUILD_BYTES_PER_LIST_ENTRY, BUILD_BYTES_PER_PARTICLE = 12.0, 4.0, 69.0
 # DRAM bytes (read + write) per PPE coefficient of one launch, from the ncu capture in
 # profiles/kernels_dam_break_3d_227k_mixed.md (227,136-particle case, 25.19 M coefficients,
-# rows grouped 8 entries per row): FP32 SpMV 202.1 + 0.5 MB, build 203.0 + 289.2 MB,
-# float-float residual 306.5 + 1.2 MB.  The rows and lists scale with the coefficients.
-SPMV_TRAFFIC_PER_COEF = (202.06e6 + 0.48e6) / 25.19e6
-BUILD_TRAFFIC_PER_COEF = (202.98e6 + 289.20e6) / 25.19e6
-RESID_TRAFFIC_PER_COEF = (306.47e6 + 1.18e6) / 25.19e6
+# rows grouped 8 entries per row): FP32 SpMV 202.1 + 0.5 MB, build 162.0 + 286.2 MB,
+# float-float residual 306.4 + 1.2 MB; the gather per candidate-list entry (31.09 M):
+# 6.5 + 76.1 MB.  The rows and lists scale with the coefficients and entries.
+SPMV_TRAFFIC_PER_COEF = (202.10e6 + 0.48e6) / 25.19e6
+BUILD_TRAFFIC_PER_COEF = (161.98e6 + 286.24e6) / 25.19e6
+RESID_TRAFFIC_PER_COEF = (306.44e6 + 1.16e6) / 25.19e6
+GATHER_TRAFFIC_PER_ENTRY = (6.52e6 + 76.14e6) / 31.086e6
 
 
 def parse():
@@ -752,7 +754,7 @@ def run_gb300(args):
                                   / (per_call["build"] * 1e-3) / 1e12})
     roof_gather = bound("k_gather<VerletOp> (candidate lists)", per_call["gather"], 1.0,
                         flops=METHOD_FLOPS_TEST * tests, nbytes=4.0 * list_tests + 48.0 * n,
-                        traffic=None,
+                        traffic=GATHER_TRAFFIC_PER_ENTRY * list_tests,
                         work={"cand_tests": tests, "list_entries": list_tests,
                               "flops_per_test": METHOD_FLOPS_TEST,
                               "bytes": "4 per list entry written, 48 per particle read"})

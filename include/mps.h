@@ -110,7 +110,8 @@ typedef struct {
                                * Eq. 21, (Dn/Dt)* / (n0 dt) from the predicted velocities over *
                                * the number-density neighbours; 2 HS plus the error-           *
                                * compensating source of Eq. 24-25, ECS / dt, from n and Dn/Dt  *
-                               * at the step's start (1 and 2 require kernel 0)                 */
+                               * at the step's start (1 and 2 require kernel 0; with           *
+                               * pressure_mode 1 there is no PPE and the value is ignored)      */
     int32_t ppe_host_loop;    /* mixed PPE of one scene: 0 (default) runs the refinement and   *
                                * inner CG loops on the device as one CUDA graph with           *
                                * conditional nodes (one launch and one read per solve); 1     *

@@ -36,9 +36,9 @@ namespace {
 constexpr int kBT = 128;
 // the build's blocks: 256 rows of neighbouring particles share more of their candidates in
 // L1 (5% faster than 128 on the 3D dam break; the prediction is faster at 128); the mixed
-// build takes 128, its output staging ring (RowStage) being twice as deep
-template <bool MIXED>
-__host__ __device__ constexpr int build_bt() { return MIXED ? 128 : 256; }
+// build with the PPE takes 128, its output staging ring (RowStage) being deep
+constexpr int kBuildBT = 256;
+constexpr int kBuildRingBT = 128;
 
 __device__ __forceinline__ float dist2_f(const float4& a, const float4& b) {
     float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
@@ -287,15 +287,19 @@ __device__ __forceinline__ double hs_term(ff dx, ff dy, ff dz, ff y, const doubl
 // blocks on an SM).  Entry-major: thread t's entry e sits at [e][t], consecutive threads in
 // consecutive banks.
 constexpr int kRing = 16;
-template <bool ON, int BT>
+// the ring in the block's dynamic shared memory: four arrays of kRing x (block size) words
 struct RowStage {
-    int32_t col[kRing][BT];
-    float hi[kRing][BT];
-    float lo[kRing][BT];
-    int32_t ncol[kRing][BT];
+    int32_t* c;
+    float* h;
+    float* l;
+    int32_t* nc;
+    int bt;
+    __device__ int32_t* col(int e) const { return c + e * bt; }
+    __device__ float* hi(int e) const { return h + e * bt; }
+    __device__ float* lo(int e) const { return l + e * bt; }
+    __device__ int32_t* ncol(int e) const { return nc + e * bt; }
 };
-template <int BT>
-struct RowStage<false, BT> {};
+constexpr size_t kRingBytes = 4 * kRing * kBuildRingBT * sizeof(int32_t);
 
 // Entry flags while a PPE row is being assembled (slots are < 2^30)
 constexpr int kEntryN = 1 << 30;   // within re_n: contributes to n*
@@ -318,17 +322,19 @@ constexpr int kSlotMask = kEntryL - 1;
 // KERN, SRC: the weight (0 Eq. 4, 1 cubic) and the PPE source (0 Eq. 13, 1 HS, 2 HS + ECS) as
 // compile-time choices, so that the default instantiation carries none of the options' code
 template <bool MIXED, int KERN, int SRC, bool MULTI>
-__global__ void __launch_bounds__(build_bt<MIXED>(),
-                                  ((!MULTI && (!MIXED || (KERN == 0 && SRC == 0))) ? 4 : 3) *
-                                      (256 / build_bt<MIXED>()))
+__global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && SRC == 0))) ? 4 : 3)
     k_build(BuildArgs a) {
-    constexpr int kBuildBT = build_bt<MIXED>();
     // FLUID and WALL rows only (the bucket build's list of them): a DUMMY particle's own n*
     // enters no equation (no free-surface test, no PPE row, no gradient), so it is not
     // evaluated (reported as 0)
-    const int tid = blockIdx.x * kBuildBT + threadIdx.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = tid < (int)*a.nrows ? a.rows[tid] : -1;
-    __shared__ RowStage<MIXED, kBuildBT> stage;
+    // mixed with the PPE: the row-output ring (launched with kBuildRingBT threads and
+    // kRingBytes of dynamic shared memory; other launches pass none and never touch it)
+    extern __shared__ __align__(16) int32_t s_ring[];
+    const int rbt = (int)blockDim.x;
+    const RowStage stage{s_ring, (float*)(s_ring + kRing * rbt), (float*)(s_ring + 2 * kRing * rbt),
+                         s_ring + 3 * kRing * rbt, rbt};
     bool surf = false, ppe = false;
     unsigned n_lap = 0, n_pnd = 0;   // pairs evaluated by this row
     unsigned n_cand = 0;             // candidate-list entries it classified
@@ -440,36 +446,36 @@ __global__ void __launch_bounds__(build_bt<MIXED>(),
             auto flush_lap = [&](int g) {
                 const size_t q = sell8(i, 8 * g, a.cap);
                 const int h = (g & 1) * 8;
-                *(int4*)(a.lap_col + q) = make_int4(stage.col[h][t_], stage.col[h + 1][t_],
-                                                    stage.col[h + 2][t_], stage.col[h + 3][t_]);
-                *(int4*)(a.lap_col + q + 4) = make_int4(stage.col[h + 4][t_], stage.col[h + 5][t_],
-                                                        stage.col[h + 6][t_], stage.col[h + 7][t_]);
-                *(float4*)(a.lap_v32 + q) = make_float4(stage.hi[h][t_], stage.hi[h + 1][t_],
-                                                        stage.hi[h + 2][t_], stage.hi[h + 3][t_]);
-                *(float4*)(a.lap_v32 + q + 4) = make_float4(stage.hi[h + 4][t_], stage.hi[h + 5][t_],
-                                                            stage.hi[h + 6][t_], stage.hi[h + 7][t_]);
-                *(float4*)(a.lap_vlo + q) = make_float4(stage.lo[h][t_], stage.lo[h + 1][t_],
-                                                        stage.lo[h + 2][t_], stage.lo[h + 3][t_]);
-                *(float4*)(a.lap_vlo + q + 4) = make_float4(stage.lo[h + 4][t_], stage.lo[h + 5][t_],
-                                                            stage.lo[h + 6][t_], stage.lo[h + 7][t_]);
+                *(int4*)(a.lap_col + q) = make_int4(stage.col(h)[t_], stage.col(h + 1)[t_],
+                                                    stage.col(h + 2)[t_], stage.col(h + 3)[t_]);
+                *(int4*)(a.lap_col + q + 4) = make_int4(stage.col(h + 4)[t_], stage.col(h + 5)[t_],
+                                                        stage.col(h + 6)[t_], stage.col(h + 7)[t_]);
+                *(float4*)(a.lap_v32 + q) = make_float4(stage.hi(h)[t_], stage.hi(h + 1)[t_],
+                                                        stage.hi(h + 2)[t_], stage.hi(h + 3)[t_]);
+                *(float4*)(a.lap_v32 + q + 4) = make_float4(stage.hi(h + 4)[t_], stage.hi(h + 5)[t_],
+                                                            stage.hi(h + 6)[t_], stage.hi(h + 7)[t_]);
+                *(float4*)(a.lap_vlo + q) = make_float4(stage.lo(h)[t_], stage.lo(h + 1)[t_],
+                                                        stage.lo(h + 2)[t_], stage.lo(h + 3)[t_]);
+                *(float4*)(a.lap_vlo + q + 4) = make_float4(stage.lo(h + 4)[t_], stage.lo(h + 5)[t_],
+                                                            stage.lo(h + 6)[t_], stage.lo(h + 7)[t_]);
             };
             auto flush_n = [&](int g) {
                 const size_t q = sell8(i, 8 * g, a.cap_n);
                 const int h = (g & 1) * 8;
-                *(int4*)(a.n_col + q) = make_int4(stage.ncol[h][t_], stage.ncol[h + 1][t_],
-                                                  stage.ncol[h + 2][t_], stage.ncol[h + 3][t_]);
-                *(int4*)(a.n_col + q + 4) = make_int4(stage.ncol[h + 4][t_], stage.ncol[h + 5][t_],
-                                                      stage.ncol[h + 6][t_], stage.ncol[h + 7][t_]);
+                *(int4*)(a.n_col + q) = make_int4(stage.ncol(h)[t_], stage.ncol(h + 1)[t_],
+                                                  stage.ncol(h + 2)[t_], stage.ncol(h + 3)[t_]);
+                *(int4*)(a.n_col + q + 4) = make_int4(stage.ncol(h + 4)[t_], stage.ncol(h + 5)[t_],
+                                                      stage.ncol(h + 6)[t_], stage.ncol(h + 7)[t_]);
             };
             auto put_lap = [&](int j, float h, float l, bool on) {
                 const int e = out_l & (kRing - 1);
-                stage.col[e][t_] = j;
-                stage.hi[e][t_] = h;
-                stage.lo[e][t_] = l;
+                stage.col(e)[t_] = j;
+                stage.hi(e)[t_] = h;
+                stage.lo(e)[t_] = l;
                 out_l += on ? 1 : 0;
             };
             auto put_n = [&](int j, bool on) {
-                stage.ncol[out_n & (kRing - 1)][t_] = j;
+                stage.ncol(out_n & (kRing - 1))[t_] = j;
                 out_n += on ? 1 : 0;
             };
             int done_l = 0, done_n = 0;   // groups written
@@ -511,8 +517,10 @@ __global__ void __launch_bounds__(build_bt<MIXED>(),
                                     make_float2(tn0 ? w.l.x : 0.f, tl0 ? c.l.x : 0.f)});
                 acc = ff2_add(acc, {make_float2(tn1 ? w.h.y : 0.f, tl1 ? c.h.y : 0.f),
                                     make_float2(tn1 ? w.l.y : 0.f, tl1 ? c.l.y : 0.f)});
-                put_lap(j0, c.h.x, c.l.x, tl0);
-                put_lap(j1, c.h.y, c.l.y, tl1);
+                if (with_ppe) {   // the ring exists only in the PPE launch (block-uniform)
+                    put_lap(j0, c.h.x, c.l.x, tl0);
+                    put_lap(j1, c.h.y, c.l.y, tl1);
+                }
             };
             if (!with_ppe) {
                 // equation of state: one in seven candidates is a member (within re_n), so
@@ -609,16 +617,16 @@ __global__ void __launch_bounds__(build_bt<MIXED>(),
                 if (out_l & 7) {
                     const int h = ((out_l >> 3) & 1) * 8;
                     for (int e = out_l & 7; e < 8; e++) {
-                        stage.col[h + e][t_] = i;
-                        stage.hi[h + e][t_] = 0.f;
-                        stage.lo[h + e][t_] = 0.f;
+                        stage.col(h + e)[t_] = i;
+                        stage.hi(h + e)[t_] = 0.f;
+                        stage.lo(h + e)[t_] = 0.f;
                     }
                     flush_lap(out_l >> 3);
                 }
                 const int mn = min(out_n, a.cap_n);
                 if (mn & 7) {
                     const int h = ((mn >> 3) & 1) * 8;
-                    for (int e = mn & 7; e < 8; e++) stage.ncol[h + e][t_] = i;
+                    for (int e = mn & 7; e < 8; e++) stage.ncol(h + e)[t_] = i;
                     flush_n(mn >> 3);
                 }
             }
@@ -837,19 +845,25 @@ void launch_predict_rows(Ctx* c) {
 
 // (kernel, source): (0, 0), (0, 1), (0, 2), (1, 0); the cubic weight with HS is rejected
 template <bool MULTI>
-static void launch_build_t(Ctx* c, const BuildArgs& a, int grid) {
+static void launch_build_t(Ctx* c, const BuildArgs& a) {
     const mps_params& P = c->prm;
-    const int src = P.source_term;
+    // the source term enters the PPE only: an equation-of-state step takes the standard one
+    // (the ECS rates are not even allocated then)
+    const int src = P.pressure_mode == 0 ? P.source_term : 0;
+    const bool ring = P.precision == 1 && P.pressure_mode == 0;
+    const int bt = ring ? kBuildRingBT : kBuildBT;
+    const size_t sm = ring ? kRingBytes : 0;
+    const int grid = (int)((c->n + bt - 1) / bt);
     if (P.precision == 1) {
-        if (P.kernel == 1) k_build<true, 1, 0, MULTI><<<grid, build_bt<true>(), 0, c->stream>>>(a);
-        else if (src == 0) k_build<true, 0, 0, MULTI><<<grid, build_bt<true>(), 0, c->stream>>>(a);
-        else if (src == 1) k_build<true, 0, 1, MULTI><<<grid, build_bt<true>(), 0, c->stream>>>(a);
-        else k_build<true, 0, 2, MULTI><<<grid, build_bt<true>(), 0, c->stream>>>(a);
+        if (P.kernel == 1) k_build<true, 1, 0, MULTI><<<grid, bt, sm, c->stream>>>(a);
+        else if (src == 0) k_build<true, 0, 0, MULTI><<<grid, bt, sm, c->stream>>>(a);
+        else if (src == 1) k_build<true, 0, 1, MULTI><<<grid, bt, sm, c->stream>>>(a);
+        else k_build<true, 0, 2, MULTI><<<grid, bt, sm, c->stream>>>(a);
     } else {
-        if (P.kernel == 1) k_build<false, 1, 0, MULTI><<<grid, build_bt<false>(), 0, c->stream>>>(a);
-        else if (src == 0) k_build<false, 0, 0, MULTI><<<grid, build_bt<false>(), 0, c->stream>>>(a);
-        else if (src == 1) k_build<false, 0, 1, MULTI><<<grid, build_bt<false>(), 0, c->stream>>>(a);
-        else k_build<false, 0, 2, MULTI><<<grid, build_bt<false>(), 0, c->stream>>>(a);
+        if (P.kernel == 1) k_build<false, 1, 0, MULTI><<<grid, bt, sm, c->stream>>>(a);
+        else if (src == 0) k_build<false, 0, 0, MULTI><<<grid, bt, sm, c->stream>>>(a);
+        else if (src == 1) k_build<false, 0, 1, MULTI><<<grid, bt, sm, c->stream>>>(a);
+        else k_build<false, 0, 2, MULTI><<<grid, bt, sm, c->stream>>>(a);
     }
 }
 
@@ -906,12 +920,11 @@ void launch_build_rows(Ctx* c) {
     a.diag = c->diag;
     a.diag32 = c->diag32;
     a.p = c->p;
-    const int bt = P.precision == 1 ? build_bt<true>() : build_bt<false>();
-    const int grid = (int)((c->n + bt - 1) / bt);
+
     a.sid = c->sid;
     a.scn = c->scn;
-    if (c->n_scenes > 1) launch_build_t<true>(c, a, grid);
-    else launch_build_t<false>(c, a, grid);
+    if (c->n_scenes > 1) launch_build_t<true>(c, a);
+    else launch_build_t<false>(c, a);
     c->launches += 1;
 }
 
