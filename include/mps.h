@@ -134,6 +134,10 @@ typedef struct {
                                * kernels per iteration; 1 two (fused: the recurrences of      *
                                * Chronopoulos and Gear; rounds differently, same stop rule)    */
     int32_t spmv_block;       /* threads per block of the FP32 SpMV: 256 or 512; 0: 512         */
+    int32_t build_block;      /* threads per block of the row build (n*, flags, PPE rows): 64, *
+                               * 128 or 256; 0: 128 on the mixed PPE path (whose blocks stage  *
+                               * their output rows in shared memory), 256 elsewhere (tuning    *
+                               * only, results identical)                                      */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;
@@ -335,26 +339,38 @@ int mps_create_ensemble(const double* pos, const double* vel, const int8_t* type
 /* Autotuning (a tool of this library; the paper has none): times the launch shapes and the
  * inner solver's form on the current state with CUDA events on the context's stream
  * (`repeats` timed runs each after one untimed run) and keeps the fastest:
+ *   - after at least one step, the cell side h = max(re)(1 + s) (Sec. 4.1's bucket size):
+ *     the cell skin s among 0.05, 0.1, 0.15, 0.2, 0.3 and the context's own, no smaller
+ *     than twice the candidate-list skin the last step's motion asked for, timed as a
+ *     bucket build plus a candidate gather; the grid (cells per axis, cell table, candidate
+ *     list capacity) is derived again for each, and afterwards params.cell_skin is the
+ *     chosen s (so a step's MPS_ESKIN limit is s max(re)/2 of that s);
  *   - the candidate gather's cell block: 32, 64, 96 or 128 threads (params.gather_block);
+ *   - the row build's block: 64, 128 or 256 threads (params.build_block);
  *   - mixed PPE only, on the system of a solve at the current state: the FP32 SpMV's block,
  *     256 or 512 threads, and the inner CG as three kernels per iteration (SpMV; x, r
  *     update; direction update) or two (the recurrences of Chronopoulos and Gear: SpMV of
  *     the residual; one pass updating direction, A-direction, x and r), the latter for the
  *     device-driven solve only.
- * Candidate lists and the solve's stop rule are the same whatever the choice; the fused CG
- * rounds differently, so a solve's result changes within its tolerance.  Afterwards the
+ * Neighbour sets and the solve's stop rule are the same whatever the choice; the fused CG,
+ * and another cell side (its candidates come in another order), round differently, so a
+ * solve's result changes within its tolerance.  Afterwards the
  * state is reordered as by a step's bucket build and p, n* and flags are those of a solve at
  * the current state (positions and velocities are not advanced).  *out (nullable) receives
- * the choice and its times.  Errors: MPS_EINVAL (repeats < 1), MPS_EDEVICE, and the errors
- * of the solve. */
+ * the choice and its times.  Errors: MPS_EINVAL (repeats < 1), MPS_ENOMEM (the cell table
+ * or candidate lists of another cell side; the context keeps its cells then), MPS_EDEVICE,
+ * and the errors of the solve. */
 typedef struct {
     int32_t gather_block;   /* threads per cell block of the candidate gather                */
     int32_t spmv_block;     /* threads per block of the FP32 SpMV of the mixed inner CG      */
     int32_t cg_fused;       /* 1: the inner CG in two kernels per iteration, 0: three        */
-    int32_t pad;
+    int32_t build_block;    /* threads per block of the row build                            */
     double gather_ms;       /* the chosen gather's time [ms]                                 */
     double spmv_ms;         /* the chosen SpMV's time [ms] (0 without a mixed PPE)            */
     double solve_ms;        /* a mixed solve's time with the chosen form [ms] (0 without)     */
+    double build_ms;        /* the chosen row build's time [ms]                              */
+    double cell_skin;       /* the chosen cell skin s (cell side h = max(re)(1 + s))         */
+    double cell_ms;         /* bucket build + candidate gather with the chosen cells [ms]    */
 } mps_tuning;
 int mps_autotune(mps_ctx* ctx, int32_t repeats, mps_tuning* out);
 

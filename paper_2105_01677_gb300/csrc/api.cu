@@ -160,6 +160,9 @@ int check_params(const mps_params* P) {
     if (P->cg_x0 < 0 || P->cg_x0 > 3) return MPS_EINVAL;
     if (P->inner_cg < 0 || P->inner_cg > 1) return MPS_EINVAL;
     if (P->spmv_block != 0 && P->spmv_block != 256 && P->spmv_block != 512) return MPS_EINVAL;
+    if (P->build_block != 0 && P->build_block != 64 && P->build_block != 128 &&
+        P->build_block != 256)
+        return MPS_EINVAL;
     if (P->kernel < 0 || P->kernel > 1 || P->gradient_form < 0 || P->gradient_form > 1 ||
         P->source_term < 0 || P->source_term > 2 || (P->source_term >= 1 && P->kernel != 0))
         return MPS_EINVAL;
@@ -365,6 +368,8 @@ int allocate(Ctx* c) {
     A(scn, (size_t)c->n_scenes) A(scene_sums, 2 * (size_t)c->n_scenes)
     if (c->n_scenes > 1) { A(sid, n) A(sid_id, n) }
     if (c->prm.pressure_mode == 0 && c->prm.source_term == 2) { A(ecs_nk, n) A(ecs_dk, n) }
+    c->cap_v_alloc = c->cap_v;
+    c->ntable_alloc = c->ntable;
     A(key, n) A(key_alt, n) A(perm, n) A(perm_alt, n)
     const int64_t tiles = ((int64_t)n + 2047) / 2048;
     A(hist, 256 * tiles) A(hist_scan, 256 * tiles)
@@ -387,6 +392,86 @@ int allocate(Ctx* c) {
     MPS_CUDA(c, cudaMemsetAsync(c->phat, 0, n * sizeof(double), c->stream));
     MPS_CUDA(c, cudaMemcpyAsync(c->scn, c->scn_host.data(), sizeof(SceneParams) * c->scn_host.size(),
                                 cudaMemcpyHostToDevice, c->stream));
+    return MPS_OK;
+}
+
+// The grid of another cell skin s (the tuner's choice of the cell side h = max(re)(1 + s)):
+// cells per axis, Morton bits, the cell table, the FP32 bands and the candidate-list capacity
+// are derived again; the cell table, its scan scratch and the candidate lists are allocated
+// again when they grow.  The state keeps its slot order; the next bucket build sorts it into
+// the new cells and the next step gathers its lists afresh.  On failure the previous grid
+// stays in force.
+int regrid(Ctx* c, double skin) {
+    if (skin == c->prm.cell_skin) return MPS_OK;
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));   // nothing in flight on the old buffers
+    const double old_skin = c->prm.cell_skin, list_skin = c->list_skin;
+    const mps_scene* sc = c->n_scenes > 1 ? c->scenes_host.data() : nullptr;
+    auto restore = [&](int rc) {
+        c->prm.cell_skin = old_skin;
+        setup(c, sc, c->n_scenes);   // the derivation that succeeded before
+        c->list_skin = list_skin;
+        return rc;
+    };
+    c->prm.cell_skin = skin;
+    int rc = setup(c, sc, c->n_scenes);
+    if (rc) return restore(rc);
+    int32_t* vl_col = nullptr;
+    uint32_t *cell_count = nullptr, *scan_scratch = nullptr;
+    int32_t* cell_start = nullptr;
+    const size_t n = (size_t)c->n;
+    if (c->cap_v > c->cap_v_alloc &&
+        (rc = alloc_dev(c, &vl_col, sell_size(c->n, c->cap_v))))
+        return restore(rc);
+    if (c->ntable > c->ntable_alloc) {
+        const int64_t tiles = ((int64_t)n + 2047) / 2048;
+        const int64_t sw = std::max(std::max(scan_scratch_words(256 * tiles),
+                                             scan_scratch_words(c->ntable + 1)),
+                                    scan_scratch_words((int64_t)n + 1));
+        if ((rc = alloc_dev(c, &cell_count, (size_t)c->ntable)) ||
+            (rc = alloc_dev(c, &cell_start, (size_t)c->ntable + 1)) ||
+            (rc = alloc_dev(c, &scan_scratch, (size_t)sw))) {
+            free_one(c, vl_col);
+            free_one(c, cell_count);
+            free_one(c, cell_start);
+            return restore(rc);
+        }
+    }
+    // the graphs captured the old grid (keys, table size, sort passes) and buffers
+    bucket_graphs_destroy(c);
+    step_graphs_destroy(c);
+    if (vl_col) {
+        free_one(c, c->vl_col);
+        c->vl_col = vl_col;
+        c->cap_v_alloc = c->cap_v;
+    }
+    if (cell_count) {
+        free_one(c, c->cell_count);
+        free_one(c, c->cell_start);
+        free_one(c, c->scan_scratch);
+        c->cell_count = cell_count;
+        c->cell_start = cell_start;
+        c->scan_scratch = scan_scratch;
+        c->ntable_alloc = c->ntable;
+    }
+    c->list_skin = std::min(list_skin, skin);
+    c->scn_skin = -1.0;
+    c->need_list = true;
+    MPS_CUDA(c, cudaMemcpyAsync(c->scn, c->scn_host.data(), sizeof(SceneParams) * c->scn_host.size(),
+                                cudaMemcpyHostToDevice, c->stream));
+    if (c->rv_var) {
+        // the step graph's table of candidate radii: the full-skin half follows s, the
+        // adaptive half is written again before the next graph step
+        const size_t S = (size_t)c->n_scenes;
+        for (size_t k = 0; k < S; k++) {
+            const SceneParams& sp = c->scn_host[k];
+            c->rv_var_host[S + k] =
+                make_radius(std::max(sp.rn.re, sp.rl.re) * (1.0 + skin), c->band_x);
+        }
+        MPS_CUDA(c, cudaMemcpyAsync(c->rv_var + S, c->rv_var_host + S, sizeof(Radius) * S,
+                                    cudaMemcpyHostToDevice, c->stream));
+        c->rv_var_skin = -1.0;
+    }
+    MPS_CUDA(c, cudaStreamSynchronize(c->stream));
     return MPS_OK;
 }
 
@@ -474,6 +559,23 @@ void stage_collect(Ctx* c, const bool* used) {
 }
 
 constexpr double kMinListSkin = 0.02;
+
+// Candidate lists of the next gather within max(re)(1 + skin) of every scene, with the FP32
+// bands of the grid in force.
+int set_candidate_radius(Ctx* c, double skin) {
+    c->gathered_skin = skin;
+    if (c->n_scenes == 1) {
+        c->r_v = make_radius(c->re_skin * (1.0 + skin), c->band_x);
+    } else if (skin != c->scn_skin) {
+        for (SceneParams& sp : c->scn_host)
+            sp.rv = make_radius(std::max(sp.rn.re, sp.rl.re) * (1.0 + skin), c->band_x);
+        MPS_CUDA(c, cudaMemcpyAsync(c->scn, c->scn_host.data(),
+                                    sizeof(SceneParams) * c->scn_host.size(),
+                                    cudaMemcpyHostToDevice, c->stream));
+        c->scn_skin = skin;
+    }
+    return MPS_OK;
+}
 }  // namespace
 
 // One step (advance) or steps 1-5 only (solve).
@@ -514,18 +616,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         }
         launch_copy_state_star(c);
         if (fresh) {
-            c->gathered_skin = adapt ? c->list_skin : P.cell_skin;
-            if (c->n_scenes == 1) {
-                c->r_v = make_radius(re_max * (1.0 + c->gathered_skin), c->band_x);
-            } else if (c->gathered_skin != c->scn_skin) {
-                for (SceneParams& sp : c->scn_host)
-                    sp.rv = make_radius(std::max(sp.rn.re, sp.rl.re) * (1.0 + c->gathered_skin),
-                                        c->band_x);
-                MPS_CUDA(c, cudaMemcpyAsync(c->scn, c->scn_host.data(),
-                                            sizeof(SceneParams) * c->scn_host.size(),
-                                            cudaMemcpyHostToDevice, c->stream));
-                c->scn_skin = c->gathered_skin;
-            }
+            if ((rc = set_candidate_radius(c, adapt ? c->list_skin : P.cell_skin))) return rc;
             MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), c->stream));
             stage_begin(c, MPS_STAGE_GATHER);
             launch_verlet(c);                                          // candidates at r_b = r^k
@@ -723,6 +814,7 @@ int mps_create(const double* pos, const double* vel, const int8_t* types, int64_
     c->steps_done = 0;
     c->cg_fused = params->inner_cg == 1;
     c->spmv_block = params->spmv_block ? params->spmv_block : 512;
+    c->build_block = params->build_block;
     c->last_cg_iters = 8;
     if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, params->device) != cudaSuccess) {
         delete c;
@@ -738,7 +830,7 @@ int mps_create(const double* pos, const double* vel, const int8_t* types, int64_
         }
         c->own_stream = true;
     }
-    if ((rc = setup(c, nullptr, 1)) || (rc = allocate(c)) ||
+    if ((rc = setup(c, nullptr, 1)) || (rc = allocate(c)) || (rc = build_rows_init(c)) ||
         (rc = upload_state(c, pos, vel, types, false))) {
         mps_destroy(c);
         return rc;
@@ -776,6 +868,8 @@ int mps_create_ensemble(const double* pos, const double* vel, const int8_t* type
     c->prm = P;
     c->cg_fused = P.inner_cg == 1;
     c->spmv_block = P.spmv_block ? P.spmv_block : 512;
+    c->build_block = P.build_block;
+    c->scenes_host.assign(scenes, scenes + n_scenes);
     c->n = n;
     c->steps_done = 0;
     c->last_cg_iters = 8;
@@ -793,7 +887,7 @@ int mps_create_ensemble(const double* pos, const double* vel, const int8_t* type
         }
         c->own_stream = true;
     }
-    if ((rc = setup(c, scenes, n_scenes)) || (rc = allocate(c))) {
+    if ((rc = setup(c, scenes, n_scenes)) || (rc = allocate(c)) || (rc = build_rows_init(c))) {
         mps_destroy(c);
         return rc;
     }
@@ -842,12 +936,54 @@ int mps_autotune(mps_ctx* c, int32_t repeats, mps_tuning* out) {
         return MPS_OK;
     };
     const size_t n = (size_t)c->n;
-    // ---- the candidate gather's block shape, on the current state
+    // ---- the cell side (after a step: the list skin then reflects the motion), timed as a
+    // bucket build plus a candidate gather at the list skin of the next step
+    t.cell_skin = c->prm.cell_skin;
     rc = [&]() -> int {
+        if (c->steps_done < 1) return MPS_OK;
+        const double s0 = c->prm.cell_skin;
+        const double lo = std::max(0.05, 2.0 * c->list_skin);
+        std::vector<double> cand{s0};
+        for (double s : {0.05, 0.1, 0.15, 0.2})
+            if (s >= lo && std::fabs(s - s0) > 1e-12) cand.push_back(s);
+        if (cand.size() < 2) return MPS_OK;
+        double best = s0;
+        float best_ms = 1e30f;
+        int r2;
+        for (double s : cand) {
+            r2 = regrid(c, s);
+            if (r2 == MPS_ENOMEM) continue;   // the tables of a finer grid do not fit
+            if (r2) return r2;
+            if ((r2 = set_candidate_radius(c, c->list_skin))) return r2;
+            auto run = [&]() -> int {
+                MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
+                int r3 = bucket_build(c, true);
+                if (r3) return r3;
+                MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), c->stream));
+                launch_verlet(c);
+                return MPS_OK;
+            };
+            // both buffer parities' bucket graphs captured before the timed runs
+            if ((r2 = run()) || (r2 = run())) return r2;
+            float ms = 0.f;
+            if ((r2 = time_of(run, &ms))) return r2;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = s;
+            }
+        }
+        if ((r2 = regrid(c, best))) return r2;
+        t.cell_skin = best;
+        t.cell_ms = best_ms;
+        return MPS_OK;
+    }();
+    // ---- the candidate gather's block shape, on the current state
+    if (!rc) rc = [&]() -> int {
         MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), c->stream));
         int r2 = bucket_build(c, true);
         if (r2) return r2;
         c->need_list = true;
+        if ((r2 = set_candidate_radius(c, c->list_skin))) return r2;
         const int shapes[4] = {32, 64, 96, 128};
         int best = c->prm.gather_block;
         float best_ms = 1e30f;
@@ -870,9 +1006,37 @@ int mps_autotune(mps_ctx* c, int32_t repeats, mps_tuning* out) {
         t.gather_ms = best_ms;
         return MPS_OK;
     }();
+    // ---- the row build's block, on the lists just gathered and the prediction from them
+    if (!rc) rc = [&]() -> int {
+        MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), c->stream));
+        launch_verlet(c);
+        launch_copy_state_star(c);
+        launch_predict_rows(c);
+        if (c->prm.pressure_mode == 0 && c->prm.source_term == 2) launch_ecs_rates(c);
+        int best = build_block_of(c), r2;
+        float best_ms = 1e30f;
+        for (int b : {64, 128, 256}) {
+            c->build_block = b;
+            float ms = 0.f;
+            r2 = time_of([&]() -> int {
+                launch_build_rows(c);
+                return MPS_OK;
+            }, &ms);
+            if (r2) return r2;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = b;
+            }
+        }
+        c->build_block = best;
+        t.build_block = best;
+        t.build_ms = best_ms;
+        return MPS_OK;
+    }();
     // ---- the mixed PPE: the FP32 SpMV's block size and the inner CG's form, on the system
     // of a solve at the current state (the state is not advanced)
-    if (!rc && c->prm.pressure_mode == 0 && c->prm.precision == 1) {
+    const bool mixed_ppe = c->prm.pressure_mode == 0 && c->prm.precision == 1;
+    if (!rc && mixed_ppe) {
         rc = [&]() -> int {
             mps_report rep;
             std::memset(&rep, 0, sizeof rep);
@@ -920,6 +1084,13 @@ int mps_autotune(mps_ctx* c, int32_t repeats, mps_tuning* out) {
     } else {
         t.spmv_block = c->spmv_block;
         t.cg_fused = c->cg_fused ? 1 : 0;
+        if (!rc) {
+            // p, n* and flags of a solve at the current state, as after the mixed PPE's tuning
+            mps_report rep;
+            std::memset(&rep, 0, sizeof rep);
+            rc = do_step(c, false, &rep);
+            if (rc == MPS_ECG_NOCONV) rc = MPS_OK;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -176,6 +176,9 @@ void launch_debug_neighbors(Ctx* c, const Radius& r, const int64_t* row_off, int
 // ---------------------------------------------------------------- rows.cu
 void launch_predict_rows(Ctx* c);
 void launch_build_rows(Ctx* c);
+// threads per block of the row build; the functions' shared-memory limits (once per context)
+int build_block_of(const Ctx* c);
+int build_rows_init(Ctx* c);
 
 // ---------------------------------------------------------------- ppe.cu
 int ppe_solve(Ctx* c, mps_report* rep);
@@ -331,13 +334,7 @@ struct Ctx {
     AdjBuffers adj;
     PpeGraph ppe_graph[2];
     BucketGraph bucket_graph[2];
-    // the candidate and predicate bands of radius re for coordinates up to X (api.cu)
-Radius make_radius(double re, double X);
-// candidate lists completed for particles beyond the full skin (skinpatch.cu)
-int skin_patch_cap(const Ctx* c);
-void launch_fast_mark(Ctx* c, double half);
-int launch_fast_patch(Ctx* c, int n_fast, float hv2);
-// whole steps as CUDA graphs (stepgraph.cu): the control block (device and pinned host
+    // whole steps as CUDA graphs (stepgraph.cu): the control block (device and pinned host
     // mirror), the two scene tables of an ensemble (adaptive and full list skin), the pinned
     // copy of the per-scene residual sums, and the control block kernels read while a step
     // is being captured (null otherwise)
@@ -428,6 +425,12 @@ int launch_fast_patch(Ctx* c, int n_fast, float hv2);
     // tuned by mps_autotune: the FP32 SpMV's block size and the inner CG's form
     int spmv_block = 512;
     bool cg_fused = false;
+    int build_block = 0;    // the row build's block (0: the path's default)
+    // capacities the grid-sized buffers were allocated with (the tuner's cell side may
+    // derive smaller ones), and an ensemble's scenes (to derive its grid again)
+    int cap_v_alloc = 0;
+    int64_t ntable_alloc = 0;
+    std::vector<mps_scene> scenes_host;
     float2* cg_xhl;         // mixed: the FP64 iterate as float-float (hi, lo) for the outer residual
     double* partials;       // per-block partial sums
     CgScalars* cg;          // device

@@ -34,9 +34,10 @@ namespace mps {
 
 namespace {
 constexpr int kBT = 128;
-// the build's blocks: 256 rows of neighbouring particles share more of their candidates in
-// L1 (5% faster than 128 on the 3D dam break; the prediction is faster at 128); the mixed
-// build with the PPE takes 128, its output staging ring (RowStage) being deep
+// the build's blocks (defaults; params.build_block and the autotuner choose 64, 128 or 256):
+// 256 rows of neighbouring particles share more of their candidates in L1 (5% faster than
+// 128 on the 3D dam break; the prediction is faster at 128); the mixed build with the PPE
+// takes 128, its output staging ring (RowStage) being deep
 constexpr int kBuildBT = 256;
 constexpr int kBuildRingBT = 128;
 
@@ -299,7 +300,8 @@ struct RowStage {
     __device__ float* lo(int e) const { return l + e * bt; }
     __device__ int32_t* ncol(int e) const { return nc + e * bt; }
 };
-constexpr size_t kRingBytes = 4 * kRing * kBuildRingBT * sizeof(int32_t);
+// dynamic shared memory of the ring for a block of bt threads (64 KB at 256 threads)
+constexpr size_t ring_bytes(int bt) { return 4 * kRing * (size_t)bt * sizeof(int32_t); }
 
 // Entry flags while a PPE row is being assembled (slots are < 2^30)
 constexpr int kEntryN = 1 << 30;   // within re_n: contributes to n*
@@ -329,8 +331,8 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
     // evaluated (reported as 0)
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = tid < (int)*a.nrows ? a.rows[tid] : -1;
-    // mixed with the PPE: the row-output ring (launched with kBuildRingBT threads and
-    // kRingBytes of dynamic shared memory; other launches pass none and never touch it)
+    // mixed with the PPE: the row-output ring (ring_bytes(blockDim.x) of dynamic shared
+    // memory; other launches pass none and never touch it)
     extern __shared__ __align__(16) int32_t s_ring[];
     const int rbt = (int)blockDim.x;
     const RowStage stage{s_ring, (float*)(s_ring + kRing * rbt), (float*)(s_ring + 2 * kRing * rbt),
@@ -845,14 +847,30 @@ void launch_predict_rows(Ctx* c) {
 
 // (kernel, source): (0, 0), (0, 1), (0, 2), (1, 0); the cubic weight with HS is rejected
 template <bool MULTI>
+static int allow_ring_t(Ctx* c) {
+    // the ring of a 256-thread block (64 KB) is above the default 48 KB of dynamic shared
+    // memory of a launch
+    const int b = (int)ring_bytes(256);
+    MPS_CUDA(c, cudaFuncSetAttribute(k_build<true, 1, 0, MULTI>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    MPS_CUDA(c, cudaFuncSetAttribute(k_build<true, 0, 0, MULTI>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    MPS_CUDA(c, cudaFuncSetAttribute(k_build<true, 0, 1, MULTI>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    MPS_CUDA(c, cudaFuncSetAttribute(k_build<true, 0, 2, MULTI>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, b));
+    return MPS_OK;
+}
+
+template <bool MULTI>
 static void launch_build_t(Ctx* c, const BuildArgs& a) {
     const mps_params& P = c->prm;
     // the source term enters the PPE only: an equation-of-state step takes the standard one
     // (the ECS rates are not even allocated then)
     const int src = P.pressure_mode == 0 ? P.source_term : 0;
     const bool ring = P.precision == 1 && P.pressure_mode == 0;
-    const int bt = ring ? kBuildRingBT : kBuildBT;
-    const size_t sm = ring ? kRingBytes : 0;
+    const int bt = build_block_of(c);
+    const size_t sm = ring ? ring_bytes(bt) : 0;
     const int grid = (int)((c->n + bt - 1) / bt);
     if (P.precision == 1) {
         if (P.kernel == 1) k_build<true, 1, 0, MULTI><<<grid, bt, sm, c->stream>>>(a);
@@ -865,6 +883,16 @@ static void launch_build_t(Ctx* c, const BuildArgs& a) {
         else if (src == 1) k_build<false, 0, 1, MULTI><<<grid, bt, sm, c->stream>>>(a);
         else k_build<false, 0, 2, MULTI><<<grid, bt, sm, c->stream>>>(a);
     }
+}
+
+int build_block_of(const Ctx* c) {
+    if (c->build_block) return c->build_block;
+    return (c->prm.precision == 1 && c->prm.pressure_mode == 0) ? kBuildRingBT : kBuildBT;
+}
+
+int build_rows_init(Ctx* c) {
+    int rc = allow_ring_t<false>(c);
+    return rc ? rc : allow_ring_t<true>(c);
 }
 
 void launch_build_rows(Ctx* c) {

@@ -57,12 +57,16 @@ int main(void) {
   printf("mps_params size %zu\n", sizeof(mps_params));
   printf("mps_report size %zu\n", sizeof(mps_report));
   printf("mps_vjp_report size %zu\n", sizeof(mps_vjp_report));
+  printf("mps_tuning size %zu\n", sizeof(mps_tuning));
   P(mps_params, dim) P(mps_params, l0) P(mps_params, g) P(mps_params, cg_max_iter)
   P(mps_params, precision) P(mps_params, nbr_cap) P(mps_params, cell_skin) P(mps_params, box_min)
   P(mps_params, box_max) P(mps_params, inner_tol) P(mps_params, ppe_operator) P(mps_params, stream)
   P(mps_params, alloc) P(mps_params, release) P(mps_params, alloc_user) P(mps_params, list_every)
   P(mps_params, gather_block) P(mps_params, kernel) P(mps_params, source_term)
-  P(mps_params, ppe_host_loop) P(mps_params, cg_x0)
+  P(mps_params, ppe_host_loop) P(mps_params, cg_x0) P(mps_params, spmv_block)
+  P(mps_params, build_block)
+  P(mps_tuning, build_block) P(mps_tuning, gather_ms) P(mps_tuning, build_ms)
+  P(mps_tuning, cell_skin) P(mps_tuning, cell_ms)
   P(mps_report, list_gathered)
   P(mps_report, cg_resid) P(mps_report, n_surface) P(mps_report, max_disp) P(mps_report, lambda)
   P(mps_report, steps_done) P(mps_report, cand_tests) P(mps_report, pairs_pnd)
@@ -89,8 +93,9 @@ def test_struct_layout_matches_binding():
     assert lay[("mps_params", "size")] == C.sizeof(mps.mps_params)
     assert lay[("mps_report", "size")] == C.sizeof(mps.mps_report)
     assert lay[("mps_vjp_report", "size")] == C.sizeof(mps.mps_vjp_report)
+    assert lay[("mps_tuning", "size")] == C.sizeof(mps.mps_tuning)
     classes = {"mps_params": mps.mps_params, "mps_report": mps.mps_report,
-               "mps_vjp_report": mps.mps_vjp_report}
+               "mps_vjp_report": mps.mps_vjp_report, "mps_tuning": mps.mps_tuning}
     for (s, f), off in lay.items():
         if f == "size":
             continue
@@ -114,7 +119,9 @@ def test_invalid_arguments_rejected_before_device_use(L):
     for kw in (dict(dim=4), dict(re_n=0.0), dict(dt=-1.0), dict(precision=2),
                dict(box_max=(0.0, 0.0, 0.0)), dict(list_every=-1), dict(kernel=2),
                dict(gradient_form=3), dict(source_term=1, kernel=1), dict(source_term=3),
-               dict(precision=1, ppe_operator=1, kernel=1), dict(cg_x0=4), dict(cg_x0=-1), dict(ppe_host_loop=2)):
+               dict(precision=1, ppe_operator=1, kernel=1), dict(cg_x0=4), dict(cg_x0=-1), dict(ppe_host_loop=2),
+               dict(build_block=96), dict(build_block=512), dict(spmv_block=128),
+               dict(gather_block=48)):
         P = mps.mps_params_default(**kw)
         rc = L.mps_create(pos.ctypes.data_as(C.POINTER(C.c_double)), None,
                           t.ctypes.data_as(C.POINTER(C.c_int8)), 3, C.byref(P), C.byref(h))

@@ -5,15 +5,22 @@
   so they are held to the mixed-precision bound against the FP64 oracle (p: relative L2 over
   fluid <= 1e-5, positions <= 1e-6 l0), on the regularised and on the stiff PPE, one scene
   and an ensemble, and must reach the same FP64 residual.
-- mps_autotune returns a valid choice with its times, and an ensemble stepped after tuning
-  keeps every scene within its tolerance and within the mixed bound of the oracle."""
+- The row build's block (64, 128 or 256 threads) changes nothing: every row is one thread's
+  walk over its candidate list, so results are bit-identical.
+- The cell side h = max(re)(1 + s) changes the candidates' order, not the neighbour sets:
+  FP64 parity with the oracle at other cell skins.
+- mps_autotune returns a valid choice with its times (cell side, gather block, build block,
+  SpMV block, inner-CG form); a scene or an ensemble stepped after tuning keeps its
+  tolerance and stays within the mixed bound of the oracle, and the grid in force is the one
+  of the chosen cell skin."""
 import numpy as np
 import pytest
 
 import __graft_entry__
 import oracle
 import scenes
-from _parity import PARITY_CG_TOL, gpu_params, oracle_params, run_gpu, run_oracle, small_3d
+from _parity import (FP64_TOL, PARITY_CG_TOL, gpu_params, oracle_params, rel_err, run_gpu,
+                     run_oracle, small_3d)
 
 pytestmark = pytest.mark.gpu
 
@@ -85,6 +92,8 @@ def test_autotune_mixed_ensemble():
         assert t["spmv_block"] in (256, 512)
         assert t["cg_fused"] in (0, 1)
         assert t["gather_ms"] > 0 and t["spmv_ms"] > 0 and t["solve_ms"] > 0
+        assert t["build_block"] in (64, 128, 256) and t["build_ms"] > 0
+        assert t["cell_skin"] in (0.1, 0.05, 0.15, 0.2) and t["cell_ms"] > 0
         for _ in range(3):
             rc, rep = ens.step(1)
             assert rc == 0 and rep["step_graph"] == 1
@@ -107,3 +116,67 @@ def test_autotune_mixed_ensemble():
         assert ep <= 1e-4, (k, ep)     # five steps of drift at the mixed bound
         assert ex <= 1e-6, (k, ex)
     del before
+
+
+@pytest.mark.parametrize("bb", [64, 128, 256])
+@pytest.mark.parametrize("case", ["2d-fp64", "3d-mixed", "3d-eos-mixed"])
+def test_build_block_changes_nothing(case, bb):
+    if case == "2d-fp64":
+        sc, kw = scenes.dam_break_2d(seed=1), dict(precision=0)
+    elif case == "3d-mixed":
+        sc, kw = small_3d(seed=2), dict(precision=1, dt=5e-5)
+    else:
+        sc, kw = small_3d(seed=3), dict(precision=1, dt=5e-5, pressure_mode=1)
+    outs = []
+    for b in (0, bb):
+        rc, rep, st, _ = run_gpu(sc, nsteps=2, **gpu_params(sc, cg_x0=0, build_block=b, **kw))
+        assert rc == 0
+        outs.append(st)
+    for key in ("p", "n_star", "pos", "vel", "flags"):
+        assert np.array_equal(outs[0][key], outs[1][key]), key
+
+
+@pytest.mark.parametrize("skin", [0.05, 0.2])
+def test_other_cell_side_fp64_parity(skin):
+    sc = small_3d(seed=5)
+    rc, rep, got, consts = run_gpu(sc, **gpu_params(sc, precision=0, cg_tol=PARITY_CG_TOL,
+                                                     dt=5e-5, cell_skin=skin))
+    orep, ost, prm = run_oracle(sc, cg_tol=PARITY_CG_TOL, dt=5e-5)
+    assert rc == 0
+    assert consts["h"] == pytest.approx(4.0 * sc.l0 * (1.0 + skin), rel=1e-12)
+    for key, ref in (("p", ost.p), ("vel", ost.vel)):
+        assert rel_err(got[key], ref) <= FP64_TOL, key
+    assert np.array_equal(got["flags"], ost.flags)
+
+
+def test_autotune_single_scene_cell_side_and_build_block():
+    """Created with cell skin 0.3 (not among the tuner's own candidates, so the tuner derives
+    other grids and comes back to one of them); the grid afterwards is that of the choice."""
+    from paper_2105_01677_gb300 import mps
+    sc = small_3d(seed=6)
+    sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
+                         **gpu_params(sc, precision=1, dt=5e-5, cg_tol=1e-8, cg_x0=3,
+                                      cell_skin=0.3))
+    try:
+        sim.step(2)
+        t = sim.autotune(2)
+        assert t["cell_skin"] in (0.3, 0.05, 0.1, 0.15, 0.2)
+        assert t["build_block"] in (64, 128, 256)
+        assert t["cell_ms"] > 0 and t["build_ms"] > 0 and t["gather_ms"] > 0
+        c = sim.constants()
+        assert c["h"] == pytest.approx(4.0 * sc.l0 * (1.0 + t["cell_skin"]), rel=1e-12)
+        for _ in range(3):
+            rc, rep = sim.step(1)
+            assert rc == 0 and rep["cg_resid"] <= 1e-8
+        got = sim.read()
+    finally:
+        sim.close()
+    prm = oracle_params(sc, dt=5e-5, cg_tol=PARITY_CG_TOL)
+    st = oracle.State.from_scene(sc)
+    for _ in range(5):
+        oracle.step(prm, st)
+    f = sc.types == scenes.FLUID
+    ep = np.linalg.norm(got["p"][f] - st.p[f]) / np.linalg.norm(st.p[f])
+    ex = np.abs(got["pos"] - st.pos).max() / sc.l0
+    assert ep <= 1e-4, ep
+    assert ex <= 1e-6, ex
