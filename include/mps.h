@@ -138,6 +138,10 @@ typedef struct {
                                * 128 or 256; 0: 128 on the mixed PPE path (whose blocks stage  *
                                * their output rows in shared memory), 256 elsewhere (tuning    *
                                * only, results identical)                                      */
+    int32_t bucket_sort;      /* graph-run bucket builds: 0 (default) sort the particles whose *
+                               * cell changed and merge them into the previous order when it   *
+                               * holds (the radix sort otherwise); 1 always the radix sort.    *
+                               * Both give the stable order by cell key: results identical.   */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;

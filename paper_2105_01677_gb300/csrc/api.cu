@@ -163,6 +163,7 @@ int check_params(const mps_params* P) {
     if (P->build_block != 0 && P->build_block != 64 && P->build_block != 128 &&
         P->build_block != 256)
         return MPS_EINVAL;
+    if (P->bucket_sort != 0 && P->bucket_sort != 1) return MPS_EINVAL;
     if (P->kernel < 0 || P->kernel > 1 || P->gradient_form < 0 || P->gradient_form > 1 ||
         P->source_term < 0 || P->source_term > 2 || (P->source_term >= 1 && P->kernel != 0))
         return MPS_EINVAL;
@@ -374,6 +375,9 @@ int allocate(Ctx* c) {
     const int64_t tiles = ((int64_t)n + 2047) / 2048;
     A(hist, 256 * tiles) A(hist_scan, 256 * tiles)
     A(cell_count, c->ntable) A(cell_start, c->ntable + 1) A(occ, n + 1)
+    c->mov_cap = (int)std::min<size_t>(n, 16384);
+    A(mvf, n) A(mov_key, c->mov_cap) A(mov_slot, c->mov_cap) A(mov_cnt, 4 * (size_t)c->mov_cap)
+    A(mov_by_slot, c->mov_cap) A(mov_by_key, c->mov_cap) A(order_ok, 1)
     A(mark_f, n + 1) A(mark_fw, n + 1) A(scan_f, n + 1) A(scan_fw, n + 1) A(rows_f, n) A(rows_fw, n)
     const int64_t sw = std::max(std::max(scan_scratch_words(256 * tiles), scan_scratch_words(c->ntable + 1)),
                                 scan_scratch_words((int64_t)n + 1));
@@ -456,6 +460,7 @@ int regrid(Ctx* c, double skin) {
     c->list_skin = std::min(list_skin, skin);
     c->scn_skin = -1.0;
     c->need_list = true;
+    c->order_valid = false;   // keys of another grid
     MPS_CUDA(c, cudaMemcpyAsync(c->scn, c->scn_host.data(), sizeof(SceneParams) * c->scn_host.size(),
                                 cudaMemcpyHostToDevice, c->stream));
     if (c->rv_var) {
@@ -511,6 +516,7 @@ int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* typ
         if (!c->st_host->differs) return MPS_OK;
     }
     c->need_list = true;
+    c->order_valid = false;   // slot = id: the next bucket build sorts from scratch
     launch_ingest(c, d_pos, d_vel, d_t, false, false);
     launch_gather_props(c);   // slot = id again
     c->guess_n = 0;   // a written state starts its solve from zero
@@ -522,6 +528,7 @@ int upload_state(Ctx* c, const double* pos, const double* vel, const int8_t* typ
 int read_status(Ctx* c) {
     MPS_CUDA(c, cudaMemcpyAsync(c->st_host, c->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+    bucket_branch_count(c, *c->st_host);
     return MPS_OK;
 }
 

@@ -25,12 +25,23 @@ constexpr int kTile = kBT * kItems;
 constexpr int kRadixBits = 8;
 constexpr int kDigits = 1 << kRadixBits;
 
+// Movers (the build from the previous order): mvf non-null records, per slot, whether its
+// key differs from the one the slot holds from the previous build, and appends up to
+// mov_cap of them as (key, slot) in arbitrary order (their count in st->n_mov).
+struct MoverOut {
+    uint8_t* mvf;
+    uint32_t* key;
+    int32_t* slot;
+    int cap;
+};
+
 __global__ void __launch_bounds__(kBT)
     k_cell_keys(double4* pos, double4* vel, int8_t* type, uint32_t* key, int32_t* slot, int n,
                 GridDesc g, DevStatus* st, int mutate, uint32_t outside_key, const uint16_t* sid,
-                const SceneParams* scn, uint32_t shift) {
+                const SceneParams* scn, uint32_t shift, MoverOut mo) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const uint32_t old_key = mo.mvf ? key[i] : 0u;
     double4 p = pos[i];
     int8_t t = type[i];
     if (mutate) {
@@ -71,6 +82,131 @@ __global__ void __launch_bounds__(kBT)
     if (mutate && k == outside_key) atomicAdd(&st->n_ghost, 1u);
     key[i] = k;
     if (slot) slot[i] = i;
+    if (mo.mvf) {
+        const bool moved = k != old_key;
+        mo.mvf[i] = moved ? 1 : 0;
+        if (moved) {
+            const unsigned q = atomicAdd(&st->n_mov, 1u);
+            if (q < (unsigned)mo.cap) {
+                mo.key[q] = k;
+                mo.slot[q] = i;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- the build from the
+// previous order.  The slots are sorted by their previous keys, with that build's cell table
+// (cs: the first slot of every key; the GHOST key, the table size, runs to n).  The stable
+// sort of the slots by their new keys -- the order the radix sort gives -- places
+//   a slot whose key did not change (a stayer) at s - #(movers m: s_m < s) +
+//       #(movers m: (k_m, s_m) < (k, s)): the stayers keep their relative order, and their
+//       keys are non-decreasing in slot order;
+//   a mover at #(stayers with (key, slot) < (k_m, s_m)) + #(movers before it), where the
+//       stayers of smaller keys are the slots before cs[k_m] less the movers among them, and
+//       the stayers of key k_m (all within [cs[k_m], cs_end[k_m]), where the mover is not)
+//       come before it when it lies after that range.
+// Counts between movers are all-pairs over tiles of 256 x 256 (the movers are few).
+__device__ __forceinline__ int old_end(const int32_t* cs, uint32_t k, uint32_t ghost_key, int n) {
+    return k < ghost_key ? cs[k + 1] : n;
+}
+
+__global__ void __launch_bounds__(kBT)
+    k_mov_count(const uint32_t* mkey, const int32_t* mslot, const DevStatus* st, int cap,
+                const int32_t* cs, uint32_t ghost_key, int n, uint32_t* cnt) {
+    const int M = (int)min(st->n_mov, (unsigned)cap);
+    const int T = (M + kBT - 1) / kBT;
+    __shared__ uint32_t s_k[kBT];
+    __shared__ int32_t s_s[kBT];
+    for (int t = blockIdx.x; t < T * T; t += gridDim.x) {
+        const int ti = t / T, tj = t - ti * T;
+        const int i = ti * kBT + threadIdx.x;
+        const int jn = min(kBT, M - tj * kBT);
+        __syncthreads();
+        if ((int)threadIdx.x < jn) {
+            s_k[threadIdx.x] = mkey[tj * kBT + threadIdx.x];
+            s_s[threadIdx.x] = mslot[tj * kBT + threadIdx.x];
+        }
+        __syncthreads();
+        if (i >= M) continue;
+        const uint32_t ki = mkey[i];
+        const int si = mslot[i];
+        const int a = ki <= ghost_key ? cs[ki] : n;
+        const int b = old_end(cs, ki, ghost_key, n);
+        uint32_t lt_ks = 0, lt_s = 0, lt_a = 0, in_r = 0;
+        for (int j = 0; j < jn; j++) {
+            const uint32_t kj = s_k[j];
+            const int sj = s_s[j];
+            lt_ks += (kj < ki || (kj == ki && sj < si)) ? 1u : 0u;
+            lt_s += sj < si ? 1u : 0u;
+            lt_a += sj < a ? 1u : 0u;
+            in_r += (sj >= a && sj < b) ? 1u : 0u;
+        }
+        atomicAdd(&cnt[4 * i + 0], lt_ks);
+        atomicAdd(&cnt[4 * i + 1], lt_s);
+        atomicAdd(&cnt[4 * i + 2], lt_a);
+        atomicAdd(&cnt[4 * i + 3], in_r);
+    }
+}
+
+__global__ void __launch_bounds__(kBT)
+    k_mov_place(const uint32_t* mkey, const int32_t* mslot, const DevStatus* st, int cap,
+                const int32_t* cs, uint32_t ghost_key, int n, const uint32_t* cnt,
+                int32_t* by_slot, unsigned long long* by_key, uint32_t* kout, int32_t* vout) {
+    const int M = (int)min(st->n_mov, (unsigned)cap);
+    for (int i = blockIdx.x * kBT + threadIdx.x; i < M; i += gridDim.x * kBT) {
+        const uint32_t ki = mkey[i];
+        const int si = mslot[i];
+        const int a = cs[ki];
+        const int b = old_end(cs, ki, ghost_key, n);
+        const uint32_t lt_ks = cnt[4 * i + 0], lt_s = cnt[4 * i + 1];
+        const uint32_t lt_a = cnt[4 * i + 2], in_r = cnt[4 * i + 3];
+        const int stay_before = (a - (int)lt_a) + (si >= b ? (b - a) - (int)in_r : 0);
+        const int dst = stay_before + (int)lt_ks;
+        by_slot[lt_s] = si;
+        by_key[lt_ks] = ((unsigned long long)ki << 32) | (unsigned)si;
+        kout[dst] = ki;
+        vout[dst] = si;
+    }
+}
+
+// first index in v[0, m) not below x
+template <class T>
+__device__ __forceinline__ int lower_bound(const T* v, int m, T x) {
+    int lo = 0, hi = m;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (v[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kBT)
+    k_stay_place(const uint32_t* kin, const uint8_t* mvf, int n, const DevStatus* st, int cap,
+                 const int32_t* by_slot, const unsigned long long* by_key, uint32_t* kout,
+                 int32_t* vout) {
+    const int s = blockIdx.x * kBT + threadIdx.x;
+    if (s >= n || mvf[s]) return;
+    const int M = (int)min(st->n_mov, (unsigned)cap);
+    const uint32_t k = kin[s];
+    int dst = s;
+    if (M > 0) {
+        dst += lower_bound(by_key, M, ((unsigned long long)k << 32) | (unsigned)s) -
+               lower_bound(by_slot, M, (int32_t)s);
+    }
+    kout[dst] = k;
+    vout[dst] = s;
+}
+
+// the branch of this build: the radix sort unless the previous order holds (the host's
+// word) and every mover was recorded
+__global__ void k_bucket_branch(const DevStatus* st, const int32_t* order_ok, int cap,
+                                cudaGraphConditionalHandle h_radix, cudaGraphConditionalHandle h_inc) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const bool inc = *order_ok != 0 && st->n_mov <= (unsigned)cap;
+    cudaGraphSetConditional(h_radix, inc ? 0u : 1u);
+    cudaGraphSetConditional(h_inc, inc ? 1u : 0u);
 }
 
 __global__ void __launch_bounds__(kBT)
@@ -212,124 +348,28 @@ void launch_cell_keys_only(Ctx* c, uint32_t* out_key) {
     // exported keys mark particles outside the grid (and GHOSTs) with 0xFFFFFFFF
     k_cell_keys<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(c->pos, c->vel, c->type, out_key,
                                                              nullptr, n, c->grid, c->st, 0,
-                                                             0xFFFFFFFFu, nullptr, nullptr, 0);
+                                                             0xFFFFFFFFu, nullptr, nullptr, 0,
+                                                             MoverOut{});
     c->launches += 1;
 }
 
-static int bucket_launches(Ctx* c, bool mutate);
-
-// The bucket build is ~25 short dependent kernels whose launch gaps cost more than their
-// work, so the stepping path replays it as one CUDA graph.  Every build swaps the state with
-// its alternate buffers (and the radix sort's keys and permutation with theirs when it
-// takes an odd number of passes), so there are two graphs, keyed by the position buffer
-// the build starts from; each remembers the buffer assignment its build leaves behind.
 namespace {
-struct BucketPtrs {
-    uint32_t *key, *key_alt;
-    int32_t *perm, *perm_alt;
-    double4 *pos, *pos_alt, *vel, *vel_alt;
-    int8_t *type, *type_alt;
-    int32_t *id, *id_alt;
-    double *p, *p_alt;
-    double *ph[Ctx::kGuessMax], *ph_alt[Ctx::kGuessMax];
-};
-BucketPtrs save_ptrs(const Ctx* c) {
-    return {c->key, c->key_alt, c->perm, c->perm_alt, c->pos, c->pos_alt, c->vel, c->vel_alt,
-            c->type, c->type_alt, c->id, c->id_alt, c->p, c->p_alt,
-            {c->ph[0], c->ph[1], c->ph[2]}, {c->ph_alt[0], c->ph_alt[1], c->ph_alt[2]}};
-}
-void load_ptrs(Ctx* c, const BucketPtrs& b) {
-    c->key = b.key; c->key_alt = b.key_alt; c->perm = b.perm; c->perm_alt = b.perm_alt;
-    c->pos = b.pos; c->pos_alt = b.pos_alt; c->vel = b.vel; c->vel_alt = b.vel_alt;
-    c->type = b.type; c->type_alt = b.type_alt; c->id = b.id; c->id_alt = b.id_alt;
-    c->p = b.p; c->p_alt = b.p_alt;
-    for (int k = 0; k < Ctx::kGuessMax; k++) {
-        c->ph[k] = b.ph[k];
-        c->ph_alt[k] = b.ph_alt[k];
-    }
-}
-}  // namespace
-
-int bucket_capture_launches(Ctx* c) { return bucket_launches(c, true); }
-
-void state_ptrs_save(const Ctx* c, void* rec) {
-    static_assert(sizeof(BucketPtrs) <= kPtrRecord, "pointer record too small");
-    const BucketPtrs b = save_ptrs(c);
-    std::memcpy(rec, &b, sizeof b);
+// ---- the stages of a bucket build (each adds its kernels to c->launches)
+void launch_keys(Ctx* c, bool mutate, bool movers) {
+    const int n = (int)c->n;
+    MoverOut mo{};
+    if (movers) mo = MoverOut{c->mvf, c->mov_key, c->mov_slot, c->mov_cap};
+    k_cell_keys<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(
+        c->pos, c->vel, c->type, c->key, c->perm, n, c->grid, c->st, mutate ? 1 : 0,
+        c->grid.ghost_key, c->sid, c->scn, c->scene_shift, mo);
+    c->launches += 1;
 }
 
-void state_ptrs_load(Ctx* c, const void* rec) {
-    BucketPtrs b;
-    std::memcpy(&b, rec, sizeof b);
-    load_ptrs(c, b);
-}
-
-int bucket_build(Ctx* c, bool mutate) {
-    if (!mutate) return bucket_launches(c, false);
-    if (c->graphs_off) return bucket_launches(c, true);
-    BucketGraph* bg = nullptr;
-    for (BucketGraph& g : c->bucket_graph)
-        if (g.exec && g.pos == c->pos) bg = &g;
-    if (!bg) {
-        for (BucketGraph& g : c->bucket_graph)
-            if (!g.exec) { bg = &g; break; }
-        if (!bg) return bucket_launches(c, true);   // not expected: more than two parities
-        const double4* start = c->pos;
-        const BucketPtrs before = save_ptrs(c);
-        const int64_t l0 = c->launches;
-        MPS_CUDA(c, cudaStreamSynchronize(c->stream));
-        MPS_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeRelaxed));
-        int rc = bucket_launches(c, true);
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-        if (rc || e != cudaSuccess) {
-            if (g) cudaGraphDestroy(g);
-            cudaGetLastError();
-            c->graphs_off = true;
-            load_ptrs(c, before);
-            c->launches = l0;
-            return rc ? rc : cuda_fail(c, e, "bucket graph capture");
-        }
-        e = cudaGraphInstantiate(&bg->exec, g, 0);
-        if (e != cudaSuccess) {
-            cudaGraphDestroy(g);
-            load_ptrs(c, before);
-            c->launches = l0;
-            return cuda_fail(c, e, "bucket graph instantiate");
-        }
-        bg->graph = g;
-        bg->pos = start;
-        bg->launches = c->launches - l0;
-        BucketPtrs after = save_ptrs(c);
-        static_assert(sizeof(BucketPtrs) <= sizeof(bg->after), "pointer record too small");
-        std::memcpy(bg->after, &after, sizeof after);
-        c->launches = l0;   // counted at the replay below
-        load_ptrs(c, before);
-    }
-    MPS_CUDA(c, cudaGraphLaunch(bg->exec, c->stream));
-    BucketPtrs after;
-    std::memcpy(&after, bg->after, sizeof after);
-    load_ptrs(c, after);
-    c->launches += bg->launches;
-    return MPS_OK;
-}
-
-void bucket_graphs_destroy(Ctx* c) {
-    for (BucketGraph& g : c->bucket_graph) {
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-        if (g.graph) cudaGraphDestroy(g.graph);
-        g = BucketGraph{};
-    }
-}
-
-static int bucket_launches(Ctx* c, bool mutate) {
+// LSD radix sort of (c->key, c->perm) over sort_bits; afterwards c->key and c->perm name
+// the buffers holding the sorted keys and the permutation
+void launch_radix(Ctx* c) {
     const int n = (int)c->n;
     cudaStream_t s = c->stream;
-    const int nb1 = (n + kBT - 1) / kBT;
-    k_cell_keys<<<nb1, kBT, 0, s>>>(c->pos, c->vel, c->type, c->key, c->perm, n, c->grid, c->st,
-                                    mutate ? 1 : 0, c->grid.ghost_key, c->sid, c->scn,
-                                    c->scene_shift);
-    // LSD radix sort over sort_bits
     const int nt = (n + kTile - 1) / kTile;
     uint32_t* kin = c->key;
     int32_t* vin = c->perm;
@@ -343,13 +383,37 @@ static int bucket_launches(Ctx* c, bool mutate) {
         uint32_t* tk = kin; kin = kout; kout = tk;
         int32_t* tv = vin; vin = vout; vout = tv;
     }
-    // kin/vin hold the sorted keys and the permutation
     if (kin != c->key) { c->key_alt = c->key; c->key = kin; }
     if (vin != c->perm) { c->perm_alt = c->perm; c->perm = vin; }
-    // cell table
+}
+
+// the build from the previous order: the new keys (slot order) in kin, the sorted keys and
+// the permutation into kout / vout (kout != kin)
+int launch_from_previous(Ctx* c, const uint32_t* kin, uint32_t* kout, int32_t* vout) {
+    const int n = (int)c->n;
+    cudaStream_t s = c->stream;
+    const uint32_t gk = c->grid.ghost_key;
+    MPS_CUDA(c, cudaMemsetAsync(c->mov_cnt, 0, 4 * sizeof(uint32_t) * (size_t)c->mov_cap, s));
+    k_mov_count<<<c->sms * 4, kBT, 0, s>>>(c->mov_key, c->mov_slot, c->st, c->mov_cap,
+                                           c->cell_start, gk, n, c->mov_cnt);
+    k_mov_place<<<(c->mov_cap + kBT - 1) / kBT, kBT, 0, s>>>(
+        c->mov_key, c->mov_slot, c->st, c->mov_cap, c->cell_start, gk, n, c->mov_cnt,
+        c->mov_by_slot, c->mov_by_key, kout, vout);
+    k_stay_place<<<(n + kBT - 1) / kBT, kBT, 0, s>>>(kin, c->mvf, n, c->st, c->mov_cap,
+                                                     c->mov_by_slot, c->mov_by_key, kout, vout);
+    c->launches += 3;
+    return MPS_OK;
+}
+
+// cell table of the sorted keys, the state permuted into the new order, the active-row
+// lists, the two-phase properties
+int launch_table_rest(Ctx* c) {
+    const int n = (int)c->n;
+    cudaStream_t s = c->stream;
+    const int nb1 = (n + kBT - 1) / kBT;
     MPS_CUDA(c, cudaMemsetAsync(c->cell_count, 0, sizeof(uint32_t) * (size_t)c->ntable, s));
     k_cell_count<<<nb1, kBT, 0, s>>>(c->key, n, c->grid.ghost_key, c->cell_count);
-    c->launches += 4 + scan_exclusive(c->cell_count, (uint32_t*)c->cell_start, c->ntable, true,
+    c->launches += 3 + scan_exclusive(c->cell_count, (uint32_t*)c->cell_start, c->ntable, true,
                                       c->scan_scratch, s);
     k_occupied<<<nb1, kBT, 0, s>>>(c->key, n, c->grid.ghost_key, c->occ, c->st);
     // permute the state into the new order
@@ -376,6 +440,188 @@ static int bucket_launches(Ctx* c, bool mutate) {
     launch_gather_props(c);   // two-phase properties follow their particles
     MPS_CUDA(c, cudaGetLastError());
     return MPS_OK;
+}
+
+// launch by launch: always the radix sort
+int bucket_launches(Ctx* c, bool mutate) {
+    launch_keys(c, mutate, false);
+    launch_radix(c);
+    int rc = launch_table_rest(c);
+    if (!rc) c->order_valid = true;
+    return rc;
+}
+
+// The bucket build is ~25 short dependent kernels whose launch gaps cost more than their
+// work, so the stepping path replays it as one CUDA graph.  Every build swaps the state with
+// its alternate buffers (and the radix sort's keys and permutation with theirs when it
+// takes an odd number of passes), so there are two graphs, keyed by the position buffer
+// the build starts from; each remembers the buffer assignment its build leaves behind.
+struct BucketPtrs {
+    uint32_t *key, *key_alt;
+    int32_t *perm, *perm_alt;
+    double4 *pos, *pos_alt, *vel, *vel_alt;
+    int8_t *type, *type_alt;
+    int32_t *id, *id_alt;
+    double *p, *p_alt;
+    double *ph[Ctx::kGuessMax], *ph_alt[Ctx::kGuessMax];
+};
+BucketPtrs save_ptrs(const Ctx* c) {
+    return {c->key, c->key_alt, c->perm, c->perm_alt, c->pos, c->pos_alt, c->vel, c->vel_alt,
+            c->type, c->type_alt, c->id, c->id_alt, c->p, c->p_alt,
+            {c->ph[0], c->ph[1], c->ph[2]}, {c->ph_alt[0], c->ph_alt[1], c->ph_alt[2]}};
+}
+void load_ptrs(Ctx* c, const BucketPtrs& b) {
+    c->key = b.key; c->key_alt = b.key_alt; c->perm = b.perm; c->perm_alt = b.perm_alt;
+    c->pos = b.pos; c->pos_alt = b.pos_alt; c->vel = b.vel; c->vel_alt = b.vel_alt;
+    c->type = b.type; c->type_alt = b.type_alt; c->id = b.id; c->id_alt = b.id_alt;
+    c->p = b.p; c->p_alt = b.p_alt;
+    for (int k = 0; k < Ctx::kGuessMax; k++) {
+        c->ph[k] = b.ph[k];
+        c->ph_alt[k] = b.ph_alt[k];
+    }
+}
+}  // namespace
+
+void state_ptrs_save(const Ctx* c, void* rec) {
+    static_assert(sizeof(BucketPtrs) <= kPtrRecord, "pointer record too small");
+    const BucketPtrs b = save_ptrs(c);
+    std::memcpy(rec, &b, sizeof b);
+}
+
+void state_ptrs_load(Ctx* c, const void* rec) {
+    BucketPtrs b;
+    std::memcpy(&b, rec, sizeof b);
+    load_ptrs(c, b);
+}
+
+// The graph form: keys (recording the movers) and the branch decision, then IF (radix) the
+// radix sort, IF (previous order) the build from the previous order into the buffers the
+// radix sort would leave its result in, then the common tail.
+int bucket_append(Ctx* c, cudaGraph_t G, cudaGraphNode_t dep, cudaGraphNode_t* tail) {
+    cudaStream_t s = c->stream;
+    const cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    cudaGraph_t R = nullptr, I = nullptr, tmp = nullptr;
+    cudaGraphConditionalHandle h_r = 0, h_i = 0;
+    cudaGraphNode_t n_keys, n_r, n_i;
+    int rc;
+    MPS_CUDA(c, cudaGraphConditionalHandleCreate(&h_r, G, 0, cudaGraphCondAssignDefault));
+    MPS_CUDA(c, cudaGraphConditionalHandleCreate(&h_i, G, 0, cudaGraphCondAssignDefault));
+    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, G, dep ? &dep : nullptr, nullptr, dep ? 1 : 0,
+                                              mode));
+    launch_keys(c, true, true);
+    k_bucket_branch<<<1, 32, 0, s>>>(c->st, c->order_ok, c->mov_cap, h_r, h_i);
+    c->launches += 1;
+    n_keys = capture_tail(s);
+    MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+    if (!n_keys) return MPS_EDEVICE;
+    uint32_t* const k_new = c->key;   // the new keys in slot order
+    uint32_t* const k_other = c->key_alt;
+    int32_t* const v_other = c->perm_alt;
+    // ---- IF: the radix sort
+    if ((rc = add_cond(c, G, n_keys, h_r, cudaGraphCondTypeIf, &n_r, &R))) return rc;
+    int64_t l = c->launches;
+    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, R, nullptr, nullptr, 0, mode));
+    launch_radix(c);
+    MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+    c->bucket_radix_launches = c->launches - l;
+    c->launches = l;
+    // ---- IF: from the previous order, into the buffers the radix sort leaves its result in
+    // (through the other pair and a copy when that is where the new keys are)
+    if ((rc = add_cond(c, G, n_r, h_i, cudaGraphCondTypeIf, &n_i, &I))) return rc;
+    l = c->launches;
+    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, I, nullptr, nullptr, 0, mode));
+    const size_t n = (size_t)c->n;
+    if (c->key != k_new) {
+        if ((rc = launch_from_previous(c, k_new, c->key, c->perm))) return rc;
+    } else {
+        if ((rc = launch_from_previous(c, k_new, k_other, v_other))) return rc;
+        MPS_CUDA(c, cudaMemcpyAsync(c->key, k_other, n * sizeof(uint32_t),
+                                    cudaMemcpyDeviceToDevice, s));
+        MPS_CUDA(c, cudaMemcpyAsync(c->perm, v_other, n * sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, s));
+    }
+    MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+    c->bucket_inc_launches = c->launches - l;
+    c->launches = l;
+    // ---- the common tail
+    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, G, &n_i, nullptr, 1, mode));
+    if ((rc = launch_table_rest(c))) return rc;
+    *tail = capture_tail(s);
+    MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+    if (!*tail) return MPS_EDEVICE;
+    return MPS_OK;
+}
+
+void bucket_branch_count(Ctx* c, const DevStatus& st) {
+    if (c->pending_branch < 0) return;
+    const bool inc = c->pending_branch != 0 && st.n_mov <= (unsigned)c->mov_cap;
+    c->launches += inc ? c->bucket_inc_launches : c->bucket_radix_launches;
+    c->pending_branch = -1;
+}
+
+// the host's word for the next graph build: whether the slot order and cell table are those
+// of the previous build with this grid
+int bucket_order_word(Ctx* c) {
+    const bool ok = c->order_valid && c->prm.bucket_sort == 0;
+    MPS_CUDA(c, cudaMemsetAsync(c->order_ok, ok ? 1 : 0, sizeof(int32_t), c->stream));
+    c->pending_branch = ok ? 1 : 0;
+    return MPS_OK;
+}
+
+int bucket_build(Ctx* c, bool mutate) {
+    if (!mutate || c->graphs_off) return bucket_launches(c, mutate);
+    BucketGraph* bg = nullptr;
+    for (BucketGraph& g : c->bucket_graph)
+        if (g.exec && g.pos == c->pos) bg = &g;
+    if (!bg) {
+        for (BucketGraph& g : c->bucket_graph)
+            if (!g.exec) { bg = &g; break; }
+        if (!bg) return bucket_launches(c, true);   // not expected: more than two parities
+        const double4* start = c->pos;
+        const BucketPtrs before = save_ptrs(c);
+        const int64_t l0 = c->launches;
+        MPS_CUDA(c, cudaStreamSynchronize(c->stream));
+        cudaGraph_t g = nullptr;
+        MPS_CUDA(c, cudaGraphCreate(&g, 0));
+        cudaGraphNode_t tail = nullptr;
+        int rc = bucket_append(c, g, nullptr, &tail);
+        cudaError_t e = cudaSuccess;
+        if (!rc) e = cudaGraphInstantiate(&bg->exec, g, 0);
+        if (rc || e != cudaSuccess) {
+            // the graph of a failed capture is left alone (the runtime may have dropped the
+            // body it was capturing into)
+            abort_capture(c);
+            bg->exec = nullptr;
+            c->graphs_off = true;
+            load_ptrs(c, before);
+            c->launches = l0;
+            return rc ? rc : cuda_fail(c, e, "bucket graph instantiate");
+        }
+        bg->graph = g;
+        bg->pos = start;
+        bg->launches = c->launches - l0;
+        BucketPtrs after = save_ptrs(c);
+        static_assert(sizeof(BucketPtrs) <= sizeof(bg->after), "pointer record too small");
+        std::memcpy(bg->after, &after, sizeof after);
+        c->launches = l0;   // counted at the replay below
+        load_ptrs(c, before);
+    }
+    if (int rc = bucket_order_word(c)) return rc;
+    MPS_CUDA(c, cudaGraphLaunch(bg->exec, c->stream));
+    BucketPtrs after;
+    std::memcpy(&after, bg->after, sizeof after);
+    load_ptrs(c, after);
+    c->launches += bg->launches;
+    c->order_valid = true;
+    return MPS_OK;
+}
+
+void bucket_graphs_destroy(Ctx* c) {
+    for (BucketGraph& g : c->bucket_graph) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+        g = BucketGraph{};
+    }
 }
 
 }  // namespace mps

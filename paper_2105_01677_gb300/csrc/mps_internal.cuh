@@ -59,6 +59,8 @@ struct DevStatus {
     unsigned long long list_tests;      // candidate-list entries classified by the build (at r*)
     unsigned int n_fast;                // particles beyond half the full skin (skinpatch.cu)
     unsigned int differs;               // a written state differs from the context's
+    unsigned int n_mov;                 // bucket build: particles whose cell key changed
+    unsigned int pad2;
 };
 
 // Scalars of one CG solve; updated by the last block of each reduction kernel.
@@ -202,7 +204,7 @@ int add_mixed_solve(Ctx* c, cudaGraph_t G, cudaGraphNode_t dep, double* x, bool 
 void mixed_init_scalars(Ctx* c, CgScalars* init);
 int64_t mixed_solve_launches(Ctx* c, bool guess, const CgScalars& h);
 // the stepping bucket build's launches and the state buffer assignment (bucket.cu)
-int bucket_capture_launches(Ctx* c);
+
 constexpr size_t kPtrRecord = 24 * sizeof(void*);
 void state_ptrs_save(const Ctx* c, void* rec);
 void state_ptrs_load(Ctx* c, const void* rec);
@@ -214,6 +216,17 @@ void launch_fast_mark(Ctx* c, double half);
 int launch_fast_patch(Ctx* c, int n_fast, float hv2);
 // whole steps as CUDA graphs (stepgraph.cu)
 bool step_graph_eligible(const Ctx* c, bool advance);
+// a conditional node of graph g after dep (null: none), its body graph in *body; the node a
+// capture into stream s ends at (null unless exactly one)
+int add_cond(Ctx* c, cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h,
+             cudaGraphConditionalNodeType type, cudaGraphNode_t* node, cudaGraph_t* body);
+cudaGraphNode_t capture_tail(cudaStream_t s);
+// the bucket build appended to graph G after dep (bucket.cu); *tail: its last node
+int bucket_append(Ctx* c, cudaGraph_t G, cudaGraphNode_t dep, cudaGraphNode_t* tail);
+// kernels of the bucket build's branch that ran (after its status was read), into launches
+void bucket_branch_count(Ctx* c, const DevStatus& st);
+// the host's word for the next graph bucket build (before the graph's launch)
+int bucket_order_word(Ctx* c);
 int step_graph_step(Ctx* c, mps_report* rep);
 int do_step(Ctx* c, bool advance, mps_report* rep);   // api.cu: the host-driven step
 void step_graphs_destroy(Ctx* c);
@@ -390,6 +403,21 @@ struct Ctx {
     uint32_t* cell_count;
     int32_t* cell_start;
     uint32_t* occ;         // occupied cell codes
+    // bucket build from the previous order (bucket.cu): the slots whose key changed (flag
+    // per slot, and up to mov_cap of them as (key, slot)), their counts and ranks, the
+    // movers sorted by slot and by (key, slot); order_ok (device word, set by the host
+    // before a build): the slot order is sorted by the keys and cell table in key/cell_start
+    uint8_t* mvf = nullptr;
+    uint32_t* mov_key = nullptr;
+    int32_t* mov_slot = nullptr;
+    uint32_t* mov_cnt = nullptr;       // 4 per mover
+    int32_t* mov_by_slot = nullptr;
+    unsigned long long* mov_by_key = nullptr;
+    int32_t* order_ok = nullptr;
+    int mov_cap = 0;
+    bool order_valid = false;          // host: what order_ok is set to before the next build
+    int64_t bucket_inc_launches = 0, bucket_radix_launches = 0;   // kernels of either branch
+    int pending_branch = -1;   // a graph bucket build ran with this order_ok, branch not counted
     // two-phase flow: per-particle density / viscosity in original order (as given) and in
     // slot order (gathered by id after every reordering); null when uniform
     double *rho_id = nullptr, *nu_id = nullptr;

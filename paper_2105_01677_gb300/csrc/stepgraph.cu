@@ -31,6 +31,28 @@
 
 namespace mps {
 
+int add_cond(Ctx* c, cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h,
+             cudaGraphConditionalNodeType type, cudaGraphNode_t* node, cudaGraph_t* body) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    MPS_CUDA(c, cudaGraphAddNode(node, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &cp));
+    *body = cp.conditional.phGraph_out[0];
+    return MPS_OK;
+}
+
+// the node a capture into `s` currently ends at (null unless exactly one)
+cudaGraphNode_t capture_tail(cudaStream_t s) {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess)
+        return nullptr;
+    return nd == 1 ? deps[0] : nullptr;
+}
+
 namespace {
 
 // the attempt's counters (the first attempt finds them zeroed by the step's status reset);
@@ -78,28 +100,6 @@ __global__ void k_attempt_check(StepCtl* ctl, const DevStatus* st, cudaGraphCond
     }
     cudaGraphSetConditional(h_loop, loop ? 1u : 0u);
     cudaGraphSetConditional(h_rest, rest ? 1u : 0u);
-}
-
-int add_cond(Ctx* c, cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h,
-             cudaGraphConditionalNodeType type, cudaGraphNode_t* node, cudaGraph_t* body) {
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = type;
-    cp.conditional.size = 1;
-    MPS_CUDA(c, cudaGraphAddNode(node, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &cp));
-    *body = cp.conditional.phGraph_out[0];
-    return MPS_OK;
-}
-
-// the node a capture into `s` currently ends at (null unless exactly one)
-cudaGraphNode_t capture_tail(cudaStream_t s) {
-    cudaStreamCaptureStatus cs;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    if (cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &deps, nullptr, &nd) != cudaSuccess)
-        return nullptr;
-    return nd == 1 ? deps[0] : nullptr;
 }
 
 int alloc_ctl(Ctx* c) {
@@ -169,7 +169,12 @@ int capture_step(Ctx* c, StepGraph* sg, cudaGraph_t G) {
     MPS_CUDA(c, cudaGraphConditionalHandleCreate(&h_rest, G, 0, cudaGraphCondAssignDefault));
     MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, G, nullptr, nullptr, 0, mode));
     MPS_CUDA(c, cudaMemsetAsync(c->st, 0, sizeof(DevStatus), s));
-    if ((rc = bucket_capture_launches(c))) return rc;
+    cudaGraphNode_t n_st = capture_tail(s);
+    MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+    if (!n_st) return MPS_EDEVICE;
+    cudaGraphNode_t n_bucket = nullptr;
+    if ((rc = bucket_append(c, G, n_st, &n_bucket))) return rc;
+    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, G, &n_bucket, nullptr, 1, mode));
     launch_copy_state_star(c);
     n_pre = capture_tail(s);
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
@@ -333,8 +338,10 @@ int step_graph_step(Ctx* c, mps_report* rep) {
     }
     MPS_CUDA(c, cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(StepCtl), cudaMemcpyHostToDevice,
                                 c->stream));
+    if ((rc = bucket_order_word(c))) return rc;
     MPS_CUDA(c, cudaGraphLaunch(sg->exec, c->stream));
     state_ptrs_load(c, sg->after);
+    c->order_valid = true;
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
     // ---- what the step left
     const DevStatus& st = *c->st_host;
@@ -363,6 +370,7 @@ int step_graph_step(Ctx* c, mps_report* rep) {
     rep->step_graph = 1;
     rep->n_fast = 0;
     c->launches += sg->launches_pre + attempts * sg->launches_attempt;
+    bucket_branch_count(c, st);
     c->list_age = 0;
     c->need_list = false;
     if (st.err) {

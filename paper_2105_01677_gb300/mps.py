@@ -39,7 +39,7 @@ class mps_params(C.Structure):
                 ("list_every", C.c_int32), ("kernel", C.c_int32), ("gradient_form", C.c_int32),
                 ("source_term", C.c_int32), ("ppe_host_loop", C.c_int32),
                 ("cg_x0", C.c_int32), ("step_graph", C.c_int32), ("inner_cg", C.c_int32),
-                ("spmv_block", C.c_int32), ("build_block", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
+                ("spmv_block", C.c_int32), ("build_block", C.c_int32), ("bucket_sort", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
                 ("alloc_user", C.c_void_p)]
 
 
