@@ -117,7 +117,11 @@ def parse():
                     help="keep the default launch shapes (the mixed runs are autotuned first)")
     ap.add_argument("--no-step-graph", action="store_true",
                     help="launch kernel by kernel instead of one CUDA graph per step "
-                         "(profiling: identical results)")
+                         "(profiling: identical results; the bucket build stays a graph)")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel one by one, the bucket build included (profiling: "
+                         "identical results; ncu does not see the kernels of graphs with "
+                         "conditional nodes)")
     ap.add_argument("--ppe-host-loop", action="store_true",
                     help="drive the mixed PPE solve from the host (profiling: identical results)")
     ap.add_argument("--cg-x0", type=int, default=3, choices=[0, 1, 2, 3],
@@ -314,7 +318,8 @@ def run_gb300(args):
     # --ppe-host-loop: the mixed PPE solve driven from the host instead of one CUDA graph
     # (identical results; ncu cannot profile the kernels of a graph with conditional nodes)
     common = dict(dt=5e-5, cg_tol=1e-8, ppe_host_loop=1 if args.ppe_host_loop else 0,
-                  cg_x0=args.cg_x0, step_graph=0 if args.no_step_graph else 1)
+                  cg_x0=args.cg_x0,
+                  step_graph=2 if args.no_graphs else (0 if args.no_step_graph else 1))
 
     def timed_steps(sim, k, profile=False, profile_steps=20):
         """CUDA-event time of k steps with the stage timers off (a step then runs as one CUDA
@@ -466,6 +471,7 @@ def run_gb300(args):
         E = scenes.ensemble_2d(count=args.ensemble_scenes, seed=args.seed + rank)
         ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
                            cg_tol=1e-8, cg_x0=args.cg_x0)
+        ens.step(2)
         tuning = ens.autotune(3)
         ens.step(args.warmup)
         barrier()
@@ -641,6 +647,7 @@ def run_gb300(args):
         ne = sum(sc.n for sc in E)
         ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
                            cg_tol=1e-8, cg_x0=args.cg_x0)
+        ens.step(2)   # the tuner's cell side needs the motion of a step
         tuning_e = ens.autotune(3)
         ens.step(args.warmup)
         barrier()

@@ -128,7 +128,10 @@ typedef struct {
     int32_t step_graph;       /* 1 (default): a step on the mixed path (device-driven PPE) or  *
                                * the equation-of-state path, with candidate lists gathered    *
                                * every step and the stage timers off, runs as one CUDA graph: *
-                               * one launch and one synchronisation; 0: launch by launch.     *
+                               * one launch and one synchronisation; 0: launch by launch (the *
+                               * bucket build still one graph); 2: every kernel launched one  *
+                               * by one, the bucket build included (for kernel profilers; the *
+                               * mixed PPE solve's own graph follows ppe_host_loop).           *
                                * Results are identical.                                        */
     int32_t inner_cg;         /* mixed inner CG of the device-driven solve: 0 (default) three  *
                                * kernels per iteration; 1 two (fused: the recurrences of      *

@@ -164,6 +164,7 @@ int check_params(const mps_params* P) {
         P->build_block != 256)
         return MPS_EINVAL;
     if (P->bucket_sort != 0 && P->bucket_sort != 1) return MPS_EINVAL;
+    if (P->step_graph < 0 || P->step_graph > 2) return MPS_EINVAL;
     if (P->kernel < 0 || P->kernel > 1 || P->gradient_form < 0 || P->gradient_form > 1 ||
         P->source_term < 0 || P->source_term > 2 || (P->source_term >= 1 && P->kernel != 0))
         return MPS_EINVAL;

@@ -569,7 +569,7 @@ int bucket_order_word(Ctx* c) {
 }
 
 int bucket_build(Ctx* c, bool mutate) {
-    if (!mutate || c->graphs_off) return bucket_launches(c, mutate);
+    if (!mutate || c->graphs_off || c->prm.step_graph == 2) return bucket_launches(c, mutate);
     BucketGraph* bg = nullptr;
     for (BucketGraph& g : c->bucket_graph)
         if (g.exec && g.pos == c->pos) bg = &g;

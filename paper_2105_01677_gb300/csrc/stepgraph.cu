@@ -276,7 +276,7 @@ int build_step_graph(Ctx* c, StepGraph* sg) {
 
 bool step_graph_eligible(const Ctx* c, bool advance) {
     const mps_params& P = c->prm;
-    return P.step_graph != 0 && advance && !c->vjp && !c->profiling && !c->force_host &&
+    return P.step_graph == 1 && advance && !c->vjp && !c->profiling && !c->force_host &&
            !c->graphs_off &&
            P.list_every <= 1 &&
            (P.pressure_mode == 1 || (P.precision == 1 && P.ppe_host_loop == 0));

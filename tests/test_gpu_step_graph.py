@@ -1,10 +1,11 @@
 """Whole steps as one CUDA graph (step_graph = 1, the default) against the same steps launched
-one by one (step_graph = 0): the kernels are the same, so every field must agree bit for
-bit, over several steps (which exercises both state-buffer parities of the graph, the guess
-history and the adaptive list skin), for one scene and for an ensemble, on the mixed PPE
-path and the equation-of-state path; the retry with the full skin, MPS_ESKIN and the device
-errors must come out as on the host-driven path.  The parity of either path with the oracle
-is covered by the other GPU tests, which run the graph by default."""
+one by one (step_graph = 0; 2 launches the bucket build kernel by kernel as well): the
+kernels are the same, so every field must agree bit for bit, over several steps (which
+exercises both state-buffer parities of the graph, the guess history and the adaptive list
+skin), for one scene and for an ensemble, on the mixed PPE path and the equation-of-state
+path; the retry with the full skin, MPS_ESKIN and the device errors must come out as on the
+host-driven path. The parity of either path with the oracle is covered by the other GPU
+tests, which run the graph by default."""
 import numpy as np
 import pytest
 
@@ -65,13 +66,16 @@ def test_step_graph_equals_launch_by_launch(case):
         kw.update(rho_i=rho_i, nu_i=nu_i)
     rg, sg = _run(sc, 6, 1, **kw)
     rh, sh = _run(sc, 6, 0, **kw)
+    # step_graph = 2: the bucket build launched kernel by kernel too (its radix sort every step)
+    rn, sn = _run(sc, 6, 2, **kw)
     assert all(r["step_graph"] == 1 for r in rg)
-    assert all(r["step_graph"] == 0 for r in rh)
+    assert all(r["step_graph"] == 0 for r in rh + rn)
     for k in range(6):
         _same(sg[k], sh[k])
+        _same(sg[k], sn[k])
         for f in ("cg_iters", "cg_outer", "cg_resid", "n_surface", "n_ppe_rows", "max_disp",
                   "cand_tests", "pairs_ppe", "pairs_pnd", "list_tests"):
-            assert rg[k][f] == rh[k][f], (k, f)
+            assert rg[k][f] == rh[k][f] == rn[k][f], (k, f)
 
 
 def test_step_graph_ensemble_equals_launch_by_launch():
