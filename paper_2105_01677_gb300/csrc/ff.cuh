@@ -189,10 +189,25 @@ __device__ __forceinline__ ff2 ff2_rsqrt_step(ff2 x, ff2 y) {
     return ff2_add_f(y, mul2(mul2(f2(0.5f), y.h), hres));
 }
 
-// one Newton step from the FP32 estimate (relative error ~1e-13)
+// one Newton step from the FP32 estimate (relative error ~1e-13).  The start y0 has no low
+// part, so y0^2 is a single exact product, and the correction y0 h / 2 (|h| ~ 1e-7) is
+// added by FastTwoSum: the values of the general step taken from (y0, 0), in fewer operations
 __device__ __forceinline__ ff2 ff2_rsqrt1(ff2 x) {
-    const ff2 y0 = {make_float2(rsqrtf(x.h.x), rsqrtf(x.h.y)), f2(0.f)};
-    return ff2_rsqrt_step(x, y0);
+    const float2 y0 = make_float2(rsqrtf(x.h.x), rsqrtf(x.h.y));
+    const ff2 t = ff2_two_prod(y0, y0);
+    ff2 u = ff2_two_prod(x.h, t.h);
+    u.l = fma2(x.h, t.l, fma2(x.l, t.h, u.l));
+    const float2 hres = sub2(sub2(f2(1.0f), u.h), u.l);
+    return ff2_fast_two_sum(y0, mul2(mul2(f2(0.5f), y0), hres));
+}
+
+// a b + c with the product's low part carried into the sum unnormalised (one FastTwoSum
+// fewer than ff2_add(ff2_mul(a, b), c); the same ~2^-46 relative error)
+__device__ __forceinline__ ff2 ff2_mul_add(ff2 a, ff2 b, ff2 c) {
+    ff2 p = ff2_two_prod(a.h, b.h);
+    p.l = fma2(a.h, b.l, fma2(a.l, b.h, p.l));
+    const ff2 s = ff2_two_sum(p.h, c.h);
+    return ff2_fast_two_sum(s.h, add2(s.l, add2(p.l, c.l)));
 }
 
 // 2/x for x > 0: the correctly rounded FP32 reciprocal y0 of x.h and one Newton step

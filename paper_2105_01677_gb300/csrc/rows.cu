@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                 // tn0 || tn1 would be taken by nearly every warp anyway)
                 const ff2 y2 = ff2_rsqrt_step(r2, y);
                 const ff2 w = KERN == 1 ? ff2_cube(ff2_one_minus(ff2_mul(ff2_mul(r2, y2), invn)))
-                                        : ff2_add_f(ff2_mul(ren, y2), f2(-1.f));
+                                        : ff2_mul_add(ren, y2, {f2(-1.f), f2(0.f)});
                 if (SRC >= 1) {
                     // HS: re_n / r^3 (r_ij . (u*_j - u*_i)), binary64 from the float-float
                     // offsets and reciprocal distance
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(kBuildBT, (!MULTI && (!MIXED || (KERN == 0 && 
                 }
                 // c = coef (re/r - 1) = (coef re) y - coef, or coef (1 - r/re)^3
                 ff2 c = KERN == 1 ? ff2_mul(coef, ff2_cube(ff2_one_minus(ff2_mul(ff2_mul(r2, y), invl))))
-                                      : ff2_add(ff2_mul(cre, y), ncoef);
+                                      : ff2_mul_add(cre, y, ncoef);
                 if (a.rho_ff) {   // two-phase: times 2/(rho_i + rho_j)
                     const float2 q0 = a.rho_ff[j0], q1 = a.rho_ff[j1];
                     c = ff2_mul(c, ff2_two_over(ff2_add({f2(rhoi.x), f2(rhoi.y)},
