@@ -622,7 +622,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
                 MPS_CUDA(c, cudaMemcpyAsync(c->pos_b, c->pos, n * sizeof(double4),
                                             cudaMemcpyDeviceToDevice, c->stream));
         }
-        launch_copy_state_star(c);
+        if (!fresh) launch_copy_state_star(c);   // a build's permutation writes r* := r itself
         if (fresh) {
             if ((rc = set_candidate_radius(c, adapt ? c->list_skin : P.cell_skin))) return rc;
             MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), c->stream));

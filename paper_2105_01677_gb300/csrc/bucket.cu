@@ -295,11 +295,18 @@ struct GuessPerm {
     int m;
 };
 
+// the step's predicted state starts as r* = r, u* = u (the prediction overwrites the FLUID
+// rows): written here with the permuted state instead of by a separate copy
+struct StarOut {
+    double4 *pos, *vel;
+    float4 *pos32, *pff;   // pff: (hi, lo) pairs, slot s at 2 s and 2 s + 1
+};
+
 __global__ void __launch_bounds__(kBT)
     k_permute(const int32_t* perm, int n, const double4* pos, const double4* vel,
               const int8_t* type, const int32_t* id, const double* p, double4* pos_o,
               double4* vel_o, int8_t* type_o, int32_t* id_o, double* p_o, GuessPerm gp,
-              float4* pos32, float4* pos32lo, float4* vel32, GridDesc g) {
+              float4* pos32, float4* pos32lo, float4* vel32, GridDesc g, StarOut so) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int j = perm[s];
@@ -321,6 +328,11 @@ __global__ void __launch_bounds__(kBT)
     l.w = 0.f;
     pos32[s] = h;
     pos32lo[s] = l;
+    so.pos[s] = x;
+    so.vel[s] = u;
+    so.pos32[s] = h;
+    so.pff[2 * s] = h;
+    so.pff[2 * s + 1] = l;
 }
 // active-row marks of the new order (one scan each gives the row lists)
 __global__ void __launch_bounds__(kBT)
@@ -405,8 +417,8 @@ int launch_from_previous(Ctx* c, const uint32_t* kin, uint32_t* kout, int32_t* v
     return MPS_OK;
 }
 
-// cell table of the sorted keys, the state permuted into the new order, the active-row
-// lists, the two-phase properties
+// cell table of the sorted keys, the state permuted into the new order (and r* := r), the
+// active-row lists, the two-phase properties
 int launch_table_rest(Ctx* c) {
     const int n = (int)c->n;
     cudaStream_t s = c->stream;
@@ -425,7 +437,8 @@ int launch_table_rest(Ctx* c) {
     }
     k_permute<<<nb1, kBT, 0, s>>>(c->perm, n, c->pos, c->vel, c->type, c->id, c->p, c->pos_alt,
                                   c->vel_alt, c->type_alt, c->id_alt, c->p_alt, gp, c->pos32,
-                                  c->pos32lo, c->vel32, c->grid);
+                                  c->pos32lo, c->vel32, c->grid,
+                                  StarOut{c->pos_star, c->vel_star, c->pos32_star, c->pff_star});
     std::swap(c->pos, c->pos_alt);
     std::swap(c->vel, c->vel_alt);
     std::swap(c->type, c->type_alt);

@@ -1,7 +1,7 @@
 // stepgraph.cu -- one time step as one CUDA graph: one launch and one stream
 // synchronisation per step instead of ~70 launches and a status read in the middle.
 //
-//   status reset -> bucket build (Sec. 4.1) -> r* := r
+//   status reset -> bucket build (Sec. 4.1), whose permutation also sets r* := r
 //   WHILE (retry) {                                         at most two attempts
 //       reset the attempt's counters, candidate radius of the attempt's skin
 //       candidate lists -> prediction (Eq. 2, Eq. 7) -> n*, flags, PPE rows (Eq. 5, 15, 13)
@@ -172,13 +172,8 @@ int capture_step(Ctx* c, StepGraph* sg, cudaGraph_t G) {
     cudaGraphNode_t n_st = capture_tail(s);
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
     if (!n_st) return MPS_EDEVICE;
-    cudaGraphNode_t n_bucket = nullptr;
-    if ((rc = bucket_append(c, G, n_st, &n_bucket))) return rc;
-    MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, G, &n_bucket, nullptr, 1, mode));
-    launch_copy_state_star(c);
-    n_pre = capture_tail(s);
-    MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
-    if (!n_pre) return MPS_EDEVICE;
+    // (the bucket build's permutation also writes r* := r)
+    if ((rc = bucket_append(c, G, n_st, &n_pre))) return rc;
     sg->launches_pre = c->launches - l;
     // ---- WHILE (retry): candidate lists, prediction, build, check
     if ((rc = add_cond(c, G, n_pre, h_loop, cudaGraphCondTypeWhile, &n_loop, &L))) return rc;

@@ -172,15 +172,6 @@ __global__ void __launch_bounds__(kBT)
     if ((threadIdx.x & 31) == 0 && v) atomicMax(&kp.st->max_disp_next_bits, v);
 }
 
-// non-fluid particles keep r = r*, u = u* (walls and dummies do not move)
-__global__ void __launch_bounds__(kBT) k_copy_back(int n, const int8_t* type, const double4* ps,
-                                                   const double4* us, double4* pos, double4* vel) {
-    int i = blockIdx.x * kBT + threadIdx.x;
-    if (i >= n || type[i] == kFluid) return;
-    pos[i] = ps[i];
-    vel[i] = us[i];
-}
-
 __global__ void __launch_bounds__(kBT)
     k_unpermute(int n, int dim, const int32_t* id, const double4* pos, const double4* vel,
                 const double* p, const double* nstar, const uint8_t* flag, const int8_t* type,
@@ -332,8 +323,9 @@ void launch_gradient_correct(Ctx* c) {
                                                      c->p, c->phat, c->nb_n_col, c->nb_n_cnt, c->cap_n,
                                                      c->r_n.re, c->r_n.re_f, c->coef_grad, P.dt, P.rho,
                                                      c->pos, c->vel, c->rows_f, c->scan_f + c->n, kp);
-    k_copy_back<<<nb, kBT, 0, c->stream>>>(n, c->type, c->pos_star, c->vel_star, c->pos, c->vel);
-    c->launches += 2;
+    // the other particles keep r = r*, u = u*: their r*, u* are copies of r, u (walls and
+    // dummies do not move), so there is nothing to write back
+    c->launches += 1;
 }
 
 void launch_unpermute(Ctx* c, double* d_pos, double* d_vel, double* d_p, double* d_nstar,
