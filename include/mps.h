@@ -145,6 +145,9 @@ typedef struct {
                                * cell changed and merge them into the previous order when it   *
                                * holds (the radix sort otherwise); 1 always the radix sort.    *
                                * Both give the stable order by cell key: results identical.   */
+    int32_t cg_unroll;        /* device-driven mixed solve: inner CG iterations per pass of its *
+                               * conditional loop (1, 2 or 4; 0: 1); the iterations after     *
+                               * convergence return at once (results identical)                */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;
@@ -358,7 +361,8 @@ int mps_create_ensemble(const double* pos, const double* vel, const int8_t* type
  *     256 or 512 threads, and the inner CG as three kernels per iteration (SpMV; x, r
  *     update; direction update) or two (the recurrences of Chronopoulos and Gear: SpMV of
  *     the residual; one pass updating direction, A-direction, x and r), the latter for the
- *     device-driven solve only.
+ *     device-driven solve only, with 1, 2 or 4 inner iterations per pass of the solve's
+ *     conditional loop (params.cg_unroll).
  * Neighbour sets and the solve's stop rule are the same whatever the choice; the fused CG,
  * and another cell side (its candidates come in another order), round differently, so a
  * solve's result changes within its tolerance.  Afterwards the
@@ -372,6 +376,8 @@ typedef struct {
     int32_t spmv_block;     /* threads per block of the FP32 SpMV of the mixed inner CG      */
     int32_t cg_fused;       /* 1: the inner CG in two kernels per iteration, 0: three        */
     int32_t build_block;    /* threads per block of the row build                            */
+    int32_t cg_unroll;      /* inner CG iterations per pass of the solve's conditional loop   */
+    int32_t pad;
     double gather_ms;       /* the chosen gather's time [ms]                                 */
     double spmv_ms;         /* the chosen SpMV's time [ms] (0 without a mixed PPE)            */
     double solve_ms;        /* a mixed solve's time with the chosen form [ms] (0 without)     */

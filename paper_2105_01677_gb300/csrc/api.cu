@@ -165,6 +165,8 @@ int check_params(const mps_params* P) {
         return MPS_EINVAL;
     if (P->bucket_sort != 0 && P->bucket_sort != 1) return MPS_EINVAL;
     if (P->step_graph < 0 || P->step_graph > 2) return MPS_EINVAL;
+    if (P->cg_unroll != 0 && P->cg_unroll != 1 && P->cg_unroll != 2 && P->cg_unroll != 4)
+        return MPS_EINVAL;
     if (P->kernel < 0 || P->kernel > 1 || P->gradient_form < 0 || P->gradient_form > 1 ||
         P->source_term < 0 || P->source_term > 2 || (P->source_term >= 1 && P->kernel != 0))
         return MPS_EINVAL;
@@ -823,6 +825,7 @@ int mps_create(const double* pos, const double* vel, const int8_t* types, int64_
     c->cg_fused = params->inner_cg == 1;
     c->spmv_block = params->spmv_block ? params->spmv_block : 512;
     c->build_block = params->build_block;
+    c->cg_unroll = params->cg_unroll ? params->cg_unroll : 1;
     c->last_cg_iters = 8;
     if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, params->device) != cudaSuccess) {
         delete c;
@@ -877,6 +880,7 @@ int mps_create_ensemble(const double* pos, const double* vel, const int8_t* type
     c->cg_fused = P.inner_cg == 1;
     c->spmv_block = P.spmv_block ? P.spmv_block : 512;
     c->build_block = P.build_block;
+    c->cg_unroll = P.cg_unroll ? P.cg_unroll : 1;
     c->scenes_host.assign(scenes, scenes + n_scenes);
     c->n = n;
     c->steps_done = 0;
@@ -1067,31 +1071,39 @@ int mps_autotune(mps_ctx* c, int32_t repeats, mps_tuning* out) {
             if (c->prm.ppe_host_loop != 0) return MPS_OK;   // the fused form is device-driven only
             best_ms = 1e30f;
             bool best_f = c->cg_fused;
+            int best_u = c->cg_unroll;
             for (bool f : {false, true}) {
-                c->cg_fused = f;
-                ppe_graphs_destroy(c);
-                float ms = 0.f;
-                r2 = time_of([&]() -> int {
-                    mps_report pr;
-                    std::memset(&pr, 0, sizeof pr);
-                    int r3 = ppe_solve(c, &pr);
-                    return (r3 == MPS_ECG_NOCONV) ? MPS_OK : r3;
-                }, &ms);
-                if (r2) return r2;
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best_f = f;
+                for (int u : {1, 2, 4}) {
+                    c->cg_fused = f;
+                    c->cg_unroll = u;
+                    ppe_graphs_destroy(c);
+                    float ms = 0.f;
+                    r2 = time_of([&]() -> int {
+                        mps_report pr;
+                        std::memset(&pr, 0, sizeof pr);
+                        int r3 = ppe_solve(c, &pr);
+                        return (r3 == MPS_ECG_NOCONV) ? MPS_OK : r3;
+                    }, &ms);
+                    if (r2) return r2;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best_f = f;
+                        best_u = u;
+                    }
                 }
             }
             c->cg_fused = best_f;
+            c->cg_unroll = best_u;
             ppe_graphs_destroy(c);
             t.cg_fused = best_f ? 1 : 0;
+            t.cg_unroll = best_u;
             t.solve_ms = best_ms;
             return MPS_OK;
         }();
     } else {
         t.spmv_block = c->spmv_block;
         t.cg_fused = c->cg_fused ? 1 : 0;
+        t.cg_unroll = c->cg_unroll;
         if (!rc) {
             // p, n* and flags of a solve at the current state, as after the mixed PPE's tuning
             mps_report rep;

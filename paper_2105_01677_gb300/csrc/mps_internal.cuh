@@ -453,6 +453,7 @@ struct Ctx {
     // tuned by mps_autotune: the FP32 SpMV's block size and the inner CG's form
     int spmv_block = 512;
     bool cg_fused = false;
+    int cg_unroll = 1;      // inner CG iterations per pass of the device-driven loop
     int build_block = 0;    // the row build's block (0: the path's default)
     // capacities the grid-sized buffers were allocated with (the tuner's cell side may
     // derive smaller ones), and an ensemble's scenes (to derive its grid again)

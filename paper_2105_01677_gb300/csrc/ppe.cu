@@ -913,15 +913,19 @@ int add_mixed_solve(Ctx* c, cudaGraph_t G, cudaGraphNode_t dep, double* x, bool 
     if (!(n_init = only_node(B))) return MPS_EDEVICE;
     if ((rc = add_while(c, B, n_init, h_in, &n_inner, &Bi))) return rc;
     MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, Bi, nullptr, nullptr, 0, mode));
-    if (c->cg_fused) {
-        launch_spmv32(c, s, sv, true);
-        k_vec32_cg<<<gv, kBT, 0, s>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_s32, c->cg_q32,
-                                      c->cg, c->partials, &c->st->counter[2], h_in);
-    } else {
-        launch_spmv32(c, s, sv);
-        k_xr32<<<gv, kBT, 0, s>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_q32, c->cg,
-                                  c->partials, &c->st->counter[2]);
-        k_d32<<<gv, kBT, 0, s>>>(n, c->cg_r32, c->cg_d32, c->cg, h_in);
+    // cg_unroll iterations per pass of the loop: once the solve is done the later kernels
+    // of the pass return at once (the conditional is set by the last of them)
+    for (int u = 0; u < c->cg_unroll; u++) {
+        if (c->cg_fused) {
+            launch_spmv32(c, s, sv, true);
+            k_vec32_cg<<<gv, kBT, 0, s>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_s32, c->cg_q32,
+                                          c->cg, c->partials, &c->st->counter[2], h_in);
+        } else {
+            launch_spmv32(c, s, sv);
+            k_xr32<<<gv, kBT, 0, s>>>(n, c->cg_x32, c->cg_r32, c->cg_d32, c->cg_q32, c->cg,
+                                      c->partials, &c->st->counter[2]);
+            k_d32<<<gv, kBT, 0, s>>>(n, c->cg_r32, c->cg_d32, c->cg, h_in);
+        }
     }
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
     MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, B, &n_inner, nullptr, 1, mode));
@@ -953,8 +957,12 @@ void mixed_init_scalars(Ctx* c, CgScalars* init) {
 // Kernels one mixed solve ran (counted like the host loop's launches)
 int64_t mixed_solve_launches(Ctx* c, bool guess, const CgScalars& h) {
     const bool multi = c->n_scenes > 1;
+    // the passes of the inner loop launch cg_unroll iterations each (those after convergence
+    // return at once); counted as if the iterations of a solve filled whole passes
+    const int64_t u = c->cg_unroll;
+    const int64_t inner = (h.total + u - 1) / u * u;
     return (guess ? (multi ? 5 : 3) : 1) + (multi ? 5 : 3) * (int64_t)h.outer +
-           (c->cg_fused ? 2 : 3) * (int64_t)h.total;
+           (c->cg_fused ? 2 : 3) * inner;
 }
 
 namespace {

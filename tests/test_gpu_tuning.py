@@ -90,7 +90,7 @@ def test_autotune_mixed_ensemble():
         t = ens.autotune(2)
         assert t["gather_block"] in (32, 64, 96, 128)
         assert t["spmv_block"] in (256, 512)
-        assert t["cg_fused"] in (0, 1)
+        assert t["cg_fused"] in (0, 1) and t["cg_unroll"] in (1, 2, 4)
         assert t["gather_ms"] > 0 and t["spmv_ms"] > 0 and t["solve_ms"] > 0
         assert t["build_block"] in (64, 128, 256) and t["build_ms"] > 0
         assert t["cell_skin"] in (0.1, 0.05, 0.15, 0.2) and t["cell_ms"] > 0
@@ -180,3 +180,32 @@ def test_autotune_single_scene_cell_side_and_build_block():
     ex = np.abs(got["pos"] - st.pos).max() / sc.l0
     assert ep <= 1e-4, ep
     assert ex <= 1e-6, ex
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+@pytest.mark.parametrize("case", ["3d-guess", "2d-stiff"])
+def test_cg_unroll_changes_nothing(case, fused):
+    """Several inner CG iterations per pass of the device-driven loop: the iterations after
+    convergence return at once, so every field and the iteration counts are bit-identical."""
+    if case == "3d-guess":
+        sc, kw = small_3d(seed=7), dict(dt=5e-5, cg_x0=3)
+    else:
+        sc, kw = scenes.dam_break_2d(seed=8), dict(alpha_c=0.0, clamp_negative_p=0, cg_x0=0)
+    outs = []
+    for u in (1, 2, 4):
+        from paper_2105_01677_gb300 import mps
+        sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
+                             **gpu_params(sc, precision=1, cg_tol=1e-8, inner_cg=fused,
+                                          cg_unroll=u, **kw))
+        try:
+            reps = [sim.step(1)[1] for _ in range(3)]
+            outs.append((reps, sim.read()))
+        finally:
+            sim.close()
+    (r1, s1) = outs[0]
+    for reps, st in outs[1:]:
+        for key in ("p", "n_star", "pos", "vel", "flags"):
+            assert np.array_equal(st[key], s1[key]), key
+        for a, b in zip(reps, r1):
+            assert a["cg_iters"] == b["cg_iters"] and a["cg_outer"] == b["cg_outer"]
+            assert a["cg_resid"] == b["cg_resid"]
