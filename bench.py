@@ -122,6 +122,10 @@ def parse():
                     help="launch every kernel one by one, the bucket build included (profiling: "
                          "identical results; ncu does not see the kernels of graphs with "
                          "conditional nodes)")
+    ap.add_argument("--build-block", type=int, default=0, choices=[0, 64, 128, 256],
+                    help="row build block without the autotuner (profiling; 0: the default)")
+    ap.add_argument("--cell-skin", type=float, default=0.1,
+                    help="cell skin s at creation (the autotuner may choose another)")
     ap.add_argument("--ppe-host-loop", action="store_true",
                     help="drive the mixed PPE solve from the host (profiling: identical results)")
     ap.add_argument("--cg-x0", type=int, default=3, choices=[0, 1, 2, 3],
@@ -318,7 +322,7 @@ def run_gb300(args):
     # --ppe-host-loop: the mixed PPE solve driven from the host instead of one CUDA graph
     # (identical results; ncu cannot profile the kernels of a graph with conditional nodes)
     common = dict(dt=5e-5, cg_tol=1e-8, ppe_host_loop=1 if args.ppe_host_loop else 0,
-                  cg_x0=args.cg_x0,
+                  cg_x0=args.cg_x0, build_block=args.build_block, cell_skin=args.cell_skin,
                   step_graph=2 if args.no_graphs else (0 if args.no_step_graph else 1))
 
     def timed_steps(sim, k, profile=False, profile_steps=20):
