@@ -77,15 +77,16 @@ ISSUED_FLOPS_LIST_TEST, ISSUED_FLOPS_PPE_PAIR, ISSUED_FLOPS_PND_PAIR = 8.0, 133.
 # list entry its slot read (4 B); per particle r* (hi and lo float4: 32 B) read and n*,
 # flag, diagonal (FP64 and FP32), right-hand side and the two list counts written (37 B).
 BUILD_BYTES_PER_COEF, BUILD_BYTES_PER_LIST_ENTRY, BUILD_BYTES_PER_PARTICLE = 12.0, 4.0, 69.0
-# DRAM bytes (read + write) per PPE coefficient of one launch, from the ncu capture in
+# DRAM bytes (read + write) per PPE coefficient of one launch, from the ncu captures in
 # profiles/kernels_dam_break_3d_227k_mixed.md (227,136-particle case, 25.19 M coefficients,
-# rows grouped 8 entries per row): FP32 SpMV 202.1 + 0.5 MB, build 162.0 + 286.2 MB,
-# float-float residual 306.4 + 1.2 MB; the gather per candidate-list entry (31.09 M):
-# 6.5 + 76.1 MB.  The rows and lists scale with the coefficients and entries.
-SPMV_TRAFFIC_PER_COEF = (202.10e6 + 0.48e6) / 25.19e6
-BUILD_TRAFFIC_PER_COEF = (161.98e6 + 286.24e6) / 25.19e6
-RESID_TRAFFIC_PER_COEF = (306.44e6 + 1.16e6) / 25.19e6
-GATHER_TRAFFIC_PER_ENTRY = (6.52e6 + 76.14e6) / 31.086e6
+# rows grouped 8 entries per row, cell skin 0.05, 256-thread build): FP32 SpMV 208.7 + 3.8
+# MB, build 163.4 + 290.1 MB, float-float residual 316.3 + 4.3 MB; the gather per
+# candidate-list entry (31.09 M): 6.2 + 77.5 MB.  The rows and lists scale with the
+# coefficients and entries.
+SPMV_TRAFFIC_PER_COEF = (208.70e6 + 3.84e6) / 25.19e6
+BUILD_TRAFFIC_PER_COEF = (163.36e6 + 290.07e6) / 25.19e6
+RESID_TRAFFIC_PER_COEF = (316.26e6 + 4.28e6) / 25.19e6
+GATHER_TRAFFIC_PER_ENTRY = (6.20e6 + 77.45e6) / 31.086e6
 
 
 def parse():
