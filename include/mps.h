@@ -148,6 +148,9 @@ typedef struct {
     int32_t cg_unroll;        /* device-driven mixed solve: inner CG iterations per pass of its *
                                * conditional loop (1, 2 or 4; 0: 1); the iterations after     *
                                * convergence return at once (results identical)                */
+    int32_t predict_tpr;      /* threads per FLUID row of the prediction: 1, 2 or 4 (0: 1); the *
+                               * row's viscosity sums are added across them, so the rounding   *
+                               * changes (well within the parity bounds)                        */
     void* stream;             /* cudaStream_t to run on, or NULL for a library-owned stream    */
     mps_alloc_fn alloc;       /* optional device allocator (see above)                        */
     mps_release_fn release;
@@ -356,6 +359,8 @@ int mps_create_ensemble(const double* pos, const double* vel, const int8_t* type
  *     list capacity) is derived again for each, and afterwards params.cell_skin is the
  *     chosen s (so a step's MPS_ESKIN limit is s max(re)/2 of that s);
  *   - the candidate gather's cell block: 32, 64, 96 or 128 threads (params.gather_block);
+ *   - the prediction's threads per FLUID row: 1, 2 or 4 (each takes every 2nd or 4th
+ *     candidate of the row's list; the row's sums are added across them);
  *   - the row build's block: 64, 128 or 256 threads (params.build_block);
  *   - mixed PPE only, on the system of a solve at the current state: the FP32 SpMV's block,
  *     256 or 512 threads, and the inner CG as three kernels per iteration (SpMV; x, r
@@ -377,13 +382,14 @@ typedef struct {
     int32_t cg_fused;       /* 1: the inner CG in two kernels per iteration, 0: three        */
     int32_t build_block;    /* threads per block of the row build                            */
     int32_t cg_unroll;      /* inner CG iterations per pass of the solve's conditional loop   */
-    int32_t pad;
+    int32_t predict_tpr;    /* threads per FLUID row of the prediction                        */
     double gather_ms;       /* the chosen gather's time [ms]                                 */
     double spmv_ms;         /* the chosen SpMV's time [ms] (0 without a mixed PPE)            */
     double solve_ms;        /* a mixed solve's time with the chosen form [ms] (0 without)     */
     double build_ms;        /* the chosen row build's time [ms]                              */
     double cell_skin;       /* the chosen cell skin s (cell side h = max(re)(1 + s))         */
     double cell_ms;         /* bucket build + candidate gather with the chosen cells [ms]    */
+    double predict_ms;      /* the chosen prediction's time [ms]                             */
 } mps_tuning;
 int mps_autotune(mps_ctx* ctx, int32_t repeats, mps_tuning* out);
 

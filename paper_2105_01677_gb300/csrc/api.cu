@@ -167,6 +167,8 @@ int check_params(const mps_params* P) {
     if (P->step_graph < 0 || P->step_graph > 2) return MPS_EINVAL;
     if (P->cg_unroll != 0 && P->cg_unroll != 1 && P->cg_unroll != 2 && P->cg_unroll != 4)
         return MPS_EINVAL;
+    if (P->predict_tpr != 0 && P->predict_tpr != 1 && P->predict_tpr != 2 && P->predict_tpr != 4)
+        return MPS_EINVAL;
     if (P->kernel < 0 || P->kernel > 1 || P->gradient_form < 0 || P->gradient_form > 1 ||
         P->source_term < 0 || P->source_term > 2 || (P->source_term >= 1 && P->kernel != 0))
         return MPS_EINVAL;
@@ -826,6 +828,7 @@ int mps_create(const double* pos, const double* vel, const int8_t* types, int64_
     c->spmv_block = params->spmv_block ? params->spmv_block : 512;
     c->build_block = params->build_block;
     c->cg_unroll = params->cg_unroll ? params->cg_unroll : 1;
+    c->predict_tpr = params->predict_tpr ? params->predict_tpr : 1;
     c->last_cg_iters = 8;
     if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, params->device) != cudaSuccess) {
         delete c;
@@ -881,6 +884,7 @@ int mps_create_ensemble(const double* pos, const double* vel, const int8_t* type
     c->spmv_block = P.spmv_block ? P.spmv_block : 512;
     c->build_block = P.build_block;
     c->cg_unroll = P.cg_unroll ? P.cg_unroll : 1;
+    c->predict_tpr = P.predict_tpr ? P.predict_tpr : 1;
     c->scenes_host.assign(scenes, scenes + n_scenes);
     c->n = n;
     c->steps_done = 0;
@@ -1018,11 +1022,32 @@ int mps_autotune(mps_ctx* c, int32_t repeats, mps_tuning* out) {
         t.gather_ms = best_ms;
         return MPS_OK;
     }();
-    // ---- the row build's block, on the lists just gathered and the prediction from them
+    // ---- the prediction's threads per row and the row build's block, on the lists just
+    // gathered (and the prediction from them)
     if (!rc) rc = [&]() -> int {
         MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), c->stream));
         launch_verlet(c);
         launch_copy_state_star(c);
+        {
+            int best = c->predict_tpr, r2;
+            float best_ms = 1e30f;
+            for (int tpr : {1, 2, 4}) {
+                c->predict_tpr = tpr;
+                float ms = 0.f;
+                r2 = time_of([&]() -> int {
+                    launch_predict_rows(c);
+                    return MPS_OK;
+                }, &ms);
+                if (r2) return r2;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = tpr;
+                }
+            }
+            c->predict_tpr = best;
+            t.predict_tpr = best;
+            t.predict_ms = best_ms;
+        }
         launch_predict_rows(c);
         if (c->prm.pressure_mode == 0 && c->prm.source_term == 2) launch_ecs_rates(c);
         int best = build_block_of(c), r2;

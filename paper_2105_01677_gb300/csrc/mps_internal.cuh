@@ -455,6 +455,7 @@ struct Ctx {
     bool cg_fused = false;
     int cg_unroll = 1;      // inner CG iterations per pass of the device-driven loop
     int build_block = 0;    // the row build's block (0: the path's default)
+    int predict_tpr = 1;    // threads per row of the prediction (tuned: 1, 2 or 4)
     // capacities the grid-sized buffers were allocated with (the tuner's cell side may
     // derive smaller ones), and an ensemble's scenes (to derive its grid again)
     int cap_v_alloc = 0;

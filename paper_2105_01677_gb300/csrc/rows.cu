@@ -103,12 +103,18 @@ struct PredictArgs {
     const double* g_dev;    // non-null: the acceleration is read here (a step graph's control block)
 };
 
-// MULTI: an ensemble, whose radii and coefficients are those of each row's scene
-template <bool MIXED, bool MULTI>
+// MULTI: an ensemble, whose radii and coefficients are those of each row's scene.
+// TPR threads per FLUID row (the bucket build's list of FLUID slots; adjacent lanes): thread
+// t of a row takes the candidates t, t + TPR, ... of its list, so each walks a chain TPR
+// times shorter; their sums are added across the lanes and the first one writes the row.
+template <bool MIXED, bool MULTI, int TPR>
 __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
-    // one thread per FLUID row (the bucket build's list of FLUID slots)
     const int tid = blockIdx.x * kBT + threadIdx.x;
-    const int i = tid < (int)*a.nrows ? a.rows[tid] : -1;
+    const int row = tid / TPR, sub = tid % TPR;
+    const int i = row < (int)*a.nrows ? a.rows[row] : -1;
+    // the lanes of one row (valid or not together)
+    const unsigned row_mask = TPR == 1 ? (1u << (threadIdx.x & 31))
+                                       : (((1u << TPR) - 1u) << ((threadIdx.x & 31) & ~(TPR - 1)));
     double disp = 0.0;
     if (i >= 0) {
         Radius R = a.r;
@@ -132,23 +138,24 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
         // FP32 terms in compensated (Kahan) FP32 sums: value f, running correction e
         float f0 = 0.f, f1 = 0.f, f2 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f;
-        // two-stage software pipeline: the slot of k+2 and the position of k+1 are in flight
-        int jn = cnt > 1 ? a.vcol[sell8(i, 1, a.cap_v)] : 0;
-        int j0 = cnt > 0 ? a.vcol[sell8(i, 0, a.cap_v)] : 0;
+        // two-stage software pipeline: the slot two candidates ahead and the position of the
+        // next one are in flight (this thread's candidates: sub, sub + TPR, ...)
+        int jn = cnt > sub + TPR ? a.vcol[sell8(i, sub + TPR, a.cap_v)] : 0;
+        int j0 = cnt > sub ? a.vcol[sell8(i, sub, a.cap_v)] : 0;
         float4 qn = a.pos32[j0];
-        // mixed: the FP32 velocity of k+1 is in flight with its position (nearly every
-        // candidate is a member)
+        // mixed: the FP32 velocity of the next candidate is in flight with its position
+        // (nearly every candidate is a member)
         float4 vn = MIXED ? a.vel32[j0] : make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int k = 0; k < cnt; k++) {
+        for (int k = sub; k < cnt; k += TPR) {
             const int j = j0;
             const float4 jh = qn;
             const float4 vj = vn;
             j0 = jn;
-            if (k + 1 < cnt) {
+            if (k + TPR < cnt) {
                 qn = a.pos32[jn];
                 if (MIXED) vn = a.vel32[jn];
             }
-            if (k + 2 < cnt) jn = a.vcol[sell8(i, k + 2, a.cap_v)];
+            if (k + 2 * TPR < cnt) jn = a.vcol[sell8(i, k + 2 * TPR, a.cap_v)];
             const float r2 = dist2_f(ih, jh);
             int t = tier1(r2, R);
             if (t == 2)
@@ -188,6 +195,12 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
             pi = a.pos[i];
             ui = a.vel[i];
         }
+        // the row's sums from its TPR threads (the same bits in each: a + b = b + a)
+        for (int o = 1; o < TPR; o <<= 1) {
+            s0 += __shfl_xor_sync(row_mask, s0, o);
+            s1 += __shfl_xor_sync(row_mask, s1, o);
+            s2 += __shfl_xor_sync(row_mask, s2, o);
+        }
         // u* = u + dt (nu lap(u) + g); r* = r + dt u*  (one rounding per operation)
         const double l0 = coef_lap * s0, l1 = coef_lap * s1, l2 = coef_lap * s2;
         double4 us, ps;
@@ -202,20 +215,22 @@ __global__ void __launch_bounds__(kBT) k_predict(PredictArgs a) {
         ps.y = __dadd_rn(pi.y, __dmul_rn(a.dt, us.y));
         ps.z = __dadd_rn(pi.z, __dmul_rn(a.dt, us.z));
         ps.w = 0.0;
-        a.vel_star[i] = us;
-        a.pos_star[i] = ps;
-        float4 h4, l4;
-        split_rel(ps.x, a.bmin0, &h4.x, &l4.x);
-        split_rel(ps.y, a.bmin1, &h4.y, &l4.y);
-        split_rel(ps.z, a.bmin2, &h4.z, &l4.z);
-        h4.w = ih.w;
-        l4.w = 0.f;
-        a.pos32_star[i] = h4;
-        a.pff_star[2 * i] = h4;
-        a.pff_star[2 * i + 1] = l4;
-        const double4 pb = a.pos_b ? a.pos_b[i] : pi;
-        const double dx = ps.x - pb.x, dy = ps.y - pb.y, dz = ps.z - pb.z;
-        disp = fma(dz, dz, fma(dy, dy, dx * dx));   // squared; the host takes the root
+        if (sub == 0) {
+            a.vel_star[i] = us;
+            a.pos_star[i] = ps;
+            float4 h4, l4;
+            split_rel(ps.x, a.bmin0, &h4.x, &l4.x);
+            split_rel(ps.y, a.bmin1, &h4.y, &l4.y);
+            split_rel(ps.z, a.bmin2, &h4.z, &l4.z);
+            h4.w = ih.w;
+            l4.w = 0.f;
+            a.pos32_star[i] = h4;
+            a.pff_star[2 * i] = h4;
+            a.pff_star[2 * i + 1] = l4;
+            const double4 pb = a.pos_b ? a.pos_b[i] : pi;
+            const double dx = ps.x - pb.x, dy = ps.y - pb.y, dz = ps.z - pb.z;
+            disp = fma(dz, dz, fma(dy, dy, dx * dx));   // squared; the host takes the root
+        }
     }
     // warp max of the squared displacement (non-negative doubles order like their bits)
     unsigned long long v = (unsigned long long)__double_as_longlong(disp);
@@ -797,6 +812,16 @@ void launch_ecs_rates(Ctx* c) {
     c->launches += 1;
 }
 
+// threads per row of the prediction (tuned: 1, 2 or 4)
+template <bool MIXED, bool MULTI>
+static void predict_tpr(Ctx* c, const PredictArgs& a) {
+    const int tpr = c->predict_tpr;
+    const int grid = (int)(((int64_t)c->n * tpr + kBT - 1) / kBT);
+    if (tpr == 4) k_predict<MIXED, MULTI, 4><<<grid, kBT, 0, c->stream>>>(a);
+    else if (tpr == 2) k_predict<MIXED, MULTI, 2><<<grid, kBT, 0, c->stream>>>(a);
+    else k_predict<MIXED, MULTI, 1><<<grid, kBT, 0, c->stream>>>(a);
+}
+
 void launch_predict_rows(Ctx* c) {
     const mps_params& P = c->prm;
     PredictArgs a;
@@ -831,16 +856,15 @@ void launch_predict_rows(Ctx* c) {
     a.bmin0 = c->grid.bmin[0];
     a.bmin1 = c->grid.bmin[1];
     a.bmin2 = c->grid.bmin[2];
-    const int grid = (int)((c->n + kBT - 1) / kBT);
     a.sid = c->sid;
     a.scn = c->scn;
     const bool multi = c->n_scenes > 1;
     if (P.precision == 1) {
-        if (multi) k_predict<true, true><<<grid, kBT, 0, c->stream>>>(a);
-        else k_predict<true, false><<<grid, kBT, 0, c->stream>>>(a);
+        if (multi) predict_tpr<true, true>(c, a);
+        else predict_tpr<true, false>(c, a);
     } else {
-        if (multi) k_predict<false, true><<<grid, kBT, 0, c->stream>>>(a);
-        else k_predict<false, false><<<grid, kBT, 0, c->stream>>>(a);
+        if (multi) predict_tpr<false, true>(c, a);
+        else predict_tpr<false, false>(c, a);
     }
     c->launches += 1;
 }

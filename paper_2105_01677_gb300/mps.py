@@ -39,7 +39,7 @@ class mps_params(C.Structure):
                 ("list_every", C.c_int32), ("kernel", C.c_int32), ("gradient_form", C.c_int32),
                 ("source_term", C.c_int32), ("ppe_host_loop", C.c_int32),
                 ("cg_x0", C.c_int32), ("step_graph", C.c_int32), ("inner_cg", C.c_int32),
-                ("spmv_block", C.c_int32), ("build_block", C.c_int32), ("bucket_sort", C.c_int32), ("cg_unroll", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
+                ("spmv_block", C.c_int32), ("build_block", C.c_int32), ("bucket_sort", C.c_int32), ("cg_unroll", C.c_int32), ("predict_tpr", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("release", RELEASE_FN),
                 ("alloc_user", C.c_void_p)]
 
 
@@ -64,15 +64,13 @@ class mps_report(C.Structure):
 
 class mps_tuning(C.Structure):
     _fields_ = [("gather_block", C.c_int32), ("spmv_block", C.c_int32), ("cg_fused", C.c_int32),
-                ("build_block", C.c_int32), ("cg_unroll", C.c_int32), ("pad", C.c_int32),
+                ("build_block", C.c_int32), ("cg_unroll", C.c_int32), ("predict_tpr", C.c_int32),
                 ("gather_ms", C.c_double), ("spmv_ms", C.c_double),
                 ("solve_ms", C.c_double), ("build_ms", C.c_double), ("cell_skin", C.c_double),
-                ("cell_ms", C.c_double)]
+                ("cell_ms", C.c_double), ("predict_ms", C.c_double)]
 
     def as_dict(self) -> dict:
-        d = {k: getattr(self, k) for k, _ in self._fields_}
-        d.pop("pad")
-        return d
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class mps_vjp_report(C.Structure):

@@ -65,8 +65,9 @@ int main(void) {
   P(mps_params, gather_block) P(mps_params, kernel) P(mps_params, source_term)
   P(mps_params, ppe_host_loop) P(mps_params, cg_x0) P(mps_params, spmv_block)
   P(mps_params, build_block) P(mps_params, bucket_sort) P(mps_params, cg_unroll)
-  P(mps_tuning, build_block) P(mps_tuning, cg_unroll) P(mps_tuning, gather_ms) P(mps_tuning, build_ms)
-  P(mps_tuning, cell_skin) P(mps_tuning, cell_ms)
+  P(mps_params, predict_tpr)
+  P(mps_tuning, build_block) P(mps_tuning, cg_unroll) P(mps_tuning, predict_tpr) P(mps_tuning, gather_ms) P(mps_tuning, build_ms)
+  P(mps_tuning, cell_skin) P(mps_tuning, cell_ms) P(mps_tuning, predict_ms)
   P(mps_report, list_gathered)
   P(mps_report, cg_resid) P(mps_report, n_surface) P(mps_report, max_disp) P(mps_report, lambda)
   P(mps_report, steps_done) P(mps_report, cand_tests) P(mps_report, pairs_pnd)
@@ -121,7 +122,7 @@ def test_invalid_arguments_rejected_before_device_use(L):
                dict(gradient_form=3), dict(source_term=1, kernel=1), dict(source_term=3),
                dict(precision=1, ppe_operator=1, kernel=1), dict(cg_x0=4), dict(cg_x0=-1), dict(ppe_host_loop=2),
                dict(build_block=96), dict(build_block=512), dict(spmv_block=128),
-               dict(gather_block=48), dict(bucket_sort=2), dict(cg_unroll=3),
+               dict(gather_block=48), dict(bucket_sort=2), dict(cg_unroll=3), dict(predict_tpr=3),
                dict(step_graph=3)):
         P = mps.mps_params_default(**kw)
         rc = L.mps_create(pos.ctypes.data_as(C.POINTER(C.c_double)), None,

@@ -111,14 +111,21 @@ def test_ensemble_multi_step_mixed_runs_and_converges():
 
 
 def test_autotune_keeps_results_bitwise():
+    """On the FP64 path the tuned launch shapes (gather block, build block) change no bit;
+    the prediction's threads per row change the order of its sums, so the untuned run takes
+    the tuner's choice of those."""
     from paper_2105_01677_gb300 import mps
     E = _ensemble(count=4, seed=7)
     outs = []
-    for tune in (False, True):
-        ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, cg_tol=1e-10)
+    tpr = 1
+    for tune in (True, False):
+        ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, cg_tol=1e-10,
+                           predict_tpr=tpr)
         try:
             if tune:
-                assert ens.autotune(2)["gather_block"] in (32, 64, 96, 128)
+                t = ens.autotune(2)
+                assert t["gather_block"] in (32, 64, 96, 128)
+                tpr = t["predict_tpr"]
             ens.step(2)
             outs.append(ens.read())
         finally:

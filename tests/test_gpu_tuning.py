@@ -91,6 +91,7 @@ def test_autotune_mixed_ensemble():
         assert t["gather_block"] in (32, 64, 96, 128)
         assert t["spmv_block"] in (256, 512)
         assert t["cg_fused"] in (0, 1) and t["cg_unroll"] in (1, 2, 4)
+        assert t["predict_tpr"] in (1, 2, 4) and t["predict_ms"] > 0
         assert t["gather_ms"] > 0 and t["spmv_ms"] > 0 and t["solve_ms"] > 0
         assert t["build_block"] in (64, 128, 256) and t["build_ms"] > 0
         assert t["cell_skin"] in (0.1, 0.05, 0.15, 0.2) and t["cell_ms"] > 0
@@ -209,3 +210,43 @@ def test_cg_unroll_changes_nothing(case, fused):
         for a, b in zip(reps, r1):
             assert a["cg_iters"] == b["cg_iters"] and a["cg_outer"] == b["cg_outer"]
             assert a["cg_resid"] == b["cg_resid"]
+
+
+@pytest.mark.parametrize("tpr", [2, 4])
+@pytest.mark.parametrize("case", ["2d-fp64", "3d-fp64", "3d-mixed", "ensemble-mixed"])
+def test_prediction_threads_per_row_parity(case, tpr):
+    """Two or four threads per FLUID row in the prediction: its viscosity sums are added in
+    another order, so the step stays within the oracle parity bounds (FP64: 1e-10 relative;
+    mixed: the mixed bound); neighbour sets, and so the flags, are unchanged."""
+    from paper_2105_01677_gb300 import mps
+    if case == "ensemble-mixed":
+        E = scenes.ensemble_2d(count=4, seed=12, fluid=(500, 2000))
+        ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
+                           cg_tol=1e-8, predict_tpr=tpr)
+        try:
+            rc, rep = ens.step(1)
+            got = ens.read()
+        finally:
+            ens.close()
+        assert rc == 0
+        for k in (0, len(E) - 1):
+            orep, ost, prm = run_oracle(E[k], dt=1e-4, cg_tol=PARITY_CG_TOL)
+            _mixed_bound(E[k], got[k], ost)
+            assert np.array_equal(got[k]["flags"], ost.flags)
+        return
+    if case == "2d-fp64":
+        sc, kw = scenes.dam_break_2d(seed=1), dict(precision=0, dt=1e-4)
+    elif case == "3d-fp64":
+        sc, kw = small_3d(seed=2), dict(precision=0, dt=5e-5)
+    else:
+        sc, kw = small_3d(seed=3), dict(precision=1, dt=5e-5)
+    tol = PARITY_CG_TOL if kw["precision"] == 0 else 1e-8
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc, cg_tol=tol, predict_tpr=tpr, **kw))
+    orep, ost, prm = run_oracle(sc, cg_tol=PARITY_CG_TOL, dt=kw["dt"])
+    assert rc == 0
+    if kw["precision"] == 0:
+        for key, ref in (("p", ost.p), ("vel", ost.vel)):
+            assert rel_err(got[key], ref) <= FP64_TOL, key
+    else:
+        _mixed_bound(sc, got, ost)
+    assert np.array_equal(got["flags"], ost.flags)
