@@ -181,6 +181,11 @@ typedef struct {
     int32_t step_graph;       /* 1 if the step ran as one CUDA graph launch                    */
     int32_t n_fast;           /* FLUID particles that moved more than half the cell skin: their *
                                * candidate lists were completed by a direct search at r*      */
+    int32_t bucket_merged;    /* the step's bucket build: 1 merged the particles whose cell    *
+                               * changed into the previous order, 0 radix-sorted, -1 none (kept *
+                               * lists)                                                        */
+    int64_t n_moved;          /* particles whose cell key changed since the previous build     *
+                               * (counted by graph-run builds; 0 launched kernel by kernel)     */
 } mps_report;
 
 /* Opaque context: device buffers, stream and derived constants of one particle system. */

@@ -664,6 +664,8 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         const DevStatus& s = *c->st_host;
         if (fresh) c->n_ghost_last = s.n_ghost;
         rep->n_ghost = c->n_ghost_last;
+        rep->bucket_merged = fresh ? c->last_bucket_merged : -1;
+        rep->n_moved = fresh ? (int64_t)s.n_mov : 0;
         rep->n_surface = s.n_surface;
         rep->n_ppe_rows = s.n_ppe;
         rep->max_disp = std::sqrt(bits_to_double(s.max_disp_bits));   // device keeps the square

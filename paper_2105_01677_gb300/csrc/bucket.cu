@@ -461,6 +461,7 @@ int bucket_launches(Ctx* c, bool mutate) {
     launch_radix(c);
     int rc = launch_table_rest(c);
     if (!rc) c->order_valid = true;
+    c->last_bucket_merged = 0;
     return rc;
 }
 
@@ -569,6 +570,7 @@ void bucket_branch_count(Ctx* c, const DevStatus& st) {
     if (c->pending_branch < 0) return;
     const bool inc = c->pending_branch != 0 && st.n_mov <= (unsigned)c->mov_cap;
     c->launches += inc ? c->bucket_inc_launches : c->bucket_radix_launches;
+    c->last_bucket_merged = inc ? 1 : 0;
     c->pending_branch = -1;
 }
 

@@ -418,6 +418,7 @@ struct Ctx {
     bool order_valid = false;          // host: what order_ok is set to before the next build
     int64_t bucket_inc_launches = 0, bucket_radix_launches = 0;   // kernels of either branch
     int pending_branch = -1;   // a graph bucket build ran with this order_ok, branch not counted
+    int last_bucket_merged = 0;   // the last bucket build merged its movers (1) or radix-sorted
     // two-phase flow: per-particle density / viscosity in original order (as given) and in
     // slot order (gathered by id after every reordering); null when uniform
     double *rho_id = nullptr, *nu_id = nullptr;

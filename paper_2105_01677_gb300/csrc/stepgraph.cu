@@ -366,6 +366,8 @@ int step_graph_step(Ctx* c, mps_report* rep) {
     rep->n_fast = 0;
     c->launches += sg->launches_pre + attempts * sg->launches_attempt;
     bucket_branch_count(c, st);
+    rep->bucket_merged = c->last_bucket_merged;
+    rep->n_moved = (int64_t)st.n_mov;
     c->list_age = 0;
     c->need_list = false;
     if (st.err) {

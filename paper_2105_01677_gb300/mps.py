@@ -54,7 +54,7 @@ class mps_report(C.Structure):
                 ("n0_pnd", C.c_double), ("n0_lap", C.c_double), ("lambda_", C.c_double),
                 ("steps_done", C.c_int64), ("cand_tests", C.c_int64), ("pairs_ppe", C.c_int64),
                 ("pairs_pnd", C.c_int64), ("list_tests", C.c_int64), ("step_graph", C.c_int32),
-                ("n_fast", C.c_int32)]
+                ("n_fast", C.c_int32), ("bucket_merged", C.c_int32), ("n_moved", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -71,7 +71,7 @@ int main(void) {
   P(mps_report, list_gathered)
   P(mps_report, cg_resid) P(mps_report, n_surface) P(mps_report, max_disp) P(mps_report, lambda)
   P(mps_report, steps_done) P(mps_report, cand_tests) P(mps_report, pairs_pnd)
-  P(mps_report, list_tests)
+  P(mps_report, list_tests) P(mps_report, bucket_merged) P(mps_report, n_moved)
   P(mps_vjp_report, cg_iters) P(mps_vjp_report, cg_resid) P(mps_vjp_report, forward)
   return 0;
 }

@@ -40,7 +40,7 @@ def _cells(pos, bmin, h):
     return np.floor((pos - np.asarray(bmin)[: pos.shape[1]]) / h).astype(np.int64)
 
 
-def _run(make, nsteps, **kw):
+def _run(make, nsteps, reports=None, **kw):
     sim = make(**kw)
     try:
         states, crossed = [], 0
@@ -49,6 +49,8 @@ def _run(make, nsteps, **kw):
         for _ in range(nsteps):
             rc, rep = sim.step(1)
             assert rc == 0
+            if reports is not None:
+                reports.append(rep)
             st = sim.read()
             states.append(st)
             if h is not None:
@@ -87,9 +89,15 @@ def test_merged_order_equals_radix_order(case):
         sim.scene = sc
         return sim
 
-    merged, crossed = _run(make, 8, bucket_sort=0)
-    radix, _ = _run(make, 8, bucket_sort=1)
+    rm, rr = [], []
+    merged, crossed = _run(make, 8, rm, bucket_sort=0)
+    radix, _ = _run(make, 8, rr, bucket_sort=1)
     assert crossed > 0, "no particle changed its cell: the merge was not exercised"
+    # the first build sorts from scratch; the (graph-run) builds after it merge
+    assert rm[0]["bucket_merged"] == 0
+    assert all(r["bucket_merged"] == 1 for r in rm[1:])
+    assert all(r["bucket_merged"] == 0 for r in rr)
+    assert sum(r["n_moved"] for r in rm[1:]) > 0
     _same(merged, radix)
 
 
@@ -129,3 +137,34 @@ def test_write_state_starts_from_the_radix_sort():
         finally:
             sim.close()
     _same([out[0]], [out[1]])
+
+
+@pytest.mark.parametrize("speed, skin, merged", [(100.0, 1.0, 1), (300.0, 1.2, 0)])
+def test_many_movers(speed, skin, merged):
+    """The full 3D dam break, off its lattice, in a shear flow along x (0 at the bottom of
+    the column in y to 100 or 300 m/s at its top; dt 5e-5, equation of state, cell skin 1 or
+    1.2): 5,000-8,000 particles change cells per step (merged), or more than the 16,384
+    movers the merge records (the radix sort takes over); either way the trajectory equals
+    the radix sort's bit for bit."""
+    from paper_2105_01677_gb300 import mps
+    sc = _stirred(scenes.dam_break_3d(seed=9), 0.0, 15)   # off the lattice, at rest
+    f = sc.types == scenes.FLUID
+    y = sc.pos[f, 1]
+    sc.vel[f, 0] = speed * (y - y.min()) / (y.max() - y.min())
+    outs, reps = [], []
+    for bs in (0, 1):
+        sim = mps.Simulation(sc, torch_alloc=True, use_torch_stream=True,
+                             **gpu_params(sc, precision=1, pressure_mode=1, dt=5e-5,
+                                          cell_skin=skin, bucket_sort=bs))
+        try:
+            rr = [sim.step(1)[1] for _ in range(3)]
+            outs.append(sim.read())
+            reps.append(rr)
+        finally:
+            sim.close()
+    assert all(r["bucket_merged"] == merged for r in reps[0][1:])
+    if merged:
+        assert all(1000 < r["n_moved"] <= 16384 for r in reps[0][1:])
+    else:
+        assert all(r["n_moved"] > 16384 for r in reps[0][1:])
+    _same([outs[0]], [outs[1]])
