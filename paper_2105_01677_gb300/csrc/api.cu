@@ -570,7 +570,6 @@ void stage_collect(Ctx* c, const bool* used) {
     }
 }
 
-constexpr double kMinListSkin = 0.02;
 
 // Candidate lists of the next gather within max(re)(1 + skin) of every scene, with the FP32
 // bands of the grid in force.
@@ -700,7 +699,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     }
     if (adapt) {
         // next list skin: three times what the motion of the lists' lifetime needs at this
-        // step's displacement, within [0.02, cell_skin]
+        // step's displacement, within [kMinListSkin, cell_skin]
         const double need = 2.0 * rep->max_disp / re_max * (keep ? P.list_every : 1);
         c->list_skin = std::min(P.cell_skin, std::max(kMinListSkin, 3.0 * need));
     }

@@ -249,6 +249,10 @@ void launch_ecs_rates(Ctx* c);
 void launch_check_stage(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types);
 void launch_same_state(Ctx* c, const double* d_pos, const double* d_vel, const int8_t* d_types);
 
+// smallest skin of the candidate lists (relative to max(re)): the next gather takes three
+// times what the last step's largest displacement needs, never less than this
+constexpr double kMinListSkin = 0.02;
+
 // ---------------------------------------------------------------- context
 // The mixed PPE solve captured as one CUDA graph (outer refinement loop around the inner
 // FP32 CG loop, both conditional WHILE nodes set by the kernels), one per buffer that the

@@ -386,8 +386,8 @@ int step_graph_step(Ctx* c, mps_report* rep) {
         return rc;
     }
     // next list skin: three times what this step's displacement needs, within
-    // [0.02, cell_skin] (as the host-driven step)
-    c->list_skin = std::min(P.cell_skin, std::max(0.02, 3.0 * (2.0 * rep->max_disp / re_max)));
+    // [kMinListSkin, cell_skin] (as the host-driven step)
+    c->list_skin = std::min(P.cell_skin, std::max(kMinListSkin, 3.0 * (2.0 * rep->max_disp / re_max)));
     c->launches += sg->launches_post;
     if (ppe) {
         const CgScalars& cg = *c->cg_host;
