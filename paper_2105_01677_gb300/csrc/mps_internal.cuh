@@ -293,6 +293,7 @@ struct StepCtl {
 // buffers), with the buffer assignment it leaves behind and its kernel counts.
 struct StepGraph {
     const double4* pos = nullptr;
+    bool kept = false;   // a step on kept candidate lists: no bucket build, no gather
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t launches_pre = 0, launches_attempt = 0, launches_post = 0;
@@ -355,7 +356,7 @@ struct Ctx {
     // mirror), the two scene tables of an ensemble (adaptive and full list skin), the pinned
     // copy of the per-scene residual sums, and the control block kernels read while a step
     // is being captured (null otherwise)
-    StepGraph step_graph[2];
+    StepGraph step_graph[4];   // (starting buffer) x (fresh lists, kept lists)
     StepCtl* ctl = nullptr;
     StepCtl* ctl_host = nullptr;
     Radius* rv_var = nullptr;          // ensemble: candidate radius of every scene, 2 skins

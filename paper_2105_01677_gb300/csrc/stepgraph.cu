@@ -172,8 +172,26 @@ int capture_step(Ctx* c, StepGraph* sg, cudaGraph_t G) {
     cudaGraphNode_t n_st = capture_tail(s);
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
     if (!n_st) return MPS_EDEVICE;
-    // (the bucket build's permutation also writes r* := r)
-    if ((rc = bucket_append(c, G, n_st, &n_pre))) return rc;
+    if (sg->kept) {
+        // kept candidate lists: the state stays in its order, r* := r copied
+        MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, G, &n_st, nullptr, 1, mode));
+        launch_copy_state_star(c);
+        n_pre = capture_tail(s);
+        MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+        if (!n_pre) return MPS_EDEVICE;
+    } else {
+        // (the bucket build's permutation also writes r* := r)
+        if ((rc = bucket_append(c, G, n_st, &n_pre))) return rc;
+        if (P.list_every > 1) {
+            // the positions the lists are gathered at
+            MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, G, &n_pre, nullptr, 1, mode));
+            MPS_CUDA(c, cudaMemcpyAsync(c->pos_b, c->pos, n * sizeof(double4),
+                                        cudaMemcpyDeviceToDevice, s));
+            n_pre = capture_tail(s);
+            MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
+            if (!n_pre) return MPS_EDEVICE;
+        }
+    }
     sg->launches_pre = c->launches - l;
     // ---- WHILE (retry): candidate lists, prediction, build, check
     if ((rc = add_cond(c, G, n_pre, h_loop, cudaGraphCondTypeWhile, &n_loop, &L))) return rc;
@@ -183,8 +201,10 @@ int capture_step(Ctx* c, StepGraph* sg, cudaGraph_t G) {
     k_attempt_begin<<<S > 1 ? (S + 255) / 256 : 1, 256, 0, s>>>(c->ctl, c->st, c->scn,
                                                                  S > 1 ? c->rv_var : nullptr, S,
                                                                  h_loop);
-    MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), s));
-    launch_verlet(c);
+    if (!sg->kept) {
+        MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), s));
+        launch_verlet(c);
+    }
     launch_predict_rows(c);
     if (ppe && P.source_term == 2) launch_ecs_rates(c);
     MPS_CUDA(c, cudaMemsetAsync(c->nstar, 0, n * sizeof(double), s));
@@ -273,7 +293,6 @@ bool step_graph_eligible(const Ctx* c, bool advance) {
     const mps_params& P = c->prm;
     return P.step_graph == 1 && advance && !c->vjp && !c->profiling && !c->force_host &&
            !c->graphs_off &&
-           P.list_every <= 1 &&
            (P.pressure_mode == 1 || (P.precision == 1 && P.ppe_host_loop == 0));
 }
 
@@ -291,14 +310,20 @@ int step_graph_step(Ctx* c, mps_report* rep) {
     const double re_max = c->re_skin;
     int rc;
     if ((rc = alloc_ctl(c))) return rc;
+    // candidate lists kept across steps (list_every > 1): a step on the kept lists runs the
+    // graph without bucket build and gather; one whose lists are due (or fell short) the
+    // full graph, as the host-driven step decides
+    const bool keep = P.list_every > 1;
+    const bool fresh = !keep || c->need_list || c->list_age >= P.list_every;
     StepGraph* sg = nullptr;
     for (StepGraph& g : c->step_graph)
-        if (g.exec && g.pos == c->pos) sg = &g;
+        if (g.exec && g.pos == c->pos && g.kept == !fresh) sg = &g;
     if (!sg) {
         for (StepGraph& g : c->step_graph)
             if (!g.exec) { sg = &g; break; }
-        if (!sg) return MPS_EDEVICE;   // a third buffer assignment: not expected
+        if (!sg) return MPS_EDEVICE;   // a further buffer assignment: not expected
         const double4* start = c->pos;
+        sg->kept = !fresh;
         rc = build_step_graph(c, sg);
         if (rc) {
             *sg = StepGraph{};   // the graph of the failed capture is left alone
@@ -309,7 +334,10 @@ int step_graph_step(Ctx* c, mps_report* rep) {
     }
     // ---- the control block of this step
     StepCtl& h = *c->ctl_host;
-    const double skin = c->list_skin;
+    // the skin of the lists this step uses: the adaptive one of a fresh gather, else the one
+    // the kept lists were gathered with (no retry inside the graph: a kept step whose lists
+    // fall short is taken again with fresh lists below)
+    const double skin = fresh ? c->list_skin : c->gathered_skin;
     if (ppe) mixed_init_scalars(c, &h.cg_init);
     h.g[0] = P.g[0];
     h.g[1] = P.g[1];
@@ -318,11 +346,11 @@ int step_graph_step(Ctx* c, mps_report* rep) {
     h.half[1] = 0.5 * P.cell_skin * re_max;
     h.hv2[0] = make_radius(re_max * (1.0 + skin), c->band_x).hi;
     h.hv2[1] = make_radius(re_max * (1.0 + P.cell_skin), c->band_x).hi;
-    h.can_retry = skin < P.cell_skin ? 1 : 0;
+    h.can_retry = (fresh && skin < P.cell_skin) ? 1 : 0;
     h.attempt = 0;
     h.skin_err = 0;
     const int S = c->n_scenes;
-    if (S > 1 && skin != c->rv_var_skin) {
+    if (fresh && S > 1 && skin != c->rv_var_skin) {
         for (int s = 0; s < S; s++) {
             const SceneParams& sp = c->scn_host[(size_t)s];
             c->rv_var_host[s] = make_radius(std::max(sp.rn.re, sp.rl.re) * (1.0 + skin), c->band_x);
@@ -333,20 +361,22 @@ int step_graph_step(Ctx* c, mps_report* rep) {
     }
     MPS_CUDA(c, cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(StepCtl), cudaMemcpyHostToDevice,
                                 c->stream));
-    if ((rc = bucket_order_word(c))) return rc;
+    if (fresh && (rc = bucket_order_word(c))) return rc;
     MPS_CUDA(c, cudaGraphLaunch(sg->exec, c->stream));
     state_ptrs_load(c, sg->after);
-    c->order_valid = true;
+    if (fresh) c->order_valid = true;
     MPS_CUDA(c, cudaStreamSynchronize(c->stream));
     // ---- what the step left
     const DevStatus& st = *c->st_host;
     const int attempts = h.attempt + 1;
-    const double used_skin = h.attempt ? P.cell_skin : skin;
-    c->gathered_skin = used_skin;
-    c->r_v = make_radius(re_max * (1.0 + used_skin), c->band_x);
-    if (S > 1) c->scn_skin = used_skin;
-    c->n_ghost_last = st.n_ghost;
-    rep->n_ghost = st.n_ghost;
+    if (fresh) {
+        const double used_skin = h.attempt ? P.cell_skin : skin;
+        c->gathered_skin = used_skin;
+        c->r_v = make_radius(re_max * (1.0 + used_skin), c->band_x);
+        if (S > 1) c->scn_skin = used_skin;
+        c->n_ghost_last = st.n_ghost;
+    }
+    rep->n_ghost = c->n_ghost_last;
     rep->n_surface = st.n_surface;
     rep->n_ppe_rows = st.n_ppe;
     double md;
@@ -361,15 +391,20 @@ int step_graph_step(Ctx* c, mps_report* rep) {
     rep->lambda = c->lambda;
     rep->cg_iters = rep->cg_outer = 0;
     rep->cg_resid = 0.0;
-    rep->list_gathered = 1;
+    rep->list_gathered = fresh ? 1 : 0;
     rep->step_graph = 1;
     rep->n_fast = 0;
     c->launches += sg->launches_pre + attempts * sg->launches_attempt;
-    bucket_branch_count(c, st);
-    rep->bucket_merged = c->last_bucket_merged;
-    rep->n_moved = (int64_t)st.n_mov;
-    c->list_age = 0;
-    c->need_list = false;
+    if (fresh) {
+        bucket_branch_count(c, st);
+        rep->bucket_merged = c->last_bucket_merged;
+        rep->n_moved = (int64_t)st.n_mov;
+        c->list_age = 0;
+        c->need_list = false;
+    } else {
+        rep->bucket_merged = -1;
+        rep->n_moved = 0;
+    }
     if (st.err) {
         if (st.err & kErrNonfinite) return MPS_ENONFINITE;
         if (st.err & kErrCoincident) return MPS_ECOINCIDENT;
@@ -377,6 +412,12 @@ int step_graph_step(Ctx* c, mps_report* rep) {
         return MPS_EDEVICE;
     }
     if (h.skin_err) {
+        if (!fresh) {
+            // the kept lists no longer cover the step (nothing was advanced): the step again
+            // on lists gathered afresh
+            c->need_list = true;
+            return step_graph_step(c, rep);
+        }
         if (S > 1) return MPS_ESKIN;
         // a particle outran the full skin: the host-driven step completes the lists of such
         // particles by a direct search (skinpatch.cu) and repeats the step (nothing advanced)
@@ -387,7 +428,9 @@ int step_graph_step(Ctx* c, mps_report* rep) {
     }
     // next list skin: three times what this step's displacement needs, within
     // [kMinListSkin, cell_skin] (as the host-driven step)
-    c->list_skin = std::min(P.cell_skin, std::max(kMinListSkin, 3.0 * (2.0 * rep->max_disp / re_max)));
+    c->list_skin = std::min(P.cell_skin,
+                            std::max(kMinListSkin, 3.0 * (2.0 * rep->max_disp / re_max) *
+                                                       (keep ? P.list_every : 1)));
     c->launches += sg->launches_post;
     if (ppe) {
         const CgScalars& cg = *c->cg_host;
@@ -412,6 +455,14 @@ int step_graph_step(Ctx* c, mps_report* rep) {
             rep->cg_resid = worst;
             if (!(worst <= P.cg_tol)) return MPS_ECG_NOCONV;
         }
+    }
+    if (keep) {
+        // where r^{k+1} stands against r_b decides whether the next step may keep the lists
+        c->list_age++;
+        const double half = 0.5 * c->gathered_skin * re_max;
+        double dn;
+        std::memcpy(&dn, &st.max_disp_next_bits, sizeof dn);
+        if (st.leave || std::sqrt(dn) > half) c->need_list = true;
     }
     c->steps_done++;
     rep->steps_done = c->steps_done;

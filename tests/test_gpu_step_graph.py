@@ -150,3 +150,35 @@ def test_step_graph_reports_skin_and_coincidence_errors():
                 assert rc == code, (sgflag, rc, code)
             finally:
                 sim.close()
+
+
+@pytest.mark.parametrize("case", ["3d-mixed-kept", "2d-eos-kept", "2d-mixed-kept-fast"])
+def test_step_graph_kept_lists_equals_launch_by_launch(case):
+    """Candidate lists kept across steps (list_every > 1): the steps on kept lists run a graph
+    without bucket build and gather, those whose lists are due the full graph; a kept step
+    whose lists fall short (fluid at 4 m/s against a skin of 0.05) is taken again on fresh
+    lists.  Every field, and which steps gathered, as launched one by one."""
+    if case == "3d-mixed-kept":
+        sc, kw = small_3d(seed=5), dict(precision=1, dt=5e-5, cg_x0=3, list_every=4)
+    elif case == "2d-eos-kept":
+        sc, kw = scenes.dam_break_2d(seed=6), dict(precision=1, pressure_mode=1, c0=20.0,
+                                                   list_every=4)
+    else:
+        sc = scenes.dam_break_2d(seed=1)
+        f = sc.types == scenes.FLUID
+        sc.vel[f] = [4.0, 0.0]
+        kw = dict(precision=1, cell_skin=0.05, list_every=10)
+    steps = 10
+    rg, sg = _run(sc, steps, 1, **kw)
+    rh, sh = _run(sc, steps, 0, **kw)
+    assert all(r["step_graph"] == 1 for r in rg)
+    gathered = [r["list_gathered"] for r in rg]
+    assert gathered == [r["list_gathered"] for r in rh]
+    assert 0 in gathered and gathered.count(1) >= 2
+    if case == "2d-mixed-kept-fast":
+        assert gathered[:5] == [1, 0, 1, 0, 1], gathered
+    for k in range(steps):
+        _same(sg[k], sh[k])
+        for f in ("cg_iters", "cg_outer", "cg_resid", "n_surface", "n_ppe_rows", "max_disp",
+                  "pairs_ppe", "pairs_pnd", "list_tests", "bucket_merged"):
+            assert rg[k][f] == rh[k][f], (k, f)
