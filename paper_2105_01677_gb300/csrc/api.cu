@@ -647,14 +647,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
             patched = true;
         }
         // per-slot outputs of the build; slots it does not visit (GHOST) keep these zeros
-        MPS_CUDA(c, cudaMemsetAsync(c->nstar, 0, n * sizeof(double), c->stream));
-        MPS_CUDA(c, cudaMemsetAsync(c->flag, 0, n, c->stream));
-        MPS_CUDA(c, cudaMemsetAsync(c->diag, 0, n * sizeof(double), c->stream));
-        MPS_CUDA(c, cudaMemsetAsync(c->diag32, 0, n * sizeof(float), c->stream));
-        MPS_CUDA(c, cudaMemsetAsync(c->bvec, 0, n * sizeof(double), c->stream));
-        MPS_CUDA(c, cudaMemsetAsync(c->nb_lap_cnt, 0, n * sizeof(int32_t), c->stream));
-        MPS_CUDA(c, cudaMemsetAsync(c->nb_n_cnt, 0, n * sizeof(int32_t), c->stream));
-        if (P.pressure_mode == 1) MPS_CUDA(c, cudaMemsetAsync(c->p, 0, n * sizeof(double), c->stream));
+        launch_clear_rows(c);
         stage_begin(c, MPS_STAGE_BUILD);
         launch_build_rows(c);                                          // 3 (+ 4 for the EOS)
         stage_end(c, MPS_STAGE_BUILD);

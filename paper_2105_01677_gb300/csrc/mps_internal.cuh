@@ -178,6 +178,9 @@ void launch_debug_neighbors(Ctx* c, const Radius& r, const int64_t* row_off, int
 // ---------------------------------------------------------------- rows.cu
 void launch_predict_rows(Ctx* c);
 void launch_build_rows(Ctx* c);
+// zeros in the build's per-slot outputs (n*, flag, diagonal, right-hand side, list counts;
+// p on the equation-of-state path): the slots it does not visit keep them
+void launch_clear_rows(Ctx* c);
 // threads per block of the row build; the functions' shared-memory limits (once per context)
 int build_block_of(const Ctx* c);
 int build_rows_init(Ctx* c);

@@ -909,6 +909,29 @@ static void launch_build_t(Ctx* c, const BuildArgs& a) {
     }
 }
 
+__global__ void __launch_bounds__(kBT)
+    k_clear_rows(int n, double* nstar, uint8_t* flag, double* diag, float* diag32, double* bvec,
+                 int32_t* lap_cnt, int32_t* n_cnt, double* p) {
+    const int i = blockIdx.x * kBT + threadIdx.x;
+    if (i >= n) return;
+    nstar[i] = 0.0;
+    flag[i] = 0;
+    diag[i] = 0.0;
+    diag32[i] = 0.f;
+    bvec[i] = 0.0;
+    lap_cnt[i] = 0;
+    n_cnt[i] = 0;
+    if (p) p[i] = 0.0;
+}
+
+void launch_clear_rows(Ctx* c) {
+    const int n = (int)c->n;
+    k_clear_rows<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(
+        n, c->nstar, c->flag, c->diag, c->diag32, c->bvec, c->nb_lap_cnt, c->nb_n_cnt,
+        c->prm.pressure_mode == 1 ? c->p : nullptr);
+    c->launches += 1;
+}
+
 int build_block_of(const Ctx* c) {
     if (c->build_block) return c->build_block;
     return (c->prm.precision == 1 && c->prm.pressure_mode == 0) ? kBuildRingBT : kBuildBT;

@@ -207,14 +207,7 @@ int capture_step(Ctx* c, StepGraph* sg, cudaGraph_t G) {
     }
     launch_predict_rows(c);
     if (ppe && P.source_term == 2) launch_ecs_rates(c);
-    MPS_CUDA(c, cudaMemsetAsync(c->nstar, 0, n * sizeof(double), s));
-    MPS_CUDA(c, cudaMemsetAsync(c->flag, 0, n, s));
-    MPS_CUDA(c, cudaMemsetAsync(c->diag, 0, n * sizeof(double), s));
-    MPS_CUDA(c, cudaMemsetAsync(c->diag32, 0, n * sizeof(float), s));
-    MPS_CUDA(c, cudaMemsetAsync(c->bvec, 0, n * sizeof(double), s));
-    MPS_CUDA(c, cudaMemsetAsync(c->nb_lap_cnt, 0, n * sizeof(int32_t), s));
-    MPS_CUDA(c, cudaMemsetAsync(c->nb_n_cnt, 0, n * sizeof(int32_t), s));
-    if (!ppe) MPS_CUDA(c, cudaMemsetAsync(c->p, 0, n * sizeof(double), s));
+    launch_clear_rows(c);
     launch_build_rows(c);
     k_attempt_check<<<1, 32, 0, s>>>(c->ctl, c->st, h_loop, h_rest);
     c->launches += 2;
