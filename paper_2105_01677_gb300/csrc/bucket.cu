@@ -6,12 +6,16 @@
 //      interleave (x in bit 0); a particle outside the grid becomes a GHOST and sorts last;
 //      in an ensemble the key is prefixed by the particle's scene (scene-major order) and
 //      the GHOST test uses the scene's own grid;
-//   2. stable LSD radix sort of (key, slot), 8-bit digits: per-tile digit histogram, a
-//      device-wide exclusive scan of the digit-major histogram table, and a stable scatter
-//      that ranks equal digits with warp match masks;
+//   2. the stable sort of (key, slot): in a graph-run build whose slots are still in the
+//      previous build's order, the particles whose key changed are ranked among themselves
+//      and merged into that order (below: "the build from the previous order"); otherwise
+//      an LSD radix sort with 8-bit digits: per-tile digit histogram, a device-wide
+//      exclusive scan of the digit-major histogram table, and a stable scatter that ranks
+//      equal digits with warp match masks (both give the same order);
 //   3. per-cell counts and their exclusive scan give cell_start (a cell's particles are
 //      contiguous in Morton order); occupied cells are collected for the gathers;
-//   4. every per-particle array is permuted into the new order (slot s <- old slot perm[s]).
+//   4. every per-particle array is permuted into the new order (slot s <- old slot perm[s]),
+//      the step's predicted state starting as a copy of it (r* := r, u* := u).
 #include <cstring>
 
 #include "mps_internal.cuh"
