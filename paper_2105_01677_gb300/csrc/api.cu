@@ -719,12 +719,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
     if (c->vjp && P.pressure_mode == 0)   // the reverse step needs p before the clamp
         MPS_CUDA(c, cudaMemcpyAsync(c->adj.ppre, c->p, n * sizeof(double),
                                     cudaMemcpyDeviceToDevice, c->stream));
-    if (P.pressure_mode == 0 || P.gradient_form == 1) {
-        launch_clamp_pmin(c);   // the equation of state clamps nothing (no PPE solve)
-    } else {
-        MPS_CUDA(c, cudaMemcpyAsync(c->phat, c->p, sizeof(double) * (size_t)c->n,
-                                    cudaMemcpyDeviceToDevice, c->stream));
-    }
+    if ((rc = launch_pressure_floor(c))) return rc;
     if (advance) launch_gradient_correct(c);                       // 6
     stage_end(c, MPS_STAGE_UPDATE);
     MPS_CUDA(c, cudaGetLastError());

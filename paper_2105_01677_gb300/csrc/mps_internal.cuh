@@ -234,6 +234,8 @@ int step_graph_step(Ctx* c, mps_report* rep);
 int do_step(Ctx* c, bool advance, mps_report* rep);   // api.cu: the host-driven step
 void step_graphs_destroy(Ctx* c);
 void launch_clamp_pmin(Ctx* c);
+// the clamp p = max(p, 0) of the PPE solution and p_hat of the gradient (update.cu)
+int launch_pressure_floor(Ctx* c);
 void launch_gradient_correct(Ctx* c);
 void launch_unpermute(Ctx* c, double* d_pos, double* d_vel, double* d_p, double* d_nstar,
                       uint8_t* d_flags, int8_t* d_types);

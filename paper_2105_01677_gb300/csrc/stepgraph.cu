@@ -238,10 +238,7 @@ int capture_step(Ctx* c, StepGraph* sg, cudaGraph_t G) {
             MPS_CUDA(c, cudaMemcpyAsync(c->ph[0], c->p, n * sizeof(double),
                                         cudaMemcpyDeviceToDevice, s));
     }
-    if (ppe || P.gradient_form == 1)
-        launch_clamp_pmin(c);
-    else
-        MPS_CUDA(c, cudaMemcpyAsync(c->phat, c->p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if ((rc = launch_pressure_floor(c))) return rc;
     launch_gradient_correct(c);
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));
     sg->launches_post = c->launches - l;

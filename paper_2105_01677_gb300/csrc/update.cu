@@ -44,6 +44,8 @@ __global__ void __launch_bounds__(kBT) k_clamp_store(int n, double* p) {
 struct Keep {
     int kernel;             // 0: re/r - 1 (Eq. 4); 1: (1 - r/re)^3
     int form;               // 0: (p_j - p_hat_i); 1: CMPS (Eq. 18)
+    int phat_mode;          // p_hat_i: 0 read from phat; 1 min(p_i, min_j p_j) over the row's
+                            // list, taken here; 2 p_i (the equation of state)
     double inv_re;          // 1/re_n
     float inv_f;
     const double* rho_s;    // two-phase: per-slot density (null: the uniform rho)
@@ -68,9 +70,14 @@ __device__ __forceinline__ double gradient_row(int i, const int8_t* type, const 
                                                double rho, double4* pos, double4* vel,
                                                const Keep& kp) {
     const double4 pi = ps[i];
-    const double ph = phat[i];
     const double pp = p[i];
     const int cnt = ncnt[i];
+    double ph = kp.phat_mode == 2 ? pp : (kp.phat_mode == 1 ? pp : phat[i]);
+    if (kp.phat_mode == 1) {
+        // the neighbourhood minimum (p already clamped in memory when the clamp is on): the
+        // same values and the same exact min as a separate pass
+        for (int k = 0; k < cnt; k++) ph = fmin(ph, p[ncol[sell8(i, k, cap_n)]]);
+    }
     double inv_re = kp.inv_re;
     float inv_f = kp.inv_f;
     if (kp.sid) {   // ensemble: the row's scene
@@ -284,6 +291,32 @@ __global__ void __launch_bounds__(kBT)
 }
 }  // namespace
 
+// With the difference-form gradient p_hat is needed by the gradient of FLUID rows only: the
+// gradient kernel takes it from the row's own list (after the clamp is stored), which saves a
+// pass over the lists; the reverse step, which keeps p_hat, and CMPS (p_hat_j of every
+// neighbour) use the separate pass.
+static bool phat_inline(const Ctx* c) { return c->prm.gradient_form == 0 && !c->vjp; }
+
+int launch_pressure_floor(Ctx* c) {
+    const int n = (int)c->n;
+    const int nb = (n + kBT - 1) / kBT;
+    const bool ppe = c->prm.pressure_mode == 0;
+    if (phat_inline(c)) {
+        if (ppe && c->prm.clamp_negative_p) {
+            k_clamp_store<<<nb, kBT, 0, c->stream>>>(n, c->p);
+            c->launches += 1;
+        }
+        return MPS_OK;
+    }
+    if (ppe || c->prm.gradient_form == 1) {
+        launch_clamp_pmin(c);   // the equation of state clamps nothing (no PPE solve)
+    } else {
+        MPS_CUDA(c, cudaMemcpyAsync(c->phat, c->p, sizeof(double) * (size_t)n,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return MPS_OK;
+}
+
 void launch_clamp_pmin(Ctx* c) {
     const int n = (int)c->n;
     const int nb = (n + kBT - 1) / kBT;
@@ -302,6 +335,7 @@ void launch_gradient_correct(Ctx* c) {
     Keep kp;
     kp.kernel = P.kernel;
     kp.form = P.gradient_form;
+    kp.phat_mode = phat_inline(c) ? (P.pressure_mode == 0 ? 1 : 2) : 0;
     kp.inv_re = c->r_n.inv_re;
     kp.inv_f = c->r_n.inv_f;
     kp.rho_s = c->rho_s;
