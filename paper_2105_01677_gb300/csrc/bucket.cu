@@ -310,8 +310,30 @@ __global__ void __launch_bounds__(kBT)
     k_permute(const int32_t* perm, int n, const double4* pos, const double4* vel,
               const int8_t* type, const int32_t* id, const double* p, double4* pos_o,
               double4* vel_o, int8_t* type_o, int32_t* id_o, double* p_o, GuessPerm gp,
-              float4* pos32, float4* pos32lo, float4* vel32, GridDesc g, StarOut so) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
+              float4* pos32, float4* pos32lo, float4* vel32, GridDesc g, StarOut so,
+              uint32_t* blk_f, uint32_t* blk_fw) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    // the block's FLUID and FLUID / WALL slots of the new order, counted for the row lists
+    {
+        __shared__ uint32_t s_cf[kBT / 32], s_cfw[kBT / 32];
+        const int tt = s < n ? (int)type[perm[s]] : -1;
+        const unsigned bf = __ballot_sync(0xffffffffu, tt == kFluid);
+        const unsigned bfw = __ballot_sync(0xffffffffu, tt == kFluid || tt == kWall);
+        if ((threadIdx.x & 31) == 0) {
+            s_cf[threadIdx.x >> 5] = __popc(bf);
+            s_cfw[threadIdx.x >> 5] = __popc(bfw);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t a = 0, b = 0;
+            for (int w = 0; w < kBT / 32; w++) {
+                a += s_cf[w];
+                b += s_cfw[w];
+            }
+            blk_f[blockIdx.x] = a;
+            blk_fw[blockIdx.x] = b;
+        }
+    }
     if (s >= n) return;
     int j = perm[s];
     double4 x = pos[j];
@@ -338,24 +360,84 @@ __global__ void __launch_bounds__(kBT)
     so.pff[2 * s] = h;
     so.pff[2 * s + 1] = l;
 }
-// active-row marks of the new order (one scan each gives the row lists)
-__global__ void __launch_bounds__(kBT)
-    k_mark_rows(int n, const int8_t* type, uint32_t* mark_f, uint32_t* mark_fw) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const int t = type[s];
-    mark_f[s] = t == kFluid ? 1u : 0u;
-    mark_fw[s] = (t == kFluid || t == kWall) ? 1u : 0u;
+// The row lists of the new order (FLUID slots, FLUID / WALL slots, each in slot order) from
+// the permutation's per-block counts: an exclusive scan of the counts in one block (their
+// totals are the lists' lengths, stored after the n entries of scan_f / scan_fw), then every
+// block places its slots at its offset plus their rank in the block (warp ballots).
+constexpr int kScanBT = 1024;
+__global__ void __launch_bounds__(kScanBT)
+    k_rows_scan(int nb, uint32_t* blk_f, uint32_t* blk_fw, uint32_t* total_f,
+                uint32_t* total_fw) {
+    __shared__ uint32_t s_w[2][kScanBT / 32];
+    __shared__ uint32_t s_carry[2];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry[0] = s_carry[1] = 0u;
+    __syncthreads();
+    for (int base = 0; base < nb; base += kScanBT) {
+        const int k = base + (int)threadIdx.x;
+        uint32_t v[2] = {k < nb ? blk_f[k] : 0u, k < nb ? blk_fw[k] : 0u};
+        uint32_t incl[2] = {v[0], v[1]};
+        for (int o = 1; o < 32; o <<= 1) {
+            for (int a = 0; a < 2; a++) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl[a], o);
+                if (lane >= o) incl[a] += y;
+            }
+        }
+        if (lane == 31) {
+            s_w[0][w] = incl[0];
+            s_w[1][w] = incl[1];
+        }
+        __syncthreads();
+        if (w == 0) {
+            for (int a = 0; a < 2; a++) {
+                uint32_t t = s_w[a][lane];
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                    if (lane >= o) t += y;
+                }
+                s_w[a][lane] = t;   // inclusive over the warps
+            }
+        }
+        __syncthreads();
+        for (int a = 0; a < 2; a++) {
+            const uint32_t before = s_carry[a] + (w > 0 ? s_w[a][w - 1] : 0u);
+            if (k < nb) (a == 0 ? blk_f : blk_fw)[k] = before + incl[a] - v[a];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_carry[0] += s_w[0][kScanBT / 32 - 1];
+            s_carry[1] += s_w[1][kScanBT / 32 - 1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *total_f = s_carry[0];
+        *total_fw = s_carry[1];
+    }
 }
 
 __global__ void __launch_bounds__(kBT)
-    k_scatter_rows(int n, const int8_t* type, const uint32_t* scan_f, const uint32_t* scan_fw,
+    k_rows_scatter(int n, const int8_t* type, const uint32_t* off_f, const uint32_t* off_fw,
                    int32_t* rows_f, int32_t* rows_fw) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const int t = type[s];
-    if (t == kFluid) rows_f[scan_f[s]] = s;
-    if (t == kFluid || t == kWall) rows_fw[scan_fw[s]] = s;
+    __shared__ uint32_t s_cf[kBT / 32], s_cfw[kBT / 32];
+    const int s = blockIdx.x * kBT + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int t = s < n ? (int)type[s] : -1;
+    const bool f = t == kFluid, fw = t == kFluid || t == kWall;
+    const unsigned bf = __ballot_sync(0xffffffffu, f), bfw = __ballot_sync(0xffffffffu, fw);
+    if (lane == 0) {
+        s_cf[w] = __popc(bf);
+        s_cfw[w] = __popc(bfw);
+    }
+    __syncthreads();
+    uint32_t of = off_f[blockIdx.x], ofw = off_fw[blockIdx.x];
+    for (int k = 0; k < w; k++) {
+        of += s_cf[k];
+        ofw += s_cfw[k];
+    }
+    const unsigned lt = (1u << lane) - 1u;
+    if (f) rows_f[of + __popc(bf & lt)] = s;
+    if (fw) rows_fw[ofw + __popc(bfw & lt)] = s;
 }
 }  // namespace
 
@@ -442,18 +524,19 @@ int launch_table_rest(Ctx* c) {
     k_permute<<<nb1, kBT, 0, s>>>(c->perm, n, c->pos, c->vel, c->type, c->id, c->p, c->pos_alt,
                                   c->vel_alt, c->type_alt, c->id_alt, c->p_alt, gp, c->pos32,
                                   c->pos32lo, c->vel32, c->grid,
-                                  StarOut{c->pos_star, c->vel_star, c->pos32_star, c->pff_star});
+                                  StarOut{c->pos_star, c->vel_star, c->pos32_star, c->pff_star},
+                                  c->mark_f, c->mark_fw);
     std::swap(c->pos, c->pos_alt);
     std::swap(c->vel, c->vel_alt);
     std::swap(c->type, c->type_alt);
     std::swap(c->id, c->id_alt);
     std::swap(c->p, c->p_alt);
     for (int k = 0; k < c->guess_m; k++) std::swap(c->ph[k], c->ph_alt[k]);
-    // FLUID rows and FLUID / WALL rows in slot order, for the per-row kernels
-    k_mark_rows<<<nb1, kBT, 0, s>>>(n, c->type, c->mark_f, c->mark_fw);
-    c->launches += 2 + scan_exclusive(c->mark_f, c->scan_f, n, true, c->scan_scratch, s);
-    c->launches += scan_exclusive(c->mark_fw, c->scan_fw, n, true, c->scan_scratch, s);
-    k_scatter_rows<<<nb1, kBT, 0, s>>>(n, c->type, c->scan_f, c->scan_fw, c->rows_f, c->rows_fw);
+    // FLUID rows and FLUID / WALL rows in slot order, for the per-row kernels (the
+    // permutation's per-block counts in mark_f / mark_fw, free until the next build)
+    k_rows_scan<<<1, kScanBT, 0, s>>>(nb1, c->mark_f, c->mark_fw, c->scan_f + n, c->scan_fw + n);
+    k_rows_scatter<<<nb1, kBT, 0, s>>>(n, c->type, c->mark_f, c->mark_fw, c->rows_f, c->rows_fw);
+    c->launches += 2;
     launch_gather_props(c);   // two-phase properties follow their particles
     MPS_CUDA(c, cudaGetLastError());
     return MPS_OK;
