@@ -279,6 +279,23 @@ __global__ void __launch_bounds__(kBT)
     if (i < n && key[i] != ghost_key) atomicAdd(&count[key[i]], 1u);
 }
 
+// cell_start[c] = the number of sorted keys below c, for c = 0 .. ntable (the GHOST key is
+// ntable): a binary search per cell, where the table is not much larger than the particle
+// count (the counts and their scan are used otherwise; both give the same table)
+__global__ void __launch_bounds__(kBT)
+    k_cell_start_search(const uint32_t* key, int n, int64_t ntable, int32_t* cell_start) {
+    for (int64_t c = blockIdx.x * (int64_t)kBT + threadIdx.x; c <= ntable;
+         c += (int64_t)gridDim.x * kBT) {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((int64_t)key[mid] < c) lo = mid + 1;
+            else hi = mid;
+        }
+        cell_start[c] = lo;
+    }
+}
+
 // first slot of each run of equal keys (sorted) marks an occupied cell
 __global__ void __launch_bounds__(kBT)
     k_occupied(const uint32_t* key, int n, uint32_t ghost_key, uint32_t* occ, DevStatus* st) {
@@ -509,10 +526,17 @@ int launch_table_rest(Ctx* c) {
     const int n = (int)c->n;
     cudaStream_t s = c->stream;
     const int nb1 = (n + kBT - 1) / kBT;
-    MPS_CUDA(c, cudaMemsetAsync(c->cell_count, 0, sizeof(uint32_t) * (size_t)c->ntable, s));
-    k_cell_count<<<nb1, kBT, 0, s>>>(c->key, n, c->grid.ghost_key, c->cell_count);
-    c->launches += 3 + scan_exclusive(c->cell_count, (uint32_t*)c->cell_start, c->ntable, true,
-                                      c->scan_scratch, s);
+    if (c->ntable <= 2 * (int64_t)n) {
+        const int64_t nbt = (c->ntable + 1 + kBT - 1) / kBT;
+        k_cell_start_search<<<(int)std::min<int64_t>(nbt, (int64_t)c->sms * 16), kBT, 0, s>>>(
+            c->key, n, c->ntable, c->cell_start);
+        c->launches += 3;
+    } else {
+        MPS_CUDA(c, cudaMemsetAsync(c->cell_count, 0, sizeof(uint32_t) * (size_t)c->ntable, s));
+        k_cell_count<<<nb1, kBT, 0, s>>>(c->key, n, c->grid.ghost_key, c->cell_count);
+        c->launches += 3 + scan_exclusive(c->cell_count, (uint32_t*)c->cell_start, c->ntable,
+                                          true, c->scan_scratch, s);
+    }
     k_occupied<<<nb1, kBT, 0, s>>>(c->key, n, c->grid.ghost_key, c->occ, c->st);
     // permute the state into the new order
     GuessPerm gp{};

@@ -110,6 +110,25 @@ def test_step_fp64_dam_break_2d(seed):
     assert rep["cg_resid"] <= PARITY_CG_TOL
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_step_in_a_large_sparse_grid(precision):
+    """The 2D dam break in a 10 m x 10 m grid: the cell table (228 x 228 cells, 2^16 Morton
+    entries) is far larger than the particle count, so it is built by counts and their scan
+    (not by a binary search per cell, as for the dense grids of the other tests)."""
+    sc = scenes.dam_break_2d(seed=4)
+    sc.box_max = sc.box_min + np.array([10.0, 10.0, 0.0])[: len(sc.box_min)]
+    tol = PARITY_CG_TOL if precision == 0 else 1e-8
+    rc, rep, got, consts = run_gpu(sc, **gpu_params(sc, precision=precision, cg_tol=tol))
+    orep, ost, prm = run_oracle(sc, cg_tol=PARITY_CG_TOL)
+    assert consts["ncell"][0] * consts["ncell"][1] > 16 * sc.n
+    if precision == 0:
+        compare_step(sc, got, ost, prm)
+    else:
+        f = sc.types == scenes.FLUID
+        assert np.linalg.norm(got["p"][f] - ost.p[f]) / np.linalg.norm(ost.p[f]) <= 1e-5
+    assert np.array_equal(got["flags"], ost.flags)
+
+
 @pytest.mark.parametrize("seed", [1, 2])
 def test_step_fp64_dam_break_3d_small(seed):
     sc = small_3d(seed=seed)
