@@ -706,11 +706,7 @@ int do_step(Ctx* c, bool advance, mps_report* rep) {
         if ((rc = ppe_solve(c, rep))) return rc;
         if (c->guess_m > 0) {
             // the next solve starts from this one (and the ones before it): shift the history
-            for (int k = c->guess_m - 1; k > 0; k--)
-                MPS_CUDA(c, cudaMemcpyAsync(c->ph[k], c->ph[k - 1], n * sizeof(double),
-                                            cudaMemcpyDeviceToDevice, c->stream));
-            MPS_CUDA(c, cudaMemcpyAsync(c->ph[0], c->p, n * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, c->stream));
+            launch_push_history(c);
             c->guess_n = std::min(c->guess_n + 1, c->guess_m);
         }
         stage_end(c, MPS_STAGE_PPE);

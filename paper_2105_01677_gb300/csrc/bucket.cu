@@ -37,6 +37,7 @@ struct MoverOut {
     uint32_t* key;
     int32_t* slot;
     int cap;
+    uint32_t* cnt;   // 4 per mover, zeroed here for the merge's counts
 };
 
 __global__ void __launch_bounds__(kBT)
@@ -46,6 +47,8 @@ __global__ void __launch_bounds__(kBT)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t old_key = mo.mvf ? key[i] : 0u;
+    if (mo.cnt)
+        for (int k = i; k < 4 * mo.cap; k += n) mo.cnt[k] = 0u;
     double4 p = pos[i];
     int8_t t = type[i];
     if (mutate) {
@@ -321,6 +324,7 @@ struct GuessPerm {
 struct StarOut {
     double4 *pos, *vel;
     float4 *pos32, *pff;   // pff: (hi, lo) pairs, slot s at 2 s and 2 s + 1
+    int32_t* vcnt;         // candidate-list counts, zeroed (the gather writes its particles')
 };
 
 __global__ void __launch_bounds__(kBT)
@@ -376,6 +380,7 @@ __global__ void __launch_bounds__(kBT)
     so.pos32[s] = h;
     so.pff[2 * s] = h;
     so.pff[2 * s + 1] = l;
+    so.vcnt[s] = 0;
 }
 // The row lists of the new order (FLUID slots, FLUID / WALL slots, each in slot order) from
 // the permutation's per-block counts: an exclusive scan of the counts in one block (their
@@ -473,7 +478,7 @@ namespace {
 void launch_keys(Ctx* c, bool mutate, bool movers) {
     const int n = (int)c->n;
     MoverOut mo{};
-    if (movers) mo = MoverOut{c->mvf, c->mov_key, c->mov_slot, c->mov_cap};
+    if (movers) mo = MoverOut{c->mvf, c->mov_key, c->mov_slot, c->mov_cap, c->mov_cnt};
     k_cell_keys<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(
         c->pos, c->vel, c->type, c->key, c->perm, n, c->grid, c->st, mutate ? 1 : 0,
         c->grid.ghost_key, c->sid, c->scn, c->scene_shift, mo);
@@ -508,7 +513,6 @@ int launch_from_previous(Ctx* c, const uint32_t* kin, uint32_t* kout, int32_t* v
     const int n = (int)c->n;
     cudaStream_t s = c->stream;
     const uint32_t gk = c->grid.ghost_key;
-    MPS_CUDA(c, cudaMemsetAsync(c->mov_cnt, 0, 4 * sizeof(uint32_t) * (size_t)c->mov_cap, s));
     k_mov_count<<<c->sms * 4, kBT, 0, s>>>(c->mov_key, c->mov_slot, c->st, c->mov_cap,
                                            c->cell_start, gk, n, c->mov_cnt);
     k_mov_place<<<(c->mov_cap + kBT - 1) / kBT, kBT, 0, s>>>(
@@ -548,7 +552,8 @@ int launch_table_rest(Ctx* c) {
     k_permute<<<nb1, kBT, 0, s>>>(c->perm, n, c->pos, c->vel, c->type, c->id, c->p, c->pos_alt,
                                   c->vel_alt, c->type_alt, c->id_alt, c->p_alt, gp, c->pos32,
                                   c->pos32lo, c->vel32, c->grid,
-                                  StarOut{c->pos_star, c->vel_star, c->pos32_star, c->pff_star},
+                                  StarOut{c->pos_star, c->vel_star, c->pos32_star, c->pff_star,
+                                          c->vl_cnt},
                                   c->mark_f, c->mark_fw);
     std::swap(c->pos, c->pos_alt);
     std::swap(c->vel, c->vel_alt);

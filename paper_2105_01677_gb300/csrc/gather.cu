@@ -389,7 +389,8 @@ void launch_gather_nw(Ctx* c, const Op& op, int blocks_per_sm) {
     static_assert(NW * kWCAP * sizeof(float4) <= 48 * 1024, "within the default dynamic shared memory");
     // blocks take occupied cells from a counter: cells differ a lot in work (full fluid
     // cells against sparse wall or surface cells), so a static split leaves SMs idle
-    cudaMemsetAsync(&c->st->gather_next, 0, sizeof(unsigned int), c->stream);
+    // (a step graph's attempts reset the counter in k_attempt_begin)
+    if (!c->capture_ctl) cudaMemsetAsync(&c->st->gather_next, 0, sizeof(unsigned int), c->stream);
     k_gather<NW, kWCAP, Op><<<c->sms * blocks_per_sm, 32 * NW, NW * kWCAP * sizeof(float4), c->stream>>>(
         op, c->cell_start, c->occ, c->st, c->grid);
 }

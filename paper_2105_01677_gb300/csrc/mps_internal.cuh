@@ -236,6 +236,8 @@ void step_graphs_destroy(Ctx* c);
 void launch_clamp_pmin(Ctx* c);
 // the clamp p = max(p, 0) of the PPE solution and p_hat of the gradient (update.cu)
 int launch_pressure_floor(Ctx* c);
+// the PPE solution before the clamp into the guess history (ph[0]), the older ones shifted
+void launch_push_history(Ctx* c);
 void launch_gradient_correct(Ctx* c);
 void launch_unpermute(Ctx* c, double* d_pos, double* d_vel, double* d_p, double* d_nstar,
                       uint8_t* d_flags, int8_t* d_types);

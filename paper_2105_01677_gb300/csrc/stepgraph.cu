@@ -73,6 +73,7 @@ __global__ void k_attempt_begin(StepCtl* ctl, DevStatus* st, SceneParams* scn, c
         st->pairs_lap = 0ull;
         st->pairs_n = 0ull;
         st->list_tests = 0ull;
+        st->gather_next = 0u;
     }
     if (var)
         for (int s = t; s < n_scenes; s += blockDim.x * gridDim.x) scn[s].rv = var[(size_t)a * n_scenes + s];
@@ -201,10 +202,9 @@ int capture_step(Ctx* c, StepGraph* sg, cudaGraph_t G) {
     k_attempt_begin<<<S > 1 ? (S + 255) / 256 : 1, 256, 0, s>>>(c->ctl, c->st, c->scn,
                                                                  S > 1 ? c->rv_var : nullptr, S,
                                                                  h_loop);
-    if (!sg->kept) {
-        MPS_CUDA(c, cudaMemsetAsync(c->vl_cnt, 0, n * sizeof(int32_t), s));
-        launch_verlet(c);
-    }
+    // the candidate-list counts of the slots the gather does not visit were zeroed by the
+    // bucket build's permutation
+    if (!sg->kept) launch_verlet(c);
     launch_predict_rows(c);
     if (ppe && P.source_term == 2) launch_ecs_rates(c);
     launch_clear_rows(c);
@@ -229,15 +229,7 @@ int capture_step(Ctx* c, StepGraph* sg, cudaGraph_t G) {
     }
     MPS_CUDA(c, cudaStreamBeginCaptureToGraph(s, R, dep ? &dep : nullptr, nullptr, dep ? 1 : 0,
                                               mode));
-    if (ppe) {
-        // the next solve starts from this one and the ones before it
-        for (int k = c->guess_m - 1; k > 0; k--)
-            MPS_CUDA(c, cudaMemcpyAsync(c->ph[k], c->ph[k - 1], n * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, s));
-        if (c->guess_m > 0)
-            MPS_CUDA(c, cudaMemcpyAsync(c->ph[0], c->p, n * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, s));
-    }
+    if (ppe && c->guess_m > 0) launch_push_history(c);   // the next solve starts from this one
     if ((rc = launch_pressure_floor(c))) return rc;
     launch_gradient_correct(c);
     MPS_CUDA(c, cudaStreamEndCapture(s, &tmp));

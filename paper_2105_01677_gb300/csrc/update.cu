@@ -32,6 +32,16 @@ __global__ void __launch_bounds__(kBT)
     phat[i] = m;
 }
 
+// the guess history of the PPE: h_2 <- h_1, h_1 <- h_0, h_0 <- p (as many as are kept)
+__global__ void __launch_bounds__(kBT) k_push_history(int n, int m, double* h0, double* h1,
+                                                      double* h2, const double* p) {
+    const int i = blockIdx.x * kBT + threadIdx.x;
+    if (i >= n) return;
+    if (m >= 3) h2[i] = h1[i];
+    if (m >= 2) h1[i] = h0[i];
+    h0[i] = p[i];
+}
+
 // p was clamped on read above; store the clamped values once every p_hat is computed
 __global__ void __launch_bounds__(kBT) k_clamp_store(int n, double* p) {
     int i = blockIdx.x * kBT + threadIdx.x;
@@ -296,6 +306,13 @@ __global__ void __launch_bounds__(kBT)
 // pass over the lists; the reverse step, which keeps p_hat, and CMPS (p_hat_j of every
 // neighbour) use the separate pass.
 static bool phat_inline(const Ctx* c) { return c->prm.gradient_form == 0 && !c->vjp; }
+
+void launch_push_history(Ctx* c) {
+    const int n = (int)c->n;
+    k_push_history<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(n, c->guess_m, c->ph[0], c->ph[1],
+                                                               c->ph[2], c->p);
+    c->launches += 1;
+}
 
 int launch_pressure_floor(Ctx* c) {
     const int n = (int)c->n;
