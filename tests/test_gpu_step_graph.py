@@ -78,16 +78,18 @@ def test_step_graph_equals_launch_by_launch(case):
             assert rg[k][f] == rh[k][f] == rn[k][f], (k, f)
 
 
-def test_step_graph_ensemble_equals_launch_by_launch():
+@pytest.mark.parametrize("list_every", [1, 3])
+def test_step_graph_ensemble_equals_launch_by_launch(list_every):
     from paper_2105_01677_gb300 import mps
     E = scenes.ensemble_2d(count=12, seed=3, fluid=(500, 3000))
     out = []
+    nsteps = 5 if list_every == 1 else 8
     for sgflag in (1, 0):
         ens = mps.Ensemble(E, torch_alloc=True, use_torch_stream=True, precision=1, dt=1e-4,
-                           cg_tol=1e-8, cg_x0=3, step_graph=sgflag)
+                           cg_tol=1e-8, cg_x0=3, step_graph=sgflag, list_every=list_every)
         try:
             reps, states, res = [], [], []
-            for _ in range(5):
+            for _ in range(nsteps):
                 rc, rep = ens.step(1)
                 reps.append(rep)
                 states.append(ens.read())
@@ -97,7 +99,10 @@ def test_step_graph_ensemble_equals_launch_by_launch():
         out.append((reps, states, res))
     (rg, sg, qg), (rh, sh, qh) = out
     assert all(r["step_graph"] == 1 for r in rg) and all(r["step_graph"] == 0 for r in rh)
-    for k in range(5):
+    assert [r["list_gathered"] for r in rg] == [r["list_gathered"] for r in rh]
+    if list_every > 1:
+        assert 0 in [r["list_gathered"] for r in rg]
+    for k in range(nsteps):
         assert np.array_equal(qg[k], qh[k])
         assert rg[k]["cg_iters"] == rh[k]["cg_iters"]
         for a, b in zip(sg[k], sh[k]):
