@@ -377,7 +377,7 @@ def run_gb300(args):
         sc5 = scenes.sloshing_3d(seed=args.seed + rank)
         dt5 = 5e-5
         sim5 = mps.Simulation(sc5, torch_alloc=True, use_torch_stream=True, precision=0,
-                              dt=dt5, cg_tol=1e-8)
+                              dt=dt5, cg_tol=1e-8, step_graph=common["step_graph"])
         force = lambda t: (float(scenes.sloshing_forcing(t * dt5)), 0.0, -9.81)
         for t in range(args.warmup):
             sim5.set_gravity(force(t))
