@@ -424,6 +424,9 @@ int regrid(Ctx* c, double skin) {
     c->prm.cell_skin = skin;
     int rc = setup(c, sc, c->n_scenes);
     if (rc) return restore(rc);
+    // smaller cells need no fewer candidate slots than the lists already have: keep the
+    // allocated capacity (headroom for compressed regions at no cost)
+    c->cap_v = std::max(c->cap_v, c->cap_v_alloc);
     int32_t* vl_col = nullptr;
     uint32_t *cell_count = nullptr, *scan_scratch = nullptr;
     int32_t* cell_start = nullptr;
