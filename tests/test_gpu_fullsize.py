@@ -89,13 +89,15 @@ def oracle_trajectory(scene):
     return prm, out
 
 
-def _gpu_trajectory(scene, **kw):
+def _gpu_trajectory(scene, tune_after=None, **kw):
     from paper_2105_01677_gb300 import mps
     sim = mps.Simulation(scene, torch_alloc=True, use_torch_stream=True,
                          **gpu_params(scene, dt=5e-5, **kw))
     states, reps = [], []
     try:
-        for _ in range(TRAJ_STEPS):
+        for k in range(TRAJ_STEPS):
+            if tune_after is not None and k == tune_after:
+                sim.tuning = sim.autotune(1)
             _, rep = sim.step(1)
             reps.append(rep)
             states.append(sim.read())
@@ -124,6 +126,28 @@ def test_fullsize_mixed_trajectory_with_quadratic_guess(scene, oracle_trajectory
         assert np.array_equal(got[k]["flags"][~band], ref[k].flags[~band]), k
     # the guess is used from the second step on: fewer inner iterations than the cold start
     assert min(r["cg_iters"] for r in reps[2:]) < reps[0]["cg_iters"]
+
+
+def test_fullsize_mixed_trajectory_tuned(scene, oracle_trajectory):
+    """The benchmarked configuration: two steps, the autotuner (cell side, gather and build
+    blocks, threads per prediction row, SpMV block, inner-CG form and unrolling), three more
+    steps; every step within the mixed bound of the oracle's trajectory (the tuned choices
+    change the order of sums, not the method), the FP64 residual <= 1e-8 each step."""
+    prm, ref = oracle_trajectory
+    got, reps = _gpu_trajectory(scene, tune_after=2, precision=1, cg_tol=1e-8, cg_x0=3)
+    f = scene.types == scenes.FLUID
+    n0, _ = oracle.lattice(3, scene.l0, 2.1 * scene.l0)
+    for k in range(TRAJ_STEPS):
+        assert reps[k]["cg_resid"] <= 1e-8
+        ep = np.linalg.norm(got[k]["p"][f] - ref[k].p[f]) / np.linalg.norm(ref[k].p[f])
+        ex = np.abs(got[k]["pos"] - ref[k].pos).max() / scene.l0
+        assert ep <= 1e-5, (k, ep)
+        assert ex <= 1e-6, (k, ex)
+        band = np.abs(ref[k].nstar - prm.beta * n0) <= 1e-7 * n0
+        assert np.array_equal(got[k]["flags"][~band], ref[k].flags[~band]), k
+    # the steps after tuning ran as one graph each, the bucket build merging its movers
+    assert all(r["step_graph"] == 1 for r in reps[2:])
+    assert all(r["bucket_merged"] == 1 for r in reps[3:])
 
 
 def test_fullsize_fp64_trajectory_with_quadratic_guess(scene, oracle_trajectory):
