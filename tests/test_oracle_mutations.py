@@ -55,6 +55,11 @@ MUTATIONS = [
     ("CMPS: p_hat_j replaced by p_hat_i", "((p[i] + p[j]) - (phat[i] + phat[j]))",
      "((p[i] + p[j]) - (phat[i] + phat[i]))"),
     ("HS: sign of Dn/Dt", "        out[i] = -s;", "        out[i] = s;"),
+    ("p_hat: dummies taken into the minimum",
+     "                if (type[j] != ORC_DUMMY && pres[j] < m) m = pres[j];\n"
+     "            }\n            phat[i] = m;\n        }\n    } else {",
+     "                if (pres[j] < m) m = pres[j];\n"
+     "            }\n            phat[i] = m;\n        }\n    } else {"),
     ("ECS: signed density deviation", "            double ecs = fabs(eps) * (dk[i] / n0)",
      "            double ecs = eps * (dk[i] / n0)"),
     ("adjoint: sign of the PPE coefficient cotangent",

@@ -364,6 +364,46 @@ def test_walls_and_dummies_do_not_move():
     assert np.array_equal(st.pos[b], sc.pos[b]) and np.all(st.vel[b] == 0.0)
 
 
+def test_step_p_hat_is_minimum_over_non_dummy_neighbours():
+    """The stabilising p_hat_i of the gradient (Eq. 14 with p_hat) is the minimum of p over i
+    and its neighbours within re, dummies left out.  A block compressed to 0.98 l0 on a
+    wall row with two dummy rows below, no gravity, viscosity or initial velocity: u* = 0,
+    r* = r, and after the step u = -(dt/rho) grad p with p_hat taken here by brute force.
+    The bottom fluid row has dummies (p = 0) at 1.96 l0 < re, so p_hat with the dummies in
+    would differ (checked below)."""
+    l0 = 0.01
+    s = 0.98 * l0
+    rows = []
+    for k, kind in [(-2, oracle.DUMMY), (-1, oracle.DUMMY), (0, oracle.WALL)]:
+        rows += [(x, k * s, kind) for x in np.arange(-4, 20) * s]
+    for j in range(1, 9):
+        rows += [(x, j * s, oracle.FLUID) for x in np.arange(16) * s]
+    a = np.array(rows)
+    pos, t = a[:, :2] + 0.1, a[:, 2].astype(np.int8)
+    sc = scenes.Scene(2, l0, pos, np.zeros_like(pos), t, np.zeros(3), np.array([0.5, 0.5, 0.0]))
+    prm = oracle.params_for(sc, g=(0.0, 0.0, 0.0), nu=0.0)
+    st = oracle.State.from_scene(sc)
+    oracle.step(prm, st)
+    re = prm.re_n
+    d2 = ((pos[:, None, :] - pos[None, :, :]) ** 2).sum(-1)
+    nbr = (d2 < re * re) & ~np.eye(len(pos), dtype=bool)
+
+    def p_hat(mask):
+        return np.array([min(st.p[i], st.p[nbr[i] & mask].min(initial=np.inf))
+                         for i in range(len(pos))])
+
+    ph = p_hat(t != oracle.DUMMY)
+    ph_with_dummies = p_hat(np.ones(len(pos), bool))
+    f = t == oracle.FLUID
+    assert np.count_nonzero(f & (ph != ph_with_dummies)) >= 8
+    n0, _ = oracle.lattice(2, l0, re)
+    u = -(prm.dt / prm.rho) * oracle.gradient(2, pos, t, re, n0, st.p, ph)
+    u_with_dummies = -(prm.dt / prm.rho) * oracle.gradient(2, pos, t, re, n0, st.p,
+                                                             ph_with_dummies)
+    np.testing.assert_allclose(st.vel[f], u[f], rtol=1e-12, atol=1e-12 * np.abs(u[f]).max())
+    assert np.abs(u_with_dummies[f] - u[f]).max() > 1e-3 * np.abs(u[f]).max()
+
+
 # ---------------------------------------------------------------- error statuses
 def test_error_statuses():
     sc = scenes.dam_break_2d(seed=1)
