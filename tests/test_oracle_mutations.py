@@ -60,6 +60,11 @@ MUTATIONS = [
      "            }\n            phat[i] = m;\n        }\n    } else {",
      "                if (pres[j] < m) m = pres[j];\n"
      "            }\n            phat[i] = m;\n        }\n    } else {"),
+    ("p_hat: the particle's own p_i left out of the minimum",
+     "                if (pres[i] < 0.0) pres[i] = 0.0;\n        for (int64_t i = 0; i < n; i++) {\n"
+     "            double m = pres[i];",
+     "                if (pres[i] < 0.0) pres[i] = 0.0;\n        for (int64_t i = 0; i < n; i++) {\n"
+     "            double m = HUGE_VAL;"),
     ("ECS: signed density deviation", "            double ecs = fabs(eps) * (dk[i] / n0)",
      "            double ecs = eps * (dk[i] / n0)"),
     ("adjoint: sign of the PPE coefficient cotangent",
