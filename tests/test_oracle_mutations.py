@@ -55,6 +55,60 @@ MUTATIONS = [
     ("CMPS: p_hat_j replaced by p_hat_i", "((p[i] + p[j]) - (phat[i] + phat[j]))",
      "((p[i] + p[j]) - (phat[i] + phat[i]))"),
     ("HS: sign of Dn/Dt", "        out[i] = -s;", "        out[i] = s;"),
+    ("gradient: 1/n0 for d/n0",
+     "        for (int a = 0; a < dim; a++) out[i * dim + a] = ((double)dim / n0) * s[a];",
+     "        for (int a = 0; a < dim; a++) out[i * dim + a] = (1.0 / n0) * s[a];"),
+    ("PPE: surface neighbours left off the diagonal (p_j = 0 not imposed)",
+     "            diag = diag + c;\n            if (in_ppe(type, flags, j)) {\n"
+     "                A->col[k] = (int32_t)j;",
+     "            if (in_ppe(type, flags, j)) {\n                diag = diag + c;\n"
+     "                A->col[k] = (int32_t)j;"),
+    ("PPE: dummy neighbours taken as coefficients",
+     "            if (type[j] == ORC_DUMMY) continue;\n            double xj, yj, zj;\n"
+     "            coords(pos, dim, j, &xj, &yj, &zj);\n"
+     "            double w = weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), p->re_lap, p->kernel);",
+     "            double xj, yj, zj;\n"
+     "            coords(pos, dim, j, &xj, &yj, &zj);\n"
+     "            double w = weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), p->re_lap, p->kernel);"),
+    ("predict: r* from the old velocity", "                    ps[q] = pos[q] + p->dt * us[q];",
+     "                    ps[q] = pos[q] + p->dt * vel[q];"),
+    ("free surface: walls never on it",
+     "        int surf = (type[i] == ORC_FLUID || type[i] == ORC_WALL) && nstar[i] <",
+     "        int surf = (type[i] == ORC_FLUID) && nstar[i] <"),
+    ("number density: dummies left out",
+     "                coords(pos, dim, j, &xj, &yj, &zj);\n"
+     "                s = s + weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), re, kernel);",
+     "                if (type[j] == ORC_DUMMY) continue;\n"
+     "                coords(pos, dim, j, &xj, &yj, &zj);\n"
+     "                s = s + weight(sqrt(dist2(xj - xi, yj - yi, zj - zi)), re, kernel);"),
+    ("equation of state: surface particles keep their pressure",
+     "            pres[i] = in_ppe(type, flags, i) ? wc_pressure(p, rho_of(p, i), nstar[i], n0)"
+     " : 0.0;\n            phat[i] = pres[i];",
+     "            pres[i] = (type[i] == ORC_FLUID || type[i] == ORC_WALL) ?"
+     " wc_pressure(p, rho_of(p, i), nstar[i], n0) : 0.0;\n            phat[i] = pres[i];"),
+    ("two-phase: correction with the reference density",
+     "                double du = -(p->dt / rho_of(p, i)) * grad[q];",
+     "                double du = -(p->dt / p->rho) * grad[q];"),
+    ("ghost: velocity kept",
+     "                for (int a = 0; a < p->dim; a++) vel[i * p->dim + a] = 0.0;", ""),
+    ("Dn/Dt: one power of r dropped", "                s = s + p->re_n / (r2 * r) * dot;",
+     "                s = s + p->re_n / r2 * dot;"),
+    ("HS: ECS without its first term",
+     "            double ecs = fabs(eps) * (dk[i] / n0) + fabs(p->dt * dk[i] / n0) * (eps / p->dt);",
+     "            double ecs = fabs(p->dt * dk[i] / n0) * (eps / p->dt);"),
+    ("HS: dt missing in b", "        double v = dstar[i] / (n0 * p->dt);",
+     "        double v = dstar[i] / n0;"),
+    ("clamp ignored on the step",
+     "        if (p->clamp_negative_p)\n            for (int64_t i = 0; i < n; i++)\n"
+     "                if (pres[i] < 0.0) pres[i] = 0.0;\n"
+     "        for (int64_t i = 0; i < n; i++) {\n            double m = pres[i];",
+     "        for (int64_t i = 0; i < n; i++) {\n            double m = pres[i];"),
+    ("PPE right-hand side: n0 of the Laplacian",
+     "            ppe_rhs(p, n, type, flags, nstar, n0, bvec);\n        }\n        rc = cg_solve",
+     "            ppe_rhs(p, n, type, flags, nstar, R.n0_lap, bvec);\n        }\n        rc = cg_solve"),
+    ("viscosity: n0 of the number density for that of the Laplacian",
+     "laplacian_from(dim, n, pos, type, p->re_lap, p->kernel, R->n0_lap, R->lambda, &nb, vel,",
+     "laplacian_from(dim, n, pos, type, p->re_lap, p->kernel, R->n0_pnd, R->lambda, &nb, vel,"),
     ("p_hat: dummies taken into the minimum",
      "                if (type[j] != ORC_DUMMY && pres[j] < m) m = pres[j];\n"
      "            }\n            phat[i] = m;\n        }\n    } else {",
