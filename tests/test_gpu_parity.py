@@ -273,6 +273,66 @@ def test_particle_leaving_grid_becomes_ghost():
     assert np.all(got["vel"][7] == 0.0)
 
 
+def _lattice_block(dim, m, spacing, origin):
+    g = np.meshgrid(*[np.arange(k) for k in m], indexing="ij")
+    return np.stack([a.reshape(-1) for a in g], axis=1).astype(np.float64) * spacing + origin
+
+
+def _mixed_bound(sc, got, ost):
+    f = sc.types == scenes.FLUID
+    assert np.linalg.norm(got["p"][f] - ost.p[f]) <= 1e-5 * np.linalg.norm(ost.p[f])
+    assert np.abs(got["pos"] - ost.pos).max() <= 1e-6 * sc.l0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fluid_block_without_walls(dim, precision):
+    """Degenerate scene: FLUID only, no walls or dummies, a block compressed to 0.98 l0 in
+    free fall.  Every row of the PPE is a FLUID row; its surface rows (1/4 of the particles in
+    2D, more than half in 3D) are the only Dirichlet conditions."""
+    l0 = 0.01
+    pos = _lattice_block(dim, (20, 12) if dim == 2 else (8, 8, 8), 0.98 * l0, 0.2)
+    box = np.array([1.0, 1.0, 1.0 if dim == 3 else 0.0])
+    sc = scenes.Scene(dim, l0, pos, np.zeros_like(pos), np.zeros(len(pos), np.int8),
+                      np.zeros(3), box)
+    tol = PARITY_CG_TOL if precision == 0 else 1e-8
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc, precision=precision, cg_tol=tol))
+    orep, ost, prm = run_oracle(sc, cg_tol=PARITY_CG_TOL)
+    assert orep["n_ppe_rows"] > 0 and ost.p.max() > 0.0
+    assert rep["n_ppe_rows"] == orep["n_ppe_rows"] and rep["n_surface"] == orep["n_surface"]
+    if precision == 0:
+        compare_step(sc, got, ost, prm)
+    else:
+        _mixed_bound(sc, got, ost)
+        assert np.array_equal(got["flags"], ost.flags)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_walls_and_dummies_only(dim, precision):
+    """Degenerate scene: the dam-break tank with its fluid taken out.  The PPE still has
+    rows (wall particles backed by dummies on two sides, n* between beta n0 and n0), with a
+    negative right-hand side: with the clamp off their pressure is negative and compared;
+    nothing moves."""
+    full = scenes.dam_break_2d(seed=1) if dim == 2 else small_3d(seed=1)
+    keep = full.types != scenes.FLUID
+    sc = scenes.Scene(dim, full.l0, full.pos[keep].copy(), full.vel[keep].copy(),
+                      full.types[keep].copy(), full.box_min, full.box_max)
+    tol = PARITY_CG_TOL if precision == 0 else 1e-8
+    rc, rep, got, _ = run_gpu(sc, **gpu_params(sc, precision=precision, cg_tol=tol,
+                                               clamp_negative_p=0))
+    orep, ost, prm = run_oracle(sc, cg_tol=PARITY_CG_TOL, clamp_negative_p=0)
+    assert orep["n_ppe_rows"] > 0 and ost.p.min() < 0.0
+    assert rep["n_ppe_rows"] == orep["n_ppe_rows"]
+    assert np.array_equal(got["pos"], sc.pos) and np.all(got["vel"] == 0.0)
+    assert np.array_equal(got["flags"], ost.flags)
+    if precision == 0:
+        compare_step(sc, got, ost, prm, fields=("p", "n_star"))
+    else:
+        w = ost.types == scenes.WALL
+        assert np.linalg.norm(got["p"][w] - ost.p[w]) <= 1e-5 * np.linalg.norm(ost.p[w])
+
+
 @pytest.mark.parametrize("case", ["coincident", "noconv", "skin", "cap"])
 def test_error_statuses(case):
     mps = _mps()
