@@ -102,6 +102,52 @@ def test_ensemble_scenes_do_not_interact_and_ghosts_per_scene():
     assert got[1]["types"][0] == scenes.GHOST
 
 
+def _degenerate_scenes():
+    """A normal dam break beside a lone particle, the tank without its fluid, a compressed
+    fluid block without walls and a scene whose particles are all GHOST."""
+    l0 = 0.01
+    normal = scenes.dam_break_2d(seed=3)
+    lone = scenes.Scene(2, l0, np.array([[0.3, 0.3]]), np.array([[0.2, -0.1]]),
+                        np.zeros(1, np.int8), np.zeros(3), np.array([1.0, 1.0, 0.0]))
+    full = scenes.dam_break_2d(seed=1)
+    keep = full.types != scenes.FLUID
+    walls = scenes.Scene(2, l0, full.pos[keep].copy(), full.vel[keep].copy(),
+                         full.types[keep].copy(), full.box_min, full.box_max)
+    g = np.meshgrid(np.arange(20), np.arange(12), indexing="ij")
+    blk = np.stack([a.reshape(-1) for a in g], axis=1).astype(np.float64) * (0.98 * l0) + 0.2
+    block = scenes.Scene(2, l0, blk, np.zeros_like(blk), np.zeros(len(blk), np.int8),
+                         np.zeros(3), np.array([1.0, 1.0, 0.0]))
+    ghosts = scenes.dam_break_2d(seed=5)
+    ghosts.types[:] = scenes.GHOST
+    return [normal, lone, walls, block, ghosts]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ensemble_with_degenerate_scenes(precision):
+    """Each scene of the ensemble matches the oracle of that scene alone, and each PPE is
+    solved to its own tolerance, whether it has rows with a nonzero right-hand side (the
+    dam break, the wall-less block), rows with a negative one (the walls), or none at all
+    (the lone particle, the GHOST scene)."""
+    E = _degenerate_scenes()
+    tol = PARITY_CG_TOL if precision == 0 else 1e-8
+    rep, got, res = _run(E, precision=precision, cg_tol=tol)
+    assert np.all(res <= tol)
+    for k, (sc, g) in enumerate(zip(E, got)):
+        prm, ost = _oracle(sc, cg_tol=PARITY_CG_TOL)
+        if k == 4:
+            assert np.array_equal(g["pos"], sc.pos) and np.all(g["types"] == scenes.GHOST)
+            continue
+        if precision == 0:
+            compare_step(sc, g, ost, prm)
+            continue
+        f = sc.types == scenes.FLUID
+        if ost.p[f].size and np.linalg.norm(ost.p[f]) > 0:
+            ep = np.linalg.norm(g["p"][f] - ost.p[f]) / np.linalg.norm(ost.p[f])
+            assert ep <= 1e-5, (k, ep)
+        assert np.abs(g["pos"] - ost.pos).max() / sc.l0 <= 1e-6, k
+        assert np.array_equal(g["flags"], ost.flags), k
+
+
 def test_ensemble_multi_step_mixed_runs_and_converges():
     E = _ensemble(count=12, seed=6)
     rep, got, res = _run(E, nsteps=10, precision=1, cg_tol=1e-8)
