@@ -125,6 +125,29 @@ def test_vjp_ghosts_match_oracle():
     assert np.all(gu[f[0]] == 0.0) and np.array_equal(gu[f[1]], gvel[f[1]])
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_vjp_fluid_block_without_walls_matches_oracle(dim):
+    """Degenerate scene for the reverse step: FLUID only (no walls, no dummies), a block
+    compressed to 0.98 l0 with seeded jitter and velocities, so that every PPE row is a
+    FLUID row and the surface rows are the only Dirichlet conditions."""
+    l0 = 0.01
+    m = (14, 10) if dim == 2 else (7, 6, 6)
+    g = np.meshgrid(*[np.arange(k) for k in m], indexing="ij")
+    pos = np.stack([a.reshape(-1) for a in g], axis=1).astype(np.float64) * (0.98 * l0) + 0.2
+    u = scenes.splitmix_uniform(5, np.arange(2 * pos.size, dtype=np.uint64))
+    pos = pos + 0.05 * l0 * (u[: pos.size].reshape(pos.shape) - 0.5)
+    vel = 0.2 * (u[pos.size:].reshape(pos.shape) - 0.5)
+    box = np.array([1.0, 1.0, 1.0 if dim == 3 else 0.0])
+    sc = scenes.Scene(dim, l0, pos, vel, np.zeros(len(pos), np.int8), np.zeros(3), box)
+    gpos, gvel = _cotangents(sc, seed=2)
+    gr, gu, gg, rep, st = _gpu_vjp(sc, gpos, gvel, cg_tol=CG)
+    prm = oracle_params(sc, cg_tol=CG)
+    ogr, ogu, ogg = oracle.step_vjp(prm, oracle.State.from_scene(sc), gpos, gvel)
+    _close(gr, ogr, what="pos")
+    _close(gu, ogu, what="vel")
+    _close(gg, ogg, what="g")
+
+
 def test_vjp_mixed_precision_bound():
     """Mixed precision repeats the forward step in its own arithmetic and solves the adjoint
     PPE with the mixed solver to the same FP64 residual; the cotangents stay within the
