@@ -49,7 +49,8 @@ UNIT = "particle-steps/s"
 # the PPE's initial guess (cg_x0); the stop rule is the same FP64 residual either way
 X0_NAMES = {0: "zero", 1: "previous step's solution (before the clamp)",
             2: "linear extrapolation of the last 2 solutions",
-            3: "quadratic extrapolation of the last 3 solutions"}
+            3: "quadratic extrapolation of the last 3 solutions",
+            4: "cubic extrapolation of the last 4 solutions"}
 WORKLOAD = "3D dam break, 0.40x0.60x0.30 m column in 1.6x0.6x0.6 m tank, l0=0.0075 m"
 
 # Whole-step algorithmic bytes per particle (matrix-free minimum: every array read or
@@ -129,9 +130,10 @@ def parse():
                     help="cell skin s at creation (the autotuner may choose another)")
     ap.add_argument("--ppe-host-loop", action="store_true",
                     help="drive the mixed PPE solve from the host (profiling: identical results)")
-    ap.add_argument("--cg-x0", type=int, default=3, choices=[0, 1, 2, 3],
-                    help="PPE initial guess: 0 zero, 1 the previous step's solution, 2 / 3 "
-                         "its linear / quadratic extrapolation (default 3); the full run also "
+    ap.add_argument("--cg-x0", type=int, default=3, choices=[0, 1, 2, 3, 4],
+                    help="PPE initial guess: 0 zero, 1 the previous step's solution, 2 / 3 / 4 "
+                         "its linear / quadratic / cubic extrapolation (default 3); the full run "
+                         "also "
                          "times the mixed step with each of the others")
     ap.add_argument("--stiff-steps", type=int, default=10,
                     help="timed steps of the stiff PPE (alpha_c = 0) comparison (0: skip)")

@@ -119,8 +119,9 @@ typedef struct {
                                * Results are identical.                                        */
     int32_t cg_x0;            /* PPE initial guess from the previous steps' solutions before  *
                                * the clamp (carried with the particles): 0 (default) x0 = 0;  *
-                               * 1 the previous solution; 2 its linear, 3 its quadratic       *
-                               * extrapolation in time from the last 2 or 3 solutions (lower  *
+                               * 1 the previous solution; 2 its linear, 3 its quadratic, 4    *
+                               * its cubic extrapolation in time from the last 2, 3 or 4      *
+                               * solutions (the polynomial through them at equal steps; lower *
                                * orders while fewer exist; none before the first solve and    *
                                * after mps_write_state).  The stop rule is unchanged (FP64    *
                                * ||b - A p|| / ||b|| <= cg_tol); a step then depends on the   *

@@ -157,7 +157,7 @@ int check_params(const mps_params* P) {
     if ((P->alloc == nullptr) != (P->release == nullptr)) return MPS_EINVAL;
     if (P->list_every < 0) return MPS_EINVAL;
     if (P->ppe_host_loop != 0 && P->ppe_host_loop != 1) return MPS_EINVAL;
-    if (P->cg_x0 < 0 || P->cg_x0 > 3) return MPS_EINVAL;
+    if (P->cg_x0 < 0 || P->cg_x0 > 4) return MPS_EINVAL;
     if (P->inner_cg < 0 || P->inner_cg > 1) return MPS_EINVAL;
     if (P->spmv_block != 0 && P->spmv_block != 256 && P->spmv_block != 512) return MPS_EINVAL;
     if (P->build_block != 0 && P->build_block != 64 && P->build_block != 128 &&

@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(kBT)
 
 // the previous PPE solutions (cg_x0 >= 1) follow their particles
 struct GuessPerm {
-    const double* in[3];
-    double* out[3];
+    const double* in[Ctx::kGuessMax];
+    double* out[Ctx::kGuessMax];
     int m;
 };
 
@@ -598,7 +598,8 @@ struct BucketPtrs {
 BucketPtrs save_ptrs(const Ctx* c) {
     return {c->key, c->key_alt, c->perm, c->perm_alt, c->pos, c->pos_alt, c->vel, c->vel_alt,
             c->type, c->type_alt, c->id, c->id_alt, c->p, c->p_alt,
-            {c->ph[0], c->ph[1], c->ph[2]}, {c->ph_alt[0], c->ph_alt[1], c->ph_alt[2]}};
+            {c->ph[0], c->ph[1], c->ph[2], c->ph[3]},
+            {c->ph_alt[0], c->ph_alt[1], c->ph_alt[2], c->ph_alt[3]}};
 }
 void load_ptrs(Ctx* c, const BucketPtrs& b) {
     c->key = b.key; c->key_alt = b.key_alt; c->perm = b.perm; c->perm_alt = b.perm_alt;

@@ -83,7 +83,7 @@ struct CgScalars {
     double inner_tol;
     int outer, total, max_outer, max_total;
     int guard_in, guard_out;
-    double gw[3];      // initial guess x0 = sum_k gw[k] ph[k] (cg_x0 >= 1)
+    double gw[4];      // initial guess x0 = sum_k gw[k] ph[k] (cg_x0 >= 1)
 };
 
 struct GridDesc {
@@ -387,7 +387,7 @@ struct Ctx {
     double *p, *p_alt;
     // cg_x0 >= 1: the last guess_m solutions before the clamp (ph[0] the latest), of which
     // guess_n are valid (0 before the first solve and after a written state)
-    static constexpr int kGuessMax = 3;
+    static constexpr int kGuessMax = 4;
     double* ph[kGuessMax] = {};
     double* ph_alt[kGuessMax] = {};
     int guess_m = 0, guess_n = 0;

@@ -435,21 +435,22 @@ __global__ void __launch_bounds__(kBT) k_bnorm64(SellView c, CgScalars* cg, doub
 
 // second kernel: x = x0 on the rows of the system, 0 elsewhere (and everywhere when b = 0,
 // whose solution is 0), with its float-float copy; r = b - A x follows (k_resid64_t or
-// k_resid_ff_t).  x0 = sum_k gw[k] h_k over the previous solutions h_0 (latest), h_1, h_2:
-// the previous one (weights 1), or its linear (2, -1) or quadratic (3, -3, 1) extrapolation
-// in time; a zero weight reads nothing
+// k_resid_ff_t).  x0 = sum_k gw[k] h_k over the previous solutions h_0 (latest) to h_3:
+// the previous one (weights 1), or its linear (2, -1), quadratic (3, -3, 1) or cubic
+// (4, -6, 4, -1) extrapolation in time; a zero weight reads nothing
 __global__ void __launch_bounds__(kBT) k_guess(int n, double* x, const double* h0,
                                                const double* h1, const double* h2,
-                                               const double* diag, float2* xhl,
-                                               const CgScalars* cg) {
+                                               const double* h3, const double* diag,
+                                               float2* xhl, const CgScalars* cg) {
     const bool any = cg->bb > 0.0;
-    const double w0 = cg->gw[0], w1 = cg->gw[1], w2 = cg->gw[2];
+    const double w0 = cg->gw[0], w1 = cg->gw[1], w2 = cg->gw[2], w3 = cg->gw[3];
     for (int i = blockIdx.x * kBT + threadIdx.x; i < n; i += gridDim.x * kBT) {
         double v = 0.0;
         if (any && diag[i] != 0.0) {
             if (w0 != 0.0) v = w0 * h0[i];
             if (w1 != 0.0) v = fma(w1, h1[i], v);
             if (w2 != 0.0) v = fma(w2, h2[i], v);
+            if (w3 != 0.0) v = fma(w3, h3[i], v);
         }
         x[i] = v;
         if (xhl) {
@@ -729,12 +730,15 @@ static int read_scalars(Ctx* c) {
 }
 
 // Weights of the initial guess over the previous solutions: the highest order the valid
-// history allows, up to cg_x0 (1 previous solution, 2 linear, 3 quadratic extrapolation)
+// history allows, up to cg_x0 (1 previous solution, 2 linear, 3 quadratic, 4 cubic
+// extrapolation: the polynomial through the last m solutions at equal time steps, taken one
+// step further, has the weights (-1)^k C(m, k + 1))
 static void guess_weights(const Ctx* c, double* w) {
-    static const double kW[4][3] = {{0.0, 0.0, 0.0}, {1.0, 0.0, 0.0}, {2.0, -1.0, 0.0},
-                                     {3.0, -3.0, 1.0}};
+    static const double kW[5][4] = {{0.0, 0.0, 0.0, 0.0}, {1.0, 0.0, 0.0, 0.0},
+                                     {2.0, -1.0, 0.0, 0.0}, {3.0, -3.0, 1.0, 0.0},
+                                     {4.0, -6.0, 4.0, -1.0}};
     const int m = std::min(c->guess_n, c->guess_m);
-    for (int k = 0; k < 3; k++) w[k] = kW[m][k];
+    for (int k = 0; k < 4; k++) w[k] = kW[m][k];
 }
 
 static int set_cg_limits(Ctx* c, int max_iters) {
@@ -880,8 +884,8 @@ int add_mixed_solve(Ctx* c, cudaGraph_t G, cudaGraphNode_t dep, double* x, bool 
         // from the previous solution: b.b, x = x0, r = b - A x and the refinement loop's
         // conditional as after a sweep (per scene in an ensemble)
         k_bnorm64<<<gs, kBT, 0, s>>>(sv, c->cg, tol2);
-        k_guess<<<gv, kBT, 0, s>>>(n, x, c->ph[0], c->ph[1], c->ph[2], c->diag, c->cg_xhl,
-                                   c->cg);
+        k_guess<<<gv, kBT, 0, s>>>(n, x, c->ph[0], c->ph[1], c->ph[2], c->ph[3], c->diag,
+                                   c->cg_xhl, c->cg);
         k_resid_ff_t<kBT><<<row_grid(c), kBT, 0, s>>>(sv, x, c->cg_xhl, c->cg_r, c->cg,
                                                       multi ? 0 : h_out);
         if (multi) {
@@ -1129,8 +1133,8 @@ static int solve(Ctx* c, double* x, const double* b, mps_report* rep, bool prima
         // bb = |b|^2, stop2 = tol^2 bb; x = x0; r = b - A x (and d = r, rho = |r|^2 in FP64)
         const SellView sv = sell_view(c, b);
         k_bnorm64<<<gs, kBT, 0, c->stream>>>(sv, c->cg, tol2);
-        k_guess<<<gv, kBT, 0, c->stream>>>(n, x, c->ph[0], c->ph[1], c->ph[2], c->diag,
-                                           c->cg_xhl, c->cg);
+        k_guess<<<gv, kBT, 0, c->stream>>>(n, x, c->ph[0], c->ph[1], c->ph[2], c->ph[3],
+                                           c->diag, c->cg_xhl, c->cg);
         if (c->prm.precision == 0)
             k_resid64_t<<<gs, kBT, 0, c->stream>>>(sv, x, c->cg_r, c->cg_d, c->cg, tol2, 0, 1);
         else

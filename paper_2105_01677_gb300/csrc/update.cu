@@ -34,9 +34,10 @@ __global__ void __launch_bounds__(kBT)
 
 // the guess history of the PPE: h_2 <- h_1, h_1 <- h_0, h_0 <- p (as many as are kept)
 __global__ void __launch_bounds__(kBT) k_push_history(int n, int m, double* h0, double* h1,
-                                                      double* h2, const double* p) {
+                                                      double* h2, double* h3, const double* p) {
     const int i = blockIdx.x * kBT + threadIdx.x;
     if (i >= n) return;
+    if (m >= 4) h3[i] = h2[i];
     if (m >= 3) h2[i] = h1[i];
     if (m >= 2) h1[i] = h0[i];
     h0[i] = p[i];
@@ -310,7 +311,7 @@ static bool phat_inline(const Ctx* c) { return c->prm.gradient_form == 0 && !c->
 void launch_push_history(Ctx* c) {
     const int n = (int)c->n;
     k_push_history<<<(n + kBT - 1) / kBT, kBT, 0, c->stream>>>(n, c->guess_m, c->ph[0], c->ph[1],
-                                                               c->ph[2], c->p);
+                                                               c->ph[2], c->ph[3], c->p);
     c->launches += 1;
 }
 

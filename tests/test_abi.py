@@ -120,7 +120,7 @@ def test_invalid_arguments_rejected_before_device_use(L):
     for kw in (dict(dim=4), dict(re_n=0.0), dict(dt=-1.0), dict(precision=2),
                dict(box_max=(0.0, 0.0, 0.0)), dict(list_every=-1), dict(kernel=2),
                dict(gradient_form=3), dict(source_term=1, kernel=1), dict(source_term=3),
-               dict(precision=1, ppe_operator=1, kernel=1), dict(cg_x0=4), dict(cg_x0=-1), dict(ppe_host_loop=2),
+               dict(precision=1, ppe_operator=1, kernel=1), dict(cg_x0=5), dict(cg_x0=-1), dict(ppe_host_loop=2),
                dict(build_block=96), dict(build_block=512), dict(spmv_block=128),
                dict(gather_block=48), dict(bucket_sort=2), dict(cg_unroll=3), dict(predict_tpr=3),
                dict(step_graph=3)):

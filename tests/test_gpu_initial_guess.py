@@ -68,7 +68,7 @@ def test_guess_trajectory_matches_oracle(scene, x0):
     assert rep["cg_resid"] <= PARITY_CG_TOL
 
 
-@pytest.mark.parametrize("precision,x0", [(0, 1), (1, 1), (1, 2), (1, 3), (0, 3)])
+@pytest.mark.parametrize("precision,x0", [(0, 1), (1, 1), (1, 2), (1, 3), (0, 3), (1, 4), (0, 4)])
 def test_guess_agrees_with_cold_start_and_cuts_iterations(precision, x0):
     sc = small_3d(seed=3)
     kw = dict(precision=precision, dt=5e-5, cg_tol=1e-8)
@@ -84,7 +84,7 @@ def test_guess_agrees_with_cold_start_and_cuts_iterations(precision, x0):
     assert np.array_equal(sw_["flags"], sc_["flags"])
 
 
-@pytest.mark.parametrize("scene,nsteps,x0", [("2d", 5, 1), ("3d", 3, 1), ("2d", 5, 3)])
+@pytest.mark.parametrize("scene,nsteps,x0", [("2d", 5, 1), ("3d", 3, 1), ("2d", 5, 3), ("2d", 6, 4)])
 def test_graph_equals_host_loop_with_guess(scene, nsteps, x0):
     sc = _scene(scene)
     dt = 1e-4 if sc.dim == 2 else 5e-5
@@ -174,12 +174,13 @@ def test_writing_back_the_same_state_changes_nothing():
 @pytest.mark.parametrize("precision", [0, 1])
 def test_short_history_uses_the_lower_orders(precision):
     """With k solutions in the history the guess is of order min(k, cg_x0): the first two
-    steps of cg_x0 = 2 are those of cg_x0 = 1 and the first three of cg_x0 = 3 are those of
-    cg_x0 = 2, bit for bit (the same weights over the same buffers); the next step differs."""
+    steps of cg_x0 = 2 are those of cg_x0 = 1, the first three of cg_x0 = 3 those of
+    cg_x0 = 2 and the first four of cg_x0 = 4 those of cg_x0 = 3, bit for bit (the same
+    weights over the same buffers); the next step differs."""
     sc = small_3d(seed=4)
     kw = dict(precision=precision, dt=5e-5)
-    runs = {x0: _steps(sc, k, cg_x0=x0, **kw) for x0, k in ((1, 3), (2, 4), (3, 4))}
-    for lo, hi, same in ((1, 2, 2), (2, 3, 3)):
+    runs = {x0: _steps(sc, k, cg_x0=x0, **kw) for x0, k in ((1, 3), (2, 4), (3, 5), (4, 5))}
+    for lo, hi, same in ((1, 2, 2), (2, 3, 3), (3, 4, 4)):
         a, b = runs[lo][0], runs[hi][0]
         for t in range(same):
             assert (a[t]["cg_iters"], a[t]["cg_resid"]) == (b[t]["cg_iters"], b[t]["cg_resid"]), (lo, hi, t)
